@@ -1,0 +1,125 @@
+"""One time step of the coupled solver (Sec. 4.2, full time-stepping scheme).
+
+Oracle (test infrastructure only).
+
+For cycles k = 0 .. n_cycles-1 (the paper uses n_cycles = 2):
+  1. advect phi with u^{n+1/2,k}; rebuild psi from the markers' centre of
+     mass; cell and edge viscosity mu^{n+1,k+1} from (phi, psi)^{n+1,k+1};
+  2. SSP-RK3 face density rho^{n+1,k+1} and the consistent convective term C
+     from rho^n (level sets at t^n averaged onto faces);
+     right-hand side  b = rho^n u^n/dt - C + (1-theta) L_mu^n u^n + rho_g g
+     with rho_g = rho^flow(phi^{n+1,k+1}) on faces (well-balanced gravity,
+     Sec. 5, for fully prescribed bodies) or rho^{n+1,k+1} (full gravity);
+     solve  rho^{n+1,k+1}/dt u~ - theta L_mu u~ + G p = b,  -D u~ = 0;
+  3. rigidity projection at X^{n+1/2,k} and the position update.
+At k = 0: u^{n+1,0} = u^n, X^{n+1,0} = X^n.  At n = 0: u^{-1} = u^0.
+"""
+import numpy as np
+
+from . import levelset, rigid, transport
+from .grid import Grid
+from .materials import Materials, face_average, flow_only
+from .operators import strain_rate_apply
+from .solve import solve_stokes
+
+
+class Props:
+    def __init__(self, rho_l=1000.0, rho_g=1.2, rho_s=1000.0, mu_l=1e-3, mu_g=1.8e-5, mu_s=None,
+                 n_cells=2.0, gravity=(0.0, 0.0, -9.81), gravity_mode="flow", theta=0.5):
+        self.rho_l, self.rho_g, self.rho_s = rho_l, rho_g, rho_s
+        self.mu_l, self.mu_g = mu_l, mu_g
+        self.mu_s = max(mu_l, mu_g) if mu_s is None else mu_s
+        self.n_cells = n_cells
+        self.gravity = np.asarray(gravity, dtype=np.float64)
+        self.gravity_mode = gravity_mode
+        self.theta = theta
+
+
+class Body:
+    def __init__(self, X, dV, lock, U_pres=(0, 0, 0), W_pres=(0, 0, 0), half=None):
+        self.X = np.array(X, dtype=np.float64)
+        self.dV = float(dV)
+        self.lock = np.asarray(lock, dtype=bool)
+        self.U_pres = np.asarray(U_pres, dtype=np.float64)
+        self.W_pres = np.asarray(W_pres, dtype=np.float64)
+        self.half = None if half is None else np.asarray(half, dtype=np.float64)
+        self.Ub = np.zeros_like(self.X)
+        self.Xcom = self.X.mean(axis=0)
+
+
+class State:
+    def __init__(self, g: Grid, props: Props, phi, psi, body=None, vel=None, p=None):
+        self.g = g
+        self.props = props
+        self.phi = np.array(phi, dtype=np.float64)
+        self.psi = np.array(psi, dtype=np.float64)
+        self.body = body
+        self.vel = [np.zeros(g.face_shape(c)) for c in range(3)] if vel is None else [np.array(a) for a in vel]
+        self.vel_old = [a.copy() for a in self.vel]
+        self.p = np.zeros(g.cell_shape) if p is None else np.array(p)
+
+
+def _materials(s: State, phi, psi):
+    pr = s.props
+    return Materials(s.g, phi, psi, pr.rho_l, pr.rho_g, pr.rho_s, pr.mu_l, pr.mu_g, pr.mu_s, pr.n_cells)
+
+
+def step(s: State, dt, n_cycles=2):
+    g, pr = s.g, s.props
+    u_n = [a.copy() for a in s.vel]
+    u_nm1 = [a.copy() for a in s.vel_old]
+    phi_n, psi_n = s.phi.copy(), s.psi.copy()
+    mat_n = _materials(s, phi_n, psi_n)
+    rho_n = mat_n.rho_face
+    Lmu_n = strain_rate_apply(g, mat_n, *u_n)
+    body = s.body
+    X_n = body.X.copy() if body is not None else None
+    Ub_n = body.Ub.copy() if body is not None else None
+    u_k = [a.copy() for a in u_n]
+    phi_k = phi_n.copy()
+    X_k = X_n.copy() if body is not None else None
+    psi_k = psi_n.copy()
+    p = s.p.copy()
+    info = {}
+    for k in range(n_cycles):
+        u_half = [0.5 * (a + b) for a, b in zip(u_k, u_n)]
+        phi_new = levelset.advect(g, u_half, phi_n, 0.5 * (phi_k + phi_n), dt)
+        if body is not None and body.half is not None:
+            psi_new = levelset.box_sdf(g, X_k.mean(axis=0), body.half)
+        else:
+            psi_new = psi_k
+        mat = _materials(s, phi_new, psi_new)
+        u1, u2 = transport.rk_velocities(u_n, u_nm1, u_k, k)
+        rho_new, C = transport.ssp_rk3(g, rho_n, u_n, u1, u2, dt)
+        if pr.gravity_mode == "flow":
+            rho_grav = [flow_only(face_average(g, phi_new, c), pr.rho_l, pr.rho_g, mat.eps) for c in range(3)]
+        else:
+            rho_grav = rho_new
+        b_u = [rho_n[c] * u_n[c] / dt - C[c] + (1.0 - pr.theta) * Lmu_n[c] + rho_grav[c] * pr.gravity[c]
+               for c in range(3)]
+        b = g.pack(b_u[0], b_u[1], b_u[2], np.zeros(g.cell_shape))
+        x = solve_stokes(g, mat, rho_new, dt, pr.theta, b)
+        ut, vt, wt, p = g.unpack(x)
+        vel_t = [ut, vt, wt]
+        if body is not None:
+            X_half = 0.5 * (X_k + X_n)
+            vel_c, Ub, Ur, Wr, Xc = rigid.constrain(g, vel_t, X_half, body.dV, body.lock,
+                                                    body.U_pres, body.W_pres)
+            X_k = rigid.update_positions(X_n, Ub, Ub_n, dt)
+            info.update(Ur=Ur, Wr=Wr, Ub=Ub)
+        else:
+            vel_c = vel_t
+        u_k = vel_c
+        phi_k = phi_new
+        psi_k = psi_new
+        info.setdefault("u_tilde", []).append(vel_t)
+    s.vel_old = u_n
+    s.vel = u_k
+    s.p = p
+    s.phi = phi_k
+    s.psi = psi_k
+    if body is not None:
+        body.X = X_k
+        body.Ub = info["Ub"]
+        body.Xcom = X_k.mean(axis=0)
+    return info

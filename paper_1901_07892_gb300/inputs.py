@@ -1,0 +1,159 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the oracle.
+
+This module holds no arithmetic of the method: it only lays out geometry
+(signed distances to flat or wavy interfaces and to boxes, marker lattices)
+and draws seeded random numbers.  Everything is numpy, float64, in the
+[k, j, i] (x fastest) layout of the staggered grid:
+
+    cells (nz, ny, nx);  u (nz, ny, nx+1);  v (nz, ny+1, nx);  w (nz+1, ny, nx).
+
+Workloads (material values of the paper's air-water examples:
+rho_l = 1000, rho_g = 1.2, mu_l = 1e-3, mu_g = 1.8e-5, n_cells = 2):
+
+* ``tank2d``  64x64 unit box, interface y = 0.5, locked 0.2x0.2 square solid
+  (rho_s = 500) centred on the interface, one marker per half cell, seeded
+  uniform[-1,1]*1e-2 velocity right-hand side, dt = 1e-3.
+* ``tank3d``  N^3 unit box, water depth 0.6 (flat or perturbed by 8 seeded
+  Fourier modes of total amplitude <= 0.05), locked 0.2x0.2x0.1 box
+  (rho_s = 500) centred on the surface.
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Case:
+    nx: int
+    ny: int
+    nz: int
+    lx: float = 1.0
+    ly: float = 1.0
+    lz: float = 1.0
+    bc: tuple = (-1.0, -1.0, -1.0, -1.0, -1.0, -1.0)
+    gravity: tuple = (0.0, 0.0, -9.81)
+    rho_l: float = 1000.0
+    rho_g: float = 1.2
+    rho_s: float = 500.0
+    mu_l: float = 1e-3
+    mu_g: float = 1.8e-5
+    mu_s: float = 1e-3
+    n_cells: float = 2.0
+    theta: float = 0.5
+    dt: float = 1e-3
+    gravity_mode: str = "flow"
+    phi: np.ndarray = None
+    psi: np.ndarray = None
+    markers: np.ndarray = None   # (N, 3)
+    dV: float = 0.0
+    lock: tuple = (True,) * 6
+    box_center: tuple = None
+    box_half: tuple = None
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def h(self):
+        return (self.lx / self.nx, self.ly / self.ny, self.lz / self.nz)
+
+    def cell_xyz(self):
+        hx, hy, hz = self.h
+        x = (np.arange(self.nx) + 0.5) * hx
+        y = (np.arange(self.ny) + 0.5) * hy
+        z = (np.arange(self.nz) + 0.5) * hz
+        return x[None, None, :], y[None, :, None], z[:, None, None]
+
+    def face_shape(self, c):
+        s = [self.nz, self.ny, self.nx]
+        s[2 - c] += 1
+        return tuple(s)
+
+
+def box_distance(xyz, center, half):
+    """Signed distance to an axis-aligned box (negative inside)."""
+    q = [np.abs(xyz[d] - center[d]) - half[d] for d in range(3)]
+    q = np.broadcast_arrays(*q)
+    outside = np.sqrt(sum(np.maximum(a, 0.0) ** 2 for a in q))
+    inside = np.minimum(np.maximum(np.maximum(q[0], q[1]), q[2]), 0.0)
+    return outside + inside
+
+
+def marker_lattice(center, half, h, active=(True, True, True)):
+    """Markers on a lattice of spacing h_d/2 filling a box (one per half
+    cell), centred on the box.  Inactive axes get one marker layer at the
+    centre.  Returns (X (N,3), dV)."""
+    axes = []
+    dV = 1.0
+    for d in range(3):
+        if active[d]:
+            sp = h[d] / 2.0
+            n = max(1, int(round(2.0 * half[d] / sp)))
+            axes.append(center[d] + (np.arange(n) - (n - 1) / 2.0) * sp)
+            dV *= sp
+        else:
+            axes.append(np.array([center[d]]))
+            dV *= h[d]
+    Z, Y, X = np.meshgrid(axes[2], axes[1], axes[0], indexing="ij")
+    return np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1), dV
+
+
+def fourier_surface(rng, nmodes=8, amp=0.05):
+    """Seeded interface perturbation eta(x, y): nmodes cosines with integer
+    wave numbers 1..4 in each direction, amplitudes summing to <= amp."""
+    kx = rng.integers(1, 5, size=nmodes)
+    ky = rng.integers(1, 5, size=nmodes)
+    a = rng.uniform(0.0, amp / nmodes, size=nmodes)
+    th = rng.uniform(0.0, 2 * np.pi, size=nmodes)
+
+    def eta(x, y):
+        s = 0.0
+        for m in range(nmodes):
+            s = s + a[m] * np.cos(2 * np.pi * (kx[m] * x + ky[m] * y) + th[m])
+        return s
+    return eta
+
+
+def tank2d(n=64, seed=0, with_body=True):
+    c = Case(nx=n, ny=n, nz=1, lz=1.0 / n, bc=(-1.0, -1.0, -1.0, -1.0, 1.0, 1.0),
+             gravity=(0.0, -9.81, 0.0), dt=1e-3)
+    x, y, z = c.cell_xyz()
+    c.phi = np.broadcast_to(y - 0.5, (1, n, n)).copy()
+    center = (0.5, 0.5, 0.5 * c.lz)
+    half = (0.1, 0.1, 0.5 * c.lz)
+    if with_body:
+        c.psi = np.broadcast_to(box_distance((x, y, z), center, (0.1, 0.1, 1e9)), (1, n, n)).copy()
+        c.markers, c.dV = marker_lattice(center, half, c.h, active=(True, True, False))
+        c.box_center, c.box_half = center, (0.1, 0.1, 1e9)
+    else:
+        c.psi = np.full((1, n, n), 1.0)
+    rng = np.random.default_rng(seed)
+    c.extra["rhs_u"] = [rng.uniform(-1.0, 1.0, size=c.face_shape(d)) * 1e-2 for d in range(3)]
+    return c
+
+
+def tank3d(n=128, seed=None, depth=0.6, with_body=True, dt=5e-4, nxyz=None, gravity_mode="flow"):
+    nx, ny, nz = (n, n, n) if nxyz is None else nxyz
+    c = Case(nx=nx, ny=ny, nz=nz, dt=dt, gravity_mode=gravity_mode)
+    x, y, z = c.cell_xyz()
+    if seed is None:
+        c.phi = np.broadcast_to(z - depth, (nz, ny, nx)).copy()
+    else:
+        eta = fourier_surface(np.random.default_rng(seed))
+        c.phi = np.broadcast_to(z - depth - eta(x, y), (nz, ny, nx)).copy()
+    center = (0.5, 0.5, depth)
+    half = (0.1, 0.1, 0.05)
+    if with_body:
+        c.psi = np.broadcast_to(box_distance((x, y, z), center, half), (nz, ny, nx)).copy()
+        c.markers, c.dV = marker_lattice(center, half, c.h)
+        c.box_center, c.box_half = center, half
+    else:
+        c.psi = np.full((nz, ny, nx), 1.0)
+    return c
+
+
+def random_faces(shape_fn, seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    return [rng.uniform(-1.0, 1.0, size=shape_fn(d)) * scale for d in range(3)]
+
+
+def random_cells(shape, seed, scale=1.0):
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, size=shape) * scale

@@ -1,0 +1,107 @@
+"""Pins for the oracle's IB4 transfers and rigid-body projection: the
+kernel's defining moment conditions, discrete adjointness S_BC = J_BC^* at
+walls (Sec. 3.3.2), exact reproduction of constant and linear fields, and
+exact recovery of an imposed rigid motion (Sec. 4.2.5)."""
+import numpy as np
+import pytest
+
+from oracle.grid import Grid, NO_SLIP, FREE_SLIP
+from oracle.ib import phi4, interpolate, spread
+from oracle.rigid import rigid_fit, constrain, body_velocity
+from paper_1901_07892_gb300 import inputs
+
+
+def test_phi4_moment_conditions():
+    rng = np.random.default_rng(0)
+    for r in rng.uniform(0, 1, 200):
+        j = np.arange(-3, 4)
+        w = phi4(r - j)
+        assert w.sum() == pytest.approx(1.0, abs=1e-14)               # partition of unity
+        assert ((r - j) * w).sum() == pytest.approx(0.0, abs=1e-14)   # first moment
+        assert w[j % 2 == 0].sum() == pytest.approx(0.5, abs=1e-14)   # even/odd split
+        assert (w * w).sum() == pytest.approx(3.0 / 8.0, abs=1e-14)  # sum of squares
+    assert phi4(0.0) == pytest.approx(0.5)
+    assert phi4(1.0) == pytest.approx(0.25)
+    assert phi4(2.0) == 0.0 and phi4(2.5) == 0.0
+    # continuity at |r| = 1
+    assert phi4(1.0 - 1e-12) == pytest.approx(phi4(1.0 + 1e-12), abs=1e-9)
+
+
+@pytest.mark.parametrize("bc", [(NO_SLIP,) * 6, (NO_SLIP, FREE_SLIP, NO_SLIP, FREE_SLIP, FREE_SLIP, NO_SLIP)])
+def test_spread_is_adjoint_of_interp_at_walls(bc):
+    g = Grid(9, 8, 7, lx=1.0, ly=0.9, lz=0.8, bc=bc)
+    rng = np.random.default_rng(1)
+    # markers everywhere, including within two cells of every wall
+    X = np.stack([rng.uniform(0, g.lx, 300), rng.uniform(0, g.ly, 300), rng.uniform(0, g.lz, 300)], 1)
+    F = rng.standard_normal((300, 3))
+    vel = [rng.standard_normal(g.face_shape(c)) * g.interior_face_mask(c) for c in range(3)]
+    dV = 1e-3
+    SF = spread(g, F, X, dV)
+    JU = interpolate(g, vel, X)
+    lhs = sum((SF[c] * vel[c]).sum() for c in range(3)) * g.hx * g.hy * g.hz
+    rhs = (F * JU).sum() * dV
+    assert lhs == pytest.approx(rhs, rel=1e-13)
+    for c in range(3):
+        assert np.all(SF[c][~g.interior_face_mask(c)] == 0.0)
+
+
+def test_interp_reproduces_linear_fields_inside():
+    g = Grid(10, 10, 10)
+    A = np.array([[0.1, 0.2, -0.3], [0.4, -0.5, 0.6], [-0.7, 0.8, 0.9]])
+    c0 = np.array([1.0, -2.0, 0.5])
+    vel = []
+    for c in range(3):
+        x, y, z = g.face_centers(c)
+        val = c0[c] + A[c, 0] * x + A[c, 1] * y + A[c, 2] * z
+        vel.append(np.broadcast_to(val, g.face_shape(c)).copy())
+    rng = np.random.default_rng(2)
+    X = rng.uniform(0.35, 0.65, (50, 3))
+    U = interpolate(g, vel, X)
+    ex = c0[None, :] + X @ A.T
+    assert np.allclose(U, ex, atol=1e-13)
+
+
+def test_rigid_fit_recovers_imposed_motion():
+    rng = np.random.default_rng(3)
+    X = rng.uniform(0, 1, (400, 3))
+    Ur = np.array([0.3, -0.1, 0.2])
+    Wr = np.array([0.05, 0.4, -0.3])
+    Xc = X.mean(0)
+    U = body_velocity(X, Xc, Ur, Wr)
+    Ur2, Wr2, Xc2 = rigid_fit(X, U)
+    assert np.allclose(Ur2, Ur, atol=1e-14)
+    assert np.allclose(Wr2, Wr, atol=1e-13)
+
+
+def test_projection_makes_body_rigid_inside():
+    """Deep inside a half-cell marker lattice, S J is the identity on smooth
+    fields, so after the correction J u equals the prescribed body velocity."""
+    g = Grid(24, 24, 24)
+    center, half = (0.5, 0.5, 0.5), (0.2, 0.2, 0.2)
+    X, dV = inputs.marker_lattice(center, half, g.h)
+    vel = [np.full(g.face_shape(c), 0.3 * (c + 1)) * g.interior_face_mask(c) for c in range(3)]
+    new, Ub, Ur, Wr, Xc = constrain(g, vel, X, dV, [True] * 6, np.zeros(3), np.zeros(3))
+    U = interpolate(g, new, X)
+    deep = np.all(np.abs(X - 0.5) < 0.2 - 3 * g.hx, axis=1)
+    assert deep.sum() > 100
+    assert np.abs(U[deep]).max() < 1e-12
+    # and the face velocities deep inside are zero
+    for c in range(3):
+        x, y, z = g.face_centers(c)
+        m = (np.abs(x - 0.5) < 0.2 - 4 * g.hx) & (np.abs(y - 0.5) < 0.2 - 4 * g.hx) & (np.abs(z - 0.5) < 0.2 - 4 * g.hx)
+        m = np.broadcast_to(m, g.face_shape(c))
+        assert np.abs(new[c][m]).max() < 1e-12
+
+
+def test_free_body_keeps_uniform_velocity():
+    """A free body in a uniform flow takes the flow's velocity and leaves the
+    field unchanged deep inside (momentum redistribution of a uniform field)."""
+    g = Grid(20, 20, 20)
+    X, dV = inputs.marker_lattice((0.5, 0.5, 0.5), (0.15, 0.15, 0.15), g.h)
+    Uin = np.array([0.2, -0.1, 0.05])
+    vel = [np.full(g.face_shape(c), Uin[c]) * g.interior_face_mask(c) for c in range(3)]
+    new, Ub, Ur, Wr, Xc = constrain(g, vel, X, dV, [False] * 6, np.zeros(3), np.zeros(3))
+    assert np.allclose(Ur, Uin, atol=1e-13)
+    assert np.allclose(Wr, 0.0, atol=1e-12)
+    for c in range(3):
+        assert np.abs(new[c] - vel[c]).max() < 1e-13
