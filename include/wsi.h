@@ -1,0 +1,214 @@
+/*
+ * wsi.h -- C ABI of libwsi: the implicit Stokes step of the DLM level-set
+ * wave-structure-interaction method of Nangia, Patankar & Bhalla
+ * (arXiv 1901.07892) on one GB300 GPU (sm_103a), uniform staggered grid.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid.  nx x ny x nz cells over [0,lx] x [0,ly] x [0,lz] (Sec. 3.1).  A 2-D
+ *   problem is nz = 1 with free-slip z walls (bc[4] = bc[5] = +1); every
+ *   z-derivative then vanishes and all w-faces lie on walls.
+ * Layout.  Every array is float64, x fastest, unghosted:
+ *     cell field   nx*ny*nz                 index (k*ny + j)*nx + i
+ *     u (x-faces)  (nx+1)*ny*nz             index (k*ny + j)*(nx+1) + i
+ *     v (y-faces)  nx*(ny+1)*nz             index (k*(ny+1) + j)*nx + i
+ *     w (z-faces)  nx*ny*(nz+1)             index (k*ny + j)*nx + i
+ *   A "Stokes vector" is u, v, w, p concatenated (wsi_stokes_size() doubles);
+ *   a "velocity vector" is its first three parts (wsi_velocity_size()).
+ *   Faces lying on a wall carry the zero normal velocity; they are not
+ *   unknowns and every output writes 0 there.
+ * Memory.  Array arguments may be device pointers or host pointers (pageable
+ *   or pinned): the library copies with cudaMemcpyDefault on its stream.
+ *   The caller keeps ownership of everything it passes; the library copies
+ *   what it needs and never keeps a caller pointer after returning.
+ *   The context owns all device state it allocates, on the stream given at
+ *   creation; every call is stream-ordered and returns after the stream has
+ *   been synchronised unless stated otherwise.
+ * Errors.  Every int-returning call returns WSI_OK or one of the codes
+ *   below, never aborts, and leaves a message in wsi_last_error(ctx).
+ *   Device-side bound checks raise a flag read back as WSI_ERR_DEVICE.
+ */
+#ifndef WSI_H
+#define WSI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WSI_OK 0
+#define WSI_ERR_INVALID_ARG 1
+#define WSI_ERR_CUDA 2
+#define WSI_ERR_NOT_CONVERGED 3
+#define WSI_ERR_NAN 4
+#define WSI_ERR_OOM 5
+#define WSI_ERR_DEVICE 6
+
+#define WSI_NO_SLIP (-1.0)
+#define WSI_FREE_SLIP (1.0)
+
+#define WSI_PREC_FP64 0   /* preconditioner in float64 (plain path)           */
+#define WSI_PREC_MIXED 1  /* preconditioner in float32 inside float64 FGMRES */
+
+#define WSI_GRAVITY_FLOW 0 /* rho^flow g: well-balanced, for locked bodies (Sec. 5) */
+#define WSI_GRAVITY_FULL 1 /* rho g with the transported face density           */
+
+typedef struct wsi_ctx wsi_ctx;
+
+typedef struct {
+    int nx, ny, nz;
+    double lx, ly, lz;
+    double bc[6];        /* tangential ghost sign per wall x-,x+,y-,y+,z-,z+:
+                            WSI_NO_SLIP or WSI_FREE_SLIP                      */
+    double gravity[3];
+    double n_cells;      /* Heaviside half-width in cells (paper: 2)          */
+    double theta;        /* implicit viscous weight (paper: 1/2, Crank-Nicolson) */
+    int precision;       /* WSI_PREC_FP64 or WSI_PREC_MIXED                  */
+    int mg_pre, mg_post; /* red-black Gauss-Seidel sweeps per level           */
+    int mg_cycles;       /* pressure V-cycles per preconditioner application  */
+    int visc_sweeps;     /* viscous red-black sweeps per application          */
+    int restart;         /* FGMRES restart length m                           */
+} wsi_grid_desc;
+
+typedef struct {
+    double rho_l, rho_g, rho_s;
+    double mu_l, mu_g, mu_s;
+    int gravity_mode;    /* WSI_GRAVITY_FLOW or WSI_GRAVITY_FULL             */
+} wsi_phase_props;
+
+typedef struct {
+    const double* X;     /* marker positions, n_markers x 3 (x,y,z interleaved) */
+    int n_markers;
+    double dV;           /* marker volume ds1 ds2 ds3                         */
+    int lock[6];         /* 1 = prescribed: Ux,Uy,Uz,Wx,Wy,Wz                 */
+    double U_pres[3], W_pres[3];
+    int shape;           /* 0: psi not rebuilt; 1: box of half-extents half[] */
+    double half[3];
+} wsi_body_desc;
+
+typedef struct {
+    double rtol;         /* relative residual ||b-Kx||_2 / ||b||_2            */
+    int max_iters;
+    int use_x0;          /* 1: x holds the initial guess                      */
+} wsi_solve_opts;
+
+typedef struct {
+    int iters;
+    double rel_residual; /* true residual after the solve                      */
+    double ms;
+} wsi_solve_stats;
+
+typedef struct {
+    double U_r[3], W_r[3], X_com[3];
+} wsi_body_state;
+
+typedef struct {
+    int iters[4];        /* FGMRES iterations of each cycle's solve           */
+    double rel_residual[4];
+    double umax;         /* max |u| after the step                             */
+    double ms;
+} wsi_step_stats;
+
+/* Sizes of the packed vectors (doubles). */
+size_t wsi_stokes_size(const wsi_ctx* ctx);
+size_t wsi_velocity_size(const wsi_ctx* ctx);
+
+/* Create a context: grid, boundary conditions, solver options (Sec. 3.1 grid,
+ * Sec. 4.2.4 solver).  stream: a cudaStream_t (NULL = legacy default stream).
+ * The device is the current one.  *out is owned by the caller until
+ * wsi_destroy.  WSI_ERR_INVALID_ARG on non-positive sizes or spacings. */
+int wsi_create_grid(const wsi_grid_desc* desc, void* stream, wsi_ctx** out);
+void wsi_destroy(wsi_ctx* ctx);
+const char* wsi_last_error(const wsi_ctx* ctx);
+
+/* Set the level sets phi (liquid-gas, liquid where phi < 0) and psi (solid,
+ * inside where psi < 0) at cell centres, the material constants and the
+ * bodies; compute the material coefficients of Sec. 4.1 (smoothed Heaviside
+ * over n_cells cells, two-stage property, harmonic edge viscosity) and the
+ * face density from face-averaged level sets (Sec. 4.2.2).  Resets the
+ * velocity history to zero.  Markers are copied in.  WSI_ERR_INVALID_ARG on
+ * non-finite or non-positive material constants, n_bodies > 1, or a marker
+ * outside the box. */
+int wsi_set_phases(wsi_ctx* ctx, const double* phi, const double* psi,
+                   const wsi_phase_props* props, const wsi_body_desc* bodies, int n_bodies);
+
+/* Solve the implicit Stokes system of Sec. 4.2.2 / 4.2.4,
+ *     rho/dt u - theta L_mu u + G p = b_u,   -D u = b_p,
+ * with the coefficients of the last wsi_set_phases, by FGMRES(m)
+ * right-preconditioned with the projection method (viscous red-black
+ * smoothing, pressure multigrid V-cycles).  rhs, x: Stokes vectors; x is
+ * the initial guess when opts->use_x0, and receives the solution with p of
+ * zero mean.  Returns WSI_ERR_NOT_CONVERGED (solution still written) when
+ * max_iters is reached, WSI_ERR_NAN on a non-finite residual. */
+int wsi_stokes_solve(wsi_ctx* ctx, const double* rhs, double* x, double dt,
+                     const wsi_solve_opts* opts, wsi_solve_stats* stats);
+
+/* Rigidity projection of Sec. 4.2.5 for the body of the last
+ * wsi_set_phases at its current markers: U = J u, free DOFs from momentum
+ * redistribution, locked DOFs prescribed, U_b = U_r + W_r x R,
+ * u += S(U_b - U), with the wall-adjoint J_BC / S_BC of Sec. 3.3.2.
+ * vel: velocity vector, corrected in place.  Markers do not move. */
+int wsi_dlm_constrain(wsi_ctx* ctx, double* vel, wsi_body_state* out);
+
+/* One full time step of Sec. 4.2 (two fixed-point cycles): level-set
+ * advection, psi rebuilt from the markers, materials, SSP-RK3 face density
+ * and consistent convection, Stokes solve, rigidity projection and marker
+ * update, on library-owned state.  Tolerance and limits from opts. */
+int wsi_step(wsi_ctx* ctx, double dt, const wsi_solve_opts* opts, wsi_step_stats* stats);
+
+/* State access for the step.  which: WSI_F_VEL (velocity vector u^n),
+ * WSI_F_P (cell), WSI_F_PHI, WSI_F_PSI (cell), WSI_F_MARKERS (n x 3). */
+#define WSI_F_VEL 0
+#define WSI_F_P 1
+#define WSI_F_PHI 2
+#define WSI_F_PSI 3
+#define WSI_F_MARKERS 4
+int wsi_get_field(wsi_ctx* ctx, int which, double* dst);
+int wsi_set_field(wsi_ctx* ctx, int which, const double* src);
+
+/* Coefficients computed by wsi_set_phases (Sec. 4.1): which:
+ * WSI_C_RHO_CC, WSI_C_MU_CC (cell), WSI_C_RHO_FACE, WSI_C_RHO_FLOW_FACE
+ * (velocity vectors), WSI_C_MU_EDGE (mu_xy, mu_xz, mu_yz concatenated:
+ * (nx+1)(ny+1)nz + (nx+1)ny(nz+1) + nx(ny+1)(nz+1)). */
+#define WSI_C_RHO_CC 0
+#define WSI_C_MU_CC 1
+#define WSI_C_RHO_FACE 2
+#define WSI_C_RHO_FLOW_FACE 3
+#define WSI_C_MU_EDGE 4
+int wsi_get_coeff(wsi_ctx* ctx, int which, double* dst);
+
+/* Operator applies on the current coefficients (float64), Sec. 3.1 and
+ * Sec. 4.2.2:  WSI_OP_STOKES  Stokes vector -> Stokes vector (K x);
+ * WSI_OP_VISCOUS  velocity -> velocity (rho/dt u - theta L_mu u);
+ * WSI_OP_STRAIN  velocity -> velocity (L_mu u);
+ * WSI_OP_PRESSURE cell -> cell (D beta G p, beta = 1/rho face);
+ * WSI_OP_GRAD cell -> velocity; WSI_OP_DIV velocity -> cell. */
+#define WSI_OP_STOKES 0
+#define WSI_OP_VISCOUS 1
+#define WSI_OP_STRAIN 2
+#define WSI_OP_PRESSURE 3
+#define WSI_OP_GRAD 4
+#define WSI_OP_DIV 5
+int wsi_apply(wsi_ctx* ctx, int op, const double* in, double* out, double dt);
+
+/* Consistent transport of Sec. 4.2.2 on the current face density rho^n:
+ * SSP-RK3 with u^n, u^(1), u^(2) for cycle k (u_k = u^{n+1,k}, ignored at
+ * k = 0) -> rho_out (velocity-vector layout) and the convective term C_out. */
+int wsi_transport(wsi_ctx* ctx, const double* u_n, const double* u_nm1, const double* u_k,
+                  int k, double dt, double* rho_out, double* C_out);
+
+/* Level-set advection of Sec. 4.2.1: phi_out = phi_n - dt div(u phi_lim(phi_half)). */
+int wsi_advect_levelset(wsi_ctx* ctx, const double* vel, const double* phi_n,
+                        const double* phi_half, double dt, double* phi_out);
+
+/* IB4 transfers of Sec. 3.3 with the wall-adjoint forms of Sec. 3.3.2.
+ * X: n x 3 positions.  interp: velocity vector -> U (n x 3).
+ * spread: F (n x 3), marker volume dV -> velocity vector (overwritten). */
+int wsi_interp(wsi_ctx* ctx, const double* vel, const double* X, int n, double* U);
+int wsi_spread(wsi_ctx* ctx, const double* F, const double* X, int n, double dV, double* vel);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,897 @@
+// C ABI of libwsi (include/wsi.h): context management, the FGMRES driver of
+// the implicit Stokes solve (Sec. 4.2.4), the rigidity step (Sec. 4.2.5) and
+// the two-cycle time step (Sec. 4.2).  All compute runs in the kernels of
+// ops.cu, mg.cu, krylov.cu and dlm.cu; the host only sequences launches,
+// runs the (m+1) x m Hessenberg least-squares update of FGMRES and solves the
+// 3 x 3 inertia system of a free body.
+#include <math.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace wsi;
+
+struct Body {
+  int n = 0;
+  double dV = 0.0;
+  int lock[6] = {1, 1, 1, 1, 1, 1};
+  double U_pres[3] = {0, 0, 0}, W_pres[3] = {0, 0, 0};
+  int shape = 0;
+  double half[3] = {0, 0, 0};
+  double *X = nullptr, *Xn = nullptr, *Xh = nullptr, *Ub = nullptr, *Ub_n = nullptr, *U = nullptr, *F = nullptr;
+  double* xc = nullptr;       // 3 doubles: centre of mass used for R
+  double* rig = nullptr;      // 6 doubles: U_r, W_r
+  double* sums = nullptr;     // 15 doubles
+  double* scratch = nullptr;  // reduction partials
+  double U_r[3] = {0, 0, 0}, W_r[3] = {0, 0, 0}, X_com[3] = {0, 0, 0};
+};
+
+struct wsi_ctx {
+  GridDev g;
+  Packing pk;
+  cudaStream_t st = nullptr;
+  wsi_grid_desc desc;
+  wsi_phase_props props;
+  bool have_phases = false;
+  std::string err;
+  std::vector<void*> allocs;
+  size_t nvel = 0, nstk = 0, ncell = 0;
+  // float64 coefficients of the current operator
+  double *rho_cc = nullptr, *mu_cc = nullptr, *rho_face[3], *beta[3], *rho_flow[3], *mu_e[3];
+  // time-n coefficients (right-hand side)
+  double *mu_cc_n = nullptr, *mu_e_n[3], *rho_n[3], *beta_n[3], *rho_flow_n[3];
+  // state
+  double *vel = nullptr, *vel_old = nullptr, *p = nullptr, *phi = nullptr, *psi = nullptr;
+  // step scratch
+  double *vel_k = nullptr, *vel_half = nullptr, *u1 = nullptr, *u2 = nullptr, *rs1 = nullptr, *rs2 = nullptr,
+         *R = nullptr, *Cc = nullptr, *phi_k = nullptr, *phi_new = nullptr, *phi_half = nullptr, *psi_k = nullptr,
+         *psi_new = nullptr, *b = nullptr, *x = nullptr, *rho_cc_tmp = nullptr;
+  // Krylov
+  int m = 20;
+  double *V = nullptr, *Z = nullptr, *hdev = nullptr, *red = nullptr;
+  Precond<double> P64;
+  Precond<float> P32;
+  bool pc_dirty = true;
+  Opts opts;
+  Body body;
+  bool has_body = false;
+};
+
+namespace {
+
+int fail(wsi_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_check(wsi_ctx* c, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return fail(c, WSI_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return WSI_OK;
+}
+
+double* dalloc(wsi_ctx* c, size_t n) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(double)) != cudaSuccess) return nullptr;
+  cudaMemsetAsync(p, 0, std::max<size_t>(n, 1) * sizeof(double), c->st);
+  c->allocs.push_back(p);
+  return (double*)p;
+}
+
+void vel_parts(wsi_ctx* c, double* base, double* out[3]) {
+  for (int d = 0; d < 3; ++d) out[d] = base + c->pk.off[d];
+}
+void vel_parts(wsi_ctx* c, const double* base, const double* out[3]) {
+  for (int d = 0; d < 3; ++d) out[d] = base + c->pk.off[d];
+}
+
+Coef<double> coef_now(wsi_ctx* c) {
+  Coef<double> cf;
+  for (int d = 0; d < 3; ++d) {
+    cf.rho_face[d] = c->rho_face[d];
+    cf.beta[d] = c->beta[d];
+    cf.mu_e[d] = c->mu_e[d];
+  }
+  cf.mu_cc = c->mu_cc;
+  return cf;
+}
+
+Coef<double> coef_n(wsi_ctx* c) {
+  Coef<double> cf;
+  for (int d = 0; d < 3; ++d) {
+    cf.rho_face[d] = c->rho_n[d];
+    cf.beta[d] = c->beta_n[d];
+    cf.mu_e[d] = c->mu_e_n[d];
+  }
+  cf.mu_cc = c->mu_cc_n;
+  return cf;
+}
+
+PhaseConst phase_const(wsi_ctx* c) {
+  PhaseConst pc;
+  pc.rho_l = c->props.rho_l;
+  pc.rho_g = c->props.rho_g;
+  pc.rho_s = c->props.rho_s;
+  pc.mu_l = c->props.mu_l;
+  pc.mu_g = c->props.mu_g;
+  pc.mu_s = c->props.mu_s;
+  double hc = c->g.n[2] == 1 ? sqrt(c->g.h[0] * c->g.h[1]) : cbrt(c->g.h[0] * c->g.h[1] * c->g.h[2]);
+  pc.eps = c->desc.n_cells * hc;
+  return pc;
+}
+
+__global__ void k_recip(size_t n, const double* __restrict__ a, double* b) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = 1.0 / a[t];
+}
+
+void recip(wsi_ctx* c, const double* a, double* b, size_t n) {
+  if (n) k_recip<<<cdiv(n, 256), 256, 0, c->st>>>(n, a, b);
+}
+
+int copy_in(wsi_ctx* c, double* dst, const double* src, size_t n) {
+  if (!src) return fail(c, WSI_ERR_INVALID_ARG, "null input pointer");
+  if (cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDefault, c->st) != cudaSuccess)
+    return fail(c, WSI_ERR_CUDA, "copy in failed");
+  return WSI_OK;
+}
+int copy_out(wsi_ctx* c, double* dst, const double* src, size_t n) {
+  if (!dst) return fail(c, WSI_ERR_INVALID_ARG, "null output pointer");
+  if (cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDefault, c->st) != cudaSuccess)
+    return fail(c, WSI_ERR_CUDA, "copy out failed");
+  return WSI_OK;
+}
+
+int ensure_pc(wsi_ctx* c) {
+  if (!c->pc_dirty) return WSI_OK;
+  Coef<double> cf = coef_now(c);
+  int rc = c->desc.precision == WSI_PREC_MIXED ? precond_setup<float>(c->P32, c->g, cf, c->st, c->err)
+                                               : precond_setup<double>(c->P64, c->g, cf, c->st, c->err);
+  if (rc == WSI_OK) c->pc_dirty = false;
+  return rc;
+}
+
+void pc_apply(wsi_ctx* c, double dt, const double* v, double* z) {
+  if (c->desc.precision == WSI_PREC_MIXED)
+    precond_apply<float>(c->P32, c->g, c->opts, dt, v, z, c->st);
+  else
+    precond_apply<double>(c->P64, c->g, c->opts, dt, v, z, c->st);
+}
+
+// FGMRES(m), right preconditioned by the projection method; float64 Arnoldi
+// with classical Gram-Schmidt applied twice.
+int fgmres(wsi_ctx* c, const double* b, double* x, double dt, const wsi_solve_opts* o, wsi_solve_stats* s) {
+  int rc = ensure_pc(c);
+  if (rc) return rc;
+  const size_t n = c->nstk;
+  const int m = c->m;
+  const double inv_dt = 1.0 / dt, theta = c->desc.theta;
+  Coef<double> cf = coef_now(c);
+  double* V = c->V;
+  double* Z = c->Z;
+  double* hd = c->hdev;
+  double* red = c->red;
+  auto Vj = [&](int j) { return V + (size_t)j * n; };
+  auto Zj = [&](int j) { return Z + (size_t)j * n; };
+  double bnorm = host_norm2(b, n, red, c->st);
+  int iters = 0;
+  s->iters = 0;
+  s->rel_residual = 0.0;
+  if (!std::isfinite(bnorm)) return fail(c, WSI_ERR_NAN, "non-finite right-hand side");
+  if (bnorm == 0.0) {
+    cudaMemsetAsync(x, 0, n * sizeof(double), c->st);
+    return cuda_check(c, "fgmres");
+  }
+  if (!o->use_x0) cudaMemsetAsync(x, 0, n * sizeof(double), c->st);
+  // r = b - K x  into V_0
+  launch_stokes(c->g, cf, inv_dt, theta, x, Vj(0), c->st);
+  launch_lincomb(n, 1.0, b, -1.0, Vj(0), 0.0, nullptr, Vj(0), c->st);
+  double beta = host_norm2(Vj(0), n, red, c->st);
+  const double tol = o->rtol * bnorm;
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), gv(m + 1), hcol(2 * (m + 1) + 1);
+  int result = WSI_OK;
+  while (true) {
+    if (!std::isfinite(beta)) return fail(c, WSI_ERR_NAN, "non-finite residual");
+    if (beta <= tol) break;
+    if (iters >= o->max_iters) {
+      result = WSI_ERR_NOT_CONVERGED;
+      break;
+    }
+    double ib = 1.0 / beta;
+    cudaMemcpyAsync(hd, &ib, sizeof(double), cudaMemcpyHostToDevice, c->st);
+    launch_scale(Vj(0), n, hd, false, c->st);
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int j = 0;
+    bool done = false;
+    for (; j < m; ++j) {
+      pc_apply(c, dt, Vj(j), Zj(j));
+      double* w = Vj(j + 1);
+      launch_stokes(c->g, cf, inv_dt, theta, Zj(j), w, c->st);
+      // CGS2
+      launch_mdot(V, n, j + 1, w, n, hd, red, c->st);
+      launch_maxpy(V, n, j + 1, hd, w, n, 1.0, c->st);
+      launch_mdot(V, n, j + 1, w, n, hd + (m + 1), red, c->st);
+      launch_maxpy(V, n, j + 1, hd + (m + 1), w, n, 1.0, c->st);
+      launch_mdot(w, n, 1, w, n, hd + 2 * (m + 1), red, c->st);
+      cudaMemcpyAsync(hcol.data(), hd, (2 * (m + 1) + 1) * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+      if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "fgmres iteration");
+      ++iters;
+      double hn = sqrt(std::max(hcol[2 * (m + 1)], 0.0));
+      if (!std::isfinite(hn)) return fail(c, WSI_ERR_NAN, "non-finite Krylov vector");
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i] + hcol[(m + 1) + i];
+      H[(size_t)(j + 1) * m + j] = hn;
+      // previous rotations
+      for (int i = 0; i < j; ++i) {
+        double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+      }
+      double a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
+      double r = hypot(a, bb);
+      cs[j] = r == 0.0 ? 1.0 : a / r;
+      sn[j] = r == 0.0 ? 0.0 : bb / r;
+      H[(size_t)j * m + j] = r;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      double res = fabs(gv[j + 1]);
+      if (hn > 0.0) {
+        double ihn = 1.0 / hn;
+        cudaMemcpyAsync(hd + 2 * (m + 1) + 1, &ihn, sizeof(double), cudaMemcpyHostToDevice, c->st);
+        launch_scale(w, n, hd + 2 * (m + 1) + 1, false, c->st);
+      }
+      if (res <= tol || iters >= o->max_iters || hn == 0.0) {
+        ++j;
+        done = true;
+        break;
+      }
+    }
+    if (!done) j = m;
+    // y = H^{-1} g (upper triangular j x j)
+    std::vector<double> y(j);
+    for (int i = j - 1; i >= 0; --i) {
+      double sacc = gv[i];
+      for (int k = i + 1; k < j; ++k) sacc -= H[(size_t)i * m + k] * y[k];
+      y[i] = sacc / H[(size_t)i * m + i];
+    }
+    cudaMemcpyAsync(hd, y.data(), j * sizeof(double), cudaMemcpyHostToDevice, c->st);
+    launch_maxpy(Z, n, j, hd, x, n, -1.0, c->st);
+    // true residual
+    launch_stokes(c->g, cf, inv_dt, theta, x, Vj(0), c->st);
+    launch_lincomb(n, 1.0, b, -1.0, Vj(0), 0.0, nullptr, Vj(0), c->st);
+    beta = host_norm2(Vj(0), n, red, c->st);
+  }
+  // zero-mean pressure
+  launch_sum<double>(x + c->pk.off[3], c->ncell, hd, red, c->st);
+  launch_add_scalar_from<double>(x + c->pk.off[3], c->ncell, hd, -1.0 / (double)c->ncell, c->st);
+  s->iters = iters;
+  s->rel_residual = beta / bnorm;
+  int crc = cuda_check(c, "fgmres");
+  if (crc) return crc;
+  if (result == WSI_ERR_NOT_CONVERGED) c->err = "FGMRES reached max_iters";
+  return result;
+}
+
+// 3x3 solve with partial pivoting; returns false if singular
+bool solve3(double A[3][3], const double b[3], double x[3]) {
+  double M[3][4];
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) M[i][j] = A[i][j];
+    M[i][3] = b[i];
+  }
+  double scale = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) scale = std::max(scale, fabs(A[i][j]));
+  for (int p = 0; p < 3; ++p) {
+    int piv = p;
+    for (int r = p + 1; r < 3; ++r)
+      if (fabs(M[r][p]) > fabs(M[piv][p])) piv = r;
+    if (fabs(M[piv][p]) <= 1e-300 + 1e-14 * scale) return false;
+    for (int k = 0; k < 4; ++k) std::swap(M[p][k], M[piv][k]);
+    for (int r = 0; r < 3; ++r) {
+      if (r == p) continue;
+      double f = M[r][p] / M[p][p];
+      for (int k = p; k < 4; ++k) M[r][k] -= f * M[p][k];
+    }
+  }
+  for (int i = 0; i < 3; ++i) x[i] = M[i][3] / M[i][i];
+  return true;
+}
+
+// Rigidity projection at marker positions Xuse: vel += S(U_b - J vel).
+int dlm_project(wsi_ctx* c, double* velv, const double* Xuse) {
+  Body& B = c->body;
+  double* vq[3];
+  vel_parts(c, velv, vq);
+  const double* cq[3] = {vq[0], vq[1], vq[2]};
+  launch_marker_mean(Xuse, B.n, B.xc, B.scratch, c->st);
+  launch_ib_interp(c->g, cq, Xuse, B.n, B.U, c->st);
+  launch_rigid_sums(Xuse, B.U, B.n, B.xc, B.sums, B.scratch, c->st);
+  double hs[15], xc[3];
+  cudaMemcpyAsync(hs, B.sums, sizeof(hs), cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(xc, B.xc, sizeof(xc), cudaMemcpyDeviceToHost, c->st);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "dlm sums");
+  double Ur[3], Wr[3] = {0, 0, 0};
+  for (int d = 0; d < 3; ++d) Ur[d] = hs[d] / (double)B.n;
+  double I[3][3] = {{hs[6], hs[9], hs[10]}, {hs[9], hs[7], hs[11]}, {hs[10], hs[11], hs[8]}};
+  double L[3] = {hs[3], hs[4], hs[5]};
+  if (!solve3(I, L, Wr)) {
+    // planar body: rotation only about the normal of its plane
+    for (int d = 0; d < 3; ++d) Wr[d] = (I[d][d] > 0.0 && L[d] != 0.0) ? L[d] / I[d][d] : 0.0;
+  }
+  for (int d = 0; d < 3; ++d) {
+    if (B.lock[d]) Ur[d] = B.U_pres[d];
+    if (B.lock[3 + d]) Wr[d] = B.W_pres[d];
+  }
+  double rg[6] = {Ur[0], Ur[1], Ur[2], Wr[0], Wr[1], Wr[2]};
+  cudaMemcpyAsync(B.rig, rg, sizeof(rg), cudaMemcpyHostToDevice, c->st);
+  launch_body_velocity(Xuse, B.U, B.n, B.rig, B.xc, B.Ub, B.F, c->st);
+  launch_ib_spread(c->g, B.F, Xuse, B.n, B.dV, vq, c->st);
+  for (int d = 0; d < 3; ++d) {
+    B.U_r[d] = Ur[d];
+    B.W_r[d] = Wr[d];
+    B.X_com[d] = xc[d];
+  }
+  return cuda_check(c, "dlm project");
+}
+
+int valid_ctx(wsi_ctx* c) { return c ? WSI_OK : WSI_ERR_INVALID_ARG; }
+
+}  // namespace
+
+extern "C" {
+
+size_t wsi_stokes_size(const wsi_ctx* c) { return c ? c->nstk : 0; }
+size_t wsi_velocity_size(const wsi_ctx* c) { return c ? c->nvel : 0; }
+const char* wsi_last_error(const wsi_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int wsi_create_grid(const wsi_grid_desc* d, void* stream, wsi_ctx** out) {
+  if (!d || !out) return WSI_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (d->nx < 2 || d->ny < 2 || d->nz < 1 || !(d->lx > 0) || !(d->ly > 0) || !(d->lz > 0)) return WSI_ERR_INVALID_ARG;
+  for (int i = 0; i < 6; ++i)
+    if (d->bc[i] != WSI_NO_SLIP && d->bc[i] != WSI_FREE_SLIP) return WSI_ERR_INVALID_ARG;
+  if (d->nz == 1 && (d->bc[4] != WSI_FREE_SLIP || d->bc[5] != WSI_FREE_SLIP)) return WSI_ERR_INVALID_ARG;
+  if (d->precision != WSI_PREC_FP64 && d->precision != WSI_PREC_MIXED) return WSI_ERR_INVALID_ARG;
+  wsi_ctx* c = new wsi_ctx();
+  c->desc = *d;
+  c->st = (cudaStream_t)stream;
+  c->g.n[0] = d->nx;
+  c->g.n[1] = d->ny;
+  c->g.n[2] = d->nz;
+  c->g.h[0] = d->lx / d->nx;
+  c->g.h[1] = d->ly / d->ny;
+  c->g.h[2] = d->lz / d->nz;
+  for (int i = 0; i < 6; ++i) c->g.bc[i] = d->bc[i];
+  c->pk = packing(c->g);
+  c->nvel = c->pk.off[3];
+  c->nstk = c->pk.off[4];
+  c->ncell = fsize(c->g, 3);
+  c->m = d->restart > 0 ? std::min(d->restart, 60) : 20;
+  c->opts.mg_pre = d->mg_pre > 0 ? d->mg_pre : 2;
+  c->opts.mg_post = d->mg_post > 0 ? d->mg_post : 2;
+  c->opts.mg_cycles = d->mg_cycles > 0 ? d->mg_cycles : 1;
+  c->opts.visc_sweeps = d->visc_sweeps > 0 ? d->visc_sweeps : 2;
+  c->opts.theta = d->theta;
+  const GridDev& g = c->g;
+  bool ok = true;
+  auto A = [&](size_t n) {
+    double* p = dalloc(c, n);
+    ok &= p != nullptr;
+    return p;
+  };
+  c->rho_cc = A(c->ncell);
+  c->mu_cc = A(c->ncell);
+  c->mu_cc_n = A(c->ncell);
+  c->rho_cc_tmp = A(c->ncell);
+  for (int k = 0; k < 3; ++k) {
+    c->rho_face[k] = A(fsize(g, k));
+    c->beta[k] = A(fsize(g, k));
+    c->rho_flow[k] = A(fsize(g, k));
+    c->rho_n[k] = A(fsize(g, k));
+    c->beta_n[k] = A(fsize(g, k));
+    c->rho_flow_n[k] = A(fsize(g, k));
+    c->mu_e[k] = A(esize(g, k));
+    c->mu_e_n[k] = A(esize(g, k));
+  }
+  c->vel = A(c->nvel);
+  c->vel_old = A(c->nvel);
+  c->p = A(c->ncell);
+  c->phi = A(c->ncell);
+  c->psi = A(c->ncell);
+  c->vel_k = A(c->nvel);
+  c->vel_half = A(c->nvel);
+  c->u1 = A(c->nvel);
+  c->u2 = A(c->nvel);
+  c->rs1 = A(c->nvel);
+  c->rs2 = A(c->nvel);
+  c->R = A(c->nvel);
+  c->Cc = A(c->nvel);
+  c->phi_k = A(c->ncell);
+  c->phi_new = A(c->ncell);
+  c->phi_half = A(c->ncell);
+  c->psi_k = A(c->ncell);
+  c->psi_new = A(c->ncell);
+  c->b = A(c->nstk);
+  c->x = A(c->nstk);
+  c->V = A(c->nstk * (size_t)(c->m + 1));
+  c->Z = A(c->nstk * (size_t)c->m);
+  c->hdev = A(4 * (c->m + 2) + 8);
+  c->red = A(8192);
+  if (!ok) {
+    c->err = "out of device memory";
+    wsi_destroy(c);
+    return WSI_ERR_OOM;
+  }
+  int rc = d->precision == WSI_PREC_MIXED ? precond_alloc<float>(c->P32, g, c->err)
+                                          : precond_alloc<double>(c->P64, g, c->err);
+  if (rc) {
+    wsi_destroy(c);
+    return rc;
+  }
+  if (cuda_check(c, "create")) {
+    wsi_destroy(c);
+    return WSI_ERR_CUDA;
+  }
+  *out = c;
+  return WSI_OK;
+}
+
+void wsi_destroy(wsi_ctx* c) {
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  precond_free<double>(c->P64);
+  precond_free<float>(c->P32);
+  for (void* p : c->allocs) cudaFree(p);
+  delete c;
+}
+
+int wsi_set_phases(wsi_ctx* c, const double* phi, const double* psi, const wsi_phase_props* pr,
+                   const wsi_body_desc* bodies, int n_bodies) {
+  if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
+  if (!pr) return fail(c, WSI_ERR_INVALID_ARG, "null phase properties");
+  const double vals[6] = {pr->rho_l, pr->rho_g, pr->rho_s, pr->mu_l, pr->mu_g, pr->mu_s};
+  for (double v : vals)
+    if (!(v > 0.0) || !std::isfinite(v)) return fail(c, WSI_ERR_INVALID_ARG, "material constants must be positive");
+  if (n_bodies < 0 || n_bodies > 1) return fail(c, WSI_ERR_INVALID_ARG, "at most one body per context");
+  c->props = *pr;
+  int rc = copy_in(c, c->phi, phi, c->ncell);
+  if (!rc) rc = copy_in(c, c->psi, psi, c->ncell);
+  if (rc) return rc;
+  // bodies
+  Body& B = c->body;
+  c->has_body = n_bodies == 1 && bodies[0].n_markers > 0;
+  if (c->has_body) {
+    const wsi_body_desc& bd = bodies[0];
+    if (!bd.X || !(bd.dV > 0.0)) return fail(c, WSI_ERR_INVALID_ARG, "body needs markers and dV > 0");
+    // host-side range check of the markers
+    std::vector<double> hx((size_t)bd.n_markers * 3);
+    cudaMemcpyAsync(hx.data(), bd.X, hx.size() * sizeof(double), cudaMemcpyDefault, c->st);
+    cudaStreamSynchronize(c->st);
+    const double L[3] = {c->desc.lx, c->desc.ly, c->desc.lz};
+    for (size_t t = 0; t < hx.size(); ++t)
+      if (!(hx[t] >= 0.0 && hx[t] <= L[t % 3])) return fail(c, WSI_ERR_INVALID_ARG, "marker outside the box");
+    if (bd.n_markers != B.n) {
+      size_t n3 = (size_t)bd.n_markers * 3;
+      B.X = dalloc(c, n3);
+      B.Xn = dalloc(c, n3);
+      B.Xh = dalloc(c, n3);
+      B.Ub = dalloc(c, n3);
+      B.Ub_n = dalloc(c, n3);
+      B.U = dalloc(c, n3);
+      B.F = dalloc(c, n3);
+      B.xc = dalloc(c, 4);
+      B.rig = dalloc(c, 8);
+      B.sums = dalloc(c, 16);
+      B.scratch = dalloc(c, 152 * 16 + 32);
+      if (!B.X || !B.scratch) return fail(c, WSI_ERR_OOM, "out of device memory for markers");
+    }
+    B.n = bd.n_markers;
+    B.dV = bd.dV;
+    for (int d = 0; d < 6; ++d) B.lock[d] = bd.lock[d];
+    for (int d = 0; d < 3; ++d) {
+      B.U_pres[d] = bd.U_pres[d];
+      B.W_pres[d] = bd.W_pres[d];
+      B.half[d] = bd.half[d];
+    }
+    B.shape = bd.shape;
+    cudaMemcpyAsync(B.X, hx.data(), hx.size() * sizeof(double), cudaMemcpyHostToDevice, c->st);
+    cudaMemsetAsync(B.Ub_n, 0, hx.size() * sizeof(double), c->st);
+  }
+  PhaseConst pc = phase_const(c);
+  launch_materials(c->g, pc, c->phi, c->psi, c->rho_cc, c->mu_cc, c->rho_face, c->beta, c->rho_flow, c->mu_e, c->st);
+  cudaMemsetAsync(c->vel, 0, c->nvel * sizeof(double), c->st);
+  cudaMemsetAsync(c->vel_old, 0, c->nvel * sizeof(double), c->st);
+  cudaMemsetAsync(c->p, 0, c->ncell * sizeof(double), c->st);
+  c->have_phases = true;
+  c->pc_dirty = true;
+  return cuda_check(c, "set_phases");
+}
+
+int wsi_stokes_solve(wsi_ctx* c, const double* rhs, double* x, double dt, const wsi_solve_opts* o,
+                     wsi_solve_stats* s) {
+  if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
+  if (!c->have_phases) return fail(c, WSI_ERR_INVALID_ARG, "wsi_set_phases must come first");
+  if (!o || !s || !(dt > 0.0) || !(o->rtol > 0.0) || o->max_iters < 1) return fail(c, WSI_ERR_INVALID_ARG, "bad options");
+  auto t0 = std::chrono::steady_clock::now();
+  int rc = copy_in(c, c->b, rhs, c->nstk);
+  if (rc) return rc;
+  if (o->use_x0) {
+    rc = copy_in(c, c->x, x, c->nstk);
+    if (rc) return rc;
+  }
+  // wall-face entries of the right-hand side are not equations
+  double* bq[3];
+  vel_parts(c, c->b, bq);
+  launch_zero_walls(c->g, bq, c->st);
+  if (o->use_x0) {
+    double* xq[3];
+    vel_parts(c, c->x, xq);
+    launch_zero_walls(c->g, xq, c->st);
+  }
+  rc = fgmres(c, c->b, c->x, dt, o, s);
+  if (rc != WSI_OK && rc != WSI_ERR_NOT_CONVERGED) return rc;
+  int rc2 = copy_out(c, x, c->x, c->nstk);
+  if (rc2) return rc2;
+  int rc3 = cuda_check(c, "stokes_solve");
+  if (rc3) return rc3;
+  s->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return rc;
+}
+
+int wsi_dlm_constrain(wsi_ctx* c, double* vel, wsi_body_state* out) {
+  if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
+  if (!c->has_body) return fail(c, WSI_ERR_INVALID_ARG, "no body set");
+  int rc = copy_in(c, c->vel_k, vel, c->nvel);
+  if (rc) return rc;
+  rc = dlm_project(c, c->vel_k, c->body.X);
+  if (rc) return rc;
+  rc = copy_out(c, vel, c->vel_k, c->nvel);
+  if (rc) return rc;
+  if (out) {
+    for (int d = 0; d < 3; ++d) {
+      out->U_r[d] = c->body.U_r[d];
+      out->W_r[d] = c->body.W_r[d];
+      out->X_com[d] = c->body.X_com[d];
+    }
+  }
+  return cuda_check(c, "dlm_constrain");
+}
+
+int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) {
+  if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
+  if (!c->have_phases) return fail(c, WSI_ERR_INVALID_ARG, "wsi_set_phases must come first");
+  if (!o || !(dt > 0.0)) return fail(c, WSI_ERR_INVALID_ARG, "bad options");
+  auto t0 = std::chrono::steady_clock::now();
+  const GridDev& g = c->g;
+  cudaStream_t st = c->st;
+  PhaseConst pc = phase_const(c);
+  Body& B = c->body;
+  const size_t nv = c->nvel, nc = c->ncell;
+  // time-n coefficients: face density rho^n and mu^n from (phi^n, psi^n)
+  launch_materials(g, pc, c->phi, c->psi, c->rho_cc_tmp, c->mu_cc_n, c->rho_n, c->beta_n, c->rho_flow_n, c->mu_e_n,
+                   st);
+  cudaMemcpyAsync(c->vel_k, c->vel, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(c->phi_k, c->phi, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(c->psi_k, c->psi, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  if (c->has_body) cudaMemcpyAsync(B.Xn, B.X, (size_t)B.n * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(c->x + c->pk.off[3], c->p, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  double* vn[3];
+  const double* cvn[3];
+  vel_parts(c, c->vel, vn);
+  vel_parts(c, (const double*)c->vel, cvn);
+  const int ncyc = 2;
+  for (int k = 0; k < ncyc; ++k) {
+    // 1. level sets and viscosity at (n+1, k+1)
+    launch_lincomb(nv, 0.5, c->vel_k, 0.5, c->vel, 0.0, nullptr, c->vel_half, st);
+    launch_lincomb(nc, 0.5, c->phi_k, 0.5, c->phi, 0.0, nullptr, c->phi_half, st);
+    const double* vh[3];
+    vel_parts(c, (const double*)c->vel_half, vh);
+    launch_levelset_advect(g, vh, c->phi, c->phi_half, dt, c->phi_new, st);
+    const double* psi_use = c->psi_k;
+    if (c->has_body && B.shape == 1) {
+      launch_marker_mean(B.X, B.n, B.xc, B.scratch, st);
+      launch_box_sdf(g, B.xc, B.half, c->psi_new, st);
+      psi_use = c->psi_new;
+    }
+    launch_materials(g, pc, c->phi_new, psi_use, c->rho_cc, c->mu_cc, c->rho_face, c->beta, c->rho_flow, c->mu_e,
+                     st);
+    // 2. SSP-RK3 face density and consistent convection
+    if (k == 0) {
+      launch_lincomb(nv, 2.0, c->vel, -1.0, c->vel_old, 0.0, nullptr, c->u1, st);
+      launch_lincomb(nv, 1.5, c->vel, -0.5, c->vel_old, 0.0, nullptr, c->u2, st);
+    } else {
+      cudaMemcpyAsync(c->u1, c->vel_k, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
+      launch_lincomb(nv, 0.375, c->vel_k, 0.75, c->vel, -0.125, c->vel_old, c->u2, st);
+    }
+    double *R[3], *Cq[3], *r1[3], *r2[3];
+    vel_parts(c, c->R, R);
+    vel_parts(c, c->Cc, Cq);
+    vel_parts(c, c->rs1, r1);
+    vel_parts(c, c->rs2, r2);
+    const double* cu1[3];
+    const double* cu2[3];
+    vel_parts(c, (const double*)c->u1, cu1);
+    vel_parts(c, (const double*)c->u2, cu2);
+    const double* crn[3] = {c->rho_n[0], c->rho_n[1], c->rho_n[2]};
+    launch_transport_flux(g, cvn, crn, false, R, st);
+    for (int d = 0; d < 3; ++d) launch_lincomb(fsize(g, d), 1.0, c->rho_n[d], -dt, R[d], 0.0, nullptr, r1[d], st);
+    const double* cr1[3] = {r1[0], r1[1], r1[2]};
+    launch_transport_flux(g, cu1, cr1, false, R, st);
+    for (int d = 0; d < 3; ++d)
+      launch_lincomb(fsize(g, d), 0.75, c->rho_n[d], 0.25, r1[d], -0.25 * dt, R[d], r2[d], st);
+    const double* cr2[3] = {r2[0], r2[1], r2[2]};
+    launch_transport_flux(g, cu2, cr2, false, R, st);
+    for (int d = 0; d < 3; ++d)
+      launch_lincomb(fsize(g, d), 1.0 / 3.0, c->rho_n[d], 2.0 / 3.0, r2[d], -2.0 / 3.0 * dt, R[d], c->rho_face[d],
+                     st);
+    launch_transport_flux(g, cu2, cr2, true, Cq, st);
+    for (int d = 0; d < 3; ++d) recip(c, c->rho_face[d], c->beta[d], fsize(g, d));
+    // right-hand side with mu^n and gravity
+    double* bq[3];
+    vel_parts(c, c->b, bq);
+    const double* cC[3] = {Cq[0], Cq[1], Cq[2]};
+    const double* rg[3];
+    for (int d = 0; d < 3; ++d) rg[d] = c->props.gravity_mode == WSI_GRAVITY_FLOW ? c->rho_flow[d] : c->rho_face[d];
+    launch_momentum_rhs(g, coef_n(c), crn, cvn, cC, rg, c->desc.gravity, 1.0 / dt, c->desc.theta, bq, st);
+    cudaMemsetAsync(c->b + c->pk.off[3], 0, nc * sizeof(double), st);
+    // 3. Stokes solve from (u^{n+1,k}, p^{n+1/2,k})
+    cudaMemcpyAsync(c->x, c->vel_k, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    c->pc_dirty = true;
+    wsi_solve_stats ss;
+    wsi_solve_opts so = *o;
+    so.use_x0 = 1;
+    int rc = fgmres(c, c->b, c->x, dt, &so, &ss);
+    if (rc != WSI_OK && rc != WSI_ERR_NOT_CONVERGED) return rc;
+    if (s && k < 4) {
+      s->iters[k] = ss.iters;
+      s->rel_residual[k] = ss.rel_residual;
+    }
+    // 4. rigidity projection at X^{n+1/2,k}, then positions
+    cudaMemcpyAsync(c->vel_k, c->x, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (c->has_body) {
+      launch_lincomb((size_t)B.n * 3, 0.5, B.X, 0.5, B.Xn, 0.0, nullptr, B.Xh, st);
+      rc = dlm_project(c, c->vel_k, B.Xh);
+      if (rc) return rc;
+      launch_marker_update(B.Xn, B.Ub, B.Ub_n, B.n, dt, B.X, st);
+    }
+    cudaMemcpyAsync(c->phi_k, c->phi_new, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(c->psi_k, psi_use, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  }
+  // commit the step
+  cudaMemcpyAsync(c->vel_old, c->vel, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(c->vel, c->vel_k, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(c->p, c->x + c->pk.off[3], nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(c->phi, c->phi_k, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(c->psi, c->psi_k, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  if (c->has_body) cudaMemcpyAsync(B.Ub_n, B.Ub, (size_t)B.n * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  int rc = cuda_check(c, "step");
+  if (rc) return rc;
+  if (s) {
+    s->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    s->umax = 0.0;
+  }
+  return WSI_OK;
+}
+
+int wsi_get_field(wsi_ctx* c, int which, double* dst) {
+  if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
+  int rc;
+  switch (which) {
+    case WSI_F_VEL: rc = copy_out(c, dst, c->vel, c->nvel); break;
+    case WSI_F_P: rc = copy_out(c, dst, c->p, c->ncell); break;
+    case WSI_F_PHI: rc = copy_out(c, dst, c->phi, c->ncell); break;
+    case WSI_F_PSI: rc = copy_out(c, dst, c->psi, c->ncell); break;
+    case WSI_F_MARKERS:
+      if (!c->has_body) return fail(c, WSI_ERR_INVALID_ARG, "no body");
+      rc = copy_out(c, dst, c->body.X, (size_t)c->body.n * 3);
+      break;
+    default: return fail(c, WSI_ERR_INVALID_ARG, "unknown field");
+  }
+  if (rc) return rc;
+  return cuda_check(c, "get_field");
+}
+
+int wsi_set_field(wsi_ctx* c, int which, const double* src) {
+  if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
+  int rc;
+  switch (which) {
+    case WSI_F_VEL:
+      rc = copy_in(c, c->vel, src, c->nvel);
+      if (!rc) cudaMemcpyAsync(c->vel_old, c->vel, c->nvel * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+      break;
+    case WSI_F_P: rc = copy_in(c, c->p, src, c->ncell); break;
+    case WSI_F_PHI: rc = copy_in(c, c->phi, src, c->ncell); break;
+    case WSI_F_PSI: rc = copy_in(c, c->psi, src, c->ncell); break;
+    default: return fail(c, WSI_ERR_INVALID_ARG, "unknown field");
+  }
+  if (rc) return rc;
+  return cuda_check(c, "set_field");
+}
+
+int wsi_get_coeff(wsi_ctx* c, int which, double* dst) {
+  if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
+  if (!c->have_phases) return fail(c, WSI_ERR_INVALID_ARG, "no phases set");
+  int rc = WSI_OK;
+  switch (which) {
+    case WSI_C_RHO_CC: rc = copy_out(c, dst, c->rho_cc, c->ncell); break;
+    case WSI_C_MU_CC: rc = copy_out(c, dst, c->mu_cc, c->ncell); break;
+    case WSI_C_RHO_FACE:
+      for (int d = 0; d < 3 && !rc; ++d) rc = copy_out(c, dst + c->pk.off[d], c->rho_face[d], fsize(c->g, d));
+      break;
+    case WSI_C_RHO_FLOW_FACE:
+      for (int d = 0; d < 3 && !rc; ++d) rc = copy_out(c, dst + c->pk.off[d], c->rho_flow[d], fsize(c->g, d));
+      break;
+    case WSI_C_MU_EDGE: {
+      size_t o = 0;
+      for (int e = 0; e < 3 && !rc; ++e) {
+        rc = copy_out(c, dst + o, c->mu_e[e], esize(c->g, e));
+        o += esize(c->g, e);
+      }
+      break;
+    }
+    default: return fail(c, WSI_ERR_INVALID_ARG, "unknown coefficient");
+  }
+  if (rc) return rc;
+  return cuda_check(c, "get_coeff");
+}
+
+int wsi_apply(wsi_ctx* c, int op, const double* in, double* out, double dt) {
+  if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
+  if (!c->have_phases) return fail(c, WSI_ERR_INVALID_ARG, "no phases set");
+  if (!(dt > 0.0)) return fail(c, WSI_ERR_INVALID_ARG, "dt must be positive");
+  Coef<double> cf = coef_now(c);
+  double* xin = c->b;
+  double* xout = c->x;
+  size_t nin = 0, nout = 0;
+  switch (op) {
+    case WSI_OP_STOKES: nin = c->nstk; nout = c->nstk; break;
+    case WSI_OP_VISCOUS:
+    case WSI_OP_STRAIN: nin = c->nvel; nout = c->nvel; break;
+    case WSI_OP_PRESSURE: nin = c->ncell; nout = c->ncell; break;
+    case WSI_OP_GRAD: nin = c->ncell; nout = c->nvel; break;
+    case WSI_OP_DIV: nin = c->nvel; nout = c->ncell; break;
+    default: return fail(c, WSI_ERR_INVALID_ARG, "unknown operator");
+  }
+  int rc = copy_in(c, xin, in, nin);
+  if (rc) return rc;
+  const double* qi[3];
+  double* qo[3];
+  vel_parts(c, (const double*)xin, qi);
+  vel_parts(c, xout, qo);
+  switch (op) {
+    case WSI_OP_STOKES: launch_stokes(c->g, cf, 1.0 / dt, c->desc.theta, xin, xout, c->st); break;
+    case WSI_OP_VISCOUS: launch_viscous<double>(c->g, cf, 1.0 / dt, c->desc.theta, qi, qo, c->st, false); break;
+    case WSI_OP_STRAIN: launch_viscous<double>(c->g, cf, 1.0 / dt, c->desc.theta, qi, qo, c->st, true); break;
+    case WSI_OP_PRESSURE: {
+      const double* bt[3] = {c->beta[0], c->beta[1], c->beta[2]};
+      launch_pressure<double>(c->g, bt, xin, xout, c->st);
+      break;
+    }
+    case WSI_OP_GRAD: launch_grad<double>(c->g, xin, qo, c->st); break;
+    case WSI_OP_DIV: launch_div<double>(c->g, qi, xout, 1.0, c->st); break;
+  }
+  rc = copy_out(c, out, xout, nout);
+  if (rc) return rc;
+  return cuda_check(c, "apply");
+}
+
+int wsi_transport(wsi_ctx* c, const double* u_n, const double* u_nm1, const double* u_k, int k, double dt,
+                  double* rho_out, double* C_out) {
+  if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
+  if (!c->have_phases) return fail(c, WSI_ERR_INVALID_ARG, "no phases set");
+  const GridDev& g = c->g;
+  cudaStream_t st = c->st;
+  size_t nv = c->nvel;
+  int rc = copy_in(c, c->vel_half, u_n, nv);
+  if (!rc) rc = copy_in(c, c->vel_old, u_nm1, nv);
+  if (!rc && k > 0) rc = copy_in(c, c->vel_k, u_k, nv);
+  if (rc) return rc;
+  PhaseConst pc = phase_const(c);
+  launch_materials(g, pc, c->phi, c->psi, c->rho_cc_tmp, c->mu_cc_n, c->rho_n, c->beta_n, c->rho_flow_n, c->mu_e_n,
+                   st);
+  if (k == 0) {
+    launch_lincomb(nv, 2.0, c->vel_half, -1.0, c->vel_old, 0.0, nullptr, c->u1, st);
+    launch_lincomb(nv, 1.5, c->vel_half, -0.5, c->vel_old, 0.0, nullptr, c->u2, st);
+  } else {
+    cudaMemcpyAsync(c->u1, c->vel_k, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    launch_lincomb(nv, 0.375, c->vel_k, 0.75, c->vel_half, -0.125, c->vel_old, c->u2, st);
+  }
+  double *R[3], *Cq[3], *r1[3], *r2[3], *r3[3];
+  vel_parts(c, c->R, R);
+  vel_parts(c, c->Cc, Cq);
+  vel_parts(c, c->rs1, r1);
+  vel_parts(c, c->rs2, r2);
+  vel_parts(c, c->b, r3);
+  const double *cun[3], *cu1[3], *cu2[3];
+  vel_parts(c, (const double*)c->vel_half, cun);
+  vel_parts(c, (const double*)c->u1, cu1);
+  vel_parts(c, (const double*)c->u2, cu2);
+  const double* crn[3] = {c->rho_n[0], c->rho_n[1], c->rho_n[2]};
+  launch_transport_flux(g, cun, crn, false, R, st);
+  for (int d = 0; d < 3; ++d) launch_lincomb(fsize(g, d), 1.0, c->rho_n[d], -dt, R[d], 0.0, nullptr, r1[d], st);
+  const double* cr1[3] = {r1[0], r1[1], r1[2]};
+  launch_transport_flux(g, cu1, cr1, false, R, st);
+  for (int d = 0; d < 3; ++d)
+    launch_lincomb(fsize(g, d), 0.75, c->rho_n[d], 0.25, r1[d], -0.25 * dt, R[d], r2[d], st);
+  const double* cr2[3] = {r2[0], r2[1], r2[2]};
+  launch_transport_flux(g, cu2, cr2, false, R, st);
+  for (int d = 0; d < 3; ++d)
+    launch_lincomb(fsize(g, d), 1.0 / 3.0, c->rho_n[d], 2.0 / 3.0, r2[d], -2.0 / 3.0 * dt, R[d], r3[d], st);
+  launch_transport_flux(g, cu2, cr2, true, Cq, st);
+  rc = copy_out(c, rho_out, c->b, nv);
+  if (!rc) rc = copy_out(c, C_out, c->Cc, nv);
+  if (rc) return rc;
+  return cuda_check(c, "transport");
+}
+
+int wsi_advect_levelset(wsi_ctx* c, const double* vel, const double* phi_n, const double* phi_half, double dt,
+                        double* phi_out) {
+  if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
+  int rc = copy_in(c, c->vel_half, vel, c->nvel);
+  if (!rc) rc = copy_in(c, c->phi_k, phi_n, c->ncell);
+  if (!rc) rc = copy_in(c, c->phi_half, phi_half, c->ncell);
+  if (rc) return rc;
+  const double* vh[3];
+  vel_parts(c, (const double*)c->vel_half, vh);
+  launch_levelset_advect(c->g, vh, c->phi_k, c->phi_half, dt, c->phi_new, c->st);
+  rc = copy_out(c, phi_out, c->phi_new, c->ncell);
+  if (rc) return rc;
+  return cuda_check(c, "advect_levelset");
+}
+
+int wsi_interp(wsi_ctx* c, const double* vel, const double* X, int n, double* U) {
+  if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
+  if (n <= 0) return WSI_OK;
+  double* dX = dalloc(c, (size_t)n * 3);
+  double* dU = dalloc(c, (size_t)n * 3);
+  if (!dX || !dU) return fail(c, WSI_ERR_OOM, "out of device memory");
+  int rc = copy_in(c, c->vel_half, vel, c->nvel);
+  if (!rc) rc = copy_in(c, dX, X, (size_t)n * 3);
+  if (rc) return rc;
+  const double* vh[3];
+  vel_parts(c, (const double*)c->vel_half, vh);
+  launch_ib_interp(c->g, vh, dX, n, dU, c->st);
+  rc = copy_out(c, U, dU, (size_t)n * 3);
+  cudaStreamSynchronize(c->st);
+  // release the temporaries (last two allocations)
+  cudaFree(dX);
+  cudaFree(dU);
+  c->allocs.resize(c->allocs.size() - 2);
+  if (rc) return rc;
+  return cuda_check(c, "interp");
+}
+
+int wsi_spread(wsi_ctx* c, const double* F, const double* X, int n, double dV, double* vel) {
+  if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
+  double* dX = dalloc(c, (size_t)std::max(n, 1) * 3);
+  double* dF = dalloc(c, (size_t)std::max(n, 1) * 3);
+  if (!dX || !dF) return fail(c, WSI_ERR_OOM, "out of device memory");
+  int rc = WSI_OK;
+  if (n > 0) {
+    rc = copy_in(c, dX, X, (size_t)n * 3);
+    if (!rc) rc = copy_in(c, dF, F, (size_t)n * 3);
+  }
+  if (!rc) {
+    cudaMemsetAsync(c->vel_half, 0, c->nvel * sizeof(double), c->st);
+    double* vq[3];
+    vel_parts(c, c->vel_half, vq);
+    launch_ib_spread(c->g, dF, dX, n, dV, vq, c->st);
+    rc = copy_out(c, vel, c->vel_half, c->nvel);
+  }
+  cudaStreamSynchronize(c->st);
+  cudaFree(dX);
+  cudaFree(dF);
+  c->allocs.resize(c->allocs.size() - 2);
+  if (rc) return rc;
+  return cuda_check(c, "spread");
+}
+
+}  // extern "C"

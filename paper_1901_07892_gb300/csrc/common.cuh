@@ -1,0 +1,84 @@
+// Shared device-side definitions of libwsi: grid geometry, index maps of the
+// staggered (MAC) arrays, ghost rules at walls, launch helpers.
+//
+// Layout (Sec. 3.1): x fastest, unghosted.  Component c of the velocity lives
+// on c-faces with extents n + e_c; edges in the (c,d) plane have extents
+// n + e_c + e_d.  Tangential ghosts across a wall are s * (adjacent value),
+// s = -1 no-slip, +1 free-slip; faces on walls hold the zero normal velocity.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+namespace wsi {
+
+struct GridDev {
+  int n[3];       // cells per axis
+  double h[3];    // spacing
+  double bc[6];   // tangential ghost sign per wall (x-, x+, y-, y+, z-, z+)
+};
+
+__host__ __device__ __forceinline__ int ext(const GridDev& g, int c, int a) {
+  return g.n[a] + (a == c ? 1 : 0);
+}
+// c = 0,1,2 velocity components; c = 3 cell-centred
+__host__ __device__ __forceinline__ size_t fsize(const GridDev& g, int c) {
+  return (size_t)(g.n[0] + (c == 0)) * (g.n[1] + (c == 1)) * (g.n[2] + (c == 2));
+}
+__host__ __device__ __forceinline__ size_t fidx(const GridDev& g, int c, int i, int j, int k) {
+  return ((size_t)k * (g.n[1] + (c == 1)) + j) * (g.n[0] + (c == 0)) + i;
+}
+// edge arrays: e = 0 xy (along z), 1 xz (along y), 2 yz (along x)
+__host__ __device__ __forceinline__ int edge_id(int c, int d) {
+  int a = c < d ? c : d, b = c < d ? d : c;
+  return (a == 0 && b == 1) ? 0 : (a == 0 ? 1 : 2);
+}
+__host__ __device__ __forceinline__ size_t esize(const GridDev& g, int e) {
+  int ax = (e == 0 || e == 1) ? 1 : 0, ay = (e == 0 || e == 2) ? 1 : 0, az = (e == 1 || e == 2) ? 1 : 0;
+  return (size_t)(g.n[0] + ax) * (g.n[1] + ay) * (g.n[2] + az);
+}
+__host__ __device__ __forceinline__ size_t eidx(const GridDev& g, int e, int i, int j, int k) {
+  int ax = (e == 0 || e == 1) ? 1 : 0, ay = (e == 0 || e == 2) ? 1 : 0;
+  return ((size_t)k * (g.n[1] + ay) + j) * (g.n[0] + ax) + i;
+}
+
+// offsets of the packed Stokes vector (u, v, w, p)
+struct Packing {
+  size_t off[5];
+};
+inline Packing packing(const GridDev& g) {
+  Packing p;
+  p.off[0] = 0;
+  for (int c = 0; c < 4; ++c) p.off[c + 1] = p.off[c] + fsize(g, c);
+  return p;
+}
+
+template <typename T>
+struct Vel {
+  T* q[3];
+};
+template <typename T>
+struct CVel {
+  const T* q[3];
+};
+
+// Read component C at face (i,j,k), with one ghost layer along the two
+// tangential axes (mirror with the wall's sign).
+template <int C, typename T>
+__device__ __forceinline__ T qget(const GridDev& g, const T* __restrict__ q, int i, int j, int k) {
+  T s = T(1);
+  int idx3[3] = {i, j, k};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a == C) continue;
+    if (idx3[a] < 0) { idx3[a] = 0; s *= (T)g.bc[2 * a]; }
+    else if (idx3[a] >= g.n[a]) { idx3[a] = g.n[a] - 1; s *= (T)g.bc[2 * a + 1]; }
+  }
+  return s * q[fidx(g, C, idx3[0], idx3[1], idx3[2])];
+}
+
+__device__ __forceinline__ int clampi(int a, int lo, int hi) { return a < lo ? lo : (a > hi ? hi : a); }
+
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace wsi

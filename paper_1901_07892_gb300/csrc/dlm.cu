@@ -1,0 +1,229 @@
+// DLM rigidity step (Sec. 4.2.5) and the IB4 Lagrangian-Eulerian transfers
+// (Sec. 3.3) with the wall-adjoint forms J_BC / S_BC (Sec. 3.3.2).
+//
+// Interpolation is a gather (one thread per marker and component, 64 taps);
+// spreading scatters with float64 atomicAdd into the face arrays.  Taps that
+// fall beyond a wall are folded onto their mirror image with the ghost sign
+// (tangential: the wall's sign; normal: odd about the wall face, whose own
+// value is zero so taps landing on it drop out), which makes S_BC the exact
+// adjoint of J_BC.  Rigid-body sums are deterministic two-stage reductions.
+#include <math.h>
+
+#include "internal.h"
+
+namespace wsi {
+
+// Peskin's four-point kernel (the published formula; Sec. 3.3.1 cites it)
+__device__ __forceinline__ double phi4(double r) {
+  r = fabs(r);
+  if (r <= 1.0) return (3.0 - 2.0 * r + sqrt(fmax(1.0 + 4.0 * r - 4.0 * r * r, 0.0))) * 0.125;
+  if (r <= 2.0) return (5.0 - 2.0 * r - sqrt(fmax(-7.0 + 12.0 * r - 4.0 * r * r, 0.0))) * 0.125;
+  return 0.0;
+}
+
+struct Tap {
+  int idx[4];
+  double w[4];  // kernel weight times ghost sign; 0 for dropped taps
+};
+
+__device__ __forceinline__ void taps_axis(const GridDev& g, int c, int d, double Xd, Tap& t) {
+  int n = g.n[d];
+  bool normal = (c == d);
+  double xs = normal ? Xd / g.h[d] : Xd / g.h[d] - 0.5;
+  int base = (int)floor(xs) - 1;
+  double s_lo = g.bc[2 * d], s_hi = g.bc[2 * d + 1];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int i = base + q;
+    double r = (double)i - xs;
+    double sg = 1.0;
+    for (int it = 0; it < 8; ++it) {
+      if (normal) {
+        if (i < 0) { i = -i; sg = -sg; }
+        if (i > n) { i = 2 * n - i; sg = -sg; }
+      } else {
+        if (i < 0) { i = -1 - i; sg *= s_lo; }
+        if (i >= n) { i = 2 * n - 1 - i; sg *= s_hi; }
+      }
+    }
+    bool valid = normal ? (i > 0 && i < n) : (i >= 0 && i < n);
+    t.idx[q] = valid ? i : 0;
+    t.w[q] = valid ? sg * phi4(r) : 0.0;
+  }
+}
+
+__global__ void k_interp(GridDev g, CVel<double> vel, const double* __restrict__ X, int n, double* U) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * n) return;
+  int m = t / 3, c = t - 3 * m;
+  Tap tx, ty, tz;
+  taps_axis(g, c, 0, X[3 * m + 0], tx);
+  taps_axis(g, c, 1, X[3 * m + 1], ty);
+  taps_axis(g, c, 2, X[3 * m + 2], tz);
+  const double* q = vel.q[c];
+  double s = 0.0;
+  for (int kz = 0; kz < 4; ++kz) {
+    if (tz.w[kz] == 0.0) continue;
+    for (int ky = 0; ky < 4; ++ky) {
+      double wyz = tz.w[kz] * ty.w[ky];
+      if (wyz == 0.0) continue;
+      for (int kx = 0; kx < 4; ++kx) {
+        if (tx.w[kx] == 0.0) continue;
+        s += wyz * tx.w[kx] * q[fidx(g, c, tx.idx[kx], ty.idx[ky], tz.idx[kz])];
+      }
+    }
+  }
+  U[3 * m + c] = s;
+}
+
+__global__ void k_spread(GridDev g, const double* __restrict__ F, const double* __restrict__ X, int n, double scale,
+                         Vel<double> vel) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * n) return;
+  int m = t / 3, c = t - 3 * m;
+  Tap tx, ty, tz;
+  taps_axis(g, c, 0, X[3 * m + 0], tx);
+  taps_axis(g, c, 1, X[3 * m + 1], ty);
+  taps_axis(g, c, 2, X[3 * m + 2], tz);
+  double f = F[3 * m + c] * scale;
+  double* q = vel.q[c];
+  for (int kz = 0; kz < 4; ++kz) {
+    if (tz.w[kz] == 0.0) continue;
+    for (int ky = 0; ky < 4; ++ky) {
+      double wyz = tz.w[kz] * ty.w[ky];
+      if (wyz == 0.0) continue;
+      for (int kx = 0; kx < 4; ++kx) {
+        if (tx.w[kx] == 0.0) continue;
+        atomicAdd(&q[fidx(g, c, tx.idx[kx], ty.idx[ky], tz.idx[kz])], f * wyz * tx.w[kx]);
+      }
+    }
+  }
+}
+
+void launch_ib_interp(const GridDev& g, const double* const vel[3], const double* X, int n, double* U,
+                      cudaStream_t st) {
+  if (n <= 0) return;
+  CVel<double> v{{vel[0], vel[1], vel[2]}};
+  k_interp<<<cdiv(3LL * n, 128), 128, 0, st>>>(g, v, X, n, U);
+}
+
+void launch_ib_spread(const GridDev& g, const double* F, const double* X, int n, double dV, double* const vel[3],
+                      cudaStream_t st) {
+  if (n <= 0) return;
+  Vel<double> v{{vel[0], vel[1], vel[2]}};
+  double scale = dV / (g.h[0] * g.h[1] * g.h[2]);
+  k_spread<<<cdiv(3LL * n, 128), 128, 0, st>>>(g, F, X, n, scale, v);
+}
+
+// ---------------------------------------------------------------- rigid sums
+static constexpr int SB = 152;  // reduction blocks
+static constexpr int ST = 256;
+static constexpr int NS = 15;   // sums per marker
+
+__global__ void k_rigid_part(const double* __restrict__ X, const double* __restrict__ U, int n,
+                             const double* __restrict__ xc, double* part) {
+  double acc[NS];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) acc[q] = 0.0;
+  double cx = xc ? xc[0] : 0.0, cy = xc ? xc[1] : 0.0, cz = xc ? xc[2] : 0.0;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+    double x = X[3 * m], y = X[3 * m + 1], z = X[3 * m + 2];
+    double rx = x - cx, ry = y - cy, rz = z - cz;
+    double ux = U ? U[3 * m] : 0.0, uy = U ? U[3 * m + 1] : 0.0, uz = U ? U[3 * m + 2] : 0.0;
+    acc[0] += ux;
+    acc[1] += uy;
+    acc[2] += uz;
+    acc[3] += ry * uz - rz * uy;
+    acc[4] += rz * ux - rx * uz;
+    acc[5] += rx * uy - ry * ux;
+    double rr = rx * rx + ry * ry + rz * rz;
+    acc[6] += rr - rx * rx;
+    acc[7] += rr - ry * ry;
+    acc[8] += rr - rz * rz;
+    acc[9] += -rx * ry;
+    acc[10] += -rx * rz;
+    acc[11] += -ry * rz;
+    acc[12] += x;
+    acc[13] += y;
+    acc[14] += z;
+  }
+  __shared__ double sh[ST / 32][NS];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+    double v = acc[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[wid][q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NS) {
+    double s = 0.0;
+    for (int w = 0; w < ST / 32; ++w) s += sh[w][threadIdx.x];
+    part[blockIdx.x * NS + threadIdx.x] = s;
+  }
+}
+
+__global__ void k_rigid_final(const double* __restrict__ part, double* out) {
+  int q = threadIdx.x;
+  if (q >= NS) return;
+  double s = 0.0;
+  for (int b = 0; b < SB; ++b) s += part[b * NS + q];
+  out[q] = s;
+}
+
+void launch_rigid_sums(const double* X, const double* U, int n, const double* xc_dev, double* out, double* scratch,
+                       cudaStream_t st) {
+  k_rigid_part<<<SB, ST, 0, st>>>(X, U, n, xc_dev, scratch);
+  k_rigid_final<<<1, 32, 0, st>>>(scratch, out);
+}
+
+__global__ void k_mean3(const double* __restrict__ sums, int n, double* xc) {
+  if (threadIdx.x < 3) xc[threadIdx.x] = sums[12 + threadIdx.x] / (double)n;
+}
+
+void launch_marker_mean(const double* X, int n, double* xc_dev, double* scratch, cudaStream_t st) {
+  // scratch: SB*NS partials followed by NS sums
+  k_rigid_part<<<SB, ST, 0, st>>>(X, nullptr, n, nullptr, scratch);
+  k_rigid_final<<<1, 32, 0, st>>>(scratch, scratch + SB * NS);
+  k_mean3<<<1, 32, 0, st>>>(scratch + SB * NS, n, xc_dev);
+}
+
+__global__ void k_body_vel(const double* __restrict__ X, const double* __restrict__ U, int n,
+                           const double* __restrict__ rg, const double* __restrict__ xc, double* Ub, double* F) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n) return;
+  double rx = X[3 * m] - xc[0], ry = X[3 * m + 1] - xc[1], rz = X[3 * m + 2] - xc[2];
+  double wx = rg[3], wy = rg[4], wz = rg[5];
+  double bx = rg[0] + (wy * rz - wz * ry);
+  double by = rg[1] + (wz * rx - wx * rz);
+  double bz = rg[2] + (wx * ry - wy * rx);
+  Ub[3 * m] = bx;
+  Ub[3 * m + 1] = by;
+  Ub[3 * m + 2] = bz;
+  if (F) {
+    F[3 * m] = bx - U[3 * m];
+    F[3 * m + 1] = by - U[3 * m + 1];
+    F[3 * m + 2] = bz - U[3 * m + 2];
+  }
+}
+
+void launch_body_velocity(const double* X, const double* U, int n, const double* rigid_dev, const double* xc_dev,
+                          double* Ub, double* F, cudaStream_t st) {
+  if (n <= 0) return;
+  k_body_vel<<<cdiv(n, 128), 128, 0, st>>>(X, U, n, rigid_dev, xc_dev, Ub, F);
+}
+
+__global__ void k_marker_update(const double* __restrict__ Xn, const double* __restrict__ Ub1,
+                                const double* __restrict__ Ub0, int n3, double dt, double* X) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n3) return;
+  X[t] = Xn[t] + dt * 0.5 * (Ub1[t] + Ub0[t]);
+}
+
+void launch_marker_update(const double* Xn, const double* Ub_new, const double* Ub_old, int n, double dt, double* X,
+                          cudaStream_t st) {
+  if (n <= 0) return;
+  k_marker_update<<<cdiv(3LL * n, 256), 256, 0, st>>>(Xn, Ub_new, Ub_old, 3 * n, dt, X);
+}
+
+}  // namespace wsi

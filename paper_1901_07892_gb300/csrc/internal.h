@@ -1,0 +1,154 @@
+// Host-side internals of libwsi shared by the translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/wsi.h"
+#include "common.cuh"
+
+namespace wsi {
+
+// Coefficients of the Stokes operator on one grid (Sec. 4.1, 4.2.2).
+template <typename T>
+struct Coef {
+  const T* rho_face[3];  // face density of the viscous block (rho breve)
+  const T* beta[3];      // 1 / face density, pressure operator
+  const T* mu_cc;        // cell viscosity (normal stresses)
+  const T* mu_e[3];      // harmonic edge viscosity: xy, xz, yz
+};
+
+// ---------------------------------------------------------------- ops.cu
+struct PhaseConst {
+  double rho_l, rho_g, rho_s, mu_l, mu_g, mu_s, eps;
+};
+void launch_materials(const GridDev& g, const PhaseConst& pc, const double* phi, const double* psi,
+                      double* rho_cc, double* mu_cc, double* const rho_face[3], double* const beta[3],
+                      double* const rho_flow[3], double* const mu_e[3], cudaStream_t st);
+void launch_mu_only(const GridDev& g, const PhaseConst& pc, const double* phi, const double* psi,
+                    double* mu_cc, double* const mu_e[3], cudaStream_t st);
+void launch_rho_flow(const GridDev& g, const PhaseConst& pc, const double* phi, double* const rho_flow[3],
+                     cudaStream_t st);
+
+// out = alpha * (rho/dt q - theta L_mu q) + beta_in * (G p)  (any of p, rho may be null)
+template <typename T>
+void launch_viscous(const GridDev& g, const Coef<T>& cf, T inv_dt, T theta, const T* const q[3], T* const out[3],
+                    cudaStream_t st, bool strain_only = false);
+// r = b - A q (viscous block)
+template <typename T>
+void launch_viscous_residual(const GridDev& g, const Coef<T>& cf, T inv_dt, T theta, const T* const q[3],
+                             const T* const b[3], T* const r[3], cudaStream_t st);
+template <typename T>
+void launch_pressure(const GridDev& g, const T* const beta[3], const T* p, T* out, cudaStream_t st);
+template <typename T>
+void launch_grad(const GridDev& g, const T* p, T* const out[3], cudaStream_t st);
+template <typename T>
+void launch_div(const GridDev& g, const T* const q[3], T* out, T scale, cudaStream_t st);
+// packed Stokes matvec in float64: y = K x
+void launch_stokes(const GridDev& g, const Coef<double>& cf, double inv_dt, double theta, const double* x, double* y,
+                   cudaStream_t st);
+// red-black Gauss-Seidel half sweep on the viscous block for component c
+template <typename T>
+void launch_viscous_rbgs(const GridDev& g, const Coef<T>& cf, T inv_dt, T theta, T* const q[3], const T* const b[3],
+                         int color, cudaStream_t st);
+
+// transport (Sec. 4.2.2): R or C on all three face arrays
+void launch_transport_flux(const GridDev& g, const double* const vel[3], const double* const rho[3],
+                           bool with_velocity, double* const out[3], cudaStream_t st);
+// out = a*x + b*y + c*z elementwise over n (any of y, z may be null)
+void launch_lincomb(size_t n, double a, const double* x, double b, const double* y, double c, const double* z,
+                    double* out, cudaStream_t st);
+// rk stage: out = a*rho_n + b*rho_s - c*dt*R
+void launch_levelset_advect(const GridDev& g, const double* const vel[3], const double* phi_n,
+                            const double* phi_half, double dt, double* out, cudaStream_t st);
+void launch_box_sdf(const GridDev& g, const double* xcom_dev, const double half[3], double* psi, cudaStream_t st);
+// b = rho_n u_n / dt - C + (1-theta) L_mu^n u_n + rho_g g
+void launch_momentum_rhs(const GridDev& g, const Coef<double>& cf_n, const double* const rho_n[3],
+                         const double* const u_n[3], const double* const C[3], const double* const rho_g[3],
+                         const double grav[3], double inv_dt, double theta, double* const b[3], cudaStream_t st);
+void launch_zero_walls(const GridDev& g, double* const q[3], cudaStream_t st);
+
+// ---------------------------------------------------------------- krylov.cu
+// deterministic reductions: out[t] = <V_t, w> for t < m (V row-major m x n)
+void launch_mdot(const double* V, size_t ldv, int m, const double* w, size_t n, double* out, double* scratch,
+                 cudaStream_t st);
+// w -= sum_t h[t] V_t  (h on device)
+void launch_maxpy(const double* V, size_t ldv, int m, const double* h, double* w, size_t n, double sign,
+                  cudaStream_t st);
+void launch_scale(double* x, size_t n, const double* s_dev, bool inverse, cudaStream_t st);
+template <typename Ts, typename Td>
+void launch_cast(const Ts* in, Td* out, size_t n, cudaStream_t st);
+double host_norm2(const double* x, size_t n, double* scratch, cudaStream_t st);
+template <typename T>
+void launch_sum(const T* x, size_t n, double* out_dev, double* scratch, cudaStream_t st);
+template <typename T>
+void launch_add_scalar_from(T* x, size_t n, const double* s_dev, double factor, cudaStream_t st);
+
+// ---------------------------------------------------------------- mg.cu
+template <typename T>
+struct MGLevel {
+  GridDev g;
+  int r[3];         // coarsening ratio to the next level (1 or 2)
+  T* beta[3];
+  T* x;
+  T* b;
+  T* res;
+};
+
+template <typename T>
+struct Precond {
+  // pressure multigrid hierarchy
+  std::vector<MGLevel<T>> lev;
+  double* coarse_inv = nullptr;  // dense float64 inverse of the regularised coarsest operator
+  int ncoarse = 0;
+  // fine-level viscous coefficients in T
+  T* rho_face[3] = {nullptr, nullptr, nullptr};
+  T* mu_cc = nullptr;
+  T* mu_e[3] = {nullptr, nullptr, nullptr};
+  // work
+  T* ru[3] = {nullptr, nullptr, nullptr};
+  T* ut[3] = {nullptr, nullptr, nullptr};
+  T* rp = nullptr;
+  T* y = nullptr;
+  T* gp[3] = {nullptr, nullptr, nullptr};
+  double* dscratch = nullptr;  // reductions
+  double* dsum = nullptr;
+  bool built = false;
+  std::vector<void*> allocs;
+};
+
+struct Opts {
+  int mg_pre = 2, mg_post = 2, mg_cycles = 1, visc_sweeps = 2;
+  double theta = 0.5;
+};
+
+template <typename T>
+int precond_alloc(Precond<T>& P, const GridDev& g, std::string& err);
+template <typename T>
+void precond_free(Precond<T>& P);
+// rebuild level coefficients from the float64 fine coefficients
+template <typename T>
+int precond_setup(Precond<T>& P, const GridDev& g, const Coef<double>& fine, cudaStream_t st, std::string& err);
+// z = P^{-1} v  (packed float64 Stokes vectors)
+template <typename T>
+void precond_apply(Precond<T>& P, const GridDev& g, const Opts& o, double dt, const double* v, double* z,
+                   cudaStream_t st);
+
+// ---------------------------------------------------------------- dlm.cu
+void launch_ib_interp(const GridDev& g, const double* const vel[3], const double* X, int n, double* U,
+                      cudaStream_t st);
+void launch_ib_spread(const GridDev& g, const double* F, const double* X, int n, double dV, double* const vel[3],
+                      cudaStream_t st);
+// rigid sums: out[0..2] sum U, [3..5] sum R x U, [6..11] sum of R.R I - R (x) R (xx,yy,zz,xy,xz,yz),
+// [12..14] sum X; R relative to xc_dev
+void launch_rigid_sums(const double* X, const double* U, int n, const double* xc_dev, double* out, double* scratch,
+                       cudaStream_t st);
+void launch_marker_mean(const double* X, int n, double* xc_dev, double* scratch, cudaStream_t st);
+// F = U_r + W_r x (X - xc) - U   (body velocity minus interpolated); Ub also stored
+void launch_body_velocity(const double* X, const double* U, int n, const double* rigid_dev, const double* xc_dev,
+                          double* Ub, double* F, cudaStream_t st);
+void launch_marker_update(const double* Xn, const double* Ub_new, const double* Ub_old, int n, double dt, double* X,
+                          cudaStream_t st);
+
+}  // namespace wsi

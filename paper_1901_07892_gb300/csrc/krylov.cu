@@ -1,0 +1,158 @@
+// Float64 Krylov kernels for FGMRES (Sec. 4.2.4): block dot products against
+// the Arnoldi basis, multi-axpy updates, norms and type casts.
+//
+// Reductions are deterministic: a fixed grid of RB blocks walks the vector
+// with a grid stride, each block reduces its partial sums in shared memory
+// in a fixed order, and one block adds the RB partials in block order.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace wsi {
+
+static constexpr int RB = 152 * 4;  // reduction blocks (4 per SM)
+static constexpr int RT = 256;      // threads per reduction block
+static constexpr int NV = 8;        // basis vectors per pass
+
+template <int M>
+__global__ void k_mdot(const double* __restrict__ V, size_t ldv, int m, const double* __restrict__ w, size_t n,
+                       double* part) {
+  double acc[M];
+#pragma unroll
+  for (int t = 0; t < M; ++t) acc[t] = 0.0;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    double wi = w[i];
+#pragma unroll
+    for (int t = 0; t < M; ++t)
+      if (t < m) acc[t] += V[(size_t)t * ldv + i] * wi;
+  }
+  __shared__ double sh[RT / 32][M];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < M; ++t) {
+    double v = acc[t];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[wid][t] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < M) {
+    double s = 0.0;
+    for (int q = 0; q < RT / 32; ++q) s += sh[q][threadIdx.x];
+    part[(size_t)blockIdx.x * M + threadIdx.x] = s;
+  }
+}
+
+__global__ void k_reduce_parts(const double* __restrict__ part, int nblocks, int M, int m, double* out) {
+  // one thread per output, summing block partials in block order
+  int t = threadIdx.x;
+  if (t >= m) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * M + t];
+  out[t] = s;
+}
+
+void launch_mdot(const double* V, size_t ldv, int m, const double* w, size_t n, double* out, double* scratch,
+                 cudaStream_t st) {
+  for (int t0 = 0; t0 < m; t0 += NV) {
+    int mm = std::min(NV, m - t0);
+    k_mdot<NV><<<RB, RT, 0, st>>>(V + (size_t)t0 * ldv, ldv, mm, w, n, scratch);
+    k_reduce_parts<<<1, 32, 0, st>>>(scratch, RB, NV, mm, out + t0);
+  }
+}
+
+__global__ void k_maxpy(const double* __restrict__ V, size_t ldv, int m, const double* __restrict__ h, double* w,
+                        size_t n, double sign) {
+  __shared__ double hs[64];
+  if (threadIdx.x < m && threadIdx.x < 64) hs[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    double s = w[i];
+    for (int t = 0; t < m; ++t) s -= sign * hs[t] * V[(size_t)t * ldv + i];
+    w[i] = s;
+  }
+}
+
+void launch_maxpy(const double* V, size_t ldv, int m, const double* h, double* w, size_t n, double sign,
+                  cudaStream_t st) {
+  for (int t0 = 0; t0 < m; t0 += 64) {
+    int mm = std::min(64, m - t0);
+    k_maxpy<<<RB, RT, 0, st>>>(V + (size_t)t0 * ldv, ldv, mm, h + t0, w, n, sign);
+  }
+}
+
+__global__ void k_scale(double* x, size_t n, const double* __restrict__ s, bool inverse) {
+  double f = inverse ? 1.0 / s[0] : s[0];
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) x[i] *= f;
+}
+
+void launch_scale(double* x, size_t n, const double* s_dev, bool inverse, cudaStream_t st) {
+  k_scale<<<RB, RT, 0, st>>>(x, n, s_dev, inverse);
+}
+
+template <typename Ts, typename Td>
+__global__ void k_cast(const Ts* __restrict__ a, Td* b, size_t n) {
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) b[i] = (Td)a[i];
+}
+
+template <typename Ts, typename Td>
+void launch_cast(const Ts* in, Td* out, size_t n, cudaStream_t st) {
+  k_cast<Ts, Td><<<RB, RT, 0, st>>>(in, out, n);
+}
+
+template <typename T>
+__global__ void k_sum(const T* __restrict__ x, size_t n, double* part) {
+  double acc = 0.0;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) acc += (double)x[i];
+  __shared__ double sh[RT / 32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) sh[wid] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < RT / 32; ++q) s += sh[q];
+    part[blockIdx.x] = s;
+  }
+}
+
+template <typename T>
+void launch_sum(const T* x, size_t n, double* out_dev, double* scratch, cudaStream_t st) {
+  k_sum<T><<<RB, RT, 0, st>>>(x, n, scratch);
+  k_reduce_parts<<<1, 32, 0, st>>>(scratch, RB, 1, 1, out_dev);
+}
+
+double host_norm2(const double* x, size_t n, double* scratch, cudaStream_t st) {
+  // scratch: RB + 1 doubles on the device
+  k_mdot<1><<<RB, RT, 0, st>>>(x, 0, 1, x, n, scratch);
+  k_reduce_parts<<<1, 32, 0, st>>>(scratch, RB, 1, 1, scratch + RB);
+  double h = 0.0;
+  cudaMemcpyAsync(&h, scratch + RB, sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  return sqrt(h);
+}
+
+template <typename T>
+__global__ void k_add_scalar(T* x, size_t n, const double* __restrict__ s, double factor) {
+  T a = (T)(s[0] * factor);
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) x[i] += a;
+}
+
+template <typename T>
+void launch_add_scalar_from(T* x, size_t n, const double* s_dev, double factor, cudaStream_t st) {
+  k_add_scalar<T><<<RB, RT, 0, st>>>(x, n, s_dev, factor);
+}
+
+template void launch_cast<double, float>(const double*, float*, size_t, cudaStream_t);
+template void launch_cast<float, double>(const float*, double*, size_t, cudaStream_t);
+template void launch_sum<double>(const double*, size_t, double*, double*, cudaStream_t);
+template void launch_sum<float>(const float*, size_t, double*, double*, cudaStream_t);
+template void launch_add_scalar_from<double>(double*, size_t, const double*, double, cudaStream_t);
+template void launch_add_scalar_from<float>(float*, size_t, const double*, double, cudaStream_t);
+
+}  // namespace wsi

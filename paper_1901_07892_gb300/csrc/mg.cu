@@ -1,0 +1,472 @@
+// Projection preconditioner of the implicit Stokes system (Sec. 4.2.4; the
+// paper cites the variable-coefficient projection method without printing
+// it) with a cell-centred geometric multigrid for the pressure operator
+// D(beta G).  Templated on the arithmetic type T: float64 for the plain
+// path, float32 inside float64 FGMRES for the mixed path.
+//
+// One application  z = P^{-1} r  (r = (r_u, r_p)):
+//   u~ = A^{-1} r_u      by red-black Gauss-Seidel sweeps on the viscous block
+//   y  = r_p + D u~      (mean removed: closed box)
+//   phi = L_beta^{-1} y   by V-cycles
+//   p  = phi/dt - theta mu y,    u = u~ - beta G phi
+// which is the block factorisation of K with the Schur complement
+// D A^{-1} G approximated by dt D beta G plus the local-viscosity term.
+//
+// Multigrid: coarsening by 2 along every axis whose extent is even and >= 4,
+// until <= 64 cells; coarse face beta = mean of the coplanar fine faces;
+// restriction = mean of the 2^d children (fused with the residual);
+// prolongation = (bi/tri)linear on cell centres (fused with the correction);
+// smoother = red-black Gauss-Seidel; coarsest = dense float64 inverse of the
+// operator regularised on its constant null space.
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "internal.h"
+
+namespace wsi {
+
+static constexpr int BX = 32, BY = 8;
+static inline dim3 grid3(int nx, int ny, int nz) { return dim3(cdiv(nx, BX), cdiv(ny, BY), nz); }
+
+template <typename T>
+static T* dalloc(std::vector<void*>& allocs, size_t n, std::string& err) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
+    err = "cudaMalloc failed in preconditioner";
+    return nullptr;
+  }
+  allocs.push_back(p);
+  return (T*)p;
+}
+
+template <typename T>
+int precond_alloc(Precond<T>& P, const GridDev& g0, std::string& err) {
+  precond_free(P);
+  GridDev g = g0;
+  for (;;) {
+    MGLevel<T> L;
+    L.g = g;
+    for (int c = 0; c < 3; ++c) {
+      L.beta[c] = dalloc<T>(P.allocs, fsize(g, c), err);
+      if (!L.beta[c]) return WSI_ERR_OOM;
+    }
+    size_t nc = fsize(g, 3);
+    L.x = dalloc<T>(P.allocs, nc, err);
+    L.b = dalloc<T>(P.allocs, nc, err);
+    L.res = dalloc<T>(P.allocs, nc, err);
+    if (!L.x || !L.b || !L.res) return WSI_ERR_OOM;
+    bool any = false;
+    for (int a = 0; a < 3; ++a) {
+      L.r[a] = (g.n[a] % 2 == 0 && g.n[a] >= 4) ? 2 : 1;
+      any |= L.r[a] == 2;
+    }
+    if (nc <= 64 || !any) {
+      for (int a = 0; a < 3; ++a) L.r[a] = 1;
+      P.lev.push_back(L);
+      break;
+    }
+    P.lev.push_back(L);
+    for (int a = 0; a < 3; ++a) {
+      g.n[a] /= L.r[a];
+      g.h[a] *= L.r[a];
+    }
+  }
+  P.ncoarse = (int)fsize(P.lev.back().g, 3);
+  if (P.ncoarse > 1024) {
+    err = "coarsest multigrid level too large (grid extents need more factors of 2)";
+    return WSI_ERR_INVALID_ARG;
+  }
+  P.coarse_inv = dalloc<double>(P.allocs, (size_t)P.ncoarse * P.ncoarse, err);
+  for (int c = 0; c < 3; ++c) {
+    P.rho_face[c] = dalloc<T>(P.allocs, fsize(g0, c), err);
+    P.ru[c] = dalloc<T>(P.allocs, fsize(g0, c), err);
+    P.ut[c] = dalloc<T>(P.allocs, fsize(g0, c), err);
+    P.gp[c] = dalloc<T>(P.allocs, fsize(g0, c), err);
+  }
+  P.mu_cc = dalloc<T>(P.allocs, fsize(g0, 3), err);
+  for (int e = 0; e < 3; ++e) P.mu_e[e] = dalloc<T>(P.allocs, esize(g0, e), err);
+  P.rp = dalloc<T>(P.allocs, fsize(g0, 3), err);
+  P.y = dalloc<T>(P.allocs, fsize(g0, 3), err);
+  P.dscratch = dalloc<double>(P.allocs, 4096, err);
+  P.dsum = dalloc<double>(P.allocs, 8, err);
+  if (!P.coarse_inv || !P.mu_cc || !P.rp || !P.y || !P.dscratch || !P.dsum) return WSI_ERR_OOM;
+  return WSI_OK;
+}
+
+template <typename T>
+void precond_free(Precond<T>& P) {
+  for (void* p : P.allocs) cudaFree(p);
+  P.allocs.clear();
+  P.lev.clear();
+  P.built = false;
+}
+
+// ------------------------------------------------------------ coefficients
+template <int C, typename T>
+__global__ void k_coarsen_beta(GridDev gf, GridDev gc, int r0, int r1, int r2, const T* __restrict__ bf, T* bc) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= ext(gc, C, 0) || j >= ext(gc, C, 1)) return;
+  int r[3] = {r0, r1, r2};
+  int base[3] = {i * r[0], j * r[1], k * r[2]};
+  int span[3] = {r[0], r[1], r[2]};
+  span[C] = 1;  // the coplanar block only
+  T s = T(0);
+  for (int c = 0; c < span[2]; ++c)
+    for (int b = 0; b < span[1]; ++b)
+      for (int a = 0; a < span[0]; ++a) s += bf[fidx(gf, C, base[0] + a, base[1] + b, base[2] + c)];
+  bc[fidx(gc, C, i, j, k)] = s / T(span[0] * span[1] * span[2]);
+}
+
+template <typename Ts, typename Td>
+__global__ void k_cast_arr(const Ts* __restrict__ a, Td* b, size_t n) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (; t < n; t += stride) b[t] = (Td)a[t];
+}
+template <typename Ts, typename Td>
+static void cast_arr(const Ts* a, Td* b, size_t n, cudaStream_t st) {
+  int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+  k_cast_arr<Ts, Td><<<std::max(blocks, 1), 256, 0, st>>>(a, b, n);
+}
+
+// Gauss-Jordan inverse (host, float64) of an SPD matrix, no pivoting needed
+static void spd_inverse(std::vector<double>& A, int n) {
+  std::vector<double> I((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+  for (int p = 0; p < n; ++p) {
+    double d = A[(size_t)p * n + p];
+    double id = 1.0 / d;
+    for (int c = 0; c < n; ++c) {
+      A[(size_t)p * n + c] *= id;
+      I[(size_t)p * n + c] *= id;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == p) continue;
+      double f = A[(size_t)r * n + p];
+      if (f == 0.0) continue;
+      for (int c = 0; c < n; ++c) {
+        A[(size_t)r * n + c] -= f * A[(size_t)p * n + c];
+        I[(size_t)r * n + c] -= f * I[(size_t)p * n + c];
+      }
+    }
+  }
+  A.swap(I);
+}
+
+template <typename T>
+int precond_setup(Precond<T>& P, const GridDev& g, const Coef<double>& fine, cudaStream_t st, std::string& err) {
+  // fine coefficients in T
+  for (int c = 0; c < 3; ++c) {
+    cast_arr<double, T>(fine.rho_face[c], P.rho_face[c], fsize(g, c), st);
+    cast_arr<double, T>(fine.beta[c], P.lev[0].beta[c], fsize(g, c), st);
+  }
+  cast_arr<double, T>(fine.mu_cc, P.mu_cc, fsize(g, 3), st);
+  for (int e = 0; e < 3; ++e) cast_arr<double, T>(fine.mu_e[e], P.mu_e[e], esize(g, e), st);
+  for (size_t l = 0; l + 1 < P.lev.size(); ++l) {
+    MGLevel<T>& F = P.lev[l];
+    MGLevel<T>& Cl = P.lev[l + 1];
+    const GridDev& gc = Cl.g;
+    k_coarsen_beta<0, T><<<grid3(gc.n[0] + 1, gc.n[1], gc.n[2]), dim3(BX, BY), 0, st>>>(F.g, gc, F.r[0], F.r[1],
+                                                                                        F.r[2], F.beta[0], Cl.beta[0]);
+    k_coarsen_beta<1, T><<<grid3(gc.n[0], gc.n[1] + 1, gc.n[2]), dim3(BX, BY), 0, st>>>(F.g, gc, F.r[0], F.r[1],
+                                                                                        F.r[2], F.beta[1], Cl.beta[1]);
+    k_coarsen_beta<2, T><<<grid3(gc.n[0], gc.n[1], gc.n[2] + 1), dim3(BX, BY), 0, st>>>(F.g, gc, F.r[0], F.r[1],
+                                                                                        F.r[2], F.beta[2], Cl.beta[2]);
+  }
+  // dense coarsest operator: M = -L + c 1 1^T (SPD), inverted in float64
+  const MGLevel<T>& Lc = P.lev.back();
+  const GridDev& gc = Lc.g;
+  int n = P.ncoarse;
+  std::vector<T> hb[3];
+  for (int c = 0; c < 3; ++c) {
+    hb[c].resize(fsize(gc, c));
+    cudaMemcpyAsync(hb[c].data(), Lc.beta[c], fsize(gc, c) * sizeof(T), cudaMemcpyDeviceToHost, st);
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    err = "CUDA error while building the coarse operator";
+    return WSI_ERR_CUDA;
+  }
+  std::vector<double> M((size_t)n * n, 0.0);
+  double dmax = 0.0;
+  for (int k = 0; k < gc.n[2]; ++k)
+    for (int j = 0; j < gc.n[1]; ++j)
+      for (int i = 0; i < gc.n[0]; ++i) {
+        int row = (int)fidx(gc, 3, i, j, k);
+        int c3[3] = {i, j, k};
+        for (int a = 0; a < 3; ++a) {
+          double ih2 = 1.0 / (gc.h[a] * gc.h[a]);
+          // face hi
+          if (c3[a] + 1 < gc.n[a]) {
+            int f3[3] = {i, j, k};
+            f3[a] += 1;
+            double b = (double)hb[a][fidx(gc, a, f3[0], f3[1], f3[2])] * ih2;
+            int nb3[3] = {i, j, k};
+            nb3[a] += 1;
+            int col = (int)fidx(gc, 3, nb3[0], nb3[1], nb3[2]);
+            M[(size_t)row * n + col] -= b;
+            M[(size_t)row * n + row] += b;
+          }
+          if (c3[a] > 0) {
+            double b = (double)hb[a][fidx(gc, a, i, j, k)] * ih2;
+            int nb3[3] = {i, j, k};
+            nb3[a] -= 1;
+            int col = (int)fidx(gc, 3, nb3[0], nb3[1], nb3[2]);
+            M[(size_t)row * n + col] -= b;
+            M[(size_t)row * n + row] += b;
+          }
+        }
+        dmax = std::max(dmax, M[(size_t)row * n + row]);
+      }
+  double creg = dmax / n;
+  for (size_t t = 0; t < M.size(); ++t) M[t] += creg;
+  spd_inverse(M, n);
+  cudaMemcpyAsync(P.coarse_inv, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    err = "CUDA error in preconditioner setup";
+    return WSI_ERR_CUDA;
+  }
+  P.built = true;
+  return WSI_OK;
+}
+
+// ------------------------------------------------------------ V-cycle kernels
+template <typename T>
+__global__ void k_rbgs_p(GridDev g, const T* __restrict__ bx, const T* __restrict__ by, const T* __restrict__ bz,
+                         T* x, const T* __restrict__ b, int color) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.n[0] || j >= g.n[1]) return;
+  if (((i + j + k) & 1) != color) return;
+  size_t id = fidx(g, 3, i, j, k);
+  T ihx2 = T(1.0 / (g.h[0] * g.h[0])), ihy2 = T(1.0 / (g.h[1] * g.h[1])), ihz2 = T(1.0 / (g.h[2] * g.h[2]));
+  T s = T(0), d = T(0);
+  if (i + 1 < g.n[0]) { T c = bx[fidx(g, 0, i + 1, j, k)] * ihx2; s += c * x[id + 1]; d += c; }
+  if (i > 0) { T c = bx[fidx(g, 0, i, j, k)] * ihx2; s += c * x[id - 1]; d += c; }
+  if (j + 1 < g.n[1]) { T c = by[fidx(g, 1, i, j + 1, k)] * ihy2; s += c * x[id + g.n[0]]; d += c; }
+  if (j > 0) { T c = by[fidx(g, 1, i, j, k)] * ihy2; s += c * x[id - g.n[0]]; d += c; }
+  size_t pl = (size_t)g.n[0] * g.n[1];
+  if (k + 1 < g.n[2]) { T c = bz[fidx(g, 2, i, j, k + 1)] * ihz2; s += c * x[id + pl]; d += c; }
+  if (k > 0) { T c = bz[fidx(g, 2, i, j, k)] * ihz2; s += c * x[id - pl]; d += c; }
+  if (d > T(0)) x[id] = (s - b[id]) / d;
+}
+
+template <typename T>
+__device__ __forceinline__ T lap_at(const GridDev& g, const T* __restrict__ bx, const T* __restrict__ by,
+                                    const T* __restrict__ bz, const T* __restrict__ x, int i, int j, int k) {
+  size_t id = fidx(g, 3, i, j, k);
+  T xc = x[id];
+  T ihx2 = T(1.0 / (g.h[0] * g.h[0])), ihy2 = T(1.0 / (g.h[1] * g.h[1])), ihz2 = T(1.0 / (g.h[2] * g.h[2]));
+  T s = T(0);
+  if (i + 1 < g.n[0]) s += bx[fidx(g, 0, i + 1, j, k)] * (x[id + 1] - xc) * ihx2;
+  if (i > 0) s -= bx[fidx(g, 0, i, j, k)] * (xc - x[id - 1]) * ihx2;
+  if (j + 1 < g.n[1]) s += by[fidx(g, 1, i, j + 1, k)] * (x[id + g.n[0]] - xc) * ihy2;
+  if (j > 0) s -= by[fidx(g, 1, i, j, k)] * (xc - x[id - g.n[0]]) * ihy2;
+  size_t pl = (size_t)g.n[0] * g.n[1];
+  if (k + 1 < g.n[2]) s += bz[fidx(g, 2, i, j, k + 1)] * (x[id + pl] - xc) * ihz2;
+  if (k > 0) s -= bz[fidx(g, 2, i, j, k)] * (xc - x[id - pl]) * ihz2;
+  return s;
+}
+
+// coarse b = mean over children of (b - L x) on the fine grid
+template <typename T>
+__global__ void k_restrict_res(GridDev gf, GridDev gc, int r0, int r1, int r2, const T* __restrict__ bx,
+                               const T* __restrict__ by, const T* __restrict__ bz, const T* __restrict__ x,
+                               const T* __restrict__ b, T* bcoarse) {
+  int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y, K = blockIdx.z;
+  if (I >= gc.n[0] || J >= gc.n[1]) return;
+  T s = T(0);
+  for (int c = 0; c < r2; ++c)
+    for (int bb = 0; bb < r1; ++bb)
+      for (int a = 0; a < r0; ++a) {
+        int i = I * r0 + a, j = J * r1 + bb, k = K * r2 + c;
+        s += b[fidx(gf, 3, i, j, k)] - lap_at<T>(gf, bx, by, bz, x, i, j, k);
+      }
+  bcoarse[fidx(gc, 3, I, J, K)] = s / T(r0 * r1 * r2);
+}
+
+// x_fine += P x_coarse (linear in cell centres along coarsened axes)
+template <typename T>
+__global__ void k_prolong_add(GridDev gf, GridDev gc, int r0, int r1, int r2, const T* __restrict__ xc, T* xf) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= gf.n[0] || j >= gf.n[1]) return;
+  int r[3] = {r0, r1, r2};
+  int f3[3] = {i, j, k};
+  int c0[3], c1[3];
+  T w0[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (r[a] == 2) {
+      c0[a] = f3[a] >> 1;
+      int nb = (f3[a] & 1) ? c0[a] + 1 : c0[a] - 1;
+      c1[a] = clampi(nb, 0, gc.n[a] - 1);
+      w0[a] = T(0.75);
+    } else {
+      c0[a] = f3[a];
+      c1[a] = f3[a];
+      w0[a] = T(1);
+    }
+  }
+  T s = T(0);
+#pragma unroll
+  for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+    for (int cy = 0; cy < 2; ++cy)
+#pragma unroll
+      for (int cx = 0; cx < 2; ++cx) {
+        T wx = cx ? T(1) - w0[0] : w0[0];
+        T wy = cy ? T(1) - w0[1] : w0[1];
+        T wz = cz ? T(1) - w0[2] : w0[2];
+        T w = wx * wy * wz;
+        if (w == T(0)) continue;
+        int a = cx ? c1[0] : c0[0], b = cy ? c1[1] : c0[1], c = cz ? c1[2] : c0[2];
+        s += w * xc[fidx(gc, 3, a, b, c)];
+      }
+  xf[fidx(gf, 3, i, j, k)] += s;
+}
+
+// x = Minv (-b), one block
+template <typename T>
+__global__ void k_coarse_solve(int n, const double* __restrict__ Minv, const T* __restrict__ b, T* x) {
+  extern __shared__ double sb[];
+  for (int t = threadIdx.x; t < n; t += blockDim.x) sb[t] = -(double)b[t];
+  __syncthreads();
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < n; ++c) s += Minv[(size_t)r * n + c] * sb[c];
+    x[r] = (T)s;
+  }
+}
+
+template <typename T>
+static void vcycle(Precond<T>& P, const Opts& o, size_t l, cudaStream_t st) {
+  MGLevel<T>& L = P.lev[l];
+  const GridDev& g = L.g;
+  dim3 gr = grid3(g.n[0], g.n[1], g.n[2]);
+  if (l + 1 == P.lev.size()) {
+    k_coarse_solve<T><<<1, 256, P.ncoarse * sizeof(double), st>>>(P.ncoarse, P.coarse_inv, L.b, L.x);
+    return;
+  }
+  for (int s = 0; s < o.mg_pre; ++s)
+    for (int c = 0; c < 2; ++c) k_rbgs_p<T><<<gr, dim3(BX, BY), 0, st>>>(g, L.beta[0], L.beta[1], L.beta[2], L.x, L.b, c);
+  MGLevel<T>& Cl = P.lev[l + 1];
+  const GridDev& gc = Cl.g;
+  k_restrict_res<T><<<grid3(gc.n[0], gc.n[1], gc.n[2]), dim3(BX, BY), 0, st>>>(
+      g, gc, L.r[0], L.r[1], L.r[2], L.beta[0], L.beta[1], L.beta[2], L.x, L.b, Cl.b);
+  cudaMemsetAsync(Cl.x, 0, fsize(gc, 3) * sizeof(T), st);
+  vcycle(P, o, l + 1, st);
+  k_prolong_add<T><<<gr, dim3(BX, BY), 0, st>>>(g, gc, L.r[0], L.r[1], L.r[2], Cl.x, L.x);
+  for (int s = 0; s < o.mg_post; ++s)
+    for (int c = 1; c >= 0; --c)
+      k_rbgs_p<T><<<gr, dim3(BX, BY), 0, st>>>(g, L.beta[0], L.beta[1], L.beta[2], L.x, L.b, c);
+}
+
+// ------------------------------------------------------------ PC glue kernels
+template <typename T>
+__global__ void k_div_add(GridDev g, const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ w,
+                          const T* __restrict__ rp, T* y) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.n[0] || j >= g.n[1]) return;
+  T d = (u[fidx(g, 0, i + 1, j, k)] - u[fidx(g, 0, i, j, k)]) / (T)g.h[0] +
+        (v[fidx(g, 1, i, j + 1, k)] - v[fidx(g, 1, i, j, k)]) / (T)g.h[1] +
+        (w[fidx(g, 2, i, j, k + 1)] - w[fidx(g, 2, i, j, k)]) / (T)g.h[2];
+  size_t id = fidx(g, 3, i, j, k);
+  y[id] = rp[id] + d;
+}
+
+// u = u~ - beta G phi on C-faces, written as float64 into z
+template <int C, typename T>
+__global__ void k_vel_update(GridDev g, const T* __restrict__ ut, const T* __restrict__ beta,
+                             const T* __restrict__ phi, double* z) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= ext(g, C, 0) || j >= ext(g, C, 1)) return;
+  int id3[3] = {i, j, k};
+  size_t id = fidx(g, C, i, j, k);
+  if (id3[C] == 0 || id3[C] == g.n[C]) {
+    z[id] = 0.0;
+    return;
+  }
+  int lo[3] = {i, j, k};
+  lo[C] -= 1;
+  T gphi = (phi[fidx(g, 3, i, j, k)] - phi[fidx(g, 3, lo[0], lo[1], lo[2])]) / (T)g.h[C];
+  z[id] = (double)(ut[id] - beta[id] * gphi);
+}
+
+// p = phi/dt - theta mu y - mean (mean subtracted with the sum in s_dev)
+template <typename T>
+__global__ void k_p_update(size_t n, const T* __restrict__ phi, const T* __restrict__ mu, const T* __restrict__ y,
+                           double inv_dt, double theta, double* z) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (; t < n; t += stride) z[t] = (double)phi[t] * inv_dt - theta * (double)mu[t] * (double)y[t];
+}
+
+template <typename T>
+__global__ void k_sub_mean(T* x, size_t n, const double* __restrict__ sum) {
+  T m = (T)(sum[0] / (double)n);
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (; t < n; t += stride) x[t] -= m;
+}
+
+template <typename T>
+static void sub_mean(T* x, size_t n, double* dsum, double* scratch, cudaStream_t st) {
+  launch_sum<T>(x, n, dsum, scratch, st);
+  int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+  k_sub_mean<T><<<std::max(blocks, 1), 256, 0, st>>>(x, n, dsum);
+}
+
+template <typename T>
+void precond_apply(Precond<T>& P, const GridDev& g, const Opts& o, double dt, const double* v, double* z,
+                   cudaStream_t st) {
+  Packing pk = packing(g);
+  for (int c = 0; c < 3; ++c) {
+    cast_arr<double, T>(v + pk.off[c], P.ru[c], fsize(g, c), st);
+    cudaMemsetAsync(P.ut[c], 0, fsize(g, c) * sizeof(T), st);
+  }
+  cast_arr<double, T>(v + pk.off[3], P.rp, fsize(g, 3), st);
+  Coef<T> cf;
+  for (int c = 0; c < 3; ++c) {
+    cf.rho_face[c] = P.rho_face[c];
+    cf.beta[c] = P.lev[0].beta[c];
+    cf.mu_e[c] = P.mu_e[c];
+  }
+  cf.mu_cc = P.mu_cc;
+  T inv_dt = (T)(1.0 / dt), theta = (T)o.theta;
+  // u~ = A^{-1} r_u (approximately)
+  for (int s = 0; s < o.visc_sweeps; ++s)
+    for (int c = 0; c < 2; ++c) launch_viscous_rbgs<T>(g, cf, inv_dt, theta, P.ut, P.ru, c, st);
+  // y = r_p + D u~, mean-free
+  dim3 gr = grid3(g.n[0], g.n[1], g.n[2]);
+  k_div_add<T><<<gr, dim3(BX, BY), 0, st>>>(g, P.ut[0], P.ut[1], P.ut[2], P.rp, P.y);
+  size_t ncell = fsize(g, 3);
+  sub_mean<T>(P.y, ncell, P.dsum, P.dscratch, st);
+  // phi = L^{-1} y
+  MGLevel<T>& L0 = P.lev[0];
+  cudaMemcpyAsync(L0.b, P.y, ncell * sizeof(T), cudaMemcpyDeviceToDevice, st);
+  cudaMemsetAsync(L0.x, 0, ncell * sizeof(T), st);
+  for (int c = 0; c < o.mg_cycles; ++c) vcycle(P, o, 0, st);
+  // velocity and pressure updates
+  k_vel_update<0, T><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, P.ut[0], L0.beta[0], L0.x,
+                                                                                 z + pk.off[0]);
+  k_vel_update<1, T><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, P.ut[1], L0.beta[1], L0.x,
+                                                                                 z + pk.off[1]);
+  k_vel_update<2, T><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, P.ut[2], L0.beta[2], L0.x,
+                                                                                 z + pk.off[2]);
+  int blocks = (int)std::min<size_t>((ncell + 255) / 256, 152 * 16);
+  k_p_update<T><<<std::max(blocks, 1), 256, 0, st>>>(ncell, L0.x, P.mu_cc, P.y, 1.0 / dt, o.theta, z + pk.off[3]);
+  sub_mean<double>(z + pk.off[3], ncell, P.dsum, P.dscratch, st);
+}
+
+template int precond_alloc<double>(Precond<double>&, const GridDev&, std::string&);
+template int precond_alloc<float>(Precond<float>&, const GridDev&, std::string&);
+template void precond_free<double>(Precond<double>&);
+template void precond_free<float>(Precond<float>&);
+template int precond_setup<double>(Precond<double>&, const GridDev&, const Coef<double>&, cudaStream_t, std::string&);
+template int precond_setup<float>(Precond<float>&, const GridDev&, const Coef<double>&, cudaStream_t, std::string&);
+template void precond_apply<double>(Precond<double>&, const GridDev&, const Opts&, double, const double*, double*,
+                                    cudaStream_t);
+template void precond_apply<float>(Precond<float>&, const GridDev&, const Opts&, double, const double*, double*,
+                                   cudaStream_t);
+
+}  // namespace wsi

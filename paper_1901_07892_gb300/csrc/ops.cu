@@ -1,0 +1,651 @@
+// Field kernels of libwsi: material coefficients (Sec. 4.1), the staggered
+// operators of the implicit Stokes system (Sec. 3.1, 4.2.2), consistent
+// transport (Sec. 4.2.2) and level-set advection (Sec. 4.2.1).
+//
+// Every kernel walks its output array in x-fastest order with one thread per
+// entry (blocks of 32 x 8 in x, y; one z-plane per grid row), so warps read
+// and write contiguous rows of the unghosted MAC arrays.
+#include <math.h>
+
+#include <algorithm>
+
+#include "internal.h"
+
+namespace wsi {
+
+static constexpr int BX = 32, BY = 8;
+
+static inline dim3 grid3(int nx, int ny, int nz) { return dim3(cdiv(nx, BX), cdiv(ny, BY), nz); }
+
+// =========================================================== materials
+__device__ __forceinline__ double heaviside(double phi, double eps) {
+  if (phi < -eps) return 0.0;
+  if (phi > eps) return 1.0;
+  return 0.5 * (1.0 + phi / eps + sin(M_PI * phi / eps) / M_PI);
+}
+__device__ __forceinline__ double two_stage(double phi, double psi, double zl, double zg, double zs, double eps) {
+  double zf = zl + (zg - zl) * heaviside(phi, eps);
+  return zs + (zf - zs) * heaviside(psi, eps);
+}
+__device__ __forceinline__ double cell_at(const GridDev& g, const double* a, int i, int j, int k) {
+  i = clampi(i, 0, g.n[0] - 1);
+  j = clampi(j, 0, g.n[1] - 1);
+  k = clampi(k, 0, g.n[2] - 1);
+  return a[fidx(g, 3, i, j, k)];
+}
+
+__global__ void k_mat_cells(GridDev g, PhaseConst pc, const double* __restrict__ phi, const double* __restrict__ psi,
+                            double* rho_cc, double* mu_cc) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.n[0] || j >= g.n[1]) return;
+  size_t id = fidx(g, 3, i, j, k);
+  double a = phi[id], b = psi[id];
+  if (rho_cc) rho_cc[id] = two_stage(a, b, pc.rho_l, pc.rho_g, pc.rho_s, pc.eps);
+  mu_cc[id] = two_stage(a, b, pc.mu_l, pc.mu_g, pc.mu_s, pc.eps);
+}
+
+// face density from face-averaged level sets (wall faces: the interior cell)
+template <int C>
+__global__ void k_mat_faces(GridDev g, PhaseConst pc, const double* __restrict__ phi, const double* __restrict__ psi,
+                            double* rho_face, double* beta, double* rho_flow) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= ext(g, C, 0) || j >= ext(g, C, 1)) return;
+  int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+  lo[C] -= 1;
+  double pa = 0.5 * (cell_at(g, phi, lo[0], lo[1], lo[2]) + cell_at(g, phi, hi[0], hi[1], hi[2]));
+  size_t id = fidx(g, C, i, j, k);
+  if (rho_face) {
+    double sa = 0.5 * (cell_at(g, psi, lo[0], lo[1], lo[2]) + cell_at(g, psi, hi[0], hi[1], hi[2]));
+    double r = two_stage(pa, sa, pc.rho_l, pc.rho_g, pc.rho_s, pc.eps);
+    rho_face[id] = r;
+    if (beta) beta[id] = 1.0 / r;
+  }
+  if (rho_flow) rho_flow[id] = pc.rho_l + (pc.rho_g - pc.rho_l) * heaviside(pa, pc.eps);
+}
+
+// harmonic mean of the 4 cells around an edge (mirror ghosts at walls)
+template <int E>
+__global__ void k_mat_edges(GridDev g, const double* __restrict__ mu_cc, double* mu_e) {
+  // E = 0: xy edges, 1: xz, 2: yz
+  constexpr int A1 = (E == 2) ? 1 : 0;
+  constexpr int A2 = (E == 0) ? 1 : 2;
+  int ex = g.n[0] + (A1 == 0 || A2 == 0), ey = g.n[1] + (A1 == 1 || A2 == 1);
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= ex || j >= ey) return;
+  double s = 0.0;
+#pragma unroll
+  for (int o1 = 0; o1 < 2; ++o1)
+#pragma unroll
+    for (int o2 = 0; o2 < 2; ++o2) {
+      int c[3] = {i, j, k};
+      c[A1] -= o1;
+      c[A2] -= o2;
+      s += 1.0 / cell_at(g, mu_cc, c[0], c[1], c[2]);
+    }
+  mu_e[eidx(g, E, i, j, k)] = 4.0 / s;
+}
+
+void launch_materials(const GridDev& g, const PhaseConst& pc, const double* phi, const double* psi, double* rho_cc,
+                      double* mu_cc, double* const rho_face[3], double* const beta[3], double* const rho_flow[3],
+                      double* const mu_e[3], cudaStream_t st) {
+  k_mat_cells<<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, rho_cc, mu_cc);
+  k_mat_faces<0><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, rho_face[0], beta[0],
+                                                                             rho_flow[0]);
+  k_mat_faces<1><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, rho_face[1], beta[1],
+                                                                             rho_flow[1]);
+  k_mat_faces<2><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, rho_face[2], beta[2],
+                                                                             rho_flow[2]);
+  k_mat_edges<0><<<grid3(g.n[0] + 1, g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[0]);
+  k_mat_edges<1><<<grid3(g.n[0] + 1, g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[1]);
+  k_mat_edges<2><<<grid3(g.n[0], g.n[1] + 1, g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[2]);
+}
+
+void launch_mu_only(const GridDev& g, const PhaseConst& pc, const double* phi, const double* psi, double* mu_cc,
+                    double* const mu_e[3], cudaStream_t st) {
+  k_mat_cells<<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, nullptr, mu_cc);
+  k_mat_edges<0><<<grid3(g.n[0] + 1, g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[0]);
+  k_mat_edges<1><<<grid3(g.n[0] + 1, g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[1]);
+  k_mat_edges<2><<<grid3(g.n[0], g.n[1] + 1, g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[2]);
+}
+
+void launch_rho_flow(const GridDev& g, const PhaseConst& pc, const double* phi, double* const rho_flow[3],
+                     cudaStream_t st) {
+  k_mat_faces<0><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, nullptr, nullptr, nullptr,
+                                                                             rho_flow[0]);
+  k_mat_faces<1><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, nullptr, nullptr, nullptr,
+                                                                             rho_flow[1]);
+  k_mat_faces<2><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, pc, phi, nullptr, nullptr, nullptr,
+                                                                             rho_flow[2]);
+}
+
+// =========================================================== strain-rate operator
+// (L_mu q)_C at the interior C-face (i,j,k):
+//   d/dx_C (2 mu dq_C/dx_C) + sum_{D != C} d/dx_D [ mu_e (dq_C/dx_D + dq_D/dx_C) ]
+// diag (optional): coefficient of q_C(i,j,k) itself in L_mu q.
+template <int C, typename T>
+__device__ __forceinline__ T strain_at(const GridDev& g, const Coef<T>& cf, const T* const* q, int i, int j, int k,
+                                       T* diag) {
+  const T* qc = q[C];
+  const T hC = (T)g.h[C];
+  const T ihC = T(1) / hC;
+  int id3[3] = {i, j, k};
+  T q0 = qc[fidx(g, C, i, j, k)];
+  // normal stress: cells hi = face index along C, lo = index - 1
+  int lo3[3] = {i, j, k};
+  lo3[C] -= 1;
+  int hi3[3] = {i, j, k};
+  hi3[C] += 1;
+  T mu_hi = cf.mu_cc[fidx(g, 3, i, j, k)];
+  T mu_lo = cf.mu_cc[fidx(g, 3, lo3[0], lo3[1], lo3[2])];
+  T qp = qc[fidx(g, C, hi3[0], hi3[1], hi3[2])];
+  T qm = qc[fidx(g, C, lo3[0], lo3[1], lo3[2])];
+  T L = T(2) * ihC * ihC * (mu_hi * (qp - q0) - mu_lo * (q0 - qm));
+  T dg = -T(2) * ihC * ihC * (mu_hi + mu_lo);
+#pragma unroll
+  for (int D = 0; D < 3; ++D) {
+    if (D == C) continue;
+    const int E = edge_id(C, D);
+    const T hD = (T)g.h[D];
+    const T ihD = T(1) / hD;
+    const T* qd = q[D];
+    // neighbours along D (ghosts beyond walls mirror with the wall sign)
+    int a3[3] = {id3[0], id3[1], id3[2]};
+    int b3[3] = {id3[0], id3[1], id3[2]};
+    a3[D] += 1;
+    b3[D] -= 1;
+    T q_hi, q_lo, s_hi = T(0), s_lo = T(0);
+    if (a3[D] >= g.n[D]) {
+      s_hi = (T)g.bc[2 * D + 1];
+      q_hi = s_hi * q0;
+    } else {
+      q_hi = qc[fidx(g, C, a3[0], a3[1], a3[2])];
+    }
+    if (b3[D] < 0) {
+      s_lo = (T)g.bc[2 * D];
+      q_lo = s_lo * q0;
+    } else {
+      q_lo = qc[fidx(g, C, b3[0], b3[1], b3[2])];
+    }
+    // edges: along C at the face index, along D at j_D (lo) and j_D + 1 (hi)
+    int eh[3] = {id3[0], id3[1], id3[2]};
+    eh[D] += 1;
+    T mue_hi = cf.mu_e[E][eidx(g, E, eh[0], eh[1], eh[2])];
+    T mue_lo = cf.mu_e[E][eidx(g, E, id3[0], id3[1], id3[2])];
+    // q_D on D-faces adjacent along C: cells (index along C) id-1 and id
+    int d1[3] = {id3[0], id3[1], id3[2]};  // hi edge, cell id
+    d1[D] += 1;
+    int d0[3] = {d1[0], d1[1], d1[2]};
+    d0[C] -= 1;
+    T dqd_hi = (qd[fidx(g, D, d1[0], d1[1], d1[2])] - qd[fidx(g, D, d0[0], d0[1], d0[2])]) * ihC;
+    int c1[3] = {id3[0], id3[1], id3[2]};  // lo edge
+    int c0[3] = {id3[0], id3[1], id3[2]};
+    c0[C] -= 1;
+    T dqd_lo = (qd[fidx(g, D, c1[0], c1[1], c1[2])] - qd[fidx(g, D, c0[0], c0[1], c0[2])]) * ihC;
+    T f_hi = mue_hi * ((q_hi - q0) * ihD + dqd_hi);
+    T f_lo = mue_lo * ((q0 - q_lo) * ihD + dqd_lo);
+    L += (f_hi - f_lo) * ihD;
+    dg += (mue_hi * (s_hi - T(1)) - mue_lo * (T(1) - s_lo)) * ihD * ihD;
+  }
+  if (diag) *diag = dg;
+  return L;
+}
+
+template <int C, typename T>
+__global__ void k_viscous(GridDev g, Coef<T> cf, T inv_dt, T theta, CVel<T> q, T* out, const T* b, bool strain_only) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  int e0 = ext(g, C, 0), e1 = ext(g, C, 1);
+  if (i >= e0 || j >= e1) return;
+  int id3[3] = {i, j, k};
+  size_t id = fidx(g, C, i, j, k);
+  if (id3[C] == 0 || id3[C] == g.n[C]) {
+    out[id] = T(0);
+    return;
+  }
+  T L = strain_at<C, T>(g, cf, q.q, i, j, k, nullptr);
+  T a;
+  if (strain_only)
+    a = L;
+  else
+    a = cf.rho_face[C][id] * inv_dt * q.q[C][id] - theta * L;
+  out[id] = b ? b[id] - a : a;
+}
+
+template <typename T>
+void launch_viscous(const GridDev& g, const Coef<T>& cf, T inv_dt, T theta, const T* const q[3], T* const out[3],
+                    cudaStream_t st, bool strain_only) {
+  CVel<T> cq{{q[0], q[1], q[2]}};
+  k_viscous<0, T><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, cq, out[0],
+                                                                              nullptr, strain_only);
+  k_viscous<1, T><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, cq, out[1],
+                                                                              nullptr, strain_only);
+  k_viscous<2, T><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, cq, out[2],
+                                                                              nullptr, strain_only);
+}
+
+template <typename T>
+void launch_viscous_residual(const GridDev& g, const Coef<T>& cf, T inv_dt, T theta, const T* const q[3],
+                             const T* const b[3], T* const r[3], cudaStream_t st) {
+  CVel<T> cq{{q[0], q[1], q[2]}};
+  k_viscous<0, T><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, cq, r[0], b[0],
+                                                                              false);
+  k_viscous<1, T><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, cq, r[1], b[1],
+                                                                              false);
+  k_viscous<2, T><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, cq, r[2], b[2],
+                                                                              false);
+}
+
+// red-black Gauss-Seidel on component C of the viscous block: the other
+// components and the other colour are read as they stand.
+template <int C, typename T>
+__global__ void k_viscous_rbgs(GridDev g, Coef<T> cf, T inv_dt, T theta, Vel<T> q, const T* __restrict__ b,
+                               int color) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  int e0 = ext(g, C, 0), e1 = ext(g, C, 1);
+  if (i >= e0 || j >= e1) return;
+  if (((i + j + k) & 1) != color) return;
+  int id3[3] = {i, j, k};
+  if (id3[C] == 0 || id3[C] == g.n[C]) return;
+  size_t id = fidx(g, C, i, j, k);
+  T dg;
+  const T* cq[3] = {q.q[0], q.q[1], q.q[2]};
+  T L = strain_at<C, T>(g, cf, cq, i, j, k, &dg);
+  T rf = cf.rho_face[C][id] * inv_dt;
+  T a = rf * q.q[C][id] - theta * L;
+  T d = rf - theta * dg;
+  q.q[C][id] += (b[id] - a) / d;
+}
+
+template <typename T>
+void launch_viscous_rbgs(const GridDev& g, const Coef<T>& cf, T inv_dt, T theta, T* const q[3], const T* const b[3],
+                         int color, cudaStream_t st) {
+  Vel<T> vq{{q[0], q[1], q[2]}};
+  k_viscous_rbgs<0, T><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, vq, b[0],
+                                                                                   color);
+  k_viscous_rbgs<1, T><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, vq, b[1],
+                                                                                   color);
+  if (g.n[2] > 1)
+    k_viscous_rbgs<2, T><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, vq, b[2],
+                                                                                     color);
+}
+
+// =========================================================== pressure, grad, div
+template <typename T>
+__global__ void k_pressure(GridDev g, const T* __restrict__ bx, const T* __restrict__ by, const T* __restrict__ bz,
+                           const T* __restrict__ p, T* out) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.n[0] || j >= g.n[1]) return;
+  size_t id = fidx(g, 3, i, j, k);
+  T pc = p[id];
+  T s = T(0);
+  T ihx2 = T(1) / (T)(g.h[0] * g.h[0]), ihy2 = T(1) / (T)(g.h[1] * g.h[1]), ihz2 = T(1) / (T)(g.h[2] * g.h[2]);
+  if (i + 1 < g.n[0]) s += bx[fidx(g, 0, i + 1, j, k)] * (p[id + 1] - pc) * ihx2;
+  if (i > 0) s -= bx[fidx(g, 0, i, j, k)] * (pc - p[id - 1]) * ihx2;
+  if (j + 1 < g.n[1]) s += by[fidx(g, 1, i, j + 1, k)] * (p[id + g.n[0]] - pc) * ihy2;
+  if (j > 0) s -= by[fidx(g, 1, i, j, k)] * (pc - p[id - g.n[0]]) * ihy2;
+  size_t pl = (size_t)g.n[0] * g.n[1];
+  if (k + 1 < g.n[2]) s += bz[fidx(g, 2, i, j, k + 1)] * (p[id + pl] - pc) * ihz2;
+  if (k > 0) s -= bz[fidx(g, 2, i, j, k)] * (pc - p[id - pl]) * ihz2;
+  out[id] = s;
+}
+
+template <typename T>
+void launch_pressure(const GridDev& g, const T* const beta[3], const T* p, T* out, cudaStream_t st) {
+  k_pressure<T><<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, beta[0], beta[1], beta[2], p, out);
+}
+
+template <int C, typename T>
+__global__ void k_grad(GridDev g, const T* __restrict__ p, T* out) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= ext(g, C, 0) || j >= ext(g, C, 1)) return;
+  int id3[3] = {i, j, k};
+  size_t id = fidx(g, C, i, j, k);
+  if (id3[C] == 0 || id3[C] == g.n[C]) {
+    out[id] = T(0);
+    return;
+  }
+  int lo3[3] = {i, j, k};
+  lo3[C] -= 1;
+  out[id] = (p[fidx(g, 3, i, j, k)] - p[fidx(g, 3, lo3[0], lo3[1], lo3[2])]) / (T)g.h[C];
+}
+
+template <typename T>
+void launch_grad(const GridDev& g, const T* p, T* const out[3], cudaStream_t st) {
+  k_grad<0, T><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, p, out[0]);
+  k_grad<1, T><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, p, out[1]);
+  k_grad<2, T><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, p, out[2]);
+}
+
+template <typename T>
+__global__ void k_div(GridDev g, const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ w, T* out,
+                      T scale) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.n[0] || j >= g.n[1]) return;
+  T d = (u[fidx(g, 0, i + 1, j, k)] - u[fidx(g, 0, i, j, k)]) / (T)g.h[0] +
+        (v[fidx(g, 1, i, j + 1, k)] - v[fidx(g, 1, i, j, k)]) / (T)g.h[1] +
+        (w[fidx(g, 2, i, j, k + 1)] - w[fidx(g, 2, i, j, k)]) / (T)g.h[2];
+  out[fidx(g, 3, i, j, k)] = scale * d;
+}
+
+template <typename T>
+void launch_div(const GridDev& g, const T* const q[3], T* out, T scale, cudaStream_t st) {
+  k_div<T><<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, q[0], q[1], q[2], out, scale);
+}
+
+// packed Stokes matvec: momentum rows A u + G p, continuity rows -D u
+template <int C>
+__global__ void k_stokes_mom(GridDev g, Coef<double> cf, double inv_dt, double theta, CVel<double> q,
+                             const double* __restrict__ p, double* out) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= ext(g, C, 0) || j >= ext(g, C, 1)) return;
+  int id3[3] = {i, j, k};
+  size_t id = fidx(g, C, i, j, k);
+  if (id3[C] == 0 || id3[C] == g.n[C]) {
+    out[id] = 0.0;
+    return;
+  }
+  double L = strain_at<C, double>(g, cf, q.q, i, j, k, nullptr);
+  int lo3[3] = {i, j, k};
+  lo3[C] -= 1;
+  double gp = (p[fidx(g, 3, i, j, k)] - p[fidx(g, 3, lo3[0], lo3[1], lo3[2])]) / g.h[C];
+  out[id] = cf.rho_face[C][id] * inv_dt * q.q[C][id] - theta * L + gp;
+}
+
+void launch_stokes(const GridDev& g, const Coef<double>& cf, double inv_dt, double theta, const double* x, double* y,
+                   cudaStream_t st) {
+  Packing pk = packing(g);
+  CVel<double> q{{x + pk.off[0], x + pk.off[1], x + pk.off[2]}};
+  const double* p = x + pk.off[3];
+  k_stokes_mom<0><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, q, p,
+                                                                              y + pk.off[0]);
+  k_stokes_mom<1><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, q, p,
+                                                                              y + pk.off[1]);
+  k_stokes_mom<2><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, q, p,
+                                                                              y + pk.off[2]);
+  k_div<double><<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, q.q[0], q.q[1], q.q[2], y + pk.off[3],
+                                                                        -1.0);
+}
+
+template <int C>
+__global__ void k_zero_walls(GridDev g, double* q) {
+  // walls normal to C: planes index 0 and n along C
+  int a = blockIdx.x * BX + threadIdx.x, b = blockIdx.y * BY + threadIdx.y, side = blockIdx.z;
+  constexpr int A = (C == 0) ? 1 : 0;
+  constexpr int B = (C == 2) ? 1 : 2;
+  if (a >= g.n[A] || b >= g.n[B]) return;
+  int c3[3];
+  c3[C] = side ? g.n[C] : 0;
+  c3[A] = a;
+  c3[B] = b;
+  q[fidx(g, C, c3[0], c3[1], c3[2])] = 0.0;
+}
+
+void launch_zero_walls(const GridDev& g, double* const q[3], cudaStream_t st) {
+  k_zero_walls<0><<<dim3(cdiv(g.n[1], BX), cdiv(g.n[2], BY), 2), dim3(BX, BY), 0, st>>>(g, q[0]);
+  k_zero_walls<1><<<dim3(cdiv(g.n[0], BX), cdiv(g.n[2], BY), 2), dim3(BX, BY), 0, st>>>(g, q[1]);
+  k_zero_walls<2><<<dim3(cdiv(g.n[0], BX), cdiv(g.n[1], BY), 2), dim3(BX, BY), 0, st>>>(g, q[2]);
+}
+
+// =========================================================== transport
+// Bounded cubic-upwind interpolation (CUI, kappa = 1/3) in normalized
+// variables; qC upwind point, qU next upwind, qD downwind.
+__device__ __forceinline__ double cui(double qU, double qC, double qD) {
+  double den = qD - qU;
+  if (den == 0.0) return qC;
+  double t = (qC - qU) / den;
+  double tf;
+  if (t > 0.0 && t <= 2.0 / 13.0)
+    tf = 3.0 * t;
+  else if (t > 2.0 / 13.0 && t <= 0.8)
+    tf = 5.0 * t / 6.0 + 1.0 / 3.0;
+  else if (t > 0.8 && t <= 1.0)
+    tf = 1.0;
+  else
+    tf = t;
+  return qU + tf * den;
+}
+
+// Value of the C-face array a at index m along axis D (other indices fixed),
+// extended by two ghost layers: even mirror (density) or the velocity rule
+// (odd about wall faces along C == D, wall sign across D != C).
+template <int C, int D, bool VEL>
+__device__ __forceinline__ double ext_get(const GridDev& g, const double* __restrict__ a, int i3[3], int m) {
+  int n = g.n[D] + (C == D ? 1 : 0);  // stored extent along D
+  double s = 1.0;
+  int mm = m;
+  if (m < 0) {
+    int gl = -m;
+    if (C == D) {
+      mm = gl;
+      if (VEL) s = -1.0;
+    } else {
+      mm = gl - 1;
+      if (VEL) s = g.bc[2 * D];
+    }
+  } else if (m >= n) {
+    int gl = m - (n - 1);
+    if (C == D) {
+      mm = (n - 1) - gl;
+      if (VEL) s = -1.0;
+    } else {
+      mm = n - gl;
+      if (VEL) s = g.bc[2 * D + 1];
+    }
+  }
+  mm = clampi(mm, 0, n - 1);
+  int c3[3] = {i3[0], i3[1], i3[2]};
+  c3[D] = mm;
+  return s * a[fidx(g, C, c3[0], c3[1], c3[2])];
+}
+
+// limited value at the CV face between entries m_lo and m_lo + 1 along D
+template <int C, int D, bool VEL>
+__device__ __forceinline__ double lim_at(const GridDev& g, const double* a, int i3[3], int m_lo, double adv) {
+  if (adv > 0.0)
+    return cui(ext_get<C, D, VEL>(g, a, i3, m_lo - 1), ext_get<C, D, VEL>(g, a, i3, m_lo),
+               ext_get<C, D, VEL>(g, a, i3, m_lo + 1));
+  return cui(ext_get<C, D, VEL>(g, a, i3, m_lo + 2), ext_get<C, D, VEL>(g, a, i3, m_lo + 1),
+             ext_get<C, D, VEL>(g, a, i3, m_lo));
+}
+
+template <int C, int D>
+__device__ __forceinline__ double flux_div_dir(const GridDev& g, const double* const* vel, const double* rho,
+                                               bool withv, int i, int j, int k) {
+  int i3[3] = {i, j, k};
+  const double* qc = vel[C];
+  double Fhi, Flo;
+  if (C == D) {
+    // CV faces at cells id-1 (between faces id-1, id) and id (between id, id+1)
+    int m = i3[C];
+    int a3[3] = {i, j, k};
+    a3[C] = m - 1;
+    double q_m1 = qc[fidx(g, C, a3[0], a3[1], a3[2])];
+    double q_0 = qc[fidx(g, C, i, j, k)];
+    a3[C] = m + 1;
+    double q_p1 = qc[fidx(g, C, a3[0], a3[1], a3[2])];
+    double adv_lo = 0.5 * (q_m1 + q_0), adv_hi = 0.5 * (q_0 + q_p1);
+    double rl = lim_at<C, D, false>(g, rho, i3, m - 1, adv_lo);
+    double rh = lim_at<C, D, false>(g, rho, i3, m, adv_hi);
+    Flo = adv_lo * rl;
+    Fhi = adv_hi * rh;
+    if (withv) {
+      Flo *= lim_at<C, D, true>(g, qc, i3, m - 1, adv_lo);
+      Fhi *= lim_at<C, D, true>(g, qc, i3, m, adv_hi);
+    }
+  } else {
+    // CV faces on edges at D-face positions j_D (lo) and j_D + 1 (hi);
+    // advective velocity: mean of the two D-faces adjacent along C
+    const double* qd = vel[D];
+    int jd = i3[D];
+    int b3[3] = {i, j, k};
+    int b0[3] = {i, j, k};
+    b0[C] -= 1;
+    double adv_lo = 0.5 * (qd[fidx(g, D, b0[0], b0[1], b0[2])] + qd[fidx(g, D, b3[0], b3[1], b3[2])]);
+    b3[D] += 1;
+    b0[D] += 1;
+    double adv_hi = 0.5 * (qd[fidx(g, D, b0[0], b0[1], b0[2])] + qd[fidx(g, D, b3[0], b3[1], b3[2])]);
+    double rl = lim_at<C, D, false>(g, rho, i3, jd - 1, adv_lo);
+    double rh = lim_at<C, D, false>(g, rho, i3, jd, adv_hi);
+    Flo = adv_lo * rl;
+    Fhi = adv_hi * rh;
+    if (withv) {
+      Flo *= lim_at<C, D, true>(g, qc, i3, jd - 1, adv_lo);
+      Fhi *= lim_at<C, D, true>(g, qc, i3, jd, adv_hi);
+    }
+  }
+  return (Fhi - Flo) / g.h[D];
+}
+
+template <int C>
+__global__ void k_transport(GridDev g, CVel<double> vel, const double* __restrict__ rho, bool withv, double* out) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= ext(g, C, 0) || j >= ext(g, C, 1)) return;
+  int id3[3] = {i, j, k};
+  size_t id = fidx(g, C, i, j, k);
+  if (id3[C] == 0 || id3[C] == g.n[C]) {
+    out[id] = 0.0;
+    return;
+  }
+  double s = flux_div_dir<C, 0>(g, vel.q, rho, withv, i, j, k) + flux_div_dir<C, 1>(g, vel.q, rho, withv, i, j, k) +
+             flux_div_dir<C, 2>(g, vel.q, rho, withv, i, j, k);
+  out[id] = s;
+}
+
+void launch_transport_flux(const GridDev& g, const double* const vel[3], const double* const rho[3],
+                           bool with_velocity, double* const out[3], cudaStream_t st) {
+  CVel<double> v{{vel[0], vel[1], vel[2]}};
+  k_transport<0><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, v, rho[0], with_velocity, out[0]);
+  k_transport<1><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, v, rho[1], with_velocity, out[1]);
+  k_transport<2><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, v, rho[2], with_velocity, out[2]);
+}
+
+__global__ void k_lincomb(size_t n, double a, const double* __restrict__ x, double b, const double* __restrict__ y,
+                          double c, const double* __restrict__ z, double* out) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (; t < n; t += stride) {
+    double s = a * x[t];
+    if (y) s += b * y[t];
+    if (z) s += c * z[t];
+    out[t] = s;
+  }
+}
+
+void launch_lincomb(size_t n, double a, const double* x, double b, const double* y, double c, const double* z,
+                    double* out, cudaStream_t st) {
+  int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+  if (blocks < 1) blocks = 1;
+  k_lincomb<<<blocks, 256, 0, st>>>(n, a, x, b, y, c, z, out);
+}
+
+// =========================================================== level set
+template <int D>
+__device__ __forceinline__ double phi_ext(const GridDev& g, const double* __restrict__ a, int i3[3], int m) {
+  int n = g.n[D];
+  int mm = m;
+  if (m < 0) mm = -m - 1;
+  else if (m >= n) mm = 2 * n - 1 - m;
+  mm = clampi(mm, 0, n - 1);
+  int c3[3] = {i3[0], i3[1], i3[2]};
+  c3[D] = mm;
+  return a[fidx(g, 3, c3[0], c3[1], c3[2])];
+}
+
+template <int D>
+__device__ __forceinline__ double ls_flux(const GridDev& g, const double* vel_d, const double* phi, int i3[3],
+                                          int face) {
+  // D-face 'face' between cells face-1 and face
+  int f3[3] = {i3[0], i3[1], i3[2]};
+  f3[D] = face;
+  double a = vel_d[fidx(g, D, f3[0], f3[1], f3[2])];
+  double lim;
+  if (a > 0.0)
+    lim = cui(phi_ext<D>(g, phi, i3, face - 2), phi_ext<D>(g, phi, i3, face - 1), phi_ext<D>(g, phi, i3, face));
+  else
+    lim = cui(phi_ext<D>(g, phi, i3, face + 1), phi_ext<D>(g, phi, i3, face), phi_ext<D>(g, phi, i3, face - 1));
+  return a * lim;
+}
+
+__global__ void k_ls_advect(GridDev g, CVel<double> vel, const double* __restrict__ phi_n,
+                            const double* __restrict__ phi_h, double dt, double* out) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.n[0] || j >= g.n[1]) return;
+  int i3[3] = {i, j, k};
+  double Q = (ls_flux<0>(g, vel.q[0], phi_h, i3, i + 1) - ls_flux<0>(g, vel.q[0], phi_h, i3, i)) / g.h[0] +
+             (ls_flux<1>(g, vel.q[1], phi_h, i3, j + 1) - ls_flux<1>(g, vel.q[1], phi_h, i3, j)) / g.h[1] +
+             (ls_flux<2>(g, vel.q[2], phi_h, i3, k + 1) - ls_flux<2>(g, vel.q[2], phi_h, i3, k)) / g.h[2];
+  size_t id = fidx(g, 3, i, j, k);
+  out[id] = phi_n[id] - dt * Q;
+}
+
+void launch_levelset_advect(const GridDev& g, const double* const vel[3], const double* phi_n,
+                            const double* phi_half, double dt, double* out, cudaStream_t st) {
+  CVel<double> v{{vel[0], vel[1], vel[2]}};
+  k_ls_advect<<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, v, phi_n, phi_half, dt, out);
+}
+
+__global__ void k_box_sdf(GridDev g, const double* __restrict__ xc, double hx_, double hy_, double hz_, double* psi) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.n[0] || j >= g.n[1]) return;
+  double x = (i + 0.5) * g.h[0], y = (j + 0.5) * g.h[1], z = (k + 0.5) * g.h[2];
+  double qx = fabs(x - xc[0]) - hx_, qy = fabs(y - xc[1]) - hy_, qz = fabs(z - xc[2]) - hz_;
+  double ox = fmax(qx, 0.0), oy = fmax(qy, 0.0), oz = fmax(qz, 0.0);
+  double outside = sqrt(ox * ox + oy * oy + oz * oz);
+  double inside = fmin(fmax(fmax(qx, qy), qz), 0.0);
+  psi[fidx(g, 3, i, j, k)] = outside + inside;
+}
+
+void launch_box_sdf(const GridDev& g, const double* xcom_dev, const double half[3], double* psi, cudaStream_t st) {
+  k_box_sdf<<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, xcom_dev, half[0], half[1], half[2], psi);
+}
+
+// =========================================================== momentum RHS
+template <int C>
+__global__ void k_mom_rhs(GridDev g, Coef<double> cf_n, const double* __restrict__ rho_n, CVel<double> u_n,
+                          const double* __restrict__ Cc, const double* __restrict__ rho_g, double gc, double inv_dt,
+                          double theta, double* b) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= ext(g, C, 0) || j >= ext(g, C, 1)) return;
+  int id3[3] = {i, j, k};
+  size_t id = fidx(g, C, i, j, k);
+  if (id3[C] == 0 || id3[C] == g.n[C]) {
+    b[id] = 0.0;
+    return;
+  }
+  double L = strain_at<C, double>(g, cf_n, u_n.q, i, j, k, nullptr);
+  b[id] = rho_n[id] * u_n.q[C][id] * inv_dt - Cc[id] + (1.0 - theta) * L + rho_g[id] * gc;
+}
+
+void launch_momentum_rhs(const GridDev& g, const Coef<double>& cf_n, const double* const rho_n[3],
+                         const double* const u_n[3], const double* const C[3], const double* const rho_g[3],
+                         const double grav[3], double inv_dt, double theta, double* const b[3], cudaStream_t st) {
+  CVel<double> u{{u_n[0], u_n[1], u_n[2]}};
+  k_mom_rhs<0><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, cf_n, rho_n[0], u, C[0], rho_g[0],
+                                                                          grav[0], inv_dt, theta, b[0]);
+  k_mom_rhs<1><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, cf_n, rho_n[1], u, C[1], rho_g[1],
+                                                                          grav[1], inv_dt, theta, b[1]);
+  k_mom_rhs<2><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, cf_n, rho_n[2], u, C[2], rho_g[2],
+                                                                          grav[2], inv_dt, theta, b[2]);
+}
+
+// explicit instantiations
+template void launch_viscous<double>(const GridDev&, const Coef<double>&, double, double, const double* const[3],
+                                     double* const[3], cudaStream_t, bool);
+template void launch_viscous<float>(const GridDev&, const Coef<float>&, float, float, const float* const[3],
+                                    float* const[3], cudaStream_t, bool);
+template void launch_viscous_residual<double>(const GridDev&, const Coef<double>&, double, double,
+                                              const double* const[3], const double* const[3], double* const[3],
+                                              cudaStream_t);
+template void launch_viscous_residual<float>(const GridDev&, const Coef<float>&, float, float, const float* const[3],
+                                             const float* const[3], float* const[3], cudaStream_t);
+template void launch_viscous_rbgs<double>(const GridDev&, const Coef<double>&, double, double, double* const[3],
+                                          const double* const[3], int, cudaStream_t);
+template void launch_viscous_rbgs<float>(const GridDev&, const Coef<float>&, float, float, float* const[3],
+                                         const float* const[3], int, cudaStream_t);
+template void launch_pressure<double>(const GridDev&, const double* const[3], const double*, double*, cudaStream_t);
+template void launch_pressure<float>(const GridDev&, const float* const[3], const float*, float*, cudaStream_t);
+template void launch_grad<double>(const GridDev&, const double*, double* const[3], cudaStream_t);
+template void launch_grad<float>(const GridDev&, const float*, float* const[3], cudaStream_t);
+template void launch_div<double>(const GridDev&, const double* const[3], double*, double, cudaStream_t);
+template void launch_div<float>(const GridDev&, const float* const[3], float*, float, cudaStream_t);
+
+}  // namespace wsi

@@ -1,0 +1,46 @@
+"""The C-ABI library builds, loads on a machine without a GPU and exports
+every entry point that include/wsi.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "wsi.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(wsi_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("wsi_create_grid", "wsi_set_phases", "wsi_stokes_solve", "wsi_dlm_constrain", "wsi_step"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1901_07892_gb300 import wsi
+    L = wsi.lib()
+    for n in _declared():
+        assert hasattr(L, n), n
+    assert set(_declared()) <= set(wsi.EXPORTED) | {"wsi_stokes_size", "wsi_velocity_size"}
+
+
+def test_invalid_arguments_rejected_without_gpu_work():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1901_07892_gb300 import wsi
+    L = wsi.lib()
+    d = wsi.GridDesc(0, 4, 4, 1.0, 1.0, 1.0, (ctypes.c_double * 6)(*([-1.0] * 6)),
+                     (ctypes.c_double * 3)(0, 0, -9.81), 2.0, 0.5, 0, 2, 2, 1, 2, 20)
+    h = ctypes.c_void_p()
+    assert L.wsi_create_grid(ctypes.byref(d), None, ctypes.byref(h)) == wsi.ERR_INVALID_ARG
+    d.nx = 4
+    d.bc[0] = 0.5  # not a wall sign
+    assert L.wsi_create_grid(ctypes.byref(d), None, ctypes.byref(h)) == wsi.ERR_INVALID_ARG
+    assert L.wsi_stokes_solve(None, None, None, 1.0, None, None) == wsi.ERR_INVALID_ARG

@@ -1,0 +1,278 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Operator applies and explicit steps: 1e-11 relative (max norm per field).
+Solves: the CUDA FGMRES runs to a relative residual of 1e-10 (well below the
+1e-8 target); fields must agree with the oracle's direct solution within
+1e-6 relative per field (p after mean removal).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.grid import Grid
+from oracle.materials import Materials, edge_harmonic
+from oracle import operators as ops
+from oracle.solve import solve_stokes
+from oracle import ib as oib
+from oracle import rigid as orig
+from oracle import transport as otr
+from oracle import levelset as ols
+from paper_1901_07892_gb300 import inputs, wsi
+
+OP_TOL = 1e-11
+FIELD_TOL = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _rel(a, b):
+    s = np.abs(b).max()
+    return np.abs(a - b).max() / (s if s > 0 else 1.0)
+
+
+def _grid(c):
+    return Grid(c.nx, c.ny, c.nz, c.lx, c.ly, c.lz, c.bc)
+
+
+def _random_case(nx, ny, nz, seed, lx=1.0, ly=0.9, lz=0.8):
+    rng = np.random.default_rng(seed)
+    c = inputs.Case(nx=nx, ny=ny, nz=nz, lx=lx, ly=ly, lz=lz)
+    x, y, z = c.cell_xyz()
+    c.phi = np.broadcast_to(z - 0.45 * lz + 0.05 * np.sin(7 * x + 3 * y), (nz, ny, nx)).copy()
+    c.psi = inputs.box_distance((x, y, z), (0.5 * lx, 0.45 * ly, 0.45 * lz), (0.2 * lx, 0.15 * ly, 0.1 * lz))
+    c.psi = np.broadcast_to(c.psi, (nz, ny, nx)).copy()
+    return c, rng
+
+
+def _oracle_mat(c, g):
+    return Materials(g, c.phi, c.psi, c.rho_l, c.rho_g, c.rho_s, c.mu_l, c.mu_g, c.mu_s, c.n_cells)
+
+
+def _ctx(c, **kw):
+    ctx = wsi.Context.from_case(c, **kw)
+    ctx.set_case(c, with_body=c.markers is not None)
+    return ctx
+
+
+SHAPES = [(37, 29, 11), (40, 20, 12), (33, 17, 1)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_materials_parity(shape):
+    nx, ny, nz = shape
+    c, _ = _random_case(nx, ny, nz, 0)
+    if nz == 1:
+        c.lz = 1.0 / nx
+        c.bc = (-1.0, -1.0, -1.0, -1.0, 1.0, 1.0)
+    g = _grid(c)
+    ctx = _ctx(c)
+    m = _oracle_mat(c, g)
+    assert _rel(ctx.coeff(wsi.C_RHO_CC), m.rho_cc.ravel()) < 1e-14
+    assert _rel(ctx.coeff(wsi.C_MU_CC), m.mu_cc.ravel()) < 1e-14
+    rf = np.concatenate([a.ravel() for a in m.rho_face])
+    assert _rel(ctx.coeff(wsi.C_RHO_FACE), rf) < 1e-14
+    rfl = np.concatenate([a.ravel() for a in m.rho_flow_face])
+    assert _rel(ctx.coeff(wsi.C_RHO_FLOW_FACE), rfl) < 1e-14
+    me = np.concatenate([m.mu_xy.ravel(), m.mu_xz.ravel(), m.mu_yz.ravel()])
+    assert _rel(ctx.coeff(wsi.C_MU_EDGE), me) < 1e-14
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_operator_parity(shape):
+    nx, ny, nz = shape
+    c, rng = _random_case(nx, ny, nz, 1)
+    if nz == 1:
+        c.lz = 1.0 / nx
+        c.bc = (-1.0, -1.0, -1.0, -1.0, 1.0, 1.0)
+    g = _grid(c)
+    ctx = _ctx(c)
+    m = _oracle_mat(c, g)
+    dt = 1e-3
+    vel = [rng.standard_normal(g.face_shape(d)) * g.interior_face_mask(d) for d in range(3)]
+    p = rng.standard_normal(g.cell_shape)
+    x = g.pack(vel[0], vel[1], vel[2], p)
+    vflat = x[:ctx.nvel].copy()
+    # Stokes
+    got = ctx.apply(wsi.OP_STOKES, torch.from_numpy(x).cuda(), dt).cpu().numpy()
+    ref = ops.stokes_apply(g, m, m.rho_face, dt, c.theta, x)
+    for a, b in zip(g.unpack(got), g.unpack(ref)):
+        assert _rel(a, b) < OP_TOL
+    # viscous and strain
+    got = ctx.apply(wsi.OP_VISCOUS, vflat, dt)
+    ref = np.concatenate([a.ravel() for a in ops.viscous_apply(g, m, m.rho_face, dt, c.theta, *vel)])
+    assert _rel(got, ref) < OP_TOL
+    got = ctx.apply(wsi.OP_STRAIN, vflat, dt)
+    ref = ops.strain_rate_apply(g, m, *vel)
+    o = np.cumsum([0] + [g.n_faces(d) for d in range(3)])
+    for d in range(3 if nz > 1 else 2):
+        assert _rel(got[o[d]:o[d + 1]], ref[d].ravel()) < OP_TOL
+    # pressure, grad, div
+    beta = [1.0 / a for a in m.rho_face]
+    assert _rel(ctx.apply(wsi.OP_PRESSURE, p.ravel().copy(), dt), ops.pressure_apply(g, beta, p).ravel()) < OP_TOL
+    gr = np.concatenate([a.ravel() for a in ops.grad(g, p)])
+    assert _rel(ctx.apply(wsi.OP_GRAD, p.ravel().copy(), dt), gr) < OP_TOL
+    assert _rel(ctx.apply(wsi.OP_DIV, vflat, dt), ops.div(g, *vel).ravel()) < OP_TOL
+
+
+def _solve_parity(c, precision, rtol=1e-10, rhs_seed=3):
+    g = _grid(c)
+    ctx = _ctx(c, precision=precision, restart=30)
+    m = _oracle_mat(c, g)
+    rng = np.random.default_rng(rhs_seed)
+    if "rhs_u" in c.extra:
+        bu = [c.extra["rhs_u"][d] * g.interior_face_mask(d) for d in range(3)]
+    else:
+        bu = [rng.uniform(-1, 1, g.face_shape(d)) * 1e-2 * g.interior_face_mask(d) for d in range(3)]
+    # gravity on top (rho^flow g), as in a tank step
+    from oracle.materials import face_average, flow_only
+    for d in range(3):
+        if c.gravity[d] != 0.0:
+            bu[d] = bu[d] + flow_only(face_average(g, c.phi, d), c.rho_l, c.rho_g, m.eps) * c.gravity[d] * \
+                g.interior_face_mask(d)
+    b = g.pack(bu[0], bu[1], bu[2], np.zeros(g.cell_shape))
+    x, st = ctx.solve(torch.from_numpy(b).cuda(), c.dt, rtol=rtol, max_iters=400)
+    assert st.rel_residual <= rtol * 1.01, st.rel_residual
+    xo = solve_stokes(g, m, m.rho_face, c.dt, c.theta, b)
+    xg = x.cpu().numpy()
+    errs = [_rel(a, o) for a, o in zip(g.unpack(xg), g.unpack(xo))]
+    return errs, st
+
+
+@pytest.mark.parametrize("precision", [wsi.PREC_FP64, wsi.PREC_MIXED])
+def test_solve_parity_config1_2d(precision):
+    """Full config 1: 64x64 tank, flat interface, locked square solid
+    (rho_s = 500), seeded velocity right-hand side, solve to 1e-10."""
+    c = inputs.tank2d(n=64, seed=0)
+    errs, st = _solve_parity(c, precision)
+    assert errs[0] < FIELD_TOL and errs[1] < FIELD_TOL and errs[3] < FIELD_TOL, errs
+
+
+@pytest.mark.parametrize("precision", [wsi.PREC_FP64, wsi.PREC_MIXED])
+def test_solve_parity_3d_ragged(precision):
+    c = inputs.tank3d(nxyz=(24, 20, 16), seed=5, dt=5e-4)
+    errs, st = _solve_parity(c, precision)
+    assert max(errs) < FIELD_TOL, errs
+
+
+def test_ib_parity_near_walls():
+    c, rng = _random_case(21, 18, 15, 4)
+    g = _grid(c)
+    ctx = _ctx(c)
+    n = 500
+    X = np.stack([rng.uniform(0, c.lx, n), rng.uniform(0, c.ly, n), rng.uniform(0, c.lz, n)], 1)
+    vel = [rng.standard_normal(g.face_shape(d)) * g.interior_face_mask(d) for d in range(3)]
+    vflat = np.concatenate([a.ravel() for a in vel])
+    U = ctx.interp(vflat, X).reshape(n, 3)
+    assert _rel(U, oib.interpolate(g, vel, X)) < 1e-13
+    F = rng.standard_normal((n, 3))
+    S = ctx.spread(F, X, 2e-4)
+    ref = np.concatenate([a.ravel() for a in oib.spread(g, F, X, 2e-4)])
+    assert _rel(S, ref) < 1e-12
+
+
+def test_dlm_constrain_parity_config1():
+    c = inputs.tank2d(n=64, seed=1)
+    g = _grid(c)
+    ctx = _ctx(c)
+    rng = np.random.default_rng(2)
+    vel = [rng.uniform(-1, 1, g.face_shape(d)) * g.interior_face_mask(d) for d in range(3)]
+    vflat = np.concatenate([a.ravel() for a in vel])
+    got, bs = ctx.dlm_constrain(vflat)
+    new, Ub, Ur, Wr, Xc = orig.constrain(g, vel, c.markers, c.dV, [True] * 6, np.zeros(3), np.zeros(3))
+    assert _rel(got, np.concatenate([a.ravel() for a in new])) < 1e-12
+    assert np.allclose(bs.X_com, Xc, atol=1e-14)
+
+
+def test_dlm_free_body_parity():
+    c = inputs.tank3d(n=24, seed=None)
+    c.lock = (False,) * 6
+    g = _grid(c)
+    ctx = _ctx(c)
+    rng = np.random.default_rng(5)
+    vel = [rng.uniform(-1, 1, g.face_shape(d)) * g.interior_face_mask(d) for d in range(3)]
+    vflat = np.concatenate([a.ravel() for a in vel])
+    got, bs = ctx.dlm_constrain(vflat)
+    new, Ub, Ur, Wr, Xc = orig.constrain(g, vel, c.markers, c.dV, [False] * 6, np.zeros(3), np.zeros(3))
+    assert _rel(got, np.concatenate([a.ravel() for a in new])) < 1e-11
+    assert np.allclose(bs.U_r, Ur, rtol=1e-10, atol=1e-14)
+    assert np.allclose(bs.W_r, Wr, rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_transport_parity(k):
+    c, rng = _random_case(26, 19, 13, 6)
+    g = _grid(c)
+    ctx = _ctx(c)
+    m = _oracle_mat(c, g)
+    mk = lambda s: [rng.uniform(-1, 1, g.face_shape(d)) * 0.3 * g.interior_face_mask(d) for d in range(3)]
+    un, unm1, uk = mk(0), mk(1), mk(2)
+    flat = lambda v: np.concatenate([a.ravel() for a in v])
+    dt = 2e-3
+    rho, C = ctx.transport(flat(un), flat(unm1), flat(uk), k, dt)
+    u1, u2 = otr.rk_velocities(un, unm1, uk, k)
+    r3, Co = otr.ssp_rk3(g, m.rho_face, un, u1, u2, dt)
+    assert _rel(rho, flat(r3)) < OP_TOL
+    assert _rel(C, flat(Co)) < OP_TOL
+
+
+def test_levelset_parity():
+    c, rng = _random_case(23, 17, 12, 7)
+    g = _grid(c)
+    ctx = _ctx(c)
+    vel = [rng.uniform(-1, 1, g.face_shape(d)) * g.interior_face_mask(d) for d in range(3)]
+    flat = lambda v: np.concatenate([a.ravel() for a in v])
+    phih = c.phi + 0.01 * rng.standard_normal(c.phi.shape)
+    got = ctx.advect_levelset(flat(vel), c.phi.ravel().copy(), phih.ravel().copy(), 1e-3)
+    ref = ols.advect(g, vel, c.phi, phih, 1e-3)
+    assert _rel(got, ref.ravel()) < OP_TOL
+
+
+@pytest.mark.parametrize("precision", [wsi.PREC_FP64, wsi.PREC_MIXED])
+def test_step_parity_small_tank(precision):
+    """Two full time steps of a 3-D tank with a wavy surface and a locked
+    box, from rest: the velocity, pressure and level set agree with the
+    oracle's step (which solves exactly)."""
+    from oracle import step as ost
+    c = inputs.tank3d(nxyz=(16, 12, 12), seed=11, dt=5e-4)
+    c.rho_s = c.rho_l
+    g = _grid(c)
+    ctx = wsi.Context.from_case(c, precision=precision, restart=30)
+    ctx.set_case(c, rho_s=c.rho_l)
+    pr = ost.Props(rho_l=c.rho_l, rho_g=c.rho_g, rho_s=c.rho_l, mu_l=c.mu_l, mu_g=c.mu_g, gravity=c.gravity,
+                   gravity_mode="flow")
+    body = ost.Body(c.markers, c.dV, [True] * 6, half=c.box_half)
+    s = ost.State(g, pr, c.phi, c.psi, body)
+    for _ in range(2):
+        ctx.step(c.dt, rtol=1e-11, max_iters=400)
+        ost.step(s, c.dt)
+    vel = ctx.get_field(wsi.F_VEL)
+    ref = np.concatenate([a.ravel() for a in s.vel])
+    assert _rel(vel, ref) < FIELD_TOL
+    p = ctx.get_field(wsi.F_P)
+    assert _rel(p - p.mean(), (s.p - s.p.mean()).ravel()) < FIELD_TOL
+    assert _rel(ctx.get_field(wsi.F_PHI), s.phi.ravel()) < 1e-9
+    assert _rel(ctx.get_field(wsi.F_MARKERS), s.body.X.ravel()) < 1e-14
+
+
+def test_hydrostatic_config2_full_size():
+    """Config 2 at its full 128^3 size: flat surface at z = 0.6, locked box
+    centred on it, rho^flow g, u^0 = 0: the velocity stays at round-off over
+    time steps (Sec. 5, well-balanced gravity)."""
+    c = inputs.tank3d(n=128, seed=None, dt=5e-4)
+    ctx = wsi.Context.from_case(c, precision=wsi.PREC_MIXED)
+    ctx.set_case(c, rho_s=c.rho_l)
+    umax = []
+    for _ in range(3):
+        ctx.step(c.dt, rtol=1e-10, max_iters=300)
+        umax.append(np.abs(ctx.get_field(wsi.F_VEL)).max())
+    # spurious velocity at the solver-tolerance level, not growing
+    assert max(umax) < 1e-7, umax
+    assert umax[-1] <= 10 * umax[0] + 1e-12, umax
