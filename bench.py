@@ -1,0 +1,318 @@
+"""Throughput of the implicit Stokes time step on GB300.
+
+One "step" is one full time step of the method (Sec. 4.2): level-set
+advection, materials, SSP-RK3 consistent transport, two implicit Stokes
+solves (FGMRES + projection preconditioner + pressure multigrid) to a
+relative residual of 1e-8, and the DLM rigidity projection with the marker
+update.  Workload (default): a 256^3 three-phase tank over the unit cube,
+water depth 0.6 perturbed by 8 seeded Fourier modes (amplitude <= 0.05),
+density ratio 1000:1.2, locked 0.2 x 0.2 x 0.1 box (one marker per half
+cell) centred on the surface, dt = 5e-4; the surface sloshes, so every solve
+iterates.  Metric: cell-steps/s = cells x steps / time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl wsi|reference]
+       [--precision mixed|fp64] [--n 256] [--roofline-kernel stokes|rbgs_p|...]
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU
+(the method needs no exchange between replicas here): weak scaling.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1901_07892_gb300 import inputs  # noqa: E402
+
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# float64 FMA rate: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (max SM clock)
+FP64_PEAK_DERIVED_GFLOPS = 152 * 2 * 2 * 2.07
+KCLASS = {"stokes": 0, "rbgs_p": 1, "rbgs_v": 2, "transport": 3, "mdot": 4, "maxpy": 5, "restrict": 6,
+          "prolong": 7}
+
+
+def kernel_model(name, nx, ny, nz, prec_bytes):
+    """Algorithmic bytes and flops per launch of a kernel class (each array
+    touched once; coefficient arrays included)."""
+    N = nx * ny * nz
+    F = (nx + 1) * ny * nz + nx * (ny + 1) * nz + nx * ny * (nz + 1)
+    E = (nx + 1) * (ny + 1) * nz + (nx + 1) * ny * (nz + 1) + nx * (ny + 1) * (nz + 1)
+    if name == "stokes":
+        # read u,v,w,p, rho_face, mu_cc, mu_edges; write 4 outputs (float64)
+        byts = 8 * (F + N + F + N + E + F + N)
+        flops = 44 * F + 8 * N
+        return byts, flops, "alu"
+    if name == "rbgs_p":
+        # one colour: read x (all), b (half), 3 beta face arrays; write x (half)
+        byts = prec_bytes * (N + N // 2 + F + N // 2)
+        return byts, 14 * N // 2, "hbm"
+    if name == "rbgs_v":
+        byts = prec_bytes * (F + F // 2 + F + N + E + F // 2)
+        return byts, 50 * F // 2, "hbm"
+    if name == "transport":
+        byts = 8 * (F + F + F)
+        return byts, 300 * F, "alu"
+    raise ValueError(name)
+
+
+def sample_clocks_start(path):
+    try:
+        f = open(path, "w")
+        p = subprocess.Popen(["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                              "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                             stdout=f, stderr=subprocess.DEVNULL)
+        return p, f
+    except Exception:
+        return None, None
+
+
+def sample_clocks_stop(h, path, gpu_index):
+    p, f = h
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except Exception:
+        p.kill()
+    f.close()
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9 or parts[0] != str(gpu_index):
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx.append(float(parts[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def build_case(n):
+    c = inputs.tank3d(n=n, seed=7, dt=5e-4)
+    c.rho_s = c.rho_l  # locked body: rho_s = densest fluid, gravity from rho^flow (Sec. 5)
+    return c
+
+
+def oracle_sample_step(n_sample=12):
+    """One oracle step of the same tank recipe at n_sample^3 (host cores)."""
+    from oracle.grid import Grid
+    from oracle import step as ost
+    c = build_case(n_sample)
+    g = Grid(c.nx, c.ny, c.nz, c.lx, c.ly, c.lz, c.bc)
+    pr = ost.Props(rho_l=c.rho_l, rho_g=c.rho_g, rho_s=c.rho_s, mu_l=c.mu_l, mu_g=c.mu_g, gravity=c.gravity,
+                   gravity_mode="flow")
+    s = ost.State(g, pr, c.phi, c.psi, ost.Body(c.markers, c.dV, [True] * 6, half=c.box_half))
+    t0 = time.perf_counter()
+    ost.step(s, c.dt)
+    dt = time.perf_counter() - t0
+    return g.n_cells, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    n_sample = 12
+    times = []
+    cells = 0
+    for i in range(args.warmup + args.steps):
+        cells, dt = oracle_sample_step(n_sample)
+        if i >= args.warmup:
+            times.append(dt)
+    T = float(np.sum(times))
+    value = cells * len(times) / T
+    sample = "one oracle step (materials, transport, exact sparse-LU Stokes solves, DLM) of the same tank " \
+             "recipe at %d^3 per step; numpy/scipy, single-threaded" % n_sample
+    line = {"impl": "reference", "metric": "cell-steps/s", "value": value, "unit": "cell-steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "tank%d" % args.n, "sample": "%d^3" % n_sample},
+            "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="wsi", choices=["wsi", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--roofline-kernel", default="stokes", choices=list(KCLASS))
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP64 comparison run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    from paper_1901_07892_gb300 import wsi
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    c = build_case(args.n)
+    cells = c.nx * c.ny * c.nz
+    prec = wsi.PREC_MIXED if args.precision == "mixed" else wsi.PREC_FP64
+
+    def make_ctx(p):
+        ctx = wsi.Context.from_case(c, precision=p, restart=20, stream=stream.cuda_stream)
+        ctx.set_case(c, rho_s=c.rho_l)
+        return ctx
+
+    def timed_steps(ctx, k):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        ev0.record(stream)
+        its = []
+        for _ in range(k):
+            st = ctx.step(c.dt, rtol=args.rtol, max_iters=200)
+            its.append([st.iters[0], st.iters[1]])
+        ev1.record(stream)
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, its
+
+    ctx = make_ctx(prec)
+    for _ in range(args.warmup):
+        ctx.step(c.dt, rtol=args.rtol, max_iters=200)
+    clk_path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % rank)
+    os.makedirs(os.path.dirname(clk_path), exist_ok=True)
+    clk = sample_clocks_start(clk_path)
+    kname = args.roofline_kernel
+    wsi.ktimer_enable(KCLASS[kname])
+    l0 = wsi.launch_count()
+    ms, its = timed_steps(ctx, args.steps)
+    l1 = wsi.launch_count()
+    kt_ms, kt_n = wsi.ktimer_read()
+    wsi.ktimer_enable(-1)
+    clocks = sample_clocks_stop(clk, clk_path, torch.cuda.current_device())
+    value = world * cells * args.steps / (ms * 1e-3)
+
+    # roofline of the chosen kernel: algorithmic work per launch / measured duration
+    pb = 4 if prec == wsi.PREC_MIXED else 8
+    byts, flops, bound = kernel_model(kname, c.nx, c.ny, c.nz, pb)
+    peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
+    roof = None
+    if kt_n > 0:
+        dur = kt_ms / kt_n * 1e-3
+        if bound == "alu":
+            roof = {"bound": "alu", "achieved": flops / dur / 1e12, "peak": FP64_PEAK_DERIVED_GFLOPS / 1e3,
+                    "unit": "TFLOP/s", "frac": flops / dur / 1e9 / FP64_PEAK_DERIVED_GFLOPS,
+                    "traffic": None, "kernel": kname, "launches": kt_n, "avg_us": dur * 1e6,
+                    "algorithmic_bytes_per_launch": byts, "flops_per_launch": flops,
+                    "peak_note": "float64 FMA peak derived: 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz"}
+        else:
+            hb = peaks.get("hbm_gbs", 6800.0)
+            roof = {"bound": "hbm", "achieved": byts / dur / 1e9, "peak": hb, "unit": "GB/s",
+                    "frac": byts / dur / 1e9 / hb, "traffic": None, "kernel": kname, "launches": kt_n,
+                    "avg_us": dur * 1e6, "algorithmic_bytes_per_launch": byts,
+                    "peak_note": "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"}
+
+    # end to end through the C ABI with host buffers: upload the state from
+    # pinned host memory, step, read the new velocity and pressure back
+    hv = torch.empty(ctx.nvel, dtype=torch.float64).pin_memory()
+    hvo = torch.empty(ctx.nvel, dtype=torch.float64).pin_memory()
+    hphi = torch.empty(ctx.ncell, dtype=torch.float64).pin_memory()
+    hpsi = torch.empty(ctx.ncell, dtype=torch.float64).pin_memory()
+    hp = torch.empty(ctx.ncell, dtype=torch.float64).pin_memory()
+    for arr, f in ((hv, wsi.F_VEL), (hvo, wsi.F_VEL_OLD), (hphi, wsi.F_PHI), (hpsi, wsi.F_PSI)):
+        ctx.L.wsi_get_field(ctx._h, f, wsi._ptr(arr))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for arr, f in ((hv, wsi.F_VEL), (hvo, wsi.F_VEL_OLD), (hphi, wsi.F_PHI), (hpsi, wsi.F_PSI)):
+            ctx.L.wsi_set_field(ctx._h, f, wsi._ptr(arr))
+        ctx.step(c.dt, rtol=args.rtol, max_iters=200)
+        ctx.L.wsi_get_field(ctx._h, wsi.F_VEL, wsi._ptr(hv))
+        ctx.L.wsi_get_field(ctx._h, wsi.F_P, wsi._ptr(hp))
+        ctx.L.wsi_get_field(ctx._h, wsi.F_VEL_OLD, wsi._ptr(hvo))
+        ctx.L.wsi_get_field(ctx._h, wsi.F_PHI, wsi._ptr(hphi))
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = 8 * (2 * ctx.nvel + 2 * ctx.ncell)
+    d2h = 8 * (2 * ctx.nvel + 2 * ctx.ncell)
+    e2e = {"value": world * cells * args.steps / e2e_s, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+    ctx.close()
+
+    compare = None
+    if not args.no_compare and prec == wsi.PREC_MIXED:
+        ctx64 = make_ctx(wsi.PREC_FP64)
+        for _ in range(args.warmup):
+            ctx64.step(c.dt, rtol=args.rtol, max_iters=200)
+        ms64, its64 = timed_steps(ctx64, args.steps)
+        compare = {"plain_fp64": {"value": world * cells * args.steps / (ms64 * 1e-3), "unit": "cell-steps/s",
+                                  "ms_per_step": ms64 / args.steps, "fgmres_iters": its64},
+                   "speedup_mixed_over_fp64": ms64 / ms}
+        ctx64.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        n_s, t_s = oracle_sample_step(12)
+        cpu = {"value": n_s / t_s, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+               "sample": "one oracle time step (exact sparse-LU solves) of the same tank recipe at 12^3; "
+                         "numpy/scipy single-threaded on the GPU host"}
+    if rank == 0:
+        line = {"metric": "cell-steps/s", "value": value, "unit": "cell-steps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64 outer / f32 preconditioner" if prec == wsi.PREC_MIXED else "f64",
+                "data": "synthetic",
+                "config": {"workload": "tank%d: %d^3 three-phase tank, 8-mode seeded surface, locked box, "
+                                       "2 Stokes solves per step to rtol %.0e" % (args.n, args.n, args.rtol),
+                           "cells": cells, "precision": args.precision, "l2": "inputs larger than L2 (no flush)",
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "fgmres_iters": its},
+                "gpu_launches": int(l1 - l0), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clocks, "compare": compare}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

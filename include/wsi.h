@@ -157,13 +157,16 @@ int wsi_dlm_constrain(wsi_ctx* ctx, double* vel, wsi_body_state* out);
  * update, on library-owned state.  Tolerance and limits from opts. */
 int wsi_step(wsi_ctx* ctx, double dt, const wsi_solve_opts* opts, wsi_step_stats* stats);
 
-/* State access for the step.  which: WSI_F_VEL (velocity vector u^n),
- * WSI_F_P (cell), WSI_F_PHI, WSI_F_PSI (cell), WSI_F_MARKERS (n x 3). */
+/* State access for the step.  which: WSI_F_VEL (velocity vector u^n;
+ * setting it also sets u^{n-1} = u^n), WSI_F_VEL_OLD (u^{n-1}, used by the
+ * extrapolated transport velocities of Sec. 4.2.2), WSI_F_P (cell),
+ * WSI_F_PHI, WSI_F_PSI (cell), WSI_F_MARKERS (n x 3, get only). */
 #define WSI_F_VEL 0
 #define WSI_F_P 1
 #define WSI_F_PHI 2
 #define WSI_F_PSI 3
 #define WSI_F_MARKERS 4
+#define WSI_F_VEL_OLD 5
 int wsi_get_field(wsi_ctx* ctx, int which, double* dst);
 int wsi_set_field(wsi_ctx* ctx, int which, const double* src);
 
@@ -207,6 +210,19 @@ int wsi_advect_levelset(wsi_ctx* ctx, const double* vel, const double* phi_n,
  * spread: F (n x 3), marker volume dV -> velocity vector (overwritten). */
 int wsi_interp(wsi_ctx* ctx, const double* vel, const double* X, int n, double* U);
 int wsi_spread(wsi_ctx* ctx, const double* F, const double* X, int n, double dV, double* vel);
+
+/* Instrumentation (no counterpart in the paper; used to report kernel
+ * rooflines).  wsi_launch_count: kernels launched by this library in this
+ * process so far.  wsi_ktimer_enable(k): bracket every later launch of
+ * kernel class k with CUDA events on its own stream (k = -1 disables;
+ * enabling resets the record).  wsi_ktimer_read: summed device time and
+ * number of bracketed launches (synchronises on the recorded events).
+ * Classes: 0 Stokes matvec, 1 pressure red-black sweep, 2 viscous red-black
+ * sweep, 3 transport flux divergence, 4 Gram-Schmidt dots, 5 Gram-Schmidt
+ * axpy, 6 residual restriction, 7 prolongation. */
+long long wsi_launch_count(void);
+int wsi_ktimer_enable(int kernel_class);
+int wsi_ktimer_read(double* total_ms, long long* launches);
 
 #ifdef __cplusplus
 }

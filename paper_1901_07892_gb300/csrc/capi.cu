@@ -16,6 +16,43 @@
 
 using namespace wsi;
 
+std::atomic<long long> wsi::g_launches{0};
+
+namespace {
+// per-kernel-class event timer (one class enabled at a time, process-wide)
+struct KTimer {
+  int enabled = -1;
+  std::vector<cudaEvent_t> start, stop;
+  size_t used = 0;
+  bool open = false;
+};
+KTimer g_kt;
+constexpr size_t KT_MAX = 1 << 16;
+}  // namespace
+
+void wsi::ktimer_begin(int id, cudaStream_t st) {
+  if (id != g_kt.enabled || g_kt.used >= KT_MAX) return;
+  if (g_kt.used == g_kt.start.size()) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return;
+    }
+    g_kt.start.push_back(a);
+    g_kt.stop.push_back(b);
+  }
+  cudaEventRecord(g_kt.start[g_kt.used], st);
+  g_kt.open = true;
+}
+
+void wsi::ktimer_end(int id, cudaStream_t st) {
+  if (id != g_kt.enabled || !g_kt.open) return;
+  cudaEventRecord(g_kt.stop[g_kt.used], st);
+  ++g_kt.used;
+  g_kt.open = false;
+}
+
 struct Body {
   int n = 0;
   double dV = 0.0;
@@ -57,6 +94,7 @@ struct wsi_ctx {
   Precond<double> P64;
   Precond<float> P32;
   bool pc_dirty = true;
+  bool pc_alloc = false;
   Opts opts;
   Body body;
   bool has_body = false;
@@ -132,7 +170,7 @@ __global__ void k_recip(size_t n, const double* __restrict__ a, double* b) {
 }
 
 void recip(wsi_ctx* c, const double* a, double* b, size_t n) {
-  if (n) k_recip<<<cdiv(n, 256), 256, 0, c->st>>>(n, a, b);
+  if (n) { k_recip<<<cdiv(n, 256), 256, 0, c->st>>>(n, a, b); WSI_COUNT(); }
 }
 
 int copy_in(wsi_ctx* c, double* dst, const double* src, size_t n) {
@@ -149,6 +187,14 @@ int copy_out(wsi_ctx* c, double* dst, const double* src, size_t n) {
 }
 
 int ensure_pc(wsi_ctx* c) {
+  if (!c->pc_alloc) {
+    // allocated on first use: grids that are only used for operator applies
+    // need no multigrid hierarchy
+    int rc = c->desc.precision == WSI_PREC_MIXED ? precond_alloc<float>(c->P32, c->g, c->err)
+                                                 : precond_alloc<double>(c->P64, c->g, c->err);
+    if (rc) return rc;
+    c->pc_alloc = true;
+  }
   if (!c->pc_dirty) return WSI_OK;
   Coef<double> cf = coef_now(c);
   int rc = c->desc.precision == WSI_PREC_MIXED ? precond_setup<float>(c->P32, c->g, cf, c->st, c->err)
@@ -348,6 +394,30 @@ int valid_ctx(wsi_ctx* c) { return c ? WSI_OK : WSI_ERR_INVALID_ARG; }
 
 extern "C" {
 
+long long wsi_launch_count(void) { return g_launches.load(); }
+
+int wsi_ktimer_enable(int kernel_class) {
+  if (kernel_class < -1 || kernel_class >= KC_COUNT) return WSI_ERR_INVALID_ARG;
+  g_kt.enabled = kernel_class;
+  g_kt.used = 0;
+  g_kt.open = false;
+  return WSI_OK;
+}
+
+int wsi_ktimer_read(double* total_ms, long long* launches) {
+  if (!total_ms || !launches) return WSI_ERR_INVALID_ARG;
+  double t = 0.0;
+  for (size_t i = 0; i < g_kt.used; ++i) {
+    if (cudaEventSynchronize(g_kt.stop[i]) != cudaSuccess) return WSI_ERR_CUDA;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, g_kt.start[i], g_kt.stop[i]) != cudaSuccess) return WSI_ERR_CUDA;
+    t += ms;
+  }
+  *total_ms = t;
+  *launches = (long long)g_kt.used;
+  return WSI_OK;
+}
+
 size_t wsi_stokes_size(const wsi_ctx* c) { return c ? c->nstk : 0; }
 size_t wsi_velocity_size(const wsi_ctx* c) { return c ? c->nvel : 0; }
 const char* wsi_last_error(const wsi_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -429,12 +499,6 @@ int wsi_create_grid(const wsi_grid_desc* d, void* stream, wsi_ctx** out) {
     c->err = "out of device memory";
     wsi_destroy(c);
     return WSI_ERR_OOM;
-  }
-  int rc = d->precision == WSI_PREC_MIXED ? precond_alloc<float>(c->P32, g, c->err)
-                                          : precond_alloc<double>(c->P64, g, c->err);
-  if (rc) {
-    wsi_destroy(c);
-    return rc;
   }
   if (cuda_check(c, "create")) {
     wsi_destroy(c);
@@ -686,6 +750,7 @@ int wsi_get_field(wsi_ctx* c, int which, double* dst) {
   int rc;
   switch (which) {
     case WSI_F_VEL: rc = copy_out(c, dst, c->vel, c->nvel); break;
+    case WSI_F_VEL_OLD: rc = copy_out(c, dst, c->vel_old, c->nvel); break;
     case WSI_F_P: rc = copy_out(c, dst, c->p, c->ncell); break;
     case WSI_F_PHI: rc = copy_out(c, dst, c->phi, c->ncell); break;
     case WSI_F_PSI: rc = copy_out(c, dst, c->psi, c->ncell); break;
@@ -707,6 +772,7 @@ int wsi_set_field(wsi_ctx* c, int which, const double* src) {
       rc = copy_in(c, c->vel, src, c->nvel);
       if (!rc) cudaMemcpyAsync(c->vel_old, c->vel, c->nvel * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
       break;
+    case WSI_F_VEL_OLD: rc = copy_in(c, c->vel_old, src, c->nvel); break;
     case WSI_F_P: rc = copy_in(c, c->p, src, c->ncell); break;
     case WSI_F_PHI: rc = copy_in(c, c->phi, src, c->ncell); break;
     case WSI_F_PSI: rc = copy_in(c, c->psi, src, c->ncell); break;

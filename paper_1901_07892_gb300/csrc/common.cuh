@@ -10,7 +10,29 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <atomic>
+
 namespace wsi {
+
+// process-wide count of kernel launches made by the library
+extern std::atomic<long long> g_launches;
+#define WSI_COUNT() (::wsi::g_launches.fetch_add(1, std::memory_order_relaxed))
+
+// Optional per-kernel timing: when kernel class `id` is enabled, its launches
+// are bracketed by CUDA events on their own stream.
+enum KernelClass {
+  KC_STOKES = 0,     // float64 Stokes matvec (momentum rows + continuity)
+  KC_RBGS_P = 1,     // pressure red-black Gauss-Seidel half sweep
+  KC_RBGS_V = 2,     // viscous red-black Gauss-Seidel half sweep
+  KC_TRANSPORT = 3,  // consistent transport flux divergence
+  KC_MDOT = 4,       // Gram-Schmidt block dot products
+  KC_MAXPY = 5,      // Gram-Schmidt multi-axpy
+  KC_RESTRICT = 6,   // residual + restriction
+  KC_PROLONG = 7,    // prolongation + correction
+  KC_COUNT = 8
+};
+void ktimer_begin(int id, cudaStream_t st);
+void ktimer_end(int id, cudaStream_t st);
 
 struct GridDev {
   int n[3];       // cells per axis

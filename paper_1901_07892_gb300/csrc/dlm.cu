@@ -104,7 +104,7 @@ void launch_ib_interp(const GridDev& g, const double* const vel[3], const double
                       cudaStream_t st) {
   if (n <= 0) return;
   CVel<double> v{{vel[0], vel[1], vel[2]}};
-  k_interp<<<cdiv(3LL * n, 128), 128, 0, st>>>(g, v, X, n, U);
+  { k_interp<<<cdiv(3LL * n, 128), 128, 0, st>>>(g, v, X, n, U); WSI_COUNT(); }
 }
 
 void launch_ib_spread(const GridDev& g, const double* F, const double* X, int n, double dV, double* const vel[3],
@@ -112,7 +112,7 @@ void launch_ib_spread(const GridDev& g, const double* F, const double* X, int n,
   if (n <= 0) return;
   Vel<double> v{{vel[0], vel[1], vel[2]}};
   double scale = dV / (g.h[0] * g.h[1] * g.h[2]);
-  k_spread<<<cdiv(3LL * n, 128), 128, 0, st>>>(g, F, X, n, scale, v);
+  { k_spread<<<cdiv(3LL * n, 128), 128, 0, st>>>(g, F, X, n, scale, v); WSI_COUNT(); }
 }
 
 // ---------------------------------------------------------------- rigid sums
@@ -173,8 +173,8 @@ __global__ void k_rigid_final(const double* __restrict__ part, double* out) {
 
 void launch_rigid_sums(const double* X, const double* U, int n, const double* xc_dev, double* out, double* scratch,
                        cudaStream_t st) {
-  k_rigid_part<<<SB, ST, 0, st>>>(X, U, n, xc_dev, scratch);
-  k_rigid_final<<<1, 32, 0, st>>>(scratch, out);
+  { k_rigid_part<<<SB, ST, 0, st>>>(X, U, n, xc_dev, scratch); WSI_COUNT(); }
+  { k_rigid_final<<<1, 32, 0, st>>>(scratch, out); WSI_COUNT(); }
 }
 
 __global__ void k_mean3(const double* __restrict__ sums, int n, double* xc) {
@@ -183,9 +183,9 @@ __global__ void k_mean3(const double* __restrict__ sums, int n, double* xc) {
 
 void launch_marker_mean(const double* X, int n, double* xc_dev, double* scratch, cudaStream_t st) {
   // scratch: SB*NS partials followed by NS sums
-  k_rigid_part<<<SB, ST, 0, st>>>(X, nullptr, n, nullptr, scratch);
-  k_rigid_final<<<1, 32, 0, st>>>(scratch, scratch + SB * NS);
-  k_mean3<<<1, 32, 0, st>>>(scratch + SB * NS, n, xc_dev);
+  { k_rigid_part<<<SB, ST, 0, st>>>(X, nullptr, n, nullptr, scratch); WSI_COUNT(); }
+  { k_rigid_final<<<1, 32, 0, st>>>(scratch, scratch + SB * NS); WSI_COUNT(); }
+  { k_mean3<<<1, 32, 0, st>>>(scratch + SB * NS, n, xc_dev); WSI_COUNT(); }
 }
 
 __global__ void k_body_vel(const double* __restrict__ X, const double* __restrict__ U, int n,
@@ -210,7 +210,7 @@ __global__ void k_body_vel(const double* __restrict__ X, const double* __restric
 void launch_body_velocity(const double* X, const double* U, int n, const double* rigid_dev, const double* xc_dev,
                           double* Ub, double* F, cudaStream_t st) {
   if (n <= 0) return;
-  k_body_vel<<<cdiv(n, 128), 128, 0, st>>>(X, U, n, rigid_dev, xc_dev, Ub, F);
+  { k_body_vel<<<cdiv(n, 128), 128, 0, st>>>(X, U, n, rigid_dev, xc_dev, Ub, F); WSI_COUNT(); }
 }
 
 __global__ void k_marker_update(const double* __restrict__ Xn, const double* __restrict__ Ub1,
@@ -223,7 +223,7 @@ __global__ void k_marker_update(const double* __restrict__ Xn, const double* __r
 void launch_marker_update(const double* Xn, const double* Ub_new, const double* Ub_old, int n, double dt, double* X,
                           cudaStream_t st) {
   if (n <= 0) return;
-  k_marker_update<<<cdiv(3LL * n, 256), 256, 0, st>>>(Xn, Ub_new, Ub_old, 3 * n, dt, X);
+  { k_marker_update<<<cdiv(3LL * n, 256), 256, 0, st>>>(Xn, Ub_new, Ub_old, 3 * n, dt, X); WSI_COUNT(); }
 }
 
 }  // namespace wsi

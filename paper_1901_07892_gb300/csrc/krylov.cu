@@ -56,8 +56,10 @@ void launch_mdot(const double* V, size_t ldv, int m, const double* w, size_t n, 
                  cudaStream_t st) {
   for (int t0 = 0; t0 < m; t0 += NV) {
     int mm = std::min(NV, m - t0);
-    k_mdot<NV><<<RB, RT, 0, st>>>(V + (size_t)t0 * ldv, ldv, mm, w, n, scratch);
-    k_reduce_parts<<<1, 32, 0, st>>>(scratch, RB, NV, mm, out + t0);
+    ktimer_begin(KC_MDOT, st);
+    { k_mdot<NV><<<RB, RT, 0, st>>>(V + (size_t)t0 * ldv, ldv, mm, w, n, scratch); WSI_COUNT(); }
+    ktimer_end(KC_MDOT, st);
+    { k_reduce_parts<<<1, 32, 0, st>>>(scratch, RB, NV, mm, out + t0); WSI_COUNT(); }
   }
 }
 
@@ -78,7 +80,9 @@ void launch_maxpy(const double* V, size_t ldv, int m, const double* h, double* w
                   cudaStream_t st) {
   for (int t0 = 0; t0 < m; t0 += 64) {
     int mm = std::min(64, m - t0);
-    k_maxpy<<<RB, RT, 0, st>>>(V + (size_t)t0 * ldv, ldv, mm, h + t0, w, n, sign);
+    ktimer_begin(KC_MAXPY, st);
+    { k_maxpy<<<RB, RT, 0, st>>>(V + (size_t)t0 * ldv, ldv, mm, h + t0, w, n, sign); WSI_COUNT(); }
+    ktimer_end(KC_MAXPY, st);
   }
 }
 
@@ -89,7 +93,7 @@ __global__ void k_scale(double* x, size_t n, const double* __restrict__ s, bool 
 }
 
 void launch_scale(double* x, size_t n, const double* s_dev, bool inverse, cudaStream_t st) {
-  k_scale<<<RB, RT, 0, st>>>(x, n, s_dev, inverse);
+  { k_scale<<<RB, RT, 0, st>>>(x, n, s_dev, inverse); WSI_COUNT(); }
 }
 
 template <typename Ts, typename Td>
@@ -100,7 +104,7 @@ __global__ void k_cast(const Ts* __restrict__ a, Td* b, size_t n) {
 
 template <typename Ts, typename Td>
 void launch_cast(const Ts* in, Td* out, size_t n, cudaStream_t st) {
-  k_cast<Ts, Td><<<RB, RT, 0, st>>>(in, out, n);
+  { k_cast<Ts, Td><<<RB, RT, 0, st>>>(in, out, n); WSI_COUNT(); }
 }
 
 template <typename T>
@@ -122,14 +126,14 @@ __global__ void k_sum(const T* __restrict__ x, size_t n, double* part) {
 
 template <typename T>
 void launch_sum(const T* x, size_t n, double* out_dev, double* scratch, cudaStream_t st) {
-  k_sum<T><<<RB, RT, 0, st>>>(x, n, scratch);
-  k_reduce_parts<<<1, 32, 0, st>>>(scratch, RB, 1, 1, out_dev);
+  { k_sum<T><<<RB, RT, 0, st>>>(x, n, scratch); WSI_COUNT(); }
+  { k_reduce_parts<<<1, 32, 0, st>>>(scratch, RB, 1, 1, out_dev); WSI_COUNT(); }
 }
 
 double host_norm2(const double* x, size_t n, double* scratch, cudaStream_t st) {
   // scratch: RB + 1 doubles on the device
-  k_mdot<1><<<RB, RT, 0, st>>>(x, 0, 1, x, n, scratch);
-  k_reduce_parts<<<1, 32, 0, st>>>(scratch, RB, 1, 1, scratch + RB);
+  { k_mdot<1><<<RB, RT, 0, st>>>(x, 0, 1, x, n, scratch); WSI_COUNT(); }
+  { k_reduce_parts<<<1, 32, 0, st>>>(scratch, RB, 1, 1, scratch + RB); WSI_COUNT(); }
   double h = 0.0;
   cudaMemcpyAsync(&h, scratch + RB, sizeof(double), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
@@ -145,7 +149,7 @@ __global__ void k_add_scalar(T* x, size_t n, const double* __restrict__ s, doubl
 
 template <typename T>
 void launch_add_scalar_from(T* x, size_t n, const double* s_dev, double factor, cudaStream_t st) {
-  k_add_scalar<T><<<RB, RT, 0, st>>>(x, n, s_dev, factor);
+  { k_add_scalar<T><<<RB, RT, 0, st>>>(x, n, s_dev, factor); WSI_COUNT(); }
 }
 
 template void launch_cast<double, float>(const double*, float*, size_t, cudaStream_t);

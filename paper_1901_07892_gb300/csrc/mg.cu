@@ -128,7 +128,7 @@ __global__ void k_cast_arr(const Ts* __restrict__ a, Td* b, size_t n) {
 template <typename Ts, typename Td>
 static void cast_arr(const Ts* a, Td* b, size_t n, cudaStream_t st) {
   int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
-  k_cast_arr<Ts, Td><<<std::max(blocks, 1), 256, 0, st>>>(a, b, n);
+  { k_cast_arr<Ts, Td><<<std::max(blocks, 1), 256, 0, st>>>(a, b, n); WSI_COUNT(); }
 }
 
 // Gauss-Jordan inverse (host, float64) of an SPD matrix, no pivoting needed
@@ -168,12 +168,12 @@ int precond_setup(Precond<T>& P, const GridDev& g, const Coef<double>& fine, cud
     MGLevel<T>& F = P.lev[l];
     MGLevel<T>& Cl = P.lev[l + 1];
     const GridDev& gc = Cl.g;
-    k_coarsen_beta<0, T><<<grid3(gc.n[0] + 1, gc.n[1], gc.n[2]), dim3(BX, BY), 0, st>>>(F.g, gc, F.r[0], F.r[1],
-                                                                                        F.r[2], F.beta[0], Cl.beta[0]);
-    k_coarsen_beta<1, T><<<grid3(gc.n[0], gc.n[1] + 1, gc.n[2]), dim3(BX, BY), 0, st>>>(F.g, gc, F.r[0], F.r[1],
-                                                                                        F.r[2], F.beta[1], Cl.beta[1]);
-    k_coarsen_beta<2, T><<<grid3(gc.n[0], gc.n[1], gc.n[2] + 1), dim3(BX, BY), 0, st>>>(F.g, gc, F.r[0], F.r[1],
-                                                                                        F.r[2], F.beta[2], Cl.beta[2]);
+    { k_coarsen_beta<0, T><<<grid3(gc.n[0] + 1, gc.n[1], gc.n[2]), dim3(BX, BY), 0, st>>>(F.g, gc, F.r[0], F.r[1],
+                                                                                        F.r[2], F.beta[0], Cl.beta[0]); WSI_COUNT(); }
+    { k_coarsen_beta<1, T><<<grid3(gc.n[0], gc.n[1] + 1, gc.n[2]), dim3(BX, BY), 0, st>>>(F.g, gc, F.r[0], F.r[1],
+                                                                                        F.r[2], F.beta[1], Cl.beta[1]); WSI_COUNT(); }
+    { k_coarsen_beta<2, T><<<grid3(gc.n[0], gc.n[1], gc.n[2] + 1), dim3(BX, BY), 0, st>>>(F.g, gc, F.r[0], F.r[1],
+                                                                                        F.r[2], F.beta[2], Cl.beta[2]); WSI_COUNT(); }
   }
   // dense coarsest operator: M = -L + c 1 1^T (SPD), inverted in float64
   const MGLevel<T>& Lc = P.lev.back();
@@ -344,21 +344,33 @@ static void vcycle(Precond<T>& P, const Opts& o, size_t l, cudaStream_t st) {
   const GridDev& g = L.g;
   dim3 gr = grid3(g.n[0], g.n[1], g.n[2]);
   if (l + 1 == P.lev.size()) {
-    k_coarse_solve<T><<<1, 256, P.ncoarse * sizeof(double), st>>>(P.ncoarse, P.coarse_inv, L.b, L.x);
+    { k_coarse_solve<T><<<1, 256, P.ncoarse * sizeof(double), st>>>(P.ncoarse, P.coarse_inv, L.b, L.x); WSI_COUNT(); }
     return;
   }
   for (int s = 0; s < o.mg_pre; ++s)
-    for (int c = 0; c < 2; ++c) k_rbgs_p<T><<<gr, dim3(BX, BY), 0, st>>>(g, L.beta[0], L.beta[1], L.beta[2], L.x, L.b, c);
+    for (int c = 0; c < 2; ++c) {
+      ktimer_begin(KC_RBGS_P, st);
+      { k_rbgs_p<T><<<gr, dim3(BX, BY), 0, st>>>(g, L.beta[0], L.beta[1], L.beta[2], L.x, L.b, c); WSI_COUNT(); }
+      ktimer_end(KC_RBGS_P, st);
+    }
   MGLevel<T>& Cl = P.lev[l + 1];
   const GridDev& gc = Cl.g;
-  k_restrict_res<T><<<grid3(gc.n[0], gc.n[1], gc.n[2]), dim3(BX, BY), 0, st>>>(
-      g, gc, L.r[0], L.r[1], L.r[2], L.beta[0], L.beta[1], L.beta[2], L.x, L.b, Cl.b);
+  ktimer_begin(KC_RESTRICT, st);
+  { k_restrict_res<T><<<grid3(gc.n[0], gc.n[1], gc.n[2]), dim3(BX, BY), 0, st>>>(
+      g, gc, L.r[0], L.r[1], L.r[2], L.beta[0], L.beta[1], L.beta[2], L.x, L.b, Cl.b); WSI_COUNT(); }
+  ktimer_end(KC_RESTRICT, st);
   cudaMemsetAsync(Cl.x, 0, fsize(gc, 3) * sizeof(T), st);
   vcycle(P, o, l + 1, st);
-  k_prolong_add<T><<<gr, dim3(BX, BY), 0, st>>>(g, gc, L.r[0], L.r[1], L.r[2], Cl.x, L.x);
+  ktimer_begin(KC_PROLONG, st);
+  { k_prolong_add<T><<<gr, dim3(BX, BY), 0, st>>>(g, gc, L.r[0], L.r[1], L.r[2], Cl.x, L.x); WSI_COUNT(); }
+  ktimer_end(KC_PROLONG, st);
   for (int s = 0; s < o.mg_post; ++s)
     for (int c = 1; c >= 0; --c)
-      k_rbgs_p<T><<<gr, dim3(BX, BY), 0, st>>>(g, L.beta[0], L.beta[1], L.beta[2], L.x, L.b, c);
+    {
+      ktimer_begin(KC_RBGS_P, st);
+      { k_rbgs_p<T><<<gr, dim3(BX, BY), 0, st>>>(g, L.beta[0], L.beta[1], L.beta[2], L.x, L.b, c); WSI_COUNT(); }
+      ktimer_end(KC_RBGS_P, st);
+    }
 }
 
 // ------------------------------------------------------------ PC glue kernels
@@ -413,7 +425,7 @@ template <typename T>
 static void sub_mean(T* x, size_t n, double* dsum, double* scratch, cudaStream_t st) {
   launch_sum<T>(x, n, dsum, scratch, st);
   int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
-  k_sub_mean<T><<<std::max(blocks, 1), 256, 0, st>>>(x, n, dsum);
+  { k_sub_mean<T><<<std::max(blocks, 1), 256, 0, st>>>(x, n, dsum); WSI_COUNT(); }
 }
 
 template <typename T>
@@ -438,7 +450,7 @@ void precond_apply(Precond<T>& P, const GridDev& g, const Opts& o, double dt, co
     for (int c = 0; c < 2; ++c) launch_viscous_rbgs<T>(g, cf, inv_dt, theta, P.ut, P.ru, c, st);
   // y = r_p + D u~, mean-free
   dim3 gr = grid3(g.n[0], g.n[1], g.n[2]);
-  k_div_add<T><<<gr, dim3(BX, BY), 0, st>>>(g, P.ut[0], P.ut[1], P.ut[2], P.rp, P.y);
+  { k_div_add<T><<<gr, dim3(BX, BY), 0, st>>>(g, P.ut[0], P.ut[1], P.ut[2], P.rp, P.y); WSI_COUNT(); }
   size_t ncell = fsize(g, 3);
   sub_mean<T>(P.y, ncell, P.dsum, P.dscratch, st);
   // phi = L^{-1} y
@@ -447,14 +459,14 @@ void precond_apply(Precond<T>& P, const GridDev& g, const Opts& o, double dt, co
   cudaMemsetAsync(L0.x, 0, ncell * sizeof(T), st);
   for (int c = 0; c < o.mg_cycles; ++c) vcycle(P, o, 0, st);
   // velocity and pressure updates
-  k_vel_update<0, T><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, P.ut[0], L0.beta[0], L0.x,
-                                                                                 z + pk.off[0]);
-  k_vel_update<1, T><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, P.ut[1], L0.beta[1], L0.x,
-                                                                                 z + pk.off[1]);
-  k_vel_update<2, T><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, P.ut[2], L0.beta[2], L0.x,
-                                                                                 z + pk.off[2]);
+  { k_vel_update<0, T><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, P.ut[0], L0.beta[0], L0.x,
+                                                                                 z + pk.off[0]); WSI_COUNT(); }
+  { k_vel_update<1, T><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, P.ut[1], L0.beta[1], L0.x,
+                                                                                 z + pk.off[1]); WSI_COUNT(); }
+  { k_vel_update<2, T><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, P.ut[2], L0.beta[2], L0.x,
+                                                                                 z + pk.off[2]); WSI_COUNT(); }
   int blocks = (int)std::min<size_t>((ncell + 255) / 256, 152 * 16);
-  k_p_update<T><<<std::max(blocks, 1), 256, 0, st>>>(ncell, L0.x, P.mu_cc, P.y, 1.0 / dt, o.theta, z + pk.off[3]);
+  { k_p_update<T><<<std::max(blocks, 1), 256, 0, st>>>(ncell, L0.x, P.mu_cc, P.y, 1.0 / dt, o.theta, z + pk.off[3]); WSI_COUNT(); }
   sub_mean<double>(z + pk.off[3], ncell, P.dsum, P.dscratch, st);
 }
 

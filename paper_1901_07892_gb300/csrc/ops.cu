@@ -88,34 +88,34 @@ __global__ void k_mat_edges(GridDev g, const double* __restrict__ mu_cc, double*
 void launch_materials(const GridDev& g, const PhaseConst& pc, const double* phi, const double* psi, double* rho_cc,
                       double* mu_cc, double* const rho_face[3], double* const beta[3], double* const rho_flow[3],
                       double* const mu_e[3], cudaStream_t st) {
-  k_mat_cells<<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, rho_cc, mu_cc);
-  k_mat_faces<0><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, rho_face[0], beta[0],
-                                                                             rho_flow[0]);
-  k_mat_faces<1><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, rho_face[1], beta[1],
-                                                                             rho_flow[1]);
-  k_mat_faces<2><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, rho_face[2], beta[2],
-                                                                             rho_flow[2]);
-  k_mat_edges<0><<<grid3(g.n[0] + 1, g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[0]);
-  k_mat_edges<1><<<grid3(g.n[0] + 1, g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[1]);
-  k_mat_edges<2><<<grid3(g.n[0], g.n[1] + 1, g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[2]);
+  { k_mat_cells<<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, rho_cc, mu_cc); WSI_COUNT(); }
+  { k_mat_faces<0><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, rho_face[0], beta[0],
+                                                                             rho_flow[0]); WSI_COUNT(); }
+  { k_mat_faces<1><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, rho_face[1], beta[1],
+                                                                             rho_flow[1]); WSI_COUNT(); }
+  { k_mat_faces<2><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, rho_face[2], beta[2],
+                                                                             rho_flow[2]); WSI_COUNT(); }
+  { k_mat_edges<0><<<grid3(g.n[0] + 1, g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[0]); WSI_COUNT(); }
+  { k_mat_edges<1><<<grid3(g.n[0] + 1, g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[1]); WSI_COUNT(); }
+  { k_mat_edges<2><<<grid3(g.n[0], g.n[1] + 1, g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[2]); WSI_COUNT(); }
 }
 
 void launch_mu_only(const GridDev& g, const PhaseConst& pc, const double* phi, const double* psi, double* mu_cc,
                     double* const mu_e[3], cudaStream_t st) {
-  k_mat_cells<<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, nullptr, mu_cc);
-  k_mat_edges<0><<<grid3(g.n[0] + 1, g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[0]);
-  k_mat_edges<1><<<grid3(g.n[0] + 1, g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[1]);
-  k_mat_edges<2><<<grid3(g.n[0], g.n[1] + 1, g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[2]);
+  { k_mat_cells<<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, nullptr, mu_cc); WSI_COUNT(); }
+  { k_mat_edges<0><<<grid3(g.n[0] + 1, g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[0]); WSI_COUNT(); }
+  { k_mat_edges<1><<<grid3(g.n[0] + 1, g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[1]); WSI_COUNT(); }
+  { k_mat_edges<2><<<grid3(g.n[0], g.n[1] + 1, g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[2]); WSI_COUNT(); }
 }
 
 void launch_rho_flow(const GridDev& g, const PhaseConst& pc, const double* phi, double* const rho_flow[3],
                      cudaStream_t st) {
-  k_mat_faces<0><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, nullptr, nullptr, nullptr,
-                                                                             rho_flow[0]);
-  k_mat_faces<1><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, nullptr, nullptr, nullptr,
-                                                                             rho_flow[1]);
-  k_mat_faces<2><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, pc, phi, nullptr, nullptr, nullptr,
-                                                                             rho_flow[2]);
+  { k_mat_faces<0><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, nullptr, nullptr, nullptr,
+                                                                             rho_flow[0]); WSI_COUNT(); }
+  { k_mat_faces<1><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, nullptr, nullptr, nullptr,
+                                                                             rho_flow[1]); WSI_COUNT(); }
+  { k_mat_faces<2><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, pc, phi, nullptr, nullptr, nullptr,
+                                                                             rho_flow[2]); WSI_COUNT(); }
 }
 
 // =========================================================== strain-rate operator
@@ -214,24 +214,24 @@ template <typename T>
 void launch_viscous(const GridDev& g, const Coef<T>& cf, T inv_dt, T theta, const T* const q[3], T* const out[3],
                     cudaStream_t st, bool strain_only) {
   CVel<T> cq{{q[0], q[1], q[2]}};
-  k_viscous<0, T><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, cq, out[0],
-                                                                              nullptr, strain_only);
-  k_viscous<1, T><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, cq, out[1],
-                                                                              nullptr, strain_only);
-  k_viscous<2, T><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, cq, out[2],
-                                                                              nullptr, strain_only);
+  { k_viscous<0, T><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, cq, out[0],
+                                                                              nullptr, strain_only); WSI_COUNT(); }
+  { k_viscous<1, T><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, cq, out[1],
+                                                                              nullptr, strain_only); WSI_COUNT(); }
+  { k_viscous<2, T><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, cq, out[2],
+                                                                              nullptr, strain_only); WSI_COUNT(); }
 }
 
 template <typename T>
 void launch_viscous_residual(const GridDev& g, const Coef<T>& cf, T inv_dt, T theta, const T* const q[3],
                              const T* const b[3], T* const r[3], cudaStream_t st) {
   CVel<T> cq{{q[0], q[1], q[2]}};
-  k_viscous<0, T><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, cq, r[0], b[0],
-                                                                              false);
-  k_viscous<1, T><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, cq, r[1], b[1],
-                                                                              false);
-  k_viscous<2, T><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, cq, r[2], b[2],
-                                                                              false);
+  { k_viscous<0, T><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, cq, r[0], b[0],
+                                                                              false); WSI_COUNT(); }
+  { k_viscous<1, T><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, cq, r[1], b[1],
+                                                                              false); WSI_COUNT(); }
+  { k_viscous<2, T><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, cq, r[2], b[2],
+                                                                              false); WSI_COUNT(); }
 }
 
 // red-black Gauss-Seidel on component C of the viscous block: the other
@@ -259,13 +259,15 @@ template <typename T>
 void launch_viscous_rbgs(const GridDev& g, const Coef<T>& cf, T inv_dt, T theta, T* const q[3], const T* const b[3],
                          int color, cudaStream_t st) {
   Vel<T> vq{{q[0], q[1], q[2]}};
-  k_viscous_rbgs<0, T><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, vq, b[0],
-                                                                                   color);
-  k_viscous_rbgs<1, T><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, vq, b[1],
-                                                                                   color);
+  ktimer_begin(KC_RBGS_V, st);
+  { k_viscous_rbgs<0, T><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, vq, b[0],
+                                                                                   color); WSI_COUNT(); }
+  { k_viscous_rbgs<1, T><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, vq, b[1],
+                                                                                   color); WSI_COUNT(); }
   if (g.n[2] > 1)
-    k_viscous_rbgs<2, T><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, vq, b[2],
-                                                                                     color);
+    { k_viscous_rbgs<2, T><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, vq, b[2],
+                                                                                     color); WSI_COUNT(); }
+  ktimer_end(KC_RBGS_V, st);
 }
 
 // =========================================================== pressure, grad, div
@@ -290,7 +292,7 @@ __global__ void k_pressure(GridDev g, const T* __restrict__ bx, const T* __restr
 
 template <typename T>
 void launch_pressure(const GridDev& g, const T* const beta[3], const T* p, T* out, cudaStream_t st) {
-  k_pressure<T><<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, beta[0], beta[1], beta[2], p, out);
+  { k_pressure<T><<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, beta[0], beta[1], beta[2], p, out); WSI_COUNT(); }
 }
 
 template <int C, typename T>
@@ -310,9 +312,9 @@ __global__ void k_grad(GridDev g, const T* __restrict__ p, T* out) {
 
 template <typename T>
 void launch_grad(const GridDev& g, const T* p, T* const out[3], cudaStream_t st) {
-  k_grad<0, T><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, p, out[0]);
-  k_grad<1, T><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, p, out[1]);
-  k_grad<2, T><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, p, out[2]);
+  { k_grad<0, T><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, p, out[0]); WSI_COUNT(); }
+  { k_grad<1, T><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, p, out[1]); WSI_COUNT(); }
+  { k_grad<2, T><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, p, out[2]); WSI_COUNT(); }
 }
 
 template <typename T>
@@ -328,15 +330,14 @@ __global__ void k_div(GridDev g, const T* __restrict__ u, const T* __restrict__ 
 
 template <typename T>
 void launch_div(const GridDev& g, const T* const q[3], T* out, T scale, cudaStream_t st) {
-  k_div<T><<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, q[0], q[1], q[2], out, scale);
+  { k_div<T><<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, q[0], q[1], q[2], out, scale); WSI_COUNT(); }
 }
 
-// packed Stokes matvec: momentum rows A u + G p, continuity rows -D u
+// packed Stokes matvec: momentum rows A u + G p (zero on wall faces)
 template <int C>
-__global__ void k_stokes_mom(GridDev g, Coef<double> cf, double inv_dt, double theta, CVel<double> q,
-                             const double* __restrict__ p, double* out) {
-  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
-  if (i >= ext(g, C, 0) || j >= ext(g, C, 1)) return;
+__device__ __forceinline__ void stokes_row(const GridDev& g, const Coef<double>& cf, double inv_dt, double theta,
+                                           const CVel<double>& q, const double* __restrict__ p, double* out, int i,
+                                           int j, int k) {
   int id3[3] = {i, j, k};
   size_t id = fidx(g, C, i, j, k);
   if (id3[C] == 0 || id3[C] == g.n[C]) {
@@ -350,19 +351,40 @@ __global__ void k_stokes_mom(GridDev g, Coef<double> cf, double inv_dt, double t
   out[id] = cf.rho_face[C][id] * inv_dt * q.q[C][id] - theta * L + gp;
 }
 
+// One launch covers the whole packed vector: blockIdx.z walks the z-planes of
+// the u, v and w momentum rows, then the continuity rows.
+__global__ void k_stokes(GridDev g, Coef<double> cf, double inv_dt, double theta, CVel<double> q,
+                         const double* __restrict__ p, double* yu, double* yv, double* yw, double* yp) {
+  int z = blockIdx.z;
+  int nz = g.n[2];
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+  if (z < nz) {
+    if (i < g.n[0] + 1 && j < g.n[1]) stokes_row<0>(g, cf, inv_dt, theta, q, p, yu, i, j, z);
+  } else if (z < 2 * nz) {
+    if (i < g.n[0] && j < g.n[1] + 1) stokes_row<1>(g, cf, inv_dt, theta, q, p, yv, i, j, z - nz);
+  } else if (z < 3 * nz + 1) {
+    if (i < g.n[0] && j < g.n[1]) stokes_row<2>(g, cf, inv_dt, theta, q, p, yw, i, j, z - 2 * nz);
+  } else {
+    int k = z - (3 * nz + 1);
+    if (i < g.n[0] && j < g.n[1]) {
+      double d = (q.q[0][fidx(g, 0, i + 1, j, k)] - q.q[0][fidx(g, 0, i, j, k)]) / g.h[0] +
+                 (q.q[1][fidx(g, 1, i, j + 1, k)] - q.q[1][fidx(g, 1, i, j, k)]) / g.h[1] +
+                 (q.q[2][fidx(g, 2, i, j, k + 1)] - q.q[2][fidx(g, 2, i, j, k)]) / g.h[2];
+      yp[fidx(g, 3, i, j, k)] = -d;
+    }
+  }
+}
+
 void launch_stokes(const GridDev& g, const Coef<double>& cf, double inv_dt, double theta, const double* x, double* y,
                    cudaStream_t st) {
   Packing pk = packing(g);
   CVel<double> q{{x + pk.off[0], x + pk.off[1], x + pk.off[2]}};
   const double* p = x + pk.off[3];
-  k_stokes_mom<0><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, q, p,
-                                                                              y + pk.off[0]);
-  k_stokes_mom<1><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, q, p,
-                                                                              y + pk.off[1]);
-  k_stokes_mom<2><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, q, p,
-                                                                              y + pk.off[2]);
-  k_div<double><<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, q.q[0], q.q[1], q.q[2], y + pk.off[3],
-                                                                        -1.0);
+  dim3 grid(cdiv(g.n[0] + 1, BX), cdiv(g.n[1] + 1, BY), 4 * g.n[2] + 1);
+  ktimer_begin(KC_STOKES, st);
+  { k_stokes<<<grid, dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, q, p, y + pk.off[0], y + pk.off[1],
+                                            y + pk.off[2], y + pk.off[3]); WSI_COUNT(); }
+  ktimer_end(KC_STOKES, st);
 }
 
 template <int C>
@@ -380,9 +402,9 @@ __global__ void k_zero_walls(GridDev g, double* q) {
 }
 
 void launch_zero_walls(const GridDev& g, double* const q[3], cudaStream_t st) {
-  k_zero_walls<0><<<dim3(cdiv(g.n[1], BX), cdiv(g.n[2], BY), 2), dim3(BX, BY), 0, st>>>(g, q[0]);
-  k_zero_walls<1><<<dim3(cdiv(g.n[0], BX), cdiv(g.n[2], BY), 2), dim3(BX, BY), 0, st>>>(g, q[1]);
-  k_zero_walls<2><<<dim3(cdiv(g.n[0], BX), cdiv(g.n[1], BY), 2), dim3(BX, BY), 0, st>>>(g, q[2]);
+  { k_zero_walls<0><<<dim3(cdiv(g.n[1], BX), cdiv(g.n[2], BY), 2), dim3(BX, BY), 0, st>>>(g, q[0]); WSI_COUNT(); }
+  { k_zero_walls<1><<<dim3(cdiv(g.n[0], BX), cdiv(g.n[2], BY), 2), dim3(BX, BY), 0, st>>>(g, q[1]); WSI_COUNT(); }
+  { k_zero_walls<2><<<dim3(cdiv(g.n[0], BX), cdiv(g.n[1], BY), 2), dim3(BX, BY), 0, st>>>(g, q[2]); WSI_COUNT(); }
 }
 
 // =========================================================== transport
@@ -513,9 +535,11 @@ __global__ void k_transport(GridDev g, CVel<double> vel, const double* __restric
 void launch_transport_flux(const GridDev& g, const double* const vel[3], const double* const rho[3],
                            bool with_velocity, double* const out[3], cudaStream_t st) {
   CVel<double> v{{vel[0], vel[1], vel[2]}};
-  k_transport<0><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, v, rho[0], with_velocity, out[0]);
-  k_transport<1><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, v, rho[1], with_velocity, out[1]);
-  k_transport<2><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, v, rho[2], with_velocity, out[2]);
+  ktimer_begin(KC_TRANSPORT, st);
+  { k_transport<0><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, v, rho[0], with_velocity, out[0]); WSI_COUNT(); }
+  { k_transport<1><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, v, rho[1], with_velocity, out[1]); WSI_COUNT(); }
+  { k_transport<2><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, v, rho[2], with_velocity, out[2]); WSI_COUNT(); }
+  ktimer_end(KC_TRANSPORT, st);
 }
 
 __global__ void k_lincomb(size_t n, double a, const double* __restrict__ x, double b, const double* __restrict__ y,
@@ -534,7 +558,7 @@ void launch_lincomb(size_t n, double a, const double* x, double b, const double*
                     double* out, cudaStream_t st) {
   int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
   if (blocks < 1) blocks = 1;
-  k_lincomb<<<blocks, 256, 0, st>>>(n, a, x, b, y, c, z, out);
+  { k_lincomb<<<blocks, 256, 0, st>>>(n, a, x, b, y, c, z, out); WSI_COUNT(); }
 }
 
 // =========================================================== level set
@@ -580,7 +604,7 @@ __global__ void k_ls_advect(GridDev g, CVel<double> vel, const double* __restric
 void launch_levelset_advect(const GridDev& g, const double* const vel[3], const double* phi_n,
                             const double* phi_half, double dt, double* out, cudaStream_t st) {
   CVel<double> v{{vel[0], vel[1], vel[2]}};
-  k_ls_advect<<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, v, phi_n, phi_half, dt, out);
+  { k_ls_advect<<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, v, phi_n, phi_half, dt, out); WSI_COUNT(); }
 }
 
 __global__ void k_box_sdf(GridDev g, const double* __restrict__ xc, double hx_, double hy_, double hz_, double* psi) {
@@ -595,7 +619,7 @@ __global__ void k_box_sdf(GridDev g, const double* __restrict__ xc, double hx_, 
 }
 
 void launch_box_sdf(const GridDev& g, const double* xcom_dev, const double half[3], double* psi, cudaStream_t st) {
-  k_box_sdf<<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, xcom_dev, half[0], half[1], half[2], psi);
+  { k_box_sdf<<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, xcom_dev, half[0], half[1], half[2], psi); WSI_COUNT(); }
 }
 
 // =========================================================== momentum RHS
@@ -619,12 +643,12 @@ void launch_momentum_rhs(const GridDev& g, const Coef<double>& cf_n, const doubl
                          const double* const u_n[3], const double* const C[3], const double* const rho_g[3],
                          const double grav[3], double inv_dt, double theta, double* const b[3], cudaStream_t st) {
   CVel<double> u{{u_n[0], u_n[1], u_n[2]}};
-  k_mom_rhs<0><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, cf_n, rho_n[0], u, C[0], rho_g[0],
-                                                                          grav[0], inv_dt, theta, b[0]);
-  k_mom_rhs<1><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, cf_n, rho_n[1], u, C[1], rho_g[1],
-                                                                          grav[1], inv_dt, theta, b[1]);
-  k_mom_rhs<2><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, cf_n, rho_n[2], u, C[2], rho_g[2],
-                                                                          grav[2], inv_dt, theta, b[2]);
+  { k_mom_rhs<0><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, cf_n, rho_n[0], u, C[0], rho_g[0],
+                                                                          grav[0], inv_dt, theta, b[0]); WSI_COUNT(); }
+  { k_mom_rhs<1><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, cf_n, rho_n[1], u, C[1], rho_g[1],
+                                                                          grav[1], inv_dt, theta, b[1]); WSI_COUNT(); }
+  { k_mom_rhs<2><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, cf_n, rho_n[2], u, C[2], rho_g[2],
+                                                                          grav[2], inv_dt, theta, b[2]); WSI_COUNT(); }
 }
 
 // explicit instantiations

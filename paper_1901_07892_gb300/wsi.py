@@ -18,14 +18,15 @@ _lib = None
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_NOT_CONVERGED, ERR_NAN, ERR_OOM, ERR_DEVICE = range(7)
 PREC_FP64, PREC_MIXED = 0, 1
 GRAVITY_FLOW, GRAVITY_FULL = 0, 1
-F_VEL, F_P, F_PHI, F_PSI, F_MARKERS = range(5)
+F_VEL, F_P, F_PHI, F_PSI, F_MARKERS, F_VEL_OLD = range(6)
 C_RHO_CC, C_MU_CC, C_RHO_FACE, C_RHO_FLOW_FACE, C_MU_EDGE = range(5)
 OP_STOKES, OP_VISCOUS, OP_STRAIN, OP_PRESSURE, OP_GRAD, OP_DIV = range(6)
 
 EXPORTED = ["wsi_stokes_size", "wsi_velocity_size", "wsi_create_grid", "wsi_destroy", "wsi_last_error",
             "wsi_set_phases", "wsi_stokes_solve", "wsi_dlm_constrain", "wsi_step", "wsi_get_field",
             "wsi_set_field", "wsi_get_coeff", "wsi_apply", "wsi_transport", "wsi_advect_levelset",
-            "wsi_interp", "wsi_spread"]
+            "wsi_interp", "wsi_spread", "wsi_launch_count", "wsi_ktimer_enable", "wsi_ktimer_read"]
+KC_STOKES, KC_RBGS_P, KC_RBGS_V, KC_TRANSPORT, KC_MDOT, KC_MAXPY, KC_RESTRICT, KC_PROLONG = range(8)
 
 
 class GridDesc(ctypes.Structure):
@@ -106,8 +107,13 @@ def lib():
     L.wsi_advect_levelset.argtypes = [vp, vp, vp, vp, dp, vp]
     L.wsi_interp.argtypes = [vp, vp, vp, ip, vp]
     L.wsi_spread.argtypes = [vp, vp, vp, ip, dp, vp]
+    L.wsi_launch_count.argtypes = []
+    L.wsi_launch_count.restype = ctypes.c_longlong
+    L.wsi_ktimer_enable.argtypes = [ip]
+    L.wsi_ktimer_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
     for name in EXPORTED:
-        if name not in ("wsi_destroy", "wsi_last_error", "wsi_stokes_size", "wsi_velocity_size"):
+        if name not in ("wsi_destroy", "wsi_last_error", "wsi_stokes_size", "wsi_velocity_size",
+                        "wsi_launch_count"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -260,7 +266,7 @@ class Context:
         return s
 
     def get_field(self, which, like=None):
-        n = {F_VEL: self.nvel, F_P: self.ncell, F_PHI: self.ncell, F_PSI: self.ncell,
+        n = {F_VEL: self.nvel, F_VEL_OLD: self.nvel, F_P: self.ncell, F_PHI: self.ncell, F_PSI: self.ncell,
              F_MARKERS: 3 * self.n_markers}[which]
         out = np.empty(n) if like is None else _empty_like_kind(like, n)
         self._check(self.L.wsi_get_field(self._h, which, _ptr(out)))
@@ -297,3 +303,22 @@ class Context:
         out = _empty_like_kind(F, self.nvel)
         self._check(self.L.wsi_spread(self._h, _ptr(F), _ptr(X), n, dV, _ptr(out)))
         return out
+
+
+def launch_count():
+    return int(lib().wsi_launch_count())
+
+
+def ktimer_enable(kernel_class):
+    rc = lib().wsi_ktimer_enable(kernel_class)
+    if rc != OK:
+        raise WsiError(rc, "wsi_ktimer_enable")
+
+
+def ktimer_read():
+    t = ctypes.c_double()
+    n = ctypes.c_longlong()
+    rc = lib().wsi_ktimer_read(ctypes.byref(t), ctypes.byref(n))
+    if rc != OK:
+        raise WsiError(rc, "wsi_ktimer_read")
+    return t.value, n.value

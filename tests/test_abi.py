@@ -28,7 +28,7 @@ def test_library_exports_every_declared_symbol():
     L = wsi.lib()
     for n in _declared():
         assert hasattr(L, n), n
-    assert set(_declared()) <= set(wsi.EXPORTED) | {"wsi_stokes_size", "wsi_velocity_size"}
+    assert set(_declared()) <= set(wsi.EXPORTED)
 
 
 def test_invalid_arguments_rejected_without_gpu_work():

@@ -122,7 +122,7 @@ def test_operator_parity(shape):
     assert _rel(ctx.apply(wsi.OP_DIV, vflat, dt), ops.div(g, *vel).ravel()) < OP_TOL
 
 
-def _solve_parity(c, precision, rtol=1e-10, rhs_seed=3):
+def _solve_parity(c, precision, rtol=1e-10, rhs_seed=3, gravity=False):
     g = _grid(c)
     ctx = _ctx(c, precision=precision, restart=30)
     m = _oracle_mat(c, g)
@@ -131,12 +131,15 @@ def _solve_parity(c, precision, rtol=1e-10, rhs_seed=3):
         bu = [c.extra["rhs_u"][d] * g.interior_face_mask(d) for d in range(3)]
     else:
         bu = [rng.uniform(-1, 1, g.face_shape(d)) * 1e-2 * g.interior_face_mask(d) for d in range(3)]
-    # gravity on top (rho^flow g), as in a tank step
-    from oracle.materials import face_average, flow_only
-    for d in range(3):
-        if c.gravity[d] != 0.0:
-            bu[d] = bu[d] + flow_only(face_average(g, c.phi, d), c.rho_l, c.rho_g, m.eps) * c.gravity[d] * \
-                g.interior_face_mask(d)
+    if gravity:
+        # rho^flow g on top, as in a tank step: the pressure gradient then
+        # carries almost all of b, and the velocity is a 1e-4 remainder, so
+        # the solve must go far below 1e-8 for 1e-6 field agreement
+        from oracle.materials import face_average, flow_only
+        for d in range(3):
+            if c.gravity[d] != 0.0:
+                bu[d] = bu[d] + flow_only(face_average(g, c.phi, d), c.rho_l, c.rho_g, m.eps) * c.gravity[d] * \
+                    g.interior_face_mask(d)
     b = g.pack(bu[0], bu[1], bu[2], np.zeros(g.cell_shape))
     x, st = ctx.solve(torch.from_numpy(b).cuda(), c.dt, rtol=rtol, max_iters=400)
     assert st.rel_residual <= rtol * 1.01, st.rel_residual
@@ -157,8 +160,17 @@ def test_solve_parity_config1_2d(precision):
 
 @pytest.mark.parametrize("precision", [wsi.PREC_FP64, wsi.PREC_MIXED])
 def test_solve_parity_3d_ragged(precision):
-    c = inputs.tank3d(nxyz=(24, 20, 16), seed=5, dt=5e-4)
+    """40 x 20 x 4 spans two 32-wide x tiles and three 8-high y tiles, both
+    with ragged tails; wavy surface and a box solid."""
+    c = inputs.tank3d(nxyz=(40, 20, 4), seed=5, dt=5e-4)
     errs, st = _solve_parity(c, precision)
+    assert max(errs) < FIELD_TOL, errs
+
+
+@pytest.mark.parametrize("precision", [wsi.PREC_FP64, wsi.PREC_MIXED])
+def test_solve_parity_gravity_dominated(precision):
+    c = inputs.tank3d(nxyz=(40, 20, 4), seed=6, dt=5e-4)
+    errs, st = _solve_parity(c, precision, rtol=1e-13, gravity=True)
     assert max(errs) < FIELD_TOL, errs
 
 
@@ -241,7 +253,7 @@ def test_step_parity_small_tank(precision):
     box, from rest: the velocity, pressure and level set agree with the
     oracle's step (which solves exactly)."""
     from oracle import step as ost
-    c = inputs.tank3d(nxyz=(16, 12, 12), seed=11, dt=5e-4)
+    c = inputs.tank3d(nxyz=(20, 16, 8), seed=11, dt=5e-4)
     c.rho_s = c.rho_l
     g = _grid(c)
     ctx = wsi.Context.from_case(c, precision=precision, restart=30)
@@ -251,7 +263,9 @@ def test_step_parity_small_tank(precision):
     body = ost.Body(c.markers, c.dV, [True] * 6, half=c.box_half)
     s = ost.State(g, pr, c.phi, c.psi, body)
     for _ in range(2):
-        ctx.step(c.dt, rtol=1e-11, max_iters=400)
+        # gravity-dominated right-hand side: solve far below 1e-8 (see
+        # test_solve_parity_gravity_dominated)
+        ctx.step(c.dt, rtol=1e-13, max_iters=600)
         ost.step(s, c.dt)
     vel = ctx.get_field(wsi.F_VEL)
     ref = np.concatenate([a.ravel() for a in s.vel])
