@@ -440,6 +440,7 @@ int wsi_create_grid(const wsi_grid_desc* d, void* stream, wsi_ctx** out) {
   c->g.h[1] = d->ly / d->ny;
   c->g.h[2] = d->lz / d->nz;
   for (int i = 0; i < 6; ++i) c->g.bc[i] = d->bc[i];
+  grid_finalize(c->g);
   c->pk = packing(c->g);
   c->nvel = c->pk.off[3];
   c->nstk = c->pk.off[4];

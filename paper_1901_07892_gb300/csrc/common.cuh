@@ -37,8 +37,16 @@ void ktimer_end(int id, cudaStream_t st);
 struct GridDev {
   int n[3];       // cells per axis
   double h[3];    // spacing
+  double ih[3];   // 1/h (set by grid_finalize)
+  double ih2[3];  // 1/h^2
   double bc[6];   // tangential ghost sign per wall (x-, x+, y-, y+, z-, z+)
 };
+inline void grid_finalize(GridDev& g) {
+  for (int a = 0; a < 3; ++a) {
+    g.ih[a] = 1.0 / g.h[a];
+    g.ih2[a] = 1.0 / (g.h[a] * g.h[a]);
+  }
+}
 
 __host__ __device__ __forceinline__ int ext(const GridDev& g, int c, int a) {
   return g.n[a] + (a == c ? 1 : 0);

@@ -29,7 +29,7 @@ struct Tap {
 __device__ __forceinline__ void taps_axis(const GridDev& g, int c, int d, double Xd, Tap& t) {
   int n = g.n[d];
   bool normal = (c == d);
-  double xs = normal ? Xd / g.h[d] : Xd / g.h[d] - 0.5;
+  double xs = normal ? Xd * g.ih[d] : Xd * g.ih[d] - 0.5;
   int base = (int)floor(xs) - 1;
   double s_lo = g.bc[2 * d], s_hi = g.bc[2 * d + 1];
 #pragma unroll

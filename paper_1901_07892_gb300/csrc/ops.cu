@@ -126,8 +126,7 @@ template <int C, typename T>
 __device__ __forceinline__ T strain_at(const GridDev& g, const Coef<T>& cf, const T* const* q, int i, int j, int k,
                                        T* diag) {
   const T* qc = q[C];
-  const T hC = (T)g.h[C];
-  const T ihC = T(1) / hC;
+  const T ihC = (T)g.ih[C];
   int id3[3] = {i, j, k};
   T q0 = qc[fidx(g, C, i, j, k)];
   // normal stress: cells hi = face index along C, lo = index - 1
@@ -145,8 +144,7 @@ __device__ __forceinline__ T strain_at(const GridDev& g, const Coef<T>& cf, cons
   for (int D = 0; D < 3; ++D) {
     if (D == C) continue;
     const int E = edge_id(C, D);
-    const T hD = (T)g.h[D];
-    const T ihD = T(1) / hD;
+    const T ihD = (T)g.ih[D];
     const T* qd = q[D];
     // neighbours along D (ghosts beyond walls mirror with the wall sign)
     int a3[3] = {id3[0], id3[1], id3[2]};
@@ -279,7 +277,7 @@ __global__ void k_pressure(GridDev g, const T* __restrict__ bx, const T* __restr
   size_t id = fidx(g, 3, i, j, k);
   T pc = p[id];
   T s = T(0);
-  T ihx2 = T(1) / (T)(g.h[0] * g.h[0]), ihy2 = T(1) / (T)(g.h[1] * g.h[1]), ihz2 = T(1) / (T)(g.h[2] * g.h[2]);
+  T ihx2 = (T)g.ih2[0], ihy2 = (T)g.ih2[1], ihz2 = (T)g.ih2[2];
   if (i + 1 < g.n[0]) s += bx[fidx(g, 0, i + 1, j, k)] * (p[id + 1] - pc) * ihx2;
   if (i > 0) s -= bx[fidx(g, 0, i, j, k)] * (pc - p[id - 1]) * ihx2;
   if (j + 1 < g.n[1]) s += by[fidx(g, 1, i, j + 1, k)] * (p[id + g.n[0]] - pc) * ihy2;
@@ -307,7 +305,7 @@ __global__ void k_grad(GridDev g, const T* __restrict__ p, T* out) {
   }
   int lo3[3] = {i, j, k};
   lo3[C] -= 1;
-  out[id] = (p[fidx(g, 3, i, j, k)] - p[fidx(g, 3, lo3[0], lo3[1], lo3[2])]) / (T)g.h[C];
+  out[id] = (p[fidx(g, 3, i, j, k)] - p[fidx(g, 3, lo3[0], lo3[1], lo3[2])]) * (T)g.ih[C];
 }
 
 template <typename T>
@@ -322,9 +320,9 @@ __global__ void k_div(GridDev g, const T* __restrict__ u, const T* __restrict__ 
                       T scale) {
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (i >= g.n[0] || j >= g.n[1]) return;
-  T d = (u[fidx(g, 0, i + 1, j, k)] - u[fidx(g, 0, i, j, k)]) / (T)g.h[0] +
-        (v[fidx(g, 1, i, j + 1, k)] - v[fidx(g, 1, i, j, k)]) / (T)g.h[1] +
-        (w[fidx(g, 2, i, j, k + 1)] - w[fidx(g, 2, i, j, k)]) / (T)g.h[2];
+  T d = (u[fidx(g, 0, i + 1, j, k)] - u[fidx(g, 0, i, j, k)]) * (T)g.ih[0] +
+        (v[fidx(g, 1, i, j + 1, k)] - v[fidx(g, 1, i, j, k)]) * (T)g.ih[1] +
+        (w[fidx(g, 2, i, j, k + 1)] - w[fidx(g, 2, i, j, k)]) * (T)g.ih[2];
   out[fidx(g, 3, i, j, k)] = scale * d;
 }
 
@@ -347,7 +345,7 @@ __device__ __forceinline__ void stokes_row(const GridDev& g, const Coef<double>&
   double L = strain_at<C, double>(g, cf, q.q, i, j, k, nullptr);
   int lo3[3] = {i, j, k};
   lo3[C] -= 1;
-  double gp = (p[fidx(g, 3, i, j, k)] - p[fidx(g, 3, lo3[0], lo3[1], lo3[2])]) / g.h[C];
+  double gp = (p[fidx(g, 3, i, j, k)] - p[fidx(g, 3, lo3[0], lo3[1], lo3[2])]) * g.ih[C];
   out[id] = cf.rho_face[C][id] * inv_dt * q.q[C][id] - theta * L + gp;
 }
 
@@ -367,9 +365,9 @@ __global__ void k_stokes(GridDev g, Coef<double> cf, double inv_dt, double theta
   } else {
     int k = z - (3 * nz + 1);
     if (i < g.n[0] && j < g.n[1]) {
-      double d = (q.q[0][fidx(g, 0, i + 1, j, k)] - q.q[0][fidx(g, 0, i, j, k)]) / g.h[0] +
-                 (q.q[1][fidx(g, 1, i, j + 1, k)] - q.q[1][fidx(g, 1, i, j, k)]) / g.h[1] +
-                 (q.q[2][fidx(g, 2, i, j, k + 1)] - q.q[2][fidx(g, 2, i, j, k)]) / g.h[2];
+      double d = (q.q[0][fidx(g, 0, i + 1, j, k)] - q.q[0][fidx(g, 0, i, j, k)]) * g.ih[0] +
+                 (q.q[1][fidx(g, 1, i, j + 1, k)] - q.q[1][fidx(g, 1, i, j, k)]) * g.ih[1] +
+                 (q.q[2][fidx(g, 2, i, j, k + 1)] - q.q[2][fidx(g, 2, i, j, k)]) * g.ih[2];
       yp[fidx(g, 3, i, j, k)] = -d;
     }
   }
@@ -410,20 +408,26 @@ void launch_zero_walls(const GridDev& g, double* const q[3], cudaStream_t st) {
 // =========================================================== transport
 // Bounded cubic-upwind interpolation (CUI, kappa = 1/3) in normalized
 // variables; qC upwind point, qU next upwind, qD downwind.
+// Division-free: with num = qC - qU and den = qD - qU, t = num/den lies in a
+// branch interval iff num*sign(den) lies in den-scaled bounds, and
+// qU + t_f den = qU + {3 num, 5 num/6 + den/3, den, num}.  (float64 division
+// costs tens of instructions at GB300's float64 rate.)
 __device__ __forceinline__ double cui(double qU, double qC, double qD) {
   double den = qD - qU;
+  double num = qC - qU;
   if (den == 0.0) return qC;
-  double t = (qC - qU) / den;
-  double tf;
-  if (t > 0.0 && t <= 2.0 / 13.0)
-    tf = 3.0 * t;
-  else if (t > 2.0 / 13.0 && t <= 0.8)
-    tf = 5.0 * t / 6.0 + 1.0 / 3.0;
-  else if (t > 0.8 && t <= 1.0)
-    tf = 1.0;
+  double a = den > 0.0 ? num : -num;  // num * sign(den)
+  double D = fabs(den);               // t = a / D
+  double f;
+  if (a > 0.0 && 13.0 * a <= 2.0 * D)
+    f = 3.0 * num;
+  else if (13.0 * a > 2.0 * D && 5.0 * a <= 4.0 * D)
+    f = num * (5.0 / 6.0) + den * (1.0 / 3.0);
+  else if (5.0 * a > 4.0 * D && a <= D)
+    f = den;
   else
-    tf = t;
-  return qU + tf * den;
+    f = num;
+  return qU + f;
 }
 
 // Value of the C-face array a at index m along axis D (other indices fixed),
@@ -514,7 +518,7 @@ __device__ __forceinline__ double flux_div_dir(const GridDev& g, const double* c
       Fhi *= lim_at<C, D, true>(g, qc, i3, jd, adv_hi);
     }
   }
-  return (Fhi - Flo) / g.h[D];
+  return (Fhi - Flo) * g.ih[D];
 }
 
 template <int C>
@@ -594,9 +598,9 @@ __global__ void k_ls_advect(GridDev g, CVel<double> vel, const double* __restric
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (i >= g.n[0] || j >= g.n[1]) return;
   int i3[3] = {i, j, k};
-  double Q = (ls_flux<0>(g, vel.q[0], phi_h, i3, i + 1) - ls_flux<0>(g, vel.q[0], phi_h, i3, i)) / g.h[0] +
-             (ls_flux<1>(g, vel.q[1], phi_h, i3, j + 1) - ls_flux<1>(g, vel.q[1], phi_h, i3, j)) / g.h[1] +
-             (ls_flux<2>(g, vel.q[2], phi_h, i3, k + 1) - ls_flux<2>(g, vel.q[2], phi_h, i3, k)) / g.h[2];
+  double Q = (ls_flux<0>(g, vel.q[0], phi_h, i3, i + 1) - ls_flux<0>(g, vel.q[0], phi_h, i3, i)) * g.ih[0] +
+             (ls_flux<1>(g, vel.q[1], phi_h, i3, j + 1) - ls_flux<1>(g, vel.q[1], phi_h, i3, j)) * g.ih[1] +
+             (ls_flux<2>(g, vel.q[2], phi_h, i3, k + 1) - ls_flux<2>(g, vel.q[2], phi_h, i3, k)) * g.ih[2];
   size_t id = fidx(g, 3, i, j, k);
   out[id] = phi_n[id] - dt * Q;
 }
