@@ -659,7 +659,7 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
     launch_lincomb(nc, 0.5, c->phi_k, 0.5, c->phi, 0.0, nullptr, c->phi_half, st);
     const double* vh[3];
     vel_parts(c, (const double*)c->vel_half, vh);
-    launch_levelset_advect(g, vh, c->phi, c->phi_half, dt, c->phi_new, st);
+    launch_levelset_advect(g, vh, c->phi, c->phi_half, dt, c->phi_new, c->desc.precision == WSI_PREC_MIXED, st);
     const double* psi_use = c->psi_k;
     if (c->has_body && B.shape == 1) {
       launch_marker_mean(B.X, B.n, B.xc, B.scratch, st);
@@ -686,18 +686,21 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
     vel_parts(c, (const double*)c->u1, cu1);
     vel_parts(c, (const double*)c->u2, cu2);
     const double* crn[3] = {c->rho_n[0], c->rho_n[1], c->rho_n[2]};
-    launch_transport_flux(g, cvn, crn, false, R, st);
-    for (int d = 0; d < 3; ++d) launch_lincomb(fsize(g, d), 1.0, c->rho_n[d], -dt, R[d], 0.0, nullptr, r1[d], st);
+    if (k == 0) {
+      // stage 1 depends on (u^n, rho^n) only: the same in every cycle
+      launch_transport_flux(g, cvn, crn, false, R, c->desc.precision == WSI_PREC_MIXED, st);
+      for (int d = 0; d < 3; ++d) launch_lincomb(fsize(g, d), 1.0, c->rho_n[d], -dt, R[d], 0.0, nullptr, r1[d], st);
+    }
     const double* cr1[3] = {r1[0], r1[1], r1[2]};
-    launch_transport_flux(g, cu1, cr1, false, R, st);
+    launch_transport_flux(g, cu1, cr1, false, R, c->desc.precision == WSI_PREC_MIXED, st);
     for (int d = 0; d < 3; ++d)
       launch_lincomb(fsize(g, d), 0.75, c->rho_n[d], 0.25, r1[d], -0.25 * dt, R[d], r2[d], st);
     const double* cr2[3] = {r2[0], r2[1], r2[2]};
-    launch_transport_flux(g, cu2, cr2, false, R, st);
+    launch_transport_flux(g, cu2, cr2, false, R, c->desc.precision == WSI_PREC_MIXED, st);
     for (int d = 0; d < 3; ++d)
       launch_lincomb(fsize(g, d), 1.0 / 3.0, c->rho_n[d], 2.0 / 3.0, r2[d], -2.0 / 3.0 * dt, R[d], c->rho_face[d],
                      st);
-    launch_transport_flux(g, cu2, cr2, true, Cq, st);
+    launch_transport_flux(g, cu2, cr2, true, Cq, c->desc.precision == WSI_PREC_MIXED, st);
     for (int d = 0; d < 3; ++d) recip(c, c->rho_face[d], c->beta[d], fsize(g, d));
     // right-hand side with mu^n and gravity
     double* bq[3];
@@ -882,17 +885,17 @@ int wsi_transport(wsi_ctx* c, const double* u_n, const double* u_nm1, const doub
   vel_parts(c, (const double*)c->u1, cu1);
   vel_parts(c, (const double*)c->u2, cu2);
   const double* crn[3] = {c->rho_n[0], c->rho_n[1], c->rho_n[2]};
-  launch_transport_flux(g, cun, crn, false, R, st);
+  launch_transport_flux(g, cun, crn, false, R, c->desc.precision == WSI_PREC_MIXED, st);
   for (int d = 0; d < 3; ++d) launch_lincomb(fsize(g, d), 1.0, c->rho_n[d], -dt, R[d], 0.0, nullptr, r1[d], st);
   const double* cr1[3] = {r1[0], r1[1], r1[2]};
-  launch_transport_flux(g, cu1, cr1, false, R, st);
+  launch_transport_flux(g, cu1, cr1, false, R, c->desc.precision == WSI_PREC_MIXED, st);
   for (int d = 0; d < 3; ++d)
     launch_lincomb(fsize(g, d), 0.75, c->rho_n[d], 0.25, r1[d], -0.25 * dt, R[d], r2[d], st);
   const double* cr2[3] = {r2[0], r2[1], r2[2]};
-  launch_transport_flux(g, cu2, cr2, false, R, st);
+  launch_transport_flux(g, cu2, cr2, false, R, c->desc.precision == WSI_PREC_MIXED, st);
   for (int d = 0; d < 3; ++d)
     launch_lincomb(fsize(g, d), 1.0 / 3.0, c->rho_n[d], 2.0 / 3.0, r2[d], -2.0 / 3.0 * dt, R[d], r3[d], st);
-  launch_transport_flux(g, cu2, cr2, true, Cq, st);
+  launch_transport_flux(g, cu2, cr2, true, Cq, c->desc.precision == WSI_PREC_MIXED, st);
   rc = copy_out(c, rho_out, c->b, nv);
   if (!rc) rc = copy_out(c, C_out, c->Cc, nv);
   if (rc) return rc;
@@ -908,7 +911,8 @@ int wsi_advect_levelset(wsi_ctx* c, const double* vel, const double* phi_n, cons
   if (rc) return rc;
   const double* vh[3];
   vel_parts(c, (const double*)c->vel_half, vh);
-  launch_levelset_advect(c->g, vh, c->phi_k, c->phi_half, dt, c->phi_new, c->st);
+  launch_levelset_advect(c->g, vh, c->phi_k, c->phi_half, dt, c->phi_new, c->desc.precision == WSI_PREC_MIXED,
+                         c->st);
   rc = copy_out(c, phi_out, c->phi_new, c->ncell);
   if (rc) return rc;
   return cuda_check(c, "advect_levelset");

@@ -53,15 +53,16 @@ template <typename T>
 void launch_viscous_rbgs(const GridDev& g, const Coef<T>& cf, T inv_dt, T theta, T* const q[3], const T* const b[3],
                          int color, cudaStream_t st);
 
-// transport (Sec. 4.2.2): R or C on all three face arrays
+// transport.cu (Sec. 4.2.2): R or C on all three face arrays; fp32 selects
+// float32 flux arithmetic (float64 storage)
 void launch_transport_flux(const GridDev& g, const double* const vel[3], const double* const rho[3],
-                           bool with_velocity, double* const out[3], cudaStream_t st);
+                           bool with_velocity, double* const out[3], bool fp32, cudaStream_t st);
 // out = a*x + b*y + c*z elementwise over n (any of y, z may be null)
 void launch_lincomb(size_t n, double a, const double* x, double b, const double* y, double c, const double* z,
                     double* out, cudaStream_t st);
 // rk stage: out = a*rho_n + b*rho_s - c*dt*R
 void launch_levelset_advect(const GridDev& g, const double* const vel[3], const double* phi_n,
-                            const double* phi_half, double dt, double* out, cudaStream_t st);
+                            const double* phi_half, double dt, double* out, bool fp32, cudaStream_t st);
 void launch_box_sdf(const GridDev& g, const double* xcom_dev, const double half[3], double* psi, cudaStream_t st);
 // b = rho_n u_n / dt - C + (1-theta) L_mu^n u_n + rho_g g
 void launch_momentum_rhs(const GridDev& g, const Coef<double>& cf_n, const double* const rho_n[3],

@@ -1,6 +1,6 @@
-// Field kernels of libwsi: material coefficients (Sec. 4.1), the staggered
-// operators of the implicit Stokes system (Sec. 3.1, 4.2.2), consistent
-// transport (Sec. 4.2.2) and level-set advection (Sec. 4.2.1).
+// Field kernels of libwsi: material coefficients (Sec. 4.1) and the staggered
+// operators of the implicit Stokes system (Sec. 3.1, 4.2.2); transport and
+// level-set advection live in transport.cu.
 //
 // Every kernel walks its output array in x-fastest order with one thread per
 // entry (blocks of 32 x 8 in x, y; one z-plane per grid row), so warps read
@@ -403,227 +403,6 @@ void launch_zero_walls(const GridDev& g, double* const q[3], cudaStream_t st) {
   { k_zero_walls<0><<<dim3(cdiv(g.n[1], BX), cdiv(g.n[2], BY), 2), dim3(BX, BY), 0, st>>>(g, q[0]); WSI_COUNT(); }
   { k_zero_walls<1><<<dim3(cdiv(g.n[0], BX), cdiv(g.n[2], BY), 2), dim3(BX, BY), 0, st>>>(g, q[1]); WSI_COUNT(); }
   { k_zero_walls<2><<<dim3(cdiv(g.n[0], BX), cdiv(g.n[1], BY), 2), dim3(BX, BY), 0, st>>>(g, q[2]); WSI_COUNT(); }
-}
-
-// =========================================================== transport
-// Bounded cubic-upwind interpolation (CUI, kappa = 1/3) in normalized
-// variables; qC upwind point, qU next upwind, qD downwind.
-// Division-free: with num = qC - qU and den = qD - qU, t = num/den lies in a
-// branch interval iff num*sign(den) lies in den-scaled bounds, and
-// qU + t_f den = qU + {3 num, 5 num/6 + den/3, den, num}.  (float64 division
-// costs tens of instructions at GB300's float64 rate.)
-__device__ __forceinline__ double cui(double qU, double qC, double qD) {
-  double den = qD - qU;
-  double num = qC - qU;
-  if (den == 0.0) return qC;
-  double a = den > 0.0 ? num : -num;  // num * sign(den)
-  double D = fabs(den);               // t = a / D
-  double f;
-  if (a > 0.0 && 13.0 * a <= 2.0 * D)
-    f = 3.0 * num;
-  else if (13.0 * a > 2.0 * D && 5.0 * a <= 4.0 * D)
-    f = num * (5.0 / 6.0) + den * (1.0 / 3.0);
-  else if (5.0 * a > 4.0 * D && a <= D)
-    f = den;
-  else
-    f = num;
-  return qU + f;
-}
-
-// Value of the C-face array a at index m along axis D (other indices fixed),
-// extended by two ghost layers: even mirror (density) or the velocity rule
-// (odd about wall faces along C == D, wall sign across D != C).
-template <int C, int D, bool VEL>
-__device__ __forceinline__ double ext_get(const GridDev& g, const double* __restrict__ a, int i3[3], int m) {
-  int n = g.n[D] + (C == D ? 1 : 0);  // stored extent along D
-  double s = 1.0;
-  int mm = m;
-  if (m < 0) {
-    int gl = -m;
-    if (C == D) {
-      mm = gl;
-      if (VEL) s = -1.0;
-    } else {
-      mm = gl - 1;
-      if (VEL) s = g.bc[2 * D];
-    }
-  } else if (m >= n) {
-    int gl = m - (n - 1);
-    if (C == D) {
-      mm = (n - 1) - gl;
-      if (VEL) s = -1.0;
-    } else {
-      mm = n - gl;
-      if (VEL) s = g.bc[2 * D + 1];
-    }
-  }
-  mm = clampi(mm, 0, n - 1);
-  int c3[3] = {i3[0], i3[1], i3[2]};
-  c3[D] = mm;
-  return s * a[fidx(g, C, c3[0], c3[1], c3[2])];
-}
-
-// limited value at the CV face between entries m_lo and m_lo + 1 along D
-template <int C, int D, bool VEL>
-__device__ __forceinline__ double lim_at(const GridDev& g, const double* a, int i3[3], int m_lo, double adv) {
-  if (adv > 0.0)
-    return cui(ext_get<C, D, VEL>(g, a, i3, m_lo - 1), ext_get<C, D, VEL>(g, a, i3, m_lo),
-               ext_get<C, D, VEL>(g, a, i3, m_lo + 1));
-  return cui(ext_get<C, D, VEL>(g, a, i3, m_lo + 2), ext_get<C, D, VEL>(g, a, i3, m_lo + 1),
-             ext_get<C, D, VEL>(g, a, i3, m_lo));
-}
-
-template <int C, int D>
-__device__ __forceinline__ double flux_div_dir(const GridDev& g, const double* const* vel, const double* rho,
-                                               bool withv, int i, int j, int k) {
-  int i3[3] = {i, j, k};
-  const double* qc = vel[C];
-  double Fhi, Flo;
-  if (C == D) {
-    // CV faces at cells id-1 (between faces id-1, id) and id (between id, id+1)
-    int m = i3[C];
-    int a3[3] = {i, j, k};
-    a3[C] = m - 1;
-    double q_m1 = qc[fidx(g, C, a3[0], a3[1], a3[2])];
-    double q_0 = qc[fidx(g, C, i, j, k)];
-    a3[C] = m + 1;
-    double q_p1 = qc[fidx(g, C, a3[0], a3[1], a3[2])];
-    double adv_lo = 0.5 * (q_m1 + q_0), adv_hi = 0.5 * (q_0 + q_p1);
-    double rl = lim_at<C, D, false>(g, rho, i3, m - 1, adv_lo);
-    double rh = lim_at<C, D, false>(g, rho, i3, m, adv_hi);
-    Flo = adv_lo * rl;
-    Fhi = adv_hi * rh;
-    if (withv) {
-      Flo *= lim_at<C, D, true>(g, qc, i3, m - 1, adv_lo);
-      Fhi *= lim_at<C, D, true>(g, qc, i3, m, adv_hi);
-    }
-  } else {
-    // CV faces on edges at D-face positions j_D (lo) and j_D + 1 (hi);
-    // advective velocity: mean of the two D-faces adjacent along C
-    const double* qd = vel[D];
-    int jd = i3[D];
-    int b3[3] = {i, j, k};
-    int b0[3] = {i, j, k};
-    b0[C] -= 1;
-    double adv_lo = 0.5 * (qd[fidx(g, D, b0[0], b0[1], b0[2])] + qd[fidx(g, D, b3[0], b3[1], b3[2])]);
-    b3[D] += 1;
-    b0[D] += 1;
-    double adv_hi = 0.5 * (qd[fidx(g, D, b0[0], b0[1], b0[2])] + qd[fidx(g, D, b3[0], b3[1], b3[2])]);
-    double rl = lim_at<C, D, false>(g, rho, i3, jd - 1, adv_lo);
-    double rh = lim_at<C, D, false>(g, rho, i3, jd, adv_hi);
-    Flo = adv_lo * rl;
-    Fhi = adv_hi * rh;
-    if (withv) {
-      Flo *= lim_at<C, D, true>(g, qc, i3, jd - 1, adv_lo);
-      Fhi *= lim_at<C, D, true>(g, qc, i3, jd, adv_hi);
-    }
-  }
-  return (Fhi - Flo) * g.ih[D];
-}
-
-template <int C>
-__global__ void k_transport(GridDev g, CVel<double> vel, const double* __restrict__ rho, bool withv, double* out) {
-  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
-  if (i >= ext(g, C, 0) || j >= ext(g, C, 1)) return;
-  int id3[3] = {i, j, k};
-  size_t id = fidx(g, C, i, j, k);
-  if (id3[C] == 0 || id3[C] == g.n[C]) {
-    out[id] = 0.0;
-    return;
-  }
-  double s = flux_div_dir<C, 0>(g, vel.q, rho, withv, i, j, k) + flux_div_dir<C, 1>(g, vel.q, rho, withv, i, j, k) +
-             flux_div_dir<C, 2>(g, vel.q, rho, withv, i, j, k);
-  out[id] = s;
-}
-
-void launch_transport_flux(const GridDev& g, const double* const vel[3], const double* const rho[3],
-                           bool with_velocity, double* const out[3], cudaStream_t st) {
-  CVel<double> v{{vel[0], vel[1], vel[2]}};
-  ktimer_begin(KC_TRANSPORT, st);
-  { k_transport<0><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, v, rho[0], with_velocity, out[0]); WSI_COUNT(); }
-  { k_transport<1><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, v, rho[1], with_velocity, out[1]); WSI_COUNT(); }
-  { k_transport<2><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, v, rho[2], with_velocity, out[2]); WSI_COUNT(); }
-  ktimer_end(KC_TRANSPORT, st);
-}
-
-__global__ void k_lincomb(size_t n, double a, const double* __restrict__ x, double b, const double* __restrict__ y,
-                          double c, const double* __restrict__ z, double* out) {
-  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (; t < n; t += stride) {
-    double s = a * x[t];
-    if (y) s += b * y[t];
-    if (z) s += c * z[t];
-    out[t] = s;
-  }
-}
-
-void launch_lincomb(size_t n, double a, const double* x, double b, const double* y, double c, const double* z,
-                    double* out, cudaStream_t st) {
-  int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
-  if (blocks < 1) blocks = 1;
-  { k_lincomb<<<blocks, 256, 0, st>>>(n, a, x, b, y, c, z, out); WSI_COUNT(); }
-}
-
-// =========================================================== level set
-template <int D>
-__device__ __forceinline__ double phi_ext(const GridDev& g, const double* __restrict__ a, int i3[3], int m) {
-  int n = g.n[D];
-  int mm = m;
-  if (m < 0) mm = -m - 1;
-  else if (m >= n) mm = 2 * n - 1 - m;
-  mm = clampi(mm, 0, n - 1);
-  int c3[3] = {i3[0], i3[1], i3[2]};
-  c3[D] = mm;
-  return a[fidx(g, 3, c3[0], c3[1], c3[2])];
-}
-
-template <int D>
-__device__ __forceinline__ double ls_flux(const GridDev& g, const double* vel_d, const double* phi, int i3[3],
-                                          int face) {
-  // D-face 'face' between cells face-1 and face
-  int f3[3] = {i3[0], i3[1], i3[2]};
-  f3[D] = face;
-  double a = vel_d[fidx(g, D, f3[0], f3[1], f3[2])];
-  double lim;
-  if (a > 0.0)
-    lim = cui(phi_ext<D>(g, phi, i3, face - 2), phi_ext<D>(g, phi, i3, face - 1), phi_ext<D>(g, phi, i3, face));
-  else
-    lim = cui(phi_ext<D>(g, phi, i3, face + 1), phi_ext<D>(g, phi, i3, face), phi_ext<D>(g, phi, i3, face - 1));
-  return a * lim;
-}
-
-__global__ void k_ls_advect(GridDev g, CVel<double> vel, const double* __restrict__ phi_n,
-                            const double* __restrict__ phi_h, double dt, double* out) {
-  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
-  if (i >= g.n[0] || j >= g.n[1]) return;
-  int i3[3] = {i, j, k};
-  double Q = (ls_flux<0>(g, vel.q[0], phi_h, i3, i + 1) - ls_flux<0>(g, vel.q[0], phi_h, i3, i)) * g.ih[0] +
-             (ls_flux<1>(g, vel.q[1], phi_h, i3, j + 1) - ls_flux<1>(g, vel.q[1], phi_h, i3, j)) * g.ih[1] +
-             (ls_flux<2>(g, vel.q[2], phi_h, i3, k + 1) - ls_flux<2>(g, vel.q[2], phi_h, i3, k)) * g.ih[2];
-  size_t id = fidx(g, 3, i, j, k);
-  out[id] = phi_n[id] - dt * Q;
-}
-
-void launch_levelset_advect(const GridDev& g, const double* const vel[3], const double* phi_n,
-                            const double* phi_half, double dt, double* out, cudaStream_t st) {
-  CVel<double> v{{vel[0], vel[1], vel[2]}};
-  { k_ls_advect<<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, v, phi_n, phi_half, dt, out); WSI_COUNT(); }
-}
-
-__global__ void k_box_sdf(GridDev g, const double* __restrict__ xc, double hx_, double hy_, double hz_, double* psi) {
-  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
-  if (i >= g.n[0] || j >= g.n[1]) return;
-  double x = (i + 0.5) * g.h[0], y = (j + 0.5) * g.h[1], z = (k + 0.5) * g.h[2];
-  double qx = fabs(x - xc[0]) - hx_, qy = fabs(y - xc[1]) - hy_, qz = fabs(z - xc[2]) - hz_;
-  double ox = fmax(qx, 0.0), oy = fmax(qy, 0.0), oz = fmax(qz, 0.0);
-  double outside = sqrt(ox * ox + oy * oy + oz * oz);
-  double inside = fmin(fmax(fmax(qx, qy), qz), 0.0);
-  psi[fidx(g, 3, i, j, k)] = outside + inside;
-}
-
-void launch_box_sdf(const GridDev& g, const double* xcom_dev, const double half[3], double* psi, cudaStream_t st) {
-  { k_box_sdf<<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, xcom_dev, half[0], half[1], half[2], psi); WSI_COUNT(); }
 }
 
 // =========================================================== momentum RHS

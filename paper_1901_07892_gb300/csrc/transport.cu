@@ -1,0 +1,328 @@
+// Consistent mass/momentum transport (Sec. 4.2.2) and level-set advection
+// (Sec. 4.2.1), with the bounded cubic-upwind (CUI) limiter.
+//
+// Transport of the C-face density (and, for the convective term, of the C
+// momentum) is a divergence over face-centred control volumes.  Each flux
+// through a control-volume face is shared by the two C-faces on either side
+// of it, so the kernel computes it once: a 32 x 8 block owns a tile of
+// C-faces in (x, y) and marches up a chunk of z-planes; x- and y-fluxes of a
+// plane go through shared memory (one halo column / row computed by the edge
+// threads), the z-flux of the plane below is kept in a register.
+//
+// Storage is float64 throughout; the flux arithmetic type T is float64 on
+// the plain path and float32 on the mixed path (an explicit stencil apply,
+// results rounded back into the float64 state).
+#include <math.h>
+
+#include <algorithm>
+
+#include "internal.h"
+
+namespace wsi {
+
+static constexpr int BX = 32, BY = 8;
+static constexpr int ZCHUNK = 8;
+
+// Division-free bounded CUI: with num = qC - qU and den = qD - qU,
+// t = num/den lies in a branch interval iff num*sign(den) lies in den-scaled
+// bounds, and qU + t_f den = qU + {3 num, 5 num/6 + den/3, den, num}.
+template <typename T>
+__device__ __forceinline__ T cui(T qU, T qC, T qD) {
+  T den = qD - qU;
+  T num = qC - qU;
+  if (den == T(0)) return qC;
+  T a = den > T(0) ? num : -num;  // num * sign(den)
+  T D = den > T(0) ? den : -den;  // t = a / D
+  T f;
+  if (a > T(0) && T(13) * a <= T(2) * D)
+    f = T(3) * num;
+  else if (T(13) * a > T(2) * D && T(5) * a <= T(4) * D)
+    f = num * T(5.0 / 6.0) + den * T(1.0 / 3.0);
+  else if (T(5) * a > T(4) * D && a <= D)
+    f = den;
+  else
+    f = num;
+  return qU + f;
+}
+
+// Value of the C-face array a at index m along axis D (other indices from
+// i3), extended by two ghost layers: even mirror (density) or the velocity
+// rule (odd about wall faces when C == D, the wall's sign across D != C).
+template <int C, int D, bool VEL, typename T>
+__device__ __forceinline__ T ext_get(const GridDev& g, const double* __restrict__ a, const int i3[3], int m) {
+  int n = g.n[D] + (C == D ? 1 : 0);  // stored extent along D
+  T s = T(1);
+  int mm = m;
+  if (m < 0) {
+    int gl = -m;
+    if (C == D) {
+      mm = gl;
+      if (VEL) s = T(-1);
+    } else {
+      mm = gl - 1;
+      if (VEL) s = (T)g.bc[2 * D];
+    }
+  } else if (m >= n) {
+    int gl = m - (n - 1);
+    if (C == D) {
+      mm = (n - 1) - gl;
+      if (VEL) s = T(-1);
+    } else {
+      mm = n - gl;
+      if (VEL) s = (T)g.bc[2 * D + 1];
+    }
+  }
+  mm = clampi(mm, 0, n - 1);
+  int c3[3] = {i3[0], i3[1], i3[2]};
+  c3[D] = mm;
+  return s * (T)a[fidx(g, C, c3[0], c3[1], c3[2])];
+}
+
+// limited value at the CV face between entries m_lo and m_lo + 1 along D
+template <int C, int D, bool VEL, typename T>
+__device__ __forceinline__ T lim_at(const GridDev& g, const double* a, const int i3[3], int m_lo, T adv) {
+  if (adv > T(0))
+    return cui<T>(ext_get<C, D, VEL, T>(g, a, i3, m_lo - 1), ext_get<C, D, VEL, T>(g, a, i3, m_lo),
+                  ext_get<C, D, VEL, T>(g, a, i3, m_lo + 1));
+  return cui<T>(ext_get<C, D, VEL, T>(g, a, i3, m_lo + 2), ext_get<C, D, VEL, T>(g, a, i3, m_lo + 1),
+                ext_get<C, D, VEL, T>(g, a, i3, m_lo));
+}
+
+// Flux through the D-direction control-volume face at position m of the
+// C-face column through i3 (the D-index of i3 is ignored):
+//   C == D: CV face at cell m, between C-faces m and m+1;
+//   C != D: CV face on the edge at D-face position m, between C-faces with
+//           D-indices m-1 and m; advective velocity from the two D-faces
+//           adjacent along C (i3 must not be a wall face along C).
+template <int C, int D, bool WITHV, typename T>
+__device__ __forceinline__ T cv_flux(const GridDev& g, const CVel<double>& vel, const double* __restrict__ rho,
+                                     const int i3[3], int m) {
+  T adv;
+  int mlo;
+  if (C == D) {
+    int a3[3] = {i3[0], i3[1], i3[2]};
+    a3[C] = m;
+    T q0 = (T)vel.q[C][fidx(g, C, a3[0], a3[1], a3[2])];
+    a3[C] = m + 1;
+    T q1 = (T)vel.q[C][fidx(g, C, a3[0], a3[1], a3[2])];
+    adv = T(0.5) * (q0 + q1);
+    mlo = m;
+  } else {
+    int b1[3] = {i3[0], i3[1], i3[2]};
+    b1[D] = m;
+    int b0[3] = {b1[0], b1[1], b1[2]};
+    b0[C] -= 1;
+    adv = T(0.5) * ((T)vel.q[D][fidx(g, D, b0[0], b0[1], b0[2])] + (T)vel.q[D][fidx(g, D, b1[0], b1[1], b1[2])]);
+    mlo = m - 1;
+  }
+  T F = adv * lim_at<C, D, false, T>(g, rho, i3, mlo, adv);
+  if (WITHV) F *= lim_at<C, D, true, T>(g, vel.q[C], i3, mlo, adv);
+  return F;
+}
+
+template <int C, bool WITHV, typename T>
+__global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, CVel<double> vel, const double* __restrict__ rho,
+                                                      double* out) {
+  __shared__ T sFx[BY][BX + 1];
+  __shared__ T sFy[BY + 1][BX];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.x * BX + tx, j = blockIdx.y * BY + ty;
+  const int e0 = ext(g, C, 0), e1 = ext(g, C, 1), e2 = ext(g, C, 2);
+  const bool inside = i < e0 && j < e1;
+  const int k0 = blockIdx.z * ZCHUNK;
+  const int k1 = min(k0 + ZCHUNK, e2);
+  // CV-face positions of this C-face: lo along D is (index - 1) for D == C
+  // (cells) and (index) for D != C (edges); hi = lo + 1
+  const int ox = (C == 0) ? -1 : 0, oy = (C == 1) ? -1 : 0, oz = (C == 2) ? -1 : 0;
+  T Fz_lo = T(0);
+  for (int k = k0; k < k1; ++k) {
+    int i3[3] = {i, j, k};
+    const int idC = (C == 0) ? i : ((C == 1) ? j : k);
+    const bool wall = idC == 0 || idC == g.n[C];
+    // x-direction fluxes: hi into column tx+1, lo halo by tx == 0
+    if (inside) {
+      bool okx = (C == 0) || !wall;
+      T hi = T(0), lo = T(0);
+      if (okx) {
+        int m = i + ox + 1;
+        if (C != 0 || m <= g.n[0] - 1) hi = cv_flux<C, 0, WITHV, T>(g, vel, rho, i3, m);
+        if (tx == 0) {
+          int ml = i + ox;
+          if (C != 0 || ml >= 0) lo = cv_flux<C, 0, WITHV, T>(g, vel, rho, i3, ml);
+        }
+      }
+      sFx[ty][tx + 1] = hi;
+      if (tx == 0) sFx[ty][0] = lo;
+      bool oky = (C == 1) || !wall;
+      hi = T(0);
+      lo = T(0);
+      if (oky) {
+        int m = j + oy + 1;
+        if (C != 1 || m <= g.n[1] - 1) hi = cv_flux<C, 1, WITHV, T>(g, vel, rho, i3, m);
+        if (ty == 0) {
+          int ml = j + oy;
+          if (C != 1 || ml >= 0) lo = cv_flux<C, 1, WITHV, T>(g, vel, rho, i3, ml);
+        }
+      }
+      sFy[ty + 1][tx] = hi;
+      if (ty == 0) sFy[0][tx] = lo;
+    }
+    __syncthreads();
+    if (inside) {
+      bool okz = (C == 2) || !wall;
+      T Fz_hi = T(0);
+      if (okz) {
+        int m = k + oz + 1;
+        if (C != 2 || m <= g.n[2] - 1) Fz_hi = cv_flux<C, 2, WITHV, T>(g, vel, rho, i3, m);
+        if (k == k0) {
+          int ml = k + oz;
+          Fz_lo = (C != 2 || ml >= 0) ? cv_flux<C, 2, WITHV, T>(g, vel, rho, i3, ml) : T(0);
+        }
+      }
+      T r = (sFx[ty][tx + 1] - sFx[ty][tx]) * (T)g.ih[0] + (sFy[ty + 1][tx] - sFy[ty][tx]) * (T)g.ih[1] +
+            (Fz_hi - Fz_lo) * (T)g.ih[2];
+      out[fidx(g, C, i, j, k)] = wall ? 0.0 : (double)r;
+      Fz_lo = Fz_hi;
+    }
+    __syncthreads();
+  }
+}
+
+template <bool WITHV, typename T>
+static void transport_all(const GridDev& g, const CVel<double>& v, const double* const rho[3], double* const out[3],
+                          cudaStream_t st) {
+  { k_transport<0, WITHV, T><<<dim3(cdiv(g.n[0] + 1, BX), cdiv(g.n[1], BY), cdiv(g.n[2], ZCHUNK)), dim3(BX, BY), 0,
+                               st>>>(g, v, rho[0], out[0]); WSI_COUNT(); }
+  { k_transport<1, WITHV, T><<<dim3(cdiv(g.n[0], BX), cdiv(g.n[1] + 1, BY), cdiv(g.n[2], ZCHUNK)), dim3(BX, BY), 0,
+                               st>>>(g, v, rho[1], out[1]); WSI_COUNT(); }
+  { k_transport<2, WITHV, T><<<dim3(cdiv(g.n[0], BX), cdiv(g.n[1], BY), cdiv(g.n[2] + 1, ZCHUNK)), dim3(BX, BY), 0,
+                               st>>>(g, v, rho[2], out[2]); WSI_COUNT(); }
+}
+
+void launch_transport_flux(const GridDev& g, const double* const vel[3], const double* const rho[3],
+                           bool with_velocity, double* const out[3], bool fp32, cudaStream_t st) {
+  CVel<double> v{{vel[0], vel[1], vel[2]}};
+  ktimer_begin(KC_TRANSPORT, st);
+  if (fp32) {
+    if (with_velocity) transport_all<true, float>(g, v, rho, out, st);
+    else transport_all<false, float>(g, v, rho, out, st);
+  } else {
+    if (with_velocity) transport_all<true, double>(g, v, rho, out, st);
+    else transport_all<false, double>(g, v, rho, out, st);
+  }
+  ktimer_end(KC_TRANSPORT, st);
+}
+
+__global__ void k_lincomb(size_t n, double a, const double* __restrict__ x, double b, const double* __restrict__ y,
+                          double c, const double* __restrict__ z, double* out) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (; t < n; t += stride) {
+    double s = a * x[t];
+    if (y) s += b * y[t];
+    if (z) s += c * z[t];
+    out[t] = s;
+  }
+}
+
+void launch_lincomb(size_t n, double a, const double* x, double b, const double* y, double c, const double* z,
+                    double* out, cudaStream_t st) {
+  int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+  if (blocks < 1) blocks = 1;
+  { k_lincomb<<<blocks, 256, 0, st>>>(n, a, x, b, y, c, z, out); WSI_COUNT(); }
+}
+
+// ================================================================ level set
+template <int D, typename T>
+__device__ __forceinline__ T phi_ext(const GridDev& g, const double* __restrict__ a, const int i3[3], int m) {
+  int n = g.n[D];
+  int mm = m;
+  if (m < 0) mm = -m - 1;
+  else if (m >= n) mm = 2 * n - 1 - m;
+  mm = clampi(mm, 0, n - 1);
+  int c3[3] = {i3[0], i3[1], i3[2]};
+  c3[D] = mm;
+  return (T)a[fidx(g, 3, c3[0], c3[1], c3[2])];
+}
+
+// flux u_D phi_lim through the D-face at position `face` (between cells
+// face-1 and face) of the cell column through i3
+template <int D, typename T>
+__device__ __forceinline__ T ls_flux(const GridDev& g, const double* __restrict__ vel_d,
+                                     const double* __restrict__ phi, const int i3[3], int face) {
+  int f3[3] = {i3[0], i3[1], i3[2]};
+  f3[D] = face;
+  T a = (T)vel_d[fidx(g, D, f3[0], f3[1], f3[2])];
+  T lim;
+  if (a > T(0))
+    lim = cui<T>(phi_ext<D, T>(g, phi, i3, face - 2), phi_ext<D, T>(g, phi, i3, face - 1),
+                 phi_ext<D, T>(g, phi, i3, face));
+  else
+    lim = cui<T>(phi_ext<D, T>(g, phi, i3, face + 1), phi_ext<D, T>(g, phi, i3, face),
+                 phi_ext<D, T>(g, phi, i3, face - 1));
+  return a * lim;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_ls_advect(GridDev g, CVel<double> vel, const double* __restrict__ phi_n,
+                                                      const double* __restrict__ phi_h, double dt, double* out) {
+  __shared__ T sFx[BY][BX + 1];
+  __shared__ T sFy[BY + 1][BX];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.x * BX + tx, j = blockIdx.y * BY + ty;
+  const bool inside = i < g.n[0] && j < g.n[1];
+  const int k0 = blockIdx.z * ZCHUNK;
+  const int k1 = min(k0 + ZCHUNK, g.n[2]);
+  T Fz_lo = T(0);
+  for (int k = k0; k < k1; ++k) {
+    int i3[3] = {i, j, k};
+    if (inside) {
+      sFx[ty][tx + 1] = ls_flux<0, T>(g, vel.q[0], phi_h, i3, i + 1);
+      if (tx == 0) sFx[ty][0] = ls_flux<0, T>(g, vel.q[0], phi_h, i3, i);
+      sFy[ty + 1][tx] = ls_flux<1, T>(g, vel.q[1], phi_h, i3, j + 1);
+      if (ty == 0) sFy[0][tx] = ls_flux<1, T>(g, vel.q[1], phi_h, i3, j);
+    }
+    __syncthreads();
+    if (inside) {
+      T Fz_hi = ls_flux<2, T>(g, vel.q[2], phi_h, i3, k + 1);
+      if (k == k0) Fz_lo = ls_flux<2, T>(g, vel.q[2], phi_h, i3, k);
+      T Q = (sFx[ty][tx + 1] - sFx[ty][tx]) * (T)g.ih[0] + (sFy[ty + 1][tx] - sFy[ty][tx]) * (T)g.ih[1] +
+            (Fz_hi - Fz_lo) * (T)g.ih[2];
+      size_t id = fidx(g, 3, i, j, k);
+      out[id] = phi_n[id] - dt * (double)Q;
+      Fz_lo = Fz_hi;
+    }
+    __syncthreads();
+  }
+}
+
+void launch_levelset_advect(const GridDev& g, const double* const vel[3], const double* phi_n,
+                            const double* phi_half, double dt, double* out, bool fp32, cudaStream_t st) {
+  CVel<double> v{{vel[0], vel[1], vel[2]}};
+  dim3 grid(cdiv(g.n[0], BX), cdiv(g.n[1], BY), cdiv(g.n[2], ZCHUNK));
+  if (fp32) {
+    k_ls_advect<float><<<grid, dim3(BX, BY), 0, st>>>(g, v, phi_n, phi_half, dt, out);
+    WSI_COUNT();
+  } else {
+    k_ls_advect<double><<<grid, dim3(BX, BY), 0, st>>>(g, v, phi_n, phi_half, dt, out);
+    WSI_COUNT();
+  }
+}
+
+__global__ void k_box_sdf(GridDev g, const double* __restrict__ xc, double hx_, double hy_, double hz_, double* psi) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.n[0] || j >= g.n[1]) return;
+  double x = (i + 0.5) * g.h[0], y = (j + 0.5) * g.h[1], z = (k + 0.5) * g.h[2];
+  double qx = fabs(x - xc[0]) - hx_, qy = fabs(y - xc[1]) - hy_, qz = fabs(z - xc[2]) - hz_;
+  double ox = fmax(qx, 0.0), oy = fmax(qy, 0.0), oz = fmax(qz, 0.0);
+  double outside = sqrt(ox * ox + oy * oy + oz * oz);
+  double inside = fmin(fmax(fmax(qx, qy), qz), 0.0);
+  psi[fidx(g, 3, i, j, k)] = outside + inside;
+}
+
+void launch_box_sdf(const GridDev& g, const double* xcom_dev, const double half[3], double* psi, cudaStream_t st) {
+  { k_box_sdf<<<dim3(cdiv(g.n[0], BX), cdiv(g.n[1], BY), g.n[2]), dim3(BX, BY), 0, st>>>(g, xcom_dev, half[0], half[1],
+                                                                                         half[2], psi); WSI_COUNT(); }
+}
+
+}  // namespace wsi
