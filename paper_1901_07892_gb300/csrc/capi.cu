@@ -98,6 +98,13 @@ struct wsi_ctx {
   Opts opts;
   Body body;
   bool has_body = false;
+  // float64 part of the momentum right-hand side fixed over a step's cycles
+  double* b0 = nullptr;
+  // float32 shadows of the explicitly transported fields (mixed path)
+  float *vn32 = nullptr, *u1_32 = nullptr, *u2_32 = nullptr, *rn32 = nullptr, *r1_32 = nullptr, *r2_32 = nullptr,
+        *R32 = nullptr, *C32 = nullptr, *vh32 = nullptr, *phih32 = nullptr, *mu_cc_n32 = nullptr,
+        *mu_e_n32[3] = {nullptr, nullptr, nullptr};
+  bool mixed() const { return desc.precision == WSI_PREC_MIXED; }
 };
 
 namespace {
@@ -388,6 +395,146 @@ int dlm_project(wsi_ctx* c, double* velv, const double* Xuse) {
   return cuda_check(c, "dlm project");
 }
 
+
+template <typename T>
+void parts(wsi_ctx* c, T* base, T* out[3]) {
+  for (int d = 0; d < 3; ++d) out[d] = base + c->pk.off[d];
+}
+template <typename T>
+void cparts(wsi_ctx* c, const T* base, const T* out[3]) {
+  for (int d = 0; d < 3; ++d) out[d] = base + c->pk.off[d];
+}
+
+// SSP-RK3 face density and the consistent convective term (Sec. 4.2.2):
+// rho_face <- rho^{n+1,k+1} (beta <- 1/rho), C into c->Cc (plain) or
+// c->C32 (mixed).  Stage 1 depends on (u^n, rho^n) only; with reuse_stage1
+// its result from an earlier cycle of the same step is kept.
+void transport_stage(wsi_ctx* c, int k, double dt, const double* un, const double* unm1, const double* uk,
+                     bool reuse_stage1) {
+  const GridDev& g = c->g;
+  cudaStream_t st = c->st;
+  const size_t nv = c->nvel;
+  if (!c->mixed()) {
+    if (k == 0) {
+      launch_lincomb(nv, 2.0, un, -1.0, unm1, 0.0, nullptr, c->u1, st);
+      launch_lincomb(nv, 1.5, un, -0.5, unm1, 0.0, nullptr, c->u2, st);
+    } else {
+      launch_lincomb(nv, 1.0, uk, 0.0, nullptr, 0.0, nullptr, c->u1, st);
+      launch_lincomb(nv, 0.375, uk, 0.75, un, -0.125, unm1, c->u2, st);
+    }
+    double *R[3], *Cq[3], *r1[3], *r2[3];
+    parts(c, c->R, R);
+    parts(c, c->Cc, Cq);
+    parts(c, c->rs1, r1);
+    parts(c, c->rs2, r2);
+    const double *cun[3], *cu1[3], *cu2[3];
+    cparts(c, un, cun);
+    cparts(c, (const double*)c->u1, cu1);
+    cparts(c, (const double*)c->u2, cu2);
+    const double* crn[3] = {c->rho_n[0], c->rho_n[1], c->rho_n[2]};
+    if (!reuse_stage1) {
+      launch_transport_flux<double>(g, cun, crn, false, R, st);
+      for (int d = 0; d < 3; ++d) launch_lincomb(fsize(g, d), 1.0, c->rho_n[d], -dt, R[d], 0.0, nullptr, r1[d], st);
+    }
+    const double* cr1[3] = {r1[0], r1[1], r1[2]};
+    launch_transport_flux<double>(g, cu1, cr1, false, R, st);
+    for (int d = 0; d < 3; ++d)
+      launch_lincomb(fsize(g, d), 0.75, c->rho_n[d], 0.25, r1[d], -0.25 * dt, R[d], r2[d], st);
+    const double* cr2[3] = {r2[0], r2[1], r2[2]};
+    launch_transport_flux<double>(g, cu2, cr2, false, R, st);
+    for (int d = 0; d < 3; ++d)
+      launch_lincomb(fsize(g, d), 1.0 / 3.0, c->rho_n[d], 2.0 / 3.0, r2[d], -2.0 / 3.0 * dt, R[d], c->rho_face[d],
+                     st);
+    launch_transport_flux<double>(g, cu2, cr2, true, Cq, st);
+  } else {
+    float *R[3], *Cq[3], *r1[3], *r2[3], *rn[3];
+    parts(c, c->R32, R);
+    parts(c, c->C32, Cq);
+    parts(c, c->r1_32, r1);
+    parts(c, c->r2_32, r2);
+    parts(c, c->rn32, rn);
+    if (k == 0) {
+      launch_lincomb_to_f32(nv, 2.0, un, -1.0, unm1, 0.0, nullptr, c->u1_32, st);
+      launch_lincomb_to_f32(nv, 1.5, un, -0.5, unm1, 0.0, nullptr, c->u2_32, st);
+    } else {
+      launch_lincomb_to_f32(nv, 1.0, uk, 0.0, nullptr, 0.0, nullptr, c->u1_32, st);
+      launch_lincomb_to_f32(nv, 0.375, uk, 0.75, un, -0.125, unm1, c->u2_32, st);
+    }
+    const float *cvn[3], *cu1[3], *cu2[3], *crn[3];
+    cparts(c, (const float*)c->vn32, cvn);
+    cparts(c, (const float*)c->u1_32, cu1);
+    cparts(c, (const float*)c->u2_32, cu2);
+    cparts(c, (const float*)c->rn32, crn);
+    if (!reuse_stage1) {
+      launch_lincomb_to_f32(nv, 1.0, un, 0.0, nullptr, 0.0, nullptr, c->vn32, st);
+      for (int d = 0; d < 3; ++d)
+        launch_lincomb_to_f32(fsize(g, d), 1.0, c->rho_n[d], 0.0, nullptr, 0.0, nullptr, rn[d], st);
+      launch_transport_flux<float>(g, cvn, crn, false, R, st);
+      launch_lincomb_f32(nv, 1.0f, c->rn32, (float)-dt, c->R32, 0.0f, nullptr, c->r1_32, st);
+    }
+    const float* cr1[3] = {r1[0], r1[1], r1[2]};
+    launch_transport_flux<float>(g, cu1, cr1, false, R, st);
+    launch_lincomb_f32(nv, 0.75f, c->rn32, 0.25f, c->r1_32, (float)(-0.25 * dt), c->R32, c->r2_32, st);
+    const float* cr2[3] = {r2[0], r2[1], r2[2]};
+    launch_transport_flux<float>(g, cu2, cr2, false, R, st);
+    for (int d = 0; d < 3; ++d)
+      launch_lincomb_mix(fsize(g, d), 1.0 / 3.0, c->rho_n[d], 2.0 / 3.0, r2[d], -2.0 / 3.0 * dt, R[d],
+                         c->rho_face[d], st);
+    launch_transport_flux<float>(g, cu2, cr2, true, Cq, st);
+  }
+  for (int d = 0; d < 3; ++d) recip(c, c->rho_face[d], c->beta[d], fsize(g, d));
+}
+
+// phi_out = phi_n - dt Q(u_half, phi_half) with u_half = (vk + vn)/2 and
+// phi_half = (phik + phin)/2 (Sec. 4.2.1)
+void levelset_stage(wsi_ctx* c, const double* vk, const double* vn, const double* phik, const double* phin,
+                    double dt, double* phi_out) {
+  const GridDev& g = c->g;
+  cudaStream_t st = c->st;
+  if (!c->mixed()) {
+    launch_lincomb(c->nvel, 0.5, vk, 0.5, vn, 0.0, nullptr, c->vel_half, st);
+    launch_lincomb(c->ncell, 0.5, phik, 0.5, phin, 0.0, nullptr, c->phi_half, st);
+    const double* vh[3];
+    cparts(c, (const double*)c->vel_half, vh);
+    launch_levelset_advect<double>(g, vh, phin, c->phi_half, dt, phi_out, st);
+  } else {
+    launch_lincomb_to_f32(c->nvel, 0.5, vk, 0.5, vn, 0.0, nullptr, c->vh32, st);
+    launch_lincomb_to_f32(c->ncell, 0.5, phik, 0.5, phin, 0.0, nullptr, c->phih32, st);
+    const float* vh[3];
+    cparts(c, (const float*)c->vh32, vh);
+    launch_levelset_advect<float>(g, vh, phin, c->phih32, dt, phi_out, st);
+  }
+}
+
+// b0 = rho^n u^n/dt + (1-theta) L_mu^n u^n  (needs transport_stage's float32
+// copy of u^n on the mixed path)
+void rhs_base(wsi_ctx* c, double dt) {
+  const GridDev& g = c->g;
+  cudaStream_t st = c->st;
+  double* b0[3];
+  parts(c, c->b0, b0);
+  const double* un[3];
+  cparts(c, (const double*)c->vel, un);
+  const double* crn[3] = {c->rho_n[0], c->rho_n[1], c->rho_n[2]};
+  if (!c->mixed()) {
+    launch_rhs_base<double>(g, coef_n(c), un, crn, un, 1.0 / dt, c->desc.theta, b0, st);
+  } else {
+    launch_lincomb_to_f32(c->ncell, 1.0, c->mu_cc_n, 0.0, nullptr, 0.0, nullptr, c->mu_cc_n32, st);
+    for (int e = 0; e < 3; ++e)
+      launch_lincomb_to_f32(esize(g, e), 1.0, c->mu_e_n[e], 0.0, nullptr, 0.0, nullptr, c->mu_e_n32[e], st);
+    Coef<float> cf;
+    for (int d = 0; d < 3; ++d) {
+      cf.rho_face[d] = nullptr;
+      cf.beta[d] = nullptr;
+      cf.mu_e[d] = c->mu_e_n32[d];
+    }
+    cf.mu_cc = c->mu_cc_n32;
+    const float* u32[3];
+    cparts(c, (const float*)c->vn32, u32);
+    launch_rhs_base<float>(g, cf, u32, crn, un, 1.0 / dt, c->desc.theta, b0, st);
+  }
+}
+
 int valid_ctx(wsi_ctx* c) { return c ? WSI_OK : WSI_ERR_INVALID_ARG; }
 
 }  // namespace
@@ -495,6 +642,23 @@ int wsi_create_grid(const wsi_grid_desc* d, void* stream, wsi_ctx** out) {
   c->V = A(c->nstk * (size_t)(c->m + 1));
   c->Z = A(c->nstk * (size_t)c->m);
   c->hdev = A(4 * (c->m + 2) + 8);
+  c->b0 = A(c->nvel);
+  if (d->precision == WSI_PREC_MIXED) {
+    // float32 shadows: half-size double allocations reinterpreted
+    auto F = [&](size_t n) { return (float*)A((n + 1) / 2); };
+    c->vn32 = F(c->nvel);
+    c->u1_32 = F(c->nvel);
+    c->u2_32 = F(c->nvel);
+    c->rn32 = F(c->nvel);
+    c->r1_32 = F(c->nvel);
+    c->r2_32 = F(c->nvel);
+    c->R32 = F(c->nvel);
+    c->C32 = F(c->nvel);
+    c->vh32 = F(c->nvel);
+    c->phih32 = F(c->ncell);
+    c->mu_cc_n32 = F(c->ncell);
+    for (int e = 0; e < 3; ++e) c->mu_e_n32[e] = F(esize(g, e));
+  }
   c->red = A(8192);
   if (!ok) {
     c->err = "out of device memory";
@@ -648,18 +812,10 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
   cudaMemcpyAsync(c->psi_k, c->psi, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
   if (c->has_body) cudaMemcpyAsync(B.Xn, B.X, (size_t)B.n * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(c->x + c->pk.off[3], c->p, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
-  double* vn[3];
-  const double* cvn[3];
-  vel_parts(c, c->vel, vn);
-  vel_parts(c, (const double*)c->vel, cvn);
   const int ncyc = 2;
   for (int k = 0; k < ncyc; ++k) {
     // 1. level sets and viscosity at (n+1, k+1)
-    launch_lincomb(nv, 0.5, c->vel_k, 0.5, c->vel, 0.0, nullptr, c->vel_half, st);
-    launch_lincomb(nc, 0.5, c->phi_k, 0.5, c->phi, 0.0, nullptr, c->phi_half, st);
-    const double* vh[3];
-    vel_parts(c, (const double*)c->vel_half, vh);
-    launch_levelset_advect(g, vh, c->phi, c->phi_half, dt, c->phi_new, c->desc.precision == WSI_PREC_MIXED, st);
+    levelset_stage(c, c->vel_k, c->vel, c->phi_k, c->phi, dt, c->phi_new);
     const double* psi_use = c->psi_k;
     if (c->has_body && B.shape == 1) {
       launch_marker_mean(B.X, B.n, B.xc, B.scratch, st);
@@ -668,47 +824,15 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
     }
     launch_materials(g, pc, c->phi_new, psi_use, c->rho_cc, c->mu_cc, c->rho_face, c->beta, c->rho_flow, c->mu_e,
                      st);
-    // 2. SSP-RK3 face density and consistent convection
-    if (k == 0) {
-      launch_lincomb(nv, 2.0, c->vel, -1.0, c->vel_old, 0.0, nullptr, c->u1, st);
-      launch_lincomb(nv, 1.5, c->vel, -0.5, c->vel_old, 0.0, nullptr, c->u2, st);
-    } else {
-      cudaMemcpyAsync(c->u1, c->vel_k, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
-      launch_lincomb(nv, 0.375, c->vel_k, 0.75, c->vel, -0.125, c->vel_old, c->u2, st);
-    }
-    double *R[3], *Cq[3], *r1[3], *r2[3];
-    vel_parts(c, c->R, R);
-    vel_parts(c, c->Cc, Cq);
-    vel_parts(c, c->rs1, r1);
-    vel_parts(c, c->rs2, r2);
-    const double* cu1[3];
-    const double* cu2[3];
-    vel_parts(c, (const double*)c->u1, cu1);
-    vel_parts(c, (const double*)c->u2, cu2);
-    const double* crn[3] = {c->rho_n[0], c->rho_n[1], c->rho_n[2]};
-    if (k == 0) {
-      // stage 1 depends on (u^n, rho^n) only: the same in every cycle
-      launch_transport_flux(g, cvn, crn, false, R, c->desc.precision == WSI_PREC_MIXED, st);
-      for (int d = 0; d < 3; ++d) launch_lincomb(fsize(g, d), 1.0, c->rho_n[d], -dt, R[d], 0.0, nullptr, r1[d], st);
-    }
-    const double* cr1[3] = {r1[0], r1[1], r1[2]};
-    launch_transport_flux(g, cu1, cr1, false, R, c->desc.precision == WSI_PREC_MIXED, st);
-    for (int d = 0; d < 3; ++d)
-      launch_lincomb(fsize(g, d), 0.75, c->rho_n[d], 0.25, r1[d], -0.25 * dt, R[d], r2[d], st);
-    const double* cr2[3] = {r2[0], r2[1], r2[2]};
-    launch_transport_flux(g, cu2, cr2, false, R, c->desc.precision == WSI_PREC_MIXED, st);
-    for (int d = 0; d < 3; ++d)
-      launch_lincomb(fsize(g, d), 1.0 / 3.0, c->rho_n[d], 2.0 / 3.0, r2[d], -2.0 / 3.0 * dt, R[d], c->rho_face[d],
-                     st);
-    launch_transport_flux(g, cu2, cr2, true, Cq, c->desc.precision == WSI_PREC_MIXED, st);
-    for (int d = 0; d < 3; ++d) recip(c, c->rho_face[d], c->beta[d], fsize(g, d));
-    // right-hand side with mu^n and gravity
-    double* bq[3];
-    vel_parts(c, c->b, bq);
-    const double* cC[3] = {Cq[0], Cq[1], Cq[2]};
+    // 2. SSP-RK3 face density and consistent convection; right-hand side
+    transport_stage(c, k, dt, c->vel, c->vel_old, c->vel_k, k > 0);
+    if (k == 0) rhs_base(c, dt);
     const double* rg[3];
     for (int d = 0; d < 3; ++d) rg[d] = c->props.gravity_mode == WSI_GRAVITY_FLOW ? c->rho_flow[d] : c->rho_face[d];
-    launch_momentum_rhs(g, coef_n(c), crn, cvn, cC, rg, c->desc.gravity, 1.0 / dt, c->desc.theta, bq, st);
+    if (c->mixed())
+      launch_rhs_cycle<float>(g, c->b0, c->C32, rg, c->desc.gravity, c->b, st);
+    else
+      launch_rhs_cycle<double>(g, c->b0, c->Cc, rg, c->desc.gravity, c->b, st);
     cudaMemsetAsync(c->b + c->pk.off[3], 0, nc * sizeof(double), st);
     // 3. Stokes solve from (u^{n+1,k}, p^{n+1/2,k})
     cudaMemcpyAsync(c->x, c->vel_k, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
@@ -857,47 +981,29 @@ int wsi_transport(wsi_ctx* c, const double* u_n, const double* u_nm1, const doub
                   double* rho_out, double* C_out) {
   if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
   if (!c->have_phases) return fail(c, WSI_ERR_INVALID_ARG, "no phases set");
-  const GridDev& g = c->g;
-  cudaStream_t st = c->st;
   size_t nv = c->nvel;
+  // u_n -> vel_half, u^{n-1} -> u1 scratch copy, u_k -> vel_k
   int rc = copy_in(c, c->vel_half, u_n, nv);
-  if (!rc) rc = copy_in(c, c->vel_old, u_nm1, nv);
+  if (!rc) rc = copy_in(c, c->rs2, u_nm1, nv);
   if (!rc && k > 0) rc = copy_in(c, c->vel_k, u_k, nv);
   if (rc) return rc;
   PhaseConst pc = phase_const(c);
-  launch_materials(g, pc, c->phi, c->psi, c->rho_cc_tmp, c->mu_cc_n, c->rho_n, c->beta_n, c->rho_flow_n, c->mu_e_n,
-                   st);
-  if (k == 0) {
-    launch_lincomb(nv, 2.0, c->vel_half, -1.0, c->vel_old, 0.0, nullptr, c->u1, st);
-    launch_lincomb(nv, 1.5, c->vel_half, -0.5, c->vel_old, 0.0, nullptr, c->u2, st);
-  } else {
-    cudaMemcpyAsync(c->u1, c->vel_k, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
-    launch_lincomb(nv, 0.375, c->vel_k, 0.75, c->vel_half, -0.125, c->vel_old, c->u2, st);
-  }
-  double *R[3], *Cq[3], *r1[3], *r2[3], *r3[3];
-  vel_parts(c, c->R, R);
-  vel_parts(c, c->Cc, Cq);
-  vel_parts(c, c->rs1, r1);
-  vel_parts(c, c->rs2, r2);
-  vel_parts(c, c->b, r3);
-  const double *cun[3], *cu1[3], *cu2[3];
-  vel_parts(c, (const double*)c->vel_half, cun);
-  vel_parts(c, (const double*)c->u1, cu1);
-  vel_parts(c, (const double*)c->u2, cu2);
-  const double* crn[3] = {c->rho_n[0], c->rho_n[1], c->rho_n[2]};
-  launch_transport_flux(g, cun, crn, false, R, c->desc.precision == WSI_PREC_MIXED, st);
-  for (int d = 0; d < 3; ++d) launch_lincomb(fsize(g, d), 1.0, c->rho_n[d], -dt, R[d], 0.0, nullptr, r1[d], st);
-  const double* cr1[3] = {r1[0], r1[1], r1[2]};
-  launch_transport_flux(g, cu1, cr1, false, R, c->desc.precision == WSI_PREC_MIXED, st);
+  launch_materials(c->g, pc, c->phi, c->psi, c->rho_cc_tmp, c->mu_cc_n, c->rho_n, c->beta_n, c->rho_flow_n,
+                   c->mu_e_n, c->st);
+  // the stage buffers of the plain path alias rs2 only after u^(1), u^(2)
+  // are formed, so copy u^{n-1} aside first
+  cudaMemcpyAsync(c->vel_old, c->rs2, nv * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  transport_stage(c, k, dt, c->vel_half, c->vel_old, c->vel_k, false);
+  double* rq[3];
+  parts(c, c->b, rq);
   for (int d = 0; d < 3; ++d)
-    launch_lincomb(fsize(g, d), 0.75, c->rho_n[d], 0.25, r1[d], -0.25 * dt, R[d], r2[d], st);
-  const double* cr2[3] = {r2[0], r2[1], r2[2]};
-  launch_transport_flux(g, cu2, cr2, false, R, c->desc.precision == WSI_PREC_MIXED, st);
-  for (int d = 0; d < 3; ++d)
-    launch_lincomb(fsize(g, d), 1.0 / 3.0, c->rho_n[d], 2.0 / 3.0, r2[d], -2.0 / 3.0 * dt, R[d], r3[d], st);
-  launch_transport_flux(g, cu2, cr2, true, Cq, c->desc.precision == WSI_PREC_MIXED, st);
+    cudaMemcpyAsync(rq[d], c->rho_face[d], fsize(c->g, d) * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  if (c->mixed())
+    launch_lincomb_mix(nv, 0.0, c->Cc, 1.0, c->C32, 0.0, c->C32, c->x, c->st);
+  else
+    cudaMemcpyAsync(c->x, c->Cc, nv * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
   rc = copy_out(c, rho_out, c->b, nv);
-  if (!rc) rc = copy_out(c, C_out, c->Cc, nv);
+  if (!rc) rc = copy_out(c, C_out, c->x, nv);
   if (rc) return rc;
   return cuda_check(c, "transport");
 }
@@ -905,14 +1011,15 @@ int wsi_transport(wsi_ctx* c, const double* u_n, const double* u_nm1, const doub
 int wsi_advect_levelset(wsi_ctx* c, const double* vel, const double* phi_n, const double* phi_half, double dt,
                         double* phi_out) {
   if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
-  int rc = copy_in(c, c->vel_half, vel, c->nvel);
-  if (!rc) rc = copy_in(c, c->phi_k, phi_n, c->ncell);
+  // phi_half = (phi_k + phi_n)/2 with phi_k = 2 phi_half - phi_n; likewise the
+  // velocity is passed as u_half = (u_half + u_half)/2
+  // (scratch buffers only: the stored level sets are left untouched)
+  int rc = copy_in(c, c->vel_k, vel, c->nvel);
+  if (!rc) rc = copy_in(c, c->psi_new, phi_n, c->ncell);
   if (!rc) rc = copy_in(c, c->phi_half, phi_half, c->ncell);
   if (rc) return rc;
-  const double* vh[3];
-  vel_parts(c, (const double*)c->vel_half, vh);
-  launch_levelset_advect(c->g, vh, c->phi_k, c->phi_half, dt, c->phi_new, c->desc.precision == WSI_PREC_MIXED,
-                         c->st);
+  launch_lincomb(c->ncell, 2.0, c->phi_half, -1.0, c->psi_new, 0.0, nullptr, c->phi_k, c->st);
+  levelset_stage(c, c->vel_k, c->vel_k, c->phi_k, c->psi_new, dt, c->phi_new);
   rc = copy_out(c, phi_out, c->phi_new, c->ncell);
   if (rc) return rc;
   return cuda_check(c, "advect_levelset");

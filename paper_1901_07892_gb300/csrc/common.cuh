@@ -41,6 +41,31 @@ struct GridDev {
   double ih2[3];  // 1/h^2
   double bc[6];   // tangential ghost sign per wall (x-, x+, y-, y+, z-, z+)
 };
+// float32 copies of the inverse spacings for float32 kernels
+struct GridF {
+  float ih[3], ih2[3];
+};
+inline GridF gridf(const GridDev& g) {
+  GridF f;
+  for (int a = 0; a < 3; ++a) {
+    f.ih[a] = (float)g.ih[a];
+    f.ih2[a] = (float)g.ih2[a];
+  }
+  return f;
+}
+template <typename T>
+__device__ __forceinline__ T ginv(const GridDev& g, const GridF& f, int a);
+template <>
+__device__ __forceinline__ double ginv<double>(const GridDev& g, const GridF&, int a) { return g.ih[a]; }
+template <>
+__device__ __forceinline__ float ginv<float>(const GridDev&, const GridF& f, int a) { return f.ih[a]; }
+template <typename T>
+__device__ __forceinline__ T ginv2(const GridDev& g, const GridF& f, int a);
+template <>
+__device__ __forceinline__ double ginv2<double>(const GridDev& g, const GridF&, int a) { return g.ih2[a]; }
+template <>
+__device__ __forceinline__ float ginv2<float>(const GridDev&, const GridF& f, int a) { return f.ih2[a]; }
+
 inline void grid_finalize(GridDev& g) {
   for (int a = 0; a < 3; ++a) {
     g.ih[a] = 1.0 / g.h[a];

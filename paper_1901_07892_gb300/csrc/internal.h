@@ -53,21 +53,34 @@ template <typename T>
 void launch_viscous_rbgs(const GridDev& g, const Coef<T>& cf, T inv_dt, T theta, T* const q[3], const T* const b[3],
                          int color, cudaStream_t st);
 
-// transport.cu (Sec. 4.2.2): R or C on all three face arrays; fp32 selects
-// float32 flux arithmetic (float64 storage)
-void launch_transport_flux(const GridDev& g, const double* const vel[3], const double* const rho[3],
-                           bool with_velocity, double* const out[3], bool fp32, cudaStream_t st);
+// transport.cu (Sec. 4.2.2): R or C on all three face arrays, storage and
+// arithmetic in T
+template <typename T>
+void launch_transport_flux(const GridDev& g, const T* const vel[3], const T* const rho[3], bool with_velocity,
+                           T* const out[3], cudaStream_t st);
 // out = a*x + b*y + c*z elementwise over n (any of y, z may be null)
 void launch_lincomb(size_t n, double a, const double* x, double b, const double* y, double c, const double* z,
                     double* out, cudaStream_t st);
-// rk stage: out = a*rho_n + b*rho_s - c*dt*R
-void launch_levelset_advect(const GridDev& g, const double* const vel[3], const double* phi_n,
-                            const double* phi_half, double dt, double* out, bool fp32, cudaStream_t st);
+void launch_lincomb_to_f32(size_t n, double a, const double* x, double b, const double* y, double c,
+                           const double* z, float* out, cudaStream_t st);
+void launch_lincomb_f32(size_t n, float a, const float* x, float b, const float* y, float c, const float* z,
+                        float* out, cudaStream_t st);
+void launch_lincomb_mix(size_t n, double a, const double* x, double b, const float* y, double c, const float* z,
+                        double* out, cudaStream_t st);
+template <typename T>
+void launch_levelset_advect(const GridDev& g, const T* const vel[3], const double* phi_n, const T* phi_half, double dt,
+                            double* out, cudaStream_t st);
 void launch_box_sdf(const GridDev& g, const double* xcom_dev, const double half[3], double* psi, cudaStream_t st);
-// b = rho_n u_n / dt - C + (1-theta) L_mu^n u_n + rho_g g
-void launch_momentum_rhs(const GridDev& g, const Coef<double>& cf_n, const double* const rho_n[3],
-                         const double* const u_n[3], const double* const C[3], const double* const rho_g[3],
-                         const double grav[3], double inv_dt, double theta, double* const b[3], cudaStream_t st);
+// part of the momentum right-hand side fixed over the cycles of a step:
+// b0 = rho_n u_n / dt + (1-theta) L_mu^n u_n, the strain term in T from
+// T copies of u_n and mu^n (zero on wall faces)
+template <typename T>
+void launch_rhs_base(const GridDev& g, const Coef<T>& cf_n, const T* const uT[3], const double* const rho_n[3],
+                     const double* const u_n[3], double inv_dt, double theta, double* const b0[3], cudaStream_t st);
+// b = b0 - C + rho_g g on every face of the packed velocity vector (walls 0)
+template <typename TC>
+void launch_rhs_cycle(const GridDev& g, const double* b0, const TC* C, const double* const rho_g[3],
+                      const double grav[3], double* b, cudaStream_t st);
 void launch_zero_walls(const GridDev& g, double* const q[3], cudaStream_t st);
 
 // ---------------------------------------------------------------- krylov.cu

@@ -406,33 +406,71 @@ void launch_zero_walls(const GridDev& g, double* const q[3], cudaStream_t st) {
 }
 
 // =========================================================== momentum RHS
-template <int C>
-__global__ void k_mom_rhs(GridDev g, Coef<double> cf_n, const double* __restrict__ rho_n, CVel<double> u_n,
-                          const double* __restrict__ Cc, const double* __restrict__ rho_g, double gc, double inv_dt,
-                          double theta, double* b) {
+template <int C, typename T>
+__global__ void k_rhs_base(GridDev g, Coef<T> cf_n, CVel<T> uT, const double* __restrict__ rho_n,
+                           const double* __restrict__ un, double inv_dt, double theta, double* b0) {
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (i >= ext(g, C, 0) || j >= ext(g, C, 1)) return;
   int id3[3] = {i, j, k};
   size_t id = fidx(g, C, i, j, k);
   if (id3[C] == 0 || id3[C] == g.n[C]) {
-    b[id] = 0.0;
+    b0[id] = 0.0;
     return;
   }
-  double L = strain_at<C, double>(g, cf_n, u_n.q, i, j, k, nullptr);
-  b[id] = rho_n[id] * u_n.q[C][id] * inv_dt - Cc[id] + (1.0 - theta) * L + rho_g[id] * gc;
+  T L = strain_at<C, T>(g, cf_n, uT.q, i, j, k, nullptr);
+  b0[id] = rho_n[id] * un[id] * inv_dt + (1.0 - theta) * (double)L;
 }
 
-void launch_momentum_rhs(const GridDev& g, const Coef<double>& cf_n, const double* const rho_n[3],
-                         const double* const u_n[3], const double* const C[3], const double* const rho_g[3],
-                         const double grav[3], double inv_dt, double theta, double* const b[3], cudaStream_t st) {
-  CVel<double> u{{u_n[0], u_n[1], u_n[2]}};
-  { k_mom_rhs<0><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, cf_n, rho_n[0], u, C[0], rho_g[0],
-                                                                          grav[0], inv_dt, theta, b[0]); WSI_COUNT(); }
-  { k_mom_rhs<1><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, cf_n, rho_n[1], u, C[1], rho_g[1],
-                                                                          grav[1], inv_dt, theta, b[1]); WSI_COUNT(); }
-  { k_mom_rhs<2><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, cf_n, rho_n[2], u, C[2], rho_g[2],
-                                                                          grav[2], inv_dt, theta, b[2]); WSI_COUNT(); }
+template <typename T>
+void launch_rhs_base(const GridDev& g, const Coef<T>& cf_n, const T* const uT[3], const double* const rho_n[3],
+                     const double* const u_n[3], double inv_dt, double theta, double* const b0[3], cudaStream_t st) {
+  CVel<T> u{{uT[0], uT[1], uT[2]}};
+  { k_rhs_base<0, T><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, cf_n, u, rho_n[0], u_n[0], inv_dt,
+                                                                               theta, b0[0]); WSI_COUNT(); }
+  { k_rhs_base<1, T><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, cf_n, u, rho_n[1], u_n[1], inv_dt,
+                                                                               theta, b0[1]); WSI_COUNT(); }
+  { k_rhs_base<2, T><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, cf_n, u, rho_n[2], u_n[2], inv_dt,
+                                                                               theta, b0[2]); WSI_COUNT(); }
 }
+
+// b = b0 - C + rho_g g over the packed velocity vector; wall faces are zero
+// in b0, C and on output
+template <typename TC>
+__global__ void k_rhs_cycle(size_t n0, size_t n1, size_t n2, const double* __restrict__ b0, const TC* __restrict__ Cc,
+                            const double* __restrict__ rg0, const double* __restrict__ rg1,
+                            const double* __restrict__ rg2, double g0, double g1, double g2, double* b) {
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t n = n0 + n1 + n2;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+    double grav;
+    if (t < n0) grav = rg0[t] * g0;
+    else if (t < n0 + n1) grav = rg1[t - n0] * g1;
+    else grav = rg2[t - n0 - n1] * g2;
+    b[t] = b0[t] - (double)Cc[t] + grav;
+  }
+}
+
+template <typename TC>
+void launch_rhs_cycle(const GridDev& g, const double* b0, const TC* C, const double* const rho_g[3],
+                      const double grav[3], double* b, cudaStream_t st) {
+  size_t n0 = fsize(g, 0), n1 = fsize(g, 1), n2 = fsize(g, 2);
+  int blocks = (int)std::min<size_t>((n0 + n1 + n2 + 255) / 256, 152 * 16);
+  { k_rhs_cycle<TC><<<blocks, 256, 0, st>>>(n0, n1, n2, b0, C, rho_g[0], rho_g[1], rho_g[2], grav[0], grav[1],
+                                            grav[2], b); WSI_COUNT(); }
+  double* q[3] = {b, b + n0, b + n0 + n1};
+  launch_zero_walls(g, q, st);
+}
+
+template void launch_rhs_base<double>(const GridDev&, const Coef<double>&, const double* const[3],
+                                      const double* const[3], const double* const[3], double, double,
+                                      double* const[3], cudaStream_t);
+template void launch_rhs_base<float>(const GridDev&, const Coef<float>&, const float* const[3],
+                                     const double* const[3], const double* const[3], double, double,
+                                     double* const[3], cudaStream_t);
+template void launch_rhs_cycle<double>(const GridDev&, const double*, const double*, const double* const[3],
+                                       const double[3], double*, cudaStream_t);
+template void launch_rhs_cycle<float>(const GridDev&, const double*, const float*, const double* const[3],
+                                      const double[3], double*, cudaStream_t);
 
 // explicit instantiations
 template void launch_viscous<double>(const GridDev&, const Coef<double>&, double, double, const double* const[3],

@@ -9,9 +9,10 @@
 // plane go through shared memory (one halo column / row computed by the edge
 // threads), the z-flux of the plane below is kept in a register.
 //
-// Storage is float64 throughout; the flux arithmetic type T is float64 on
-// the plain path and float32 on the mixed path (an explicit stencil apply,
-// results rounded back into the float64 state).
+// Storage and arithmetic type T: float64 on the plain path; float32 on the
+// mixed path, where the step keeps float32 shadow copies of the transported
+// fields (an explicit stencil apply; reading float32 avoids a float64->float32
+// conversion per load, which issues on GB300's narrow float64 pipe).
 #include <math.h>
 
 #include <algorithm>
@@ -49,7 +50,7 @@ __device__ __forceinline__ T cui(T qU, T qC, T qD) {
 // i3), extended by two ghost layers: even mirror (density) or the velocity
 // rule (odd about wall faces when C == D, the wall's sign across D != C).
 template <int C, int D, bool VEL, typename T>
-__device__ __forceinline__ T ext_get(const GridDev& g, const double* __restrict__ a, const int i3[3], int m) {
+__device__ __forceinline__ T ext_get(const GridDev& g, const T* __restrict__ a, const int i3[3], int m) {
   int n = g.n[D] + (C == D ? 1 : 0);  // stored extent along D
   T s = T(1);
   int mm = m;
@@ -75,12 +76,12 @@ __device__ __forceinline__ T ext_get(const GridDev& g, const double* __restrict_
   mm = clampi(mm, 0, n - 1);
   int c3[3] = {i3[0], i3[1], i3[2]};
   c3[D] = mm;
-  return s * (T)a[fidx(g, C, c3[0], c3[1], c3[2])];
+  return s * a[fidx(g, C, c3[0], c3[1], c3[2])];
 }
 
 // limited value at the CV face between entries m_lo and m_lo + 1 along D
 template <int C, int D, bool VEL, typename T>
-__device__ __forceinline__ T lim_at(const GridDev& g, const double* a, const int i3[3], int m_lo, T adv) {
+__device__ __forceinline__ T lim_at(const GridDev& g, const T* a, const int i3[3], int m_lo, T adv) {
   if (adv > T(0))
     return cui<T>(ext_get<C, D, VEL, T>(g, a, i3, m_lo - 1), ext_get<C, D, VEL, T>(g, a, i3, m_lo),
                   ext_get<C, D, VEL, T>(g, a, i3, m_lo + 1));
@@ -95,16 +96,16 @@ __device__ __forceinline__ T lim_at(const GridDev& g, const double* a, const int
 //           D-indices m-1 and m; advective velocity from the two D-faces
 //           adjacent along C (i3 must not be a wall face along C).
 template <int C, int D, bool WITHV, typename T>
-__device__ __forceinline__ T cv_flux(const GridDev& g, const CVel<double>& vel, const double* __restrict__ rho,
+__device__ __forceinline__ T cv_flux(const GridDev& g, const CVel<T>& vel, const T* __restrict__ rho,
                                      const int i3[3], int m) {
   T adv;
   int mlo;
   if (C == D) {
     int a3[3] = {i3[0], i3[1], i3[2]};
     a3[C] = m;
-    T q0 = (T)vel.q[C][fidx(g, C, a3[0], a3[1], a3[2])];
+    T q0 = vel.q[C][fidx(g, C, a3[0], a3[1], a3[2])];
     a3[C] = m + 1;
-    T q1 = (T)vel.q[C][fidx(g, C, a3[0], a3[1], a3[2])];
+    T q1 = vel.q[C][fidx(g, C, a3[0], a3[1], a3[2])];
     adv = T(0.5) * (q0 + q1);
     mlo = m;
   } else {
@@ -112,7 +113,7 @@ __device__ __forceinline__ T cv_flux(const GridDev& g, const CVel<double>& vel, 
     b1[D] = m;
     int b0[3] = {b1[0], b1[1], b1[2]};
     b0[C] -= 1;
-    adv = T(0.5) * ((T)vel.q[D][fidx(g, D, b0[0], b0[1], b0[2])] + (T)vel.q[D][fidx(g, D, b1[0], b1[1], b1[2])]);
+    adv = T(0.5) * (vel.q[D][fidx(g, D, b0[0], b0[1], b0[2])] + vel.q[D][fidx(g, D, b1[0], b1[1], b1[2])]);
     mlo = m - 1;
   }
   T F = adv * lim_at<C, D, false, T>(g, rho, i3, mlo, adv);
@@ -121,8 +122,8 @@ __device__ __forceinline__ T cv_flux(const GridDev& g, const CVel<double>& vel, 
 }
 
 template <int C, bool WITHV, typename T>
-__global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, CVel<double> vel, const double* __restrict__ rho,
-                                                      double* out) {
+__global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, GridF gf, CVel<T> vel, const T* __restrict__ rho,
+                                                      T* out) {
   __shared__ T sFx[BY][BX + 1];
   __shared__ T sFy[BY + 1][BX];
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -179,9 +180,9 @@ __global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, CVel<double> ve
           Fz_lo = (C != 2 || ml >= 0) ? cv_flux<C, 2, WITHV, T>(g, vel, rho, i3, ml) : T(0);
         }
       }
-      T r = (sFx[ty][tx + 1] - sFx[ty][tx]) * (T)g.ih[0] + (sFy[ty + 1][tx] - sFy[ty][tx]) * (T)g.ih[1] +
-            (Fz_hi - Fz_lo) * (T)g.ih[2];
-      out[fidx(g, C, i, j, k)] = wall ? 0.0 : (double)r;
+      T r = (sFx[ty][tx + 1] - sFx[ty][tx]) * ginv<T>(g, gf, 0) + (sFy[ty + 1][tx] - sFy[ty][tx]) * ginv<T>(g, gf, 1) +
+            (Fz_hi - Fz_lo) * ginv<T>(g, gf, 2);
+      out[fidx(g, C, i, j, k)] = wall ? T(0) : r;
       Fz_lo = Fz_hi;
     }
     __syncthreads();
@@ -189,52 +190,91 @@ __global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, CVel<double> ve
 }
 
 template <bool WITHV, typename T>
-static void transport_all(const GridDev& g, const CVel<double>& v, const double* const rho[3], double* const out[3],
+static void transport_all(const GridDev& g, const CVel<T>& v, const T* const rho[3], T* const out[3],
                           cudaStream_t st) {
+  GridF gf = gridf(g);
   { k_transport<0, WITHV, T><<<dim3(cdiv(g.n[0] + 1, BX), cdiv(g.n[1], BY), cdiv(g.n[2], ZCHUNK)), dim3(BX, BY), 0,
-                               st>>>(g, v, rho[0], out[0]); WSI_COUNT(); }
+                               st>>>(g, gf, v, rho[0], out[0]); WSI_COUNT(); }
   { k_transport<1, WITHV, T><<<dim3(cdiv(g.n[0], BX), cdiv(g.n[1] + 1, BY), cdiv(g.n[2], ZCHUNK)), dim3(BX, BY), 0,
-                               st>>>(g, v, rho[1], out[1]); WSI_COUNT(); }
+                               st>>>(g, gf, v, rho[1], out[1]); WSI_COUNT(); }
   { k_transport<2, WITHV, T><<<dim3(cdiv(g.n[0], BX), cdiv(g.n[1], BY), cdiv(g.n[2] + 1, ZCHUNK)), dim3(BX, BY), 0,
-                               st>>>(g, v, rho[2], out[2]); WSI_COUNT(); }
+                               st>>>(g, gf, v, rho[2], out[2]); WSI_COUNT(); }
 }
 
-void launch_transport_flux(const GridDev& g, const double* const vel[3], const double* const rho[3],
-                           bool with_velocity, double* const out[3], bool fp32, cudaStream_t st) {
-  CVel<double> v{{vel[0], vel[1], vel[2]}};
+template <typename T>
+void launch_transport_flux(const GridDev& g, const T* const vel[3], const T* const rho[3], bool with_velocity,
+                           T* const out[3], cudaStream_t st) {
+  CVel<T> v{{vel[0], vel[1], vel[2]}};
   ktimer_begin(KC_TRANSPORT, st);
-  if (fp32) {
-    if (with_velocity) transport_all<true, float>(g, v, rho, out, st);
-    else transport_all<false, float>(g, v, rho, out, st);
-  } else {
-    if (with_velocity) transport_all<true, double>(g, v, rho, out, st);
-    else transport_all<false, double>(g, v, rho, out, st);
-  }
+  if (with_velocity)
+    transport_all<true, T>(g, v, rho, out, st);
+  else
+    transport_all<false, T>(g, v, rho, out, st);
   ktimer_end(KC_TRANSPORT, st);
 }
+template void launch_transport_flux<double>(const GridDev&, const double* const[3], const double* const[3], bool,
+                                            double* const[3], cudaStream_t);
+template void launch_transport_flux<float>(const GridDev&, const float* const[3], const float* const[3], bool,
+                                           float* const[3], cudaStream_t);
 
-__global__ void k_lincomb(size_t n, double a, const double* __restrict__ x, double b, const double* __restrict__ y,
-                          double c, const double* __restrict__ z, double* out) {
+template <typename Ti, typename To>
+__global__ void k_lincomb(size_t n, double a, const Ti* __restrict__ x, double b, const Ti* __restrict__ y, double c,
+                          const Ti* __restrict__ z, To* out) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t stride = (size_t)gridDim.x * blockDim.x;
   for (; t < n; t += stride) {
-    double s = a * x[t];
+    double s = a * (double)x[t];
+    if (y) s += b * (double)y[t];
+    if (z) s += c * (double)z[t];
+    out[t] = (To)s;
+  }
+}
+
+// same in float32 arithmetic (float32 inputs and outputs)
+__global__ void k_lincomb_f(size_t n, float a, const float* __restrict__ x, float b, const float* __restrict__ y,
+                            float c, const float* __restrict__ z, float* out) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (; t < n; t += stride) {
+    float s = a * x[t];
     if (y) s += b * y[t];
     if (z) s += c * z[t];
     out[t] = s;
   }
 }
 
+static int lc_blocks(size_t n) {
+  int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+  return blocks < 1 ? 1 : blocks;
+}
+
 void launch_lincomb(size_t n, double a, const double* x, double b, const double* y, double c, const double* z,
                     double* out, cudaStream_t st) {
-  int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
-  if (blocks < 1) blocks = 1;
-  { k_lincomb<<<blocks, 256, 0, st>>>(n, a, x, b, y, c, z, out); WSI_COUNT(); }
+  { k_lincomb<double, double><<<lc_blocks(n), 256, 0, st>>>(n, a, x, b, y, c, z, out); WSI_COUNT(); }
+}
+void launch_lincomb_to_f32(size_t n, double a, const double* x, double b, const double* y, double c,
+                           const double* z, float* out, cudaStream_t st) {
+  { k_lincomb<double, float><<<lc_blocks(n), 256, 0, st>>>(n, a, x, b, y, c, z, out); WSI_COUNT(); }
+}
+void launch_lincomb_f32(size_t n, float a, const float* x, float b, const float* y, float c, const float* z,
+                        float* out, cudaStream_t st) {
+  { k_lincomb_f<<<lc_blocks(n), 256, 0, st>>>(n, a, x, b, y, c, z, out); WSI_COUNT(); }
+}
+// out = a*x64 + b*y32 + c*z32 in float64
+__global__ void k_lincomb_mix(size_t n, double a, const double* __restrict__ x, double b, const float* __restrict__ y,
+                              double c, const float* __restrict__ z, double* out) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (; t < n; t += stride) out[t] = a * x[t] + b * (double)y[t] + c * (double)z[t];
+}
+void launch_lincomb_mix(size_t n, double a, const double* x, double b, const float* y, double c, const float* z,
+                        double* out, cudaStream_t st) {
+  { k_lincomb_mix<<<lc_blocks(n), 256, 0, st>>>(n, a, x, b, y, c, z, out); WSI_COUNT(); }
 }
 
 // ================================================================ level set
 template <int D, typename T>
-__device__ __forceinline__ T phi_ext(const GridDev& g, const double* __restrict__ a, const int i3[3], int m) {
+__device__ __forceinline__ T phi_ext(const GridDev& g, const T* __restrict__ a, const int i3[3], int m) {
   int n = g.n[D];
   int mm = m;
   if (m < 0) mm = -m - 1;
@@ -242,17 +282,17 @@ __device__ __forceinline__ T phi_ext(const GridDev& g, const double* __restrict_
   mm = clampi(mm, 0, n - 1);
   int c3[3] = {i3[0], i3[1], i3[2]};
   c3[D] = mm;
-  return (T)a[fidx(g, 3, c3[0], c3[1], c3[2])];
+  return a[fidx(g, 3, c3[0], c3[1], c3[2])];
 }
 
 // flux u_D phi_lim through the D-face at position `face` (between cells
 // face-1 and face) of the cell column through i3
 template <int D, typename T>
-__device__ __forceinline__ T ls_flux(const GridDev& g, const double* __restrict__ vel_d,
-                                     const double* __restrict__ phi, const int i3[3], int face) {
+__device__ __forceinline__ T ls_flux(const GridDev& g, const T* __restrict__ vel_d, const T* __restrict__ phi,
+                                     const int i3[3], int face) {
   int f3[3] = {i3[0], i3[1], i3[2]};
   f3[D] = face;
-  T a = (T)vel_d[fidx(g, D, f3[0], f3[1], f3[2])];
+  T a = vel_d[fidx(g, D, f3[0], f3[1], f3[2])];
   T lim;
   if (a > T(0))
     lim = cui<T>(phi_ext<D, T>(g, phi, i3, face - 2), phi_ext<D, T>(g, phi, i3, face - 1),
@@ -264,8 +304,9 @@ __device__ __forceinline__ T ls_flux(const GridDev& g, const double* __restrict_
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_ls_advect(GridDev g, CVel<double> vel, const double* __restrict__ phi_n,
-                                                      const double* __restrict__ phi_h, double dt, double* out) {
+__global__ void __launch_bounds__(BX* BY) k_ls_advect(GridDev g, GridF gf, CVel<T> vel,
+                                                      const double* __restrict__ phi_n, const T* __restrict__ phi_h,
+                                                      double dt, double* out) {
   __shared__ T sFx[BY][BX + 1];
   __shared__ T sFy[BY + 1][BX];
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -286,8 +327,8 @@ __global__ void __launch_bounds__(BX* BY) k_ls_advect(GridDev g, CVel<double> ve
     if (inside) {
       T Fz_hi = ls_flux<2, T>(g, vel.q[2], phi_h, i3, k + 1);
       if (k == k0) Fz_lo = ls_flux<2, T>(g, vel.q[2], phi_h, i3, k);
-      T Q = (sFx[ty][tx + 1] - sFx[ty][tx]) * (T)g.ih[0] + (sFy[ty + 1][tx] - sFy[ty][tx]) * (T)g.ih[1] +
-            (Fz_hi - Fz_lo) * (T)g.ih[2];
+      T Q = (sFx[ty][tx + 1] - sFx[ty][tx]) * ginv<T>(g, gf, 0) + (sFy[ty + 1][tx] - sFy[ty][tx]) * ginv<T>(g, gf, 1) +
+            (Fz_hi - Fz_lo) * ginv<T>(g, gf, 2);
       size_t id = fidx(g, 3, i, j, k);
       out[id] = phi_n[id] - dt * (double)Q;
       Fz_lo = Fz_hi;
@@ -296,18 +337,17 @@ __global__ void __launch_bounds__(BX* BY) k_ls_advect(GridDev g, CVel<double> ve
   }
 }
 
-void launch_levelset_advect(const GridDev& g, const double* const vel[3], const double* phi_n,
-                            const double* phi_half, double dt, double* out, bool fp32, cudaStream_t st) {
-  CVel<double> v{{vel[0], vel[1], vel[2]}};
+template <typename T>
+void launch_levelset_advect(const GridDev& g, const T* const vel[3], const double* phi_n, const T* phi_half, double dt,
+                            double* out, cudaStream_t st) {
+  CVel<T> v{{vel[0], vel[1], vel[2]}};
   dim3 grid(cdiv(g.n[0], BX), cdiv(g.n[1], BY), cdiv(g.n[2], ZCHUNK));
-  if (fp32) {
-    k_ls_advect<float><<<grid, dim3(BX, BY), 0, st>>>(g, v, phi_n, phi_half, dt, out);
-    WSI_COUNT();
-  } else {
-    k_ls_advect<double><<<grid, dim3(BX, BY), 0, st>>>(g, v, phi_n, phi_half, dt, out);
-    WSI_COUNT();
-  }
+  { k_ls_advect<T><<<grid, dim3(BX, BY), 0, st>>>(g, gridf(g), v, phi_n, phi_half, dt, out); WSI_COUNT(); }
 }
+template void launch_levelset_advect<double>(const GridDev&, const double* const[3], const double*, const double*,
+                                             double, double*, cudaStream_t);
+template void launch_levelset_advect<float>(const GridDev&, const float* const[3], const double*, const float*,
+                                            double, double*, cudaStream_t);
 
 __global__ void k_box_sdf(GridDev g, const double* __restrict__ xc, double hx_, double hy_, double hz_, double* psi) {
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
