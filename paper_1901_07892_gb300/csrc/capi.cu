@@ -100,6 +100,9 @@ struct wsi_ctx {
   bool has_body = false;
   // float64 part of the momentum right-hand side fixed over a step's cycles
   double* b0 = nullptr;
+  double* inv_mu = nullptr;  // materials scratch: 1/mu per cell
+  // a fully locked body at rest never moves: psi is rebuilt once, then kept
+  bool psi_static_done = false;
   // float32 shadows of the explicitly transported fields (mixed path)
   float *vn32 = nullptr, *u1_32 = nullptr, *u2_32 = nullptr, *rn32 = nullptr, *r1_32 = nullptr, *r2_32 = nullptr,
         *R32 = nullptr, *C32 = nullptr, *vh32 = nullptr, *phih32 = nullptr, *mu_cc_n32 = nullptr,
@@ -168,6 +171,7 @@ PhaseConst phase_const(wsi_ctx* c) {
   pc.mu_s = c->props.mu_s;
   double hc = c->g.n[2] == 1 ? sqrt(c->g.h[0] * c->g.h[1]) : cbrt(c->g.h[0] * c->g.h[1] * c->g.h[2]);
   pc.eps = c->desc.n_cells * hc;
+  pc.inv_mu = c->inv_mu;
   return pc;
 }
 
@@ -267,18 +271,40 @@ int fgmres(wsi_ctx* c, const double* b, double* x, double dt, const wsi_solve_op
       pc_apply(c, dt, Vj(j), Zj(j));
       double* w = Vj(j + 1);
       launch_stokes(c->g, cf, inv_dt, theta, Zj(j), w, c->st);
-      // CGS2
-      launch_mdot(V, n, j + 1, w, n, hd, red, c->st);
-      launch_maxpy(V, n, j + 1, hd, w, n, 1.0, c->st);
-      launch_mdot(V, n, j + 1, w, n, hd + (m + 1), red, c->st);
-      launch_maxpy(V, n, j + 1, hd + (m + 1), w, n, 1.0, c->st);
-      launch_mdot(w, n, 1, w, n, hd + 2 * (m + 1), red, c->st);
-      cudaMemcpyAsync(hcol.data(), hd, (2 * (m + 1) + 1) * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+      // Classical Gram-Schmidt.  One pass gives h = V^T w together with w.w
+      // (w is V_{j+1}, the last row), so ||w - V h||^2 = w.w - |h|^2 needs no
+      // second pass; when that cancels by more than half (the DGKS test) the
+      // vector is orthogonalised a second time.  The final axpy also
+      // normalises.
+      const size_t o2 = (size_t)m + 2, osc = 2 * (size_t)m + 4;
+      launch_mdot(V, n, j + 2, w, n, hd, red, c->st);
+      cudaMemcpyAsync(hcol.data(), hd, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, c->st);
       if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "fgmres iteration");
       ++iters;
-      double hn = sqrt(std::max(hcol[2 * (m + 1)], 0.0));
+      double ww = hcol[j + 1], hh = 0.0;
+      for (int i = 0; i <= j; ++i) hh += hcol[i] * hcol[i];
+      double hn2 = ww - hh;
+      std::vector<double> hsum(hcol.begin(), hcol.begin() + (j + 1));
+      const double* hcoef = hd;
+      if (!(hn2 >= 0.5 * ww)) {
+        launch_maxpy(V, n, j + 1, hd, w, n, 1.0, c->st);
+        launch_mdot(V, n, j + 2, w, n, hd + o2, red, c->st);
+        cudaMemcpyAsync(hcol.data(), hd + o2, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+        if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "fgmres reorthogonalisation");
+        double ww2 = hcol[j + 1], hh2 = 0.0;
+        for (int i = 0; i <= j; ++i) {
+          hh2 += hcol[i] * hcol[i];
+          hsum[i] += hcol[i];
+        }
+        hn2 = ww2 - hh2;
+        hcoef = hd + o2;
+      }
+      double hn = sqrt(std::max(hn2, 0.0));
       if (!std::isfinite(hn)) return fail(c, WSI_ERR_NAN, "non-finite Krylov vector");
-      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i] + hcol[(m + 1) + i];
+      double ihn = hn > 0.0 ? 1.0 / hn : 0.0;
+      cudaMemcpyAsync(hd + osc, &ihn, sizeof(double), cudaMemcpyHostToDevice, c->st);
+      launch_maxpy(V, n, j + 1, hcoef, w, n, 1.0, c->st, hd + osc);
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hsum[i];
       H[(size_t)(j + 1) * m + j] = hn;
       // previous rotations
       for (int i = 0; i < j; ++i) {
@@ -295,11 +321,6 @@ int fgmres(wsi_ctx* c, const double* b, double* x, double dt, const wsi_solve_op
       gv[j + 1] = -sn[j] * gv[j];
       gv[j] = cs[j] * gv[j];
       double res = fabs(gv[j + 1]);
-      if (hn > 0.0) {
-        double ihn = 1.0 / hn;
-        cudaMemcpyAsync(hd + 2 * (m + 1) + 1, &ihn, sizeof(double), cudaMemcpyHostToDevice, c->st);
-        launch_scale(w, n, hd + 2 * (m + 1) + 1, false, c->st);
-      }
       if (res <= tol || iters >= o->max_iters || hn == 0.0) {
         ++j;
         done = true;
@@ -643,6 +664,7 @@ int wsi_create_grid(const wsi_grid_desc* d, void* stream, wsi_ctx** out) {
   c->Z = A(c->nstk * (size_t)c->m);
   c->hdev = A(4 * (c->m + 2) + 8);
   c->b0 = A(c->nvel);
+  c->inv_mu = A(c->ncell);
   if (d->precision == WSI_PREC_MIXED) {
     // float32 shadows: half-size double allocations reinterpreted
     auto F = [&](size_t n) { return (float*)A((n + 1) / 2); };
@@ -740,6 +762,7 @@ int wsi_set_phases(wsi_ctx* c, const double* phi, const double* psi, const wsi_p
   cudaMemsetAsync(c->vel_old, 0, c->nvel * sizeof(double), c->st);
   cudaMemsetAsync(c->p, 0, c->ncell * sizeof(double), c->st);
   c->have_phases = true;
+  c->psi_static_done = false;
   c->pc_dirty = true;
   return cuda_check(c, "set_phases");
 }
@@ -817,10 +840,14 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
     // 1. level sets and viscosity at (n+1, k+1)
     levelset_stage(c, c->vel_k, c->vel, c->phi_k, c->phi, dt, c->phi_new);
     const double* psi_use = c->psi_k;
-    if (c->has_body && B.shape == 1) {
+    const bool at_rest = B.lock[0] && B.lock[1] && B.lock[2] && B.lock[3] && B.lock[4] && B.lock[5] &&
+                         B.U_pres[0] == 0.0 && B.U_pres[1] == 0.0 && B.U_pres[2] == 0.0 && B.W_pres[0] == 0.0 &&
+                         B.W_pres[1] == 0.0 && B.W_pres[2] == 0.0;
+    if (c->has_body && B.shape == 1 && !(at_rest && c->psi_static_done)) {
       launch_marker_mean(B.X, B.n, B.xc, B.scratch, st);
       launch_box_sdf(g, B.xc, B.half, c->psi_new, st);
       psi_use = c->psi_new;
+      if (at_rest && k + 1 == ncyc) c->psi_static_done = true;
     }
     launch_materials(g, pc, c->phi_new, psi_use, c->rho_cc, c->mu_cc, c->rho_face, c->beta, c->rho_flow, c->mu_e,
                      st);
@@ -903,7 +930,10 @@ int wsi_set_field(wsi_ctx* c, int which, const double* src) {
     case WSI_F_VEL_OLD: rc = copy_in(c, c->vel_old, src, c->nvel); break;
     case WSI_F_P: rc = copy_in(c, c->p, src, c->ncell); break;
     case WSI_F_PHI: rc = copy_in(c, c->phi, src, c->ncell); break;
-    case WSI_F_PSI: rc = copy_in(c, c->psi, src, c->ncell); break;
+    case WSI_F_PSI:
+      rc = copy_in(c, c->psi, src, c->ncell);
+      c->psi_static_done = false;
+      break;
     default: return fail(c, WSI_ERR_INVALID_ARG, "unknown field");
   }
   if (rc) return rc;

@@ -55,7 +55,7 @@ __device__ __forceinline__ void taps_axis(const GridDev& g, int c, int d, double
 __global__ void k_interp(GridDev g, CVel<double> vel, const double* __restrict__ X, int n, double* U) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * n) return;
-  int m = t / 3, c = t - 3 * m;
+  int c = t / n, m = t - c * n;  // neighbouring threads: neighbouring markers
   Tap tx, ty, tz;
   taps_axis(g, c, 0, X[3 * m + 0], tx);
   taps_axis(g, c, 1, X[3 * m + 1], ty);
@@ -80,7 +80,7 @@ __global__ void k_spread(GridDev g, const double* __restrict__ F, const double* 
                          Vel<double> vel) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * n) return;
-  int m = t / 3, c = t - 3 * m;
+  int c = t / n, m = t - c * n;  // neighbouring threads: neighbouring markers
   Tap tx, ty, tz;
   taps_axis(g, c, 0, X[3 * m + 0], tx);
   taps_axis(g, c, 1, X[3 * m + 1], ty);

@@ -22,6 +22,7 @@ struct Coef {
 // ---------------------------------------------------------------- ops.cu
 struct PhaseConst {
   double rho_l, rho_g, rho_s, mu_l, mu_g, mu_s, eps;
+  double* inv_mu;  // scratch of one cell field for 1/mu (null: edges divide per access)
 };
 void launch_materials(const GridDev& g, const PhaseConst& pc, const double* phi, const double* psi,
                       double* rho_cc, double* mu_cc, double* const rho_face[3], double* const beta[3],
@@ -87,9 +88,10 @@ void launch_zero_walls(const GridDev& g, double* const q[3], cudaStream_t st);
 // deterministic reductions: out[t] = <V_t, w> for t < m (V row-major m x n)
 void launch_mdot(const double* V, size_t ldv, int m, const double* w, size_t n, double* out, double* scratch,
                  cudaStream_t st);
-// w -= sum_t h[t] V_t  (h on device)
+// w = (w - sign * sum_t h[t] V_t) * scale  (h and scale on device; scale
+// null = 1)
 void launch_maxpy(const double* V, size_t ldv, int m, const double* h, double* w, size_t n, double sign,
-                  cudaStream_t st);
+                  cudaStream_t st, const double* scale_dev = nullptr);
 void launch_scale(double* x, size_t n, const double* s_dev, bool inverse, cudaStream_t st);
 template <typename Ts, typename Td>
 void launch_cast(const Ts* in, Td* out, size_t n, cudaStream_t st);

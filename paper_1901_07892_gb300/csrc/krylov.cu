@@ -43,13 +43,23 @@ __global__ void k_mdot(const double* __restrict__ V, size_t ldv, int m, const do
   }
 }
 
+// one block per output t < m: the block's threads stride over the nblocks
+// partials in a fixed pattern and combine them with a fixed tree
 __global__ void k_reduce_parts(const double* __restrict__ part, int nblocks, int M, int m, double* out) {
-  // one thread per output, summing block partials in block order
-  int t = threadIdx.x;
+  int t = blockIdx.x;
   if (t >= m) return;
   double s = 0.0;
-  for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * M + t];
-  out[t] = s;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += part[(size_t)b * M + t];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  __shared__ double sh[32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a += sh[q];
+    out[t] = a;
+  }
 }
 
 void launch_mdot(const double* V, size_t ldv, int m, const double* w, size_t n, double* out, double* scratch,
@@ -59,29 +69,32 @@ void launch_mdot(const double* V, size_t ldv, int m, const double* w, size_t n, 
     ktimer_begin(KC_MDOT, st);
     { k_mdot<NV><<<RB, RT, 0, st>>>(V + (size_t)t0 * ldv, ldv, mm, w, n, scratch); WSI_COUNT(); }
     ktimer_end(KC_MDOT, st);
-    { k_reduce_parts<<<1, 32, 0, st>>>(scratch, RB, NV, mm, out + t0); WSI_COUNT(); }
+    { k_reduce_parts<<<mm, 256, 0, st>>>(scratch, RB, NV, mm, out + t0); WSI_COUNT(); }
   }
 }
 
+// w = (w - sign * sum_t h[t] V_t) * scale[0]   (scale may be null: 1)
 __global__ void k_maxpy(const double* __restrict__ V, size_t ldv, int m, const double* __restrict__ h, double* w,
-                        size_t n, double sign) {
+                        size_t n, double sign, const double* __restrict__ scale) {
   __shared__ double hs[64];
-  if (threadIdx.x < m && threadIdx.x < 64) hs[threadIdx.x] = h[threadIdx.x];
+  if (threadIdx.x < m && threadIdx.x < 64) hs[threadIdx.x] = sign * h[threadIdx.x];
   __syncthreads();
+  const double f = scale ? scale[0] : 1.0;
   size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     double s = w[i];
-    for (int t = 0; t < m; ++t) s -= sign * hs[t] * V[(size_t)t * ldv + i];
-    w[i] = s;
+    for (int t = 0; t < m; ++t) s -= hs[t] * V[(size_t)t * ldv + i];
+    w[i] = scale ? s * f : s;
   }
 }
 
 void launch_maxpy(const double* V, size_t ldv, int m, const double* h, double* w, size_t n, double sign,
-                  cudaStream_t st) {
+                  cudaStream_t st, const double* scale_dev) {
   for (int t0 = 0; t0 < m; t0 += 64) {
     int mm = std::min(64, m - t0);
+    const double* sc = (t0 + 64 >= m) ? scale_dev : nullptr;
     ktimer_begin(KC_MAXPY, st);
-    { k_maxpy<<<RB, RT, 0, st>>>(V + (size_t)t0 * ldv, ldv, mm, h + t0, w, n, sign); WSI_COUNT(); }
+    { k_maxpy<<<RB, RT, 0, st>>>(V + (size_t)t0 * ldv, ldv, mm, h + t0, w, n, sign, sc); WSI_COUNT(); }
     ktimer_end(KC_MAXPY, st);
   }
 }
@@ -127,13 +140,13 @@ __global__ void k_sum(const T* __restrict__ x, size_t n, double* part) {
 template <typename T>
 void launch_sum(const T* x, size_t n, double* out_dev, double* scratch, cudaStream_t st) {
   { k_sum<T><<<RB, RT, 0, st>>>(x, n, scratch); WSI_COUNT(); }
-  { k_reduce_parts<<<1, 32, 0, st>>>(scratch, RB, 1, 1, out_dev); WSI_COUNT(); }
+  { k_reduce_parts<<<1, 256, 0, st>>>(scratch, RB, 1, 1, out_dev); WSI_COUNT(); }
 }
 
 double host_norm2(const double* x, size_t n, double* scratch, cudaStream_t st) {
   // scratch: RB + 1 doubles on the device
   { k_mdot<1><<<RB, RT, 0, st>>>(x, 0, 1, x, n, scratch); WSI_COUNT(); }
-  { k_reduce_parts<<<1, 32, 0, st>>>(scratch, RB, 1, 1, scratch + RB); WSI_COUNT(); }
+  { k_reduce_parts<<<1, 256, 0, st>>>(scratch, RB, 1, 1, scratch + RB); WSI_COUNT(); }
   double h = 0.0;
   cudaMemcpyAsync(&h, scratch + RB, sizeof(double), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);

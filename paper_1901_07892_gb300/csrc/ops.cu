@@ -41,7 +41,9 @@ __global__ void k_mat_cells(GridDev g, PhaseConst pc, const double* __restrict__
   size_t id = fidx(g, 3, i, j, k);
   double a = phi[id], b = psi[id];
   if (rho_cc) rho_cc[id] = two_stage(a, b, pc.rho_l, pc.rho_g, pc.rho_s, pc.eps);
-  mu_cc[id] = two_stage(a, b, pc.mu_l, pc.mu_g, pc.mu_s, pc.eps);
+  double mu = two_stage(a, b, pc.mu_l, pc.mu_g, pc.mu_s, pc.eps);
+  mu_cc[id] = mu;
+  if (pc.inv_mu) pc.inv_mu[id] = 1.0 / mu;
 }
 
 // face density from face-averaged level sets (wall faces: the interior cell)
@@ -63,9 +65,13 @@ __global__ void k_mat_faces(GridDev g, PhaseConst pc, const double* __restrict__
   if (rho_flow) rho_flow[id] = pc.rho_l + (pc.rho_g - pc.rho_l) * heaviside(pa, pc.eps);
 }
 
-// harmonic mean of the 4 cells around an edge (mirror ghosts at walls)
+// Harmonic mean 4 / sum(1/mu) of the 4 cells around an edge (mirror ghosts
+// at walls).  The reciprocals come precomputed once per cell when inv_mu is
+// given: a float64 division costs tens of instructions at GB300's float64
+// rate, and each cell feeds twelve edges.
 template <int E>
-__global__ void k_mat_edges(GridDev g, const double* __restrict__ mu_cc, double* mu_e) {
+__global__ void k_mat_edges(GridDev g, const double* __restrict__ mu_cc, const double* __restrict__ inv_mu,
+                            double* mu_e) {
   // E = 0: xy edges, 1: xz, 2: yz
   constexpr int A1 = (E == 2) ? 1 : 0;
   constexpr int A2 = (E == 0) ? 1 : 2;
@@ -80,7 +86,7 @@ __global__ void k_mat_edges(GridDev g, const double* __restrict__ mu_cc, double*
       int c[3] = {i, j, k};
       c[A1] -= o1;
       c[A2] -= o2;
-      s += 1.0 / cell_at(g, mu_cc, c[0], c[1], c[2]);
+      s += inv_mu ? cell_at(g, inv_mu, c[0], c[1], c[2]) : 1.0 / cell_at(g, mu_cc, c[0], c[1], c[2]);
     }
   mu_e[eidx(g, E, i, j, k)] = 4.0 / s;
 }
@@ -95,17 +101,17 @@ void launch_materials(const GridDev& g, const PhaseConst& pc, const double* phi,
                                                                              rho_flow[1]); WSI_COUNT(); }
   { k_mat_faces<2><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, rho_face[2], beta[2],
                                                                              rho_flow[2]); WSI_COUNT(); }
-  { k_mat_edges<0><<<grid3(g.n[0] + 1, g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[0]); WSI_COUNT(); }
-  { k_mat_edges<1><<<grid3(g.n[0] + 1, g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[1]); WSI_COUNT(); }
-  { k_mat_edges<2><<<grid3(g.n[0], g.n[1] + 1, g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[2]); WSI_COUNT(); }
+  { k_mat_edges<0><<<grid3(g.n[0] + 1, g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, mu_cc, pc.inv_mu, mu_e[0]); WSI_COUNT(); }
+  { k_mat_edges<1><<<grid3(g.n[0] + 1, g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, pc.inv_mu, mu_e[1]); WSI_COUNT(); }
+  { k_mat_edges<2><<<grid3(g.n[0], g.n[1] + 1, g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, pc.inv_mu, mu_e[2]); WSI_COUNT(); }
 }
 
 void launch_mu_only(const GridDev& g, const PhaseConst& pc, const double* phi, const double* psi, double* mu_cc,
                     double* const mu_e[3], cudaStream_t st) {
   { k_mat_cells<<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, nullptr, mu_cc); WSI_COUNT(); }
-  { k_mat_edges<0><<<grid3(g.n[0] + 1, g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[0]); WSI_COUNT(); }
-  { k_mat_edges<1><<<grid3(g.n[0] + 1, g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[1]); WSI_COUNT(); }
-  { k_mat_edges<2><<<grid3(g.n[0], g.n[1] + 1, g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, mu_e[2]); WSI_COUNT(); }
+  { k_mat_edges<0><<<grid3(g.n[0] + 1, g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, mu_cc, pc.inv_mu, mu_e[0]); WSI_COUNT(); }
+  { k_mat_edges<1><<<grid3(g.n[0] + 1, g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, pc.inv_mu, mu_e[1]); WSI_COUNT(); }
+  { k_mat_edges<2><<<grid3(g.n[0], g.n[1] + 1, g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, pc.inv_mu, mu_e[2]); WSI_COUNT(); }
 }
 
 void launch_rho_flow(const GridDev& g, const PhaseConst& pc, const double* phi, double* const rho_flow[3],
