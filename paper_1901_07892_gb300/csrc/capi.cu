@@ -103,6 +103,8 @@ struct wsi_ctx {
   double* inv_mu = nullptr;  // materials scratch: 1/mu per cell
   // a fully locked body at rest never moves: psi is rebuilt once, then kept
   bool psi_static_done = false;
+  // mu_cc / mu_e hold mu(phi^n, psi^n) (true right after a step)
+  bool mat_n_valid = false;
   // float32 shadows of the explicitly transported fields (mixed path)
   float *vn32 = nullptr, *u1_32 = nullptr, *u2_32 = nullptr, *rn32 = nullptr, *r1_32 = nullptr, *r2_32 = nullptr,
         *R32 = nullptr, *C32 = nullptr, *vh32 = nullptr, *phih32 = nullptr, *mu_cc_n32 = nullptr,
@@ -763,6 +765,7 @@ int wsi_set_phases(wsi_ctx* c, const double* phi, const double* psi, const wsi_p
   cudaMemsetAsync(c->p, 0, c->ncell * sizeof(double), c->st);
   c->have_phases = true;
   c->psi_static_done = false;
+  c->mat_n_valid = false;
   c->pc_dirty = true;
   return cuda_check(c, "set_phases");
 }
@@ -827,9 +830,17 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
   PhaseConst pc = phase_const(c);
   Body& B = c->body;
   const size_t nv = c->nvel, nc = c->ncell;
-  // time-n coefficients: face density rho^n and mu^n from (phi^n, psi^n)
-  launch_materials(g, pc, c->phi, c->psi, c->rho_cc_tmp, c->mu_cc_n, c->rho_n, c->beta_n, c->rho_flow_n, c->mu_e_n,
-                   st);
+  // time-n coefficients: face density rho^n and mu^n from (phi^n, psi^n).
+  // After a step, the viscosity of its last cycle is already mu^n.
+  if (c->mat_n_valid) {
+    std::swap(c->mu_cc, c->mu_cc_n);
+    for (int e = 0; e < 3; ++e) std::swap(c->mu_e[e], c->mu_e_n[e]);
+    launch_face_density(g, pc, c->phi, c->psi, c->rho_n, st);
+  } else {
+    launch_materials(g, pc, c->phi, c->psi, c->rho_cc_tmp, c->mu_cc_n, c->rho_n, c->beta_n, c->rho_flow_n, c->mu_e_n,
+                     st);
+  }
+  c->mat_n_valid = false;
   cudaMemcpyAsync(c->vel_k, c->vel, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(c->phi_k, c->phi, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(c->psi_k, c->psi, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
@@ -893,6 +904,7 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
   if (c->has_body) cudaMemcpyAsync(B.Ub_n, B.Ub, (size_t)B.n * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
   int rc = cuda_check(c, "step");
   if (rc) return rc;
+  c->mat_n_valid = true;
   if (s) {
     s->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     s->umax = 0.0;
@@ -929,10 +941,14 @@ int wsi_set_field(wsi_ctx* c, int which, const double* src) {
       break;
     case WSI_F_VEL_OLD: rc = copy_in(c, c->vel_old, src, c->nvel); break;
     case WSI_F_P: rc = copy_in(c, c->p, src, c->ncell); break;
-    case WSI_F_PHI: rc = copy_in(c, c->phi, src, c->ncell); break;
+    case WSI_F_PHI:
+      rc = copy_in(c, c->phi, src, c->ncell);
+      c->mat_n_valid = false;
+      break;
     case WSI_F_PSI:
       rc = copy_in(c, c->psi, src, c->ncell);
       c->psi_static_done = false;
+      c->mat_n_valid = false;
       break;
     default: return fail(c, WSI_ERR_INVALID_ARG, "unknown field");
   }
@@ -1024,6 +1040,8 @@ int wsi_transport(wsi_ctx* c, const double* u_n, const double* u_nm1, const doub
   // are formed, so copy u^{n-1} aside first
   cudaMemcpyAsync(c->vel_old, c->rs2, nv * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
   transport_stage(c, k, dt, c->vel_half, c->vel_old, c->vel_k, false);
+  c->mat_n_valid = false;  // the operator coefficients now hold the transported density
+  c->pc_dirty = true;
   double* rq[3];
   parts(c, c->b, rq);
   for (int d = 0; d < 3; ++d)

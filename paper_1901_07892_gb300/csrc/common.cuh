@@ -40,37 +40,37 @@ struct GridDev {
   double ih[3];   // 1/h (set by grid_finalize)
   double ih2[3];  // 1/h^2
   double bc[6];   // tangential ghost sign per wall (x-, x+, y-, y+, z-, z+)
+  // float32 copies for float32 kernels (a float64->float32 conversion issues
+  // on the narrow float64 pipe, so kernels never convert these per thread)
+  float ihf[3], ih2f[3], bcf[6];
 };
-// float32 copies of the inverse spacings for float32 kernels
-struct GridF {
-  float ih[3], ih2[3];
-};
-inline GridF gridf(const GridDev& g) {
-  GridF f;
-  for (int a = 0; a < 3; ++a) {
-    f.ih[a] = (float)g.ih[a];
-    f.ih2[a] = (float)g.ih2[a];
-  }
-  return f;
-}
 template <typename T>
-__device__ __forceinline__ T ginv(const GridDev& g, const GridF& f, int a);
+__host__ __device__ __forceinline__ T ginv(const GridDev& g, int a);
 template <>
-__device__ __forceinline__ double ginv<double>(const GridDev& g, const GridF&, int a) { return g.ih[a]; }
+__host__ __device__ __forceinline__ double ginv<double>(const GridDev& g, int a) { return g.ih[a]; }
 template <>
-__device__ __forceinline__ float ginv<float>(const GridDev&, const GridF& f, int a) { return f.ih[a]; }
+__host__ __device__ __forceinline__ float ginv<float>(const GridDev& g, int a) { return g.ihf[a]; }
 template <typename T>
-__device__ __forceinline__ T ginv2(const GridDev& g, const GridF& f, int a);
+__host__ __device__ __forceinline__ T ginv2(const GridDev& g, int a);
 template <>
-__device__ __forceinline__ double ginv2<double>(const GridDev& g, const GridF&, int a) { return g.ih2[a]; }
+__host__ __device__ __forceinline__ double ginv2<double>(const GridDev& g, int a) { return g.ih2[a]; }
 template <>
-__device__ __forceinline__ float ginv2<float>(const GridDev&, const GridF& f, int a) { return f.ih2[a]; }
+__host__ __device__ __forceinline__ float ginv2<float>(const GridDev& g, int a) { return g.ih2f[a]; }
+template <typename T>
+__host__ __device__ __forceinline__ T gbc(const GridDev& g, int a);
+template <>
+__host__ __device__ __forceinline__ double gbc<double>(const GridDev& g, int a) { return g.bc[a]; }
+template <>
+__host__ __device__ __forceinline__ float gbc<float>(const GridDev& g, int a) { return g.bcf[a]; }
 
 inline void grid_finalize(GridDev& g) {
   for (int a = 0; a < 3; ++a) {
     g.ih[a] = 1.0 / g.h[a];
     g.ih2[a] = 1.0 / (g.h[a] * g.h[a]);
+    g.ihf[a] = (float)g.ih[a];
+    g.ih2f[a] = (float)g.ih2[a];
   }
+  for (int a = 0; a < 6; ++a) g.bcf[a] = (float)g.bc[a];
 }
 
 __host__ __device__ __forceinline__ int ext(const GridDev& g, int c, int a) {
@@ -133,6 +133,36 @@ __device__ __forceinline__ T qget(const GridDev& g, const T* __restrict__ q, int
 }
 
 __device__ __forceinline__ int clampi(int a, int lo, int hi) { return a < lo ? lo : (a > hi ? hi : a); }
+
+// float64 -> float32 by integer operations on the IEEE-754 bit patterns:
+// sign, exponent rebiased by 1023 - 127, top 23 significand bits, rounded
+// half-up on the 24th dropped bit (a carry may move into the exponent, which
+// is the correct rounding).  |a| < 2^-126 flushes to signed zero; overflow,
+// infinities and NaN become infinity.  The hardware conversion issues on
+// the float64 pipe, which on GB300 runs at 1/64 of the float32 rate; this
+// one runs on the integer pipes.
+__device__ __forceinline__ float d2f_fast(double a) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(a);
+  unsigned int hi = (unsigned int)(b >> 32);
+  unsigned int sign = hi & 0x80000000u;
+  int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
+  unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  unsigned int f = ((unsigned int)e << 23) | (unsigned int)(m >> 29);
+  f += (unsigned int)(m >> 28) & 1u;
+  if (f >= 0x7F800000u) f = 0x7F800000u;
+  return __uint_as_float(sign | f);
+}
+
+template <typename To, typename Ti>
+__device__ __forceinline__ To cvt(Ti a) {
+  return (To)a;
+}
+template <>
+__device__ __forceinline__ float cvt<float, double>(double a) {
+  return d2f_fast(a);
+}
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 

@@ -27,6 +27,9 @@ struct PhaseConst {
 void launch_materials(const GridDev& g, const PhaseConst& pc, const double* phi, const double* psi,
                       double* rho_cc, double* mu_cc, double* const rho_face[3], double* const beta[3],
                       double* const rho_flow[3], double* const mu_e[3], cudaStream_t st);
+// level-set face density only (Sec. 4.2.2: rho^n from phi^n, psi^n on faces)
+void launch_face_density(const GridDev& g, const PhaseConst& pc, const double* phi, const double* psi,
+                         double* const rho_face[3], cudaStream_t st);
 void launch_mu_only(const GridDev& g, const PhaseConst& pc, const double* phi, const double* psi,
                     double* mu_cc, double* const mu_e[3], cudaStream_t st);
 void launch_rho_flow(const GridDev& g, const PhaseConst& pc, const double* phi, double* const rho_flow[3],

@@ -20,12 +20,20 @@ __global__ void k_mdot(const double* __restrict__ V, size_t ldv, int m, const do
   double acc[M];
 #pragma unroll
   for (int t = 0; t < M; ++t) acc[t] = 0.0;
+  // four independent elements per iteration keep enough loads in flight
+  // to cover HBM latency
   size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    double wi = w[i];
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 4 * stride) {
+    double wi[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) wi[u] = (i + u * stride < n) ? w[i + u * stride] : 0.0;
 #pragma unroll
     for (int t = 0; t < M; ++t)
-      if (t < m) acc[t] += V[(size_t)t * ldv + i] * wi;
+      if (t < m) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (i + u * stride < n) acc[t] += V[(size_t)t * ldv + i + u * stride] * wi[u];
+      }
   }
   __shared__ double sh[RT / 32][M];
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -81,10 +89,18 @@ __global__ void k_maxpy(const double* __restrict__ V, size_t ldv, int m, const d
   __syncthreads();
   const double f = scale ? scale[0] : 1.0;
   size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    double s = w[i];
-    for (int t = 0; t < m; ++t) s -= hs[t] * V[(size_t)t * ldv + i];
-    w[i] = scale ? s * f : s;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += 4 * stride) {
+    double s[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s[u] = (i + u * stride < n) ? w[i + u * stride] : 0.0;
+    for (int t = 0; t < m; ++t) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i + u * stride < n) s[u] -= hs[t] * V[(size_t)t * ldv + i + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (i + u * stride < n) w[i + u * stride] = scale ? s[u] * f : s[u];
   }
 }
 

@@ -124,7 +124,7 @@ template <typename Ts, typename Td>
 __global__ void k_cast_arr(const Ts* __restrict__ a, Td* b, size_t n) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (; t < n; t += stride) b[t] = (Td)a[t];
+  for (; t < n; t += stride) b[t] = cvt<Td, Ts>(a[t]);
 }
 template <typename Ts, typename Td>
 static void cast_arr(const Ts* a, Td* b, size_t n, cudaStream_t st) {
@@ -240,7 +240,7 @@ __global__ void k_rbgs_p(GridDev g, const T* __restrict__ bx, const T* __restric
   if (i >= g.n[0] || j >= g.n[1]) return;
   if (((i + j + k) & 1) != color) return;
   size_t id = fidx(g, 3, i, j, k);
-  T ihx2 = (T)g.ih2[0], ihy2 = (T)g.ih2[1], ihz2 = (T)g.ih2[2];
+  T ihx2 = ginv2<T>(g, 0), ihy2 = ginv2<T>(g, 1), ihz2 = ginv2<T>(g, 2);
   T s = T(0), d = T(0);
   if (i + 1 < g.n[0]) { T c = bx[fidx(g, 0, i + 1, j, k)] * ihx2; s += c * x[id + 1]; d += c; }
   if (i > 0) { T c = bx[fidx(g, 0, i, j, k)] * ihx2; s += c * x[id - 1]; d += c; }
@@ -257,7 +257,7 @@ __device__ __forceinline__ T lap_at(const GridDev& g, const T* __restrict__ bx, 
                                     const T* __restrict__ bz, const T* __restrict__ x, int i, int j, int k) {
   size_t id = fidx(g, 3, i, j, k);
   T xc = x[id];
-  T ihx2 = (T)g.ih2[0], ihy2 = (T)g.ih2[1], ihz2 = (T)g.ih2[2];
+  T ihx2 = ginv2<T>(g, 0), ihy2 = ginv2<T>(g, 1), ihz2 = ginv2<T>(g, 2);
   T s = T(0);
   if (i + 1 < g.n[0]) s += bx[fidx(g, 0, i + 1, j, k)] * (x[id + 1] - xc) * ihx2;
   if (i > 0) s -= bx[fidx(g, 0, i, j, k)] * (xc - x[id - 1]) * ihx2;
@@ -380,9 +380,9 @@ __global__ void k_div_add(GridDev g, const T* __restrict__ u, const T* __restric
                           const T* __restrict__ rp, T* y) {
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (i >= g.n[0] || j >= g.n[1]) return;
-  T d = (u[fidx(g, 0, i + 1, j, k)] - u[fidx(g, 0, i, j, k)]) * (T)g.ih[0] +
-        (v[fidx(g, 1, i, j + 1, k)] - v[fidx(g, 1, i, j, k)]) * (T)g.ih[1] +
-        (w[fidx(g, 2, i, j, k + 1)] - w[fidx(g, 2, i, j, k)]) * (T)g.ih[2];
+  T d = (u[fidx(g, 0, i + 1, j, k)] - u[fidx(g, 0, i, j, k)]) * ginv<T>(g, 0) +
+        (v[fidx(g, 1, i, j + 1, k)] - v[fidx(g, 1, i, j, k)]) * ginv<T>(g, 1) +
+        (w[fidx(g, 2, i, j, k + 1)] - w[fidx(g, 2, i, j, k)]) * ginv<T>(g, 2);
   size_t id = fidx(g, 3, i, j, k);
   y[id] = rp[id] + d;
 }
@@ -401,7 +401,7 @@ __global__ void k_vel_update(GridDev g, const T* __restrict__ ut, const T* __res
   }
   int lo[3] = {i, j, k};
   lo[C] -= 1;
-  T gphi = (phi[fidx(g, 3, i, j, k)] - phi[fidx(g, 3, lo[0], lo[1], lo[2])]) * (T)g.ih[C];
+  T gphi = (phi[fidx(g, 3, i, j, k)] - phi[fidx(g, 3, lo[0], lo[1], lo[2])]) * ginv<T>(g, C);
   z[id] = (double)(ut[id] - beta[id] * gphi);
 }
 

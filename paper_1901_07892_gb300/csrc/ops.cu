@@ -106,6 +106,16 @@ void launch_materials(const GridDev& g, const PhaseConst& pc, const double* phi,
   { k_mat_edges<2><<<grid3(g.n[0], g.n[1] + 1, g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, pc.inv_mu, mu_e[2]); WSI_COUNT(); }
 }
 
+void launch_face_density(const GridDev& g, const PhaseConst& pc, const double* phi, const double* psi,
+                         double* const rho_face[3], cudaStream_t st) {
+  { k_mat_faces<0><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, rho_face[0], nullptr,
+                                                                             nullptr); WSI_COUNT(); }
+  { k_mat_faces<1><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, rho_face[1], nullptr,
+                                                                             nullptr); WSI_COUNT(); }
+  { k_mat_faces<2><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, rho_face[2], nullptr,
+                                                                             nullptr); WSI_COUNT(); }
+}
+
 void launch_mu_only(const GridDev& g, const PhaseConst& pc, const double* phi, const double* psi, double* mu_cc,
                     double* const mu_e[3], cudaStream_t st) {
   { k_mat_cells<<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, nullptr, mu_cc); WSI_COUNT(); }
@@ -132,7 +142,7 @@ template <int C, typename T>
 __device__ __forceinline__ T strain_at(const GridDev& g, const Coef<T>& cf, const T* const* q, int i, int j, int k,
                                        T* diag) {
   const T* qc = q[C];
-  const T ihC = (T)g.ih[C];
+  const T ihC = ginv<T>(g, C);
   int id3[3] = {i, j, k};
   T q0 = qc[fidx(g, C, i, j, k)];
   // normal stress: cells hi = face index along C, lo = index - 1
@@ -150,7 +160,7 @@ __device__ __forceinline__ T strain_at(const GridDev& g, const Coef<T>& cf, cons
   for (int D = 0; D < 3; ++D) {
     if (D == C) continue;
     const int E = edge_id(C, D);
-    const T ihD = (T)g.ih[D];
+    const T ihD = ginv<T>(g, D);
     const T* qd = q[D];
     // neighbours along D (ghosts beyond walls mirror with the wall sign)
     int a3[3] = {id3[0], id3[1], id3[2]};
@@ -159,13 +169,13 @@ __device__ __forceinline__ T strain_at(const GridDev& g, const Coef<T>& cf, cons
     b3[D] -= 1;
     T q_hi, q_lo, s_hi = T(0), s_lo = T(0);
     if (a3[D] >= g.n[D]) {
-      s_hi = (T)g.bc[2 * D + 1];
+      s_hi = gbc<T>(g, 2 * D + 1);
       q_hi = s_hi * q0;
     } else {
       q_hi = qc[fidx(g, C, a3[0], a3[1], a3[2])];
     }
     if (b3[D] < 0) {
-      s_lo = (T)g.bc[2 * D];
+      s_lo = gbc<T>(g, 2 * D);
       q_lo = s_lo * q0;
     } else {
       q_lo = qc[fidx(g, C, b3[0], b3[1], b3[2])];
@@ -283,7 +293,7 @@ __global__ void k_pressure(GridDev g, const T* __restrict__ bx, const T* __restr
   size_t id = fidx(g, 3, i, j, k);
   T pc = p[id];
   T s = T(0);
-  T ihx2 = (T)g.ih2[0], ihy2 = (T)g.ih2[1], ihz2 = (T)g.ih2[2];
+  T ihx2 = ginv2<T>(g, 0), ihy2 = ginv2<T>(g, 1), ihz2 = ginv2<T>(g, 2);
   if (i + 1 < g.n[0]) s += bx[fidx(g, 0, i + 1, j, k)] * (p[id + 1] - pc) * ihx2;
   if (i > 0) s -= bx[fidx(g, 0, i, j, k)] * (pc - p[id - 1]) * ihx2;
   if (j + 1 < g.n[1]) s += by[fidx(g, 1, i, j + 1, k)] * (p[id + g.n[0]] - pc) * ihy2;
@@ -311,7 +321,7 @@ __global__ void k_grad(GridDev g, const T* __restrict__ p, T* out) {
   }
   int lo3[3] = {i, j, k};
   lo3[C] -= 1;
-  out[id] = (p[fidx(g, 3, i, j, k)] - p[fidx(g, 3, lo3[0], lo3[1], lo3[2])]) * (T)g.ih[C];
+  out[id] = (p[fidx(g, 3, i, j, k)] - p[fidx(g, 3, lo3[0], lo3[1], lo3[2])]) * ginv<T>(g, C);
 }
 
 template <typename T>
@@ -326,9 +336,9 @@ __global__ void k_div(GridDev g, const T* __restrict__ u, const T* __restrict__ 
                       T scale) {
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (i >= g.n[0] || j >= g.n[1]) return;
-  T d = (u[fidx(g, 0, i + 1, j, k)] - u[fidx(g, 0, i, j, k)]) * (T)g.ih[0] +
-        (v[fidx(g, 1, i, j + 1, k)] - v[fidx(g, 1, i, j, k)]) * (T)g.ih[1] +
-        (w[fidx(g, 2, i, j, k + 1)] - w[fidx(g, 2, i, j, k)]) * (T)g.ih[2];
+  T d = (u[fidx(g, 0, i + 1, j, k)] - u[fidx(g, 0, i, j, k)]) * ginv<T>(g, 0) +
+        (v[fidx(g, 1, i, j + 1, k)] - v[fidx(g, 1, i, j, k)]) * ginv<T>(g, 1) +
+        (w[fidx(g, 2, i, j, k + 1)] - w[fidx(g, 2, i, j, k)]) * ginv<T>(g, 2);
   out[fidx(g, 3, i, j, k)] = scale * d;
 }
 

@@ -61,7 +61,7 @@ __device__ __forceinline__ T ext_get(const GridDev& g, const T* __restrict__ a, 
       if (VEL) s = T(-1);
     } else {
       mm = gl - 1;
-      if (VEL) s = (T)g.bc[2 * D];
+      if (VEL) s = gbc<T>(g, 2 * D);
     }
   } else if (m >= n) {
     int gl = m - (n - 1);
@@ -70,7 +70,7 @@ __device__ __forceinline__ T ext_get(const GridDev& g, const T* __restrict__ a, 
       if (VEL) s = T(-1);
     } else {
       mm = n - gl;
-      if (VEL) s = (T)g.bc[2 * D + 1];
+      if (VEL) s = gbc<T>(g, 2 * D + 1);
     }
   }
   mm = clampi(mm, 0, n - 1);
@@ -122,7 +122,7 @@ __device__ __forceinline__ T cv_flux(const GridDev& g, const CVel<T>& vel, const
 }
 
 template <int C, bool WITHV, typename T>
-__global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, GridF gf, CVel<T> vel, const T* __restrict__ rho,
+__global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, CVel<T> vel, const T* __restrict__ rho,
                                                       T* out) {
   __shared__ T sFx[BY][BX + 1];
   __shared__ T sFy[BY + 1][BX];
@@ -180,8 +180,8 @@ __global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, GridF gf, CVel<
           Fz_lo = (C != 2 || ml >= 0) ? cv_flux<C, 2, WITHV, T>(g, vel, rho, i3, ml) : T(0);
         }
       }
-      T r = (sFx[ty][tx + 1] - sFx[ty][tx]) * ginv<T>(g, gf, 0) + (sFy[ty + 1][tx] - sFy[ty][tx]) * ginv<T>(g, gf, 1) +
-            (Fz_hi - Fz_lo) * ginv<T>(g, gf, 2);
+      T r = (sFx[ty][tx + 1] - sFx[ty][tx]) * ginv<T>(g, 0) + (sFy[ty + 1][tx] - sFy[ty][tx]) * ginv<T>(g, 1) +
+            (Fz_hi - Fz_lo) * ginv<T>(g, 2);
       out[fidx(g, C, i, j, k)] = wall ? T(0) : r;
       Fz_lo = Fz_hi;
     }
@@ -192,13 +192,12 @@ __global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, GridF gf, CVel<
 template <bool WITHV, typename T>
 static void transport_all(const GridDev& g, const CVel<T>& v, const T* const rho[3], T* const out[3],
                           cudaStream_t st) {
-  GridF gf = gridf(g);
   { k_transport<0, WITHV, T><<<dim3(cdiv(g.n[0] + 1, BX), cdiv(g.n[1], BY), cdiv(g.n[2], ZCHUNK)), dim3(BX, BY), 0,
-                               st>>>(g, gf, v, rho[0], out[0]); WSI_COUNT(); }
+                               st>>>(g, v, rho[0], out[0]); WSI_COUNT(); }
   { k_transport<1, WITHV, T><<<dim3(cdiv(g.n[0], BX), cdiv(g.n[1] + 1, BY), cdiv(g.n[2], ZCHUNK)), dim3(BX, BY), 0,
-                               st>>>(g, gf, v, rho[1], out[1]); WSI_COUNT(); }
+                               st>>>(g, v, rho[1], out[1]); WSI_COUNT(); }
   { k_transport<2, WITHV, T><<<dim3(cdiv(g.n[0], BX), cdiv(g.n[1], BY), cdiv(g.n[2] + 1, ZCHUNK)), dim3(BX, BY), 0,
-                               st>>>(g, gf, v, rho[2], out[2]); WSI_COUNT(); }
+                               st>>>(g, v, rho[2], out[2]); WSI_COUNT(); }
 }
 
 template <typename T>
@@ -230,6 +229,20 @@ __global__ void k_lincomb(size_t n, double a, const Ti* __restrict__ x, double b
   }
 }
 
+// float64 inputs, float32 arithmetic and output: the inputs are rounded by
+// integer operations (d2f_fast), keeping the float64 pipe idle
+__global__ void k_lincomb_tof(size_t n, float a, const double* __restrict__ x, float b, const double* __restrict__ y,
+                              float c, const double* __restrict__ z, float* out) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (; t < n; t += stride) {
+    float s = a * d2f_fast(x[t]);
+    if (y) s += b * d2f_fast(y[t]);
+    if (z) s += c * d2f_fast(z[t]);
+    out[t] = s;
+  }
+}
+
 // same in float32 arithmetic (float32 inputs and outputs)
 __global__ void k_lincomb_f(size_t n, float a, const float* __restrict__ x, float b, const float* __restrict__ y,
                             float c, const float* __restrict__ z, float* out) {
@@ -254,7 +267,7 @@ void launch_lincomb(size_t n, double a, const double* x, double b, const double*
 }
 void launch_lincomb_to_f32(size_t n, double a, const double* x, double b, const double* y, double c,
                            const double* z, float* out, cudaStream_t st) {
-  { k_lincomb<double, float><<<lc_blocks(n), 256, 0, st>>>(n, a, x, b, y, c, z, out); WSI_COUNT(); }
+  { k_lincomb_tof<<<lc_blocks(n), 256, 0, st>>>(n, (float)a, x, (float)b, y, (float)c, z, out); WSI_COUNT(); }
 }
 void launch_lincomb_f32(size_t n, float a, const float* x, float b, const float* y, float c, const float* z,
                         float* out, cudaStream_t st) {
@@ -304,7 +317,7 @@ __device__ __forceinline__ T ls_flux(const GridDev& g, const T* __restrict__ vel
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_ls_advect(GridDev g, GridF gf, CVel<T> vel,
+__global__ void __launch_bounds__(BX* BY) k_ls_advect(GridDev g, CVel<T> vel,
                                                       const double* __restrict__ phi_n, const T* __restrict__ phi_h,
                                                       double dt, double* out) {
   __shared__ T sFx[BY][BX + 1];
@@ -327,8 +340,8 @@ __global__ void __launch_bounds__(BX* BY) k_ls_advect(GridDev g, GridF gf, CVel<
     if (inside) {
       T Fz_hi = ls_flux<2, T>(g, vel.q[2], phi_h, i3, k + 1);
       if (k == k0) Fz_lo = ls_flux<2, T>(g, vel.q[2], phi_h, i3, k);
-      T Q = (sFx[ty][tx + 1] - sFx[ty][tx]) * ginv<T>(g, gf, 0) + (sFy[ty + 1][tx] - sFy[ty][tx]) * ginv<T>(g, gf, 1) +
-            (Fz_hi - Fz_lo) * ginv<T>(g, gf, 2);
+      T Q = (sFx[ty][tx + 1] - sFx[ty][tx]) * ginv<T>(g, 0) + (sFy[ty + 1][tx] - sFy[ty][tx]) * ginv<T>(g, 1) +
+            (Fz_hi - Fz_lo) * ginv<T>(g, 2);
       size_t id = fidx(g, 3, i, j, k);
       out[id] = phi_n[id] - dt * (double)Q;
       Fz_lo = Fz_hi;
@@ -342,7 +355,7 @@ void launch_levelset_advect(const GridDev& g, const T* const vel[3], const doubl
                             double* out, cudaStream_t st) {
   CVel<T> v{{vel[0], vel[1], vel[2]}};
   dim3 grid(cdiv(g.n[0], BX), cdiv(g.n[1], BY), cdiv(g.n[2], ZCHUNK));
-  { k_ls_advect<T><<<grid, dim3(BX, BY), 0, st>>>(g, gridf(g), v, phi_n, phi_half, dt, out); WSI_COUNT(); }
+  { k_ls_advect<T><<<grid, dim3(BX, BY), 0, st>>>(g, v, phi_n, phi_half, dt, out); WSI_COUNT(); }
 }
 template void launch_levelset_advect<double>(const GridDev&, const double* const[3], const double*, const double*,
                                              double, double*, cudaStream_t);
