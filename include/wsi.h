@@ -211,6 +211,26 @@ int wsi_advect_levelset(wsi_ctx* ctx, const double* vel, const double* phi_n,
 int wsi_interp(wsi_ctx* ctx, const double* vel, const double* X, int n, double* U);
 int wsi_spread(wsi_ctx* ctx, const double* F, const double* X, int n, double dV, double* vel);
 
+/* Numerical wave tank of Sec. 7.1: second-order Stokes wave of height H,
+ * period T over still-water depth `depth` (dispersion omega^2 = g k tanh kd
+ * solved by Newton's method; g = |gravity|).  At the end of every wsi_step
+ * the velocity and phi are relaxed, q <- a q + (1-a) q_target with
+ * a = 1 - (exp(xb^3.5) - 1)/(e - 1), in a generation zone [0, x_gen]
+ * (targets: phi = y - eta, liquid-only Stokes velocity) and a damping zone
+ * [x_damp, lx] (targets: still water), y = height above still water along
+ * axis `vertical` (1 or 2).  t0 sets the time of the current state; each
+ * step advances it by dt.  NULL disables the zones.
+ * wsi_wave_relax applies one relaxation at time t to a velocity vector and
+ * (optionally, phi may be NULL) a cell field, in place. */
+typedef struct {
+    double H, T, depth;
+    double x_gen, x_damp;
+    double t0;
+    int vertical;
+} wsi_wave_desc;
+int wsi_set_waves(wsi_ctx* ctx, const wsi_wave_desc* w);
+int wsi_wave_relax(wsi_ctx* ctx, double t, double* vel, double* phi);
+
 /* Instrumentation (no counterpart in the paper; used to report kernel
  * rooflines).  wsi_launch_count: kernels launched by this library in this
  * process so far.  wsi_ktimer_enable(k): bracket every later launch of

@@ -13,6 +13,7 @@ For cycles k = 0 .. n_cycles-1 (the paper uses n_cycles = 2):
      solve  rho^{n+1,k+1}/dt u~ - theta L_mu u~ + G p = b,  -D u~ = 0;
   3. rigidity projection at X^{n+1/2,k} and the position update.
 At k = 0: u^{n+1,0} = u^n, X^{n+1,0} = X^n.  At n = 0: u^{-1} = u^0.
+With wave zones, u^{n+1} and phi^{n+1} are relaxed at t^{n+1} (Sec. 7.1).
 """
 import numpy as np
 
@@ -48,8 +49,10 @@ class Body:
 
 
 class State:
-    def __init__(self, g: Grid, props: Props, phi, psi, body=None, vel=None, p=None):
+    def __init__(self, g: Grid, props: Props, phi, psi, body=None, vel=None, p=None, zones=None, time=0.0):
         self.g = g
+        self.zones = zones  # waves.Zones or None (Sec. 7.1 relaxation at step end)
+        self.time = time
         self.props = props
         self.phi = np.array(phi, dtype=np.float64)
         self.psi = np.array(psi, dtype=np.float64)
@@ -113,6 +116,9 @@ def step(s: State, dt, n_cycles=2):
         phi_k = phi_new
         psi_k = psi_new
         info.setdefault("u_tilde", []).append(vel_t)
+    if s.zones is not None:
+        u_k, phi_k = s.zones.relax(g, u_k, phi_k, s.time + dt, pr.n_cells)
+    s.time += dt
     s.vel_old = u_n
     s.vel = u_k
     s.p = p

@@ -105,6 +105,10 @@ struct wsi_ctx {
   bool psi_static_done = false;
   // mu_cc / mu_e hold mu(phi^n, psi^n) (true right after a step)
   bool mat_n_valid = false;
+  // wave tank relaxation zones (Sec. 7.1) and the time of the state
+  bool has_waves = false;
+  WaveDev wave;
+  double time = 0.0;
   // float32 shadows of the explicitly transported fields (mixed path)
   float *vn32 = nullptr, *u1_32 = nullptr, *u2_32 = nullptr, *rn32 = nullptr, *r1_32 = nullptr, *r2_32 = nullptr,
         *R32 = nullptr, *C32 = nullptr, *vh32 = nullptr, *phih32 = nullptr, *mu_cc_n32 = nullptr,
@@ -895,6 +899,13 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
     cudaMemcpyAsync(c->phi_k, c->phi_new, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(c->psi_k, psi_use, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
   }
+  // wave generation / damping zones relax u^{n+1} and phi^{n+1} (Sec. 7.1)
+  if (c->has_waves) {
+    double* vq[3];
+    parts(c, c->vel_k, vq);
+    launch_wave_relax(g, c->wave, c->time + dt, vq, c->phi_k, st);
+  }
+  c->time += dt;
   // commit the step
   cudaMemcpyAsync(c->vel_old, c->vel, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(c->vel, c->vel_k, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
@@ -1054,6 +1065,42 @@ int wsi_transport(wsi_ctx* c, const double* u_n, const double* u_nm1, const doub
   if (!rc) rc = copy_out(c, C_out, c->x, nv);
   if (rc) return rc;
   return cuda_check(c, "transport");
+}
+
+int wsi_set_waves(wsi_ctx* c, const wsi_wave_desc* w) {
+  if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
+  if (!w) {
+    c->has_waves = false;
+    return WSI_OK;
+  }
+  const double L[3] = {c->desc.lx, c->desc.ly, c->desc.lz};
+  if (!(w->H > 0.0) || !(w->T > 0.0) || !(w->depth > 0.0) || w->vertical < 1 || w->vertical > 2 ||
+      !(w->x_gen > 0.0) || !(w->x_damp > w->x_gen) || !(w->x_damp < c->desc.lx) ||
+      !(w->depth < L[w->vertical]))
+    return fail(c, WSI_ERR_INVALID_ARG, "bad wave description");
+  const double* gv = c->desc.gravity;
+  double gmag = sqrt(gv[0] * gv[0] + gv[1] * gv[1] + gv[2] * gv[2]);
+  if (!(gmag > 0.0)) return fail(c, WSI_ERR_INVALID_ARG, "waves need gravity");
+  PhaseConst pc = phase_const(c);
+  c->wave = wave_setup(w->H, w->T, w->depth, w->x_gen, w->x_damp, c->desc.lx, w->vertical, pc.eps, gmag);
+  c->has_waves = true;
+  c->time = w->t0;
+  return WSI_OK;
+}
+
+int wsi_wave_relax(wsi_ctx* c, double t, double* vel, double* phi) {
+  if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
+  if (!c->has_waves) return fail(c, WSI_ERR_INVALID_ARG, "wsi_set_waves must come first");
+  int rc = copy_in(c, c->vel_half, vel, c->nvel);
+  if (!rc && phi) rc = copy_in(c, c->phi_half, phi, c->ncell);
+  if (rc) return rc;
+  double* vq[3];
+  parts(c, c->vel_half, vq);
+  launch_wave_relax(c->g, c->wave, t, vq, phi ? c->phi_half : nullptr, c->st);
+  rc = copy_out(c, vel, c->vel_half, c->nvel);
+  if (!rc && phi) rc = copy_out(c, phi, c->phi_half, c->ncell);
+  if (rc) return rc;
+  return cuda_check(c, "wave_relax");
 }
 
 int wsi_advect_levelset(wsi_ctx* c, const double* vel, const double* phi_n, const double* phi_half, double dt,

@@ -154,6 +154,16 @@ template <typename T>
 void precond_apply(Precond<T>& P, const GridDev& g, const Opts& o, double dt, const double* v, double* z,
                    cudaStream_t st);
 
+// ---------------------------------------------------------------- waves.cu
+struct WaveDev {
+  double H, d, omega, k, a1, a2, c2, x_gen, x_damp, lx, eps;
+  int vert;
+};
+WaveDev wave_setup(double H, double T, double d, double x_gen, double x_damp, double lx, int vert, double eps,
+                   double grav);
+void launch_wave_relax(const GridDev& g, const WaveDev& w, double t, double* const vel[3], double* phi,
+                       cudaStream_t st);
+
 // ---------------------------------------------------------------- dlm.cu
 void launch_ib_interp(const GridDev& g, const double* const vel[3], const double* X, int n, double* U,
                       cudaStream_t st);

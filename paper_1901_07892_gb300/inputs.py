@@ -157,3 +157,53 @@ def random_faces(shape_fn, seed, scale=1.0):
 
 def random_cells(shape, seed, scale=1.0):
     return np.random.default_rng(seed).uniform(-1.0, 1.0, size=shape) * scale
+
+
+def polygon_distance_xz(x, z, verts):
+    """Signed distance (negative inside) to a convex polygon in the (x, z)
+    plane, vertices counter-clockwise."""
+    x, z = np.broadcast_arrays(x, z)
+    d2 = np.full(x.shape, np.inf)
+    inside = np.ones(x.shape, dtype=bool)
+    n = len(verts)
+    for a in range(n):
+        x0, z0 = verts[a]
+        x1, z1 = verts[(a + 1) % n]
+        ex, ez = x1 - x0, z1 - z0
+        wx, wz = x - x0, z - z0
+        t = np.clip((wx * ex + wz * ez) / (ex * ex + ez * ez), 0.0, 1.0)
+        dx, dz = wx - t * ex, wz - t * ez
+        d2 = np.minimum(d2, dx * dx + dz * dz)
+        inside &= (ex * wz - ez * wx) >= 0.0
+    d = np.sqrt(d2)
+    return np.where(inside, -d, d)
+
+
+def wave_tank(nx=256, ny=128, nz=128, lx=4.0, ly=1.0, lz=1.0, depth=0.5, H=0.05, T=1.0, dt=0.01,
+              with_bar=True):
+    """Numerical wave tank: still water of depth `depth`, a second-order
+    Stokes wave generated in [0, 0.5] and damped in [lx-0.5, lx], and a locked
+    submerged trapezoidal bar on the bed (0.3 high, base x in [1.5, 2.5], top
+    0.182 long centred at x = 2, spanning the tank), one marker per half cell.
+    The bar is locked with rho_s = rho_l (Sec. 5)."""
+    c = Case(nx=nx, ny=ny, nz=nz, lx=lx, ly=ly, lz=lz, dt=dt)
+    c.rho_s = c.rho_l
+    x, y, z = c.cell_xyz()
+    c.phi = np.broadcast_to(z - depth, (nz, ny, nx)).copy()
+    verts = [(1.5, 0.0), (2.5, 0.0), (2.0 + 0.091, 0.3), (2.0 - 0.091, 0.3)]
+    c.extra["wave"] = dict(H=H, T=T, depth=depth, x_gen=0.5, x_damp=lx - 0.5)
+    if with_bar:
+        c.psi = np.broadcast_to(polygon_distance_xz(x, z, verts), (nz, ny, nx)).copy()
+        hx, hy, hz = c.h
+        xs = (np.arange(int(round(1.0 / (hx / 2)))) + 0.5) * (hx / 2) + 1.5
+        zs = (np.arange(int(round(0.3 / (hz / 2)))) + 0.5) * (hz / 2)
+        ys = (np.arange(int(round(ly / (hy / 2)))) + 0.5) * (hy / 2)
+        Xg, Zg = np.meshgrid(xs, zs, indexing="ij")
+        keep = polygon_distance_xz(Xg, Zg, verts) < 0.0
+        px, pz = Xg[keep], Zg[keep]
+        Y = np.repeat(ys, px.size)
+        c.markers = np.stack([np.tile(px, ys.size), Y, np.tile(pz, ys.size)], axis=1)
+        c.dV = (hx / 2) * (hy / 2) * (hz / 2)
+    else:
+        c.psi = np.full((nz, ny, nx), 1.0)
+    return c

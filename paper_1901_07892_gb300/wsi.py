@@ -25,7 +25,8 @@ OP_STOKES, OP_VISCOUS, OP_STRAIN, OP_PRESSURE, OP_GRAD, OP_DIV = range(6)
 EXPORTED = ["wsi_stokes_size", "wsi_velocity_size", "wsi_create_grid", "wsi_destroy", "wsi_last_error",
             "wsi_set_phases", "wsi_stokes_solve", "wsi_dlm_constrain", "wsi_step", "wsi_get_field",
             "wsi_set_field", "wsi_get_coeff", "wsi_apply", "wsi_transport", "wsi_advect_levelset",
-            "wsi_interp", "wsi_spread", "wsi_launch_count", "wsi_ktimer_enable", "wsi_ktimer_read"]
+            "wsi_interp", "wsi_spread", "wsi_set_waves", "wsi_wave_relax", "wsi_launch_count",
+            "wsi_ktimer_enable", "wsi_ktimer_read"]
 KC_STOKES, KC_RBGS_P, KC_RBGS_V, KC_TRANSPORT, KC_MDOT, KC_MAXPY, KC_RESTRICT, KC_PROLONG = range(8)
 
 
@@ -65,6 +66,12 @@ class BodyState(ctypes.Structure):
 class StepStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int * 4), ("rel_residual", ctypes.c_double * 4),
                 ("umax", ctypes.c_double), ("ms", ctypes.c_double)]
+
+
+class WaveDesc(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_double), ("T", ctypes.c_double), ("depth", ctypes.c_double),
+                ("x_gen", ctypes.c_double), ("x_damp", ctypes.c_double), ("t0", ctypes.c_double),
+                ("vertical", ctypes.c_int)]
 
 
 class WsiError(RuntimeError):
@@ -107,6 +114,8 @@ def lib():
     L.wsi_advect_levelset.argtypes = [vp, vp, vp, vp, dp, vp]
     L.wsi_interp.argtypes = [vp, vp, vp, ip, vp]
     L.wsi_spread.argtypes = [vp, vp, vp, ip, dp, vp]
+    L.wsi_set_waves.argtypes = [vp, ctypes.POINTER(WaveDesc)]
+    L.wsi_wave_relax.argtypes = [vp, dp, vp, vp]
     L.wsi_launch_count.argtypes = []
     L.wsi_launch_count.restype = ctypes.c_longlong
     L.wsi_ktimer_enable.argtypes = [ip]
@@ -289,6 +298,18 @@ class Context:
         out = _empty_like_kind(phi_n, self.ncell)
         self._check(self.L.wsi_advect_levelset(self._h, _ptr(vel), _ptr(phi_n), _ptr(phi_half), dt, _ptr(out)))
         return out
+
+    def set_waves(self, H, T, depth, x_gen, x_damp, t0=0.0, vertical=2):
+        w = WaveDesc(H, T, depth, x_gen, x_damp, t0, vertical)
+        self._check(self.L.wsi_set_waves(self._h, ctypes.byref(w)))
+
+    def wave_relax(self, t, vel, phi):
+        v = _flat(vel)
+        v = v.copy() if not _is_torch(v) else v.clone()
+        p = _flat(phi)
+        p = p.copy() if not _is_torch(p) else p.clone()
+        self._check(self.L.wsi_wave_relax(self._h, t, _ptr(v), _ptr(p)))
+        return v, p
 
     def interp(self, vel, X):
         vel, X = _flat(vel), _flat(X)
