@@ -227,8 +227,20 @@ void pc_apply(wsi_ctx* c, double dt, const double* v, double* z) {
     precond_apply<double>(c->P64, c->g, c->opts, dt, v, z, c->st);
 }
 
+// K x: float64 on the plain path; on the mixed path the strain-rate term in
+// double-float arithmetic (same accuracy class, a fraction of the float64
+// instructions)
+void stokes_mv(wsi_ctx* c, const Coef<double>& cf, double inv_dt, double theta, const double* x, double* y,
+               cudaStream_t st) {
+  if (c->mixed())
+    launch_stokes_df(c->g, cf, inv_dt, theta, x, y, st);
+  else
+    launch_stokes(c->g, cf, inv_dt, theta, x, y, st);
+}
+
 // FGMRES(m), right preconditioned by the projection method; float64 Arnoldi
-// with classical Gram-Schmidt applied twice.
+// with classical Gram-Schmidt (see the iteration for the re-orthogonalisation
+// rule).
 int fgmres(wsi_ctx* c, const double* b, double* x, double dt, const wsi_solve_opts* o, wsi_solve_stats* s) {
   int rc = ensure_pc(c);
   if (rc) return rc;
@@ -253,7 +265,7 @@ int fgmres(wsi_ctx* c, const double* b, double* x, double dt, const wsi_solve_op
   }
   if (!o->use_x0) cudaMemsetAsync(x, 0, n * sizeof(double), c->st);
   // r = b - K x  into V_0
-  launch_stokes(c->g, cf, inv_dt, theta, x, Vj(0), c->st);
+  stokes_mv(c, cf, inv_dt, theta, x, Vj(0), c->st);
   launch_lincomb(n, 1.0, b, -1.0, Vj(0), 0.0, nullptr, Vj(0), c->st);
   double beta = host_norm2(Vj(0), n, red, c->st);
   const double tol = o->rtol * bnorm;
@@ -276,7 +288,7 @@ int fgmres(wsi_ctx* c, const double* b, double* x, double dt, const wsi_solve_op
     for (; j < m; ++j) {
       pc_apply(c, dt, Vj(j), Zj(j));
       double* w = Vj(j + 1);
-      launch_stokes(c->g, cf, inv_dt, theta, Zj(j), w, c->st);
+      stokes_mv(c, cf, inv_dt, theta, Zj(j), w, c->st);
       // Classical Gram-Schmidt.  One pass gives h = V^T w together with w.w
       // (w is V_{j+1}, the last row), so ||w - V h||^2 = w.w - |h|^2 needs no
       // second pass; when that cancels by more than half (the DGKS test) the
@@ -344,7 +356,7 @@ int fgmres(wsi_ctx* c, const double* b, double* x, double dt, const wsi_solve_op
     cudaMemcpyAsync(hd, y.data(), j * sizeof(double), cudaMemcpyHostToDevice, c->st);
     launch_maxpy(Z, n, j, hd, x, n, -1.0, c->st);
     // true residual
-    launch_stokes(c->g, cf, inv_dt, theta, x, Vj(0), c->st);
+    stokes_mv(c, cf, inv_dt, theta, x, Vj(0), c->st);
     launch_lincomb(n, 1.0, b, -1.0, Vj(0), 0.0, nullptr, Vj(0), c->st);
     beta = host_norm2(Vj(0), n, red, c->st);
   }
@@ -1018,7 +1030,7 @@ int wsi_apply(wsi_ctx* c, int op, const double* in, double* out, double dt) {
   vel_parts(c, (const double*)xin, qi);
   vel_parts(c, xout, qo);
   switch (op) {
-    case WSI_OP_STOKES: launch_stokes(c->g, cf, 1.0 / dt, c->desc.theta, xin, xout, c->st); break;
+    case WSI_OP_STOKES: stokes_mv(c, cf, 1.0 / dt, c->desc.theta, xin, xout, c->st); break;
     case WSI_OP_VISCOUS: launch_viscous<double>(c->g, cf, 1.0 / dt, c->desc.theta, qi, qo, c->st, false); break;
     case WSI_OP_STRAIN: launch_viscous<double>(c->g, cf, 1.0 / dt, c->desc.theta, qi, qo, c->st, true); break;
     case WSI_OP_PRESSURE: {

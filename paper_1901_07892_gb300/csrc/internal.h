@@ -52,6 +52,9 @@ void launch_div(const GridDev& g, const T* const q[3], T* out, T scale, cudaStre
 // packed Stokes matvec in float64: y = K x
 void launch_stokes(const GridDev& g, const Coef<double>& cf, double inv_dt, double theta, const double* x, double* y,
                    cudaStream_t st);
+// same, strain-rate term in double-float arithmetic (dfstokes.cu)
+void launch_stokes_df(const GridDev& g, const Coef<double>& cf, double inv_dt, double theta, const double* x,
+                      double* y, cudaStream_t st);
 // red-black Gauss-Seidel half sweep on the viscous block for component c
 template <typename T>
 void launch_viscous_rbgs(const GridDev& g, const Coef<T>& cf, T inv_dt, T theta, T* const q[3], const T* const b[3],

@@ -333,3 +333,37 @@ def test_hydrostatic_config2_full_size():
     # spurious velocity at the solver-tolerance level, not growing
     assert max(umax) < 1e-7, umax
     assert umax[-1] <= 10 * umax[0] + 1e-12, umax
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_stokes_apply_mixed_double_float(shape):
+    """The mixed path's Stokes matvec (strain term in double-float
+    arithmetic) meets the same 1e-11 bound as the float64 one."""
+    nx, ny, nz = shape
+    c, rng = _random_case(nx, ny, nz, 9)
+    if nz == 1:
+        c.lz = 1.0 / nx
+        c.bc = (-1.0, -1.0, -1.0, -1.0, 1.0, 1.0)
+    g = _grid(c)
+    ctx = _ctx(c, precision=wsi.PREC_MIXED)
+    m = _oracle_mat(c, g)
+    dt = 1e-3
+    vel = [rng.standard_normal(g.face_shape(d)) * g.interior_face_mask(d) for d in range(3)]
+    # smooth plus small-scale content, so cancellations in differences matter
+    vel = [a + 1e3 for a in vel]
+    vel = [a * g.interior_face_mask(d) for d, a in enumerate(vel)]
+    p = rng.standard_normal(g.cell_shape)
+    x = g.pack(vel[0], vel[1], vel[2], p)
+    got = ctx.apply(wsi.OP_STOKES, x, dt)
+    ref = ops.stokes_apply(g, m, m.rho_face, dt, c.theta, x)
+    for a, b in zip(g.unpack(got), g.unpack(ref)):
+        assert _rel(a, b) < OP_TOL
+    # the strain part alone, where the double-float arithmetic matters
+    L = ops.strain_rate_apply(g, m, *vel)
+    Kx_minus = [ref_c - (m.rho_face[d] / dt * vel[d] + ops.grad(g, p)[d]) * g.interior_face_mask(d)
+                for d, ref_c in enumerate(g.unpack(ref)[:3])]
+    got_L = [(gc - (m.rho_face[d] / dt * vel[d] + ops.grad(g, p)[d]) * g.interior_face_mask(d)) / -c.theta
+             for d, gc in enumerate(g.unpack(got)[:3])]
+    for d in range(3 if nz > 1 else 2):
+        scale = np.abs(L[d]).max()
+        assert np.abs(got_L[d] - L[d]).max() <= 1e-6 * scale + 1e-12 * np.abs(m.rho_face[d] / dt * vel[d]).max()
