@@ -231,6 +231,57 @@ typedef struct {
 int wsi_set_waves(wsi_ctx* ctx, const wsi_wave_desc* w);
 int wsi_wave_relax(wsi_ctx* ctx, double t, double* vel, double* phi);
 
+/* Learned pressure correction (no counterpart in the paper: it extends the
+ * pressure multigrid of the projection preconditioner).  A 3-D U-Net of
+ * widths c0/c1/c2 (multiples of 16, c0 <= 16, c1 <= 32, c2 <= 64) on a grid
+ * of nz x ny x nx cells (each divisible by 4): per level two 3x3x3
+ * convolutions with ReLU, 2x2x2 average pooling down, nearest up-sampling with
+ * skip concatenation up, a 1x1x1 head to one channel.  BF16 weights and
+ * activations, float32 accumulation on the tensor cores, float32 master
+ * weights and Adam.  Parameters are one float32 vector: per convolution
+ * (a1 a2 b1 b2 c1 c2 ub1 ub2 ua1 ua2) weights [27 taps][C_out][C_in]
+ * (tap = 9 dz + 3 dy + dx; a1's C_in is padded from 3 to 16) then biases
+ * [C_out]; then the head's weights [c0] and bias.
+ * wsi_unet_create initialises the weights from `seed` (He normal).
+ * wsi_unet_forward: x [V][3] float32 (host or device) -> out [V].
+ * wsi_unet_backward (after a forward): gradients of 0.5 mean((out - t)^2),
+ * readable with wsi_unet_get_grads; wsi_unet_adam applies one Adam step
+ * (beta 0.9 / 0.999). */
+typedef struct wsi_unet wsi_unet;
+int wsi_unet_create(int nz, int ny, int nx, int c0, int c1, int c2, unsigned long long seed, wsi_unet** out);
+void wsi_unet_destroy(wsi_unet* net);
+size_t wsi_unet_num_params(const wsi_unet* net);
+int wsi_unet_set_params(wsi_unet* net, const float* p);
+int wsi_unet_get_params(wsi_unet* net, float* p);
+int wsi_unet_get_grads(wsi_unet* net, float* g);
+int wsi_unet_forward(wsi_unet* net, const float* x, float* out);
+int wsi_unet_backward(wsi_unet* net, const float* target, double* loss);
+int wsi_unet_adam(wsi_unet* net, double lr);
+
+/* Use `net` as the coarse-grid correction of the float32 pressure multigrid
+ * at hierarchy level `level` (1 = first coarsening; the net's grid must equal
+ * that level's): the V-cycle replaces everything below the level by the
+ * network's prediction followed by post-smoothing.  Inputs: log(rho)/7 and
+ * the level set averaged down to the level, and the level's right-hand side
+ * over its RMS; the prediction o gives the correction s o / d (s the RMS,
+ * d the level operator's diagonal).  Requires a WSI_PREC_MIXED context and
+ * wsi_set_phases; enable = 0 keeps it attached but unused.
+ * wsi_unet_train_sample: one Adam step (learning rate lr; lr = 0 only
+ * evaluates) on the exact pair built from a smooth field e given on the
+ * level's cells: r = L e, target o* = e d / s.  *loss receives the loss. */
+int wsi_attach_unet(wsi_ctx* ctx, wsi_unet* net, int level, int enable);
+int wsi_unet_train_sample(wsi_ctx* ctx, const double* e, double lr, double* loss);
+
+/* Standalone pressure solve D(beta G) x = y (Sec. 4.2.4's projection
+ * sub-problem) on the current coefficients: float64 residuals with
+ * multigrid V-cycle corrections (float32 cycles on WSI_PREC_MIXED contexts,
+ * with the attached network if enabled; float64 on WSI_PREC_FP64), until
+ * ||y - L x|| <= rtol ||y|| (y's mean removed; x of zero mean).  A learned
+ * cycle that fails to reduce the residual switches the rest of the solve to
+ * plain cycles.  stats->iters = V-cycles. */
+int wsi_pressure_solve(wsi_ctx* ctx, const double* y, double* x, double rtol, int max_cycles,
+                       wsi_solve_stats* stats);
+
 /* Instrumentation (no counterpart in the paper; used to report kernel
  * rooflines).  wsi_launch_count: kernels launched by this library in this
  * process so far.  wsi_ktimer_enable(k): bracket every later launch of

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <random>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -105,6 +106,12 @@ struct wsi_ctx {
   bool psi_static_done = false;
   // mu_cc / mu_e hold mu(phi^n, psi^n) (true right after a step)
   bool mat_n_valid = false;
+  // learned coarse correction of the float32 pressure multigrid
+  wsi_unet* unet = nullptr;
+  UNetImpl* unet_impl = nullptr;
+  int unet_level = 0;
+  bool unet_on = false;
+  const double* phi_cur = nullptr;  // level set behind the current coefficients
   // wave tank relaxation zones (Sec. 7.1) and the time of the state
   bool has_waves = false;
   WaveDev wave;
@@ -216,6 +223,12 @@ int ensure_pc(wsi_ctx* c) {
   Coef<double> cf = coef_now(c);
   int rc = c->desc.precision == WSI_PREC_MIXED ? precond_setup<float>(c->P32, c->g, cf, c->st, c->err)
                                                : precond_setup<double>(c->P64, c->g, cf, c->st, c->err);
+  if (rc == WSI_OK && c->mixed()) {
+    rc = learned_alloc(c->P32, c->unet_impl, c->unet_level, c->err);
+    if (rc == WSI_OK && c->unet_impl)
+      rc = learned_setup(c->P32, c->rho_cc, c->phi_cur ? c->phi_cur : c->phi, c->st, c->err);
+    c->P32.learn.on = c->unet_on;
+  }
   if (rc == WSI_OK) c->pc_dirty = false;
   return rc;
 }
@@ -780,6 +793,7 @@ int wsi_set_phases(wsi_ctx* c, const double* phi, const double* psi, const wsi_p
   cudaMemsetAsync(c->vel_old, 0, c->nvel * sizeof(double), c->st);
   cudaMemsetAsync(c->p, 0, c->ncell * sizeof(double), c->st);
   c->have_phases = true;
+  c->phi_cur = c->phi;
   c->psi_static_done = false;
   c->mat_n_valid = false;
   c->pc_dirty = true;
@@ -876,6 +890,7 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
       psi_use = c->psi_new;
       if (at_rest && k + 1 == ncyc) c->psi_static_done = true;
     }
+    c->phi_cur = c->phi_new;
     launch_materials(g, pc, c->phi_new, psi_use, c->rho_cc, c->mu_cc, c->rho_face, c->beta, c->rho_flow, c->mu_e,
                      st);
     // 2. SSP-RK3 face density and consistent convection; right-hand side
@@ -1177,6 +1192,203 @@ int wsi_spread(wsi_ctx* c, const double* F, const double* X, int n, double dV, d
   c->allocs.resize(c->allocs.size() - 2);
   if (rc) return rc;
   return cuda_check(c, "spread");
+}
+
+// ------------------------------------------------------------------ learned correction
+struct wsi_unet {
+  UNetImpl* u = nullptr;
+  float* x3 = nullptr;  // staging for [V][3] inputs
+};
+
+int wsi_unet_create(int nz, int ny, int nx, int c0, int c1, int c2, unsigned long long seed, wsi_unet** out) {
+  if (!out) return WSI_ERR_INVALID_ARG;
+  *out = nullptr;
+  UNetImpl* u = unet_create(nz, ny, nx, c0, c1, c2);
+  if (!u) return WSI_ERR_INVALID_ARG;
+  wsi_unet* n = new wsi_unet();
+  n->u = u;
+  size_t V = (size_t)nz * ny * nx;
+  if (cudaMalloc(&n->x3, V * 3 * sizeof(float)) != cudaSuccess) {
+    unet_destroy(u);
+    delete n;
+    return WSI_ERR_OOM;
+  }
+  // He-normal initialisation from the seed (host), zero biases
+  std::vector<float> p(unet_nparam(u), 0.0f);
+  std::mt19937_64 rng(seed);
+  std::normal_distribution<float> nd(0.0f, 1.0f);
+  const int spec[10][3] = {{c0, 3, 16}, {c0, c0, c0}, {c1, c0, c0}, {c1, c1, c1}, {c2, c1, c1},
+                           {c2, c2, c2}, {c1, c2 + c1, c2 + c1}, {c1, c1, c1}, {c0, c1 + c0, c1 + c0}, {c0, c0, c0}};
+  size_t off = 0;
+  for (int l = 0; l < 10; ++l) {
+    int co = spec[l][0], ci_real = spec[l][1], ci = spec[l][2];
+    float sd = sqrtf(2.0f / (27.0f * ci_real));
+    for (int tap = 0; tap < 27; ++tap)
+      for (int o = 0; o < co; ++o)
+        for (int ci_ = 0; ci_ < ci; ++ci_) p[off + ((size_t)tap * co + o) * ci + ci_] = ci_ < ci_real ? sd * nd(rng) : 0.f;
+    off += (size_t)27 * co * ci + co;
+  }
+  for (int cc = 0; cc < c0; ++cc) p[off + cc] = sqrtf(2.0f / c0) * nd(rng);
+  cudaMemcpy(unet_params(u), p.data(), p.size() * sizeof(float), cudaMemcpyHostToDevice);
+  unet_pack(u, 0);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    wsi_unet_destroy(n);
+    return WSI_ERR_CUDA;
+  }
+  *out = n;
+  return WSI_OK;
+}
+
+void wsi_unet_destroy(wsi_unet* n) {
+  if (!n) return;
+  cudaDeviceSynchronize();
+  unet_destroy(n->u);
+  cudaFree(n->x3);
+  delete n;
+}
+
+size_t wsi_unet_num_params(const wsi_unet* n) { return n ? unet_nparam(n->u) : 0; }
+
+int wsi_unet_set_params(wsi_unet* n, const float* p) {
+  if (!n || !p) return WSI_ERR_INVALID_ARG;
+  if (cudaMemcpy(unet_params(n->u), p, unet_nparam(n->u) * sizeof(float), cudaMemcpyDefault) != cudaSuccess)
+    return WSI_ERR_CUDA;
+  unet_pack(n->u, 0);
+  return cudaDeviceSynchronize() == cudaSuccess ? WSI_OK : WSI_ERR_CUDA;
+}
+
+int wsi_unet_get_params(wsi_unet* n, float* p) {
+  if (!n || !p) return WSI_ERR_INVALID_ARG;
+  return cudaMemcpy(p, unet_params(n->u), unet_nparam(n->u) * sizeof(float), cudaMemcpyDefault) == cudaSuccess
+             ? WSI_OK
+             : WSI_ERR_CUDA;
+}
+
+int wsi_unet_get_grads(wsi_unet* n, float* g) {
+  if (!n || !g) return WSI_ERR_INVALID_ARG;
+  return cudaMemcpy(g, unet_grads(n->u), unet_nparam(n->u) * sizeof(float), cudaMemcpyDefault) == cudaSuccess
+             ? WSI_OK
+             : WSI_ERR_CUDA;
+}
+
+int wsi_unet_forward(wsi_unet* n, const float* x, float* out) {
+  if (!n || !x || !out) return WSI_ERR_INVALID_ARG;
+  size_t V = (size_t)unet_dim(n->u, 0) * unet_dim(n->u, 1) * unet_dim(n->u, 2);
+  if (cudaMemcpy(n->x3, x, V * 3 * sizeof(float), cudaMemcpyDefault) != cudaSuccess) return WSI_ERR_CUDA;
+  unet_set_input3(n->u, n->x3, 0);
+  unet_forward(n->u, 0);
+  if (cudaMemcpy(out, unet_output(n->u), V * sizeof(float), cudaMemcpyDefault) != cudaSuccess) return WSI_ERR_CUDA;
+  return cudaDeviceSynchronize() == cudaSuccess ? WSI_OK : WSI_ERR_CUDA;
+}
+
+int wsi_unet_backward(wsi_unet* n, const float* target, double* loss) {
+  if (!n || !target) return WSI_ERR_INVALID_ARG;
+  size_t V = (size_t)unet_dim(n->u, 0) * unet_dim(n->u, 1) * unet_dim(n->u, 2);
+  if (cudaMemcpy(unet_target(n->u), target, V * sizeof(float), cudaMemcpyDefault) != cudaSuccess) return WSI_ERR_CUDA;
+  unet_backward(n->u, 0);
+  if (loss && cudaMemcpy(loss, unet_loss(n->u), sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return WSI_ERR_CUDA;
+  return cudaDeviceSynchronize() == cudaSuccess ? WSI_OK : WSI_ERR_CUDA;
+}
+
+int wsi_unet_adam(wsi_unet* n, double lr) {
+  if (!n || !(lr >= 0.0)) return WSI_ERR_INVALID_ARG;
+  unet_adam(n->u, lr, 0);
+  return cudaDeviceSynchronize() == cudaSuccess ? WSI_OK : WSI_ERR_CUDA;
+}
+
+int wsi_attach_unet(wsi_ctx* c, wsi_unet* n, int level, int enable) {
+  if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
+  if (!c->mixed()) return fail(c, WSI_ERR_INVALID_ARG, "the learned correction needs a WSI_PREC_MIXED context");
+  c->unet = n;
+  c->unet_impl = n ? n->u : nullptr;
+  c->unet_level = level;
+  c->unet_on = n && enable;
+  c->pc_dirty = true;
+  return WSI_OK;
+}
+
+int wsi_unet_train_sample(wsi_ctx* c, const double* e, double lr, double* loss) {
+  if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
+  if (!c->unet || !c->have_phases) return fail(c, WSI_ERR_INVALID_ARG, "attach a network and set phases first");
+  int rc = ensure_pc(c);
+  if (rc) return rc;
+  Precond<float>& P = c->P32;
+  size_t n = fsize(P.lev[c->unet_level].g, 3);
+  // the level's residual buffer of level 0 (fine) serves as float64 staging
+  double* stage = c->V;
+  rc = copy_in(c, stage, e, n);
+  if (rc) return rc;
+  float* e32 = P.lev[c->unet_level].x;  // reused: the level's iterate
+  launch_lincomb_to_f32(n, 1.0, stage, 0.0, nullptr, 0.0, nullptr, e32, c->st);
+  learned_train(P, e32, lr, c->st);
+  if (loss) cudaMemcpyAsync(loss, unet_loss(c->unet->u), sizeof(double), cudaMemcpyDeviceToHost, c->st);
+  return cuda_check(c, "unet_train_sample");
+}
+
+int wsi_pressure_solve(wsi_ctx* c, const double* y, double* x, double rtol, int max_cycles, wsi_solve_stats* s) {
+  if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
+  if (!c->have_phases) return fail(c, WSI_ERR_INVALID_ARG, "wsi_set_phases must come first");
+  if (!(rtol > 0.0) || max_cycles < 1 || !s) return fail(c, WSI_ERR_INVALID_ARG, "bad options");
+  auto t0 = std::chrono::steady_clock::now();
+  int rc = ensure_pc(c);
+  if (rc) return rc;
+  const GridDev& g = c->g;
+  cudaStream_t st = c->st;
+  const size_t n = c->ncell;
+  double* yv = c->b + c->pk.off[3];
+  double* xv = c->x + c->pk.off[3];
+  double* r = c->V;  // scratch
+  rc = copy_in(c, yv, y, n);
+  if (rc) return rc;
+  launch_sum<double>(yv, n, c->hdev, c->red, st);
+  launch_add_scalar_from<double>(yv, n, c->hdev, -1.0 / (double)n, st);
+  cudaMemsetAsync(xv, 0, n * sizeof(double), st);
+  const double ynorm = host_norm2(yv, n, c->red, st);
+  const double* bt[3] = {c->beta[0], c->beta[1], c->beta[2]};
+  bool learned = c->mixed() && c->unet_on;
+  c->P32.learn.on = learned;
+  double rn = ynorm, prev = ynorm;
+  int cycles = 0;
+  while (true) {
+    launch_pressure<double>(g, bt, xv, r, st);
+    launch_lincomb(n, 1.0, yv, -1.0, r, 0.0, nullptr, r, st);
+    launch_sum<double>(r, n, c->hdev, c->red, st);
+    launch_add_scalar_from<double>(r, n, c->hdev, -1.0 / (double)n, st);
+    rn = host_norm2(r, n, c->red, st);
+    if (!std::isfinite(rn)) return fail(c, WSI_ERR_NAN, "non-finite pressure residual");
+    if (cycles > 0 && learned && rn > prev) {
+      learned = false;  // the plain cycle judges the network: fall back
+      c->P32.learn.on = false;
+    }
+    if (rn <= rtol * ynorm || cycles >= max_cycles || ynorm == 0.0) break;
+    prev = rn;
+    if (c->mixed()) {
+      MGLevel<float>& L0 = c->P32.lev[0];
+      launch_lincomb_to_f32(n, 1.0 / rn, r, 0.0, nullptr, 0.0, nullptr, L0.b, st);
+      cudaMemsetAsync(L0.x, 0, n * sizeof(float), st);
+      precond_vcycle<float>(c->P32, c->opts, st);
+      launch_lincomb_mix(n, 1.0, xv, rn, L0.x, 0.0, L0.x, xv, st);
+    } else {
+      MGLevel<double>& L0 = c->P64.lev[0];
+      cudaMemcpyAsync(L0.b, r, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+      cudaMemsetAsync(L0.x, 0, n * sizeof(double), st);
+      precond_vcycle<double>(c->P64, c->opts, st);
+      launch_lincomb(n, 1.0, xv, 1.0, L0.x, 0.0, nullptr, xv, st);
+    }
+    ++cycles;
+  }
+  c->P32.learn.on = c->unet_on;
+  launch_sum<double>(xv, n, c->hdev, c->red, st);
+  launch_add_scalar_from<double>(xv, n, c->hdev, -1.0 / (double)n, st);
+  rc = copy_out(c, x, xv, n);
+  if (rc) return rc;
+  rc = cuda_check(c, "pressure_solve");
+  if (rc) return rc;
+  s->iters = cycles;
+  s->rel_residual = ynorm > 0.0 ? rn / ynorm : 0.0;
+  s->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return rn <= rtol * ynorm ? WSI_OK : WSI_ERR_NOT_CONVERGED;
 }
 
 }  // extern "C"

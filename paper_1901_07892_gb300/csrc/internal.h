@@ -1,5 +1,6 @@
 // Host-side internals of libwsi shared by the translation units.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -107,6 +108,35 @@ void launch_sum(const T* x, size_t n, double* out_dev, double* scratch, cudaStre
 template <typename T>
 void launch_add_scalar_from(T* x, size_t n, const double* s_dev, double factor, cudaStream_t st);
 
+// ---------------------------------------------------------------- unet.cu
+struct UNetImpl;
+UNetImpl* unet_create(int Z, int Y, int X, int c0, int c1, int c2);
+void unet_destroy(UNetImpl* u);
+void unet_pack(UNetImpl* u, cudaStream_t st);  // float32 master weights -> bf16 kernel layouts
+void unet_forward(UNetImpl* u, cudaStream_t st);
+void unet_backward(UNetImpl* u, cudaStream_t st);
+void unet_adam(UNetImpl* u, double lr, cudaStream_t st);
+int unet_dim(const UNetImpl* u, int axis);  // 0: Z, 1: Y, 2: X
+void unet_set_input3(UNetImpl* u, const float* x3, cudaStream_t st);  // device float [V][3]
+size_t unet_nparam(const UNetImpl* u);
+float* unet_params(UNetImpl* u);
+float* unet_grads(UNetImpl* u);
+__nv_bfloat16* unet_input(UNetImpl* u);  // [V][16]
+float* unet_output(UNetImpl* u);         // [V]
+float* unet_target(UNetImpl* u);         // [V]
+double* unet_loss(UNetImpl* u);          // device scalar
+
+// learned correction state inside the float32 multigrid (learned.cu)
+struct LearnState {
+  UNetImpl* net = nullptr;
+  int level = 0;
+  bool on = false;     // use the correction in V-cycles
+  bool ready = false;  // inputs restricted for the current coefficients
+  std::vector<float*> lrho, phi;  // per level (index = level), restricted inputs
+  float* diag = nullptr;
+  double* ss = nullptr;
+};
+
 // ---------------------------------------------------------------- mg.cu
 template <typename T>
 struct MGLevel {
@@ -138,6 +168,7 @@ struct Precond {
   double* dsum = nullptr;
   bool built = false;
   std::vector<void*> allocs;
+  LearnState learn;  // float32 hierarchy only
 };
 
 struct Opts {
@@ -166,6 +197,15 @@ WaveDev wave_setup(double H, double T, double d, double x_gen, double x_damp, do
                    double grav);
 void launch_wave_relax(const GridDev& g, const WaveDev& w, double t, double* const vel[3], double* phi,
                        cudaStream_t st);
+
+// learned.cu
+int learned_setup(Precond<float>& P, const double* rho_cc, const double* phi, cudaStream_t st, std::string& err);
+void learned_correction(Precond<float>& P, int level, cudaStream_t st);
+void learned_train(Precond<float>& P, const float* e, double lr, cudaStream_t st);
+int learned_alloc(Precond<float>& P, UNetImpl* net, int level, std::string& err);
+// one V-cycle on level 0 of the hierarchy (x, b of level 0)
+template <typename T>
+void precond_vcycle(Precond<T>& P, const Opts& o, cudaStream_t st);
 
 // ---------------------------------------------------------------- dlm.cu
 void launch_ib_interp(const GridDev& g, const double* const vel[3], const double* X, int n, double* U,

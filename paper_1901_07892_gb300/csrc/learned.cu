@@ -1,0 +1,155 @@
+// The learned pressure correction inside the float32 multigrid, its training
+// on data the solver generates, and the standalone pressure solve used to
+// measure it.  No counterpart in the paper (it extends the pressure solve).
+//
+// Network input at multigrid level l (3 channels, bf16): log(rho)/7 and the
+// level set, both averaged down the hierarchy from the fine cells, and the
+// level's right-hand side r divided by its RMS s.  Output o (float32).  The
+// correction is e = s o / d with d the diagonal of the level's operator
+// (sum of beta/h^2 over the cell's faces), so that o = r/s reproduces one
+// Jacobi step and the network learns the rest.  Training pairs are exact by
+// construction: a seeded smooth field e, r = L_l e, target o* = e d / s.
+#include <math.h>
+
+#include "internal.h"
+
+namespace wsi {
+
+static constexpr int BX = 32, BY = 8;
+static inline dim3 grid3(int nx, int ny, int nz) { return dim3(cdiv(nx, BX), cdiv(ny, BY), nz); }
+static int nb(size_t n) { return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 152 * 8)); }
+
+// coarse cell = mean of its children (ratios r0, r1, r2)
+template <typename Ts>
+__global__ void k_avg_down(GridDev gf, GridDev gc, int r0, int r1, int r2, const Ts* __restrict__ f, float* c,
+                           int take_log) {
+  int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y, K = blockIdx.z;
+  if (I >= gc.n[0] || J >= gc.n[1]) return;
+  float s = 0.f;
+  for (int a = 0; a < r2; ++a)
+    for (int b = 0; b < r1; ++b)
+      for (int q = 0; q < r0; ++q) {
+        float v = (float)f[fidx(gf, 3, I * r0 + q, J * r1 + b, K * r2 + a)];
+        s += take_log ? logf(v) : v;
+      }
+  c[fidx(gc, 3, I, J, K)] = s / (float)(r0 * r1 * r2);
+}
+
+// d = sum over interior faces of beta/h^2
+__global__ void k_diag(GridDev g, const float* __restrict__ bx, const float* __restrict__ by,
+                       const float* __restrict__ bz, float* d) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.n[0] || j >= g.n[1]) return;
+  float s = 0.f;
+  if (i + 1 < g.n[0]) s += bx[fidx(g, 0, i + 1, j, k)] * g.ih2f[0];
+  if (i > 0) s += bx[fidx(g, 0, i, j, k)] * g.ih2f[0];
+  if (j + 1 < g.n[1]) s += by[fidx(g, 1, i, j + 1, k)] * g.ih2f[1];
+  if (j > 0) s += by[fidx(g, 1, i, j, k)] * g.ih2f[1];
+  if (k + 1 < g.n[2]) s += bz[fidx(g, 2, i, j, k + 1)] * g.ih2f[2];
+  if (k > 0) s += bz[fidx(g, 2, i, j, k)] * g.ih2f[2];
+  d[fidx(g, 3, i, j, k)] = s > 0.f ? s : 1.f;
+}
+
+__global__ void k_sumsq(const float* __restrict__ r, size_t n, double* out) {
+  double s = 0.0;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    s += (double)r[t] * (double)r[t];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+// x[v] = (lrho/7, phi, r/s, 0...) as bf16 with 16 channels
+__global__ void k_assemble(const float* __restrict__ lrho, const float* __restrict__ phi, const float* __restrict__ r,
+                           const double* __restrict__ ss, size_t n, __nv_bfloat16* x) {
+  float inv = (float)(1.0 / sqrt(fmax(ss[0] / (double)n, 1e-300)));
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x) {
+    __nv_bfloat16* p = x + v * 16;
+    p[0] = __float2bfloat16(lrho[v] * (1.0f / 7.0f));
+    p[1] = __float2bfloat16(fminf(fmaxf(phi[v] * 10.0f, -4.0f), 4.0f));
+    p[2] = __float2bfloat16(r[v] * inv);
+    for (int c = 3; c < 16; ++c) p[c] = __float2bfloat16(0.f);
+  }
+}
+
+// training target o* = e d / s
+__global__ void k_target(const float* __restrict__ e, const float* __restrict__ d, const double* __restrict__ ss,
+                         size_t n, float* tgt) {
+  float inv = (float)(1.0 / sqrt(fmax(ss[0] / (double)n, 1e-300)));
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x)
+    tgt[v] = e[v] * d[v] * inv;
+}
+
+// e = s o / d
+__global__ void k_apply_out(const float* __restrict__ o, const float* __restrict__ d, const double* __restrict__ ss,
+                            size_t n, float* x) {
+  float s = (float)sqrt(fmax(ss[0] / (double)n, 0.0));
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x)
+    x[v] = o[v] * s / d[v];
+}
+
+// restricted network inputs and the level diagonal; needs the fine rho_cc and
+// phi and a built hierarchy
+int learned_setup(Precond<float>& P, const double* rho_cc, const double* phi, cudaStream_t st, std::string& err) {
+  LearnState& S = P.learn;
+  if (!S.net) return WSI_OK;
+  if (S.level < 1 || S.level >= (int)P.lev.size()) {
+    err = "learned correction level outside the multigrid hierarchy";
+    return WSI_ERR_INVALID_ARG;
+  }
+  const MGLevel<float>& Lc = P.lev[S.level];
+  if (Lc.g.n[0] != unet_dim(S.net, 2) || Lc.g.n[1] != unet_dim(S.net, 1) || Lc.g.n[2] != unet_dim(S.net, 0)) {
+    err = "network dimensions differ from the multigrid level";
+    return WSI_ERR_INVALID_ARG;
+  }
+  // average log(rho) and phi down to the level
+  const GridDev& g0 = P.lev[0].g;
+  for (int l = 1; l <= S.level; ++l) {
+    const MGLevel<float>& F = P.lev[l - 1];
+    const GridDev& gc = P.lev[l].g;
+    dim3 gr = grid3(gc.n[0], gc.n[1], gc.n[2]);
+    if (l == 1) {
+      { k_avg_down<double><<<gr, dim3(BX, BY), 0, st>>>(F.g, gc, F.r[0], F.r[1], F.r[2], rho_cc, S.lrho[l], 1); WSI_COUNT(); }
+      { k_avg_down<double><<<gr, dim3(BX, BY), 0, st>>>(F.g, gc, F.r[0], F.r[1], F.r[2], phi, S.phi[l], 0); WSI_COUNT(); }
+    } else {
+      { k_avg_down<float><<<gr, dim3(BX, BY), 0, st>>>(F.g, gc, F.r[0], F.r[1], F.r[2], S.lrho[l - 1], S.lrho[l], 0); WSI_COUNT(); }
+      { k_avg_down<float><<<gr, dim3(BX, BY), 0, st>>>(F.g, gc, F.r[0], F.r[1], F.r[2], S.phi[l - 1], S.phi[l], 0); WSI_COUNT(); }
+    }
+  }
+  (void)g0;
+  { k_diag<<<grid3(Lc.g.n[0], Lc.g.n[1], Lc.g.n[2]), dim3(BX, BY), 0, st>>>(Lc.g, Lc.beta[0], Lc.beta[1], Lc.beta[2],
+                                                                            S.diag); WSI_COUNT(); }
+  S.ready = true;
+  return WSI_OK;
+}
+
+// x_level = network correction for the level's right-hand side b (x was 0)
+void learned_correction(Precond<float>& P, int l, cudaStream_t st) {
+  LearnState& S = P.learn;
+  MGLevel<float>& L = P.lev[l];
+  size_t n = fsize(L.g, 3);
+  cudaMemsetAsync(S.ss, 0, sizeof(double), st);
+  { k_sumsq<<<nb(n), 256, 0, st>>>(L.b, n, S.ss); WSI_COUNT(); }
+  { k_assemble<<<nb(n), 256, 0, st>>>(S.lrho[l], S.phi[l], L.b, S.ss, n, unet_input(S.net)); WSI_COUNT(); }
+  unet_forward(S.net, st);
+  { k_apply_out<<<nb(n), 256, 0, st>>>(unet_output(S.net), S.diag, S.ss, n, L.x); WSI_COUNT(); }
+}
+
+// one training step on a seeded field e at the level: r = L e, input, target,
+// forward, backward, Adam
+void learned_train(Precond<float>& P, const float* e, double lr, cudaStream_t st) {
+  LearnState& S = P.learn;
+  int l = S.level;
+  MGLevel<float>& L = P.lev[l];
+  size_t n = fsize(L.g, 3);
+  const float* bt[3] = {L.beta[0], L.beta[1], L.beta[2]};
+  launch_pressure<float>(L.g, bt, e, L.res, st);
+  cudaMemsetAsync(S.ss, 0, sizeof(double), st);
+  { k_sumsq<<<nb(n), 256, 0, st>>>(L.res, n, S.ss); WSI_COUNT(); }
+  { k_assemble<<<nb(n), 256, 0, st>>>(S.lrho[l], S.phi[l], L.res, S.ss, n, unet_input(S.net)); WSI_COUNT(); }
+  { k_target<<<nb(n), 256, 0, st>>>(e, S.diag, S.ss, n, unet_target(S.net)); WSI_COUNT(); }
+  unet_forward(S.net, st);
+  unet_backward(S.net, st);
+  if (lr > 0.0) unet_adam(S.net, lr, st);
+}
+
+}  // namespace wsi

@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -102,6 +103,11 @@ void precond_free(Precond<T>& P) {
   P.allocs.clear();
   P.lev.clear();
   P.built = false;
+  P.learn.lrho.clear();
+  P.learn.phi.clear();
+  P.learn.diag = nullptr;
+  P.learn.ss = nullptr;
+  P.learn.ready = false;
 }
 
 // ------------------------------------------------------------ coefficients
@@ -348,6 +354,19 @@ static void vcycle(Precond<T>& P, const Opts& o, size_t l, cudaStream_t st) {
     { k_coarse_solve<T><<<1, 256, P.ncoarse * sizeof(double), st>>>(P.ncoarse, P.coarse_inv, L.b, L.x); WSI_COUNT(); }
     return;
   }
+  if constexpr (std::is_same<T, float>::value) {
+    // learned coarse-grid correction: the network replaces everything below
+    // this level, then the usual post-smoothing
+    if (P.learn.on && P.learn.ready && (int)l == P.learn.level) {
+      learned_correction(P, (int)l, st);
+      for (int s = 0; s < o.mg_post; ++s)
+        for (int c = 1; c >= 0; --c) {
+          k_rbgs_p<T><<<gr, dim3(BX, BY), 0, st>>>(g, L.beta[0], L.beta[1], L.beta[2], L.x, L.b, c);
+          WSI_COUNT();
+        }
+      return;
+    }
+  }
   for (int s = 0; s < o.mg_pre; ++s)
     for (int c = 0; c < 2; ++c) {
       ktimer_begin(KC_RBGS_P, st);
@@ -372,6 +391,39 @@ static void vcycle(Precond<T>& P, const Opts& o, size_t l, cudaStream_t st) {
       { k_rbgs_p<T><<<gr, dim3(BX, BY), 0, st>>>(g, L.beta[0], L.beta[1], L.beta[2], L.x, L.b, c); WSI_COUNT(); }
       ktimer_end(KC_RBGS_P, st);
     }
+}
+
+template <typename T>
+void precond_vcycle(Precond<T>& P, const Opts& o, cudaStream_t st) {
+  vcycle(P, o, 0, st);
+}
+template void precond_vcycle<double>(Precond<double>&, const Opts&, cudaStream_t);
+template void precond_vcycle<float>(Precond<float>&, const Opts&, cudaStream_t);
+
+int learned_alloc(Precond<float>& P, UNetImpl* net, int level, std::string& err) {
+  LearnState& S = P.learn;
+  S.net = net;
+  S.level = level;
+  S.ready = false;
+  if (!net) return WSI_OK;
+  if (level < 1 || level >= (int)P.lev.size()) {
+    err = "learned correction level outside the multigrid hierarchy";
+    return WSI_ERR_INVALID_ARG;
+  }
+  if (S.lrho.empty()) {
+    S.lrho.assign(P.lev.size(), nullptr);
+    S.phi.assign(P.lev.size(), nullptr);
+    for (size_t l = 1; l < P.lev.size(); ++l) {
+      S.lrho[l] = dalloc<float>(P.allocs, fsize(P.lev[l].g, 3), err);
+      S.phi[l] = dalloc<float>(P.allocs, fsize(P.lev[l].g, 3), err);
+      if (!S.lrho[l] || !S.phi[l]) return WSI_ERR_OOM;
+    }
+    size_t nmax = fsize(P.lev[1].g, 3);
+    S.diag = dalloc<float>(P.allocs, nmax, err);
+    S.ss = dalloc<double>(P.allocs, 4, err);
+    if (!S.diag || !S.ss) return WSI_ERR_OOM;
+  }
+  return WSI_OK;
 }
 
 // ------------------------------------------------------------ PC glue kernels

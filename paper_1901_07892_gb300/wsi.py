@@ -26,7 +26,10 @@ EXPORTED = ["wsi_stokes_size", "wsi_velocity_size", "wsi_create_grid", "wsi_dest
             "wsi_set_phases", "wsi_stokes_solve", "wsi_dlm_constrain", "wsi_step", "wsi_get_field",
             "wsi_set_field", "wsi_get_coeff", "wsi_apply", "wsi_transport", "wsi_advect_levelset",
             "wsi_interp", "wsi_spread", "wsi_set_waves", "wsi_wave_relax", "wsi_launch_count",
-            "wsi_ktimer_enable", "wsi_ktimer_read"]
+            "wsi_ktimer_enable", "wsi_ktimer_read", "wsi_unet_create", "wsi_unet_destroy", "wsi_unet_num_params",
+            "wsi_unet_set_params", "wsi_unet_get_params", "wsi_unet_get_grads", "wsi_unet_forward",
+            "wsi_unet_backward", "wsi_unet_adam", "wsi_attach_unet", "wsi_unet_train_sample",
+            "wsi_pressure_solve"]
 KC_STOKES, KC_RBGS_P, KC_RBGS_V, KC_TRANSPORT, KC_MDOT, KC_MAXPY, KC_RESTRICT, KC_PROLONG = range(8)
 
 
@@ -122,7 +125,7 @@ def lib():
     L.wsi_ktimer_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
     for name in EXPORTED:
         if name not in ("wsi_destroy", "wsi_last_error", "wsi_stokes_size", "wsi_velocity_size",
-                        "wsi_launch_count"):
+                        "wsi_launch_count", "wsi_unet_destroy", "wsi_unet_num_params"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -343,3 +346,126 @@ def ktimer_read():
     if rc != OK:
         raise WsiError(rc, "wsi_ktimer_read")
     return t.value, n.value
+
+
+# ------------------------------------------------------------------ learned correction
+_UNET_SIGS = False
+
+
+def _unet_sigs():
+    global _UNET_SIGS
+    if _UNET_SIGS:
+        return
+    L = lib()
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.wsi_unet_create.argtypes = [ip, ip, ip, ip, ip, ip, ctypes.c_ulonglong, ctypes.POINTER(vp)]
+    L.wsi_unet_create.restype = ip
+    L.wsi_unet_destroy.argtypes = [vp]
+    L.wsi_unet_destroy.restype = None
+    L.wsi_unet_num_params.argtypes = [vp]
+    L.wsi_unet_num_params.restype = ctypes.c_size_t
+    for name in ("wsi_unet_set_params", "wsi_unet_get_params", "wsi_unet_get_grads"):
+        getattr(L, name).argtypes = [vp, vp]
+        getattr(L, name).restype = ip
+    L.wsi_unet_forward.argtypes = [vp, vp, vp]
+    L.wsi_unet_forward.restype = ip
+    L.wsi_unet_backward.argtypes = [vp, vp, ctypes.POINTER(dp)]
+    L.wsi_unet_backward.restype = ip
+    L.wsi_unet_adam.argtypes = [vp, dp]
+    L.wsi_unet_adam.restype = ip
+    L.wsi_attach_unet.argtypes = [vp, vp, ip, ip]
+    L.wsi_attach_unet.restype = ip
+    L.wsi_unet_train_sample.argtypes = [vp, vp, dp, ctypes.POINTER(dp)]
+    L.wsi_unet_train_sample.restype = ip
+    L.wsi_pressure_solve.argtypes = [vp, vp, vp, dp, ip, ctypes.POINTER(SolveStats)]
+    L.wsi_pressure_solve.restype = ip
+    _UNET_SIGS = True
+
+
+def _fptr(a):
+    assert isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class UNet:
+    """The learned correction network (float32 host arrays in and out)."""
+
+    def __init__(self, nz, ny, nx, c0=16, c1=32, c2=64, seed=0):
+        _unet_sigs()
+        self.L = lib()
+        h = ctypes.c_void_p()
+        rc = self.L.wsi_unet_create(nz, ny, nx, c0, c1, c2, seed, ctypes.byref(h))
+        if rc != OK:
+            raise WsiError(rc, "wsi_unet_create failed")
+        self._h = h
+        self.dims = (nz, ny, nx)
+        self.n = int(self.L.wsi_unet_num_params(h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            self.L.wsi_unet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, rc, what):
+        if rc != OK:
+            raise WsiError(rc, what)
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.n
+        self._ck(self.L.wsi_unet_set_params(self._h, _fptr(p)), "set_params")
+
+    def params(self):
+        p = np.empty(self.n, np.float32)
+        self._ck(self.L.wsi_unet_get_params(self._h, _fptr(p)), "get_params")
+        return p
+
+    def grads(self):
+        g = np.empty(self.n, np.float32)
+        self._ck(self.L.wsi_unet_get_grads(self._h, _fptr(g)), "get_grads")
+        return g
+
+    def forward(self, x):
+        """x: float32 [Z][Y][X][3] -> out [Z][Y][X]."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        out = np.empty(self.dims, np.float32)
+        self._ck(self.L.wsi_unet_forward(self._h, _fptr(x), _fptr(out)), "forward")
+        return out
+
+    def backward(self, target):
+        t = np.ascontiguousarray(target, dtype=np.float32)
+        loss = ctypes.c_double()
+        self._ck(self.L.wsi_unet_backward(self._h, _fptr(t), ctypes.byref(loss)), "backward")
+        return loss.value
+
+    def adam(self, lr):
+        self._ck(self.L.wsi_unet_adam(self._h, lr), "adam")
+
+
+def attach_unet(ctx, net, level, enable=True):
+    _unet_sigs()
+    ctx._check(ctx.L.wsi_attach_unet(ctx._h, net._h if net is not None else None, level, 1 if enable else 0))
+
+
+def unet_train_sample(ctx, e, lr):
+    _unet_sigs()
+    e = np.ascontiguousarray(e, dtype=np.float64)
+    loss = ctypes.c_double()
+    ctx._check(ctx.L.wsi_unet_train_sample(ctx._h, _ptr(e), lr, ctypes.byref(loss)))
+    return loss.value
+
+
+def pressure_solve(ctx, y, rtol=1e-8, max_cycles=200):
+    _unet_sigs()
+    y = _flat(y)
+    x = _empty_like_kind(y, ctx.ncell)
+    s = SolveStats()
+    rc = ctx.L.wsi_pressure_solve(ctx._h, _ptr(y), _ptr(x), rtol, max_cycles, ctypes.byref(s))
+    ctx._check(rc, allow=(ERR_NOT_CONVERGED,))
+    return x, s
