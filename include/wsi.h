@@ -97,6 +97,8 @@ typedef struct {
     int iters;
     double rel_residual; /* true residual after the solve                      */
     double ms;
+    int learned_rejected; /* wsi_pressure_solve: cycle whose learned correction
+                             was undone (-1: none); else -1                   */
 } wsi_solve_stats;
 
 typedef struct {
@@ -258,17 +260,25 @@ int wsi_unet_forward(wsi_unet* net, const float* x, float* out);
 int wsi_unet_backward(wsi_unet* net, const float* target, double* loss);
 int wsi_unet_adam(wsi_unet* net, double lr);
 
-/* Use `net` as the coarse-grid correction of the float32 pressure multigrid
- * at hierarchy level `level` (1 = first coarsening; the net's grid must equal
- * that level's): the V-cycle replaces everything below the level by the
- * network's prediction followed by post-smoothing.  Inputs: log(rho)/7 and
- * the level set averaged down to the level, and the level's right-hand side
- * over its RMS; the prediction o gives the correction s o / d (s the RMS,
- * d the level operator's diagonal).  Requires a WSI_PREC_MIXED context and
- * wsi_set_phases; enable = 0 keeps it attached but unused.
+/* Use `net` in the float32 pressure multigrid at hierarchy level `level`
+ * (1 = first coarsening; the net's grid must equal that level's).
+ * enable = WSI_LEARN_REPLACE: the V-cycle replaces everything below the level
+ * by the network's prediction for the level's right-hand side, followed by
+ * post-smoothing.  enable = WSI_LEARN_AUGMENT: the plain coarse-grid
+ * correction runs, then the network's prediction for the level's residual is
+ * added before post-smoothing.  enable = WSI_LEARN_OFF keeps it attached but
+ * unused.  Inputs: log(rho)/7 and the level set averaged down to the level,
+ * and the right-hand side (or residual) over its RMS; the prediction o gives
+ * the correction s o / d (s the RMS, d the level operator's diagonal).
+ * Requires a WSI_PREC_MIXED context and wsi_set_phases.
  * wsi_unet_train_sample: one Adam step (learning rate lr; lr = 0 only
  * evaluates) on the exact pair built from a smooth field e given on the
- * level's cells: r = L e, target o* = e d / s.  *loss receives the loss. */
+ * level's cells (float64, x fastest): r = L e and target o* = e d / s for
+ * the replacing mode; for the augmenting mode the plain coarse-grid
+ * correction x1 of r is run first and the pair is (r - L x1, e - x1).  The
+ * mode is the one last given to wsi_attach_unet (WSI_LEARN_OFF trains the
+ * replacing mode).  *loss receives the loss. */
+enum { WSI_LEARN_OFF = 0, WSI_LEARN_REPLACE = 1, WSI_LEARN_AUGMENT = 2 };
 int wsi_attach_unet(wsi_ctx* ctx, wsi_unet* net, int level, int enable);
 int wsi_unet_train_sample(wsi_ctx* ctx, const double* e, double lr, double* loss);
 

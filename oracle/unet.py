@@ -9,8 +9,28 @@ up-sampling with skip concatenation up, and a 1x1x1 head to one channel.
 Tensors are [C, Z, Y, X] float64; convolutions use zero padding 1.
 Weights: W[o, c, dz, dy, dx], bias b[o].  forward() returns the output and a
 tape; backward() returns the gradients of 0.5 * mean((out - target)^2).
+
+Both take an optional storage rounding `rnd` applied wherever a tensor is
+stored between operations (convolution and pooling outputs, the gradients
+passed between layers), so that a network whose kernels store activations in
+bfloat16 can be compared with the same storage decisions (`bf16` below).
+Arithmetic stays float64; the default is no rounding.
 """
 import numpy as np
+
+
+def bf16(a):
+    """Round to the nearest bfloat16 (ties to even), via float32: the value a
+    float32 accumulator would hold, then its upper 16 bits with
+    round-to-nearest-even on the lower 16."""
+    f = np.ascontiguousarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64).reshape(np.shape(a))
+
+
+def _ident(a):
+    return a
 
 LAYERS = ("a1", "a2", "b1", "b2", "c1", "c2", "ub1", "ub2", "ua1", "ua2")
 
@@ -78,19 +98,20 @@ def up_backward(d):
     return d.reshape(C, Z // 2, 2, Y // 2, 2, X // 2, 2).sum(axis=(2, 4, 6))
 
 
-def forward(p, x):
+def forward(p, x, rnd=None):
+    R = rnd or _ident
     t = {"x": x}
 
     def cr(name, inp):
         pre = conv3(inp, p[name + ".w"], p[name + ".b"])
-        out = np.maximum(pre, 0.0)
+        out = R(np.maximum(pre, 0.0))
         t[name + ".in"] = inp
         t[name + ".out"] = out
         return out
 
     a = cr("a2", cr("a1", x))
-    b = cr("b2", cr("b1", pool(a)))
-    c = cr("c2", cr("c1", pool(b)))
+    b = cr("b2", cr("b1", R(pool(a))))
+    c = cr("c2", cr("c1", R(pool(b))))
     ub = cr("ub2", cr("ub1", np.concatenate([up(c), b], axis=0)))
     ua = cr("ua2", cr("ua1", np.concatenate([up(ub), a], axis=0)))
     w = p["head.w"][:, :, 0, 0, 0]
@@ -104,30 +125,30 @@ def loss(out, target):
     return 0.5 * np.mean((out - target) ** 2)
 
 
-def backward(p, t, out, target):
+def backward(p, t, out, target, rnd=None):
+    R = rnd or _ident
     g = {}
     dout = (out - target) / out.size
     ua = t["head.in"]
     w = p["head.w"][:, :, 0, 0, 0]
     g["head.w"] = np.tensordot(dout, ua, axes=([1, 2, 3], [1, 2, 3]))[:, :, None, None, None]
     g["head.b"] = dout.sum(axis=(1, 2, 3))
-    d = np.tensordot(w, dout, axes=([0], [0]))
+    d = R(np.tensordot(w, dout, axes=([0], [0])))
 
     def crb(name, d):
         d = d * (t[name + ".out"] > 0.0)
         dx, dw, db = conv3_backward(t[name + ".in"], p[name + ".w"], d)
         g[name + ".w"], g[name + ".b"] = dw, db
-        return dx
+        return R(dx)
 
-    c0 = t["a"].shape[0]
     c1 = t["b"].shape[0]
     d = crb("ua1", crb("ua2", d))
     d_up_ub, d_a_skip = d[:c1], d[c1:]
-    d = crb("ub1", crb("ub2", up_backward(d_up_ub)))
+    d = crb("ub1", crb("ub2", R(up_backward(d_up_ub))))
     d_up_c, d_b_skip = d[:t["c"].shape[0]], d[t["c"].shape[0]:]
-    d = crb("c1", crb("c2", up_backward(d_up_c)))
-    d = pool_backward(d, None) + d_b_skip
+    d = crb("c1", crb("c2", R(up_backward(d_up_c))))
+    d = R(pool_backward(d, None) + d_b_skip)
     d = crb("b1", crb("b2", d))
-    d = pool_backward(d, None) + d_a_skip
+    d = R(pool_backward(d, None) + d_a_skip)
     dx = crb("a1", crb("a2", d))
     return g, dx

@@ -270,6 +270,7 @@ int fgmres(wsi_ctx* c, const double* b, double* x, double dt, const wsi_solve_op
   double bnorm = host_norm2(b, n, red, c->st);
   int iters = 0;
   s->iters = 0;
+  s->learned_rejected = -1;
   s->rel_residual = 0.0;
   if (!std::isfinite(bnorm)) return fail(c, WSI_ERR_NAN, "non-finite right-hand side");
   if (bnorm == 0.0) {
@@ -1303,7 +1304,9 @@ int wsi_attach_unet(wsi_ctx* c, wsi_unet* n, int level, int enable) {
   c->unet = n;
   c->unet_impl = n ? n->u : nullptr;
   c->unet_level = level;
-  c->unet_on = n && enable;
+  if (enable < WSI_LEARN_OFF || enable > WSI_LEARN_AUGMENT) return fail(c, WSI_ERR_INVALID_ARG, "bad learned mode");
+  c->unet_on = n && enable != WSI_LEARN_OFF;
+  c->P32.learn.mode = enable == WSI_LEARN_AUGMENT ? WSI_LEARN_AUGMENT : WSI_LEARN_REPLACE;
   c->pc_dirty = true;
   return WSI_OK;
 }
@@ -1319,9 +1322,9 @@ int wsi_unet_train_sample(wsi_ctx* c, const double* e, double lr, double* loss) 
   double* stage = c->V;
   rc = copy_in(c, stage, e, n);
   if (rc) return rc;
-  float* e32 = P.lev[c->unet_level].x;  // reused: the level's iterate
+  float* e32 = P.learn.e;
   launch_lincomb_to_f32(n, 1.0, stage, 0.0, nullptr, 0.0, nullptr, e32, c->st);
-  learned_train(P, e32, lr, c->st);
+  learned_train(P, c->opts, e32, lr, c->st);
   if (loss) cudaMemcpyAsync(loss, unet_loss(c->unet->u), sizeof(double), cudaMemcpyDeviceToHost, c->st);
   return cuda_check(c, "unet_train_sample");
 }
@@ -1330,6 +1333,7 @@ int wsi_pressure_solve(wsi_ctx* c, const double* y, double* x, double rtol, int 
   if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
   if (!c->have_phases) return fail(c, WSI_ERR_INVALID_ARG, "wsi_set_phases must come first");
   if (!(rtol > 0.0) || max_cycles < 1 || !s) return fail(c, WSI_ERR_INVALID_ARG, "bad options");
+  s->learned_rejected = -1;
   auto t0 = std::chrono::steady_clock::now();
   int rc = ensure_pc(c);
   if (rc) return rc;
@@ -1346,9 +1350,14 @@ int wsi_pressure_solve(wsi_ctx* c, const double* y, double* x, double rtol, int 
   cudaMemsetAsync(xv, 0, n * sizeof(double), st);
   const double ynorm = host_norm2(yv, n, c->red, st);
   const double* bt[3] = {c->beta[0], c->beta[1], c->beta[2]};
+  // The plain V-cycle judges the network: the first two cycles are plain and
+  // the second one's residual reduction is the bar; a learned cycle that
+  // reduces the residual less is undone and the solve continues plain.
+  const int plain_cycles = 2;
   bool learned = c->mixed() && c->unet_on;
-  c->P32.learn.on = learned;
-  double rn = ynorm, prev = ynorm;
+  bool last_learned = false;
+  double* xb = c->Z;  // iterate before a learned cycle
+  double rn = ynorm, prev = ynorm, rho_plain = 1.0;
   int cycles = 0;
   while (true) {
     launch_pressure<double>(g, bt, xv, r, st);
@@ -1356,13 +1365,19 @@ int wsi_pressure_solve(wsi_ctx* c, const double* y, double* x, double rtol, int 
     launch_sum<double>(r, n, c->hdev, c->red, st);
     launch_add_scalar_from<double>(r, n, c->hdev, -1.0 / (double)n, st);
     rn = host_norm2(r, n, c->red, st);
-    if (!std::isfinite(rn)) return fail(c, WSI_ERR_NAN, "non-finite pressure residual");
-    if (cycles > 0 && learned && rn > prev) {
-      learned = false;  // the plain cycle judges the network: fall back
-      c->P32.learn.on = false;
+    if (!std::isfinite(rn) && !last_learned) return fail(c, WSI_ERR_NAN, "non-finite pressure residual");
+    if (last_learned && !(rn <= rho_plain * prev)) {
+      cudaMemcpyAsync(xv, xb, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+      learned = last_learned = false;
+      s->learned_rejected = cycles;
+      continue;  // residual of the restored iterate
     }
+    if (cycles == plain_cycles && prev > 0.0) rho_plain = rn / prev;
     if (rn <= rtol * ynorm || cycles >= max_cycles || ynorm == 0.0) break;
     prev = rn;
+    const bool use = learned && cycles >= plain_cycles;
+    c->P32.learn.on = use;
+    if (use) cudaMemcpyAsync(xb, xv, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
     if (c->mixed()) {
       MGLevel<float>& L0 = c->P32.lev[0];
       launch_lincomb_to_f32(n, 1.0 / rn, r, 0.0, nullptr, 0.0, nullptr, L0.b, st);
@@ -1376,6 +1391,7 @@ int wsi_pressure_solve(wsi_ctx* c, const double* y, double* x, double rtol, int 
       precond_vcycle<double>(c->P64, c->opts, st);
       launch_lincomb(n, 1.0, xv, 1.0, L0.x, 0.0, nullptr, xv, st);
     }
+    last_learned = use;
     ++cycles;
   }
   c->P32.learn.on = c->unet_on;

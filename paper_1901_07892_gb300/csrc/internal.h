@@ -131,9 +131,11 @@ struct LearnState {
   UNetImpl* net = nullptr;
   int level = 0;
   bool on = false;     // use the correction in V-cycles
+  int mode = 1;        // WSI_LEARN_REPLACE or WSI_LEARN_AUGMENT
   bool ready = false;  // inputs restricted for the current coefficients
   std::vector<float*> lrho, phi;  // per level (index = level), restricted inputs
   float* diag = nullptr;
+  float* e = nullptr;  // training field on the level
   double* ss = nullptr;
 };
 
@@ -200,12 +202,19 @@ void launch_wave_relax(const GridDev& g, const WaveDev& w, double t, double* con
 
 // learned.cu
 int learned_setup(Precond<float>& P, const double* rho_cc, const double* phi, cudaStream_t st, std::string& err);
-void learned_correction(Precond<float>& P, int level, cudaStream_t st);
-void learned_train(Precond<float>& P, const float* e, double lr, cudaStream_t st);
+// x_level (+)= network correction for rhs (the level's b, or a residual)
+void learned_correction(Precond<float>& P, int level, const float* rhs, bool add, cudaStream_t st);
+// one training step on the exact pair of a smooth field e (device float on
+// the level); for the augmenting mode the pair is taken after the plain
+// coarse-grid correction of r = L e
+void learned_train(Precond<float>& P, const Opts& o, const float* e, double lr, cudaStream_t st);
 int learned_alloc(Precond<float>& P, UNetImpl* net, int level, std::string& err);
 // one V-cycle on level 0 of the hierarchy (x, b of level 0)
 template <typename T>
 void precond_vcycle(Precond<T>& P, const Opts& o, cudaStream_t st);
+// everything of a V-cycle on level l but the post-smoothing (x, b of level l)
+template <typename T>
+void precond_coarse_part(Precond<T>& P, const Opts& o, int l, cudaStream_t st);
 
 // ---------------------------------------------------------------- dlm.cu
 void launch_ib_interp(const GridDev& g, const double* const vel[3], const double* X, int n, double* U,

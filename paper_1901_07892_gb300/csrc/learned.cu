@@ -71,20 +71,22 @@ __global__ void k_assemble(const float* __restrict__ lrho, const float* __restri
   }
 }
 
-// training target o* = e d / s
-__global__ void k_target(const float* __restrict__ e, const float* __restrict__ d, const double* __restrict__ ss,
-                         size_t n, float* tgt) {
+// training target o* = (e - x) d / s  (x null: 0)
+__global__ void k_target(const float* __restrict__ e, const float* __restrict__ x, const float* __restrict__ d,
+                         const double* __restrict__ ss, size_t n, float* tgt) {
   float inv = (float)(1.0 / sqrt(fmax(ss[0] / (double)n, 1e-300)));
   for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x)
-    tgt[v] = e[v] * d[v] * inv;
+    tgt[v] = (x ? e[v] - x[v] : e[v]) * d[v] * inv;
 }
 
-// e = s o / d
+// x = s o / d, or x += s o / d
 __global__ void k_apply_out(const float* __restrict__ o, const float* __restrict__ d, const double* __restrict__ ss,
-                            size_t n, float* x) {
+                            size_t n, int add, float* x) {
   float s = (float)sqrt(fmax(ss[0] / (double)n, 0.0));
-  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x)
-    x[v] = o[v] * s / d[v];
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x) {
+    float e = o[v] * s / d[v];
+    x[v] = add ? x[v] + e : e;
+  }
 }
 
 // restricted network inputs and the level diagonal; needs the fine rho_cc and
@@ -122,31 +124,43 @@ int learned_setup(Precond<float>& P, const double* rho_cc, const double* phi, cu
   return WSI_OK;
 }
 
-// x_level = network correction for the level's right-hand side b (x was 0)
-void learned_correction(Precond<float>& P, int l, cudaStream_t st) {
+// x_level = (or +=) network correction for rhs on level l
+void learned_correction(Precond<float>& P, int l, const float* rhs, bool add, cudaStream_t st) {
   LearnState& S = P.learn;
   MGLevel<float>& L = P.lev[l];
   size_t n = fsize(L.g, 3);
   cudaMemsetAsync(S.ss, 0, sizeof(double), st);
-  { k_sumsq<<<nb(n), 256, 0, st>>>(L.b, n, S.ss); WSI_COUNT(); }
-  { k_assemble<<<nb(n), 256, 0, st>>>(S.lrho[l], S.phi[l], L.b, S.ss, n, unet_input(S.net)); WSI_COUNT(); }
+  { k_sumsq<<<nb(n), 256, 0, st>>>(rhs, n, S.ss); WSI_COUNT(); }
+  { k_assemble<<<nb(n), 256, 0, st>>>(S.lrho[l], S.phi[l], rhs, S.ss, n, unet_input(S.net)); WSI_COUNT(); }
   unet_forward(S.net, st);
-  { k_apply_out<<<nb(n), 256, 0, st>>>(unet_output(S.net), S.diag, S.ss, n, L.x); WSI_COUNT(); }
+  { k_apply_out<<<nb(n), 256, 0, st>>>(unet_output(S.net), S.diag, S.ss, n, add ? 1 : 0, L.x); WSI_COUNT(); }
 }
 
-// one training step on a seeded field e at the level: r = L e, input, target,
-// forward, backward, Adam
-void learned_train(Precond<float>& P, const float* e, double lr, cudaStream_t st) {
+// one training step on a seeded field e at the level.  Replacing mode: the
+// network sees r = L e and learns e.  Augmenting mode: the plain coarse-grid
+// correction of r (pre-smoothing, coarser cycle, prolongation) gives x1; the
+// network sees the residual r - L x1 and learns the error e - x1 it leaves,
+// exact because e is known.  Then forward, backward and Adam.
+void learned_train(Precond<float>& P, const Opts& o, const float* e, double lr, cudaStream_t st) {
   LearnState& S = P.learn;
   int l = S.level;
   MGLevel<float>& L = P.lev[l];
   size_t n = fsize(L.g, 3);
   const float* bt[3] = {L.beta[0], L.beta[1], L.beta[2]};
   launch_pressure<float>(L.g, bt, e, L.res, st);
+  const float* x1 = nullptr;
+  if (S.mode == WSI_LEARN_AUGMENT) {
+    cudaMemcpyAsync(L.b, L.res, n * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    cudaMemsetAsync(L.x, 0, n * sizeof(float), st);
+    precond_coarse_part<float>(P, o, l, st);
+    launch_pressure<float>(L.g, bt, L.x, L.res, st);
+    launch_lincomb_f32(n, 1.f, L.b, -1.f, L.res, 0.f, nullptr, L.res, st);
+    x1 = L.x;
+  }
   cudaMemsetAsync(S.ss, 0, sizeof(double), st);
   { k_sumsq<<<nb(n), 256, 0, st>>>(L.res, n, S.ss); WSI_COUNT(); }
   { k_assemble<<<nb(n), 256, 0, st>>>(S.lrho[l], S.phi[l], L.res, S.ss, n, unet_input(S.net)); WSI_COUNT(); }
-  { k_target<<<nb(n), 256, 0, st>>>(e, S.diag, S.ss, n, unet_target(S.net)); WSI_COUNT(); }
+  { k_target<<<nb(n), 256, 0, st>>>(e, x1, S.diag, S.ss, n, unet_target(S.net)); WSI_COUNT(); }
   unet_forward(S.net, st);
   unet_backward(S.net, st);
   if (lr > 0.0) unet_adam(S.net, lr, st);

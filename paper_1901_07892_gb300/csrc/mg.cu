@@ -106,6 +106,7 @@ void precond_free(Precond<T>& P) {
   P.learn.lrho.clear();
   P.learn.phi.clear();
   P.learn.diag = nullptr;
+  P.learn.e = nullptr;
   P.learn.ss = nullptr;
   P.learn.ready = false;
 }
@@ -346,27 +347,15 @@ __global__ void k_coarse_solve(int n, const double* __restrict__ Minv, const T* 
 }
 
 template <typename T>
-static void vcycle(Precond<T>& P, const Opts& o, size_t l, cudaStream_t st) {
+static void vcycle(Precond<T>& P, const Opts& o, size_t l, cudaStream_t st);
+
+// pre-smoothing, residual restriction, the coarser cycle and prolongation on
+// level l (everything of a V-cycle at l but the post-smoothing)
+template <typename T>
+static void coarse_part(Precond<T>& P, const Opts& o, size_t l, cudaStream_t st) {
   MGLevel<T>& L = P.lev[l];
   const GridDev& g = L.g;
   dim3 gr = grid3(g.n[0], g.n[1], g.n[2]);
-  if (l + 1 == P.lev.size()) {
-    { k_coarse_solve<T><<<1, 256, P.ncoarse * sizeof(double), st>>>(P.ncoarse, P.coarse_inv, L.b, L.x); WSI_COUNT(); }
-    return;
-  }
-  if constexpr (std::is_same<T, float>::value) {
-    // learned coarse-grid correction: the network replaces everything below
-    // this level, then the usual post-smoothing
-    if (P.learn.on && P.learn.ready && (int)l == P.learn.level) {
-      learned_correction(P, (int)l, st);
-      for (int s = 0; s < o.mg_post; ++s)
-        for (int c = 1; c >= 0; --c) {
-          k_rbgs_p<T><<<gr, dim3(BX, BY), 0, st>>>(g, L.beta[0], L.beta[1], L.beta[2], L.x, L.b, c);
-          WSI_COUNT();
-        }
-      return;
-    }
-  }
   for (int s = 0; s < o.mg_pre; ++s)
     for (int c = 0; c < 2; ++c) {
       ktimer_begin(KC_RBGS_P, st);
@@ -384,6 +373,48 @@ static void vcycle(Precond<T>& P, const Opts& o, size_t l, cudaStream_t st) {
   ktimer_begin(KC_PROLONG, st);
   { k_prolong_add<T><<<gr, dim3(BX, BY), 0, st>>>(g, gc, L.r[0], L.r[1], L.r[2], Cl.x, L.x); WSI_COUNT(); }
   ktimer_end(KC_PROLONG, st);
+}
+
+template <typename T>
+void precond_coarse_part(Precond<T>& P, const Opts& o, int l, cudaStream_t st) {
+  coarse_part(P, o, (size_t)l, st);
+}
+template void precond_coarse_part<float>(Precond<float>&, const Opts&, int, cudaStream_t);
+
+template <typename T>
+static void vcycle(Precond<T>& P, const Opts& o, size_t l, cudaStream_t st) {
+  MGLevel<T>& L = P.lev[l];
+  const GridDev& g = L.g;
+  dim3 gr = grid3(g.n[0], g.n[1], g.n[2]);
+  if (l + 1 == P.lev.size()) {
+    { k_coarse_solve<T><<<1, 256, P.ncoarse * sizeof(double), st>>>(P.ncoarse, P.coarse_inv, L.b, L.x); WSI_COUNT(); }
+    return;
+  }
+  if constexpr (std::is_same<T, float>::value) {
+    // learned coarse-grid correction: the network replaces everything below
+    // this level, then the usual post-smoothing
+    if (P.learn.on && P.learn.ready && (int)l == P.learn.level && P.learn.mode == WSI_LEARN_REPLACE) {
+      learned_correction(P, (int)l, L.b, false, st);
+      for (int s = 0; s < o.mg_post; ++s)
+        for (int c = 1; c >= 0; --c) {
+          k_rbgs_p<T><<<gr, dim3(BX, BY), 0, st>>>(g, L.beta[0], L.beta[1], L.beta[2], L.x, L.b, c);
+          WSI_COUNT();
+        }
+      return;
+    }
+  }
+  coarse_part(P, o, l, st);
+  if constexpr (std::is_same<T, float>::value) {
+    // learned augmentation: the network's correction of the residual left
+    // by the plain coarse-grid correction
+    if (P.learn.on && P.learn.ready && (int)l == P.learn.level && P.learn.mode == WSI_LEARN_AUGMENT) {
+      const size_t n = fsize(g, 3);
+      const T* bt[3] = {L.beta[0], L.beta[1], L.beta[2]};
+      launch_pressure<T>(g, bt, L.x, L.res, st);
+      launch_lincomb_f32(n, 1.f, L.b, -1.f, L.res, 0.f, nullptr, L.res, st);
+      learned_correction(P, (int)l, L.res, true, st);
+    }
+  }
   for (int s = 0; s < o.mg_post; ++s)
     for (int c = 1; c >= 0; --c)
     {
@@ -420,8 +451,9 @@ int learned_alloc(Precond<float>& P, UNetImpl* net, int level, std::string& err)
     }
     size_t nmax = fsize(P.lev[1].g, 3);
     S.diag = dalloc<float>(P.allocs, nmax, err);
+    S.e = dalloc<float>(P.allocs, nmax, err);
     S.ss = dalloc<double>(P.allocs, 4, err);
-    if (!S.diag || !S.ss) return WSI_ERR_OOM;
+    if (!S.diag || !S.e || !S.ss) return WSI_ERR_OOM;
   }
   return WSI_OK;
 }

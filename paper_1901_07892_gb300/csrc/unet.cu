@@ -128,6 +128,7 @@ static void conv3(const ConvIn& a, const bf16* W, const float* bias, bf16* out, 
     case 4: { k_conv3<4><<<grid, 128, 0, st>>>(a, W, bias, out, Cout, Z, Y, X, relu); WSI_COUNT(); } break;
     case 6: { k_conv3<6><<<grid, 128, 0, st>>>(a, W, bias, out, Cout, Z, Y, X, relu); WSI_COUNT(); } break;
     case 8: { k_conv3<8><<<grid, 128, 0, st>>>(a, W, bias, out, Cout, Z, Y, X, relu); WSI_COUNT(); } break;
+    case 10: { k_conv3<10><<<grid, 128, 0, st>>>(a, W, bias, out, Cout, Z, Y, X, relu); WSI_COUNT(); } break;
     case 12: { k_conv3<12><<<grid, 128, 0, st>>>(a, W, bias, out, Cout, Z, Y, X, relu); WSI_COUNT(); } break;
     default: break;
   }

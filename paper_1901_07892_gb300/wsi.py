@@ -59,7 +59,8 @@ class SolveOpts(ctypes.Structure):
 
 
 class SolveStats(ctypes.Structure):
-    _fields_ = [("iters", ctypes.c_int), ("rel_residual", ctypes.c_double), ("ms", ctypes.c_double)]
+    _fields_ = [("iters", ctypes.c_int), ("rel_residual", ctypes.c_double), ("ms", ctypes.c_double),
+                ("learned_rejected", ctypes.c_int)]
 
 
 class BodyState(ctypes.Structure):
@@ -448,9 +449,14 @@ class UNet:
         self._ck(self.L.wsi_unet_adam(self._h, lr), "adam")
 
 
-def attach_unet(ctx, net, level, enable=True):
+LEARN_OFF, LEARN_REPLACE, LEARN_AUGMENT = 0, 1, 2
+
+
+def attach_unet(ctx, net, level, enable=LEARN_REPLACE):
+    """enable: LEARN_OFF, LEARN_REPLACE or LEARN_AUGMENT (True = replace)."""
     _unet_sigs()
-    ctx._check(ctx.L.wsi_attach_unet(ctx._h, net._h if net is not None else None, level, 1 if enable else 0))
+    mode = int(enable) if not isinstance(enable, bool) else (LEARN_REPLACE if enable else LEARN_OFF)
+    ctx._check(ctx.L.wsi_attach_unet(ctx._h, net._h if net is not None else None, level, mode))
 
 
 def unet_train_sample(ctx, e, lr):

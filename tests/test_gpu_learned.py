@@ -30,11 +30,7 @@ def _built():
 
 
 def _bf16(a):
-    """Round float32 values to bfloat16 (nearest-even) and back."""
-    a = np.ascontiguousarray(a, dtype=np.float32)
-    u = a.view(np.uint32).astype(np.uint64)
-    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
-    return r.astype(np.uint32).view(np.float32)
+    return ou.bf16(a).astype(np.float32)
 
 
 def _unpack(p, c0, c1, c2):
@@ -70,6 +66,12 @@ def _pack_grads(g, c0, c1, c2):
 
 
 def test_forward_and_gradients_match_reference():
+    """Against the float64 reference twice: with its storage rounded to
+    bfloat16 where the kernels store bfloat16 (activations and the gradients
+    passed between layers), which leaves only float32-vs-float64 accumulation
+    and rare rounding-boundary flips (relative 1e-2 per layer); and without
+    any rounding, where ten layers of bfloat16 storage give a few percent on
+    the output."""
     c0, c1, c2 = 16, 32, 64
     net = wsi.UNet(8, 8, 8, c0, c1, c2, seed=3)
     rng = np.random.default_rng(0)
@@ -81,23 +83,31 @@ def test_forward_and_gradients_match_reference():
     loss = net.backward(t)
     g = net.grads()
     P = _unpack(p, c0, c1, c2)
-    ref, tape = ou.forward(P, np.transpose(x, (3, 0, 1, 2)).astype(np.float64))
-    ref_loss = ou.loss(ref, t[None].astype(np.float64))
-    gr, _ = ou.backward(P, tape, ref, t[None].astype(np.float64))
+    x64 = np.transpose(x, (3, 0, 1, 2)).astype(np.float64)
+    t64 = t[None].astype(np.float64)
+    # no storage rounding in the reference: bfloat16 error budget
+    ref, _ = ou.forward(P, x64)
     err = np.linalg.norm(out - ref[0]) / np.linalg.norm(ref[0])
     assert err < 3e-2, err
-    assert loss == pytest.approx(ref_loss, rel=5e-2)
+    # the kernels' storage decisions taken by the reference too
+    ref, tape = ou.forward(P, x64, rnd=ou.bf16)
+    err = np.linalg.norm(out - ref[0]) / np.linalg.norm(ref[0])
+    assert err < 2e-3, err
+    assert loss == pytest.approx(ou.loss(ref, t64), rel=2e-3)
+    gr, _ = ou.backward(P, tape, ref, t64, rnd=ou.bf16)
     G = _pack_grads(gr, c0, c1, c2)
-    # per layer: weights and biases
     off = 0
     shapes = ou.layer_shapes(3, c0, c1, c2)
+    errs = {}
     for name in NAMES:
         co, ci = shapes[name]
         n = 27 * co * (16 if name == "a1" else ci) + co
         a, b = g[off:off + n], G[off:off + n]
-        assert np.linalg.norm(a - b) <= 6e-2 * np.linalg.norm(b) + 1e-12, name
+        errs[name] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
         off += n
-    assert np.linalg.norm(g[off:] - G[off:]) <= 3e-2 * np.linalg.norm(G[off:])
+    errs["head"] = float(np.linalg.norm(g[off:] - G[off:]) / np.linalg.norm(G[off:]))
+    print("relative gradient error per layer", errs)
+    assert max(errs.values()) < 1e-2, errs
 
 
 def _smooth_field(rng, n, modes=6):
@@ -116,26 +126,39 @@ def _tank(seed, n=64):
     return c
 
 
-def test_training_lowers_loss_and_gain_is_measured():
-    n, level = 64, 2
-    nc = n // 4
-    net = wsi.UNet(nc, nc, nc, 16, 32, 64, seed=11)
-    rng = np.random.default_rng(5)
+def _train(net, level, mode, tanks, steps, rng, n):
     losses = []
-    t0 = time.time()
-    for tank_seed in range(6):
-        c = _tank(1000 + tank_seed, n)
+    for tank_seed in tanks:
+        c = _tank(tank_seed, n)
         ctx = wsi.Context.from_case(c, precision=wsi.PREC_MIXED)
         ctx.set_case(c, with_body=False)
-        wsi.attach_unet(ctx, net, level, enable=False)
-        for _ in range(60):
-            losses.append(wsi.unet_train_sample(ctx, _smooth_field(rng, nc), 2e-3))
+        wsi.attach_unet(ctx, net, level, enable=mode)
+        for k in range(steps):
+            lr = 2e-3 if len(losses) < 0.7 * steps * len(tanks) else 5e-4
+            losses.append(wsi.unet_train_sample(ctx, _smooth_field(rng, n >> level), lr))
         ctx.close()
-    train_s = time.time() - t0
-    first, last = np.mean(losses[:20]), np.mean(losses[-20:])
-    assert last < 0.5 * first, (first, last)
-    # gain on unseen tanks: V-cycles and time to 1e-8 of a pressure solve
-    results = []
+    return losses
+
+
+def test_training_lowers_loss_and_gain_is_measured():
+    """Train on exact pairs the solver's level operator generates (64^3 tanks,
+    network on the 16^3 level) for each learned mode, then solve unseen
+    tanks' pressure systems to 1e-8 with plain, replacing and augmenting
+    cycles.  Every solve converges (the plain cycle judges each learned one
+    and undoes it when it reduces the residual less, so a learned solve takes
+    at most two cycles more than the plain one); the cycle counts and times
+    are recorded."""
+    n, level = 64, 2
+    nc = n >> level
+    nets, summary = {}, {"train": {}, "solves": []}
+    for mode, flag in (("replace", wsi.LEARN_REPLACE), ("augment", wsi.LEARN_AUGMENT)):
+        net = wsi.UNet(nc, nc, nc, 16, 32, 64, seed=11)
+        t0 = time.time()
+        losses = _train(net, level, flag, range(1000, 1006), 200, np.random.default_rng(5), n)
+        summary["train"][mode] = {"steps": len(losses), "seconds": time.time() - t0,
+                                  "loss_first50": float(np.mean(losses[:50])),
+                                  "loss_last50": float(np.mean(losses[-50:]))}
+        nets[mode] = (net, flag)
     for s in (2000, 2001, 2002):
         c = _tank(s, n)
         ctx = wsi.Context.from_case(c, precision=wsi.PREC_MIXED)
@@ -143,16 +166,27 @@ def test_training_lowers_loss_and_gain_is_measured():
         y = inputs.random_cells(c.phi.shape, s)
         y -= y.mean()
         row = {"seed": s}
-        for mode in ("plain", "learned"):
-            wsi.attach_unet(ctx, net, level, enable=(mode == "learned"))
+        for mode in ("plain", "replace", "augment"):
+            net, flag = nets.get(mode, (nets["replace"][0], wsi.LEARN_OFF))
+            wsi.attach_unet(ctx, net, level, enable=flag)
             x, st = wsi.pressure_solve(ctx, y.ravel().copy(), rtol=1e-8, max_cycles=200)
-            assert st.rel_residual <= 1e-8, (mode, st.rel_residual)
-            row[mode] = {"cycles": st.iters, "ms": st.ms}
-        results.append(row)
+            row[mode] = {"cycles": st.iters, "ms": st.ms, "rejected_at": st.learned_rejected,
+                         "rel_residual": st.rel_residual}
         ctx.close()
-    summary = {"train_steps": len(losses), "train_seconds": train_s, "loss_first20": first, "loss_last20": last,
-               "solves": results}
+        c64 = wsi.Context.from_case(c, precision=wsi.PREC_FP64)
+        c64.set_case(c, with_body=False)
+        x, st = wsi.pressure_solve(c64, y.ravel().copy(), rtol=1e-8, max_cycles=200)
+        row["plain_fp64"] = {"cycles": st.iters, "ms": st.ms, "rel_residual": st.rel_residual}
+        c64.close()
+        summary["solves"].append(row)
     os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
     with open(os.path.join(ROOT, "gpurun_out", "learned_gain.json"), "w") as f:
         json.dump(summary, f, indent=1)
     print(json.dumps(summary))
+    for mode, tr in summary["train"].items():
+        assert tr["loss_last50"] < 0.5 * tr["loss_first50"], (mode, tr)
+    for row in summary["solves"]:
+        for mode in ("plain", "replace", "augment", "plain_fp64"):
+            assert row[mode]["rel_residual"] <= 1e-8, (mode, row)
+        for mode in ("replace", "augment"):
+            assert row[mode]["cycles"] <= row["plain"]["cycles"] + 2, row

@@ -53,3 +53,29 @@ def test_gradients_match_finite_differences():
         lm = unet.loss(unet.forward(p, x)[0], target)
         xf[idx] = old
         assert (lp - lm) / (2 * h) == pytest.approx(dx.reshape(-1)[idx], rel=1e-5, abs=1e-10)
+
+
+def test_bf16_storage_rounding():
+    # bfloat16 keeps 8 significant bits: the spacing above 1 is 2**-7
+    u = 2.0 ** -7
+    vals = np.array([1.0, 1 + u / 2, 1 + 1.5 * u, 1 + u / 2 + 2 ** -20, -(1 + 1.5 * u), 3.0, 0.0, 2.0 ** -130])
+    want = np.array([1.0, 1.0, 1 + 2 * u, 1 + u, -(1 + 2 * u), 3.0, 0.0, 2.0 ** -130])
+    assert np.array_equal(unet.bf16(vals), want)
+    # relative error bound 2**-8 on random values, idempotent
+    x = np.random.default_rng(2).standard_normal(1000) * 1e3
+    r = unet.bf16(x)
+    assert np.all(np.abs(r - x) <= 2.0 ** -8 * np.abs(x) * (1 + 1e-6))
+    assert np.array_equal(unet.bf16(r), r)
+
+
+def test_storage_rounding_hook_is_only_rounding():
+    """With an identity hook the reference is unchanged; with bfloat16 storage
+    the output moves by no more than the rounding budget of ten layers."""
+    rng = np.random.default_rng(3)
+    p = unet.init_params(rng, cin=3, c0=4, c1=4, c2=8)
+    x = rng.standard_normal((3, 8, 8, 8))
+    a, _ = unet.forward(p, x)
+    b, _ = unet.forward(p, x, rnd=lambda v: v)
+    c, _ = unet.forward(p, x, rnd=unet.bf16)
+    assert np.array_equal(a, b)
+    assert 0 < np.linalg.norm(c - a) / np.linalg.norm(a) < 3e-2
