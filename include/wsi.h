@@ -119,7 +119,8 @@ size_t wsi_velocity_size(const wsi_ctx* ctx);
 /* Create a context: grid, boundary conditions, solver options (Sec. 3.1 grid,
  * Sec. 4.2.4 solver).  stream: a cudaStream_t (NULL = legacy default stream).
  * The device is the current one.  *out is owned by the caller until
- * wsi_destroy.  WSI_ERR_INVALID_ARG on non-positive sizes or spacings. */
+ * wsi_destroy.  WSI_ERR_INVALID_ARG on non-positive sizes or spacings, or
+ * a grid with (nx+1)(ny+1)(nz+1) >= 2^31 (32-bit array offsets). */
 int wsi_create_grid(const wsi_grid_desc* desc, void* stream, wsi_ctx** out);
 void wsi_destroy(wsi_ctx* ctx);
 const char* wsi_last_error(const wsi_ctx* ctx);

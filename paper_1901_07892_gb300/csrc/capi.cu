@@ -185,6 +185,7 @@ PhaseConst phase_const(wsi_ctx* c) {
   double hc = c->g.n[2] == 1 ? sqrt(c->g.h[0] * c->g.h[1]) : cbrt(c->g.h[0] * c->g.h[1] * c->g.h[2]);
   pc.eps = c->desc.n_cells * hc;
   pc.inv_mu = c->inv_mu;
+  phase_tables(pc);
   return pc;
 }
 
@@ -630,6 +631,7 @@ int wsi_create_grid(const wsi_grid_desc* d, void* stream, wsi_ctx** out) {
     if (d->bc[i] != WSI_NO_SLIP && d->bc[i] != WSI_FREE_SLIP) return WSI_ERR_INVALID_ARG;
   if (d->nz == 1 && (d->bc[4] != WSI_FREE_SLIP || d->bc[5] != WSI_FREE_SLIP)) return WSI_ERR_INVALID_ARG;
   if (d->precision != WSI_PREC_FP64 && d->precision != WSI_PREC_MIXED) return WSI_ERR_INVALID_ARG;
+  if ((double)(d->nx + 1) * (d->ny + 1) * (d->nz + 1) >= 2147483648.0) return WSI_ERR_INVALID_ARG;
   wsi_ctx* c = new wsi_ctx();
   c->desc = *d;
   c->st = (cudaStream_t)stream;

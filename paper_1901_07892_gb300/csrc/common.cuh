@@ -155,6 +155,18 @@ __device__ __forceinline__ float d2f_fast(double a) {
   return __uint_as_float(sign | f);
 }
 
+// float32 -> float64 exactly, by integer operations (normal numbers and
+// zero; float32 subnormals become zero)
+__device__ __forceinline__ double f2d_fast(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int e = (u >> 23) & 0xFFu;
+  if (e == 0) return 0.0;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned long long ed = (unsigned long long)(e == 255u ? 2047u : e - 127u + 1023u) << 52;
+  const unsigned long long m = (unsigned long long)(u & 0x7FFFFFu) << 29;
+  return __longlong_as_double((long long)(sign | ed | m));
+}
+
 template <typename To, typename Ti>
 __device__ __forceinline__ To cvt(Ti a) {
   return (To)a;

@@ -1,18 +1,19 @@
-// Stokes matvec of the mixed path with the strain-rate term in double-float
-// arithmetic.
+// Stokes matvec of the mixed path in double-float arithmetic.
 //
-// GB300 issues float64 arithmetic at 1/64 of its float32 rate, and the
+// GB300 issues float64 arithmetic at about 1/64 of its float32 rate, and the
 // float64 Stokes matvec (about 130 float64 operations per cell) is the
-// largest single kernel of a time step.  Here each momentum row
-//     y = (rho/dt) q + G p - theta L_mu q
-// keeps the short terms in float64 and evaluates L_mu q -- about 35
-// operations -- with unevaluated float32 pairs (hi + lo, a 48-bit
-// significand): Dekker's exact product via fused multiply-add, Knuth's
-// error-free two-sum, renormalised after every operation.  Inputs stay
-// float64 in memory and are split into (hi, lo) by integer operations on
-// their bit patterns, so the float64 pipe only sees the final combination.
-// Relative error of L_mu q ~1e-14, far below what the float64 residual of
-// FGMRES needs; magnitudes below 2^-126 ~ 1.2e-38 are flushed to zero.
+// largest single kernel of a time step.  Here every row
+//     y_u = (rho/dt) q + G p - theta L_mu q,    y_p = -D q
+// is evaluated with unevaluated float32 pairs (hi + lo): Dekker's exact
+// product via fused multiply-add and Knuth's error-free sum of the leading
+// parts (the trailing parts are added plainly, an error of ~2^-46 of the
+// operands' magnitude, the class of a float64 operation on rounded inputs).
+// Inputs stay float64 in memory and are split into (hi, lo) by integer
+// operations on their bit patterns (47 significant bits kept); the float64
+// pipe sees one addition per row, which forms the float64 result.
+// Magnitudes below 2^-126 ~ 1.2e-38 are flushed to zero, and below 2^-103
+// only their leading 24 bits are kept.  Array offsets are 32-bit: every
+// array holds fewer than 2^31 elements (checked when the grid is created).
 #include <math.h>
 
 #include "internal.h"
@@ -25,16 +26,17 @@ struct dfl {
   float h, l;
 };
 
-// exact truncation of a float64 to its leading 24 significand bits (hi) and
-// the next 29 bits rounded to a float (lo); a = hi + lo to ~2^-47 relative
+// float64 -> (hi, lo): hi = the leading 24 significand bits (truncated), lo =
+// the next 23 bits, both exact, by integer operations and one float32
+// subtraction and multiplication
 __device__ __forceinline__ dfl df_split(double a) {
-  unsigned long long b = (unsigned long long)__double_as_longlong(a);
-  unsigned int hw = (unsigned int)(b >> 32);
-  unsigned int sign = hw & 0x80000000u;
-  int e = (int)((hw >> 20) & 0x7FFu);
-  int ef = e - 1023 + 127;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+  const unsigned int hw = (unsigned int)(b >> 32), lw = (unsigned int)b;
+  const unsigned int sign = hw & 0x80000000u;
+  const int e = (int)((hw >> 20) & 0x7FFu);
+  const int ef = e - 896;  // float32 biased exponent
   dfl r;
-  if (ef <= 0 || e == 0) {
+  if (ef <= 0) {
     r.h = 0.0f;
     r.l = 0.0f;
     return r;
@@ -44,11 +46,12 @@ __device__ __forceinline__ dfl df_split(double a) {
     r.l = 0.0f;
     return r;
   }
-  unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-  r.h = __uint_as_float(sign | ((unsigned int)ef << 23) | (unsigned int)(m >> 29));
-  unsigned int rem = (unsigned int)(m & 0x1FFFFFFFull);  // 29 bits, weight 2^(e-1075)
-  float lo = ldexpf((float)rem, e - 1075);
-  r.l = sign ? -lo : lo;
+  r.h = __uint_as_float(sign | ((unsigned int)ef << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
+  // bits 28..6 of the low word, weight 2^(e - 1069): as a fraction in [0, 1)
+  // (exact), then scaled by the signed power of two 2^(e - 1046)
+  const float frac = __uint_as_float(0x3F800000u | ((lw & 0x1FFFFFFFu) >> 6)) - 1.0f;
+  const int se = e - 919;
+  r.l = se > 0 ? frac * __uint_as_float(sign | ((unsigned int)se << 23)) : 0.0f;
   return r;
 }
 
@@ -66,14 +69,12 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - v)) + (b - v);
 }
 
+// error-free sum of the leading parts, trailing parts added plainly
 __device__ __forceinline__ dfl df_add(dfl x, dfl y) {
-  float s, e, t, f;
+  float s, e;
   two_sum(x.h, y.h, s, e);
-  two_sum(x.l, y.l, t, f);
-  e += t;
-  dfl r = quick_two_sum(s, e);
-  r.l += f;
-  return quick_two_sum(r.h, r.l);
+  e += x.l + y.l;
+  return quick_two_sum(s, e);
 }
 
 __device__ __forceinline__ dfl df_neg(dfl x) {
@@ -106,102 +107,92 @@ __device__ __forceinline__ double f2d_exact(float f) {
 __device__ __forceinline__ double df_to_double(dfl x) { return f2d_exact(x.h) + f2d_exact(x.l); }
 
 struct DfConst {
-  dfl ih[3];     // 1/h
+  dfl ih[3];       // 1/h
   dfl two_ih2[3];  // 2/h^2
+  dfl inv_dt;
+  dfl mtheta;      // -theta
+  float bcs[6];    // tangential ghost sign per wall
+  int fs[3][3];    // strides of face array C along each axis
+  int cs[3];       // strides of the cell arrays
+  int es[3][3];    // strides of edge array E
 };
 
-// L_mu q at the interior C-face (i,j,k) in double-float
+// momentum row C at the interior C-face (i, j, kk)
 template <int C>
-__device__ __forceinline__ dfl strain_df(const GridDev& g, const DfConst& k, const Coef<double>& cf,
-                                         const double* const* q, int i, int j, int kk) {
-  const double* qc = q[C];
-  int id3[3] = {i, j, kk};
-  int lo3[3] = {i, j, kk};
-  lo3[C] -= 1;
-  int hi3[3] = {i, j, kk};
-  hi3[C] += 1;
-  dfl q0 = df_split(qc[fidx(g, C, i, j, kk)]);
-  dfl qp = df_split(qc[fidx(g, C, hi3[0], hi3[1], hi3[2])]);
-  dfl qm = df_split(qc[fidx(g, C, lo3[0], lo3[1], lo3[2])]);
-  dfl mu_hi = df_split(cf.mu_cc[fidx(g, 3, i, j, kk)]);
-  dfl mu_lo = df_split(cf.mu_cc[fidx(g, 3, lo3[0], lo3[1], lo3[2])]);
-  dfl L = df_mul(k.two_ih2[C], df_sub(df_mul(mu_hi, df_sub(qp, q0)), df_mul(mu_lo, df_sub(q0, qm))));
+__device__ __forceinline__ double row_df(const GridDev& g, const DfConst& k, const Coef<double>& cf,
+                                         const CVel<double>& q, const double* __restrict__ p, int i, int j, int kk) {
+  const int id3[3] = {i, j, kk};
+  const int fb = i + j * k.fs[C][1] + kk * k.fs[C][2];
+  const int cb = i + j * k.cs[1] + kk * k.cs[2];  // the cell on the + side of the face
+  const double* __restrict__ qc = q.q[C];
+  const int sC = k.fs[C][C];
+  const dfl q0 = df_split(qc[fb]);
+  const dfl qp = df_split(qc[fb + sC]), qm = df_split(qc[fb - sC]);
+  const dfl muh = df_split(cf.mu_cc[cb]), mul = df_split(cf.mu_cc[cb - k.cs[C]]);
+  dfl L = df_mul(k.two_ih2[C], df_sub(df_mul(muh, df_sub(qp, q0)), df_mul(mul, df_sub(q0, qm))));
 #pragma unroll
   for (int D = 0; D < 3; ++D) {
     if (D == C) continue;
     const int E = edge_id(C, D);
-    const double* qd = q[D];
-    int a3[3] = {id3[0], id3[1], id3[2]};
-    int b3[3] = {id3[0], id3[1], id3[2]};
-    a3[D] += 1;
-    b3[D] -= 1;
-    dfl q_hi, q_lo;
-    if (a3[D] >= g.n[D]) {
-      q_hi = g.bc[2 * D + 1] < 0.0 ? df_neg(q0) : q0;
+    const int sD = k.fs[C][D];
+    dfl qh, ql;
+    if (id3[D] + 1 < g.n[D]) {
+      qh = df_split(qc[fb + sD]);
     } else {
-      q_hi = df_split(qc[fidx(g, C, a3[0], a3[1], a3[2])]);
+      qh = k.bcs[2 * D + 1] < 0.0f ? df_neg(q0) : q0;
     }
-    if (b3[D] < 0) {
-      q_lo = g.bc[2 * D] < 0.0 ? df_neg(q0) : q0;
+    if (id3[D] > 0) {
+      ql = df_split(qc[fb - sD]);
     } else {
-      q_lo = df_split(qc[fidx(g, C, b3[0], b3[1], b3[2])]);
+      ql = k.bcs[2 * D] < 0.0f ? df_neg(q0) : q0;
     }
-    int eh[3] = {id3[0], id3[1], id3[2]};
-    eh[D] += 1;
-    dfl mue_hi = df_split(cf.mu_e[E][eidx(g, E, eh[0], eh[1], eh[2])]);
-    dfl mue_lo = df_split(cf.mu_e[E][eidx(g, E, id3[0], id3[1], id3[2])]);
-    int d1[3] = {id3[0], id3[1], id3[2]};
-    d1[D] += 1;
-    int d0[3] = {d1[0], d1[1], d1[2]};
-    d0[C] -= 1;
-    int c0[3] = {id3[0], id3[1], id3[2]};
-    c0[C] -= 1;
-    dfl dqd_hi = df_mul(df_sub(df_split(qd[fidx(g, D, d1[0], d1[1], d1[2])]),
-                               df_split(qd[fidx(g, D, d0[0], d0[1], d0[2])])), k.ih[C]);
-    dfl dqd_lo = df_mul(df_sub(df_split(qd[fidx(g, D, id3[0], id3[1], id3[2])]),
-                               df_split(qd[fidx(g, D, c0[0], c0[1], c0[2])])), k.ih[C]);
-    dfl f_hi = df_mul(mue_hi, df_add(df_mul(df_sub(q_hi, q0), k.ih[D]), dqd_hi));
-    dfl f_lo = df_mul(mue_lo, df_add(df_mul(df_sub(q0, q_lo), k.ih[D]), dqd_lo));
-    L = df_add(L, df_mul(df_sub(f_hi, f_lo), k.ih[D]));
+    const int eb = i + j * k.es[E][1] + kk * k.es[E][2];
+    const dfl meh = df_split(cf.mu_e[E][eb + k.es[E][D]]), mel = df_split(cf.mu_e[E][eb]);
+    const double* __restrict__ qd = q.q[D];
+    const int db = i + j * k.fs[D][1] + kk * k.fs[D][2];
+    const int dD = k.fs[D][D], dC = k.fs[D][C];
+    const dfl a1 = df_split(qd[db + dD]), a0 = df_split(qd[db + dD - dC]);
+    const dfl b1 = df_split(qd[db]), b0 = df_split(qd[db - dC]);
+    const dfl fh = df_mul(meh, df_add(df_mul(df_sub(qh, q0), k.ih[D]), df_mul(df_sub(a1, a0), k.ih[C])));
+    const dfl fl = df_mul(mel, df_add(df_mul(df_sub(q0, ql), k.ih[D]), df_mul(df_sub(b1, b0), k.ih[C])));
+    L = df_add(L, df_mul(df_sub(fh, fl), k.ih[D]));
   }
-  return L;
+  const dfl rq = df_mul(df_mul(df_split(cf.rho_face[C][fb]), k.inv_dt), q0);
+  const dfl gp = df_mul(df_sub(df_split(p[cb]), df_split(p[cb - k.cs[C]])), k.ih[C]);
+  return df_to_double(df_add(df_add(rq, gp), df_mul(k.mtheta, L)));
 }
 
 template <int C>
 __device__ __forceinline__ void stokes_row_df(const GridDev& g, const DfConst& k, const Coef<double>& cf,
-                                              double inv_dt, double theta, const CVel<double>& q,
-                                              const double* __restrict__ p, double* out, int i, int j, int kk) {
-  int id3[3] = {i, j, kk};
-  size_t id = fidx(g, C, i, j, kk);
-  if (id3[C] == 0 || id3[C] == g.n[C]) {
-    out[id] = 0.0;
-    return;
-  }
-  double L = df_to_double(strain_df<C>(g, k, cf, q.q, i, j, kk));
-  int lo3[3] = {i, j, kk};
-  lo3[C] -= 1;
-  double gp = (p[fidx(g, 3, i, j, kk)] - p[fidx(g, 3, lo3[0], lo3[1], lo3[2])]) * g.ih[C];
-  out[id] = fma(-theta, L, cf.rho_face[C][id] * inv_dt * q.q[C][id] + gp);
+                                              const CVel<double>& q, const double* __restrict__ p, double* out,
+                                              int i, int j, int kk) {
+  const int id3[3] = {i, j, kk};
+  const int fb = i + j * k.fs[C][1] + kk * k.fs[C][2];
+  out[fb] = (id3[C] == 0 || id3[C] == g.n[C]) ? 0.0 : row_df<C>(g, k, cf, q, p, i, j, kk);
 }
 
-__global__ void k_stokes_df(GridDev g, DfConst k, Coef<double> cf, double inv_dt, double theta, CVel<double> q,
-                            const double* __restrict__ p, double* yu, double* yv, double* yw, double* yp) {
-  int z = blockIdx.z;
-  int nz = g.n[2];
-  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+__global__ void __launch_bounds__(256) k_stokes_df(GridDev g, DfConst k, Coef<double> cf, CVel<double> q,
+                                                   const double* __restrict__ p, double* yu, double* yv, double* yw,
+                                                   double* yp) {
+  const int z = blockIdx.z;
+  const int nz = g.n[2];
+  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   if (z < nz) {
-    if (i < g.n[0] + 1 && j < g.n[1]) stokes_row_df<0>(g, k, cf, inv_dt, theta, q, p, yu, i, j, z);
+    if (i < g.n[0] + 1 && j < g.n[1]) stokes_row_df<0>(g, k, cf, q, p, yu, i, j, z);
   } else if (z < 2 * nz) {
-    if (i < g.n[0] && j < g.n[1] + 1) stokes_row_df<1>(g, k, cf, inv_dt, theta, q, p, yv, i, j, z - nz);
+    if (i < g.n[0] && j < g.n[1] + 1) stokes_row_df<1>(g, k, cf, q, p, yv, i, j, z - nz);
   } else if (z < 3 * nz + 1) {
-    if (i < g.n[0] && j < g.n[1]) stokes_row_df<2>(g, k, cf, inv_dt, theta, q, p, yw, i, j, z - 2 * nz);
+    if (i < g.n[0] && j < g.n[1]) stokes_row_df<2>(g, k, cf, q, p, yw, i, j, z - 2 * nz);
   } else {
-    int kk = z - (3 * nz + 1);
+    const int kk = z - (3 * nz + 1);
     if (i < g.n[0] && j < g.n[1]) {
-      double d = (q.q[0][fidx(g, 0, i + 1, j, kk)] - q.q[0][fidx(g, 0, i, j, kk)]) * g.ih[0] +
-                 (q.q[1][fidx(g, 1, i, j + 1, kk)] - q.q[1][fidx(g, 1, i, j, kk)]) * g.ih[1] +
-                 (q.q[2][fidx(g, 2, i, j, kk + 1)] - q.q[2][fidx(g, 2, i, j, kk)]) * g.ih[2];
-      yp[fidx(g, 3, i, j, kk)] = -d;
+      const int f0 = i + j * k.fs[0][1] + kk * k.fs[0][2];
+      const int f1 = i + j * k.fs[1][1] + kk * k.fs[1][2];
+      const int f2 = i + j * k.fs[2][1] + kk * k.fs[2][2];
+      const dfl dx = df_mul(df_sub(df_split(q.q[0][f0 + 1]), df_split(q.q[0][f0])), k.ih[0]);
+      const dfl dy = df_mul(df_sub(df_split(q.q[1][f1 + k.fs[1][1]]), df_split(q.q[1][f1])), k.ih[1]);
+      const dfl dz = df_mul(df_sub(df_split(q.q[2][f2 + k.fs[2][2]]), df_split(q.q[2][f2])), k.ih[2]);
+      yp[i + j * k.cs[1] + kk * k.cs[2]] = -df_to_double(df_add(df_add(dx, dy), dz));
     }
   }
 }
@@ -223,10 +214,27 @@ void launch_stokes_df(const GridDev& g, const Coef<double>& cf, double inv_dt, d
     k.ih[a] = host_split(g.ih[a]);
     k.two_ih2[a] = host_split(2.0 * g.ih2[a]);
   }
+  k.inv_dt = host_split(inv_dt);
+  k.mtheta = host_split(-theta);
+  for (int w = 0; w < 6; ++w) k.bcs[w] = (float)g.bc[w];
+  const int n0 = g.n[0], n1 = g.n[1];
+  for (int c = 0; c < 3; ++c) {
+    const int fx = n0 + (c == 0), fy = n1 + (c == 1);
+    k.fs[c][0] = 1;
+    k.fs[c][1] = fx;
+    k.fs[c][2] = fx * fy;
+    const int ax = (c == 0 || c == 1) ? 1 : 0, ay = (c == 0 || c == 2) ? 1 : 0;
+    k.es[c][0] = 1;
+    k.es[c][1] = n0 + ax;
+    k.es[c][2] = (n0 + ax) * (n1 + ay);
+  }
+  k.cs[0] = 1;
+  k.cs[1] = n0;
+  k.cs[2] = n0 * n1;
   dim3 grid(cdiv(g.n[0] + 1, BX), cdiv(g.n[1] + 1, BY), 4 * g.n[2] + 1);
   ktimer_begin(KC_STOKES, st);
-  { k_stokes_df<<<grid, dim3(BX, BY), 0, st>>>(g, k, cf, inv_dt, theta, q, p, y + pk.off[0], y + pk.off[1],
-                                               y + pk.off[2], y + pk.off[3]); WSI_COUNT(); }
+  { k_stokes_df<<<grid, dim3(BX, BY), 0, st>>>(g, k, cf, q, p, y + pk.off[0], y + pk.off[1], y + pk.off[2],
+                                               y + pk.off[3]); WSI_COUNT(); }
   ktimer_end(KC_STOKES, st);
 }
 

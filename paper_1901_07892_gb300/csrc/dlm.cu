@@ -1,8 +1,9 @@
 // DLM rigidity step (Sec. 4.2.5) and the IB4 Lagrangian-Eulerian transfers
 // (Sec. 3.3) with the wall-adjoint forms J_BC / S_BC (Sec. 3.3.2).
 //
-// Interpolation is a gather (one thread per marker and component, 64 taps);
-// spreading scatters with float64 atomicAdd into the face arrays.  Taps that
+// Interpolation is a gather (one thread per marker: the kernel weights of
+// each axis are shared by the three components, 64 taps each); spreading
+// scatters with float64 atomicAdd into the face arrays.  Taps that
 // fall beyond a wall are folded onto their mirror image with the ghost sign
 // (tangential: the wall's sign; normal: odd about the wall face, whose own
 // value is zero so taps landing on it drop out), which makes S_BC the exact
@@ -13,11 +14,22 @@
 
 namespace wsi {
 
+// square root to ~1e-15 relative with two float64 operations: a float32
+// seed refined by one Newton (Heron) step, s1 = s0 + (x - s0^2) / (2 s0),
+// the reciprocal taken in float32 (its error enters only to second order)
+__device__ __forceinline__ double sqrt_nr(double x) {
+  const float xf = d2f_fast(x);
+  if (!(xf > 0.0f)) return 0.0;
+  const float s0f = sqrtf(xf);
+  const double s0 = f2d_fast(s0f);
+  return fma(fma(-s0, s0, x), f2d_fast(0.5f / s0f), s0);
+}
+
 // Peskin's four-point kernel (the published formula; Sec. 3.3.1 cites it)
 __device__ __forceinline__ double phi4(double r) {
   r = fabs(r);
-  if (r <= 1.0) return (3.0 - 2.0 * r + sqrt(fmax(1.0 + 4.0 * r - 4.0 * r * r, 0.0))) * 0.125;
-  if (r <= 2.0) return (5.0 - 2.0 * r - sqrt(fmax(-7.0 + 12.0 * r - 4.0 * r * r, 0.0))) * 0.125;
+  if (r <= 1.0) return (3.0 - 2.0 * r + sqrt_nr(1.0 + 4.0 * r - 4.0 * r * r)) * 0.125;
+  if (r <= 2.0) return (5.0 - 2.0 * r - sqrt_nr(-7.0 + 12.0 * r - 4.0 * r * r)) * 0.125;
   return 0.0;
 }
 
@@ -26,16 +38,18 @@ struct Tap {
   double w[4];  // kernel weight times ghost sign; 0 for dropped taps
 };
 
-__device__ __forceinline__ void taps_axis(const GridDev& g, int c, int d, double Xd, Tap& t) {
-  int n = g.n[d];
-  bool normal = (c == d);
-  double xs = normal ? Xd * g.ih[d] : Xd * g.ih[d] - 0.5;
-  int base = (int)floor(xs) - 1;
-  double s_lo = g.bc[2 * d], s_hi = g.bc[2 * d + 1];
+// the four taps along axis d of a marker at coordinate Xd, for a component
+// normal to d (normal = true: faces at integer positions) or tangential
+// (cell centres, offset by half a cell)
+__device__ __forceinline__ void taps_axis(const GridDev& g, bool normal, int d, double Xd, Tap& t) {
+  const int n = g.n[d];
+  const double xs = normal ? Xd * g.ih[d] : Xd * g.ih[d] - 0.5;
+  const int base = (int)floor(xs) - 1;
+  const double s_lo = g.bc[2 * d], s_hi = g.bc[2 * d + 1];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     int i = base + q;
-    double r = (double)i - xs;
+    const double r = (double)i - xs;
     double sg = 1.0;
     for (int it = 0; it < 8; ++it) {
       if (normal) {
@@ -46,55 +60,87 @@ __device__ __forceinline__ void taps_axis(const GridDev& g, int c, int d, double
         if (i >= n) { i = 2 * n - 1 - i; sg *= s_hi; }
       }
     }
-    bool valid = normal ? (i > 0 && i < n) : (i >= 0 && i < n);
+    const bool valid = normal ? (i > 0 && i < n) : (i >= 0 && i < n);
     t.idx[q] = valid ? i : 0;
-    t.w[q] = valid ? sg * phi4(r) : 0.0;
+    const double w = phi4(r);
+    t.w[q] = valid ? (sg < 0.0 ? -w : w) : 0.0;
   }
 }
 
-__global__ void k_interp(GridDev g, CVel<double> vel, const double* __restrict__ X, int n, double* U) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 3 * n) return;
-  int c = t / n, m = t - c * n;  // neighbouring threads: neighbouring markers
-  Tap tx, ty, tz;
-  taps_axis(g, c, 0, X[3 * m + 0], tx);
-  taps_axis(g, c, 1, X[3 * m + 1], ty);
-  taps_axis(g, c, 2, X[3 * m + 2], tz);
-  const double* q = vel.q[c];
-  double s = 0.0;
-  for (int kz = 0; kz < 4; ++kz) {
-    if (tz.w[kz] == 0.0) continue;
-    for (int ky = 0; ky < 4; ++ky) {
-      double wyz = tz.w[kz] * ty.w[ky];
-      if (wyz == 0.0) continue;
-      for (int kx = 0; kx < 4; ++kx) {
-        if (tx.w[kx] == 0.0) continue;
-        s += wyz * tx.w[kx] * q[fidx(g, c, tx.idx[kx], ty.idx[ky], tz.idx[kz])];
+// per marker: the normal and tangential taps of each axis (components share
+// them: component c uses the normal taps on axis c, tangential elsewhere)
+struct MarkerTaps {
+  Tap tn[3], tt[3];
+};
+
+__device__ __forceinline__ void marker_taps(const GridDev& g, const double* __restrict__ X, int m, MarkerTaps& T) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double xd = X[3 * m + d];
+    taps_axis(g, true, d, xd, T.tn[d]);
+    taps_axis(g, false, d, xd, T.tt[d]);
+  }
+}
+
+// one thread per marker, all three components; separable sums
+// sum_z w_z sum_y w_y sum_x w_x q
+__global__ void __launch_bounds__(128) k_interp(GridDev g, CVel<double> vel, const double* __restrict__ X, int n,
+                                                double* U) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n) return;
+  MarkerTaps T;
+  marker_taps(g, X, m, T);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const Tap& tx = c == 0 ? T.tn[0] : T.tt[0];
+    const Tap& ty = c == 1 ? T.tn[1] : T.tt[1];
+    const Tap& tz = c == 2 ? T.tn[2] : T.tt[2];
+    const double* __restrict__ q = vel.q[c];
+    const size_t sx = (size_t)(g.n[0] + (c == 0)), sy = sx * (size_t)(g.n[1] + (c == 1));
+    double s = 0.0;
+    for (int kz = 0; kz < 4; ++kz) {
+      if (tz.w[kz] == 0.0) continue;
+      double sz = 0.0;
+      for (int ky = 0; ky < 4; ++ky) {
+        if (ty.w[ky] == 0.0) continue;
+        const double* row = q + (size_t)tz.idx[kz] * sy + (size_t)ty.idx[ky] * sx;
+        double sr = 0.0;
+#pragma unroll
+        for (int kx = 0; kx < 4; ++kx) sr = fma(tx.w[kx], row[tx.idx[kx]], sr);
+        sz = fma(ty.w[ky], sr, sz);
       }
+      s = fma(tz.w[kz], sz, s);
     }
+    U[3 * m + c] = s;
   }
-  U[3 * m + c] = s;
 }
 
-__global__ void k_spread(GridDev g, const double* __restrict__ F, const double* __restrict__ X, int n, double scale,
-                         Vel<double> vel) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 3 * n) return;
-  int c = t / n, m = t - c * n;  // neighbouring threads: neighbouring markers
-  Tap tx, ty, tz;
-  taps_axis(g, c, 0, X[3 * m + 0], tx);
-  taps_axis(g, c, 1, X[3 * m + 1], ty);
-  taps_axis(g, c, 2, X[3 * m + 2], tz);
-  double f = F[3 * m + c] * scale;
-  double* q = vel.q[c];
-  for (int kz = 0; kz < 4; ++kz) {
-    if (tz.w[kz] == 0.0) continue;
-    for (int ky = 0; ky < 4; ++ky) {
-      double wyz = tz.w[kz] * ty.w[ky];
-      if (wyz == 0.0) continue;
-      for (int kx = 0; kx < 4; ++kx) {
-        if (tx.w[kx] == 0.0) continue;
-        atomicAdd(&q[fidx(g, c, tx.idx[kx], ty.idx[ky], tz.idx[kz])], f * wyz * tx.w[kx]);
+__global__ void __launch_bounds__(128) k_spread(GridDev g, const double* __restrict__ F,
+                                                const double* __restrict__ X, int n, double scale, Vel<double> vel) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n) return;
+  MarkerTaps T;
+  marker_taps(g, X, m, T);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const Tap& tx = c == 0 ? T.tn[0] : T.tt[0];
+    const Tap& ty = c == 1 ? T.tn[1] : T.tt[1];
+    const Tap& tz = c == 2 ? T.tn[2] : T.tt[2];
+    double* q = vel.q[c];
+    const size_t sx = (size_t)(g.n[0] + (c == 0)), sy = sx * (size_t)(g.n[1] + (c == 1));
+    const double f = F[3 * m + c] * scale;
+    double fx[4];
+#pragma unroll
+    for (int kx = 0; kx < 4; ++kx) fx[kx] = f * tx.w[kx];
+    for (int kz = 0; kz < 4; ++kz) {
+      if (tz.w[kz] == 0.0) continue;
+      for (int ky = 0; ky < 4; ++ky) {
+        const double wyz = tz.w[kz] * ty.w[ky];
+        if (wyz == 0.0) continue;
+        double* row = q + (size_t)tz.idx[kz] * sy + (size_t)ty.idx[ky] * sx;
+#pragma unroll
+        for (int kx = 0; kx < 4; ++kx)
+          if (tx.w[kx] != 0.0) atomicAdd(&row[tx.idx[kx]], wyz * fx[kx]);
       }
     }
   }
@@ -104,7 +150,7 @@ void launch_ib_interp(const GridDev& g, const double* const vel[3], const double
                       cudaStream_t st) {
   if (n <= 0) return;
   CVel<double> v{{vel[0], vel[1], vel[2]}};
-  { k_interp<<<cdiv(3LL * n, 128), 128, 0, st>>>(g, v, X, n, U); WSI_COUNT(); }
+  { k_interp<<<cdiv(n, 128), 128, 0, st>>>(g, v, X, n, U); WSI_COUNT(); }
 }
 
 void launch_ib_spread(const GridDev& g, const double* F, const double* X, int n, double dV, double* const vel[3],
@@ -112,7 +158,7 @@ void launch_ib_spread(const GridDev& g, const double* F, const double* X, int n,
   if (n <= 0) return;
   Vel<double> v{{vel[0], vel[1], vel[2]}};
   double scale = dV / (g.h[0] * g.h[1] * g.h[2]);
-  { k_spread<<<cdiv(3LL * n, 128), 128, 0, st>>>(g, F, X, n, scale, v); WSI_COUNT(); }
+  { k_spread<<<cdiv(n, 128), 128, 0, st>>>(g, F, X, n, scale, v); WSI_COUNT(); }
 }
 
 // ---------------------------------------------------------------- rigid sums

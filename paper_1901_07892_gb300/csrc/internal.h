@@ -24,7 +24,15 @@ struct Coef {
 struct PhaseConst {
   double rho_l, rho_g, rho_s, mu_l, mu_g, mu_s, eps;
   double* inv_mu;  // scratch of one cell field for 1/mu (null: edges divide per access)
+  // filled by phase_tables(): 1/eps, and the values a cell, face or edge
+  // takes away from both smoothing bands, indexed h1 + 2 h2 with h1, h2 in
+  // {0, 1} the two Heavisides, each computed by the same expression as inside
+  // the bands so that both give identical results there
+  double inv_eps;
+  double rho_tab[4], beta_tab[4], flow_tab[2], mu_tab[4], imu_tab[4], mue_tab[4];
 };
+// fill the derived fields of pc from its properties (host)
+void phase_tables(PhaseConst& pc);
 void launch_materials(const GridDev& g, const PhaseConst& pc, const double* phi, const double* psi,
                       double* rho_cc, double* mu_cc, double* const rho_face[3], double* const beta[3],
                       double* const rho_flow[3], double* const mu_e[3], cudaStream_t st);

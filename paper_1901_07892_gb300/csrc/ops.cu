@@ -18,15 +18,36 @@ static constexpr int BX = 32, BY = 8;
 static inline dim3 grid3(int nx, int ny, int nz) { return dim3(cdiv(nx, BX), cdiv(ny, BY), nz); }
 
 // =========================================================== materials
-__device__ __forceinline__ double heaviside(double phi, double eps) {
-  if (phi < -eps) return 0.0;
-  if (phi > eps) return 1.0;
-  return 0.5 * (1.0 + phi / eps + sin(M_PI * phi / eps) / M_PI);
+// Smoothed Heaviside of Sec. 2 with t = phi / eps: 0 for t <= -1, 1 for
+// t >= 1, the sine ramp between.  The band test runs on a float32 copy of t
+// made by integer operations (float64 comparisons issue on GB300's narrow
+// float64 pipe); where that copy is ambiguous, |t| within 2^-24 of 1, the
+// ramp differs from its limit by ~(1 - |t|)^3, far below float64 resolution.
+// code: 0 or 1 away from the band (value exactly 0 or 1), 2 inside.
+__device__ __forceinline__ double heav(double phi, double inv_eps, int& code) {
+  const double t = phi * inv_eps;
+  const float tf = d2f_fast(t);
+  if (tf <= -1.0f) {
+    code = 0;
+    return 0.0;
+  }
+  if (tf >= 1.0f) {
+    code = 1;
+    return 1.0;
+  }
+  code = 2;
+  return 0.5 * (1.0 + t + sin(M_PI * t) / M_PI);
 }
-__device__ __forceinline__ double two_stage(double phi, double psi, double zl, double zg, double zs, double eps) {
-  double zf = zl + (zg - zl) * heaviside(phi, eps);
-  return zs + (zf - zs) * heaviside(psi, eps);
+
+// two-stage blend (Sec. 2): fluid value from phi, then solid from psi; away
+// from both bands the value comes from the table (same expression, host)
+__device__ __forceinline__ double two_stage(double h1, int c1, double h2, int c2, double zl, double zg, double zs,
+                                            const double* tab) {
+  if (c1 < 2 && c2 < 2) return tab[c1 + 2 * c2];
+  const double zf = zl + (zg - zl) * h1;
+  return zs + (zf - zs) * h2;
 }
+
 __device__ __forceinline__ double cell_at(const GridDev& g, const double* a, int i, int j, int k) {
   i = clampi(i, 0, g.n[0] - 1);
   j = clampi(j, 0, g.n[1] - 1);
@@ -39,11 +60,12 @@ __global__ void k_mat_cells(GridDev g, PhaseConst pc, const double* __restrict__
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (i >= g.n[0] || j >= g.n[1]) return;
   size_t id = fidx(g, 3, i, j, k);
-  double a = phi[id], b = psi[id];
-  if (rho_cc) rho_cc[id] = two_stage(a, b, pc.rho_l, pc.rho_g, pc.rho_s, pc.eps);
-  double mu = two_stage(a, b, pc.mu_l, pc.mu_g, pc.mu_s, pc.eps);
+  int c1, c2;
+  const double h1 = heav(phi[id], pc.inv_eps, c1), h2 = heav(psi[id], pc.inv_eps, c2);
+  if (rho_cc) rho_cc[id] = two_stage(h1, c1, h2, c2, pc.rho_l, pc.rho_g, pc.rho_s, pc.rho_tab);
+  const double mu = two_stage(h1, c1, h2, c2, pc.mu_l, pc.mu_g, pc.mu_s, pc.mu_tab);
   mu_cc[id] = mu;
-  if (pc.inv_mu) pc.inv_mu[id] = 1.0 / mu;
+  if (pc.inv_mu) pc.inv_mu[id] = (c1 < 2 && c2 < 2) ? pc.imu_tab[c1 + 2 * c2] : 1.0 / mu;
 }
 
 // face density from face-averaged level sets (wall faces: the interior cell)
@@ -54,31 +76,36 @@ __global__ void k_mat_faces(GridDev g, PhaseConst pc, const double* __restrict__
   if (i >= ext(g, C, 0) || j >= ext(g, C, 1)) return;
   int lo[3] = {i, j, k}, hi[3] = {i, j, k};
   lo[C] -= 1;
-  double pa = 0.5 * (cell_at(g, phi, lo[0], lo[1], lo[2]) + cell_at(g, phi, hi[0], hi[1], hi[2]));
+  const double pa = 0.5 * (cell_at(g, phi, lo[0], lo[1], lo[2]) + cell_at(g, phi, hi[0], hi[1], hi[2]));
+  int c1;
+  const double h1 = heav(pa, pc.inv_eps, c1);
   size_t id = fidx(g, C, i, j, k);
   if (rho_face) {
-    double sa = 0.5 * (cell_at(g, psi, lo[0], lo[1], lo[2]) + cell_at(g, psi, hi[0], hi[1], hi[2]));
-    double r = two_stage(pa, sa, pc.rho_l, pc.rho_g, pc.rho_s, pc.eps);
+    const double sa = 0.5 * (cell_at(g, psi, lo[0], lo[1], lo[2]) + cell_at(g, psi, hi[0], hi[1], hi[2]));
+    int c2;
+    const double h2 = heav(sa, pc.inv_eps, c2);
+    const double r = two_stage(h1, c1, h2, c2, pc.rho_l, pc.rho_g, pc.rho_s, pc.rho_tab);
     rho_face[id] = r;
-    if (beta) beta[id] = 1.0 / r;
+    if (beta) beta[id] = (c1 < 2 && c2 < 2) ? pc.beta_tab[c1 + 2 * c2] : 1.0 / r;
   }
-  if (rho_flow) rho_flow[id] = pc.rho_l + (pc.rho_g - pc.rho_l) * heaviside(pa, pc.eps);
+  if (rho_flow) rho_flow[id] = c1 < 2 ? pc.flow_tab[c1] : pc.rho_l + (pc.rho_g - pc.rho_l) * h1;
 }
 
 // Harmonic mean 4 / sum(1/mu) of the 4 cells around an edge (mirror ghosts
 // at walls).  The reciprocals come precomputed once per cell when inv_mu is
 // given: a float64 division costs tens of instructions at GB300's float64
-// rate, and each cell feeds twelve edges.
+// rate, and each cell feeds twelve edges.  Where the four reciprocals are
+// bit-identical table values the mean comes from the table as well.
 template <int E>
-__global__ void k_mat_edges(GridDev g, const double* __restrict__ mu_cc, const double* __restrict__ inv_mu,
-                            double* mu_e) {
+__global__ void k_mat_edges(GridDev g, PhaseConst pc, const double* __restrict__ mu_cc,
+                            const double* __restrict__ inv_mu, double* mu_e) {
   // E = 0: xy edges, 1: xz, 2: yz
   constexpr int A1 = (E == 2) ? 1 : 0;
   constexpr int A2 = (E == 0) ? 1 : 2;
   int ex = g.n[0] + (A1 == 0 || A2 == 0), ey = g.n[1] + (A1 == 1 || A2 == 1);
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (i >= ex || j >= ey) return;
-  double s = 0.0;
+  double v[4];
 #pragma unroll
   for (int o1 = 0; o1 < 2; ++o1)
 #pragma unroll
@@ -86,9 +113,35 @@ __global__ void k_mat_edges(GridDev g, const double* __restrict__ mu_cc, const d
       int c[3] = {i, j, k};
       c[A1] -= o1;
       c[A2] -= o2;
-      s += inv_mu ? cell_at(g, inv_mu, c[0], c[1], c[2]) : 1.0 / cell_at(g, mu_cc, c[0], c[1], c[2]);
+      v[2 * o1 + o2] = inv_mu ? cell_at(g, inv_mu, c[0], c[1], c[2]) : 1.0 / cell_at(g, mu_cc, c[0], c[1], c[2]);
     }
-  mu_e[eidx(g, E, i, j, k)] = 4.0 / s;
+  const long long b0 = __double_as_longlong(v[0]);
+  if (b0 == __double_as_longlong(v[1]) && b0 == __double_as_longlong(v[2]) && b0 == __double_as_longlong(v[3])) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (b0 == __double_as_longlong(pc.imu_tab[t])) {
+        mu_e[eidx(g, E, i, j, k)] = pc.mue_tab[t];
+        return;
+      }
+  }
+  mu_e[eidx(g, E, i, j, k)] = 4.0 / (((v[0] + v[1]) + v[2]) + v[3]);
+}
+
+void phase_tables(PhaseConst& pc) {
+  pc.inv_eps = 1.0 / pc.eps;
+  for (int h2 = 0; h2 < 2; ++h2)
+    for (int h1 = 0; h1 < 2; ++h1) {
+      const int t = h1 + 2 * h2;
+      const double rf = pc.rho_l + (pc.rho_g - pc.rho_l) * (double)h1;
+      pc.rho_tab[t] = pc.rho_s + (rf - pc.rho_s) * (double)h2;
+      pc.beta_tab[t] = 1.0 / pc.rho_tab[t];
+      const double mf = pc.mu_l + (pc.mu_g - pc.mu_l) * (double)h1;
+      pc.mu_tab[t] = pc.mu_s + (mf - pc.mu_s) * (double)h2;
+      pc.imu_tab[t] = 1.0 / pc.mu_tab[t];
+      const double x = pc.imu_tab[t];
+      pc.mue_tab[t] = 4.0 / (((x + x) + x) + x);
+    }
+  for (int h1 = 0; h1 < 2; ++h1) pc.flow_tab[h1] = pc.rho_l + (pc.rho_g - pc.rho_l) * (double)h1;
 }
 
 void launch_materials(const GridDev& g, const PhaseConst& pc, const double* phi, const double* psi, double* rho_cc,
@@ -101,9 +154,9 @@ void launch_materials(const GridDev& g, const PhaseConst& pc, const double* phi,
                                                                              rho_flow[1]); WSI_COUNT(); }
   { k_mat_faces<2><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, rho_face[2], beta[2],
                                                                              rho_flow[2]); WSI_COUNT(); }
-  { k_mat_edges<0><<<grid3(g.n[0] + 1, g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, mu_cc, pc.inv_mu, mu_e[0]); WSI_COUNT(); }
-  { k_mat_edges<1><<<grid3(g.n[0] + 1, g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, pc.inv_mu, mu_e[1]); WSI_COUNT(); }
-  { k_mat_edges<2><<<grid3(g.n[0], g.n[1] + 1, g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, pc.inv_mu, mu_e[2]); WSI_COUNT(); }
+  { k_mat_edges<0><<<grid3(g.n[0] + 1, g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, mu_cc, pc.inv_mu, mu_e[0]); WSI_COUNT(); }
+  { k_mat_edges<1><<<grid3(g.n[0] + 1, g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, pc, mu_cc, pc.inv_mu, mu_e[1]); WSI_COUNT(); }
+  { k_mat_edges<2><<<grid3(g.n[0], g.n[1] + 1, g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, pc, mu_cc, pc.inv_mu, mu_e[2]); WSI_COUNT(); }
 }
 
 void launch_face_density(const GridDev& g, const PhaseConst& pc, const double* phi, const double* psi,
@@ -119,9 +172,9 @@ void launch_face_density(const GridDev& g, const PhaseConst& pc, const double* p
 void launch_mu_only(const GridDev& g, const PhaseConst& pc, const double* phi, const double* psi, double* mu_cc,
                     double* const mu_e[3], cudaStream_t st) {
   { k_mat_cells<<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, nullptr, mu_cc); WSI_COUNT(); }
-  { k_mat_edges<0><<<grid3(g.n[0] + 1, g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, mu_cc, pc.inv_mu, mu_e[0]); WSI_COUNT(); }
-  { k_mat_edges<1><<<grid3(g.n[0] + 1, g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, pc.inv_mu, mu_e[1]); WSI_COUNT(); }
-  { k_mat_edges<2><<<grid3(g.n[0], g.n[1] + 1, g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, mu_cc, pc.inv_mu, mu_e[2]); WSI_COUNT(); }
+  { k_mat_edges<0><<<grid3(g.n[0] + 1, g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, mu_cc, pc.inv_mu, mu_e[0]); WSI_COUNT(); }
+  { k_mat_edges<1><<<grid3(g.n[0] + 1, g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, pc, mu_cc, pc.inv_mu, mu_e[1]); WSI_COUNT(); }
+  { k_mat_edges<2><<<grid3(g.n[0], g.n[1] + 1, g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, pc, mu_cc, pc.inv_mu, mu_e[2]); WSI_COUNT(); }
 }
 
 void launch_rho_flow(const GridDev& g, const PhaseConst& pc, const double* phi, double* const rho_flow[3],
