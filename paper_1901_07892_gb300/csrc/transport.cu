@@ -22,7 +22,7 @@
 namespace wsi {
 
 static constexpr int BX = 32, BY = 8;
-static constexpr int ZCHUNK = 8;
+static constexpr int ZCHUNK = 32;
 
 // Division-free bounded CUI: with num = qC - qU and den = qD - qU,
 // t = num/den lies in a branch interval iff num*sign(den) lies in den-scaled
@@ -121,6 +121,87 @@ __device__ __forceinline__ T cv_flux(const GridDev& g, const CVel<T>& vel, const
   return F;
 }
 
+// Entry m of the C-face array along axis D with two ghost layers: the stored
+// index it maps to and the velocity ghost sign (ext_get without the load).
+template <int C, int D, typename T>
+__device__ __forceinline__ int mirror_index(const GridDev& g, int m, T& s) {
+  const int n = g.n[D] + (C == D ? 1 : 0);
+  int mm = m;
+  s = T(1);
+  if (m < 0) {
+    const int gl = -m;
+    if (C == D) {
+      mm = gl;
+      s = T(-1);
+    } else {
+      mm = gl - 1;
+      s = gbc<T>(g, 2 * D);
+    }
+  } else if (m >= n) {
+    const int gl = m - (n - 1);
+    if (C == D) {
+      mm = (n - 1) - gl;
+      s = T(-1);
+    } else {
+      mm = n - gl;
+      s = gbc<T>(g, 2 * D + 1);
+    }
+  }
+  return clampi(mm, 0, n - 1);
+}
+
+// Limiter taps of the two CV faces of a column along D: entries mlo-2 ..
+// mlo+2, mlo that of the hi face; the hi face uses entries 1..4, the lo face
+// (one position lower) entries 0..3.
+template <typename T>
+struct Taps {
+  int o[5];  // offsets into the C-face array from the column base
+  T s[5];    // velocity ghost signs
+};
+
+template <int C, int D, typename T>
+__device__ __forceinline__ void make_taps(const GridDev& g, int mlo, int stride, Taps<T>& t) {
+#pragma unroll
+  for (int q = 0; q < 5; ++q) t.o[q] = mirror_index<C, D, T>(g, mlo - 2 + q, t.s[q]) * stride;
+}
+
+// limited value from the four taps for advective velocity adv
+template <typename T>
+__device__ __forceinline__ T lim4(T t0, T t1, T t2, T t3, T adv) {
+  return adv > T(0) ? cui<T>(t0, t1, t2) : cui<T>(t3, t2, t1);
+}
+
+// flux through the CV face whose taps start at entry f (0: lo face, 1: hi)
+template <bool WITHV, typename T>
+__device__ __forceinline__ T flux_from(const T* __restrict__ rho, const T* __restrict__ qc, size_t base,
+                                       const Taps<T>& t, int f, T adv) {
+  T F = adv * lim4<T>(rho[base + t.o[f]], rho[base + t.o[f + 1]], rho[base + t.o[f + 2]], rho[base + t.o[f + 3]],
+                      adv);
+  if (WITHV)
+    F *= lim4<T>(t.s[f] * qc[base + t.o[f]], t.s[f + 1] * qc[base + t.o[f + 1]], t.s[f + 2] * qc[base + t.o[f + 2]],
+                 t.s[f + 3] * qc[base + t.o[f + 3]], adv);
+  return F;
+}
+
+// advective velocity at the D-direction CV face at position m of the C-face
+// column through (i, j, k): C == D: mean of C-faces m and m+1; else mean of
+// the two D-faces at D-index m adjacent along C
+template <int C, int D, typename T>
+__device__ __forceinline__ T adv_at(const GridDev& g, const CVel<T>& vel, int i, int j, int k, int m) {
+  int a[3] = {i, j, k};
+  a[D] = m;
+  if (C == D) {
+    const size_t id = fidx(g, C, a[0], a[1], a[2]);
+    const size_t st = C == 0 ? 1 : (C == 1 ? (size_t)g.n[0] : (size_t)g.n[0] * g.n[1]);
+    return T(0.5) * (vel.q[C][id] + vel.q[C][id + st]);
+  }
+  const size_t id1 = fidx(g, D, a[0], a[1], a[2]);
+  const size_t sc = C == 0 ? 1 : (C == 1 ? (size_t)(g.n[0] + (D == 0)) : (size_t)(g.n[0] + (D == 0)) * (g.n[1] + (D == 1)));
+  return T(0.5) * (vel.q[D][id1 - sc] + vel.q[D][id1]);
+}
+
+// The limiter taps along x and y depend only on the thread's (i, j) and are
+// built once; along z once per plane.  Array offsets follow from strides.
 template <int C, bool WITHV, typename T>
 __global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, CVel<T> vel, const T* __restrict__ rho,
                                                       T* out) {
@@ -132,57 +213,59 @@ __global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, CVel<T> vel, co
   const bool inside = i < e0 && j < e1;
   const int k0 = blockIdx.z * ZCHUNK;
   const int k1 = min(k0 + ZCHUNK, e2);
-  // CV-face positions of this C-face: lo along D is (index - 1) for D == C
-  // (cells) and (index) for D != C (edges); hi = lo + 1
   const int ox = (C == 0) ? -1 : 0, oy = (C == 1) ? -1 : 0, oz = (C == 2) ? -1 : 0;
+  const size_t fx = (size_t)e0, plane = (size_t)e0 * e1;
+  const T* __restrict__ qc = vel.q[C];
+  // CV-face positions: hi = index + o + 1, lo = index + o; the taps start at
+  // mlo = m (C == D) or m - 1 (C != D)
+  const int mxh = i + ox + 1, mxl = i + ox, myh = j + oy + 1, myl = j + oy;
+  Taps<T> tx5, ty5;
+  make_taps<C, 0, T>(g, C == 0 ? mxh : mxh - 1, 1, tx5);
+  make_taps<C, 1, T>(g, C == 1 ? myh : myh - 1, (int)fx, ty5);
   T Fz_lo = T(0);
   for (int k = k0; k < k1; ++k) {
-    int i3[3] = {i, j, k};
     const int idC = (C == 0) ? i : ((C == 1) ? j : k);
     const bool wall = idC == 0 || idC == g.n[C];
-    // x-direction fluxes: hi into column tx+1, lo halo by tx == 0
+    const size_t rowx = (size_t)k * plane + (size_t)j * fx;  // x taps: row base
+    const size_t coly = (size_t)k * plane + (size_t)i;       // y taps: column base
     if (inside) {
-      bool okx = (C == 0) || !wall;
+      const bool okx = (C == 0) || !wall;
       T hi = T(0), lo = T(0);
       if (okx) {
-        int m = i + ox + 1;
-        if (C != 0 || m <= g.n[0] - 1) hi = cv_flux<C, 0, WITHV, T>(g, vel, rho, i3, m);
-        if (tx == 0) {
-          int ml = i + ox;
-          if (C != 0 || ml >= 0) lo = cv_flux<C, 0, WITHV, T>(g, vel, rho, i3, ml);
-        }
+        if (C != 0 || mxh <= g.n[0] - 1) hi = flux_from<WITHV, T>(rho, qc, rowx, tx5, 1, adv_at<C, 0, T>(g, vel, i, j, k, mxh));
+        if (tx == 0 && (C != 0 || mxl >= 0)) lo = flux_from<WITHV, T>(rho, qc, rowx, tx5, 0, adv_at<C, 0, T>(g, vel, i, j, k, mxl));
       }
       sFx[ty][tx + 1] = hi;
       if (tx == 0) sFx[ty][0] = lo;
-      bool oky = (C == 1) || !wall;
+      const bool oky = (C == 1) || !wall;
       hi = T(0);
       lo = T(0);
       if (oky) {
-        int m = j + oy + 1;
-        if (C != 1 || m <= g.n[1] - 1) hi = cv_flux<C, 1, WITHV, T>(g, vel, rho, i3, m);
-        if (ty == 0) {
-          int ml = j + oy;
-          if (C != 1 || ml >= 0) lo = cv_flux<C, 1, WITHV, T>(g, vel, rho, i3, ml);
-        }
+        if (C != 1 || myh <= g.n[1] - 1) hi = flux_from<WITHV, T>(rho, qc, coly, ty5, 1, adv_at<C, 1, T>(g, vel, i, j, k, myh));
+        if (ty == 0 && (C != 1 || myl >= 0)) lo = flux_from<WITHV, T>(rho, qc, coly, ty5, 0, adv_at<C, 1, T>(g, vel, i, j, k, myl));
       }
       sFy[ty + 1][tx] = hi;
       if (ty == 0) sFy[0][tx] = lo;
     }
     __syncthreads();
     if (inside) {
-      bool okz = (C == 2) || !wall;
+      const bool okz = (C == 2) || !wall;
       T Fz_hi = T(0);
       if (okz) {
-        int m = k + oz + 1;
-        if (C != 2 || m <= g.n[2] - 1) Fz_hi = cv_flux<C, 2, WITHV, T>(g, vel, rho, i3, m);
+        const size_t colz = (size_t)j * fx + (size_t)i;
+        const int mzh = k + oz + 1;
+        Taps<T> tz;
+        make_taps<C, 2, T>(g, C == 2 ? mzh : mzh - 1, (int)plane, tz);
+        if (C != 2 || mzh <= g.n[2] - 1) Fz_hi = flux_from<WITHV, T>(rho, qc, colz, tz, 1, adv_at<C, 2, T>(g, vel, i, j, k, mzh));
         if (k == k0) {
-          int ml = k + oz;
-          Fz_lo = (C != 2 || ml >= 0) ? cv_flux<C, 2, WITHV, T>(g, vel, rho, i3, ml) : T(0);
+          const int mzl = k + oz;
+          Fz_lo = (C != 2 || mzl >= 0) ? flux_from<WITHV, T>(rho, qc, colz, tz, 0, adv_at<C, 2, T>(g, vel, i, j, k, mzl))
+                                       : T(0);
         }
       }
-      T r = (sFx[ty][tx + 1] - sFx[ty][tx]) * ginv<T>(g, 0) + (sFy[ty + 1][tx] - sFy[ty][tx]) * ginv<T>(g, 1) +
-            (Fz_hi - Fz_lo) * ginv<T>(g, 2);
-      out[fidx(g, C, i, j, k)] = wall ? T(0) : r;
+      const T r = (sFx[ty][tx + 1] - sFx[ty][tx]) * ginv<T>(g, 0) + (sFy[ty + 1][tx] - sFy[ty][tx]) * ginv<T>(g, 1) +
+                  (Fz_hi - Fz_lo) * ginv<T>(g, 2);
+      out[(size_t)k * plane + (size_t)j * fx + i] = wall ? T(0) : r;
       Fz_lo = Fz_hi;
     }
     __syncthreads();
