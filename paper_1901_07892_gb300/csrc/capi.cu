@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <chrono>
 #include <random>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -102,6 +103,12 @@ struct wsi_ctx {
   // float64 part of the momentum right-hand side fixed over a step's cycles
   double* b0 = nullptr;
   double* inv_mu = nullptr;  // materials scratch: 1/mu per cell
+  // mixed path: split (hi, lo) copies of the operator coefficients (refreshed
+  // at the start of every solve) and of the matvec input
+  float2* df_rho[3] = {nullptr, nullptr, nullptr};
+  float2* df_mu_cc = nullptr;
+  float2* df_mu_e[3] = {nullptr, nullptr, nullptr};
+  float2* df_x = nullptr;
   // a fully locked body at rest never moves: psi is rebuilt once, then kept
   bool psi_static_done = false;
   // mu_cc / mu_e hold mu(phi^n, psi^n) (true right after a step)
@@ -241,15 +248,33 @@ void pc_apply(wsi_ctx* c, double dt, const double* v, double* z) {
     precond_apply<double>(c->P64, c->g, c->opts, dt, v, z, c->st);
 }
 
-// K x: float64 on the plain path; on the mixed path the strain-rate term in
-// double-float arithmetic (same accuracy class, a fraction of the float64
-// instructions)
+// split copies of the coefficients for the double-float matvec (mixed path)
+void df_coef_refresh(wsi_ctx* c, const Coef<double>& cf) {
+  if (!c->mixed()) return;
+  for (int d = 0; d < 3; ++d) {
+    launch_df_split(cf.rho_face[d], c->df_rho[d], fsize(c->g, d), c->st);
+    launch_df_split(cf.mu_e[d], c->df_mu_e[d], esize(c->g, d), c->st);
+  }
+  launch_df_split(cf.mu_cc, c->df_mu_cc, c->ncell, c->st);
+}
+
+// K x: float64 on the plain path; on the mixed path in double-float
+// arithmetic (same accuracy class, a fraction of the float64 instructions)
+// from the coefficients split by the last df_coef_refresh
 void stokes_mv(wsi_ctx* c, const Coef<double>& cf, double inv_dt, double theta, const double* x, double* y,
                cudaStream_t st) {
-  if (c->mixed())
-    launch_stokes_df(c->g, cf, inv_dt, theta, x, y, st);
-  else
+  if (c->mixed()) {
+    DfCoef dc;
+    for (int d = 0; d < 3; ++d) {
+      dc.rho_face[d] = c->df_rho[d];
+      dc.mu_e[d] = c->df_mu_e[d];
+    }
+    dc.mu_cc = c->df_mu_cc;
+    launch_df_split(x, c->df_x, c->nstk, st);
+    launch_stokes_df(c->g, dc, inv_dt, theta, c->df_x, y, st);
+  } else {
     launch_stokes(c->g, cf, inv_dt, theta, x, y, st);
+  }
 }
 
 // FGMRES(m), right preconditioned by the projection method; float64 Arnoldi
@@ -262,6 +287,7 @@ int fgmres(wsi_ctx* c, const double* b, double* x, double dt, const wsi_solve_op
   const int m = c->m;
   const double inv_dt = 1.0 / dt, theta = c->desc.theta;
   Coef<double> cf = coef_now(c);
+  df_coef_refresh(c, cf);
   double* V = c->V;
   double* Z = c->Z;
   double* hd = c->hdev;
@@ -714,6 +740,14 @@ int wsi_create_grid(const wsi_grid_desc* d, void* stream, wsi_ctx** out) {
     c->phih32 = F(c->ncell);
     c->mu_cc_n32 = F(c->ncell);
     for (int e = 0; e < 3; ++e) c->mu_e_n32[e] = F(esize(g, e));
+    // double-float operands: one float2 per element, the size of a double
+    auto P2 = [&](size_t n) { return (float2*)A(n); };
+    for (int d = 0; d < 3; ++d) {
+      c->df_rho[d] = P2(fsize(g, d));
+      c->df_mu_e[d] = P2(esize(g, d));
+    }
+    c->df_mu_cc = P2(c->ncell);
+    c->df_x = P2(c->nstk);
   }
   c->red = A(8192);
   if (!ok) {
@@ -945,7 +979,8 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
   if (c->has_body) cudaMemcpyAsync(B.Ub_n, B.Ub, (size_t)B.n * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
   int rc = cuda_check(c, "step");
   if (rc) return rc;
-  c->mat_n_valid = true;
+  // the last cycle's viscosity is mu(phi^{n+1}) unless the zones relaxed phi
+  c->mat_n_valid = !c->has_waves;
   if (s) {
     s->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     s->umax = 0.0;
@@ -1048,7 +1083,10 @@ int wsi_apply(wsi_ctx* c, int op, const double* in, double* out, double dt) {
   vel_parts(c, (const double*)xin, qi);
   vel_parts(c, xout, qo);
   switch (op) {
-    case WSI_OP_STOKES: stokes_mv(c, cf, 1.0 / dt, c->desc.theta, xin, xout, c->st); break;
+    case WSI_OP_STOKES:
+      df_coef_refresh(c, cf);
+      stokes_mv(c, cf, 1.0 / dt, c->desc.theta, xin, xout, c->st);
+      break;
     case WSI_OP_VISCOUS: launch_viscous<double>(c->g, cf, 1.0 / dt, c->desc.theta, qi, qo, c->st, false); break;
     case WSI_OP_STRAIN: launch_viscous<double>(c->g, cf, 1.0 / dt, c->desc.theta, qi, qo, c->st, true); break;
     case WSI_OP_PRESSURE: {
@@ -1198,6 +1236,106 @@ int wsi_spread(wsi_ctx* c, const double* F, const double* X, int n, double dV, d
 }
 
 // ------------------------------------------------------------------ learned correction
+// ------------------------------------------------------------ checkpoint
+namespace {
+const char kCkptMagic[8] = {'W', 'S', 'I', 'C', 'K', 'P', 'T', '1'};
+
+struct CkptHeader {
+  char magic[8];
+  int nx, ny, nz, precision, n_markers, psi_static_done;
+  double time;
+  double U_r[3], W_r[3], X_com[3];
+};
+
+bool write_dev(FILE* f, const double* d, size_t n, std::vector<double>& h) {
+  h.resize(n);
+  if (n && cudaMemcpy(h.data(), d, n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+  return fwrite(h.data(), sizeof(double), n, f) == n;
+}
+bool read_dev(FILE* f, double* d, size_t n, std::vector<double>& h) {
+  h.resize(n);
+  if (fread(h.data(), sizeof(double), n, f) != n) return false;
+  return !n || cudaMemcpy(d, h.data(), n * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+}
+}  // namespace
+
+int wsi_checkpoint(wsi_ctx* c, const char* path) {
+  if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
+  if (!c->have_phases || !path) return fail(c, WSI_ERR_INVALID_ARG, "checkpoint needs phases and a path");
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return fail(c, WSI_ERR_CUDA, "checkpoint: stream error");
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(c, WSI_ERR_INVALID_ARG, "checkpoint: cannot open file");
+  CkptHeader hd;
+  memset(&hd, 0, sizeof(hd));
+  memcpy(hd.magic, kCkptMagic, 8);
+  hd.nx = c->g.n[0];
+  hd.ny = c->g.n[1];
+  hd.nz = c->g.n[2];
+  hd.precision = c->desc.precision;
+  hd.n_markers = c->has_body ? c->body.n : 0;
+  hd.psi_static_done = c->psi_static_done ? 1 : 0;
+  hd.time = c->time;
+  for (int a = 0; a < 3; ++a) {
+    hd.U_r[a] = c->body.U_r[a];
+    hd.W_r[a] = c->body.W_r[a];
+    hd.X_com[a] = c->body.X_com[a];
+  }
+  std::vector<double> h;
+  bool ok = fwrite(&hd, sizeof(hd), 1, f) == 1;
+  ok = ok && write_dev(f, c->vel, c->nvel, h) && write_dev(f, c->vel_old, c->nvel, h) &&
+       write_dev(f, c->p, c->ncell, h) && write_dev(f, c->phi, c->ncell, h) && write_dev(f, c->psi, c->ncell, h);
+  if (ok && c->has_body) {
+    const size_t nm = (size_t)c->body.n * 3;
+    ok = write_dev(f, c->body.X, nm, h) && write_dev(f, c->body.Ub_n, nm, h) && write_dev(f, c->body.xc, 3, h);
+  }
+  ok = (fclose(f) == 0) && ok;
+  return ok ? WSI_OK : fail(c, WSI_ERR_CUDA, "checkpoint: write failed");
+}
+
+int wsi_restore(wsi_ctx* c, const char* path) {
+  if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
+  if (!c->have_phases || !path) return fail(c, WSI_ERR_INVALID_ARG, "restore needs phases and a path");
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(c, WSI_ERR_INVALID_ARG, "restore: cannot open file");
+  CkptHeader hd;
+  if (fread(&hd, sizeof(hd), 1, f) != 1 || memcmp(hd.magic, kCkptMagic, 8) != 0) {
+    fclose(f);
+    return fail(c, WSI_ERR_INVALID_ARG, "restore: not a checkpoint");
+  }
+  if (hd.nx != c->g.n[0] || hd.ny != c->g.n[1] || hd.nz != c->g.n[2] || hd.precision != c->desc.precision ||
+      hd.n_markers != (c->has_body ? c->body.n : 0)) {
+    fclose(f);
+    return fail(c, WSI_ERR_INVALID_ARG, "restore: grid, precision or marker count differ");
+  }
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) {
+    fclose(f);
+    return fail(c, WSI_ERR_CUDA, "restore: stream error");
+  }
+  std::vector<double> h;
+  bool ok = read_dev(f, c->vel, c->nvel, h) && read_dev(f, c->vel_old, c->nvel, h) && read_dev(f, c->p, c->ncell, h) &&
+            read_dev(f, c->phi, c->ncell, h) && read_dev(f, c->psi, c->ncell, h);
+  if (ok && c->has_body) {
+    const size_t nm = (size_t)c->body.n * 3;
+    ok = read_dev(f, c->body.X, nm, h) && read_dev(f, c->body.Ub_n, nm, h) && read_dev(f, c->body.xc, 3, h);
+  }
+  fclose(f);
+  if (!ok) return fail(c, WSI_ERR_INVALID_ARG, "restore: truncated file");
+  c->time = hd.time;
+  c->psi_static_done = hd.psi_static_done != 0;
+  for (int a = 0; a < 3; ++a) {
+    c->body.U_r[a] = hd.U_r[a];
+    c->body.W_r[a] = hd.W_r[a];
+    c->body.X_com[a] = hd.X_com[a];
+  }
+  // operator coefficients follow from the restored level sets
+  PhaseConst pc = phase_const(c);
+  launch_materials(c->g, pc, c->phi, c->psi, c->rho_cc, c->mu_cc, c->rho_face, c->beta, c->rho_flow, c->mu_e, c->st);
+  c->phi_cur = c->phi;
+  c->mat_n_valid = false;
+  c->pc_dirty = true;
+  return cuda_check(c, "restore");
+}
+
 struct wsi_unet {
   UNetImpl* u = nullptr;
   float* x3 = nullptr;  // staging for [V][3] inputs
@@ -1297,6 +1435,63 @@ int wsi_unet_backward(wsi_unet* n, const float* target, double* loss) {
 int wsi_unet_adam(wsi_unet* n, double lr) {
   if (!n || !(lr >= 0.0)) return WSI_ERR_INVALID_ARG;
   unet_adam(n->u, lr, 0);
+  return cudaDeviceSynchronize() == cudaSuccess ? WSI_OK : WSI_ERR_CUDA;
+}
+
+namespace {
+const char kNetMagic[8] = {'W', 'S', 'I', 'U', 'N', 'E', 'T', '1'};
+struct NetHeader {
+  char magic[8];
+  int c0, c1, c2, step;
+  unsigned long long nparam;
+};
+}  // namespace
+
+int wsi_unet_save(wsi_unet* n, const char* path) {
+  if (!n || !path) return WSI_ERR_INVALID_ARG;
+  const size_t np = unet_nparam(n->u);
+  std::vector<float> h(np * 3);
+  if (cudaDeviceSynchronize() != cudaSuccess) return WSI_ERR_CUDA;
+  const float* src[3] = {unet_params(n->u), unet_moment(n->u, 0), unet_moment(n->u, 1)};
+  for (int a = 0; a < 3; ++a)
+    if (cudaMemcpy(h.data() + a * np, src[a], np * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return WSI_ERR_CUDA;
+  NetHeader hd;
+  memset(&hd, 0, sizeof(hd));
+  memcpy(hd.magic, kNetMagic, 8);
+  hd.c0 = unet_width(n->u, 0);
+  hd.c1 = unet_width(n->u, 1);
+  hd.c2 = unet_width(n->u, 2);
+  hd.step = *unet_step_count(n->u);
+  hd.nparam = np;
+  FILE* f = fopen(path, "wb");
+  if (!f) return WSI_ERR_INVALID_ARG;
+  bool ok = fwrite(&hd, sizeof(hd), 1, f) == 1 && fwrite(h.data(), sizeof(float), h.size(), f) == h.size();
+  ok = (fclose(f) == 0) && ok;
+  return ok ? WSI_OK : WSI_ERR_CUDA;
+}
+
+int wsi_unet_load(wsi_unet* n, const char* path) {
+  if (!n || !path) return WSI_ERR_INVALID_ARG;
+  FILE* f = fopen(path, "rb");
+  if (!f) return WSI_ERR_INVALID_ARG;
+  NetHeader hd;
+  const size_t np = unet_nparam(n->u);
+  if (fread(&hd, sizeof(hd), 1, f) != 1 || memcmp(hd.magic, kNetMagic, 8) != 0 || hd.nparam != np ||
+      hd.c0 != unet_width(n->u, 0) || hd.c1 != unet_width(n->u, 1) || hd.c2 != unet_width(n->u, 2)) {
+    fclose(f);
+    return WSI_ERR_INVALID_ARG;
+  }
+  std::vector<float> h(np * 3);
+  const bool ok = fread(h.data(), sizeof(float), h.size(), f) == h.size();
+  fclose(f);
+  if (!ok) return WSI_ERR_INVALID_ARG;
+  float* dst[3] = {unet_params(n->u), unet_moment(n->u, 0), unet_moment(n->u, 1)};
+  for (int a = 0; a < 3; ++a)
+    if (cudaMemcpy(dst[a], h.data() + a * np, np * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+      return WSI_ERR_CUDA;
+  *unet_step_count(n->u) = hd.step;
+  unet_pack(n->u, 0);
   return cudaDeviceSynchronize() == cudaSuccess ? WSI_OK : WSI_ERR_CUDA;
 }
 

@@ -8,13 +8,18 @@
 // product via fused multiply-add and Knuth's error-free sum of the leading
 // parts (the trailing parts are added plainly, an error of ~2^-46 of the
 // operands' magnitude, the class of a float64 operation on rounded inputs).
-// Inputs stay float64 in memory and are split into (hi, lo) by integer
-// operations on their bit patterns (47 significant bits kept); the float64
-// pipe sees one addition per row, which forms the float64 result.
+// The operands are split into (hi, lo) float32 pairs by integer operations
+// on their bit patterns (47 significant bits kept) in separate streaming
+// passes: the coefficients once per solve, the input vector once per
+// matvec; the matvec then reads pairs (8 bytes, as many as a float64) and
+// issues no split.  The float64 pipe sees one addition per row, which forms
+// the float64 result.
 // Magnitudes below 2^-126 ~ 1.2e-38 are flushed to zero, and below 2^-103
 // only their leading 24 bits are kept.  Array offsets are 32-bit: every
 // array holds fewer than 2^31 elements (checked when the grid is created).
 #include <math.h>
+
+#include <algorithm>
 
 #include "internal.h"
 
@@ -117,18 +122,26 @@ struct DfConst {
   int es[3][3];    // strides of edge array E
 };
 
-// momentum row C at the interior C-face (i, j, kk)
+__device__ __forceinline__ dfl ldp(const float2* __restrict__ a, int i) {
+  const float2 v = __ldg(a + i);
+  dfl r;
+  r.h = v.x;
+  r.l = v.y;
+  return r;
+}
+
+// momentum row C at the interior C-face (i, j, kk); all operands pre-split
 template <int C>
-__device__ __forceinline__ double row_df(const GridDev& g, const DfConst& k, const Coef<double>& cf,
-                                         const CVel<double>& q, const double* __restrict__ p, int i, int j, int kk) {
+__device__ __forceinline__ double row_df(const GridDev& g, const DfConst& k, const DfCoef& cf, const DfVec& x, int i,
+                                         int j, int kk) {
   const int id3[3] = {i, j, kk};
   const int fb = i + j * k.fs[C][1] + kk * k.fs[C][2];
   const int cb = i + j * k.cs[1] + kk * k.cs[2];  // the cell on the + side of the face
-  const double* __restrict__ qc = q.q[C];
+  const float2* __restrict__ qc = x.q[C];
   const int sC = k.fs[C][C];
-  const dfl q0 = df_split(qc[fb]);
-  const dfl qp = df_split(qc[fb + sC]), qm = df_split(qc[fb - sC]);
-  const dfl muh = df_split(cf.mu_cc[cb]), mul = df_split(cf.mu_cc[cb - k.cs[C]]);
+  const dfl q0 = ldp(qc, fb);
+  const dfl qp = ldp(qc, fb + sC), qm = ldp(qc, fb - sC);
+  const dfl muh = ldp(cf.mu_cc, cb), mul = ldp(cf.mu_cc, cb - k.cs[C]);
   dfl L = df_mul(k.two_ih2[C], df_sub(df_mul(muh, df_sub(qp, q0)), df_mul(mul, df_sub(q0, qm))));
 #pragma unroll
   for (int D = 0; D < 3; ++D) {
@@ -137,64 +150,77 @@ __device__ __forceinline__ double row_df(const GridDev& g, const DfConst& k, con
     const int sD = k.fs[C][D];
     dfl qh, ql;
     if (id3[D] + 1 < g.n[D]) {
-      qh = df_split(qc[fb + sD]);
+      qh = ldp(qc, fb + sD);
     } else {
       qh = k.bcs[2 * D + 1] < 0.0f ? df_neg(q0) : q0;
     }
     if (id3[D] > 0) {
-      ql = df_split(qc[fb - sD]);
+      ql = ldp(qc, fb - sD);
     } else {
       ql = k.bcs[2 * D] < 0.0f ? df_neg(q0) : q0;
     }
     const int eb = i + j * k.es[E][1] + kk * k.es[E][2];
-    const dfl meh = df_split(cf.mu_e[E][eb + k.es[E][D]]), mel = df_split(cf.mu_e[E][eb]);
-    const double* __restrict__ qd = q.q[D];
+    const dfl meh = ldp(cf.mu_e[E], eb + k.es[E][D]), mel = ldp(cf.mu_e[E], eb);
+    const float2* __restrict__ qd = x.q[D];
     const int db = i + j * k.fs[D][1] + kk * k.fs[D][2];
     const int dD = k.fs[D][D], dC = k.fs[D][C];
-    const dfl a1 = df_split(qd[db + dD]), a0 = df_split(qd[db + dD - dC]);
-    const dfl b1 = df_split(qd[db]), b0 = df_split(qd[db - dC]);
+    const dfl a1 = ldp(qd, db + dD), a0 = ldp(qd, db + dD - dC);
+    const dfl b1 = ldp(qd, db), b0 = ldp(qd, db - dC);
     const dfl fh = df_mul(meh, df_add(df_mul(df_sub(qh, q0), k.ih[D]), df_mul(df_sub(a1, a0), k.ih[C])));
     const dfl fl = df_mul(mel, df_add(df_mul(df_sub(q0, ql), k.ih[D]), df_mul(df_sub(b1, b0), k.ih[C])));
     L = df_add(L, df_mul(df_sub(fh, fl), k.ih[D]));
   }
-  const dfl rq = df_mul(df_mul(df_split(cf.rho_face[C][fb]), k.inv_dt), q0);
-  const dfl gp = df_mul(df_sub(df_split(p[cb]), df_split(p[cb - k.cs[C]])), k.ih[C]);
+  const dfl rq = df_mul(df_mul(ldp(cf.rho_face[C], fb), k.inv_dt), q0);
+  const dfl gp = df_mul(df_sub(ldp(x.p, cb), ldp(x.p, cb - k.cs[C])), k.ih[C]);
   return df_to_double(df_add(df_add(rq, gp), df_mul(k.mtheta, L)));
 }
 
 template <int C>
-__device__ __forceinline__ void stokes_row_df(const GridDev& g, const DfConst& k, const Coef<double>& cf,
-                                              const CVel<double>& q, const double* __restrict__ p, double* out,
-                                              int i, int j, int kk) {
+__device__ __forceinline__ void stokes_row_df(const GridDev& g, const DfConst& k, const DfCoef& cf, const DfVec& x,
+                                              double* out, int i, int j, int kk) {
   const int id3[3] = {i, j, kk};
   const int fb = i + j * k.fs[C][1] + kk * k.fs[C][2];
-  out[fb] = (id3[C] == 0 || id3[C] == g.n[C]) ? 0.0 : row_df<C>(g, k, cf, q, p, i, j, kk);
+  out[fb] = (id3[C] == 0 || id3[C] == g.n[C]) ? 0.0 : row_df<C>(g, k, cf, x, i, j, kk);
 }
 
-__global__ void __launch_bounds__(256) k_stokes_df(GridDev g, DfConst k, Coef<double> cf, CVel<double> q,
-                                                   const double* __restrict__ p, double* yu, double* yv, double* yw,
-                                                   double* yp) {
+__global__ void __launch_bounds__(256) k_stokes_df(GridDev g, DfConst k, DfCoef cf, DfVec x, double* yu, double* yv,
+                                                   double* yw, double* yp) {
   const int z = blockIdx.z;
   const int nz = g.n[2];
   const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   if (z < nz) {
-    if (i < g.n[0] + 1 && j < g.n[1]) stokes_row_df<0>(g, k, cf, q, p, yu, i, j, z);
+    if (i < g.n[0] + 1 && j < g.n[1]) stokes_row_df<0>(g, k, cf, x, yu, i, j, z);
   } else if (z < 2 * nz) {
-    if (i < g.n[0] && j < g.n[1] + 1) stokes_row_df<1>(g, k, cf, q, p, yv, i, j, z - nz);
+    if (i < g.n[0] && j < g.n[1] + 1) stokes_row_df<1>(g, k, cf, x, yv, i, j, z - nz);
   } else if (z < 3 * nz + 1) {
-    if (i < g.n[0] && j < g.n[1]) stokes_row_df<2>(g, k, cf, q, p, yw, i, j, z - 2 * nz);
+    if (i < g.n[0] && j < g.n[1]) stokes_row_df<2>(g, k, cf, x, yw, i, j, z - 2 * nz);
   } else {
     const int kk = z - (3 * nz + 1);
     if (i < g.n[0] && j < g.n[1]) {
       const int f0 = i + j * k.fs[0][1] + kk * k.fs[0][2];
       const int f1 = i + j * k.fs[1][1] + kk * k.fs[1][2];
       const int f2 = i + j * k.fs[2][1] + kk * k.fs[2][2];
-      const dfl dx = df_mul(df_sub(df_split(q.q[0][f0 + 1]), df_split(q.q[0][f0])), k.ih[0]);
-      const dfl dy = df_mul(df_sub(df_split(q.q[1][f1 + k.fs[1][1]]), df_split(q.q[1][f1])), k.ih[1]);
-      const dfl dz = df_mul(df_sub(df_split(q.q[2][f2 + k.fs[2][2]]), df_split(q.q[2][f2])), k.ih[2]);
+      const dfl dx = df_mul(df_sub(ldp(x.q[0], f0 + 1), ldp(x.q[0], f0)), k.ih[0]);
+      const dfl dy = df_mul(df_sub(ldp(x.q[1], f1 + k.fs[1][1]), ldp(x.q[1], f1)), k.ih[1]);
+      const dfl dz = df_mul(df_sub(ldp(x.q[2], f2 + k.fs[2][2]), ldp(x.q[2], f2)), k.ih[2]);
       yp[i + j * k.cs[1] + kk * k.cs[2]] = -df_to_double(df_add(df_add(dx, dy), dz));
     }
   }
+}
+
+// x (float64) -> (hi, lo) pairs, n elements; four per thread
+__global__ void k_df_split(const double* __restrict__ x, float2* out, size_t n) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+    const dfl d = df_split(x[t]);
+    out[t] = make_float2(d.h, d.l);
+  }
+}
+
+void launch_df_split(const double* x, float2* out, size_t n, cudaStream_t st) {
+  if (!n) return;
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+  { k_df_split<<<blocks, 256, 0, st>>>(x, out, n); WSI_COUNT(); }
 }
 
 static dfl host_split(double a) {
@@ -204,11 +230,10 @@ static dfl host_split(double a) {
   return r;
 }
 
-void launch_stokes_df(const GridDev& g, const Coef<double>& cf, double inv_dt, double theta, const double* x,
-                      double* y, cudaStream_t st) {
+void launch_stokes_df(const GridDev& g, const DfCoef& cf, double inv_dt, double theta, const float2* x, double* y,
+                      cudaStream_t st) {
   Packing pk = packing(g);
-  CVel<double> q{{x + pk.off[0], x + pk.off[1], x + pk.off[2]}};
-  const double* p = x + pk.off[3];
+  DfVec xv{{x + pk.off[0], x + pk.off[1], x + pk.off[2]}, x + pk.off[3]};
   DfConst k;
   for (int a = 0; a < 3; ++a) {
     k.ih[a] = host_split(g.ih[a]);
@@ -233,7 +258,7 @@ void launch_stokes_df(const GridDev& g, const Coef<double>& cf, double inv_dt, d
   k.cs[2] = n0 * n1;
   dim3 grid(cdiv(g.n[0] + 1, BX), cdiv(g.n[1] + 1, BY), 4 * g.n[2] + 1);
   ktimer_begin(KC_STOKES, st);
-  { k_stokes_df<<<grid, dim3(BX, BY), 0, st>>>(g, k, cf, q, p, y + pk.off[0], y + pk.off[1], y + pk.off[2],
+  { k_stokes_df<<<grid, dim3(BX, BY), 0, st>>>(g, k, cf, xv, y + pk.off[0], y + pk.off[1], y + pk.off[2],
                                                y + pk.off[3]); WSI_COUNT(); }
   ktimer_end(KC_STOKES, st);
 }

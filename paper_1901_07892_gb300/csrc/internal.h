@@ -61,9 +61,22 @@ void launch_div(const GridDev& g, const T* const q[3], T* out, T scale, cudaStre
 // packed Stokes matvec in float64: y = K x
 void launch_stokes(const GridDev& g, const Coef<double>& cf, double inv_dt, double theta, const double* x, double* y,
                    cudaStream_t st);
-// same, strain-rate term in double-float arithmetic (dfstokes.cu)
-void launch_stokes_df(const GridDev& g, const Coef<double>& cf, double inv_dt, double theta, const double* x,
-                      double* y, cudaStream_t st);
+// Operands of the double-float Stokes matvec (dfstokes.cu): (hi, lo) float32
+// pairs of the coefficients and of a packed Stokes vector
+struct DfCoef {
+  const float2* rho_face[3];
+  const float2* mu_cc;
+  const float2* mu_e[3];
+};
+struct DfVec {
+  const float2* q[3];
+  const float2* p;
+};
+// out[i] = (hi, lo) split of x[i]
+void launch_df_split(const double* x, float2* out, size_t n, cudaStream_t st);
+// y = K x in double-float arithmetic from the split coefficients and x
+void launch_stokes_df(const GridDev& g, const DfCoef& cf, double inv_dt, double theta, const float2* x, double* y,
+                      cudaStream_t st);
 // red-black Gauss-Seidel half sweep on the viscous block for component c
 template <typename T>
 void launch_viscous_rbgs(const GridDev& g, const Coef<T>& cf, T inv_dt, T theta, T* const q[3], const T* const b[3],
@@ -133,6 +146,9 @@ __nv_bfloat16* unet_input(UNetImpl* u);  // [V][16]
 float* unet_output(UNetImpl* u);         // [V]
 float* unet_target(UNetImpl* u);         // [V]
 double* unet_loss(UNetImpl* u);          // device scalar
+float* unet_moment(UNetImpl* u, int which);  // Adam first (0) / second (1) moments
+int* unet_step_count(UNetImpl* u);           // Adam steps taken
+int unet_width(const UNetImpl* u, int level);  // c0, c1, c2
 
 // learned correction state inside the float32 multigrid (learned.cu)
 struct LearnState {
@@ -154,6 +170,7 @@ struct MGLevel {
   int r[3];         // coarsening ratio to the next level (1 or 2)
   T* beta[3];
   T* x;
+  T* x2;  // second iterate buffer: a fused red-black sweep reads x, writes x2, then the two swap
   T* b;
   T* res;
 };
