@@ -173,6 +173,18 @@ int wsi_step(wsi_ctx* ctx, double dt, const wsi_solve_opts* opts, wsi_step_stats
 int wsi_get_field(wsi_ctx* ctx, int which, double* dst);
 int wsi_set_field(wsi_ctx* ctx, int which, const double* src);
 
+/* Checkpoint / restart of the time-stepping state (no counterpart in the
+ * paper): u^n, u^{n-1}, p, phi, psi, the markers, their velocity U_b^n, the
+ * body's rigid velocities and centre, the time and the static-psi flag, to a
+ * host file (native byte order).  wsi_restore needs a context created with
+ * the same grid and precision and wsi_set_phases with the same body (the
+ * phase properties and body description are not stored); it recomputes the
+ * operator coefficients from the restored level sets, so that stepping on
+ * continues exactly as without the interruption.  Errors:
+ * WSI_ERR_INVALID_ARG (no phases, unreadable file, other grid), WSI_ERR_CUDA. */
+int wsi_checkpoint(wsi_ctx* ctx, const char* path);
+int wsi_restore(wsi_ctx* ctx, const char* path);
+
 /* Coefficients computed by wsi_set_phases (Sec. 4.1): which:
  * WSI_C_RHO_CC, WSI_C_MU_CC (cell), WSI_C_RHO_FACE, WSI_C_RHO_FLOW_FACE
  * (velocity vectors), WSI_C_MU_EDGE (mu_xy, mu_xz, mu_yz concatenated:
@@ -279,6 +291,13 @@ int wsi_unet_adam(wsi_unet* net, double lr);
  * correction x1 of r is run first and the pair is (r - L x1, e - x1).  The
  * mode is the one last given to wsi_attach_unet (WSI_LEARN_OFF trains the
  * replacing mode).  *loss receives the loss. */
+/* Network weights and Adam state to / from a file (float32, native byte
+ * order, with a header of the widths; a net of other widths is rejected with
+ * WSI_ERR_INVALID_ARG).  The grid size is not stored: weights of one net
+ * load into a net of any size with the same widths. */
+int wsi_unet_save(wsi_unet* net, const char* path);
+int wsi_unet_load(wsi_unet* net, const char* path);
+
 enum { WSI_LEARN_OFF = 0, WSI_LEARN_REPLACE = 1, WSI_LEARN_AUGMENT = 2 };
 int wsi_attach_unet(wsi_ctx* ctx, wsi_unet* net, int level, int enable);
 int wsi_unet_train_sample(wsi_ctx* ctx, const double* e, double lr, double* loss);

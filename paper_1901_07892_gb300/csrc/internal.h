@@ -170,7 +170,6 @@ struct MGLevel {
   int r[3];         // coarsening ratio to the next level (1 or 2)
   T* beta[3];
   T* x;
-  T* x2;  // second iterate buffer: a fused red-black sweep reads x, writes x2, then the two swap
   T* b;
   T* res;
 };

@@ -536,6 +536,9 @@ __nv_bfloat16* unet_input(UNetImpl* u) { return u->x; }
 float* unet_output(UNetImpl* u) { return u->out; }
 float* unet_target(UNetImpl* u) { return u->tgt; }
 double* unet_loss(UNetImpl* u) { return u->loss; }
+float* unet_moment(UNetImpl* u, int which) { return which == 0 ? u->m : u->v; }
+int* unet_step_count(UNetImpl* u) { return &u->step; }
+int unet_width(const UNetImpl* u, int level) { return level == 0 ? u->c0 : (level == 1 ? u->c1 : u->c2); }
 
 void unet_adam(UNetImpl* u, double lr, cudaStream_t st) {
   u->step += 1;

@@ -29,7 +29,7 @@ EXPORTED = ["wsi_stokes_size", "wsi_velocity_size", "wsi_create_grid", "wsi_dest
             "wsi_ktimer_enable", "wsi_ktimer_read", "wsi_unet_create", "wsi_unet_destroy", "wsi_unet_num_params",
             "wsi_unet_set_params", "wsi_unet_get_params", "wsi_unet_get_grads", "wsi_unet_forward",
             "wsi_unet_backward", "wsi_unet_adam", "wsi_attach_unet", "wsi_unet_train_sample",
-            "wsi_pressure_solve"]
+            "wsi_pressure_solve", "wsi_checkpoint", "wsi_restore", "wsi_unet_save", "wsi_unet_load"]
 KC_STOKES, KC_RBGS_P, KC_RBGS_V, KC_TRANSPORT, KC_MDOT, KC_MAXPY, KC_RESTRICT, KC_PROLONG = range(8)
 
 
@@ -303,6 +303,14 @@ class Context:
         self._check(self.L.wsi_advect_levelset(self._h, _ptr(vel), _ptr(phi_n), _ptr(phi_half), dt, _ptr(out)))
         return out
 
+    def checkpoint(self, path):
+        self.L.wsi_checkpoint.argtypes = [ctypes.c_void_p, ctypes.c_char_p]
+        self._check(self.L.wsi_checkpoint(self._h, str(path).encode()))
+
+    def restore(self, path):
+        self.L.wsi_restore.argtypes = [ctypes.c_void_p, ctypes.c_char_p]
+        self._check(self.L.wsi_restore(self._h, str(path).encode()))
+
     def set_waves(self, H, T, depth, x_gen, x_damp, t0=0.0, vertical=2):
         w = WaveDesc(H, T, depth, x_gen, x_damp, t0, vertical)
         self._check(self.L.wsi_set_waves(self._h, ctypes.byref(w)))
@@ -447,6 +455,14 @@ class UNet:
 
     def adam(self, lr):
         self._ck(self.L.wsi_unet_adam(self._h, lr), "adam")
+
+    def save(self, path):
+        self.L.wsi_unet_save.argtypes = [ctypes.c_void_p, ctypes.c_char_p]
+        self._ck(self.L.wsi_unet_save(self._h, str(path).encode()), "save")
+
+    def load(self, path):
+        self.L.wsi_unet_load.argtypes = [ctypes.c_void_p, ctypes.c_char_p]
+        self._ck(self.L.wsi_unet_load(self._h, str(path).encode()), "load")
 
 
 LEARN_OFF, LEARN_REPLACE, LEARN_AUGMENT = 0, 1, 2
