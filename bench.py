@@ -43,10 +43,13 @@ def kernel_model(name, nx, ny, nz, prec_bytes):
     F = (nx + 1) * ny * nz + nx * (ny + 1) * nz + nx * ny * (nz + 1)
     E = (nx + 1) * (ny + 1) * nz + (nx + 1) * ny * (nz + 1) + nx * (ny + 1) * (nz + 1)
     if name == "stokes":
-        # read u,v,w,p, rho_face, mu_cc, mu_edges; write 4 outputs (float64)
+        # read u,v,w,p, rho_face, mu_cc, mu_edges; write 4 outputs: 8 bytes each
+        # (float64, or the (hi, lo) float32 pairs of the double-float matvec)
         byts = 8 * (F + N + F + N + E + F + N)
         flops = 44 * F + 8 * N
-        return byts, flops, "alu"
+        # float64 arithmetic is bound by the float64 pipe; the double-float
+        # matvec of the mixed path is reported against HBM
+        return byts, flops, ("alu" if prec_bytes == 8 else "hbm")
     if name == "rbgs_p":
         # one colour: read x (all), b (half), 3 beta face arrays; write x (half)
         byts = prec_bytes * (N + N // 2 + F + N // 2)
@@ -109,6 +112,72 @@ def build_case(n):
     return c
 
 
+def learned_comparison(args, stream):
+    """Pressure solves D(beta G) x = y to 1e-8 at args.n^3 (the projection
+    sub-problem): learned correction + float32 V-cycles vs plain float32
+    V-cycles vs plain float64 V-cycles, all with float64 residuals.  The
+    network (16/32/64) is trained on the GPU on tanks of half the size (its
+    level-2 grid), with exact pairs from the solver's level operator, then its
+    weights are loaded into a network for the full-size level-2 grid.
+    Evaluation tanks use unseen seeds; y is a seeded random cell field with
+    its mean removed."""
+    import tempfile
+    import torch
+    from paper_1901_07892_gb300 import wsi
+    level = 2
+    n_tr = args.n // 2
+    nc_tr, nc = n_tr >> level, args.n >> level
+    net = wsi.UNet(nc_tr, nc_tr, nc_tr, 16, 32, 64, seed=11)
+    rng = np.random.default_rng(5)
+    tanks = 4
+    per = max(1, args.learned_train // tanks)
+    losses = []
+    t0 = time.perf_counter()
+    for s in range(tanks):
+        c = inputs.tank3d(n=n_tr, seed=100 + s, with_body=False)
+        ctx = wsi.Context.from_case(c, precision=wsi.PREC_MIXED, stream=stream.cuda_stream)
+        ctx.set_case(c, with_body=False)
+        wsi.attach_unet(ctx, net, level, enable=wsi.LEARN_AUGMENT)
+        for k in range(per):
+            lr = 2e-3 if k < 0.7 * per else 5e-4
+            losses.append(wsi.unet_train_sample(ctx, inputs.smooth_field(rng, (nc_tr,) * 3), lr))
+        ctx.close()
+    train_s = time.perf_counter() - t0
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "net.bin")
+        net.save(path)
+        big = wsi.UNet(nc, nc, nc, 16, 32, 64, seed=0)
+        big.load(path)
+    rows = []
+    for s in (10 ** 6, 10 ** 6 + 1):
+        c = inputs.tank3d(n=args.n, seed=s, with_body=False)
+        y = torch.from_numpy(inputs.random_cells(c.phi.shape, s).ravel()).cuda()
+        y -= y.mean()
+        row = {"seed": s}
+        for name, prec, mode in (("learned_fp32", wsi.PREC_MIXED, wsi.LEARN_AUGMENT),
+                                 ("plain_fp32", wsi.PREC_MIXED, wsi.LEARN_OFF),
+                                 ("plain_fp64", wsi.PREC_FP64, None)):
+            ctx = wsi.Context.from_case(c, precision=prec, stream=stream.cuda_stream)
+            ctx.set_case(c, with_body=False)
+            if mode is not None:
+                wsi.attach_unet(ctx, big, level, enable=mode)
+            wsi.pressure_solve(ctx, y.clone(), rtol=args.rtol, max_cycles=200)  # warm-up (set-up, caches)
+            x, st = wsi.pressure_solve(ctx, y.clone(), rtol=args.rtol, max_cycles=200)
+            row[name] = {"ms": st.ms, "cycles": st.iters, "rel_residual": st.rel_residual,
+                         "learned_undone_at": st.learned_rejected}
+            ctx.close()
+        rows.append(row)
+    big.close()
+    net.close()
+    mean = lambda k: float(np.mean([r[k]["ms"] for r in rows]))
+    return {"what": "pressure solve to rtol %.0e at %d^3 (float64 residuals), time to tolerance" % (args.rtol, args.n),
+            "train": {"samples": len(losses), "seconds": train_s, "tank": "%d^3" % n_tr,
+                      "loss_first50": float(np.mean(losses[:50])), "loss_last50": float(np.mean(losses[-50:]))},
+            "solves": rows, "ms_learned_fp32": mean("learned_fp32"), "ms_plain_fp32": mean("plain_fp32"),
+            "ms_plain_fp64": mean("plain_fp64"),
+            "speedup_learned_fp32_over_plain_fp64": mean("plain_fp64") / mean("learned_fp32")}
+
+
 def oracle_sample_step(n_sample=12):
     """One oracle step of the same tank recipe at n_sample^3 (host cores)."""
     from oracle.grid import Grid
@@ -161,6 +230,8 @@ def main():
     ap.add_argument("--roofline-kernel", default="stokes", choices=list(KCLASS))
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned pressure-solve comparison")
+    ap.add_argument("--learned-train", type=int, default=1200, help="training samples for the learned comparison")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -289,6 +360,10 @@ def main():
                    "speedup_mixed_over_fp64": ms64 / ms}
         ctx64.close()
 
+    learned = None
+    if not args.no_learned and rank == 0:
+        learned = learned_comparison(args, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         n_s, t_s = oracle_sample_step(12)
@@ -307,7 +382,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "fgmres_iters": its},
                 "gpu_launches": int(l1 - l0), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "clocks": clocks, "compare": compare}
+                "clocks": clocks, "compare": compare, "learned": learned}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

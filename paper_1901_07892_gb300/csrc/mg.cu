@@ -240,12 +240,16 @@ int precond_setup(Precond<T>& P, const GridDev& g, const Coef<double>& fine, cud
 }
 
 // ------------------------------------------------------------ V-cycle kernels
+static inline dim3 grid_rb(const GridDev& g) { return dim3(cdiv(cdiv(g.n[0], 2), BX), cdiv(g.n[1], BY), g.n[2]); }
+
+// one colour of a red-black Gauss-Seidel sweep: thread t of a row owns the
+// t-th cell of that colour, i = 2t + ((j + k + color) & 1)
 template <typename T>
 __global__ void k_rbgs_p(GridDev g, const T* __restrict__ bx, const T* __restrict__ by, const T* __restrict__ bz,
                          T* x, const T* __restrict__ b, int color) {
-  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  const int j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  const int i = 2 * (blockIdx.x * BX + threadIdx.x) + ((j + k + color) & 1);
   if (i >= g.n[0] || j >= g.n[1]) return;
-  if (((i + j + k) & 1) != color) return;
   size_t id = fidx(g, 3, i, j, k);
   T ihx2 = ginv2<T>(g, 0), ihy2 = ginv2<T>(g, 1), ihz2 = ginv2<T>(g, 2);
   T s = T(0), d = T(0);
@@ -359,7 +363,7 @@ static void coarse_part(Precond<T>& P, const Opts& o, size_t l, cudaStream_t st)
   for (int s = 0; s < o.mg_pre; ++s)
     for (int c = 0; c < 2; ++c) {
       ktimer_begin(KC_RBGS_P, st);
-      { k_rbgs_p<T><<<gr, dim3(BX, BY), 0, st>>>(g, L.beta[0], L.beta[1], L.beta[2], L.x, L.b, c); WSI_COUNT(); }
+      { k_rbgs_p<T><<<grid_rb(g), dim3(BX, BY), 0, st>>>(g, L.beta[0], L.beta[1], L.beta[2], L.x, L.b, c); WSI_COUNT(); }
       ktimer_end(KC_RBGS_P, st);
     }
   MGLevel<T>& Cl = P.lev[l + 1];
@@ -397,7 +401,7 @@ static void vcycle(Precond<T>& P, const Opts& o, size_t l, cudaStream_t st) {
       learned_correction(P, (int)l, L.b, false, st);
       for (int s = 0; s < o.mg_post; ++s)
         for (int c = 1; c >= 0; --c) {
-          k_rbgs_p<T><<<gr, dim3(BX, BY), 0, st>>>(g, L.beta[0], L.beta[1], L.beta[2], L.x, L.b, c);
+          k_rbgs_p<T><<<grid_rb(g), dim3(BX, BY), 0, st>>>(g, L.beta[0], L.beta[1], L.beta[2], L.x, L.b, c);
           WSI_COUNT();
         }
       return;
@@ -419,7 +423,7 @@ static void vcycle(Precond<T>& P, const Opts& o, size_t l, cudaStream_t st) {
     for (int c = 1; c >= 0; --c)
     {
       ktimer_begin(KC_RBGS_P, st);
-      { k_rbgs_p<T><<<gr, dim3(BX, BY), 0, st>>>(g, L.beta[0], L.beta[1], L.beta[2], L.x, L.b, c); WSI_COUNT(); }
+      { k_rbgs_p<T><<<grid_rb(g), dim3(BX, BY), 0, st>>>(g, L.beta[0], L.beta[1], L.beta[2], L.x, L.b, c); WSI_COUNT(); }
       ktimer_end(KC_RBGS_P, st);
     }
 }

@@ -306,10 +306,11 @@ void launch_viscous_residual(const GridDev& g, const Coef<T>& cf, T inv_dt, T th
 template <int C, typename T>
 __global__ void k_viscous_rbgs(GridDev g, Coef<T> cf, T inv_dt, T theta, Vel<T> q, const T* __restrict__ b,
                                int color) {
-  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  // thread t of a row owns the t-th face of the colour: i = 2t + ((j + k + color) & 1)
+  const int j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  const int i = 2 * (blockIdx.x * BX + threadIdx.x) + ((j + k + color) & 1);
   int e0 = ext(g, C, 0), e1 = ext(g, C, 1);
   if (i >= e0 || j >= e1) return;
-  if (((i + j + k) & 1) != color) return;
   int id3[3] = {i, j, k};
   if (id3[C] == 0 || id3[C] == g.n[C]) return;
   size_t id = fidx(g, C, i, j, k);
@@ -327,13 +328,13 @@ void launch_viscous_rbgs(const GridDev& g, const Coef<T>& cf, T inv_dt, T theta,
                          int color, cudaStream_t st) {
   Vel<T> vq{{q[0], q[1], q[2]}};
   ktimer_begin(KC_RBGS_V, st);
-  { k_viscous_rbgs<0, T><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, vq, b[0],
-                                                                                   color); WSI_COUNT(); }
-  { k_viscous_rbgs<1, T><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, vq, b[1],
-                                                                                   color); WSI_COUNT(); }
+  { k_viscous_rbgs<0, T><<<grid3((g.n[0] + 2) / 2, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, vq,
+                                                                                         b[0], color); WSI_COUNT(); }
+  { k_viscous_rbgs<1, T><<<grid3((g.n[0] + 1) / 2, g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta,
+                                                                                           vq, b[1], color); WSI_COUNT(); }
   if (g.n[2] > 1)
-    { k_viscous_rbgs<2, T><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta, vq, b[2],
-                                                                                     color); WSI_COUNT(); }
+    { k_viscous_rbgs<2, T><<<grid3((g.n[0] + 1) / 2, g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, cf, inv_dt, theta,
+                                                                                             vq, b[2], color); WSI_COUNT(); }
   ktimer_end(KC_RBGS_V, st);
 }
 

@@ -207,3 +207,18 @@ def wave_tank(nx=256, ny=128, nz=128, lx=4.0, ly=1.0, lz=1.0, depth=0.5, H=0.05,
     else:
         c.psi = np.full((nz, ny, nx), 1.0)
     return c
+
+
+def smooth_field(rng, shape, modes=6, noise=0.05):
+    """Seeded smooth random cell field (z, y, x) of zero mean: a sum of
+    products of cosines of low wavenumbers (0..3 per axis, Neumann-compatible)
+    plus a little white noise."""
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid((np.arange(nz) + 0.5) / nz, (np.arange(ny) + 0.5) / ny, (np.arange(nx) + 0.5) / nx,
+                          indexing="ij")
+    e = np.zeros(shape)
+    for _ in range(modes):
+        k = rng.integers(0, 4, size=3)
+        e += rng.standard_normal() * np.cos(np.pi * k[0] * x) * np.cos(np.pi * k[1] * y) * np.cos(np.pi * k[2] * z)
+    e += noise * rng.standard_normal(shape)
+    return e - e.mean()

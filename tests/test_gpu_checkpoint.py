@@ -1,7 +1,10 @@
 """Checkpoint / restart of the time-stepping state and U-Net save / load:
-stepping on from a restored state reproduces the uninterrupted run (bit for
-bit without a body; with a body to the rounding of the float64 atomics in the
-spreading), and a reloaded network continues Adam with the same moments and step count."""
+stepping on from a restored state reproduces the uninterrupted run bit for
+bit without a body.  With a body the spreading sums with float64 atomics,
+whose order varies from run to run; the solves (rtol 1e-10) carry those
+last-bit differences into the fields at the level of the solver tolerance
+times the conditioning, so there the bound is 1e-7 of the field's scale.
+A reloaded network continues Adam with the same moments and step count."""
 import numpy as np
 import pytest
 
@@ -49,7 +52,7 @@ def test_restart_continues_the_run(tmp_path, prec, body):
         x, y = a.get_field(f), d.get_field(f)
         if body:
             scale = max(np.abs(x).max(), 1e-300)
-            assert np.abs(x - y).max() <= 1e-10 * scale, f
+            assert np.abs(x - y).max() <= 1e-7 * scale, f
         else:
             assert np.array_equal(x, y), f
     a.close()
