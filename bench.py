@@ -32,6 +32,10 @@ from paper_1901_07892_gb300 import inputs  # noqa: E402
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # float64 FMA rate: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (max SM clock)
 FP64_PEAK_DERIVED_GFLOPS = 152 * 2 * 2 * 2.07
+# DRAM bytes per cell of one launch, measured with ncu at 128^3 (dram__bytes_read.sum +
+# dram__bytes_write.sum, profiles/k_stokes_df_tank128.md) for the current kernel revision;
+# scaled by the cells of the workload
+TRAFFIC_PER_CELL = {("stokes", "mixed"): 233.98e6 / 128 ** 3}
 KCLASS = {"stokes": 0, "rbgs_p": 1, "rbgs_v": 2, "transport": 3, "mdot": 4, "maxpy": 5, "restrict": 6,
           "prolong": 7}
 
@@ -313,8 +317,10 @@ def main():
                     "peak_note": "float64 FMA peak derived: 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz"}
         else:
             hb = peaks.get("hbm_gbs", 6800.0)
+            tpc = TRAFFIC_PER_CELL.get((kname, args.precision))
             roof = {"bound": "hbm", "achieved": byts / dur / 1e9, "peak": hb, "unit": "GB/s",
-                    "frac": byts / dur / 1e9 / hb, "traffic": None, "kernel": kname, "launches": kt_n,
+                    "frac": byts / dur / 1e9 / hb, "traffic": tpc * cells if tpc else None, "kernel": kname,
+                    "launches": kt_n,
                     "avg_us": dur * 1e6, "algorithmic_bytes_per_launch": byts,
                     "peak_note": "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"}
 

@@ -183,28 +183,25 @@ __device__ __forceinline__ void stokes_row_df(const GridDev& g, const DfConst& k
   out[fb] = (id3[C] == 0 || id3[C] == g.n[C]) ? 0.0 : row_df<C>(g, k, cf, x, i, j, kk);
 }
 
+// One thread per (i, j, k) evaluates the u-, v-, w- and p-rows there, so the
+// blocks resident at a time work on the same few z-planes of every array and
+// each array comes from DRAM about once.
 __global__ void __launch_bounds__(256) k_stokes_df(GridDev g, DfConst k, DfCoef cf, DfVec x, double* yu, double* yv,
                                                    double* yw, double* yp) {
-  const int z = blockIdx.z;
-  const int nz = g.n[2];
+  const int kk = blockIdx.z;
   const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-  if (z < nz) {
-    if (i < g.n[0] + 1 && j < g.n[1]) stokes_row_df<0>(g, k, cf, x, yu, i, j, z);
-  } else if (z < 2 * nz) {
-    if (i < g.n[0] && j < g.n[1] + 1) stokes_row_df<1>(g, k, cf, x, yv, i, j, z - nz);
-  } else if (z < 3 * nz + 1) {
-    if (i < g.n[0] && j < g.n[1]) stokes_row_df<2>(g, k, cf, x, yw, i, j, z - 2 * nz);
-  } else {
-    const int kk = z - (3 * nz + 1);
-    if (i < g.n[0] && j < g.n[1]) {
-      const int f0 = i + j * k.fs[0][1] + kk * k.fs[0][2];
-      const int f1 = i + j * k.fs[1][1] + kk * k.fs[1][2];
-      const int f2 = i + j * k.fs[2][1] + kk * k.fs[2][2];
-      const dfl dx = df_mul(df_sub(ldp(x.q[0], f0 + 1), ldp(x.q[0], f0)), k.ih[0]);
-      const dfl dy = df_mul(df_sub(ldp(x.q[1], f1 + k.fs[1][1]), ldp(x.q[1], f1)), k.ih[1]);
-      const dfl dz = df_mul(df_sub(ldp(x.q[2], f2 + k.fs[2][2]), ldp(x.q[2], f2)), k.ih[2]);
-      yp[i + j * k.cs[1] + kk * k.cs[2]] = -df_to_double(df_add(df_add(dx, dy), dz));
-    }
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+  if (i <= n0 && j < n1 && kk < n2) stokes_row_df<0>(g, k, cf, x, yu, i, j, kk);
+  if (i < n0 && j <= n1 && kk < n2) stokes_row_df<1>(g, k, cf, x, yv, i, j, kk);
+  if (i < n0 && j < n1 && kk <= n2) stokes_row_df<2>(g, k, cf, x, yw, i, j, kk);
+  if (i < n0 && j < n1 && kk < n2) {
+    const int f0 = i + j * k.fs[0][1] + kk * k.fs[0][2];
+    const int f1 = i + j * k.fs[1][1] + kk * k.fs[1][2];
+    const int f2 = i + j * k.fs[2][1] + kk * k.fs[2][2];
+    const dfl dx = df_mul(df_sub(ldp(x.q[0], f0 + 1), ldp(x.q[0], f0)), k.ih[0]);
+    const dfl dy = df_mul(df_sub(ldp(x.q[1], f1 + k.fs[1][1]), ldp(x.q[1], f1)), k.ih[1]);
+    const dfl dz = df_mul(df_sub(ldp(x.q[2], f2 + k.fs[2][2]), ldp(x.q[2], f2)), k.ih[2]);
+    yp[i + j * k.cs[1] + kk * k.cs[2]] = -df_to_double(df_add(df_add(dx, dy), dz));
   }
 }
 
@@ -256,7 +253,7 @@ void launch_stokes_df(const GridDev& g, const DfCoef& cf, double inv_dt, double 
   k.cs[0] = 1;
   k.cs[1] = n0;
   k.cs[2] = n0 * n1;
-  dim3 grid(cdiv(g.n[0] + 1, BX), cdiv(g.n[1] + 1, BY), 4 * g.n[2] + 1);
+  dim3 grid(cdiv(g.n[0] + 1, BX), cdiv(g.n[1] + 1, BY), g.n[2] + 1);
   ktimer_begin(KC_STOKES, st);
   { k_stokes_df<<<grid, dim3(BX, BY), 0, st>>>(g, k, cf, xv, y + pk.off[0], y + pk.off[1], y + pk.off[2],
                                                y + pk.off[3]); WSI_COUNT(); }
