@@ -312,6 +312,19 @@ int wsi_unet_train_sample(wsi_ctx* ctx, const double* e, double lr, double* loss
 int wsi_pressure_solve(wsi_ctx* ctx, const double* y, double* x, double rtol, int max_cycles,
                        wsi_solve_stats* stats);
 
+/* Float64 2-norm sqrt(sum x_i^2) of n doubles at device pointer x, written
+ * to *out (host or device pointer) before the call returns; deterministic
+ * (fixed reduction tree).  The paper has no counterpart: this is the
+ * allocation-free variant of the reductions the solver runs on its own
+ * scratch, for callers that must not allocate device memory after set-up.
+ * Its scratch is static device memory (64 KiB of partial sums), so it
+ * allocates nothing; the first call on a device does the set-up (looks up
+ * that memory) and should come before any stream capture.  n > 2^27
+ * (134,217,728) is rejected with WSI_ERR_INVALID_ARG.  Calls that can
+ * overlap (other streams, host threads) share the scratch and race.
+ * stream: a cudaStream_t (NULL = legacy default stream). */
+int wsi_norm2_noalloc(const double* x, size_t n, double* out, void* stream);
+
 /* Instrumentation (no counterpart in the paper; used to report kernel
  * rooflines).  wsi_launch_count: kernels launched by this library in this
  * process so far.  wsi_ktimer_enable(k): bracket every later launch of

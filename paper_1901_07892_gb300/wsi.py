@@ -29,7 +29,8 @@ EXPORTED = ["wsi_stokes_size", "wsi_velocity_size", "wsi_create_grid", "wsi_dest
             "wsi_ktimer_enable", "wsi_ktimer_read", "wsi_unet_create", "wsi_unet_destroy", "wsi_unet_num_params",
             "wsi_unet_set_params", "wsi_unet_get_params", "wsi_unet_get_grads", "wsi_unet_forward",
             "wsi_unet_backward", "wsi_unet_adam", "wsi_attach_unet", "wsi_unet_train_sample",
-            "wsi_pressure_solve", "wsi_checkpoint", "wsi_restore", "wsi_unet_save", "wsi_unet_load"]
+            "wsi_pressure_solve", "wsi_checkpoint", "wsi_restore", "wsi_unet_save", "wsi_unet_load",
+            "wsi_norm2_noalloc"]
 KC_STOKES, KC_RBGS_P, KC_RBGS_V, KC_TRANSPORT, KC_MDOT, KC_MAXPY, KC_RESTRICT, KC_PROLONG = range(8)
 
 
@@ -336,6 +337,20 @@ class Context:
         out = _empty_like_kind(F, self.nvel)
         self._check(self.L.wsi_spread(self._h, _ptr(F), _ptr(X), n, dV, _ptr(out)))
         return out
+
+
+def norm2_noalloc(x, stream=None):
+    """Float64 2-norm of a device vector through the allocation-free entry point."""
+    L = lib()
+    L.wsi_norm2_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.c_void_p]
+    L.wsi_norm2_noalloc.restype = ctypes.c_int
+    out = ctypes.c_double()
+    n = int(x.numel()) if _is_torch(x) else int(np.asarray(x).size)
+    rc = L.wsi_norm2_noalloc(_ptr(x), n, ctypes.byref(out), stream)
+    if rc != OK:
+        raise WsiError(rc, "wsi_norm2_noalloc failed")
+    return out.value
 
 
 def launch_count():
