@@ -198,7 +198,7 @@ PhaseConst phase_const(wsi_ctx* c) {
 
 __global__ void k_recip(size_t n, const double* __restrict__ a, double* b) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) b[t] = 1.0 / a[t];
+  if (t < n) b[t] = rcp_nr(a[t]);
 }
 
 void recip(wsi_ctx* c, const double* a, double* b, size_t n) {

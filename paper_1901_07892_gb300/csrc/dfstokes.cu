@@ -20,6 +20,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "internal.h"
 
@@ -116,11 +117,22 @@ struct DfConst {
   dfl two_ih2[3];  // 2/h^2
   dfl inv_dt;
   dfl mtheta;      // -theta
+  unsigned pw;     // bit set: that constant is a power of two (bits 0-2 ih, 3-5 two_ih2, 6 mtheta, 7 inv_dt)
   float bcs[6];    // tangential ghost sign per wall
   int fs[3][3];    // strides of face array C along each axis
   int cs[3];       // strides of the cell arrays
   int es[3][3];    // strides of edge array E
 };
+
+// x * c for a constant c; exact scaling of both parts when c is a power of two
+__device__ __forceinline__ dfl df_mulc(dfl x, dfl c, bool pow2) {
+  if (pow2) {
+    x.h *= c.h;
+    x.l *= c.h;
+    return x;
+  }
+  return df_mul(x, c);
+}
 
 __device__ __forceinline__ dfl ldp(const float2* __restrict__ a, int i) {
   const float2 v = __ldg(a + i);
@@ -142,7 +154,7 @@ __device__ __forceinline__ double row_df(const GridDev& g, const DfConst& k, con
   const dfl q0 = ldp(qc, fb);
   const dfl qp = ldp(qc, fb + sC), qm = ldp(qc, fb - sC);
   const dfl muh = ldp(cf.mu_cc, cb), mul = ldp(cf.mu_cc, cb - k.cs[C]);
-  dfl L = df_mul(k.two_ih2[C], df_sub(df_mul(muh, df_sub(qp, q0)), df_mul(mul, df_sub(q0, qm))));
+  dfl L = df_mulc(df_sub(df_mul(muh, df_sub(qp, q0)), df_mul(mul, df_sub(q0, qm))), k.two_ih2[C], (k.pw >> (3 + C)) & 1);
 #pragma unroll
   for (int D = 0; D < 3; ++D) {
     if (D == C) continue;
@@ -166,13 +178,14 @@ __device__ __forceinline__ double row_df(const GridDev& g, const DfConst& k, con
     const int dD = k.fs[D][D], dC = k.fs[D][C];
     const dfl a1 = ldp(qd, db + dD), a0 = ldp(qd, db + dD - dC);
     const dfl b1 = ldp(qd, db), b0 = ldp(qd, db - dC);
-    const dfl fh = df_mul(meh, df_add(df_mul(df_sub(qh, q0), k.ih[D]), df_mul(df_sub(a1, a0), k.ih[C])));
-    const dfl fl = df_mul(mel, df_add(df_mul(df_sub(q0, ql), k.ih[D]), df_mul(df_sub(b1, b0), k.ih[C])));
-    L = df_add(L, df_mul(df_sub(fh, fl), k.ih[D]));
+    const bool pD = (k.pw >> D) & 1, pC = (k.pw >> C) & 1;
+    const dfl fh = df_mul(meh, df_add(df_mulc(df_sub(qh, q0), k.ih[D], pD), df_mulc(df_sub(a1, a0), k.ih[C], pC)));
+    const dfl fl = df_mul(mel, df_add(df_mulc(df_sub(q0, ql), k.ih[D], pD), df_mulc(df_sub(b1, b0), k.ih[C], pC)));
+    L = df_add(L, df_mulc(df_sub(fh, fl), k.ih[D], pD));
   }
-  const dfl rq = df_mul(df_mul(ldp(cf.rho_face[C], fb), k.inv_dt), q0);
-  const dfl gp = df_mul(df_sub(ldp(x.p, cb), ldp(x.p, cb - k.cs[C])), k.ih[C]);
-  return df_to_double(df_add(df_add(rq, gp), df_mul(k.mtheta, L)));
+  const dfl rq = df_mul(df_mulc(ldp(cf.rho_face[C], fb), k.inv_dt, (k.pw >> 7) & 1), q0);
+  const dfl gp = df_mulc(df_sub(ldp(x.p, cb), ldp(x.p, cb - k.cs[C])), k.ih[C], (k.pw >> C) & 1);
+  return df_to_double(df_add(df_add(rq, gp), df_mulc(L, k.mtheta, (k.pw >> 6) & 1)));
 }
 
 template <int C>
@@ -198,9 +211,9 @@ __global__ void __launch_bounds__(256) k_stokes_df(GridDev g, DfConst k, DfCoef 
     const int f0 = i + j * k.fs[0][1] + kk * k.fs[0][2];
     const int f1 = i + j * k.fs[1][1] + kk * k.fs[1][2];
     const int f2 = i + j * k.fs[2][1] + kk * k.fs[2][2];
-    const dfl dx = df_mul(df_sub(ldp(x.q[0], f0 + 1), ldp(x.q[0], f0)), k.ih[0]);
-    const dfl dy = df_mul(df_sub(ldp(x.q[1], f1 + k.fs[1][1]), ldp(x.q[1], f1)), k.ih[1]);
-    const dfl dz = df_mul(df_sub(ldp(x.q[2], f2 + k.fs[2][2]), ldp(x.q[2], f2)), k.ih[2]);
+    const dfl dx = df_mulc(df_sub(ldp(x.q[0], f0 + 1), ldp(x.q[0], f0)), k.ih[0], k.pw & 1);
+    const dfl dy = df_mulc(df_sub(ldp(x.q[1], f1 + k.fs[1][1]), ldp(x.q[1], f1)), k.ih[1], (k.pw >> 1) & 1);
+    const dfl dz = df_mulc(df_sub(ldp(x.q[2], f2 + k.fs[2][2]), ldp(x.q[2], f2)), k.ih[2], (k.pw >> 2) & 1);
     yp[i + j * k.cs[1] + kk * k.cs[2]] = -df_to_double(df_add(df_add(dx, dy), dz));
   }
 }
@@ -227,6 +240,11 @@ static dfl host_split(double a) {
   return r;
 }
 
+static bool host_pow2(const dfl& c) {
+  int e = 0;
+  return c.l == 0.0f && c.h != 0.0f && std::fabs(std::frexp((double)c.h, &e)) == 0.5;
+}
+
 void launch_stokes_df(const GridDev& g, const DfCoef& cf, double inv_dt, double theta, const float2* x, double* y,
                       cudaStream_t st) {
   Packing pk = packing(g);
@@ -238,6 +256,13 @@ void launch_stokes_df(const GridDev& g, const DfCoef& cf, double inv_dt, double 
   }
   k.inv_dt = host_split(inv_dt);
   k.mtheta = host_split(-theta);
+  k.pw = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (host_pow2(k.ih[a])) k.pw |= 1u << a;
+    if (host_pow2(k.two_ih2[a])) k.pw |= 1u << (3 + a);
+  }
+  if (host_pow2(k.mtheta)) k.pw |= 1u << 6;
+  if (host_pow2(k.inv_dt)) k.pw |= 1u << 7;
   for (int w = 0; w < 6; ++w) k.bcs[w] = (float)g.bc[w];
   const int n0 = g.n[0], n1 = g.n[1];
   for (int c = 0; c < 3; ++c) {

@@ -128,7 +128,7 @@ void launch_scale(double* x, size_t n, const double* s_dev, bool inverse, cudaSt
 template <typename Ts, typename Td>
 __global__ void k_cast(const Ts* __restrict__ a, Td* b, size_t n) {
   size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) b[i] = (Td)a[i];
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) b[i] = cvt<Td, Ts>(a[i]);
 }
 
 template <typename Ts, typename Td>
@@ -140,7 +140,7 @@ template <typename T>
 __global__ void k_sum(const T* __restrict__ x, size_t n, double* part) {
   double acc = 0.0;
   size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) acc += (double)x[i];
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) acc += cvt<double, T>(x[i]);
   __shared__ double sh[RT / 32];
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);

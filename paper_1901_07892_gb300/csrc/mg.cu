@@ -490,7 +490,7 @@ __global__ void k_vel_update(GridDev g, const T* __restrict__ ut, const T* __res
   int lo[3] = {i, j, k};
   lo[C] -= 1;
   T gphi = (phi[fidx(g, 3, i, j, k)] - phi[fidx(g, 3, lo[0], lo[1], lo[2])]) * ginv<T>(g, C);
-  z[id] = (double)(ut[id] - beta[id] * gphi);
+  z[id] = cvt<double, T>(ut[id] - beta[id] * gphi);
 }
 
 // p = phi/dt - theta mu y - mean (mean subtracted with the sum in s_dev)
@@ -499,7 +499,13 @@ __global__ void k_p_update(size_t n, const T* __restrict__ phi, const T* __restr
                            double inv_dt, double theta, double* z) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (; t < n; t += stride) z[t] = (double)phi[t] * inv_dt - theta * (double)mu[t] * (double)y[t];
+  if constexpr (std::is_same<T, float>::value) {
+    // float32 preconditioner: float32 arithmetic, exact widening by integer operations
+    const float fi = (float)inv_dt, ft = (float)theta;
+    for (; t < n; t += stride) z[t] = f2d_fast(phi[t] * fi - ft * mu[t] * y[t]);
+  } else {
+    for (; t < n; t += stride) z[t] = (double)phi[t] * inv_dt - theta * (double)mu[t] * (double)y[t];
+  }
 }
 
 template <typename T>

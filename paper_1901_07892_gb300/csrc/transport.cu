@@ -304,10 +304,13 @@ __global__ void k_lincomb(size_t n, double a, const Ti* __restrict__ x, double b
                           const Ti* __restrict__ z, To* out) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t stride = (size_t)gridDim.x * blockDim.x;
+  // coefficients of +-1 and 0 skip their multiplication (float64 operations
+  // are scarce); the common forms are x - y and x + c z
+  const bool a1 = a == 1.0, b1 = b == 1.0, bm1 = b == -1.0, c1 = c == 1.0, cm1 = c == -1.0;
   for (; t < n; t += stride) {
-    double s = a * (double)x[t];
-    if (y) s += b * (double)y[t];
-    if (z) s += c * (double)z[t];
+    double s = a1 ? (double)x[t] : a * (double)x[t];
+    if (y) s = b1 ? s + (double)y[t] : (bm1 ? s - (double)y[t] : fma(b, (double)y[t], s));
+    if (z) s = c1 ? s + (double)z[t] : (cm1 ? s - (double)z[t] : fma(c, (double)z[t], s));
     out[t] = (To)s;
   }
 }
@@ -361,7 +364,7 @@ __global__ void k_lincomb_mix(size_t n, double a, const double* __restrict__ x, 
                               double c, const float* __restrict__ z, double* out) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (; t < n; t += stride) out[t] = a * x[t] + b * (double)y[t] + c * (double)z[t];
+  for (; t < n; t += stride) out[t] = a * x[t] + b * f2d_fast(y[t]) + c * f2d_fast(z[t]);
 }
 void launch_lincomb_mix(size_t n, double a, const double* x, double b, const float* y, double c, const float* z,
                         double* out, cudaStream_t st) {
