@@ -286,11 +286,13 @@ int wsi_unet_adam(wsi_unet* net, double lr);
  * Requires a WSI_PREC_MIXED context and wsi_set_phases.
  * wsi_unet_train_sample: one Adam step (learning rate lr; lr = 0 only
  * evaluates) on the exact pair built from a smooth field e given on the
- * level's cells (float64, x fastest): r = L e and target o* = e d / s for
- * the replacing mode; for the augmenting mode the plain coarse-grid
+ * level's cells (float64, x fastest): right-hand side r = L e with solution
+ * e for the replacing mode; for the augmenting mode the plain coarse-grid
  * correction x1 of r is run first and the pair is (r - L x1, e - x1).  The
  * mode is the one last given to wsi_attach_unet (WSI_LEARN_OFF trains the
- * replacing mode).  *loss receives the loss. */
+ * replacing mode).  The loss is what the plain cycle judges a correction by:
+ * 1/2 mean((L t)^2)/s^2 + 0.05 mean((d t)^2)/s^2 with t the error of the
+ * corrected iterate; *loss receives it. */
 /* Network weights and Adam state to / from a file (float32, native byte
  * order, with a header of the widths; a net of other widths is rejected with
  * WSI_ERR_INVALID_ARG).  The grid size is not stored: weights of one net

@@ -1522,7 +1522,7 @@ int wsi_unet_train_sample(wsi_ctx* c, const double* e, double lr, double* loss) 
   float* e32 = P.learn.e;
   launch_lincomb_to_f32(n, 1.0, stage, 0.0, nullptr, 0.0, nullptr, e32, c->st);
   learned_train(P, c->opts, e32, lr, c->st);
-  if (loss) cudaMemcpyAsync(loss, unet_loss(c->unet->u), sizeof(double), cudaMemcpyDeviceToHost, c->st);
+  if (loss) cudaMemcpyAsync(loss, learned_loss(P), sizeof(double), cudaMemcpyDeviceToHost, c->st);
   return cuda_check(c, "unet_train_sample");
 }
 

@@ -160,7 +160,10 @@ struct LearnState {
   std::vector<float*> lrho, phi;  // per level (index = level), restricted inputs
   float* diag = nullptr;
   float* e = nullptr;  // training field on the level
-  double* ss = nullptr;
+  float* t1 = nullptr;  // training scratch on the level: error, L error, L L error
+  float* t2 = nullptr;
+  float* t3 = nullptr;
+  double* ss = nullptr;  // [0] sum of squares of the network input, [1] training loss
 };
 
 // ---------------------------------------------------------------- mg.cu
@@ -230,8 +233,10 @@ int learned_setup(Precond<float>& P, const double* rho_cc, const double* phi, cu
 void learned_correction(Precond<float>& P, int level, const float* rhs, bool add, cudaStream_t st);
 // one training step on the exact pair of a smooth field e (device float on
 // the level); for the augmenting mode the pair is taken after the plain
-// coarse-grid correction of r = L e
+// coarse-grid correction of r = L e.  The loss (device scalar: learned_loss)
+// is the residual norm of the correction plus a small error term.
 void learned_train(Precond<float>& P, const Opts& o, const float* e, double lr, cudaStream_t st);
+const double* learned_loss(const Precond<float>& P);
 int learned_alloc(Precond<float>& P, UNetImpl* net, int level, std::string& err);
 // one V-cycle on level 0 of the hierarchy (x, b of level 0)
 template <typename T>

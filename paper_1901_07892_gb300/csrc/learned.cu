@@ -4,11 +4,13 @@
 //
 // Network input at multigrid level l (3 channels, bf16): log(rho)/7 and the
 // level set, both averaged down the hierarchy from the fine cells, and the
-// level's right-hand side r divided by its RMS s.  Output o (float32).  The
-// correction is e = s o / d with d the diagonal of the level's operator
-// (sum of beta/h^2 over the cell's faces), so that o = r/s reproduces one
-// Jacobi step and the network learns the rest.  Training pairs are exact by
-// construction: a seeded smooth field e, r = L_l e, target o* = e d / s.
+// level's right-hand side (or residual) r divided by its RMS s.  Output o
+// (float32).  The correction is e = s o / d with d the diagonal of the
+// level's operator (sum of beta/h^2 over the cell's faces), so that o = r/s
+// reproduces one Jacobi step and the network learns the rest.  Training
+// pairs are exact by construction: a seeded smooth field e and r = L_l e;
+// the loss is the residual the correction leaves, the quantity the plain
+// cycle judges it by.
 #include <math.h>
 
 #include "internal.h"
@@ -71,12 +73,47 @@ __global__ void k_assemble(const float* __restrict__ lrho, const float* __restri
   }
 }
 
-// training target o* = (e - x) d / s  (x null: 0)
-__global__ void k_target(const float* __restrict__ e, const float* __restrict__ x, const float* __restrict__ d,
-                         const double* __restrict__ ss, size_t n, float* tgt) {
-  float inv = (float)(1.0 / sqrt(fmax(ss[0] / (double)n, 1e-300)));
+// error of the network's correction: t1 = s o / d - (e - x)   (x null: 0)
+__global__ void k_corr_error(const float* __restrict__ o, const float* __restrict__ e, const float* __restrict__ x,
+                             const float* __restrict__ d, const double* __restrict__ ss, size_t n, float* t1) {
+  const float s = (float)sqrt(fmax(ss[0] / (double)n, 1e-300));
   for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x)
-    tgt[v] = (x ? e[v] - x[v] : e[v]) * d[v] * inv;
+    t1[v] = o[v] * s / d[v] - (x ? e[v] - x[v] : e[v]);
+}
+
+// Gradient of the loss
+//   J = 1/2 mean((L t1)^2) / s^2 + lambda/2 mean((d t1)^2) / s^2
+// (residual left by the correction, in units of the input's RMS s, plus a
+// small error term) with respect to the network output o (t1 = s o/d - e):
+//   dJ/do = (L L t1 / (s d) + lambda d t1 / s) / n,
+// handed to the network's backward pass as the target tgt = o - n dJ/do
+// (its output gradient is (o - tgt) / n).  t3 = L L t1 (L symmetric).
+__global__ void k_resid_target(const float* __restrict__ o, const float* __restrict__ t1, const float* __restrict__ t3,
+                               const float* __restrict__ d, const double* __restrict__ ss, size_t n, float lambda,
+                               float* tgt) {
+  const float s = (float)sqrt(fmax(ss[0] / (double)n, 1e-300));
+  const float is = 1.0f / s;
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x)
+    tgt[v] = o[v] - (t3[v] * is / d[v] + lambda * d[v] * t1[v] * is);
+}
+
+// loss = 1/2 mean(t2^2)/s^2 + lambda/2 mean((d t1)^2)/s^2, one block
+__global__ void k_resid_loss(const float* __restrict__ t1, const float* __restrict__ t2, const float* __restrict__ d,
+                             size_t n, float lambda, double* ss) {
+  __shared__ double sh[32];
+  double a = 0.0;
+  for (size_t v = threadIdx.x; v < n; v += blockDim.x) {
+    const double r = t2[v], q = (double)d[v] * t1[v];
+    a += r * r + lambda * q * q;
+  }
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    ss[1] = 0.5 * t / (double)n / fmax(ss[0] / (double)n, 1e-300);
+  }
 }
 
 // x = s o / d, or x += s o / d
@@ -137,15 +174,18 @@ void learned_correction(Precond<float>& P, int l, const float* rhs, bool add, cu
 }
 
 // one training step on a seeded field e at the level.  Replacing mode: the
-// network sees r = L e and learns e.  Augmenting mode: the plain coarse-grid
-// correction of r (pre-smoothing, coarser cycle, prolongation) gives x1; the
-// network sees the residual r - L x1 and learns the error e - x1 it leaves,
-// exact because e is known.  Then forward, backward and Adam.
+// network sees r = L e and corrects toward e.  Augmenting mode: the plain
+// coarse-grid correction of r (pre-smoothing, coarser cycle, prolongation)
+// gives x1; the network sees the residual r - L x1 and corrects toward the
+// error e - x1 it leaves, exact because e is known.  The loss is the
+// residual the correction leaves (what the plain cycle judges it by) plus a
+// small error term; then backward and Adam.
 void learned_train(Precond<float>& P, const Opts& o, const float* e, double lr, cudaStream_t st) {
   LearnState& S = P.learn;
-  int l = S.level;
+  const int l = S.level;
   MGLevel<float>& L = P.lev[l];
-  size_t n = fsize(L.g, 3);
+  const size_t n = fsize(L.g, 3);
+  const float lambda = 0.1f;
   const float* bt[3] = {L.beta[0], L.beta[1], L.beta[2]};
   launch_pressure<float>(L.g, bt, e, L.res, st);
   const float* x1 = nullptr;
@@ -157,13 +197,20 @@ void learned_train(Precond<float>& P, const Opts& o, const float* e, double lr, 
     launch_lincomb_f32(n, 1.f, L.b, -1.f, L.res, 0.f, nullptr, L.res, st);
     x1 = L.x;
   }
-  cudaMemsetAsync(S.ss, 0, sizeof(double), st);
+  cudaMemsetAsync(S.ss, 0, 2 * sizeof(double), st);
   { k_sumsq<<<nb(n), 256, 0, st>>>(L.res, n, S.ss); WSI_COUNT(); }
   { k_assemble<<<nb(n), 256, 0, st>>>(S.lrho[l], S.phi[l], L.res, S.ss, n, unet_input(S.net)); WSI_COUNT(); }
-  { k_target<<<nb(n), 256, 0, st>>>(e, x1, S.diag, S.ss, n, unet_target(S.net)); WSI_COUNT(); }
   unet_forward(S.net, st);
+  const float* out = unet_output(S.net);
+  { k_corr_error<<<nb(n), 256, 0, st>>>(out, e, x1, S.diag, S.ss, n, S.t1); WSI_COUNT(); }
+  launch_pressure<float>(L.g, bt, S.t1, S.t2, st);
+  launch_pressure<float>(L.g, bt, S.t2, S.t3, st);
+  { k_resid_loss<<<1, 1024, 0, st>>>(S.t1, S.t2, S.diag, n, lambda, S.ss); WSI_COUNT(); }
+  { k_resid_target<<<nb(n), 256, 0, st>>>(out, S.t1, S.t3, S.diag, S.ss, n, lambda, unet_target(S.net)); WSI_COUNT(); }
   unet_backward(S.net, st);
   if (lr > 0.0) unet_adam(S.net, lr, st);
 }
+
+const double* learned_loss(const Precond<float>& P) { return P.learn.ss + 1; }
 
 }  // namespace wsi

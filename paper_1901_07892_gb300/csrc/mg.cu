@@ -107,6 +107,7 @@ void precond_free(Precond<T>& P) {
   P.learn.phi.clear();
   P.learn.diag = nullptr;
   P.learn.e = nullptr;
+  P.learn.t1 = P.learn.t2 = P.learn.t3 = nullptr;
   P.learn.ss = nullptr;
   P.learn.ready = false;
 }
@@ -456,8 +457,11 @@ int learned_alloc(Precond<float>& P, UNetImpl* net, int level, std::string& err)
     size_t nmax = fsize(P.lev[1].g, 3);
     S.diag = dalloc<float>(P.allocs, nmax, err);
     S.e = dalloc<float>(P.allocs, nmax, err);
+    S.t1 = dalloc<float>(P.allocs, nmax, err);
+    S.t2 = dalloc<float>(P.allocs, nmax, err);
+    S.t3 = dalloc<float>(P.allocs, nmax, err);
     S.ss = dalloc<double>(P.allocs, 4, err);
-    if (!S.diag || !S.e || !S.ss) return WSI_ERR_OOM;
+    if (!S.diag || !S.e || !S.t1 || !S.t2 || !S.t3 || !S.ss) return WSI_ERR_OOM;
   }
   return WSI_OK;
 }
