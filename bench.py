@@ -235,6 +235,8 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned pressure-solve comparison")
+    ap.add_argument("--visc-sweeps", type=int, default=2, help="viscous red-black sweeps per preconditioner apply")
+    ap.add_argument("--mg", default="2,2", help="pressure V-cycle pre,post smoothing sweeps")
     ap.add_argument("--learned-train", type=int, default=1200, help="training samples for the learned comparison")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -264,7 +266,9 @@ def main():
     prec = wsi.PREC_MIXED if args.precision == "mixed" else wsi.PREC_FP64
 
     def make_ctx(p):
-        ctx = wsi.Context.from_case(c, precision=p, restart=20, stream=stream.cuda_stream)
+        pre, post = (int(v) for v in args.mg.split(","))
+        ctx = wsi.Context.from_case(c, precision=p, restart=20, stream=stream.cuda_stream, mg_pre=pre, mg_post=post,
+                                    visc_sweeps=args.visc_sweeps)
         ctx.set_case(c, rho_s=c.rho_l)
         return ctx
 
@@ -386,6 +390,7 @@ def main():
                                        "2 Stokes solves per step to rtol %.0e" % (args.n, args.n, args.rtol),
                            "cells": cells, "precision": args.precision, "l2": "inputs larger than L2 (no flush)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
+                           "mg_pre_post": args.mg, "visc_sweeps": args.visc_sweeps,
                            "fgmres_iters": its},
                 "gpu_launches": int(l1 - l0), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks, "compare": compare, "learned": learned}

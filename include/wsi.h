@@ -67,8 +67,11 @@ typedef struct {
     int precision;       /* WSI_PREC_FP64 or WSI_PREC_MIXED                  */
     int mg_pre, mg_post; /* red-black Gauss-Seidel sweeps per level           */
     int mg_cycles;       /* pressure V-cycles per preconditioner application  */
-    int visc_sweeps;     /* viscous red-black sweeps per application          */
+    int visc_sweeps;     /* viscous red-black sweeps per application (and per
+                            level and side of a viscous V-cycle)              */
     int restart;         /* FGMRES restart length m                           */
+    int visc_mg;         /* viscous V-cycles per application; 0: visc_sweeps
+                            sweeps on the fine grid only                      */
 } wsi_grid_desc;
 
 typedef struct {

@@ -678,6 +678,7 @@ int wsi_create_grid(const wsi_grid_desc* d, void* stream, wsi_ctx** out) {
   c->opts.mg_post = d->mg_post > 0 ? d->mg_post : 2;
   c->opts.mg_cycles = d->mg_cycles > 0 ? d->mg_cycles : 1;
   c->opts.visc_sweeps = d->visc_sweeps > 0 ? d->visc_sweeps : 2;
+  c->opts.visc_mg = d->visc_mg > 0 ? d->visc_mg : 0;
   c->opts.theta = d->theta;
   const GridDev& g = c->g;
   bool ok = true;

@@ -177,6 +177,18 @@ struct MGLevel {
   T* res;
 };
 
+// one level of the viscous multigrid (levels >= 1; level 0 uses the fine
+// coefficients and the preconditioner's work arrays)
+template <typename T>
+struct VLevel {
+  T* rho_face[3];
+  T* mu_cc;
+  T* mu_e[3];
+  T* u[3];
+  T* b[3];
+  T* res[3];
+};
+
 template <typename T>
 struct Precond {
   // pressure multigrid hierarchy
@@ -198,10 +210,13 @@ struct Precond {
   bool built = false;
   std::vector<void*> allocs;
   LearnState learn;  // float32 hierarchy only
+  std::vector<VLevel<T>> vlev;  // viscous multigrid, index = level (entry 0 unused)
+  T* vres0[3] = {nullptr, nullptr, nullptr};  // fine-level viscous residual
 };
 
 struct Opts {
   int mg_pre = 2, mg_post = 2, mg_cycles = 1, visc_sweeps = 2;
+  int visc_mg = 0;  // > 0: that many viscous V-cycles (visc_sweeps pre and post) instead of plain sweeps
   double theta = 0.5;
 };
 

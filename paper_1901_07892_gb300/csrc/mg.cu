@@ -43,6 +43,30 @@ static T* dalloc(std::vector<void*>& allocs, size_t n, std::string& err) {
 }
 
 template <typename T>
+static int vlev_alloc(Precond<T>& P, std::string& err) {
+  P.vlev.assign(P.lev.size(), VLevel<T>{});
+  for (int c = 0; c < 3; ++c) {
+    P.vres0[c] = dalloc<T>(P.allocs, fsize(P.lev[0].g, c), err);
+    if (!P.vres0[c]) return WSI_ERR_OOM;
+  }
+  for (size_t l = 1; l < P.lev.size(); ++l) {
+    const GridDev& g = P.lev[l].g;
+    VLevel<T>& V = P.vlev[l];
+    for (int c = 0; c < 3; ++c) {
+      V.rho_face[c] = dalloc<T>(P.allocs, fsize(g, c), err);
+      V.u[c] = dalloc<T>(P.allocs, fsize(g, c), err);
+      V.b[c] = dalloc<T>(P.allocs, fsize(g, c), err);
+      V.res[c] = dalloc<T>(P.allocs, fsize(g, c), err);
+      V.mu_e[c] = dalloc<T>(P.allocs, esize(g, c), err);
+      if (!V.rho_face[c] || !V.u[c] || !V.b[c] || !V.res[c] || !V.mu_e[c]) return WSI_ERR_OOM;
+    }
+    V.mu_cc = dalloc<T>(P.allocs, fsize(g, 3), err);
+    if (!V.mu_cc) return WSI_ERR_OOM;
+  }
+  return WSI_OK;
+}
+
+template <typename T>
 int precond_alloc(Precond<T>& P, const GridDev& g0, std::string& err) {
   precond_free(P);
   GridDev g = g0;
@@ -94,7 +118,7 @@ int precond_alloc(Precond<T>& P, const GridDev& g0, std::string& err) {
   P.dscratch = dalloc<double>(P.allocs, 4096, err);
   P.dsum = dalloc<double>(P.allocs, 8, err);
   if (!P.coarse_inv || !P.mu_cc || !P.rp || !P.y || !P.dscratch || !P.dsum) return WSI_ERR_OOM;
-  return WSI_OK;
+  return vlev_alloc(P, err);
 }
 
 template <typename T>
@@ -126,6 +150,105 @@ __global__ void k_coarsen_beta(GridDev gf, GridDev gc, int r0, int r1, int r2, c
     for (int b = 0; b < span[1]; ++b)
       for (int a = 0; a < span[0]; ++a) s += bf[fidx(gf, C, base[0] + a, base[1] + b, base[2] + c)];
   bc[fidx(gc, C, i, j, k)] = s / T(span[0] * span[1] * span[2]);
+}
+
+// coarse cell viscosity: mean of the children
+template <typename T>
+__global__ void k_vmu_down(GridDev gf, GridDev gc, int r0, int r1, int r2, const T* __restrict__ mf, T* mc) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= gc.n[0] || j >= gc.n[1]) return;
+  T s = T(0);
+  for (int c = 0; c < r2; ++c)
+    for (int b = 0; b < r1; ++b)
+      for (int a = 0; a < r0; ++a) s += mf[fidx(gf, 3, i * r0 + a, j * r1 + b, k * r2 + c)];
+  mc[fidx(gc, 3, i, j, k)] = s / T(r0 * r1 * r2);
+}
+
+// coarse edge viscosity: harmonic mean of the four coarse cells around the
+// edge (indices clamped at walls), the fine-grid rule on the coarse grid
+template <int E, typename T>
+__global__ void k_vedges(GridDev g, const T* __restrict__ mu, T* mu_e) {
+  constexpr int A1 = (E == 2) ? 1 : 0;
+  constexpr int A2 = (E == 0) ? 1 : 2;
+  const int ex = g.n[0] + (A1 == 0 || A2 == 0), ey = g.n[1] + (A1 == 1 || A2 == 1);
+  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= ex || j >= ey) return;
+  T s = T(0);
+  for (int o1 = 0; o1 < 2; ++o1)
+    for (int o2 = 0; o2 < 2; ++o2) {
+      int c[3] = {i, j, k};
+      c[A1] -= o1;
+      c[A2] -= o2;
+      for (int a = 0; a < 3; ++a) c[a] = clampi(c[a], 0, g.n[a] - 1);
+      s += T(1) / mu[fidx(g, 3, c[0], c[1], c[2])];
+    }
+  mu_e[eidx(g, E, i, j, k)] = T(4) / s;
+}
+
+// Face restriction of component C: full weighting (1/4, 1/2, 1/4) across the
+// coarse face along C where that axis coarsens, the mean of the children
+// across it; wall faces of the coarse grid are not unknowns (0)
+template <int C, typename T>
+__global__ void k_vrestrict(GridDev gf, GridDev gc, int r0, int r1, int r2, const T* __restrict__ rf, T* bc) {
+  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= ext(gc, C, 0) || j >= ext(gc, C, 1)) return;
+  const int I3[3] = {i, j, k};
+  const size_t id = fidx(gc, C, i, j, k);
+  if (I3[C] == 0 || I3[C] == gc.n[C]) {
+    bc[id] = T(0);
+    return;
+  }
+  const int r[3] = {r0, r1, r2};
+  int span[3] = {r0, r1, r2};
+  span[C] = 1;
+  T s = T(0);
+  for (int c = 0; c < span[2]; ++c)
+    for (int b = 0; b < span[1]; ++b)
+      for (int a = 0; a < span[0]; ++a) {
+        int f[3] = {i * r[0] + a, j * r[1] + b, k * r[2] + c};
+        if (r[C] == 2) {
+          f[C] = 2 * I3[C];
+          T v = T(0.5) * rf[fidx(gf, C, f[0], f[1], f[2])];
+          f[C] -= 1;
+          v += T(0.25) * rf[fidx(gf, C, f[0], f[1], f[2])];
+          f[C] += 2;
+          v += T(0.25) * rf[fidx(gf, C, f[0], f[1], f[2])];
+          s += v;
+        } else {
+          f[C] = I3[C];
+          s += rf[fidx(gf, C, f[0], f[1], f[2])];
+        }
+      }
+  bc[id] = s / T(span[0] * span[1] * span[2]);
+}
+
+// Face prolongation of component C, added to the fine iterate: linear along
+// C where that axis coarsens (coincident faces take the coarse value, the
+// faces between two coarse faces their mean), constant across it
+template <int C, typename T>
+__global__ void k_vprolong(GridDev gf, GridDev gc, int r0, int r1, int r2, const T* __restrict__ uc, T* uf) {
+  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= ext(gf, C, 0) || j >= ext(gf, C, 1)) return;
+  const int i3[3] = {i, j, k};
+  if (i3[C] == 0 || i3[C] == gf.n[C]) return;
+  const int r[3] = {r0, r1, r2};
+  int I[3];
+  for (int a = 0; a < 3; ++a) I[a] = a == C ? i3[a] : i3[a] / r[a];
+  T v;
+  if (r[C] == 2) {
+    if ((i3[C] & 1) == 0) {
+      I[C] = i3[C] / 2;
+      v = uc[fidx(gc, C, I[0], I[1], I[2])];
+    } else {
+      I[C] = (i3[C] - 1) / 2;
+      v = uc[fidx(gc, C, I[0], I[1], I[2])];
+      I[C] += 1;
+      v = T(0.5) * (v + uc[fidx(gc, C, I[0], I[1], I[2])]);
+    }
+  } else {
+    v = uc[fidx(gc, C, I[0], I[1], I[2])];
+  }
+  uf[fidx(gf, C, i, j, k)] += v;
 }
 
 template <typename Ts, typename Td>
@@ -183,6 +306,23 @@ int precond_setup(Precond<T>& P, const GridDev& g, const Coef<double>& fine, cud
                                                                                         F.r[2], F.beta[1], Cl.beta[1]); WSI_COUNT(); }
     { k_coarsen_beta<2, T><<<grid3(gc.n[0], gc.n[1], gc.n[2] + 1), dim3(BX, BY), 0, st>>>(F.g, gc, F.r[0], F.r[1],
                                                                                         F.r[2], F.beta[2], Cl.beta[2]); WSI_COUNT(); }
+    // viscous coefficients: face density like beta (coplanar mean), cell
+    // viscosity the mean of the children, edge viscosity harmonic again
+    const T* rf[3] = {l == 0 ? P.rho_face[0] : P.vlev[l].rho_face[0], l == 0 ? P.rho_face[1] : P.vlev[l].rho_face[1],
+                      l == 0 ? P.rho_face[2] : P.vlev[l].rho_face[2]};
+    const T* mf = l == 0 ? P.mu_cc : P.vlev[l].mu_cc;
+    VLevel<T>& VC = P.vlev[l + 1];
+    { k_coarsen_beta<0, T><<<grid3(gc.n[0] + 1, gc.n[1], gc.n[2]), dim3(BX, BY), 0, st>>>(F.g, gc, F.r[0], F.r[1],
+                                                                                        F.r[2], rf[0], VC.rho_face[0]); WSI_COUNT(); }
+    { k_coarsen_beta<1, T><<<grid3(gc.n[0], gc.n[1] + 1, gc.n[2]), dim3(BX, BY), 0, st>>>(F.g, gc, F.r[0], F.r[1],
+                                                                                        F.r[2], rf[1], VC.rho_face[1]); WSI_COUNT(); }
+    { k_coarsen_beta<2, T><<<grid3(gc.n[0], gc.n[1], gc.n[2] + 1), dim3(BX, BY), 0, st>>>(F.g, gc, F.r[0], F.r[1],
+                                                                                        F.r[2], rf[2], VC.rho_face[2]); WSI_COUNT(); }
+    { k_vmu_down<T><<<grid3(gc.n[0], gc.n[1], gc.n[2]), dim3(BX, BY), 0, st>>>(F.g, gc, F.r[0], F.r[1], F.r[2], mf,
+                                                                             VC.mu_cc); WSI_COUNT(); }
+    { k_vedges<0, T><<<grid3(gc.n[0] + 1, gc.n[1] + 1, gc.n[2]), dim3(BX, BY), 0, st>>>(gc, VC.mu_cc, VC.mu_e[0]); WSI_COUNT(); }
+    { k_vedges<1, T><<<grid3(gc.n[0] + 1, gc.n[1], gc.n[2] + 1), dim3(BX, BY), 0, st>>>(gc, VC.mu_cc, VC.mu_e[1]); WSI_COUNT(); }
+    { k_vedges<2, T><<<grid3(gc.n[0], gc.n[1] + 1, gc.n[2] + 1), dim3(BX, BY), 0, st>>>(gc, VC.mu_cc, VC.mu_e[2]); WSI_COUNT(); }
   }
   // dense coarsest operator: M = -L + c 1 1^T (SPD), inverted in float64
   const MGLevel<T>& Lc = P.lev.back();
@@ -527,6 +667,52 @@ static void sub_mean(T* x, size_t n, double* dsum, double* scratch, cudaStream_t
   { k_sub_mean<T><<<std::max(blocks, 1), 256, 0, st>>>(x, n, dsum); WSI_COUNT(); }
 }
 
+// Viscous V-cycle on level l for A u = b, A = rho/dt - theta L_mu on that
+// level's grid and coefficients: sweeps, face-residual restriction, the
+// coarser cycle (sweeps alone on the coarsest level), prolongation, sweeps.
+template <typename T>
+static void vcycle_visc(Precond<T>& P, const Opts& o, size_t l, const Coef<T>& cf0, T* const u0[3],
+                        const T* const b0[3], T inv_dt, T theta, cudaStream_t st) {
+  const GridDev& g = P.lev[l].g;
+  Coef<T> cf = cf0;
+  T* const* u = u0;
+  const T* const* b = b0;
+  VLevel<T>& V = P.vlev[l];
+  if (l > 0) {
+    for (int c = 0; c < 3; ++c) {
+      cf.rho_face[c] = V.rho_face[c];
+      cf.mu_e[c] = V.mu_e[c];
+      cf.beta[c] = nullptr;
+    }
+    cf.mu_cc = V.mu_cc;
+    u = V.u;
+    b = V.b;
+  }
+  const bool coarsest = l + 1 == P.lev.size();
+  const int nsw = coarsest ? 4 * o.visc_sweeps : o.visc_sweeps;
+  for (int s = 0; s < nsw; ++s)
+    for (int c = 0; c < 2; ++c) launch_viscous_rbgs<T>(g, cf, inv_dt, theta, u, b, c, st);
+  if (coarsest) return;
+  T* res[3];
+  for (int c = 0; c < 3; ++c) res[c] = l == 0 ? P.vres0[c] : V.res[c];
+  const T* uc[3] = {u[0], u[1], u[2]};
+  launch_viscous_residual<T>(g, cf, inv_dt, theta, uc, b, res, st);
+  const MGLevel<T>& F = P.lev[l];
+  const GridDev& gc = P.lev[l + 1].g;
+  VLevel<T>& VC = P.vlev[l + 1];
+  const int r0 = F.r[0], r1 = F.r[1], r2 = F.r[2];
+  { k_vrestrict<0, T><<<grid3(gc.n[0] + 1, gc.n[1], gc.n[2]), dim3(BX, BY), 0, st>>>(g, gc, r0, r1, r2, res[0], VC.b[0]); WSI_COUNT(); }
+  { k_vrestrict<1, T><<<grid3(gc.n[0], gc.n[1] + 1, gc.n[2]), dim3(BX, BY), 0, st>>>(g, gc, r0, r1, r2, res[1], VC.b[1]); WSI_COUNT(); }
+  { k_vrestrict<2, T><<<grid3(gc.n[0], gc.n[1], gc.n[2] + 1), dim3(BX, BY), 0, st>>>(g, gc, r0, r1, r2, res[2], VC.b[2]); WSI_COUNT(); }
+  for (int c = 0; c < 3; ++c) cudaMemsetAsync(VC.u[c], 0, fsize(gc, c) * sizeof(T), st);
+  vcycle_visc<T>(P, o, l + 1, cf0, u0, b0, inv_dt, theta, st);
+  { k_vprolong<0, T><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, gc, r0, r1, r2, VC.u[0], u[0]); WSI_COUNT(); }
+  { k_vprolong<1, T><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, gc, r0, r1, r2, VC.u[1], u[1]); WSI_COUNT(); }
+  { k_vprolong<2, T><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, gc, r0, r1, r2, VC.u[2], u[2]); WSI_COUNT(); }
+  for (int s = 0; s < o.visc_sweeps; ++s)
+    for (int c = 1; c >= 0; --c) launch_viscous_rbgs<T>(g, cf, inv_dt, theta, u, b, c, st);
+}
+
 template <typename T>
 void precond_apply(Precond<T>& P, const GridDev& g, const Opts& o, double dt, const double* v, double* z,
                    cudaStream_t st) {
@@ -544,9 +730,13 @@ void precond_apply(Precond<T>& P, const GridDev& g, const Opts& o, double dt, co
   }
   cf.mu_cc = P.mu_cc;
   T inv_dt = (T)(1.0 / dt), theta = (T)o.theta;
-  // u~ = A^{-1} r_u (approximately)
-  for (int s = 0; s < o.visc_sweeps; ++s)
-    for (int c = 0; c < 2; ++c) launch_viscous_rbgs<T>(g, cf, inv_dt, theta, P.ut, P.ru, c, st);
+  // u~ = A^{-1} r_u (approximately): red-black sweeps, or viscous V-cycles
+  if (o.visc_mg > 0) {
+    for (int c = 0; c < o.visc_mg; ++c) vcycle_visc<T>(P, o, 0, cf, P.ut, P.ru, inv_dt, theta, st);
+  } else {
+    for (int s = 0; s < o.visc_sweeps; ++s)
+      for (int c = 0; c < 2; ++c) launch_viscous_rbgs<T>(g, cf, inv_dt, theta, P.ut, P.ru, c, st);
+  }
   // y = r_p + D u~, mean-free
   dim3 gr = grid3(g.n[0], g.n[1], g.n[2]);
   { k_div_add<T><<<gr, dim3(BX, BY), 0, st>>>(g, P.ut[0], P.ut[1], P.ut[2], P.rp, P.y); WSI_COUNT(); }

@@ -40,7 +40,8 @@ class GridDesc(ctypes.Structure):
                 ("bc", ctypes.c_double * 6), ("gravity", ctypes.c_double * 3),
                 ("n_cells", ctypes.c_double), ("theta", ctypes.c_double),
                 ("precision", ctypes.c_int), ("mg_pre", ctypes.c_int), ("mg_post", ctypes.c_int),
-                ("mg_cycles", ctypes.c_int), ("visc_sweeps", ctypes.c_int), ("restart", ctypes.c_int)]
+                ("mg_cycles", ctypes.c_int), ("visc_sweeps", ctypes.c_int), ("restart", ctypes.c_int),
+                ("visc_mg", ctypes.c_int)]
 
 
 class PhaseProps(ctypes.Structure):
@@ -166,10 +167,10 @@ class Context:
 
     def __init__(self, nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, bc=(-1.0,) * 6, gravity=(0.0, 0.0, -9.81),
                  n_cells=2.0, theta=0.5, precision=PREC_FP64, mg_pre=2, mg_post=2, mg_cycles=1,
-                 visc_sweeps=2, restart=20, stream=None):
+                 visc_sweeps=2, restart=20, stream=None, visc_mg=0):
         L = lib()
         d = GridDesc(nx, ny, nz, lx, ly, lz, (ctypes.c_double * 6)(*bc), (ctypes.c_double * 3)(*gravity),
-                     n_cells, theta, precision, mg_pre, mg_post, mg_cycles, visc_sweeps, restart)
+                     n_cells, theta, precision, mg_pre, mg_post, mg_cycles, visc_sweeps, restart, visc_mg)
         h = ctypes.c_void_p()
         st = ctypes.c_void_p(stream) if stream is not None else None
         rc = L.wsi_create_grid(ctypes.byref(d), st, ctypes.byref(h))
