@@ -3,54 +3,60 @@
 //
 // Interpolation is a gather (one thread per marker: the kernel weights of
 // each axis are shared by the three components, 64 taps each); spreading
-// scatters with float64 atomicAdd into the face arrays.  Taps that
+// scatters with float64 atomicAdd into the face arrays.  Weights and sums are
+// double-float (float64 accuracy on the float32 pipes; GB300's float64 rate
+// is 1/64 of its float32 rate).  Taps that
 // fall beyond a wall are folded onto their mirror image with the ghost sign
 // (tangential: the wall's sign; normal: odd about the wall face, whose own
 // value is zero so taps landing on it drop out), which makes S_BC the exact
 // adjoint of J_BC.  Rigid-body sums are deterministic two-stage reductions.
 #include <math.h>
 
+#include "df.cuh"
 #include "internal.h"
 
 namespace wsi {
 
-// square root to ~1e-15 relative with two float64 operations: a float32
-// seed refined by one Newton (Heron) step, s1 = s0 + (x - s0^2) / (2 s0),
-// the reciprocal taken in float32 (its error enters only to second order)
-__device__ __forceinline__ double sqrt_nr(double x) {
-  const float xf = d2f_fast(x);
-  if (!(xf > 0.0f)) return 0.0;
-  const float s0f = sqrtf(xf);
-  const double s0 = f2d_fast(s0f);
-  return fma(fma(-s0, s0, x), f2d_fast(0.5f / s0f), s0);
-}
-
-// Peskin's four-point kernel (the published formula; Sec. 3.3.1 cites it)
-__device__ __forceinline__ double phi4(double r) {
-  r = fabs(r);
-  if (r <= 1.0) return (3.0 - 2.0 * r + sqrt_nr(1.0 + 4.0 * r - 4.0 * r * r)) * 0.125;
-  if (r <= 2.0) return (5.0 - 2.0 * r - sqrt_nr(-7.0 + 12.0 * r - 4.0 * r * r)) * 0.125;
-  return 0.0;
+// Peskin's four-point kernel (the published formula; Sec. 3.3.1 cites it),
+// evaluated in double-float arithmetic (float64 accuracy on the float32
+// pipes): r = |r|; (3 - 2r + sqrt(1 + 4r - 4r^2))/8 for r <= 1,
+// (5 - 2r - sqrt(-7 + 12r - 4r^2))/8 for 1 < r <= 2, 0 beyond.  The branch
+// is chosen on the leading part of r; the branches agree in value and slope
+// at r = 1 and r = 2, so the choice at a tie costs O(lo^2).
+__device__ __forceinline__ dfl phi4_df(dfl r) {
+  if (r.h < 0.0f) r = df_neg(r);
+  if (r.h > 2.0f) return df_from_float(0.0f);
+  const dfl r2 = df_mul(r, r);
+  const dfl two_r = df_scale(r, 2.0f);
+  if (r.h <= 1.0f) {
+    // 1 + 4r - 4r^2
+    const dfl u = df_add(df_from_float(1.0f), df_scale(df_sub(r, r2), 4.0f));
+    return df_scale(df_add(df_sub(df_from_float(3.0f), two_r), df_sqrt(u)), 0.125f);
+  }
+  // -7 + 12r - 4r^2
+  const dfl u = df_sub(df_sub(df_mul(r, df_from_float(12.0f)), df_scale(r2, 4.0f)), df_from_float(7.0f));
+  return df_scale(df_sub(df_sub(df_from_float(5.0f), two_r), df_sqrt(u)), 0.125f);
 }
 
 struct Tap {
   int idx[4];
-  double w[4];  // kernel weight times ghost sign; 0 for dropped taps
+  dfl w[4];  // kernel weight times ghost sign; 0 for dropped taps
 };
 
 // the four taps along axis d of a marker at coordinate Xd, for a component
 // normal to d (normal = true: faces at integer positions) or tangential
-// (cell centres, offset by half a cell)
-__device__ __forceinline__ void taps_axis(const GridDev& g, bool normal, int d, double Xd, Tap& t) {
+// (cell centres, offset by half a cell); positions in double-float
+__device__ __forceinline__ void taps_axis(const GridDev& g, bool normal, int d, dfl Xd, dfl ih, Tap& t) {
   const int n = g.n[d];
-  const double xs = normal ? Xd * g.ih[d] : Xd * g.ih[d] - 0.5;
-  const int base = (int)floor(xs) - 1;
-  const double s_lo = g.bc[2 * d], s_hi = g.bc[2 * d + 1];
+  dfl xs = df_mul(Xd, ih);
+  if (!normal) xs = df_sub(xs, df_from_float(0.5f));
+  const int base = df_floor(xs) - 1;
+  const float s_lo = g.bcf[2 * d], s_hi = g.bcf[2 * d + 1];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     int i = base + q;
-    const double r = (double)i - xs;
-    double sg = 1.0;
+    const dfl r = df_sub(df_from_float((float)i), xs);
+    float sg = 1.0f;
     for (int it = 0; it < 8; ++it) {
       if (normal) {
         if (i < 0) { i = -i; sg = -sg; }
@@ -62,8 +68,8 @@ __device__ __forceinline__ void taps_axis(const GridDev& g, bool normal, int d, 
     }
     const bool valid = normal ? (i > 0 && i < n) : (i >= 0 && i < n);
     t.idx[q] = valid ? i : 0;
-    const double w = phi4(r);
-    t.w[q] = valid ? (sg < 0.0 ? -w : w) : 0.0;
+    const dfl w = phi4_df(r);
+    t.w[q] = valid ? (sg < 0.0f ? df_neg(w) : w) : df_from_float(0.0f);
   }
 }
 
@@ -76,14 +82,16 @@ struct MarkerTaps {
 __device__ __forceinline__ void marker_taps(const GridDev& g, const double* __restrict__ X, int m, MarkerTaps& T) {
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const double xd = X[3 * m + d];
-    taps_axis(g, true, d, xd, T.tn[d]);
-    taps_axis(g, false, d, xd, T.tt[d]);
+    const dfl xd = df_split(X[3 * m + d]);
+    const dfl ih = df_split(g.ih[d]);
+    taps_axis(g, true, d, xd, ih, T.tn[d]);
+    taps_axis(g, false, d, xd, ih, T.tt[d]);
   }
 }
 
 // one thread per marker, all three components; separable sums
-// sum_z w_z sum_y w_y sum_x w_x q
+// sum_z w_z sum_y w_y sum_x w_x q in double-float, one float64 addition per
+// component at the end
 __global__ void __launch_bounds__(128) k_interp(GridDev g, CVel<double> vel, const double* __restrict__ X, int n,
                                                 double* U) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -97,21 +105,23 @@ __global__ void __launch_bounds__(128) k_interp(GridDev g, CVel<double> vel, con
     const Tap& tz = c == 2 ? T.tn[2] : T.tt[2];
     const double* __restrict__ q = vel.q[c];
     const size_t sx = (size_t)(g.n[0] + (c == 0)), sy = sx * (size_t)(g.n[1] + (c == 1));
-    double s = 0.0;
-    for (int kz = 0; kz < 4; ++kz) {
-      if (tz.w[kz] == 0.0) continue;
-      double sz = 0.0;
-      for (int ky = 0; ky < 4; ++ky) {
-        if (ty.w[ky] == 0.0) continue;
-        const double* row = q + (size_t)tz.idx[kz] * sy + (size_t)ty.idx[ky] * sx;
-        double sr = 0.0;
+    dfl s = df_from_float(0.0f);
 #pragma unroll
-        for (int kx = 0; kx < 4; ++kx) sr = fma(tx.w[kx], row[tx.idx[kx]], sr);
-        sz = fma(ty.w[ky], sr, sz);
+    for (int kz = 0; kz < 4; ++kz) {
+      if (tz.w[kz].h == 0.0f) continue;
+      dfl sz = df_from_float(0.0f);
+#pragma unroll
+      for (int ky = 0; ky < 4; ++ky) {
+        if (ty.w[ky].h == 0.0f) continue;
+        const double* row = q + (size_t)tz.idx[kz] * sy + (size_t)ty.idx[ky] * sx;
+        dfl sr = df_from_float(0.0f);
+#pragma unroll
+        for (int kx = 0; kx < 4; ++kx) sr = df_add(sr, df_mul(tx.w[kx], df_split(row[tx.idx[kx]])));
+        sz = df_add(sz, df_mul(ty.w[ky], sr));
       }
-      s = fma(tz.w[kz], sz, s);
+      s = df_add(s, df_mul(tz.w[kz], sz));
     }
-    U[3 * m + c] = s;
+    U[3 * m + c] = df_to_double(s);
   }
 }
 
@@ -121,6 +131,7 @@ __global__ void __launch_bounds__(128) k_spread(GridDev g, const double* __restr
   if (m >= n) return;
   MarkerTaps T;
   marker_taps(g, X, m, T);
+  const dfl sc = df_split(scale);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const Tap& tx = c == 0 ? T.tn[0] : T.tt[0];
@@ -128,19 +139,21 @@ __global__ void __launch_bounds__(128) k_spread(GridDev g, const double* __restr
     const Tap& tz = c == 2 ? T.tn[2] : T.tt[2];
     double* q = vel.q[c];
     const size_t sx = (size_t)(g.n[0] + (c == 0)), sy = sx * (size_t)(g.n[1] + (c == 1));
-    const double f = F[3 * m + c] * scale;
-    double fx[4];
+    const dfl f = df_mul(df_split(F[3 * m + c]), sc);
+    dfl fx[4];
 #pragma unroll
-    for (int kx = 0; kx < 4; ++kx) fx[kx] = f * tx.w[kx];
+    for (int kx = 0; kx < 4; ++kx) fx[kx] = df_mul(f, tx.w[kx]);
+#pragma unroll
     for (int kz = 0; kz < 4; ++kz) {
-      if (tz.w[kz] == 0.0) continue;
+      if (tz.w[kz].h == 0.0f) continue;
+#pragma unroll
       for (int ky = 0; ky < 4; ++ky) {
-        const double wyz = tz.w[kz] * ty.w[ky];
-        if (wyz == 0.0) continue;
+        if (ty.w[ky].h == 0.0f) continue;
+        const dfl wyz = df_mul(tz.w[kz], ty.w[ky]);
         double* row = q + (size_t)tz.idx[kz] * sy + (size_t)ty.idx[ky] * sx;
 #pragma unroll
         for (int kx = 0; kx < 4; ++kx)
-          if (tx.w[kx] != 0.0) atomicAdd(&row[tx.idx[kx]], wyz * fx[kx]);
+          if (tx.w[kx].h != 0.0f) atomicAdd(&row[tx.idx[kx]], df_to_double(df_mul(wyz, fx[kx])));
       }
     }
   }

@@ -29,6 +29,7 @@ struct PhaseConst {
   // {0, 1} the two Heavisides, each computed by the same expression as inside
   // the bands so that both give identical results there
   double inv_eps;
+  float inv_eps_f;
   double rho_tab[4], beta_tab[4], flow_tab[2], mu_tab[4], imu_tab[4], mue_tab[4];
 };
 // fill the derived fields of pc from its properties (host)

@@ -24,6 +24,17 @@ static inline dim3 grid3(int nx, int ny, int nz) { return dim3(cdiv(nx, BX), cdi
 // float64 pipe); where that copy is ambiguous, |t| within 2^-24 of 1, the
 // ramp differs from its limit by ~(1 - |t|)^3, far below float64 resolution.
 // code: 0 or 1 away from the band (value exactly 0 or 1), 2 inside.
+// Float32 pre-test: tf, a float32 estimate of t = phi/eps whose error is at
+// most `bound` (a few units in the last float32 place of the magnitudes that
+// formed it), decides the code without any float64 operation when it lies
+// beyond the band edges by more than that bound; otherwise 2 (undecided:
+// the float64 path runs).
+__device__ __forceinline__ int band_code_f(float tf, float bound) {
+  if (tf < -1.0f - bound) return 0;
+  if (tf > 1.0f + bound) return 1;
+  return 2;
+}
+
 __device__ __forceinline__ double heav(double phi, double inv_eps, int& code) {
   const double t = phi * inv_eps;
   const float tf = d2f_fast(t);
@@ -60,8 +71,19 @@ __global__ void k_mat_cells(GridDev g, PhaseConst pc, const double* __restrict__
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (i >= g.n[0] || j >= g.n[1]) return;
   size_t id = fidx(g, 3, i, j, k);
-  int c1, c2;
-  const double h1 = heav(phi[id], pc.inv_eps, c1), h2 = heav(psi[id], pc.inv_eps, c2);
+  const double a = phi[id], b = psi[id];
+  const float ie = pc.inv_eps_f;
+  const float af = d2f_fast(a), bf = d2f_fast(b);
+  // bound: 2^-20 |t|, far above the float32 rounding of phi and of phi/eps
+  int c1 = band_code_f(af * ie, 9.5367431640625e-07f * fabsf(af * ie)),
+      c2 = band_code_f(bf * ie, 9.5367431640625e-07f * fabsf(bf * ie));
+  if (c1 < 2 && c2 < 2) {
+    if (rho_cc) rho_cc[id] = pc.rho_tab[c1 + 2 * c2];
+    mu_cc[id] = pc.mu_tab[c1 + 2 * c2];
+    if (pc.inv_mu) pc.inv_mu[id] = pc.imu_tab[c1 + 2 * c2];
+    return;
+  }
+  const double h1 = heav(a, pc.inv_eps, c1), h2 = heav(b, pc.inv_eps, c2);
   if (rho_cc) rho_cc[id] = two_stage(h1, c1, h2, c2, pc.rho_l, pc.rho_g, pc.rho_s, pc.rho_tab);
   const double mu = two_stage(h1, c1, h2, c2, pc.mu_l, pc.mu_g, pc.mu_s, pc.mu_tab);
   mu_cc[id] = mu;
@@ -76,13 +98,33 @@ __global__ void k_mat_faces(GridDev g, PhaseConst pc, const double* __restrict__
   if (i >= ext(g, C, 0) || j >= ext(g, C, 1)) return;
   int lo[3] = {i, j, k}, hi[3] = {i, j, k};
   lo[C] -= 1;
-  const double pa = 0.5 * (cell_at(g, phi, lo[0], lo[1], lo[2]) + cell_at(g, phi, hi[0], hi[1], hi[2]));
-  int c1;
-  const double h1 = heav(pa, pc.inv_eps, c1);
+  const double pl = cell_at(g, phi, lo[0], lo[1], lo[2]), ph = cell_at(g, phi, hi[0], hi[1], hi[2]);
   size_t id = fidx(g, C, i, j, k);
+  const float ie = pc.inv_eps_f;
+  // bound: 2^-20 (|phi_lo| + |phi_hi|)/eps, far above the float32 rounding of
+  // the two values, their mean and the scaling
+  const float plf = d2f_fast(pl), phf = d2f_fast(ph);
+  int c1 = band_code_f(0.5f * (plf + phf) * ie, 9.5367431640625e-07f * (fabsf(plf) + fabsf(phf)) * ie);
+  double sl = 0.0, sh = 0.0;
+  int c2 = 0;
   if (rho_face) {
-    const double sa = 0.5 * (cell_at(g, psi, lo[0], lo[1], lo[2]) + cell_at(g, psi, hi[0], hi[1], hi[2]));
-    int c2;
+    sl = cell_at(g, psi, lo[0], lo[1], lo[2]);
+    sh = cell_at(g, psi, hi[0], hi[1], hi[2]);
+    const float slf = d2f_fast(sl), shf = d2f_fast(sh);
+    c2 = band_code_f(0.5f * (slf + shf) * ie, 9.5367431640625e-07f * (fabsf(slf) + fabsf(shf)) * ie);
+  }
+  if (c1 < 2 && c2 < 2) {  // away from both bands: table values only
+    if (rho_face) {
+      rho_face[id] = pc.rho_tab[c1 + 2 * c2];
+      if (beta) beta[id] = pc.beta_tab[c1 + 2 * c2];
+    }
+    if (rho_flow) rho_flow[id] = pc.flow_tab[c1];
+    return;
+  }
+  const double pa = 0.5 * (pl + ph);
+  const double h1 = heav(pa, pc.inv_eps, c1);
+  if (rho_face) {
+    const double sa = 0.5 * (sl + sh);
     const double h2 = heav(sa, pc.inv_eps, c2);
     const double r = two_stage(h1, c1, h2, c2, pc.rho_l, pc.rho_g, pc.rho_s, pc.rho_tab);
     rho_face[id] = r;
@@ -129,6 +171,7 @@ __global__ void k_mat_edges(GridDev g, PhaseConst pc, const double* __restrict__
 
 void phase_tables(PhaseConst& pc) {
   pc.inv_eps = 1.0 / pc.eps;
+  pc.inv_eps_f = (float)pc.inv_eps;
   for (int h2 = 0; h2 < 2; ++h2)
     for (int h1 = 0; h1 < 2; ++h1) {
       const int t = h1 + 2 * h2;
