@@ -220,7 +220,8 @@ def test_ib_parity_near_walls():
     vel = [rng.standard_normal(g.face_shape(d)) * g.interior_face_mask(d) for d in range(3)]
     vflat = np.concatenate([a.ravel() for a in vel])
     U = ctx.interp(vflat, X).reshape(n, 3)
-    assert _rel(U, oib.interpolate(g, vel, X)) < 1e-13
+    # the operator-apply bound; the double-float sums land near 1e-13
+    assert _rel(U, oib.interpolate(g, vel, X)) < OP_TOL
     F = rng.standard_normal((n, 3))
     S = ctx.spread(F, X, 2e-4)
     ref = np.concatenate([a.ravel() for a in oib.spread(g, F, X, 2e-4)])
