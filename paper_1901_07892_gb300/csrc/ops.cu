@@ -555,11 +555,16 @@ __global__ void k_rhs_cycle(size_t n0, size_t n1, size_t n2, const double* __res
   size_t stride = (size_t)gridDim.x * blockDim.x;
   size_t n = n0 + n1 + n2;
   for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
-    double grav;
-    if (t < n0) grav = rg0[t] * g0;
-    else if (t < n0 + n1) grav = rg1[t - n0] * g1;
-    else grav = rg2[t - n0 - n1] * g2;
-    b[t] = b0[t] - (double)Cc[t] + grav;
+    // components without gravity skip the density load and the product
+    double grav = 0.0;
+    if (t < n0) {
+      if (g0 != 0.0) grav = rg0[t] * g0;
+    } else if (t < n0 + n1) {
+      if (g1 != 0.0) grav = rg1[t - n0] * g1;
+    } else if (g2 != 0.0) {
+      grav = rg2[t - n0 - n1] * g2;
+    }
+    b[t] = b0[t] - cvt<double, TC>(Cc[t]) + grav;
   }
 }
 

@@ -7,7 +7,8 @@
 // of it, so the kernel computes it once: a 32 x 8 block owns a tile of
 // C-faces in (x, y) and marches up a chunk of z-planes; x- and y-fluxes of a
 // plane go through shared memory (one halo column / row computed by the edge
-// threads), the z-flux of the plane below is kept in a register.
+// threads), the z-flux of the plane below is kept in a register.  The
+// limiter's inputs are staged per plane in shared memory (see k_transport).
 //
 // Storage and arithmetic type T: float64 on the plain path; float32 on the
 // mixed path, where the step keeps float32 shadow copies of the transported
@@ -46,83 +47,10 @@ __device__ __forceinline__ T cui(T qU, T qC, T qD) {
   return qU + f;
 }
 
-// Value of the C-face array a at index m along axis D (other indices from
-// i3), extended by two ghost layers: even mirror (density) or the velocity
-// rule (odd about wall faces when C == D, the wall's sign across D != C).
-template <int C, int D, bool VEL, typename T>
-__device__ __forceinline__ T ext_get(const GridDev& g, const T* __restrict__ a, const int i3[3], int m) {
-  int n = g.n[D] + (C == D ? 1 : 0);  // stored extent along D
-  T s = T(1);
-  int mm = m;
-  if (m < 0) {
-    int gl = -m;
-    if (C == D) {
-      mm = gl;
-      if (VEL) s = T(-1);
-    } else {
-      mm = gl - 1;
-      if (VEL) s = gbc<T>(g, 2 * D);
-    }
-  } else if (m >= n) {
-    int gl = m - (n - 1);
-    if (C == D) {
-      mm = (n - 1) - gl;
-      if (VEL) s = T(-1);
-    } else {
-      mm = n - gl;
-      if (VEL) s = gbc<T>(g, 2 * D + 1);
-    }
-  }
-  mm = clampi(mm, 0, n - 1);
-  int c3[3] = {i3[0], i3[1], i3[2]};
-  c3[D] = mm;
-  return s * a[fidx(g, C, c3[0], c3[1], c3[2])];
-}
-
-// limited value at the CV face between entries m_lo and m_lo + 1 along D
-template <int C, int D, bool VEL, typename T>
-__device__ __forceinline__ T lim_at(const GridDev& g, const T* a, const int i3[3], int m_lo, T adv) {
-  if (adv > T(0))
-    return cui<T>(ext_get<C, D, VEL, T>(g, a, i3, m_lo - 1), ext_get<C, D, VEL, T>(g, a, i3, m_lo),
-                  ext_get<C, D, VEL, T>(g, a, i3, m_lo + 1));
-  return cui<T>(ext_get<C, D, VEL, T>(g, a, i3, m_lo + 2), ext_get<C, D, VEL, T>(g, a, i3, m_lo + 1),
-                ext_get<C, D, VEL, T>(g, a, i3, m_lo));
-}
-
-// Flux through the D-direction control-volume face at position m of the
-// C-face column through i3 (the D-index of i3 is ignored):
-//   C == D: CV face at cell m, between C-faces m and m+1;
-//   C != D: CV face on the edge at D-face position m, between C-faces with
-//           D-indices m-1 and m; advective velocity from the two D-faces
-//           adjacent along C (i3 must not be a wall face along C).
-template <int C, int D, bool WITHV, typename T>
-__device__ __forceinline__ T cv_flux(const GridDev& g, const CVel<T>& vel, const T* __restrict__ rho,
-                                     const int i3[3], int m) {
-  T adv;
-  int mlo;
-  if (C == D) {
-    int a3[3] = {i3[0], i3[1], i3[2]};
-    a3[C] = m;
-    T q0 = vel.q[C][fidx(g, C, a3[0], a3[1], a3[2])];
-    a3[C] = m + 1;
-    T q1 = vel.q[C][fidx(g, C, a3[0], a3[1], a3[2])];
-    adv = T(0.5) * (q0 + q1);
-    mlo = m;
-  } else {
-    int b1[3] = {i3[0], i3[1], i3[2]};
-    b1[D] = m;
-    int b0[3] = {b1[0], b1[1], b1[2]};
-    b0[C] -= 1;
-    adv = T(0.5) * (vel.q[D][fidx(g, D, b0[0], b0[1], b0[2])] + vel.q[D][fidx(g, D, b1[0], b1[1], b1[2])]);
-    mlo = m - 1;
-  }
-  T F = adv * lim_at<C, D, false, T>(g, rho, i3, mlo, adv);
-  if (WITHV) F *= lim_at<C, D, true, T>(g, vel.q[C], i3, mlo, adv);
-  return F;
-}
-
-// Entry m of the C-face array along axis D with two ghost layers: the stored
-// index it maps to and the velocity ghost sign (ext_get without the load).
+// Entry m of the C-face array along axis D extended by two ghost layers: the
+// stored index it maps to and the velocity ghost sign.  Density ghosts are
+// even mirrors; velocity ghosts are odd about wall faces when C == D (the wall
+// face itself is zero) and take the wall's tangential sign across D != C.
 template <int C, int D, typename T>
 __device__ __forceinline__ int mirror_index(const GridDev& g, int m, T& s) {
   const int n = g.n[D] + (C == D ? 1 : 0);
@@ -150,37 +78,10 @@ __device__ __forceinline__ int mirror_index(const GridDev& g, int m, T& s) {
   return clampi(mm, 0, n - 1);
 }
 
-// Limiter taps of the two CV faces of a column along D: entries mlo-2 ..
-// mlo+2, mlo that of the hi face; the hi face uses entries 1..4, the lo face
-// (one position lower) entries 0..3.
-template <typename T>
-struct Taps {
-  int o[5];  // offsets into the C-face array from the column base
-  T s[5];    // velocity ghost signs
-};
-
-template <int C, int D, typename T>
-__device__ __forceinline__ void make_taps(const GridDev& g, int mlo, int stride, Taps<T>& t) {
-#pragma unroll
-  for (int q = 0; q < 5; ++q) t.o[q] = mirror_index<C, D, T>(g, mlo - 2 + q, t.s[q]) * stride;
-}
-
 // limited value from the four taps for advective velocity adv
 template <typename T>
 __device__ __forceinline__ T lim4(T t0, T t1, T t2, T t3, T adv) {
   return adv > T(0) ? cui<T>(t0, t1, t2) : cui<T>(t3, t2, t1);
-}
-
-// flux through the CV face whose taps start at entry f (0: lo face, 1: hi)
-template <bool WITHV, typename T>
-__device__ __forceinline__ T flux_from(const T* __restrict__ rho, const T* __restrict__ qc, size_t base,
-                                       const Taps<T>& t, int f, T adv) {
-  T F = adv * lim4<T>(rho[base + t.o[f]], rho[base + t.o[f + 1]], rho[base + t.o[f + 2]], rho[base + t.o[f + 3]],
-                      adv);
-  if (WITHV)
-    F *= lim4<T>(t.s[f] * qc[base + t.o[f]], t.s[f + 1] * qc[base + t.o[f + 1]], t.s[f + 2] * qc[base + t.o[f + 2]],
-                 t.s[f + 3] * qc[base + t.o[f + 3]], adv);
-  return F;
 }
 
 // advective velocity at the D-direction CV face at position m of the C-face
@@ -200,87 +101,175 @@ __device__ __forceinline__ T adv_at(const GridDev& g, const CVel<T>& vel, int i,
   return T(0.5) * (vel.q[D][id1 - sc] + vel.q[D][id1]);
 }
 
-// The limiter taps along x and y depend only on the thread's (i, j) and are
-// built once; along z once per plane.  Array offsets follow from strides.
+// Per z-plane the block stages the transported field (and, for C, the
+// velocity component) of its tile with a two-entry halo in x and y into
+// shared memory, ghosts already mirrored (the mirror offsets of the staged
+// entries depend only on x and y: computed once per thread); the four
+// limiter taps of every x- and y-flux then come from shared memory.  Along z
+// each thread keeps its column's last four entries in registers.  Advective
+// velocities are read from global memory (two values per flux, coalesced).
 template <int C, bool WITHV, typename T>
-__global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, CVel<T> vel, const T* __restrict__ rho,
-                                                      T* out) {
+__global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, CVel<T> vel, const T* __restrict__ rho, T* out,
+                                                      int zchunk) {
+  constexpr int HX = BX + 4, HY = BY + 4, NS = (HX * HY + BX * BY - 1) / (BX * BY);
+  __shared__ T sR[HY][HX];
+  __shared__ T sQ[WITHV ? HY : 1][WITHV ? HX : 1];
   __shared__ T sFx[BY][BX + 1];
   __shared__ T sFy[BY + 1][BX];
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int i = blockIdx.x * BX + tx, j = blockIdx.y * BY + ty;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+  const int i = x0 + tx, j = y0 + ty;
   const int e0 = ext(g, C, 0), e1 = ext(g, C, 1), e2 = ext(g, C, 2);
   const bool inside = i < e0 && j < e1;
-  const int k0 = blockIdx.z * ZCHUNK;
-  const int k1 = min(k0 + ZCHUNK, e2);
+  const int k0 = blockIdx.z * zchunk;
+  const int k1 = min(k0 + zchunk, e2);
   const int ox = (C == 0) ? -1 : 0, oy = (C == 1) ? -1 : 0, oz = (C == 2) ? -1 : 0;
-  const size_t fx = (size_t)e0, plane = (size_t)e0 * e1;
+  const size_t plane = (size_t)e0 * e1;
   const T* __restrict__ qc = vel.q[C];
-  // CV-face positions: hi = index + o + 1, lo = index + o; the taps start at
-  // mlo = m (C == D) or m - 1 (C != D)
-  const int mxh = i + ox + 1, mxl = i + ox, myh = j + oy + 1, myl = j + oy;
-  Taps<T> tx5, ty5;
-  make_taps<C, 0, T>(g, C == 0 ? mxh : mxh - 1, 1, tx5);
-  make_taps<C, 1, T>(g, C == 1 ? myh : myh - 1, (int)fx, ty5);
+  // staged entries of this thread: in-plane offset (mirrored) and velocity sign
+  int soff[NS];
+  T ssg[NS];
+#pragma unroll
+  for (int r = 0; r < NS; ++r) {
+    const int t = tid + r * BX * BY;
+    soff[r] = -1;
+    ssg[r] = T(1);
+    if (t < HX * HY) {
+      const int hy = t / HX, hx = t - hy * HX;
+      T sx, sy;
+      const int mx = mirror_index<C, 0, T>(g, x0 - 2 + hx, sx);
+      const int my = mirror_index<C, 1, T>(g, y0 - 2 + hy, sy);
+      soff[r] = my * e0 + mx;
+      ssg[r] = sx * sy;
+    }
+  }
+  // z window: entries k-1 .. k+2 of this column (density, velocity)
+  const size_t col = (size_t)min(j, e1 - 1) * e0 + min(i, e0 - 1);
+  T zr[4], zq[4];
+  auto zload = [&](int m, T& r_, T& q_) {
+    T sz;
+    const int mm = mirror_index<C, 2, T>(g, m, sz);
+    r_ = rho[(size_t)mm * plane + col];
+    q_ = WITHV ? sz * qc[(size_t)mm * plane + col] : T(0);
+  };
+#pragma unroll
+  for (int q = 0; q < 4; ++q) zload(k0 - 2 + q, zr[q], zq[q]);
   T Fz_lo = T(0);
   for (int k = k0; k < k1; ++k) {
+    // stage plane k
+#pragma unroll
+    for (int r = 0; r < NS; ++r) {
+      const int t = tid + r * BX * BY;
+      if (soff[r] >= 0) {
+        const int hy = t / HX, hx = t - hy * HX;
+        const size_t a = (size_t)k * plane + soff[r];
+        sR[hy][hx] = rho[a];
+        if (WITHV) sQ[hy][hx] = ssg[r] * qc[a];
+      }
+    }
+    __syncthreads();
     const int idC = (C == 0) ? i : ((C == 1) ? j : k);
     const bool wall = idC == 0 || idC == g.n[C];
-    const size_t rowx = (size_t)k * plane + (size_t)j * fx;  // x taps: row base
-    const size_t coly = (size_t)k * plane + (size_t)i;       // y taps: column base
     if (inside) {
+      // x-fluxes: hi through the CV face above i (taps i-1 .. i+2), lo below (taps i-2 .. i+1)
       const bool okx = (C == 0) || !wall;
       T hi = T(0), lo = T(0);
+      const int mxh = i + ox + 1, mxl = i + ox;
       if (okx) {
-        if (C != 0 || mxh <= g.n[0] - 1) hi = flux_from<WITHV, T>(rho, qc, rowx, tx5, 1, adv_at<C, 0, T>(g, vel, i, j, k, mxh));
-        if (tx == 0 && (C != 0 || mxl >= 0)) lo = flux_from<WITHV, T>(rho, qc, rowx, tx5, 0, adv_at<C, 0, T>(g, vel, i, j, k, mxl));
+        const int hy = ty + 2;
+        if (C != 0 || mxh <= g.n[0] - 1) {
+          const T adv = adv_at<C, 0, T>(g, vel, i, j, k, mxh);
+          hi = adv * lim4<T>(sR[hy][tx + 1], sR[hy][tx + 2], sR[hy][tx + 3], sR[hy][tx + 4], adv);
+          if (WITHV) hi *= lim4<T>(sQ[hy][tx + 1], sQ[hy][tx + 2], sQ[hy][tx + 3], sQ[hy][tx + 4], adv);
+        }
+        if (tx == 0 && (C != 0 || mxl >= 0)) {
+          const T adv = adv_at<C, 0, T>(g, vel, i, j, k, mxl);
+          lo = adv * lim4<T>(sR[hy][tx], sR[hy][tx + 1], sR[hy][tx + 2], sR[hy][tx + 3], adv);
+          if (WITHV) lo *= lim4<T>(sQ[hy][tx], sQ[hy][tx + 1], sQ[hy][tx + 2], sQ[hy][tx + 3], adv);
+        }
       }
       sFx[ty][tx + 1] = hi;
       if (tx == 0) sFx[ty][0] = lo;
+      // y-fluxes
       const bool oky = (C == 1) || !wall;
       hi = T(0);
       lo = T(0);
+      const int myh = j + oy + 1, myl = j + oy;
       if (oky) {
-        if (C != 1 || myh <= g.n[1] - 1) hi = flux_from<WITHV, T>(rho, qc, coly, ty5, 1, adv_at<C, 1, T>(g, vel, i, j, k, myh));
-        if (ty == 0 && (C != 1 || myl >= 0)) lo = flux_from<WITHV, T>(rho, qc, coly, ty5, 0, adv_at<C, 1, T>(g, vel, i, j, k, myl));
+        const int hx = tx + 2;
+        if (C != 1 || myh <= g.n[1] - 1) {
+          const T adv = adv_at<C, 1, T>(g, vel, i, j, k, myh);
+          hi = adv * lim4<T>(sR[ty + 1][hx], sR[ty + 2][hx], sR[ty + 3][hx], sR[ty + 4][hx], adv);
+          if (WITHV) hi *= lim4<T>(sQ[ty + 1][hx], sQ[ty + 2][hx], sQ[ty + 3][hx], sQ[ty + 4][hx], adv);
+        }
+        if (ty == 0 && (C != 1 || myl >= 0)) {
+          const T adv = adv_at<C, 1, T>(g, vel, i, j, k, myl);
+          lo = adv * lim4<T>(sR[ty][hx], sR[ty + 1][hx], sR[ty + 2][hx], sR[ty + 3][hx], adv);
+          if (WITHV) lo *= lim4<T>(sQ[ty][hx], sQ[ty + 1][hx], sQ[ty + 2][hx], sQ[ty + 3][hx], adv);
+        }
       }
       sFy[ty + 1][tx] = hi;
       if (ty == 0) sFy[0][tx] = lo;
     }
     __syncthreads();
+    if (k == k0) {
+      // lo z-flux of the chunk, from the window's entries k0-2 .. k0+1
+      const bool okz = (C == 2) || !wall;
+      const int mzl = k + oz;
+      Fz_lo = T(0);
+      if (inside && okz && (C != 2 || mzl >= 0)) {
+        const T adv = adv_at<C, 2, T>(g, vel, i, j, k, mzl);
+        Fz_lo = adv * lim4<T>(zr[0], zr[1], zr[2], zr[3], adv);
+        if (WITHV) Fz_lo *= lim4<T>(zq[0], zq[1], zq[2], zq[3], adv);
+      }
+    }
+    // z window -> entries k-1 .. k+2
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      zr[q] = zr[q + 1];
+      zq[q] = zq[q + 1];
+    }
+    zload(k + 2, zr[3], zq[3]);
     if (inside) {
       const bool okz = (C == 2) || !wall;
       T Fz_hi = T(0);
-      if (okz) {
-        const size_t colz = (size_t)j * fx + (size_t)i;
-        const int mzh = k + oz + 1;
-        Taps<T> tz;
-        make_taps<C, 2, T>(g, C == 2 ? mzh : mzh - 1, (int)plane, tz);
-        if (C != 2 || mzh <= g.n[2] - 1) Fz_hi = flux_from<WITHV, T>(rho, qc, colz, tz, 1, adv_at<C, 2, T>(g, vel, i, j, k, mzh));
-        if (k == k0) {
-          const int mzl = k + oz;
-          Fz_lo = (C != 2 || mzl >= 0) ? flux_from<WITHV, T>(rho, qc, colz, tz, 0, adv_at<C, 2, T>(g, vel, i, j, k, mzl))
-                                       : T(0);
-        }
+      const int mzh = k + oz + 1;
+      if (okz && (C != 2 || mzh <= g.n[2] - 1)) {
+        const T adv = adv_at<C, 2, T>(g, vel, i, j, k, mzh);
+        Fz_hi = adv * lim4<T>(zr[0], zr[1], zr[2], zr[3], adv);
+        if (WITHV) Fz_hi *= lim4<T>(zq[0], zq[1], zq[2], zq[3], adv);
       }
       const T r = (sFx[ty][tx + 1] - sFx[ty][tx]) * ginv<T>(g, 0) + (sFy[ty + 1][tx] - sFy[ty][tx]) * ginv<T>(g, 1) +
                   (Fz_hi - Fz_lo) * ginv<T>(g, 2);
-      out[(size_t)k * plane + (size_t)j * fx + i] = wall ? T(0) : r;
+      out[(size_t)k * plane + (size_t)j * e0 + i] = wall ? T(0) : r;
       Fz_lo = Fz_hi;
     }
     __syncthreads();
   }
 }
 
+// z-chunk of the transport kernels: long marches amortise the chunk start,
+// but the grid must still fill the GPU (about 8 blocks per SM)
+static int transport_chunk(int ex, int ey, int ez) {
+  const long long base = (long long)cdiv(ex, BX) * cdiv(ey, BY);
+  int c = 32;
+  while (c > 4 && base * cdiv(ez, c) < 152LL * 8) c /= 2;
+  return c;
+}
+
 template <bool WITHV, typename T>
 static void transport_all(const GridDev& g, const CVel<T>& v, const T* const rho[3], T* const out[3],
                           cudaStream_t st) {
-  { k_transport<0, WITHV, T><<<dim3(cdiv(g.n[0] + 1, BX), cdiv(g.n[1], BY), cdiv(g.n[2], ZCHUNK)), dim3(BX, BY), 0,
-                               st>>>(g, v, rho[0], out[0]); WSI_COUNT(); }
-  { k_transport<1, WITHV, T><<<dim3(cdiv(g.n[0], BX), cdiv(g.n[1] + 1, BY), cdiv(g.n[2], ZCHUNK)), dim3(BX, BY), 0,
-                               st>>>(g, v, rho[1], out[1]); WSI_COUNT(); }
-  { k_transport<2, WITHV, T><<<dim3(cdiv(g.n[0], BX), cdiv(g.n[1], BY), cdiv(g.n[2] + 1, ZCHUNK)), dim3(BX, BY), 0,
-                               st>>>(g, v, rho[2], out[2]); WSI_COUNT(); }
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+  int zc = transport_chunk(n0 + 1, n1, n2);
+  { k_transport<0, WITHV, T><<<dim3(cdiv(n0 + 1, BX), cdiv(n1, BY), cdiv(n2, zc)), dim3(BX, BY), 0, st>>>(
+      g, v, rho[0], out[0], zc); WSI_COUNT(); }
+  zc = transport_chunk(n0, n1 + 1, n2);
+  { k_transport<1, WITHV, T><<<dim3(cdiv(n0, BX), cdiv(n1 + 1, BY), cdiv(n2, zc)), dim3(BX, BY), 0, st>>>(
+      g, v, rho[1], out[1], zc); WSI_COUNT(); }
+  zc = transport_chunk(n0, n1, n2 + 1);
+  { k_transport<2, WITHV, T><<<dim3(cdiv(n0, BX), cdiv(n1, BY), cdiv(n2 + 1, zc)), dim3(BX, BY), 0, st>>>(
+      g, v, rho[2], out[2], zc); WSI_COUNT(); }
 }
 
 template <typename T>
