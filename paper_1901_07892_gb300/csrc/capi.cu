@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "df.cuh"
 #include "internal.h"
 
 using namespace wsi;
@@ -196,9 +197,23 @@ PhaseConst phase_const(wsi_ctx* c) {
   return pc;
 }
 
+// 1/a in double-float arithmetic: float32 reciprocal r, residual 1 - a r
+// formed with a split into (hi, lo) and fused multiply-adds, one Newton step;
+// one float64 addition forms the result (~1e-14 relative).  Zero,
+// subnormal-range and non-finite a take the float64 division.
 __global__ void k_recip(size_t n, const double* __restrict__ a, double* b) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) b[t] = rcp_nr(a[t]);
+  if (t >= n) return;
+  const double v = a[t];
+  const dfl x = df_split(v);
+  if (!(fabsf(x.h) > 1e-30f) || !(fabsf(x.h) < 1e30f)) {
+    b[t] = 1.0 / v;
+    return;
+  }
+  const float r = 1.0f / x.h;
+  // e = 1 - x r, exactly enough: fma for the leading product, lo part plainly
+  const float e = fmaf(-x.h, r, 1.0f) - x.l * r;
+  b[t] = df_to_double(quick_two_sum(r, r * e));
 }
 
 void recip(wsi_ctx* c, const double* a, double* b, size_t n) {
