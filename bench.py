@@ -116,6 +116,22 @@ def build_case(n):
     return c
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of every rank's x (the whole job takes as long as its
+    slowest replica); x itself when not distributed."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, cells, steps, seconds):
+    """Whole-job cell-steps/s: every replica advances its own grid."""
+    return world * cells * steps / seconds
+
+
 def learned_comparison(args, stream):
     """Pressure solves D(beta G) x = y to 1e-8 at args.n^3 (the projection
     sub-problem): learned correction + float32 V-cycles vs plain float32
@@ -283,11 +299,7 @@ def main():
             its.append([st.iters[0], st.iters[1]])
         ev1.record(stream)
         barrier()
-        ms = ev0.elapsed_time(ev1)
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
         return ms, its
 
     ctx = make_ctx(prec)
@@ -304,7 +316,7 @@ def main():
     kt_ms, kt_n = wsi.ktimer_read()
     wsi.ktimer_enable(-1)
     clocks = sample_clocks_stop(clk, clk_path, torch.cuda.current_device())
-    value = world * cells * args.steps / (ms * 1e-3)
+    value = job_throughput(world, cells, args.steps, ms * 1e-3)
 
     # roofline of the chosen kernel: algorithmic work per launch / measured duration
     pb = 4 if prec == wsi.PREC_MIXED else 8
@@ -348,14 +360,10 @@ def main():
         ctx.L.wsi_get_field(ctx._h, wsi.F_VEL_OLD, wsi._ptr(hvo))
         ctx.L.wsi_get_field(ctx._h, wsi.F_PHI, wsi._ptr(hphi))
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     h2d = 8 * (2 * ctx.nvel + 2 * ctx.ncell)
     d2h = 8 * (2 * ctx.nvel + 2 * ctx.ncell)
-    e2e = {"value": world * cells * args.steps / e2e_s, "unit": "cell-steps/s", "h2d_bytes_per_step": h2d,
+    e2e = {"value": job_throughput(world, cells, args.steps, e2e_s), "unit": "cell-steps/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
     ctx.close()
 
