@@ -156,6 +156,21 @@ __global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, CVel<T> vel, co
   for (int q = 0; q < 4; ++q) zload(k0 - 2 + q, zr[q], zq[q]);
   T Fz_lo = T(0);
   for (int k = k0; k < k1; ++k) {
+    const int idC = (C == 0) ? i : ((C == 1) ? j : k);
+    const bool wall = idC == 0 || idC == g.n[C];
+    // which fluxes this thread forms, and their advective velocities: loaded
+    // before the staging barrier so that their latency overlaps it
+    const int mxh = i + ox + 1, mxl = i + ox, myh = j + oy + 1, myl = j + oy;
+    const bool okx = inside && ((C == 0) || !wall), oky = inside && ((C == 1) || !wall);
+    const bool fxh = okx && (C != 0 || mxh <= g.n[0] - 1), fxl = okx && tx == 0 && (C != 0 || mxl >= 0);
+    const bool fyh = oky && (C != 1 || myh <= g.n[1] - 1), fyl = oky && ty == 0 && (C != 1 || myl >= 0);
+    const T axh = fxh ? adv_at<C, 0, T>(g, vel, i, j, k, mxh) : T(0);
+    const T axl = fxl ? adv_at<C, 0, T>(g, vel, i, j, k, mxl) : T(0);
+    const T ayh = fyh ? adv_at<C, 1, T>(g, vel, i, j, k, myh) : T(0);
+    const T ayl = fyl ? adv_at<C, 1, T>(g, vel, i, j, k, myl) : T(0);
+    const int mzh = k + oz + 1;
+    const bool fzh = inside && ((C == 2) || !wall) && (C != 2 || mzh <= g.n[2] - 1);
+    const T azh = fzh ? adv_at<C, 2, T>(g, vel, i, j, k, mzh) : T(0);
     // stage plane k
 #pragma unroll
     for (int r = 0; r < NS; ++r) {
@@ -168,45 +183,31 @@ __global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, CVel<T> vel, co
       }
     }
     __syncthreads();
-    const int idC = (C == 0) ? i : ((C == 1) ? j : k);
-    const bool wall = idC == 0 || idC == g.n[C];
     if (inside) {
       // x-fluxes: hi through the CV face above i (taps i-1 .. i+2), lo below (taps i-2 .. i+1)
-      const bool okx = (C == 0) || !wall;
       T hi = T(0), lo = T(0);
-      const int mxh = i + ox + 1, mxl = i + ox;
-      if (okx) {
-        const int hy = ty + 2;
-        if (C != 0 || mxh <= g.n[0] - 1) {
-          const T adv = adv_at<C, 0, T>(g, vel, i, j, k, mxh);
-          hi = adv * lim4<T>(sR[hy][tx + 1], sR[hy][tx + 2], sR[hy][tx + 3], sR[hy][tx + 4], adv);
-          if (WITHV) hi *= lim4<T>(sQ[hy][tx + 1], sQ[hy][tx + 2], sQ[hy][tx + 3], sQ[hy][tx + 4], adv);
-        }
-        if (tx == 0 && (C != 0 || mxl >= 0)) {
-          const T adv = adv_at<C, 0, T>(g, vel, i, j, k, mxl);
-          lo = adv * lim4<T>(sR[hy][tx], sR[hy][tx + 1], sR[hy][tx + 2], sR[hy][tx + 3], adv);
-          if (WITHV) lo *= lim4<T>(sQ[hy][tx], sQ[hy][tx + 1], sQ[hy][tx + 2], sQ[hy][tx + 3], adv);
-        }
+      const int hy = ty + 2;
+      if (fxh) {
+        hi = axh * lim4<T>(sR[hy][tx + 1], sR[hy][tx + 2], sR[hy][tx + 3], sR[hy][tx + 4], axh);
+        if (WITHV) hi *= lim4<T>(sQ[hy][tx + 1], sQ[hy][tx + 2], sQ[hy][tx + 3], sQ[hy][tx + 4], axh);
+      }
+      if (fxl) {
+        lo = axl * lim4<T>(sR[hy][tx], sR[hy][tx + 1], sR[hy][tx + 2], sR[hy][tx + 3], axl);
+        if (WITHV) lo *= lim4<T>(sQ[hy][tx], sQ[hy][tx + 1], sQ[hy][tx + 2], sQ[hy][tx + 3], axl);
       }
       sFx[ty][tx + 1] = hi;
       if (tx == 0) sFx[ty][0] = lo;
       // y-fluxes
-      const bool oky = (C == 1) || !wall;
       hi = T(0);
       lo = T(0);
-      const int myh = j + oy + 1, myl = j + oy;
-      if (oky) {
-        const int hx = tx + 2;
-        if (C != 1 || myh <= g.n[1] - 1) {
-          const T adv = adv_at<C, 1, T>(g, vel, i, j, k, myh);
-          hi = adv * lim4<T>(sR[ty + 1][hx], sR[ty + 2][hx], sR[ty + 3][hx], sR[ty + 4][hx], adv);
-          if (WITHV) hi *= lim4<T>(sQ[ty + 1][hx], sQ[ty + 2][hx], sQ[ty + 3][hx], sQ[ty + 4][hx], adv);
-        }
-        if (ty == 0 && (C != 1 || myl >= 0)) {
-          const T adv = adv_at<C, 1, T>(g, vel, i, j, k, myl);
-          lo = adv * lim4<T>(sR[ty][hx], sR[ty + 1][hx], sR[ty + 2][hx], sR[ty + 3][hx], adv);
-          if (WITHV) lo *= lim4<T>(sQ[ty][hx], sQ[ty + 1][hx], sQ[ty + 2][hx], sQ[ty + 3][hx], adv);
-        }
+      const int hx = tx + 2;
+      if (fyh) {
+        hi = ayh * lim4<T>(sR[ty + 1][hx], sR[ty + 2][hx], sR[ty + 3][hx], sR[ty + 4][hx], ayh);
+        if (WITHV) hi *= lim4<T>(sQ[ty + 1][hx], sQ[ty + 2][hx], sQ[ty + 3][hx], sQ[ty + 4][hx], ayh);
+      }
+      if (fyl) {
+        lo = ayl * lim4<T>(sR[ty][hx], sR[ty + 1][hx], sR[ty + 2][hx], sR[ty + 3][hx], ayl);
+        if (WITHV) lo *= lim4<T>(sQ[ty][hx], sQ[ty + 1][hx], sQ[ty + 2][hx], sQ[ty + 3][hx], ayl);
       }
       sFy[ty + 1][tx] = hi;
       if (ty == 0) sFy[0][tx] = lo;
@@ -231,13 +232,10 @@ __global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, CVel<T> vel, co
     }
     zload(k + 2, zr[3], zq[3]);
     if (inside) {
-      const bool okz = (C == 2) || !wall;
       T Fz_hi = T(0);
-      const int mzh = k + oz + 1;
-      if (okz && (C != 2 || mzh <= g.n[2] - 1)) {
-        const T adv = adv_at<C, 2, T>(g, vel, i, j, k, mzh);
-        Fz_hi = adv * lim4<T>(zr[0], zr[1], zr[2], zr[3], adv);
-        if (WITHV) Fz_hi *= lim4<T>(zq[0], zq[1], zq[2], zq[3], adv);
+      if (fzh) {
+        Fz_hi = azh * lim4<T>(zr[0], zr[1], zr[2], zr[3], azh);
+        if (WITHV) Fz_hi *= lim4<T>(zq[0], zq[1], zq[2], zq[3], azh);
       }
       const T r = (sFx[ty][tx + 1] - sFx[ty][tx]) * ginv<T>(g, 0) + (sFy[ty + 1][tx] - sFy[ty][tx]) * ginv<T>(g, 1) +
                   (Fz_hi - Fz_lo) * ginv<T>(g, 2);
