@@ -23,7 +23,6 @@
 namespace wsi {
 
 static constexpr int BX = 32, BY = 8;
-static constexpr int ZCHUNK = 32;
 
 // Division-free bounded CUI: with num = qC - qU and den = qD - qU,
 // t = num/den lies in a branch interval iff num*sign(den) lies in den-scaled
@@ -359,64 +358,86 @@ void launch_lincomb_mix(size_t n, double a, const double* x, double b, const flo
 }
 
 // ================================================================ level set
-template <int D, typename T>
-__device__ __forceinline__ T phi_ext(const GridDev& g, const T* __restrict__ a, const int i3[3], int m) {
-  int n = g.n[D];
+// Same staging as k_transport: per z-plane the tile of phi^{n+1/2} with a
+// two-cell halo (Neumann mirror ghosts applied while staging) in shared
+// memory, the z taps in a four-entry register window, the face velocities
+// loaded before the staging barrier.
+template <typename T>
+__device__ __forceinline__ int ls_mirror(int m, int n) {
   int mm = m;
   if (m < 0) mm = -m - 1;
   else if (m >= n) mm = 2 * n - 1 - m;
-  mm = clampi(mm, 0, n - 1);
-  int c3[3] = {i3[0], i3[1], i3[2]};
-  c3[D] = mm;
-  return a[fidx(g, 3, c3[0], c3[1], c3[2])];
-}
-
-// flux u_D phi_lim through the D-face at position `face` (between cells
-// face-1 and face) of the cell column through i3
-template <int D, typename T>
-__device__ __forceinline__ T ls_flux(const GridDev& g, const T* __restrict__ vel_d, const T* __restrict__ phi,
-                                     const int i3[3], int face) {
-  int f3[3] = {i3[0], i3[1], i3[2]};
-  f3[D] = face;
-  T a = vel_d[fidx(g, D, f3[0], f3[1], f3[2])];
-  T lim;
-  if (a > T(0))
-    lim = cui<T>(phi_ext<D, T>(g, phi, i3, face - 2), phi_ext<D, T>(g, phi, i3, face - 1),
-                 phi_ext<D, T>(g, phi, i3, face));
-  else
-    lim = cui<T>(phi_ext<D, T>(g, phi, i3, face + 1), phi_ext<D, T>(g, phi, i3, face),
-                 phi_ext<D, T>(g, phi, i3, face - 1));
-  return a * lim;
+  return clampi(mm, 0, n - 1);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(BX* BY) k_ls_advect(GridDev g, CVel<T> vel,
                                                       const double* __restrict__ phi_n, const T* __restrict__ phi_h,
-                                                      double dt, double* out) {
+                                                      double dt, double* out, int zchunk) {
+  constexpr int HX = BX + 4, HY = BY + 4, NS = (HX * HY + BX * BY - 1) / (BX * BY);
+  __shared__ T sP[HY][HX];
   __shared__ T sFx[BY][BX + 1];
   __shared__ T sFy[BY + 1][BX];
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int i = blockIdx.x * BX + tx, j = blockIdx.y * BY + ty;
-  const bool inside = i < g.n[0] && j < g.n[1];
-  const int k0 = blockIdx.z * ZCHUNK;
-  const int k1 = min(k0 + ZCHUNK, g.n[2]);
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+  const int i = x0 + tx, j = y0 + ty;
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+  const bool inside = i < n0 && j < n1;
+  const int k0 = blockIdx.z * zchunk;
+  const int k1 = min(k0 + zchunk, n2);
+  const size_t plane = (size_t)n0 * n1;
+  int soff[NS];
+#pragma unroll
+  for (int r = 0; r < NS; ++r) {
+    const int t = tid + r * BX * BY;
+    soff[r] = -1;
+    if (t < HX * HY) {
+      const int hy = t / HX, hx = t - hy * HX;
+      soff[r] = ls_mirror<T>(y0 - 2 + hy, n1) * n0 + ls_mirror<T>(x0 - 2 + hx, n0);
+    }
+  }
+  const size_t col = (size_t)min(j, n1 - 1) * n0 + min(i, n0 - 1);
+  T zp[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) zp[q] = phi_h[(size_t)ls_mirror<T>(k0 - 2 + q, n2) * plane + col];
   T Fz_lo = T(0);
   for (int k = k0; k < k1; ++k) {
-    int i3[3] = {i, j, k};
+    T ux = T(0), uxl = T(0), vy = T(0), vyl = T(0), wz = T(0), wzl = T(0);
     if (inside) {
-      sFx[ty][tx + 1] = ls_flux<0, T>(g, vel.q[0], phi_h, i3, i + 1);
-      if (tx == 0) sFx[ty][0] = ls_flux<0, T>(g, vel.q[0], phi_h, i3, i);
-      sFy[ty + 1][tx] = ls_flux<1, T>(g, vel.q[1], phi_h, i3, j + 1);
-      if (ty == 0) sFy[0][tx] = ls_flux<1, T>(g, vel.q[1], phi_h, i3, j);
+      ux = vel.q[0][fidx(g, 0, i + 1, j, k)];
+      if (tx == 0) uxl = vel.q[0][fidx(g, 0, i, j, k)];
+      vy = vel.q[1][fidx(g, 1, i, j + 1, k)];
+      if (ty == 0) vyl = vel.q[1][fidx(g, 1, i, j, k)];
+      wz = vel.q[2][fidx(g, 2, i, j, k + 1)];
+      if (k == k0) wzl = vel.q[2][fidx(g, 2, i, j, k)];
+    }
+#pragma unroll
+    for (int r = 0; r < NS; ++r) {
+      const int t = tid + r * BX * BY;
+      if (soff[r] >= 0) {
+        const int hy = t / HX, hx = t - hy * HX;
+        sP[hy][hx] = phi_h[(size_t)k * plane + soff[r]];
+      }
     }
     __syncthreads();
     if (inside) {
-      T Fz_hi = ls_flux<2, T>(g, vel.q[2], phi_h, i3, k + 1);
-      if (k == k0) Fz_lo = ls_flux<2, T>(g, vel.q[2], phi_h, i3, k);
-      T Q = (sFx[ty][tx + 1] - sFx[ty][tx]) * ginv<T>(g, 0) + (sFy[ty + 1][tx] - sFy[ty][tx]) * ginv<T>(g, 1) +
-            (Fz_hi - Fz_lo) * ginv<T>(g, 2);
-      size_t id = fidx(g, 3, i, j, k);
-      out[id] = phi_n[id] - dt * (double)Q;
+      const int hy = ty + 2, hx = tx + 2;
+      sFx[ty][tx + 1] = ux * lim4<T>(sP[hy][tx + 1], sP[hy][tx + 2], sP[hy][tx + 3], sP[hy][tx + 4], ux);
+      if (tx == 0) sFx[ty][0] = uxl * lim4<T>(sP[hy][tx], sP[hy][tx + 1], sP[hy][tx + 2], sP[hy][tx + 3], uxl);
+      sFy[ty + 1][tx] = vy * lim4<T>(sP[ty + 1][hx], sP[ty + 2][hx], sP[ty + 3][hx], sP[ty + 4][hx], vy);
+      if (ty == 0) sFy[0][tx] = vyl * lim4<T>(sP[ty][hx], sP[ty + 1][hx], sP[ty + 2][hx], sP[ty + 3][hx], vyl);
+    }
+    __syncthreads();
+    if (k == k0) Fz_lo = wzl * lim4<T>(zp[0], zp[1], zp[2], zp[3], wzl);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) zp[q] = zp[q + 1];
+    zp[3] = phi_h[(size_t)ls_mirror<T>(k + 2, n2) * plane + col];
+    if (inside) {
+      const T Fz_hi = wz * lim4<T>(zp[0], zp[1], zp[2], zp[3], wz);
+      const T Q = (sFx[ty][tx + 1] - sFx[ty][tx]) * ginv<T>(g, 0) + (sFy[ty + 1][tx] - sFy[ty][tx]) * ginv<T>(g, 1) +
+                  (Fz_hi - Fz_lo) * ginv<T>(g, 2);
+      const size_t id = (size_t)k * plane + (size_t)j * n0 + i;
+      out[id] = phi_n[id] - dt * cvt<double, T>(Q);
       Fz_lo = Fz_hi;
     }
     __syncthreads();
@@ -427,8 +448,9 @@ template <typename T>
 void launch_levelset_advect(const GridDev& g, const T* const vel[3], const double* phi_n, const T* phi_half, double dt,
                             double* out, cudaStream_t st) {
   CVel<T> v{{vel[0], vel[1], vel[2]}};
-  dim3 grid(cdiv(g.n[0], BX), cdiv(g.n[1], BY), cdiv(g.n[2], ZCHUNK));
-  { k_ls_advect<T><<<grid, dim3(BX, BY), 0, st>>>(g, v, phi_n, phi_half, dt, out); WSI_COUNT(); }
+  const int zc = transport_chunk(g.n[0], g.n[1], g.n[2]);
+  dim3 grid(cdiv(g.n[0], BX), cdiv(g.n[1], BY), cdiv(g.n[2], zc));
+  { k_ls_advect<T><<<grid, dim3(BX, BY), 0, st>>>(g, v, phi_n, phi_half, dt, out, zc); WSI_COUNT(); }
 }
 template void launch_levelset_advect<double>(const GridDev&, const double* const[3], const double*, const double*,
                                              double, double*, cudaStream_t);
