@@ -110,10 +110,30 @@ def sample_clocks_stop(h, path, gpu_index):
             "samples": len(sm)}
 
 
-def build_case(n):
+def build_case(n, workload="tank"):
+    """tank: n^3 sloshing tank with a locked box (rho_s = densest fluid,
+    gravity from rho^flow, Sec. 5).  cylinder: the largest configuration's
+    wave tank, (2n) x n x n cells over 8 x 2 x 2 m, water depth 1 m, a
+    free-floating cylinder (radius 0.15 m, length 1.6 m, rho_s = 500, free in
+    surge, heave and pitch) under a regular wave (H 0.1 m, T 1.2 s) generated
+    over x in [0, 1] and damped over [7, 8]."""
+    if workload == "cylinder":
+        c = inputs.tank_cylinder(nxyz=(2 * n, n, n), lxyz=(8.0, 2.0, 2.0), depth=1.0, radius=0.15, length=1.6,
+                                 dt=2.5e-3)
+        c.extra["waves"] = dict(H=0.1, T=1.2, depth=1.0, x_gen=1.0, x_damp=7.0)
+        return c
     c = inputs.tank3d(n=n, seed=7, dt=5e-4)
     c.rho_s = c.rho_l  # locked body: rho_s = densest fluid, gravity from rho^flow (Sec. 5)
     return c
+
+
+def workload_name(args):
+    if args.workload == "cylinder":
+        return ("cylinder%d: %dx%dx%d wave tank 8x2x2 m, regular wave H 0.1 m T 1.2 s, free-floating cylinder "
+                "(r 0.15 m, L 1.6 m, rho_s 500), 2 Stokes solves per step to rtol %.0e"
+                % (args.n, 2 * args.n, args.n, args.n, args.rtol))
+    return ("tank%d: %d^3 three-phase tank, 8-mode seeded surface, locked box, 2 Stokes solves per step to rtol %.0e"
+            % (args.n, args.n, args.rtol))
 
 
 def max_over_ranks(x, dist, device):
@@ -198,15 +218,23 @@ def learned_comparison(args, stream):
             "speedup_learned_fp32_over_plain_fp64": mean("plain_fp64") / mean("learned_fp32")}
 
 
-def oracle_sample_step(n_sample=12):
-    """One oracle step of the same tank recipe at n_sample^3 (host cores)."""
+def oracle_sample_step(n_sample=12, workload="tank"):
+    """One oracle step of the same recipe at a small size (host cores):
+    n_sample^3 for the tank, (2 n_sample) x n_sample x n_sample for the
+    cylinder tank (without the wave zones)."""
     from oracle.grid import Grid
     from oracle import step as ost
-    c = build_case(n_sample)
+    c = build_case(n_sample, workload)
     g = Grid(c.nx, c.ny, c.nz, c.lx, c.ly, c.lz, c.bc)
-    pr = ost.Props(rho_l=c.rho_l, rho_g=c.rho_g, rho_s=c.rho_s, mu_l=c.mu_l, mu_g=c.mu_g, gravity=c.gravity,
-                   gravity_mode="flow")
-    s = ost.State(g, pr, c.phi, c.psi, ost.Body(c.markers, c.dV, [True] * 6, half=c.box_half))
+    if workload == "cylinder":
+        pr = ost.Props(rho_l=c.rho_l, rho_g=c.rho_g, rho_s=c.rho_s, mu_l=c.mu_l, mu_g=c.mu_g, gravity=c.gravity,
+                       gravity_mode="full")
+        body = ost.Body(c.markers, c.dV, list(c.lock), cylinder=c.extra["cylinder"])
+    else:
+        pr = ost.Props(rho_l=c.rho_l, rho_g=c.rho_g, rho_s=c.rho_s, mu_l=c.mu_l, mu_g=c.mu_g, gravity=c.gravity,
+                       gravity_mode="flow")
+        body = ost.Body(c.markers, c.dV, [True] * 6, half=c.box_half)
+    s = ost.State(g, pr, c.phi, c.psi, body)
     t0 = time.perf_counter()
     ost.step(s, c.dt)
     dt = time.perf_counter() - t0
@@ -220,17 +248,19 @@ def run_reference(args, rank, world):
     times = []
     cells = 0
     for i in range(args.warmup + args.steps):
-        cells, dt = oracle_sample_step(n_sample)
+        cells, dt = oracle_sample_step(n_sample, args.workload)
         if i >= args.warmup:
             times.append(dt)
     T = float(np.sum(times))
     value = cells * len(times) / T
-    sample = "one oracle step (materials, transport, exact sparse-LU Stokes solves, DLM) of the same tank " \
-             "recipe at %d^3 per step; numpy/scipy, single-threaded" % n_sample
+    sample = "one oracle step (materials, transport, exact sparse-LU Stokes solves, DLM) of the same %s " \
+             "recipe at %s per step; numpy/scipy, single-threaded" % (
+                 args.workload, "%d^3" % n_sample if args.workload == "tank" else "%dx%dx%d" % (2 * n_sample, n_sample,
+                                                                                                  n_sample))
     line = {"impl": "reference", "metric": "cell-steps/s", "value": value, "unit": "cell-steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "tank%d" % args.n, "sample": "%d^3" % n_sample},
+            "data": "synthetic", "config": {"workload": workload_name(args), "sample": sample},
             "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -254,6 +284,8 @@ def main():
     ap.add_argument("--visc-sweeps", type=int, default=2, help="viscous red-black sweeps per preconditioner apply")
     ap.add_argument("--mg", default="2,2", help="pressure V-cycle pre,post smoothing sweeps")
     ap.add_argument("--learned-train", type=int, default=1200, help="training samples for the learned comparison")
+    ap.add_argument("--workload", default="tank", choices=["tank", "cylinder"],
+                    help="tank: n^3 sloshing tank (default); cylinder: (2n) x n x n wave tank with a free cylinder")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -277,7 +309,7 @@ def main():
         torch.cuda.synchronize()
 
     stream = torch.cuda.current_stream()
-    c = build_case(args.n)
+    c = build_case(args.n, args.workload)
     cells = c.nx * c.ny * c.nz
     prec = wsi.PREC_MIXED if args.precision == "mixed" else wsi.PREC_FP64
 
@@ -285,7 +317,11 @@ def main():
         pre, post = (int(v) for v in args.mg.split(","))
         ctx = wsi.Context.from_case(c, precision=p, restart=20, stream=stream.cuda_stream, mg_pre=pre, mg_post=post,
                                     visc_sweeps=args.visc_sweeps)
-        ctx.set_case(c, rho_s=c.rho_l)
+        if args.workload == "cylinder":
+            ctx.set_case(c)
+            ctx.set_waves(**c.extra["waves"])
+        else:
+            ctx.set_case(c, rho_s=c.rho_l)
         return ctx
 
     def timed_steps(ctx, k):
@@ -379,23 +415,23 @@ def main():
         ctx64.close()
 
     learned = None
-    if not args.no_learned and rank == 0:
+    if not args.no_learned and rank == 0 and args.workload == "tank":
         learned = learned_comparison(args, stream)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        n_s, t_s = oracle_sample_step(12)
+        n_s, t_s = oracle_sample_step(12 if args.workload == "tank" else 8, args.workload)
         cpu = {"value": n_s / t_s, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
-               "sample": "one oracle time step (exact sparse-LU solves) of the same tank recipe at 12^3; "
-                         "numpy/scipy single-threaded on the GPU host"}
+               "sample": "one oracle time step (exact sparse-LU solves) of the same %s recipe at %s; "
+                         "numpy/scipy single-threaded on the GPU host"
+                         % (args.workload, "12^3" if args.workload == "tank" else "16x8x8 without wave zones")}
     if rank == 0:
         line = {"metric": "cell-steps/s", "value": value, "unit": "cell-steps/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64 outer / f32 preconditioner" if prec == wsi.PREC_MIXED else "f64",
                 "data": "synthetic",
-                "config": {"workload": "tank%d: %d^3 three-phase tank, 8-mode seeded surface, locked box, "
-                                       "2 Stokes solves per step to rtol %.0e" % (args.n, args.n, args.rtol),
+                "config": {"workload": workload_name(args),
                            "cells": cells, "precision": args.precision, "l2": "inputs larger than L2 (no flush)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "mg_pre_post": args.mg, "visc_sweeps": args.visc_sweeps,

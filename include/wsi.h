@@ -86,7 +86,11 @@ typedef struct {
     double dV;           /* marker volume ds1 ds2 ds3                         */
     int lock[6];         /* 1 = prescribed: Ux,Uy,Uz,Wx,Wy,Wz                 */
     double U_pres[3], W_pres[3];
-    int shape;           /* 0: psi not rebuilt; 1: box of half-extents half[] */
+    int shape;           /* psi rebuilt each cycle as the signed distance about
+                            the markers' mean (Sec. 4.1): 0 none (psi kept);
+                            1 box of half-extents half[0..2]; 2 cylinder with
+                            its axis along y, radius half[0], half length
+                            half[1]                                         */
     double half[3];
 } wsi_body_desc;
 

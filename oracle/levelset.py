@@ -50,6 +50,21 @@ def advect(g: Grid, vel, phi_n, phi_half, dt):
     return phi_n - dt * Q
 
 
+def cylinder_sdf(g: Grid, center, radius, half_length):
+    """Signed distance to a solid circular cylinder with its axis along y,
+    capped at |y - y_c| = half_length (Sec. 4.1: psi is the analytic signed
+    distance of the body about its centre of mass).  Outside: the Euclidean
+    distance to the closed cylinder; inside: minus the distance to the
+    nearest of the mantle and the two caps."""
+    x, y, z = g.cell_centers()
+    qr = np.sqrt((x - center[0]) ** 2 + (z - center[2]) ** 2) - radius
+    qy = np.abs(y - center[1]) - half_length
+    qr, qy = np.broadcast_arrays(qr, qy)
+    outside = np.sqrt(np.maximum(qr, 0.0) ** 2 + np.maximum(qy, 0.0) ** 2)
+    inside = np.minimum(np.maximum(qr, qy), 0.0)
+    return outside + inside
+
+
 def box_sdf(g: Grid, center, half):
     x, y, z = g.cell_centers()
     q = [np.abs(x - center[0]) - half[0], np.abs(y - center[1]) - half[1], np.abs(z - center[2]) - half[2]]

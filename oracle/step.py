@@ -37,13 +37,15 @@ class Props:
 
 
 class Body:
-    def __init__(self, X, dV, lock, U_pres=(0, 0, 0), W_pres=(0, 0, 0), half=None):
+    def __init__(self, X, dV, lock, U_pres=(0, 0, 0), W_pres=(0, 0, 0), half=None, cylinder=None):
         self.X = np.array(X, dtype=np.float64)
         self.dV = float(dV)
         self.lock = np.asarray(lock, dtype=bool)
         self.U_pres = np.asarray(U_pres, dtype=np.float64)
         self.W_pres = np.asarray(W_pres, dtype=np.float64)
         self.half = None if half is None else np.asarray(half, dtype=np.float64)
+        # (radius, half length) of a cylinder along y, or None
+        self.cylinder = None if cylinder is None else (float(cylinder[0]), float(cylinder[1]))
         self.Ub = np.zeros_like(self.X)
         self.Xcom = self.X.mean(axis=0)
 
@@ -89,6 +91,8 @@ def step(s: State, dt, n_cycles=2):
         phi_new = levelset.advect(g, u_half, phi_n, 0.5 * (phi_k + phi_n), dt)
         if body is not None and body.half is not None:
             psi_new = levelset.box_sdf(g, X_k.mean(axis=0), body.half)
+        elif body is not None and body.cylinder is not None:
+            psi_new = levelset.cylinder_sdf(g, X_k.mean(axis=0), *body.cylinder)
         else:
             psi_new = psi_k
         mat = _materials(s, phi_new, psi_new)

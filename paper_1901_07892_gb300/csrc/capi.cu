@@ -836,6 +836,7 @@ int wsi_set_phases(wsi_ctx* c, const double* phi, const double* psi, const wsi_p
       B.W_pres[d] = bd.W_pres[d];
       B.half[d] = bd.half[d];
     }
+    if (bd.shape < 0 || bd.shape > 2) return fail(c, WSI_ERR_INVALID_ARG, "unknown body shape");
     B.shape = bd.shape;
     cudaMemcpyAsync(B.X, hx.data(), hx.size() * sizeof(double), cudaMemcpyHostToDevice, c->st);
     cudaMemsetAsync(B.Ub_n, 0, hx.size() * sizeof(double), c->st);
@@ -937,9 +938,12 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
     const bool at_rest = B.lock[0] && B.lock[1] && B.lock[2] && B.lock[3] && B.lock[4] && B.lock[5] &&
                          B.U_pres[0] == 0.0 && B.U_pres[1] == 0.0 && B.U_pres[2] == 0.0 && B.W_pres[0] == 0.0 &&
                          B.W_pres[1] == 0.0 && B.W_pres[2] == 0.0;
-    if (c->has_body && B.shape == 1 && !(at_rest && c->psi_static_done)) {
+    if (c->has_body && (B.shape == 1 || B.shape == 2) && !(at_rest && c->psi_static_done)) {
       launch_marker_mean(B.X, B.n, B.xc, B.scratch, st);
-      launch_box_sdf(g, B.xc, B.half, c->psi_new, st);
+      if (B.shape == 1)
+        launch_box_sdf(g, B.xc, B.half, c->psi_new, st);
+      else
+        launch_cyl_sdf(g, B.xc, B.half[0], B.half[1], c->psi_new, st);
       psi_use = c->psi_new;
       if (at_rest && k + 1 == ncyc) c->psi_static_done = true;
     }

@@ -101,6 +101,8 @@ template <typename T>
 void launch_levelset_advect(const GridDev& g, const T* const vel[3], const double* phi_n, const T* phi_half, double dt,
                             double* out, cudaStream_t st);
 void launch_box_sdf(const GridDev& g, const double* xcom_dev, const double half[3], double* psi, cudaStream_t st);
+void launch_cyl_sdf(const GridDev& g, const double* xcom_dev, double radius, double half_length, double* psi,
+                    cudaStream_t st);
 // part of the momentum right-hand side fixed over the cycles of a step:
 // b0 = rho_n u_n / dt + (1-theta) L_mu^n u_n, the strain term in T from
 // T copies of u_n and mu^n (zero on wall faces)

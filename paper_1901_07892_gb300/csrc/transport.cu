@@ -468,6 +468,23 @@ __global__ void k_box_sdf(GridDev g, const double* __restrict__ xc, double hx_, 
   psi[fidx(g, 3, i, j, k)] = outside + inside;
 }
 
+// capped cylinder with its axis along y (radius r, half length hl) about xc
+__global__ void k_cyl_sdf(GridDev g, const double* __restrict__ xc, double r, double hl, double* psi) {
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.n[0] || j >= g.n[1]) return;
+  double x = (i + 0.5) * g.h[0], y = (j + 0.5) * g.h[1], z = (k + 0.5) * g.h[2];
+  double dx = x - xc[0], dz = z - xc[2];
+  double qr = sqrt(dx * dx + dz * dz) - r, qy = fabs(y - xc[1]) - hl;
+  double or_ = fmax(qr, 0.0), oy = fmax(qy, 0.0);
+  psi[fidx(g, 3, i, j, k)] = sqrt(or_ * or_ + oy * oy) + fmin(fmax(qr, qy), 0.0);
+}
+
+void launch_cyl_sdf(const GridDev& g, const double* xcom_dev, double radius, double half_length, double* psi,
+                    cudaStream_t st) {
+  { k_cyl_sdf<<<dim3(cdiv(g.n[0], BX), cdiv(g.n[1], BY), g.n[2]), dim3(BX, BY), 0, st>>>(g, xcom_dev, radius,
+                                                                                          half_length, psi); WSI_COUNT(); }
+}
+
 void launch_box_sdf(const GridDev& g, const double* xcom_dev, const double half[3], double* psi, cudaStream_t st) {
   { k_box_sdf<<<dim3(cdiv(g.n[0], BX), cdiv(g.n[1], BY), g.n[2]), dim3(BX, BY), 0, st>>>(g, xcom_dev, half[0], half[1],
                                                                                          half[2], psi); WSI_COUNT(); }

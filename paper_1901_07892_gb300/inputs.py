@@ -222,3 +222,42 @@ def smooth_field(rng, shape, modes=6, noise=0.05):
         e += rng.standard_normal() * np.cos(np.pi * k[0] * x) * np.cos(np.pi * k[1] * y) * np.cos(np.pi * k[2] * z)
     e += noise * rng.standard_normal(shape)
     return e - e.mean()
+
+
+def cylinder_distance(xyz, center, radius, half_length):
+    """Signed distance to a capped cylinder with its axis along y (input
+    generator; the library and the oracle compute their own)."""
+    x, y, z = xyz
+    qr = np.sqrt((x - center[0]) ** 2 + (z - center[2]) ** 2) - radius
+    qy = np.abs(y - center[1]) - half_length
+    qr, qy = np.broadcast_arrays(qr, qy)
+    return np.sqrt(np.maximum(qr, 0.0) ** 2 + np.maximum(qy, 0.0) ** 2) + np.minimum(np.maximum(qr, qy), 0.0)
+
+
+def cylinder_lattice(center, radius, half_length, h):
+    """Markers at half-cell spacing filling a cylinder along y: the points of
+    the box lattice around it that lie inside.  Returns (X (N,3), dV)."""
+    X, dV = marker_lattice(center, (radius, half_length, radius), h)
+    r2 = (X[:, 0] - center[0]) ** 2 + (X[:, 2] - center[2]) ** 2
+    return X[r2 <= radius * radius], dV
+
+
+def tank_cylinder(nxyz=(32, 16, 16), lxyz=(2.0, 1.0, 1.0), seed=None, depth=0.5, radius=0.15, length=0.6,
+                  dt=5e-4, rho_s=500.0):
+    """Tank with a free-floating horizontal cylinder along y (config 5's body,
+    scaled): axis at the still-water depth, rho_s = 500, free in surge, heave
+    and pitch (x, z translation, rotation about y), the other DOFs locked."""
+    nx, ny, nz = nxyz
+    c = Case(nx=nx, ny=ny, nz=nz, lx=lxyz[0], ly=lxyz[1], lz=lxyz[2], dt=dt, gravity_mode="full", rho_s=rho_s)
+    x, y, z = c.cell_xyz()
+    if seed is None:
+        c.phi = np.broadcast_to(z - depth, (nz, ny, nx)).copy()
+    else:
+        eta = fourier_surface(np.random.default_rng(seed))
+        c.phi = np.broadcast_to(z - depth - eta(x / lxyz[0], y / lxyz[1]), (nz, ny, nx)).copy()
+    center = (0.5 * lxyz[0], 0.5 * lxyz[1], depth)
+    c.psi = np.broadcast_to(cylinder_distance((x, y, z), center, radius, 0.5 * length), (nz, ny, nx)).copy()
+    c.markers, c.dV = cylinder_lattice(center, radius, 0.5 * length, c.h)
+    c.lock = (False, True, False, True, False, True)
+    c.extra["cylinder"] = (radius, 0.5 * length)
+    return c

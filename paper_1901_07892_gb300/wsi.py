@@ -207,7 +207,8 @@ class Context:
 
     # ---------------------------------------------------------------- set-up
     def set_phases(self, phi, psi, rho_l, rho_g, rho_s, mu_l, mu_g, mu_s, gravity_mode=GRAVITY_FLOW,
-                   markers=None, dV=0.0, lock=(1,) * 6, U_pres=(0, 0, 0), W_pres=(0, 0, 0), box_half=None):
+                   markers=None, dV=0.0, lock=(1,) * 6, U_pres=(0, 0, 0), W_pres=(0, 0, 0), box_half=None,
+                   cylinder=None):
         props = PhaseProps(rho_l, rho_g, rho_s, mu_l, mu_g, mu_s, gravity_mode)
         phi, psi = _flat(phi), _flat(psi)
         nb = 0
@@ -224,6 +225,9 @@ class Context:
             if box_half is not None:
                 body.shape = 1
                 body.half = (ctypes.c_double * 3)(*box_half)
+            elif cylinder is not None:
+                body.shape = 2
+                body.half = (ctypes.c_double * 3)(cylinder[0], cylinder[1], 0.0)
             nb = 1
             self.n_markers = len(markers)
         rc = self.L.wsi_set_phases(self._h, _ptr(phi), _ptr(psi), ctypes.byref(props), ctypes.byref(body), nb)
@@ -236,7 +240,8 @@ class Context:
                         case.mu_l, case.mu_g, case.mu_s, gmode,
                         markers=case.markers if with_body else None, dV=case.dV,
                         lock=[int(b) for b in case.lock],
-                        box_half=case.box_half if with_body else None, **kw)
+                        box_half=case.box_half if with_body else None,
+                        cylinder=case.extra.get("cylinder") if with_body else None, **kw)
 
     # ---------------------------------------------------------------- compute
     def solve(self, rhs, dt, rtol=1e-10, max_iters=200, x0=None):

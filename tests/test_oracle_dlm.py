@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 from oracle.grid import Grid, NO_SLIP, FREE_SLIP
+from oracle import levelset
 from oracle.ib import phi4, interpolate, spread
 from oracle.rigid import rigid_fit, constrain, body_velocity
 from paper_1901_07892_gb300 import inputs
@@ -105,3 +106,32 @@ def test_free_body_keeps_uniform_velocity():
     assert np.allclose(Wr, 0.0, atol=1e-12)
     for c in range(3):
         assert np.abs(new[c] - vel[c]).max() < 1e-13
+
+
+def test_cylinder_sdf_closed_forms():
+    """Signed distance to a capped cylinder along y (radius 0.2, half length
+    0.3, centre (0.5, 0.5, 0.5)): on the axis at the centre -0.2 (the mantle
+    is nearer than the caps); beside the mantle the radial gap; beyond a cap
+    the axial gap; off a rim corner the Euclidean distance to the rim."""
+    from oracle.grid import Grid
+    g = Grid(10, 10, 10, 1.0, 1.0, 1.0, (-1.0,) * 6)
+    c, R, hl = (0.5, 0.5, 0.5), 0.2, 0.3
+    d = levelset.cylinder_sdf(g, c, R, hl)
+    x, y, z = g.cell_centers()
+    X, Y, Z = np.broadcast_arrays(x, y, z)
+
+    def at(px, py, pz):
+        k, j, i = int(pz * 10), int(py * 10), int(px * 10)
+        return d[k, j, i], (X[k, j, i], Y[k, j, i], Z[k, j, i])
+
+    v, (px, py, pz) = at(0.55, 0.55, 0.55)  # near the centre: inside, mantle nearest
+    rr = np.hypot(px - 0.5, pz - 0.5)
+    assert v == pytest.approx(max(rr - R, abs(py - 0.5) - hl))
+    v, (px, py, pz) = at(0.95, 0.55, 0.55)  # beside the mantle
+    assert v == pytest.approx(np.hypot(px - 0.5, pz - 0.5) - R)
+    v, (px, py, pz) = at(0.55, 0.95, 0.55)  # beyond a cap
+    assert v == pytest.approx(abs(py - 0.5) - hl)
+    v, (px, py, pz) = at(0.95, 0.95, 0.95)  # off the rim
+    assert v == pytest.approx(np.hypot(np.hypot(px - 0.5, pz - 0.5) - R, abs(py - 0.5) - hl))
+    # a distance function: |grad d| = 1 away from the medial surfaces
+    assert np.all(np.abs(d) <= np.sqrt(3.0))
