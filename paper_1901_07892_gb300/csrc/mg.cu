@@ -82,9 +82,16 @@ int precond_alloc(Precond<T>& P, const GridDev& g0, std::string& err) {
     L.b = dalloc<T>(P.allocs, nc, err);
     L.res = dalloc<T>(P.allocs, nc, err);
     if (!L.x || !L.b || !L.res) return WSI_ERR_OOM;
+    // Semi-coarsening on anisotropic grids: an axis coarsens only while its
+    // spacing is within 1.5x of the finest active spacing, so a grid with
+    // hx = 2 hy = 2 hz first coarsens y and z and then all three (point
+    // smoothers damp the weakly coupled direction poorly).
+    double hmin = 1e300;
+    for (int a = 0; a < 3; ++a)
+      if (g.n[a] > 1) hmin = std::min(hmin, g.h[a]);
     bool any = false;
     for (int a = 0; a < 3; ++a) {
-      L.r[a] = (g.n[a] % 2 == 0 && g.n[a] >= 4) ? 2 : 1;
+      L.r[a] = (g.n[a] % 2 == 0 && g.n[a] >= 4 && g.h[a] <= 1.5 * hmin) ? 2 : 1;
       any |= L.r[a] == 2;
     }
     if (nc <= 64 || !any) {
