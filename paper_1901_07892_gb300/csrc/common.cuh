@@ -180,17 +180,6 @@ __device__ __forceinline__ double cvt<double, float>(float a) {
   return f2d_fast(a);
 }
 
-// 1/a to ~1 ulp with four float64 operations: a float32 reciprocal refined by
-// two Newton steps r <- r + r (1 - a r) (each squares the relative error);
-// zero, subnormal-range and non-finite a take the float64 division
-__device__ __forceinline__ double rcp_nr(double a) {
-  const float af = d2f_fast(a);
-  if (!(fabsf(af) > 0.0f) || isinf(af)) return 1.0 / a;
-  double r = f2d_fast(1.0f / af);
-  r = fma(r, fma(-a, r, 1.0), r);
-  r = fma(r, fma(-a, r, 1.0), r);
-  return r;
-}
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 

@@ -40,10 +40,6 @@ void launch_materials(const GridDev& g, const PhaseConst& pc, const double* phi,
 // level-set face density only (Sec. 4.2.2: rho^n from phi^n, psi^n on faces)
 void launch_face_density(const GridDev& g, const PhaseConst& pc, const double* phi, const double* psi,
                          double* const rho_face[3], cudaStream_t st);
-void launch_mu_only(const GridDev& g, const PhaseConst& pc, const double* phi, const double* psi,
-                    double* mu_cc, double* const mu_e[3], cudaStream_t st);
-void launch_rho_flow(const GridDev& g, const PhaseConst& pc, const double* phi, double* const rho_flow[3],
-                     cudaStream_t st);
 
 // out = alpha * (rho/dt q - theta L_mu q) + beta_in * (G p)  (any of p, rho may be null)
 template <typename T>
@@ -124,8 +120,6 @@ void launch_mdot(const double* V, size_t ldv, int m, const double* w, size_t n, 
 void launch_maxpy(const double* V, size_t ldv, int m, const double* h, double* w, size_t n, double sign,
                   cudaStream_t st, const double* scale_dev = nullptr);
 void launch_scale(double* x, size_t n, const double* s_dev, bool inverse, cudaStream_t st);
-template <typename Ts, typename Td>
-void launch_cast(const Ts* in, Td* out, size_t n, cudaStream_t st);
 double host_norm2(const double* x, size_t n, double* scratch, cudaStream_t st);
 template <typename T>
 void launch_sum(const T* x, size_t n, double* out_dev, double* scratch, cudaStream_t st);

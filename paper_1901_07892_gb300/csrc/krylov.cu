@@ -125,17 +125,6 @@ void launch_scale(double* x, size_t n, const double* s_dev, bool inverse, cudaSt
   { k_scale<<<RB, RT, 0, st>>>(x, n, s_dev, inverse); WSI_COUNT(); }
 }
 
-template <typename Ts, typename Td>
-__global__ void k_cast(const Ts* __restrict__ a, Td* b, size_t n) {
-  size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) b[i] = cvt<Td, Ts>(a[i]);
-}
-
-template <typename Ts, typename Td>
-void launch_cast(const Ts* in, Td* out, size_t n, cudaStream_t st) {
-  { k_cast<Ts, Td><<<RB, RT, 0, st>>>(in, out, n); WSI_COUNT(); }
-}
-
 template <typename T>
 __global__ void k_sum(const T* __restrict__ x, size_t n, double* part) {
   double acc = 0.0;
@@ -181,8 +170,6 @@ void launch_add_scalar_from(T* x, size_t n, const double* s_dev, double factor, 
   { k_add_scalar<T><<<RB, RT, 0, st>>>(x, n, s_dev, factor); WSI_COUNT(); }
 }
 
-template void launch_cast<double, float>(const double*, float*, size_t, cudaStream_t);
-template void launch_cast<float, double>(const float*, double*, size_t, cudaStream_t);
 template void launch_sum<double>(const double*, size_t, double*, double*, cudaStream_t);
 template void launch_sum<float>(const float*, size_t, double*, double*, cudaStream_t);
 template void launch_add_scalar_from<double>(double*, size_t, const double*, double, cudaStream_t);

@@ -212,24 +212,6 @@ void launch_face_density(const GridDev& g, const PhaseConst& pc, const double* p
                                                                              nullptr); WSI_COUNT(); }
 }
 
-void launch_mu_only(const GridDev& g, const PhaseConst& pc, const double* phi, const double* psi, double* mu_cc,
-                    double* const mu_e[3], cudaStream_t st) {
-  { k_mat_cells<<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, psi, nullptr, mu_cc); WSI_COUNT(); }
-  { k_mat_edges<0><<<grid3(g.n[0] + 1, g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, mu_cc, pc.inv_mu, mu_e[0]); WSI_COUNT(); }
-  { k_mat_edges<1><<<grid3(g.n[0] + 1, g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, pc, mu_cc, pc.inv_mu, mu_e[1]); WSI_COUNT(); }
-  { k_mat_edges<2><<<grid3(g.n[0], g.n[1] + 1, g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, pc, mu_cc, pc.inv_mu, mu_e[2]); WSI_COUNT(); }
-}
-
-void launch_rho_flow(const GridDev& g, const PhaseConst& pc, const double* phi, double* const rho_flow[3],
-                     cudaStream_t st) {
-  { k_mat_faces<0><<<grid3(g.n[0] + 1, g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, nullptr, nullptr, nullptr,
-                                                                             rho_flow[0]); WSI_COUNT(); }
-  { k_mat_faces<1><<<grid3(g.n[0], g.n[1] + 1, g.n[2]), dim3(BX, BY), 0, st>>>(g, pc, phi, nullptr, nullptr, nullptr,
-                                                                             rho_flow[1]); WSI_COUNT(); }
-  { k_mat_faces<2><<<grid3(g.n[0], g.n[1], g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, pc, phi, nullptr, nullptr, nullptr,
-                                                                             rho_flow[2]); WSI_COUNT(); }
-}
-
 // =========================================================== strain-rate operator
 // (L_mu q)_C at the interior C-face (i,j,k):
 //   d/dx_C (2 mu dq_C/dx_C) + sum_{D != C} d/dx_D [ mu_e (dq_C/dx_D + dq_D/dx_C) ]
