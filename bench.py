@@ -117,6 +117,12 @@ def build_case(n, workload="tank"):
     free-floating cylinder (radius 0.15 m, length 1.6 m, rho_s = 500, free in
     surge, heave and pitch) under a regular wave (H 0.1 m, T 1.2 s) generated
     over x in [0, 1] and damped over [7, 8]."""
+    if workload == "wave":
+        # the wave tank: (n) x (n/2) x (n/2) cells over 4 x 1 x 1 m, depth 0.5 m,
+        # second-order Stokes wave H 0.05 m, T 1 s, locked trapezoidal bar
+        c = inputs.wave_tank(nx=n, ny=n // 2, nz=n // 2, dt=0.01)
+        c.extra["waves"] = dict(c.extra["wave"])
+        return c
     if workload == "cylinder":
         c = inputs.tank_cylinder(nxyz=(2 * n, n, n), lxyz=(8.0, 2.0, 2.0), depth=1.0, radius=0.15, length=1.6,
                                  dt=2.5e-3)
@@ -128,6 +134,9 @@ def build_case(n, workload="tank"):
 
 
 def workload_name(args):
+    if args.workload == "wave":
+        return ("wave%d: %dx%dx%d wave tank 4x1x1 m, second-order Stokes wave H 0.05 m T 1 s, locked trapezoidal "
+                "bar, 2 Stokes solves per step to rtol %.0e" % (args.n, args.n, args.n // 2, args.n // 2, args.rtol))
     if args.workload == "cylinder":
         return ("cylinder%d: %dx%dx%d wave tank 8x2x2 m, regular wave H 0.1 m T 1.2 s, free-floating cylinder "
                 "(r 0.15 m, L 1.6 m, rho_s 500), 2 Stokes solves per step to rtol %.0e"
@@ -221,7 +230,8 @@ def learned_comparison(args, stream):
 def oracle_sample_step(n_sample=12, workload="tank"):
     """One oracle step of the same recipe at a small size (host cores):
     n_sample^3 for the tank, (2 n_sample) x n_sample x n_sample for the
-    cylinder tank (without the wave zones)."""
+    cylinder tank, n_sample x n_sample/2 x n_sample/2 for the wave tank (the
+    last two without the wave zones)."""
     from oracle.grid import Grid
     from oracle import step as ost
     c = build_case(n_sample, workload)
@@ -230,6 +240,10 @@ def oracle_sample_step(n_sample=12, workload="tank"):
         pr = ost.Props(rho_l=c.rho_l, rho_g=c.rho_g, rho_s=c.rho_s, mu_l=c.mu_l, mu_g=c.mu_g, gravity=c.gravity,
                        gravity_mode="full")
         body = ost.Body(c.markers, c.dV, list(c.lock), cylinder=c.extra["cylinder"])
+    elif workload == "wave":
+        pr = ost.Props(rho_l=c.rho_l, rho_g=c.rho_g, rho_s=c.rho_s, mu_l=c.mu_l, mu_g=c.mu_g, gravity=c.gravity,
+                       gravity_mode="flow")
+        body = ost.Body(c.markers, c.dV, [True] * 6)
     else:
         pr = ost.Props(rho_l=c.rho_l, rho_g=c.rho_g, rho_s=c.rho_s, mu_l=c.mu_l, mu_g=c.mu_g, gravity=c.gravity,
                        gravity_mode="flow")
@@ -244,7 +258,7 @@ def oracle_sample_step(n_sample=12, workload="tank"):
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    n_sample = 12
+    n_sample = {"tank": 12, "cylinder": 8, "wave": 16}[args.workload]
     times = []
     cells = 0
     for i in range(args.warmup + args.steps):
@@ -255,8 +269,8 @@ def run_reference(args, rank, world):
     value = cells * len(times) / T
     sample = "one oracle step (materials, transport, exact sparse-LU Stokes solves, DLM) of the same %s " \
              "recipe at %s per step; numpy/scipy, single-threaded" % (
-                 args.workload, "%d^3" % n_sample if args.workload == "tank" else "%dx%dx%d" % (2 * n_sample, n_sample,
-                                                                                                  n_sample))
+                 args.workload, {"tank": "%d^3" % n_sample, "cylinder": "%dx%dx%d" % (2 * n_sample, n_sample, n_sample),
+                                 "wave": "%dx%dx%d" % (n_sample, n_sample // 2, n_sample // 2)}[args.workload])
     line = {"impl": "reference", "metric": "cell-steps/s", "value": value, "unit": "cell-steps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -284,8 +298,9 @@ def main():
     ap.add_argument("--visc-sweeps", type=int, default=2, help="viscous red-black sweeps per preconditioner apply")
     ap.add_argument("--mg", default="2,2", help="pressure V-cycle pre,post smoothing sweeps")
     ap.add_argument("--learned-train", type=int, default=1200, help="training samples for the learned comparison")
-    ap.add_argument("--workload", default="tank", choices=["tank", "cylinder"],
-                    help="tank: n^3 sloshing tank (default); cylinder: (2n) x n x n wave tank with a free cylinder")
+    ap.add_argument("--workload", default="tank", choices=["tank", "cylinder", "wave"],
+                    help="tank: n^3 sloshing tank (default); cylinder: (2n) x n x n wave tank with a free cylinder; "
+                         "wave: n x n/2 x n/2 wave tank with a submerged bar")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -317,7 +332,7 @@ def main():
         pre, post = (int(v) for v in args.mg.split(","))
         ctx = wsi.Context.from_case(c, precision=p, restart=20, stream=stream.cuda_stream, mg_pre=pre, mg_post=post,
                                     visc_sweeps=args.visc_sweeps)
-        if args.workload == "cylinder":
+        if args.workload in ("cylinder", "wave"):
             ctx.set_case(c)
             ctx.set_waves(**c.extra["waves"])
         else:
@@ -420,11 +435,12 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        n_s, t_s = oracle_sample_step(12 if args.workload == "tank" else 8, args.workload)
+        n_s, t_s = oracle_sample_step({"tank": 12, "cylinder": 8, "wave": 16}[args.workload], args.workload)
         cpu = {"value": n_s / t_s, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
                "sample": "one oracle time step (exact sparse-LU solves) of the same %s recipe at %s; "
                          "numpy/scipy single-threaded on the GPU host"
-                         % (args.workload, "12^3" if args.workload == "tank" else "16x8x8 without wave zones")}
+                         % (args.workload, {"tank": "12^3", "cylinder": "16x8x8 without wave zones",
+                                            "wave": "16x8x8 without wave zones"}[args.workload])}
     if rank == 0:
         line = {"metric": "cell-steps/s", "value": value, "unit": "cell-steps/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
