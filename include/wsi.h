@@ -26,7 +26,8 @@
  *   been synchronised unless stated otherwise.
  * Errors.  Every int-returning call returns WSI_OK or one of the codes
  *   below, never aborts, and leaves a message in wsi_last_error(ctx).
- *   Device-side bound checks raise a flag read back as WSI_ERR_DEVICE.
+ *   Device-side bound checks raise a flag read back as WSI_ERR_DEVICE (the
+ *   marker update of wsi_step checks that every marker stays in the box).
  */
 #ifndef WSI_H
 #define WSI_H
@@ -164,7 +165,11 @@ int wsi_dlm_constrain(wsi_ctx* ctx, double* vel, wsi_body_state* out);
 /* One full time step of Sec. 4.2 (two fixed-point cycles): level-set
  * advection, psi rebuilt from the markers, materials, SSP-RK3 face density
  * and consistent convection, Stokes solve, rigidity projection and marker
- * update, on library-owned state.  Tolerance and limits from opts. */
+ * update, on library-owned state.  Tolerance and limits from opts.
+ * WSI_ERR_DEVICE when the device bound check of the marker update saw a
+ * marker leave the box by more than half a cell or turn non-finite; the step
+ * is then committed as computed and the flag cleared, so the caller decides
+ * whether to go on. */
 int wsi_step(wsi_ctx* ctx, double dt, const wsi_solve_opts* opts, wsi_step_stats* stats);
 
 /* State access for the step.  which: WSI_F_VEL (velocity vector u^n;

@@ -66,6 +66,7 @@ struct Body {
   double *X = nullptr, *Xn = nullptr, *Xh = nullptr, *Ub = nullptr, *Ub_n = nullptr, *U = nullptr, *F = nullptr;
   double* xc = nullptr;       // 3 doubles: centre of mass used for R
   double* rig = nullptr;      // 6 doubles: U_r, W_r
+  int* flag = nullptr;        // device bound check of the marker update
   double* sums = nullptr;     // 15 doubles
   double* scratch = nullptr;  // reduction partials
   double U_r[3] = {0, 0, 0}, W_r[3] = {0, 0, 0}, X_com[3] = {0, 0, 0};
@@ -824,6 +825,7 @@ int wsi_set_phases(wsi_ctx* c, const double* phi, const double* psi, const wsi_p
       B.F = dalloc(c, n3);
       B.xc = dalloc(c, 4);
       B.rig = dalloc(c, 8);
+      B.flag = (int*)dalloc(c, 1);
       B.sums = dalloc(c, 16);
       B.scratch = dalloc(c, 152 * 16 + 32);
       if (!B.X || !B.scratch) return fail(c, WSI_ERR_OOM, "out of device memory for markers");
@@ -978,7 +980,7 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
       launch_lincomb((size_t)B.n * 3, 0.5, B.X, 0.5, B.Xn, 0.0, nullptr, B.Xh, st);
       rc = dlm_project(c, c->vel_k, B.Xh);
       if (rc) return rc;
-      launch_marker_update(B.Xn, B.Ub, B.Ub_n, B.n, dt, B.X, st);
+      launch_marker_update(g, B.Xn, B.Ub, B.Ub_n, B.n, dt, B.X, B.flag, st);
     }
     cudaMemcpyAsync(c->phi_k, c->phi_new, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
     cudaMemcpyAsync(c->psi_k, psi_use, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
@@ -997,8 +999,15 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
   cudaMemcpyAsync(c->phi, c->phi_k, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(c->psi, c->psi_k, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
   if (c->has_body) cudaMemcpyAsync(B.Ub_n, B.Ub, (size_t)B.n * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  int hflag = 0;
+  if (c->has_body && B.flag) cudaMemcpyAsync(&hflag, B.flag, sizeof(int), cudaMemcpyDeviceToHost, st);
   int rc = cuda_check(c, "step");
   if (rc) return rc;
+  if (hflag) {
+    cudaMemsetAsync(B.flag, 0, sizeof(int), st);
+    cudaStreamSynchronize(st);
+    return fail(c, WSI_ERR_DEVICE, "a marker left the box or is not finite (device bound check of the marker update)");
+  }
   // the last cycle's viscosity is mu(phi^{n+1}) unless the zones relaxed phi
   c->mat_n_valid = !c->has_waves;
   if (s) {

@@ -272,17 +272,24 @@ void launch_body_velocity(const double* X, const double* U, int n, const double*
   { k_body_vel<<<cdiv(n, 128), 128, 0, st>>>(X, U, n, rigid_dev, xc_dev, Ub, F); WSI_COUNT(); }
 }
 
-__global__ void k_marker_update(const double* __restrict__ Xn, const double* __restrict__ Ub1,
-                                const double* __restrict__ Ub0, int n3, double dt, double* X) {
+// X = X^n + dt (U_b^{n+1} + U_b^n) / 2 (Sec. 4.2.5).  Device bound check: a
+// position that is not finite or lies outside the box by more than half a
+// cell sets *flag (the step then reports WSI_ERR_DEVICE); nothing traps.
+__global__ void k_marker_update(GridDev g, const double* __restrict__ Xn, const double* __restrict__ Ub1,
+                                const double* __restrict__ Ub0, int n3, double dt, double* X, int* flag) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n3) return;
-  X[t] = Xn[t] + dt * 0.5 * (Ub1[t] + Ub0[t]);
+  const double v = Xn[t] + dt * 0.5 * (Ub1[t] + Ub0[t]);
+  X[t] = v;
+  const int d = t % 3;
+  const double tol = 0.5 * g.h[d];
+  if (flag && !(v >= -tol && v <= g.n[d] * g.h[d] + tol)) atomicOr(flag, 1);
 }
 
-void launch_marker_update(const double* Xn, const double* Ub_new, const double* Ub_old, int n, double dt, double* X,
-                          cudaStream_t st) {
+void launch_marker_update(const GridDev& g, const double* Xn, const double* Ub_new, const double* Ub_old, int n,
+                          double dt, double* X, int* flag, cudaStream_t st) {
   if (n <= 0) return;
-  { k_marker_update<<<cdiv(3LL * n, 256), 256, 0, st>>>(Xn, Ub_new, Ub_old, 3 * n, dt, X); WSI_COUNT(); }
+  { k_marker_update<<<cdiv(3LL * n, 256), 256, 0, st>>>(g, Xn, Ub_new, Ub_old, 3 * n, dt, X, flag); WSI_COUNT(); }
 }
 
 }  // namespace wsi

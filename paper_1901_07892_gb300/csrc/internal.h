@@ -270,7 +270,9 @@ void launch_marker_mean(const double* X, int n, double* xc_dev, double* scratch,
 // F = U_r + W_r x (X - xc) - U   (body velocity minus interpolated); Ub also stored
 void launch_body_velocity(const double* X, const double* U, int n, const double* rigid_dev, const double* xc_dev,
                           double* Ub, double* F, cudaStream_t st);
-void launch_marker_update(const double* Xn, const double* Ub_new, const double* Ub_old, int n, double dt, double* X,
-                          cudaStream_t st);
+// X = X^n + dt (U_b^{n+1} + U_b^n) / 2; *flag |= 1 when a marker leaves the box
+// (by more than half a cell) or is not finite (flag may be null)
+void launch_marker_update(const GridDev& g, const double* Xn, const double* Ub_new, const double* Ub_old, int n,
+                          double dt, double* X, int* flag, cudaStream_t st);
 
 }  // namespace wsi
