@@ -37,7 +37,7 @@ FP64_PEAK_DERIVED_GFLOPS = 152 * 2 * 2 * 2.07
 # scaled by the cells of the workload
 TRAFFIC_PER_CELL = {("stokes", "mixed"): 234.08e6 / 128 ** 3}
 KCLASS = {"stokes": 0, "rbgs_p": 1, "rbgs_v": 2, "transport": 3, "mdot": 4, "maxpy": 5, "restrict": 6,
-          "prolong": 7}
+          "prolong": 7, "reinit": 8}
 
 
 def kernel_model(name, nx, ny, nz, prec_bytes):
@@ -64,6 +64,10 @@ def kernel_model(name, nx, ny, nz, prec_bytes):
     if name == "transport":
         byts = 8 * (F + F + F)
         return byts, 300 * F, "alu"
+    if name == "reinit":
+        # first stage: read phi and phi~, write phi*; second stage: also read
+        # phi^m; the average of the two per launch
+        return prec_bytes * 7 * N // 2, 90 * N, "hbm"
     raise ValueError(name)
 
 
@@ -134,6 +138,11 @@ def build_case(n, workload="tank"):
 
 
 def workload_name(args):
+    name = _base_workload_name(args)
+    return name + (", phi reinitialised (%d pseudo-time steps)" % args.reinit if args.reinit else "")
+
+
+def _base_workload_name(args):
     if args.workload == "wave":
         return ("wave%d: %dx%dx%d wave tank 4x1x1 m, second-order Stokes wave H 0.05 m T 1 s, locked trapezoidal "
                 "bar, 2 Stokes solves per step to rtol %.0e" % (args.n, args.n, args.n // 2, args.n // 2, args.rtol))
@@ -227,7 +236,7 @@ def learned_comparison(args, stream):
             "speedup_learned_fp32_over_plain_fp64": mean("plain_fp64") / mean("learned_fp32")}
 
 
-def oracle_sample_step(n_sample=12, workload="tank"):
+def oracle_sample_step(n_sample=12, workload="tank", reinit_iters=0):
     """One oracle step of the same recipe at a small size (host cores):
     n_sample^3 for the tank, (2 n_sample) x n_sample x n_sample for the
     cylinder tank, n_sample x n_sample/2 x n_sample/2 for the wave tank (the
@@ -250,7 +259,7 @@ def oracle_sample_step(n_sample=12, workload="tank"):
         body = ost.Body(c.markers, c.dV, [True] * 6, half=c.box_half)
     s = ost.State(g, pr, c.phi, c.psi, body)
     t0 = time.perf_counter()
-    ost.step(s, c.dt)
+    ost.step(s, c.dt, reinit_iters=reinit_iters)
     dt = time.perf_counter() - t0
     return g.n_cells, dt
 
@@ -262,7 +271,7 @@ def run_reference(args, rank, world):
     times = []
     cells = 0
     for i in range(args.warmup + args.steps):
-        cells, dt = oracle_sample_step(n_sample, args.workload)
+        cells, dt = oracle_sample_step(n_sample, args.workload, args.reinit)
         if i >= args.warmup:
             times.append(dt)
     T = float(np.sum(times))
@@ -296,6 +305,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned pressure-solve comparison")
     ap.add_argument("--visc-sweeps", type=int, default=2, help="viscous red-black sweeps per preconditioner apply")
+    ap.add_argument("--reinit", type=int, default=0,
+                    help="pseudo-time steps of the level-set reinitialisation at the end of every step")
     ap.add_argument("--mg", default="2,2", help="pressure V-cycle pre,post smoothing sweeps")
     ap.add_argument("--learned-train", type=int, default=1200, help="training samples for the learned comparison")
     ap.add_argument("--workload", default="tank", choices=["tank", "cylinder", "wave"],
@@ -331,7 +342,7 @@ def main():
     def make_ctx(p):
         pre, post = (int(v) for v in args.mg.split(","))
         ctx = wsi.Context.from_case(c, precision=p, restart=20, stream=stream.cuda_stream, mg_pre=pre, mg_post=post,
-                                    visc_sweeps=args.visc_sweeps)
+                                    visc_sweeps=args.visc_sweeps, reinit_iters=args.reinit)
         if args.workload in ("cylinder", "wave"):
             ctx.set_case(c)
             ctx.set_waves(**c.extra["waves"])
@@ -435,7 +446,8 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        n_s, t_s = oracle_sample_step({"tank": 12, "cylinder": 8, "wave": 16}[args.workload], args.workload)
+        n_s, t_s = oracle_sample_step({"tank": 12, "cylinder": 8, "wave": 16}[args.workload], args.workload,
+                                      args.reinit)
         cpu = {"value": n_s / t_s, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
                "sample": "one oracle time step (exact sparse-LU solves) of the same %s recipe at %s; "
                          "numpy/scipy single-threaded on the GPU host"
@@ -451,7 +463,7 @@ def main():
                            "cells": cells, "precision": args.precision, "l2": "inputs larger than L2 (no flush)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "mg_pre_post": args.mg, "visc_sweeps": args.visc_sweeps,
-                           "fgmres_iters": its},
+                           "fgmres_iters": its, "reinit_iters": args.reinit},
                 "gpu_launches": int(l1 - l0), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks, "compare": compare, "learned": learned}
         print(json.dumps(line), flush=True)

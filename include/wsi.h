@@ -73,6 +73,9 @@ typedef struct {
     int restart;         /* FGMRES restart length m                           */
     int visc_mg;         /* viscous V-cycles per application; 0: visc_sweeps
                             sweeps on the fine grid only                      */
+    int reinit_iters;    /* pseudo-time steps of the level-set
+                            reinitialisation at the end of every wsi_step
+                            (Sec. 4.1); 0: phi is not reinitialised          */
 } wsi_grid_desc;
 
 typedef struct {
@@ -231,6 +234,20 @@ int wsi_transport(wsi_ctx* ctx, const double* u_n, const double* u_nm1, const do
 /* Level-set advection of Sec. 4.2.1: phi_out = phi_n - dt div(u phi_lim(phi_half)). */
 int wsi_advect_levelset(wsi_ctx* ctx, const double* vel, const double* phi_n,
                         const double* phi_half, double dt, double* phi_out);
+
+/* Reinitialisation of the flow level set (Sec. 4.1): iters steps of the
+ * eikonal equation  d phi/d tau + sgn(phi~)(|grad phi| - 1) = 0  from
+ * phi~ = phi, with second-order ENO one-sided differences, the subcell fix
+ * of Min (2010) where phi~ changes sign between neighbours (the interface at
+ * the zero of the quadratic through phi~, phi = 0 there), the Godunov
+ * Hamiltonian of sgn(phi~), two-stage TVD Runge-Kutta with the local step
+ * 0.3 min(h, subcell distances), and Neumann mirror ghosts.  sgn(phi~) and
+ * the subcell distances stay fixed (immobile interface).  phi: cells
+ * (Nx Ny Nz doubles, x fastest, host or device), updated in place.
+ * Arithmetic in float64 (WSI_PREC_FP64) or float32 (WSI_PREC_MIXED, the
+ * change then added to the float64 input).  WSI_ERR_INVALID_ARG for a null
+ * phi or iters < 0; iters = 0 leaves phi unchanged. */
+int wsi_reinit(wsi_ctx* ctx, double* phi, int iters);
 
 /* IB4 transfers of Sec. 3.3 with the wall-adjoint forms of Sec. 3.3.2.
  * X: n x 3 positions.  interp: velocity vector -> U (n x 3).

@@ -14,10 +14,12 @@ For cycles k = 0 .. n_cycles-1 (the paper uses n_cycles = 2):
   3. rigidity projection at X^{n+1/2,k} and the position update.
 At k = 0: u^{n+1,0} = u^n, X^{n+1,0} = X^n.  At n = 0: u^{-1} = u^0.
 With wave zones, u^{n+1} and phi^{n+1} are relaxed at t^{n+1} (Sec. 7.1).
+With reinit_iters > 0, phi^{n+1} is then reinitialised to a signed distance
+(Sec. 4.1; reinit.py) before the step is committed.
 """
 import numpy as np
 
-from . import levelset, rigid, transport
+from . import levelset, reinit, rigid, transport
 from .grid import Grid
 from .materials import Materials, face_average, flow_only
 from .operators import strain_rate_apply
@@ -69,7 +71,7 @@ def _materials(s: State, phi, psi):
     return Materials(s.g, phi, psi, pr.rho_l, pr.rho_g, pr.rho_s, pr.mu_l, pr.mu_g, pr.mu_s, pr.n_cells)
 
 
-def step(s: State, dt, n_cycles=2):
+def step(s: State, dt, n_cycles=2, reinit_iters=0):
     g, pr = s.g, s.props
     u_n = [a.copy() for a in s.vel]
     u_nm1 = [a.copy() for a in s.vel_old]
@@ -122,6 +124,8 @@ def step(s: State, dt, n_cycles=2):
         info.setdefault("u_tilde", []).append(vel_t)
     if s.zones is not None:
         u_k, phi_k = s.zones.relax(g, u_k, phi_k, s.time + dt, pr.n_cells)
+    if reinit_iters > 0:
+        phi_k = reinit.reinit(g, phi_k, reinit_iters)
     s.time += dt
     s.vel_old = u_n
     s.vel = u_k

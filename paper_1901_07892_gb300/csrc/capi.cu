@@ -115,6 +115,7 @@ struct wsi_ctx {
   bool psi_static_done = false;
   // mu_cc / mu_e hold mu(phi^n, psi^n) (true right after a step)
   bool mat_n_valid = false;
+  double* ri_scratch = nullptr;  // reinitialisation: 3 x ncell doubles, on first use
   // learned coarse correction of the float32 pressure multigrid
   wsi_unet* unet = nullptr;
   UNetImpl* unet_impl = nullptr;
@@ -635,6 +636,22 @@ int valid_ctx(wsi_ctx* c) { return c ? WSI_OK : WSI_ERR_INVALID_ARG; }
 
 }  // namespace
 
+// pseudo-time CFL number of the reinitialisation (local step cfl * h_min)
+constexpr double kReinitCfl = 0.3;
+
+int reinit_phi(wsi_ctx* c, double* phi, int iters) {
+  if (iters <= 0) return WSI_OK;
+  if (!c->ri_scratch) {
+    c->ri_scratch = dalloc(c, 3 * c->ncell);
+    if (!c->ri_scratch) return fail(c, WSI_ERR_OOM, "reinitialisation scratch");
+  }
+  if (c->mixed())
+    reinit_levelset<float>(c->g, phi, iters, kReinitCfl, c->ri_scratch, c->st);
+  else
+    reinit_levelset<double>(c->g, phi, iters, kReinitCfl, c->ri_scratch, c->st);
+  return WSI_OK;
+}
+
 extern "C" {
 
 long long wsi_launch_count(void) { return g_launches.load(); }
@@ -673,6 +690,7 @@ int wsi_create_grid(const wsi_grid_desc* d, void* stream, wsi_ctx** out) {
     if (d->bc[i] != WSI_NO_SLIP && d->bc[i] != WSI_FREE_SLIP) return WSI_ERR_INVALID_ARG;
   if (d->nz == 1 && (d->bc[4] != WSI_FREE_SLIP || d->bc[5] != WSI_FREE_SLIP)) return WSI_ERR_INVALID_ARG;
   if (d->precision != WSI_PREC_FP64 && d->precision != WSI_PREC_MIXED) return WSI_ERR_INVALID_ARG;
+  if (d->reinit_iters < 0) return WSI_ERR_INVALID_ARG;
   if ((double)(d->nx + 1) * (d->ny + 1) * (d->nz + 1) >= 2147483648.0) return WSI_ERR_INVALID_ARG;
   wsi_ctx* c = new wsi_ctx();
   c->desc = *d;
@@ -991,6 +1009,11 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
     parts(c, c->vel_k, vq);
     launch_wave_relax(g, c->wave, c->time + dt, vq, c->phi_k, st);
   }
+  // phi^{n+1} brought back to a signed distance (Sec. 4.1)
+  if (c->desc.reinit_iters > 0) {
+    int rr = reinit_phi(c, c->phi_k, c->desc.reinit_iters);
+    if (rr) return rr;
+  }
   c->time += dt;
   // commit the step
   cudaMemcpyAsync(c->vel_old, c->vel, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
@@ -1009,7 +1032,7 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
     return fail(c, WSI_ERR_DEVICE, "a marker left the box or is not finite (device bound check of the marker update)");
   }
   // the last cycle's viscosity is mu(phi^{n+1}) unless the zones relaxed phi
-  c->mat_n_valid = !c->has_waves;
+  c->mat_n_valid = !c->has_waves && c->desc.reinit_iters == 0;
   if (s) {
     s->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     s->umax = 0.0;
@@ -1215,6 +1238,15 @@ int wsi_advect_levelset(wsi_ctx* c, const double* vel, const double* phi_n, cons
   rc = copy_out(c, phi_out, c->phi_new, c->ncell);
   if (rc) return rc;
   return cuda_check(c, "advect_levelset");
+}
+
+int wsi_reinit(wsi_ctx* c, double* phi, int iters) {
+  if (valid_ctx(c) || !phi || iters < 0) return WSI_ERR_INVALID_ARG;
+  int rc = copy_in(c, c->phi_new, phi, c->ncell);
+  if (!rc) rc = reinit_phi(c, c->phi_new, iters);
+  if (!rc) rc = copy_out(c, phi, c->phi_new, c->ncell);
+  if (rc) return rc;
+  return cuda_check(c, "reinit");
 }
 
 int wsi_interp(wsi_ctx* c, const double* vel, const double* X, int n, double* U) {

@@ -29,7 +29,8 @@ enum KernelClass {
   KC_MAXPY = 5,      // Gram-Schmidt multi-axpy
   KC_RESTRICT = 6,   // residual + restriction
   KC_PROLONG = 7,    // prolongation + correction
-  KC_COUNT = 8
+  KC_REINIT = 8,     // level-set reinitialisation stage
+  KC_COUNT = 9
 };
 void ktimer_begin(int id, cudaStream_t st);
 void ktimer_end(int id, cudaStream_t st);

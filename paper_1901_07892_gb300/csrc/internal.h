@@ -93,6 +93,17 @@ void launch_lincomb_f32(size_t n, float a, const float* x, float b, const float*
                         float* out, cudaStream_t st);
 void launch_lincomb_mix(size_t n, double a, const double* x, double b, const float* y, double c, const float* z,
                         double* out, cudaStream_t st);
+// z-chunk of the plane-marching stencil kernels for an ex x ey x ez box of
+// points (32 x 8 tiles): long marches, yet about 8 blocks per SM
+int transport_chunk(int ex, int ey, int ez);
+
+// ---------------------------------------------------------------- reinit.cu
+// iters pseudo-time steps of the level-set reinitialisation (Sec. 4.1) on
+// the device level set phi (cells, in place), arithmetic in T; scratch holds
+// 3 cells x ncell doubles
+template <typename T>
+void reinit_levelset(const GridDev& g, double* phi, int iters, double cfl, void* scratch, cudaStream_t st);
+
 template <typename T>
 void launch_levelset_advect(const GridDev& g, const T* const vel[3], const double* phi_n, const T* phi_half, double dt,
                             double* out, cudaStream_t st);

@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, CVel<T> vel, co
 
 // z-chunk of the transport kernels: long marches amortise the chunk start,
 // but the grid must still fill the GPU (about 8 blocks per SM)
-static int transport_chunk(int ex, int ey, int ez) {
+int transport_chunk(int ex, int ey, int ez) {
   const long long base = (long long)cdiv(ex, BX) * cdiv(ey, BY);
   int c = 32;
   while (c > 4 && base * cdiv(ez, c) < 152LL * 8) c /= 2;

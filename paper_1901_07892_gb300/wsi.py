@@ -30,8 +30,8 @@ EXPORTED = ["wsi_stokes_size", "wsi_velocity_size", "wsi_create_grid", "wsi_dest
             "wsi_unet_set_params", "wsi_unet_get_params", "wsi_unet_get_grads", "wsi_unet_forward",
             "wsi_unet_backward", "wsi_unet_adam", "wsi_attach_unet", "wsi_unet_train_sample",
             "wsi_pressure_solve", "wsi_checkpoint", "wsi_restore", "wsi_unet_save", "wsi_unet_load",
-            "wsi_norm2_noalloc"]
-KC_STOKES, KC_RBGS_P, KC_RBGS_V, KC_TRANSPORT, KC_MDOT, KC_MAXPY, KC_RESTRICT, KC_PROLONG = range(8)
+            "wsi_norm2_noalloc", "wsi_reinit"]
+KC_STOKES, KC_RBGS_P, KC_RBGS_V, KC_TRANSPORT, KC_MDOT, KC_MAXPY, KC_RESTRICT, KC_PROLONG, KC_REINIT = range(9)
 
 
 class GridDesc(ctypes.Structure):
@@ -41,7 +41,7 @@ class GridDesc(ctypes.Structure):
                 ("n_cells", ctypes.c_double), ("theta", ctypes.c_double),
                 ("precision", ctypes.c_int), ("mg_pre", ctypes.c_int), ("mg_post", ctypes.c_int),
                 ("mg_cycles", ctypes.c_int), ("visc_sweeps", ctypes.c_int), ("restart", ctypes.c_int),
-                ("visc_mg", ctypes.c_int)]
+                ("visc_mg", ctypes.c_int), ("reinit_iters", ctypes.c_int)]
 
 
 class PhaseProps(ctypes.Structure):
@@ -118,6 +118,7 @@ def lib():
     L.wsi_apply.argtypes = [vp, ip, vp, vp, dp]
     L.wsi_transport.argtypes = [vp, vp, vp, vp, ip, dp, vp, vp]
     L.wsi_advect_levelset.argtypes = [vp, vp, vp, vp, dp, vp]
+    L.wsi_reinit.argtypes = [vp, vp, ip]
     L.wsi_interp.argtypes = [vp, vp, vp, ip, vp]
     L.wsi_spread.argtypes = [vp, vp, vp, ip, dp, vp]
     L.wsi_set_waves.argtypes = [vp, ctypes.POINTER(WaveDesc)]
@@ -167,10 +168,11 @@ class Context:
 
     def __init__(self, nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, bc=(-1.0,) * 6, gravity=(0.0, 0.0, -9.81),
                  n_cells=2.0, theta=0.5, precision=PREC_FP64, mg_pre=2, mg_post=2, mg_cycles=1,
-                 visc_sweeps=2, restart=20, stream=None, visc_mg=0):
+                 visc_sweeps=2, restart=20, stream=None, visc_mg=0, reinit_iters=0):
         L = lib()
         d = GridDesc(nx, ny, nz, lx, ly, lz, (ctypes.c_double * 6)(*bc), (ctypes.c_double * 3)(*gravity),
-                     n_cells, theta, precision, mg_pre, mg_post, mg_cycles, visc_sweeps, restart, visc_mg)
+                     n_cells, theta, precision, mg_pre, mg_post, mg_cycles, visc_sweeps, restart, visc_mg,
+                     reinit_iters)
         h = ctypes.c_void_p()
         st = ctypes.c_void_p(stream) if stream is not None else None
         rc = L.wsi_create_grid(ctypes.byref(d), st, ctypes.byref(h))
@@ -308,6 +310,14 @@ class Context:
         vel, phi_n, phi_half = _flat(vel), _flat(phi_n), _flat(phi_half)
         out = _empty_like_kind(phi_n, self.ncell)
         self._check(self.L.wsi_advect_levelset(self._h, _ptr(vel), _ptr(phi_n), _ptr(phi_half), dt, _ptr(out)))
+        return out
+
+    def reinit(self, phi, iters):
+        """Level-set reinitialisation (Sec. 4.1); returns the new level set
+        (a copy: the argument is left unchanged)."""
+        out = _flat(phi)
+        out = out.clone() if _is_torch(out) else out.copy()
+        self._check(self.L.wsi_reinit(self._h, _ptr(out), int(iters)))
         return out
 
     def checkpoint(self, path):
