@@ -83,16 +83,65 @@ __device__ __forceinline__ double widen<double>(double v) { return v; }
 template <>
 __device__ __forceinline__ double widen<float>(float v) { return f2d_fast(v); }
 
+// Per-cell code of phi~, computed once per call (phi~ is fixed): bits 0-1
+// the sign (0 zero, 1 positive, 2 negative); bit 2 + 2d (3 + 2d) set when
+// phi~ changes sign towards the lower (upper) neighbour along axis d.  A
+// mirror ghost equals its cell, so no crossing is flagged across a wall.
+template <typename T>
+__global__ void k_reinit_code(GridDev g, const T* __restrict__ q0, unsigned char* __restrict__ code) {
+  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
+  const size_t plane = (size_t)n0 * n1, n = plane * n2;
+  for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < n; id += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(id / plane);
+    const size_t r = id - (size_t)k * plane;
+    const int j = (int)(r / n0), i = (int)(r - (size_t)j * n0);
+    const T q = q0[id];
+    unsigned c = q > T(0) ? 1u : (q < T(0) ? 2u : 0u);
+    const int cc[3] = {i, j, k}, nn[3] = {n0, n1, n2};
+    const size_t sd[3] = {1, (size_t)n0, plane};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (cc[d] > 0 && q * q0[id - sd[d]] < T(0)) c |= 4u << (2 * d);
+      if (cc[d] + 1 < nn[d] && q * q0[id + sd[d]] < T(0)) c |= 8u << (2 * d);
+    }
+    code[id] = (unsigned char)c;
+  }
+}
+
+// subcell distances of one axis (rare path: the cell is next to the
+// interface along this axis); taps of phi~ from global memory
+template <typename T>
+__device__ __forceinline__ void subcell_axis(const T* __restrict__ q0, size_t id, int c, int n, size_t stride,
+                                             unsigned bits, const T p[5], T h, T ih, T mp, T mm, T& Dm, T& Dp,
+                                             T& hloc) {
+  T q[5];
+#pragma unroll
+  for (int m = 0; m < 5; ++m) q[m] = q0[id + (ptrdiff_t)(mirror_cell(c - 2 + m, n) - c) * (ptrdiff_t)stride];
+  const T qc = q[1] - T(2) * q[2] + q[3];
+  if (bits & 2u) {
+    const T qp = q[2] - T(2) * q[3] + q[4];
+    const T hp = fmin(fmax(h * iface_frac(q[2], q[3], minmod_(qc, qp)), T(1e-10) * h), h);
+    Dp = -p[2] / hp - T(0.5) * hp * mp * ih * ih;
+    hloc = fmin(hloc, hp);
+  }
+  if (bits & 1u) {
+    const T qm = q[0] - T(2) * q[1] + q[2];
+    const T hm = fmin(fmax(h * iface_frac(q[2], q[1], minmod_(qc, qm)), T(1e-10) * h), h);
+    Dm = p[2] / hm + T(0.5) * hm * mm * ih * ih;
+    hloc = fmin(hloc, hm);
+  }
+}
+
 // One stage: v = pin + dtau L(pin);  with pavg:  v = (pavg + v) / 2.
 // Written to pout, or with out64 (float32 path, last stage) as the change
 // v - phi~ added to the float64 level set in out64.
 template <typename T>
-__global__ void __launch_bounds__(RX* RY) k_reinit(GridDev g, ReinitAxes<T> ax, const T* __restrict__ q0,
-                                                   const T* __restrict__ pin, const T* pavg, T* pout, double* out64,
-                                                   int zchunk) {
+__global__ void __launch_bounds__(RX* RY) k_reinit(GridDev g, ReinitAxes<T> ax,
+                                                   const unsigned char* __restrict__ code,
+                                                   const T* __restrict__ q0, const T* __restrict__ pin,
+                                                   const T* pavg, T* pout, double* out64, int zchunk) {
   constexpr int HX = RX + 4, HY = RY + 4, NS = (HX * HY + RX * RY - 1) / (RX * RY);
-  __shared__ T sP[HY][HX];
-  __shared__ T sQ[HY][HX];
+  __shared__ T sP[HY * HX];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * RX + tx;
   const int x0 = blockIdx.x * RX, y0 = blockIdx.y * RY;
   const int i = x0 + tx, j = y0 + ty;
@@ -112,49 +161,38 @@ __global__ void __launch_bounds__(RX* RY) k_reinit(GridDev g, ReinitAxes<T> ax, 
     }
   }
   const size_t col = (size_t)min(j, n1 - 1) * n0 + min(i, n0 - 1);
-  T zp[5], zq[5];
+  T zp[5];
 #pragma unroll
-  for (int m = 0; m < 5; ++m) {
-    const size_t o = (size_t)mirror_cell(k0 - 2 + m, n2) * plane + col;
-    zp[m] = pin[o];
-    zq[m] = q0[o];
-  }
+  for (int m = 0; m < 5; ++m) zp[m] = pin[(size_t)mirror_cell(k0 - 2 + m, n2) * plane + col];
   for (int k = k0; k < k1; ++k) {
+    const size_t id = (size_t)k * plane + col;
+    const unsigned cd = inside ? code[id] : 0u;
 #pragma unroll
-    for (int r = 0; r < NS; ++r) {
-      const int t = tid + r * RX * RY;
-      if (soff[r] >= 0) {
-        const int hy = t / HX, hx = t - hy * HX;
-        sP[hy][hx] = pin[(size_t)k * plane + soff[r]];
-        sQ[hy][hx] = q0[(size_t)k * plane + soff[r]];
-      }
-    }
+    for (int r = 0; r < NS; ++r)
+      if (soff[r] >= 0) sP[tid + r * RX * RY] = pin[(size_t)k * plane + soff[r]];
     __syncthreads();
     if (inside) {
-      const T qc = zq[2];
-      const T s = qc > T(0) ? T(1) : (qc < T(0) ? T(-1) : T(0));
+      const T s = (cd & 3u) == 1u ? T(1) : ((cd & 3u) == 2u ? T(-1) : T(0));
       T g2 = T(0), hmin = T(0);
       bool any = false;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         if (!ax.active[d]) continue;
-        T p[5], q[5];
-        if (d == 2) {
+        T p[5];
 #pragma unroll
-          for (int m = 0; m < 5; ++m) {
-            p[m] = zp[m];
-            q[m] = zq[m];
-          }
-        } else {
-#pragma unroll
-          for (int m = 0; m < 5; ++m) {
-            const int hy = d == 0 ? ty + 2 : ty + m, hx = d == 0 ? tx + m : tx + 2;
-            p[m] = sP[hy][hx];
-            q[m] = sQ[hy][hx];
-          }
+        for (int m = 0; m < 5; ++m)
+          p[m] = d == 2 ? zp[m] : (d == 0 ? sP[(ty + 2) * HX + tx + m] : sP[(ty + m) * HX + tx + 2]);
+        const T pm = p[0] - T(2) * p[1] + p[2], pc = p[1] - T(2) * p[2] + p[3], pp = p[2] - T(2) * p[3] + p[4];
+        const T mp = minmod_(pc, pp), mm = minmod_(pc, pm);
+        T Dp = (p[3] - p[2]) * ax.ih[d] - T(0.5) * mp * ax.ih[d];
+        T Dm = (p[2] - p[1]) * ax.ih[d] + T(0.5) * mm * ax.ih[d];
+        T hloc = ax.h[d];
+        const unsigned bits = (cd >> (2 + 2 * d)) & 3u;
+        if (bits) {
+          const int c = d == 0 ? i : (d == 1 ? j : k);
+          const size_t stride = d == 0 ? 1 : (d == 1 ? (size_t)n0 : plane);
+          subcell_axis(q0, id, c, g.n[d], stride, bits, p, ax.h[d], ax.ih[d], mp, mm, Dm, Dp, hloc);
         }
-        T Dm, Dp, hloc;
-        eno_axis(p, q, ax.h[d], ax.ih[d], Dm, Dp, hloc);
         const T a = s > T(0) ? fmax(Dm, T(0)) : fmin(Dm, T(0));
         const T b = s > T(0) ? fmin(Dp, T(0)) : fmax(Dp, T(0));
         g2 += fmax(a * a, b * b);
@@ -163,20 +201,14 @@ __global__ void __launch_bounds__(RX* RY) k_reinit(GridDev g, ReinitAxes<T> ax, 
       }
       const T dtau = any ? ax.cfl * hmin : T(0);
       T v = zp[2] + dtau * (-s * (sqrt(g2) - T(1)));
-      const size_t id = (size_t)k * plane + (size_t)j * n0 + i;
       if (pavg) v = T(0.5) * pavg[id] + T(0.5) * v;
-      if (out64) out64[id] = out64[id] + widen<T>(v - qc);
+      if (out64) out64[id] = out64[id] + widen<T>(v - q0[id]);
       else pout[id] = v;
     }
     __syncthreads();
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      zp[m] = zp[m + 1];
-      zq[m] = zq[m + 1];
-    }
-    const size_t o = (size_t)mirror_cell(k + 3, n2) * plane + col;
-    zp[4] = pin[o];
-    zq[4] = q0[o];
+    for (int m = 0; m < 4; ++m) zp[m] = zp[m + 1];
+    zp[4] = pin[(size_t)mirror_cell(k + 3, n2) * plane + col];
   }
 }
 
@@ -186,12 +218,12 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, si
 }
 
 template <typename T>
-static void stage(const GridDev& g, const ReinitAxes<T>& ax, const T* q0, const T* pin, const T* pavg, T* pout,
-                  double* out64, cudaStream_t st) {
+static void stage(const GridDev& g, const ReinitAxes<T>& ax, const unsigned char* code, const T* q0, const T* pin,
+                  const T* pavg, T* pout, double* out64, cudaStream_t st) {
   const int zc = transport_chunk(g.n[0], g.n[1], g.n[2]);
   dim3 grid(cdiv(g.n[0], RX), cdiv(g.n[1], RY), cdiv(g.n[2], zc));
   ktimer_begin(KC_REINIT, st);
-  { k_reinit<T><<<grid, dim3(RX, RY), 0, st>>>(g, ax, q0, pin, pavg, pout, out64, zc); WSI_COUNT(); }
+  { k_reinit<T><<<grid, dim3(RX, RY), 0, st>>>(g, ax, code, q0, pin, pavg, pout, out64, zc); WSI_COUNT(); }
   ktimer_end(KC_REINIT, st);
 }
 
@@ -209,26 +241,27 @@ void reinit_levelset(const GridDev& g, double* phi, int iters, double cfl, void*
   T* q0 = (T*)scratch;  // phi~, fixed for the whole iteration
   T* B = q0 + n;        // first-stage result
   T* A = B + n;         // iterate (float32 path; the float64 path iterates in phi)
+  // the per-cell code of phi~ after the three arrays (scratch: 3 n doubles;
+  // the float64 path uses the third array's space, which it does not need)
+  unsigned char* code = sizeof(T) == sizeof(double) ? (unsigned char*)A : (unsigned char*)(A + n);
+  const int blocks = std::max((int)std::min<size_t>((n + 255) / 256, 152 * 16), 1);
   if constexpr (sizeof(T) == sizeof(double)) {
     cudaMemcpyAsync(q0, phi, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
-    const T* cur = q0;
-    for (int m = 0; m < iters; ++m) {
-      stage<T>(g, ax, q0, cur, nullptr, B, nullptr, st);
-      stage<T>(g, ax, q0, B, cur, (T*)phi, nullptr, st);
-      cur = (const T*)phi;
-    }
   } else {
-    const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
-    { k_to_f32<<<std::max(blocks, 1), 256, 0, st>>>(phi, (float*)q0, n); WSI_COUNT(); }
-    const T* cur = q0;
-    for (int m = 0; m < iters; ++m) {
-      stage<T>(g, ax, q0, cur, nullptr, B, nullptr, st);
-      if (m + 1 == iters) {
-        stage<T>(g, ax, q0, B, cur, nullptr, phi, st);
-      } else {
-        stage<T>(g, ax, q0, B, cur, A, nullptr, st);
-        cur = A;
-      }
+    { k_to_f32<<<blocks, 256, 0, st>>>(phi, (float*)q0, n); WSI_COUNT(); }
+  }
+  { k_reinit_code<T><<<blocks, 256, 0, st>>>(g, q0, code); WSI_COUNT(); }
+  const T* cur = q0;
+  for (int m = 0; m < iters; ++m) {
+    stage<T>(g, ax, code, q0, cur, nullptr, B, nullptr, st);
+    if constexpr (sizeof(T) == sizeof(double)) {
+      stage<T>(g, ax, code, q0, B, cur, (T*)phi, nullptr, st);
+      cur = (const T*)phi;
+    } else if (m + 1 == iters) {
+      stage<T>(g, ax, code, q0, B, cur, nullptr, phi, st);
+    } else {
+      stage<T>(g, ax, code, q0, B, cur, A, nullptr, st);
+      cur = A;
     }
   }
 }
