@@ -52,30 +52,6 @@ __device__ __forceinline__ T iface_frac(T a, T b, T c) {
   return T(0.5) - T(2) * c0 / (c1 + copysign(sqrt(disc), c1));
 }
 
-// D-, D+ along one axis from the five taps p[0..4] (cells i-2..i+2) of phi
-// and q[0..4] of phi~; hloc = smallest interface distance (h if none)
-template <typename T>
-__device__ __forceinline__ void eno_axis(const T p[5], const T q[5], T h, T ih, T& Dm, T& Dp, T& hloc) {
-  const T pm = p[0] - T(2) * p[1] + p[2], pc = p[1] - T(2) * p[2] + p[3], pp = p[2] - T(2) * p[3] + p[4];
-  const T mp = minmod_(pc, pp), mm = minmod_(pc, pm);
-  Dp = (p[3] - p[2]) * ih - T(0.5) * mp * ih;
-  Dm = (p[2] - p[1]) * ih + T(0.5) * mm * ih;
-  hloc = h;
-  const T qc = q[1] - T(2) * q[2] + q[3];
-  if (q[2] * q[3] < T(0)) {
-    const T qp = q[2] - T(2) * q[3] + q[4];
-    const T hp = fmin(fmax(h * iface_frac(q[2], q[3], minmod_(qc, qp)), T(1e-10) * h), h);
-    Dp = -p[2] / hp - T(0.5) * hp * mp * ih * ih;
-    hloc = fmin(hloc, hp);
-  }
-  if (q[2] * q[1] < T(0)) {
-    const T qm = q[0] - T(2) * q[1] + q[2];
-    const T hm = fmin(fmax(h * iface_frac(q[2], q[1], minmod_(qc, qm)), T(1e-10) * h), h);
-    Dm = p[2] / hm + T(0.5) * hm * mm * ih * ih;
-    hloc = fmin(hloc, hm);
-  }
-}
-
 template <typename T>
 __device__ __forceinline__ double widen(T v);
 template <>
@@ -164,13 +140,26 @@ __global__ void __launch_bounds__(RX* RY) k_reinit(GridDev g, ReinitAxes<T> ax,
   T zp[5];
 #pragma unroll
   for (int m = 0; m < 5; ++m) zp[m] = pin[(size_t)mirror_cell(k0 - 2 + m, n2) * plane + col];
+  // software pipeline: the tile, code byte and next z tap of plane k + 1
+  // are loaded while plane k is computed
+  T nxt[NS];
+#pragma unroll
+  for (int r = 0; r < NS; ++r) nxt[r] = soff[r] >= 0 ? pin[(size_t)k0 * plane + soff[r]] : T(0);
+  unsigned cd_next = inside && k0 < k1 ? code[(size_t)k0 * plane + col] : 0u;
   for (int k = k0; k < k1; ++k) {
     const size_t id = (size_t)k * plane + col;
-    const unsigned cd = inside ? code[id] : 0u;
+    const unsigned cd = cd_next;
 #pragma unroll
     for (int r = 0; r < NS; ++r)
-      if (soff[r] >= 0) sP[tid + r * RX * RY] = pin[(size_t)k * plane + soff[r]];
+      if (soff[r] >= 0) sP[tid + r * RX * RY] = nxt[r];
     __syncthreads();
+    if (k + 1 < k1) {
+#pragma unroll
+      for (int r = 0; r < NS; ++r)
+        if (soff[r] >= 0) nxt[r] = pin[(size_t)(k + 1) * plane + soff[r]];
+      cd_next = inside ? code[id + plane] : 0u;
+    }
+    const T z_in = pin[(size_t)mirror_cell(k + 3, n2) * plane + col];
     if (inside) {
       const T s = (cd & 3u) == 1u ? T(1) : ((cd & 3u) == 2u ? T(-1) : T(0));
       T g2 = T(0), hmin = T(0);
@@ -193,9 +182,10 @@ __global__ void __launch_bounds__(RX* RY) k_reinit(GridDev g, ReinitAxes<T> ax,
           const size_t stride = d == 0 ? 1 : (d == 1 ? (size_t)n0 : plane);
           subcell_axis(q0, id, c, g.n[d], stride, bits, p, ax.h[d], ax.ih[d], mp, mm, Dm, Dp, hloc);
         }
-        const T a = s > T(0) ? fmax(Dm, T(0)) : fmin(Dm, T(0));
-        const T b = s > T(0) ? fmin(Dp, T(0)) : fmax(Dp, T(0));
-        g2 += fmax(a * a, b * b);
+        // Godunov: s > 0 takes max(D-, 0) and min(D+, 0), s < 0 min(D-, 0)
+        // and max(D+, 0); both are max(s D-, -s D+, 0) in magnitude
+        const T t = fmax(fmax(s * Dm, -s * Dp), T(0));
+        g2 += t * t;
         hmin = any ? fmin(hmin, hloc) : hloc;
         any = true;
       }
@@ -208,7 +198,7 @@ __global__ void __launch_bounds__(RX* RY) k_reinit(GridDev g, ReinitAxes<T> ax,
     __syncthreads();
 #pragma unroll
     for (int m = 0; m < 4; ++m) zp[m] = zp[m + 1];
-    zp[4] = pin[(size_t)mirror_cell(k + 3, n2) * plane + col];
+    zp[4] = z_in;
   }
 }
 
