@@ -65,9 +65,10 @@ def kernel_model(name, nx, ny, nz, prec_bytes):
         byts = 8 * (F + F + F)
         return byts, 300 * F, "alu"
     if name == "reinit":
-        # first stage: read phi and phi~, write phi*; second stage: also read
-        # phi^m; the average of the two per launch
-        return prec_bytes * 7 * N // 2, 90 * N, "hbm"
+        # first stage: read phi and the one-byte sign/crossing code, write
+        # phi*; second stage: also read phi^m (phi~ itself is read only next
+        # to the interface); the average of the two per launch
+        return (5 * prec_bytes + 2) * N // 2, 90 * N, "hbm"
     raise ValueError(name)
 
 

@@ -12,10 +12,15 @@
 // throughout (immobile interface, Son 2005).  Neumann mirror ghosts.
 //
 // Layout: one thread per (x, y) column, marching a z-chunk; per z-plane the
-// block's tile of phi and phi~ with a two-cell halo is staged in shared
-// memory (ghosts mirrored while staging), the z taps come from five-entry
-// register windows.  HBM bound: per stage phi and phi~ are read once and phi
-// written once (plus phi^m in the second stage).
+// block's tile of phi with a two-cell halo is staged in shared memory (ghosts
+// mirrored while staging), the z taps come from a five-entry register window,
+// and the loads of the next plane are in flight while a plane is computed.
+// phi~ enters through a one-byte code per cell (its sign and the axes along
+// which it changes sign), made once per call; its values are read only for
+// the subcell distances next to the interface.  Per stage phi is read once
+// and written once (plus phi^m in the second stage) with the code byte: 9 or
+// 13 bytes per cell in float32.  The arithmetic per cell (three axes of ENO2
+// differences and minmod limiters) keeps the issue slots busier than HBM.
 #include "internal.h"
 
 namespace wsi {
