@@ -140,6 +140,8 @@ def build_case(n, workload="tank"):
 
 def workload_name(args):
     name = _base_workload_name(args)
+    if getattr(args, "form", "consistent") == "nonconservative":
+        name += ", non-conservative momentum form"
     return name + (", phi reinitialised (%d pseudo-time steps)" % args.reinit if args.reinit else "")
 
 
@@ -237,7 +239,7 @@ def learned_comparison(args, stream):
             "speedup_learned_fp32_over_plain_fp64": mean("plain_fp64") / mean("learned_fp32")}
 
 
-def oracle_sample_step(n_sample=12, workload="tank", reinit_iters=0):
+def oracle_sample_step(n_sample=12, workload="tank", reinit_iters=0, form="consistent"):
     """One oracle step of the same recipe at a small size (host cores):
     n_sample^3 for the tank, (2 n_sample) x n_sample x n_sample for the
     cylinder tank, n_sample x n_sample/2 x n_sample/2 for the wave tank (the
@@ -260,7 +262,7 @@ def oracle_sample_step(n_sample=12, workload="tank", reinit_iters=0):
         body = ost.Body(c.markers, c.dV, [True] * 6, half=c.box_half)
     s = ost.State(g, pr, c.phi, c.psi, body)
     t0 = time.perf_counter()
-    ost.step(s, c.dt, reinit_iters=reinit_iters)
+    ost.step(s, c.dt, reinit_iters=reinit_iters, form=form)
     dt = time.perf_counter() - t0
     return g.n_cells, dt
 
@@ -272,7 +274,7 @@ def run_reference(args, rank, world):
     times = []
     cells = 0
     for i in range(args.warmup + args.steps):
-        cells, dt = oracle_sample_step(n_sample, args.workload, args.reinit)
+        cells, dt = oracle_sample_step(n_sample, args.workload, args.reinit, args.form)
         if i >= args.warmup:
             times.append(dt)
     T = float(np.sum(times))
@@ -306,6 +308,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned pressure-solve comparison")
     ap.add_argument("--visc-sweeps", type=int, default=2, help="viscous red-black sweeps per preconditioner apply")
+    ap.add_argument("--form", default="consistent", choices=["consistent", "nonconservative"],
+                    help="momentum formulation: consistent mass/momentum transport (default) or the "
+                         "non-conservative one with the level-set density")
     ap.add_argument("--reinit", type=int, default=0,
                     help="pseudo-time steps of the level-set reinitialisation at the end of every step")
     ap.add_argument("--mg", default="2,2", help="pressure V-cycle pre,post smoothing sweeps")
@@ -343,7 +348,9 @@ def main():
     def make_ctx(p):
         pre, post = (int(v) for v in args.mg.split(","))
         ctx = wsi.Context.from_case(c, precision=p, restart=20, stream=stream.cuda_stream, mg_pre=pre, mg_post=post,
-                                    visc_sweeps=args.visc_sweeps, reinit_iters=args.reinit)
+                                    visc_sweeps=args.visc_sweeps, reinit_iters=args.reinit,
+                                    transport_form=(wsi.FORM_NONCONSERVATIVE if args.form == "nonconservative"
+                                                    else wsi.FORM_CONSISTENT))
         if args.workload in ("cylinder", "wave"):
             ctx.set_case(c)
             ctx.set_waves(**c.extra["waves"])
@@ -448,7 +455,7 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu:
         n_s, t_s = oracle_sample_step({"tank": 12, "cylinder": 8, "wave": 16}[args.workload], args.workload,
-                                      args.reinit)
+                                      args.reinit, args.form)
         cpu = {"value": n_s / t_s, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
                "sample": "one oracle time step (exact sparse-LU solves) of the same %s recipe at %s; "
                          "numpy/scipy single-threaded on the GPU host"
@@ -464,7 +471,7 @@ def main():
                            "cells": cells, "precision": args.precision, "l2": "inputs larger than L2 (no flush)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "mg_pre_post": args.mg, "visc_sweeps": args.visc_sweeps,
-                           "fgmres_iters": its, "reinit_iters": args.reinit},
+                           "fgmres_iters": its, "reinit_iters": args.reinit, "form": args.form},
                 "gpu_launches": int(l1 - l0), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks, "compare": compare, "learned": learned}
         print(json.dumps(line), flush=True)

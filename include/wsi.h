@@ -52,6 +52,11 @@ extern "C" {
 #define WSI_PREC_FP64 0   /* preconditioner in float64 (plain path)           */
 #define WSI_PREC_MIXED 1  /* preconditioner in float32 inside float64 FGMRES */
 
+#define WSI_FORM_CONSISTENT 0      /* SSP-RK3 mass transport, consistent momentum
+                                      convection (Sec. 4.2.2; the default)    */
+#define WSI_FORM_NONCONSERVATIVE 1 /* level-set face density, explicit CUI
+                                      convection N(u^{n+1/2}) (Sec. 4.2.3)    */
+
 #define WSI_GRAVITY_FLOW 0 /* rho^flow g: well-balanced, for locked bodies (Sec. 5) */
 #define WSI_GRAVITY_FULL 1 /* rho g with the transported face density           */
 
@@ -76,6 +81,8 @@ typedef struct {
     int reinit_iters;    /* pseudo-time steps of the level-set
                             reinitialisation at the end of every wsi_step
                             (Sec. 4.1); 0: phi is not reinitialised          */
+    int transport_form;  /* WSI_FORM_CONSISTENT or WSI_FORM_NONCONSERVATIVE
+                            (the formulation wsi_step integrates)            */
 } wsi_grid_desc;
 
 typedef struct {
@@ -168,7 +175,12 @@ int wsi_dlm_constrain(wsi_ctx* ctx, double* vel, wsi_body_state* out);
 /* One full time step of Sec. 4.2 (two fixed-point cycles): level-set
  * advection, psi rebuilt from the markers, materials, SSP-RK3 face density
  * and consistent convection, Stokes solve, rigidity projection and marker
- * update, on library-owned state.  Tolerance and limits from opts.
+ * update, on library-owned state.  With transport_form =
+ * WSI_FORM_NONCONSERVATIVE the momentum equation of Sec. 4.2.3 replaces the
+ * consistent one: rho^{n+1,k+1} (u - u^n)/dt + rho^{n+1,k+1} N = -G p +
+ * L_mu u (same Crank-Nicolson split) + rho_g g, with rho^{n+1,k+1} the face
+ * density of the level sets and N the CUI-limited div(u^{n+1/2,k} u) (no mass
+ * transport).  Tolerance and limits from opts.
  * WSI_ERR_DEVICE when the device bound check of the marker update saw a
  * marker leave the box by more than half a cell or turn non-finite; the step
  * is then committed as computed and the flag cleared, so the caller decides

@@ -16,6 +16,14 @@ At k = 0: u^{n+1,0} = u^n, X^{n+1,0} = X^n.  At n = 0: u^{-1} = u^0.
 With wave zones, u^{n+1} and phi^{n+1} are relaxed at t^{n+1} (Sec. 7.1).
 With reinit_iters > 0, phi^{n+1} is then reinitialised to a signed distance
 (Sec. 4.1; reinit.py) before the step is committed.
+
+form = "nonconservative" takes the paper's non-conservative, inconsistent
+formulation (Sec. 4.2.3) instead of step 2: the face density of the
+momentum equation is rho^{n+1,k+1} from the level sets (no mass transport),
+and the convection is the explicit CUI-limited N = div(u^{n+1/2,k} u^{n+1/2,k})
+with u^{n+1/2,k} = (u^{n+1,k} + u^n)/2:
+  rho^{n+1,k+1} (u~ - u^n)/dt + rho^{n+1,k+1} N = -G p + L_mu u (Crank-Nicolson
+  split as above) + rho_g g.
 """
 import numpy as np
 
@@ -71,7 +79,7 @@ def _materials(s: State, phi, psi):
     return Materials(s.g, phi, psi, pr.rho_l, pr.rho_g, pr.rho_s, pr.mu_l, pr.mu_g, pr.mu_s, pr.n_cells)
 
 
-def step(s: State, dt, n_cycles=2, reinit_iters=0):
+def step(s: State, dt, n_cycles=2, reinit_iters=0, form="consistent"):
     g, pr = s.g, s.props
     u_n = [a.copy() for a in s.vel]
     u_nm1 = [a.copy() for a in s.vel_old]
@@ -98,14 +106,25 @@ def step(s: State, dt, n_cycles=2, reinit_iters=0):
         else:
             psi_new = psi_k
         mat = _materials(s, phi_new, psi_new)
-        u1, u2 = transport.rk_velocities(u_n, u_nm1, u_k, k)
-        rho_new, C = transport.ssp_rk3(g, rho_n, u_n, u1, u2, dt)
+        if form == "consistent":
+            u1, u2 = transport.rk_velocities(u_n, u_nm1, u_k, k)
+            rho_new, C = transport.ssp_rk3(g, rho_n, u_n, u1, u2, dt)
+        elif form == "nonconservative":
+            rho_new = mat.rho_face
+            ones = [np.ones(g.face_shape(c)) for c in range(3)]
+            N = transport.convective(g, [0.5 * (a + b) for a, b in zip(u_k, u_n)], ones)
+        else:
+            raise ValueError(form)
         if pr.gravity_mode == "flow":
             rho_grav = [flow_only(face_average(g, phi_new, c), pr.rho_l, pr.rho_g, mat.eps) for c in range(3)]
         else:
             rho_grav = rho_new
-        b_u = [rho_n[c] * u_n[c] / dt - C[c] + (1.0 - pr.theta) * Lmu_n[c] + rho_grav[c] * pr.gravity[c]
-               for c in range(3)]
+        if form == "consistent":
+            b_u = [rho_n[c] * u_n[c] / dt - C[c] + (1.0 - pr.theta) * Lmu_n[c] + rho_grav[c] * pr.gravity[c]
+                   for c in range(3)]
+        else:
+            b_u = [rho_new[c] * (u_n[c] / dt - N[c]) + (1.0 - pr.theta) * Lmu_n[c] + rho_grav[c] * pr.gravity[c]
+                   for c in range(3)]
         b = g.pack(b_u[0], b_u[1], b_u[2], np.zeros(g.cell_shape))
         x = solve_stokes(g, mat, rho_new, dt, pr.theta, b)
         ut, vt, wt, p = g.unpack(x)

@@ -116,6 +116,7 @@ struct wsi_ctx {
   // mu_cc / mu_e hold mu(phi^n, psi^n) (true right after a step)
   bool mat_n_valid = false;
   double* ri_scratch = nullptr;  // reinitialisation: 3 x ncell doubles, on first use
+  void* ones = nullptr;          // unit face density of the non-conservative convection, on first use
   // learned coarse correction of the float32 pressure multigrid
   wsi_unet* unet = nullptr;
   UNetImpl* unet_impl = nullptr;
@@ -605,7 +606,9 @@ void levelset_stage(wsi_ctx* c, const double* vk, const double* vn, const double
 
 // b0 = rho^n u^n/dt + (1-theta) L_mu^n u^n  (needs transport_stage's float32
 // copy of u^n on the mixed path)
-void rhs_base(wsi_ctx* c, double dt) {
+// b0 = rho^n u^n w + (1 - theta) L_mu^n u^n; w = 1/dt for the consistent
+// form, 0 for the non-conservative one (its mass term uses rho^{n+1,k+1})
+void rhs_base(wsi_ctx* c, double w) {
   const GridDev& g = c->g;
   cudaStream_t st = c->st;
   double* b0[3];
@@ -614,7 +617,7 @@ void rhs_base(wsi_ctx* c, double dt) {
   cparts(c, (const double*)c->vel, un);
   const double* crn[3] = {c->rho_n[0], c->rho_n[1], c->rho_n[2]};
   if (!c->mixed()) {
-    launch_rhs_base<double>(g, coef_n(c), un, crn, un, 1.0 / dt, c->desc.theta, b0, st);
+    launch_rhs_base<double>(g, coef_n(c), un, crn, un, w, c->desc.theta, b0, st);
   } else {
     launch_lincomb_to_f32(c->ncell, 1.0, c->mu_cc_n, 0.0, nullptr, 0.0, nullptr, c->mu_cc_n32, st);
     for (int e = 0; e < 3; ++e)
@@ -628,13 +631,57 @@ void rhs_base(wsi_ctx* c, double dt) {
     cf.mu_cc = c->mu_cc_n32;
     const float* u32[3];
     cparts(c, (const float*)c->vn32, u32);
-    launch_rhs_base<float>(g, cf, u32, crn, un, 1.0 / dt, c->desc.theta, b0, st);
+    launch_rhs_base<float>(g, cf, u32, crn, un, w, c->desc.theta, b0, st);
   }
 }
 
 int valid_ctx(wsi_ctx* c) { return c ? WSI_OK : WSI_ERR_INVALID_ARG; }
 
 }  // namespace
+
+__global__ void k_fill_one(double* a, float* f, size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    if (a) a[t] = 1.0;
+    if (f) f[t] = 1.0f;
+  }
+}
+
+// Non-conservative convection (Sec. 4.2.3): N = div(u^{n+1/2,k} u_lim) with
+// the CUI-limited velocity on the face control volumes, i.e. the momentum
+// flux of the consistent scheme at unit density, from the half-step velocity
+// the level-set stage of this cycle formed (vel_half, or vh32 on the mixed
+// path).  Result in Cc (float64) or C32 (float32).
+int nc_convection(wsi_ctx* c) {
+  const GridDev& g = c->g;
+  cudaStream_t st = c->st;
+  const size_t nv = c->nvel;
+  if (!c->ones) {
+    c->ones = dalloc(c, nv);
+    if (!c->ones) return fail(c, WSI_ERR_OOM, "unit density");
+    const int blocks = (int)std::min<size_t>((nv + 255) / 256, 152 * 16);
+    if (c->mixed())
+      k_fill_one<<<blocks, 256, 0, st>>>(nullptr, (float*)c->ones, nv);
+    else
+      k_fill_one<<<blocks, 256, 0, st>>>((double*)c->ones, nullptr, nv);
+    WSI_COUNT();
+  }
+  if (c->mixed()) {
+    const float *vh[3], *one[3];
+    float* N[3];
+    cparts(c, (const float*)c->vh32, vh);
+    cparts(c, (const float*)c->ones, one);
+    parts(c, c->C32, N);
+    launch_transport_flux<float>(g, vh, one, true, N, st);
+  } else {
+    const double *vh[3], *one[3];
+    double* N[3];
+    cparts(c, (const double*)c->vel_half, vh);
+    cparts(c, (const double*)c->ones, one);
+    parts(c, c->Cc, N);
+    launch_transport_flux<double>(g, vh, one, true, N, st);
+  }
+  return WSI_OK;
+}
 
 // pseudo-time CFL number of the reinitialisation (local step cfl * h_min)
 constexpr double kReinitCfl = 0.3;
@@ -691,6 +738,8 @@ int wsi_create_grid(const wsi_grid_desc* d, void* stream, wsi_ctx** out) {
   if (d->nz == 1 && (d->bc[4] != WSI_FREE_SLIP || d->bc[5] != WSI_FREE_SLIP)) return WSI_ERR_INVALID_ARG;
   if (d->precision != WSI_PREC_FP64 && d->precision != WSI_PREC_MIXED) return WSI_ERR_INVALID_ARG;
   if (d->reinit_iters < 0) return WSI_ERR_INVALID_ARG;
+  if (d->transport_form != WSI_FORM_CONSISTENT && d->transport_form != WSI_FORM_NONCONSERVATIVE)
+    return WSI_ERR_INVALID_ARG;
   if ((double)(d->nx + 1) * (d->ny + 1) * (d->nz + 1) >= 2147483648.0) return WSI_ERR_INVALID_ARG;
   wsi_ctx* c = new wsi_ctx();
   c->desc = *d;
@@ -970,15 +1019,34 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
     c->phi_cur = c->phi_new;
     launch_materials(g, pc, c->phi_new, psi_use, c->rho_cc, c->mu_cc, c->rho_face, c->beta, c->rho_flow, c->mu_e,
                      st);
-    // 2. SSP-RK3 face density and consistent convection; right-hand side
-    transport_stage(c, k, dt, c->vel, c->vel_old, c->vel_k, k > 0);
-    if (k == 0) rhs_base(c, dt);
+    // 2. SSP-RK3 face density and consistent convection; right-hand side.
+    //    Non-conservative form (Sec. 4.2.3): the level sets' face density
+    //    rho^{n+1,k+1} stays in the operator, N from the half-step velocity.
+    const bool nc = c->desc.transport_form == WSI_FORM_NONCONSERVATIVE;
+    if (nc) {
+      int rn = nc_convection(c);
+      if (rn) return rn;
+      if (k == 0) {
+        if (c->mixed()) launch_lincomb_to_f32(nv, 1.0, c->vel, 0.0, nullptr, 0.0, nullptr, c->vn32, st);
+        rhs_base(c, 0.0);
+      }
+    } else {
+      transport_stage(c, k, dt, c->vel, c->vel_old, c->vel_k, k > 0);
+      if (k == 0) rhs_base(c, 1.0 / dt);
+    }
     const double* rg[3];
     for (int d = 0; d < 3; ++d) rg[d] = c->props.gravity_mode == WSI_GRAVITY_FLOW ? c->rho_flow[d] : c->rho_face[d];
-    if (c->mixed())
+    if (nc) {
+      const double* rf[3] = {c->rho_face[0], c->rho_face[1], c->rho_face[2]};
+      if (c->mixed())
+        launch_rhs_nc<float>(g, c->b0, c->C32, rf, c->vel, 1.0 / dt, rg, c->desc.gravity, c->b, st);
+      else
+        launch_rhs_nc<double>(g, c->b0, c->Cc, rf, c->vel, 1.0 / dt, rg, c->desc.gravity, c->b, st);
+    } else if (c->mixed()) {
       launch_rhs_cycle<float>(g, c->b0, c->C32, rg, c->desc.gravity, c->b, st);
-    else
+    } else {
       launch_rhs_cycle<double>(g, c->b0, c->Cc, rg, c->desc.gravity, c->b, st);
+    }
     cudaMemsetAsync(c->b + c->pk.off[3], 0, nc * sizeof(double), st);
     // 3. Stokes solve from (u^{n+1,k}, p^{n+1/2,k})
     cudaMemcpyAsync(c->x, c->vel_k, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);

@@ -121,6 +121,10 @@ template <typename TC>
 void launch_rhs_cycle(const GridDev& g, const double* b0, const TC* C, const double* const rho_g[3],
                       const double grav[3], double* b, cudaStream_t st);
 void launch_zero_walls(const GridDev& g, double* const q[3], cudaStream_t st);
+// non-conservative form: b = b0 + rho (u^n/dt - N) + rho_g g (walls 0)
+template <typename TN>
+void launch_rhs_nc(const GridDev& g, const double* b0, const TN* N, const double* const rho[3], const double* u_n,
+                   double inv_dt, const double* const rho_g[3], const double grav[3], double* b, cudaStream_t st);
 
 // ---------------------------------------------------------------- krylov.cu
 // deterministic reductions: out[t] = <V_t, w> for t < m (V row-major m x n)

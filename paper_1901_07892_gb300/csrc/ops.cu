@@ -561,6 +561,50 @@ void launch_rhs_cycle(const GridDev& g, const double* b0, const TC* C, const dou
   launch_zero_walls(g, q, st);
 }
 
+// Non-conservative form (Sec. 4.2.3): b = b0 + rho (u^n/dt - N) + rho_g g with
+// b0 = (1 - theta) L_mu^n u^n and rho = rho^{n+1,k+1} the face density of the
+// level sets; wall faces are zero on output
+template <typename TN>
+__global__ void k_rhs_nc(size_t n0, size_t n1, size_t n2, const double* __restrict__ b0, const TN* __restrict__ N,
+                         const double* __restrict__ r0, const double* __restrict__ r1, const double* __restrict__ r2,
+                         const double* __restrict__ un, double inv_dt, const double* __restrict__ rg0,
+                         const double* __restrict__ rg1, const double* __restrict__ rg2, double g0, double g1,
+                         double g2, double* b) {
+  size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t n = n0 + n1 + n2;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+    double rho, grav = 0.0;
+    if (t < n0) {
+      rho = r0[t];
+      if (g0 != 0.0) grav = rg0[t] * g0;
+    } else if (t < n0 + n1) {
+      rho = r1[t - n0];
+      if (g1 != 0.0) grav = rg1[t - n0] * g1;
+    } else {
+      rho = r2[t - n0 - n1];
+      if (g2 != 0.0) grav = rg2[t - n0 - n1] * g2;
+    }
+    b[t] = b0[t] + rho * (un[t] * inv_dt - cvt<double, TN>(N[t])) + grav;
+  }
+}
+
+template <typename TN>
+void launch_rhs_nc(const GridDev& g, const double* b0, const TN* N, const double* const rho[3], const double* u_n,
+                   double inv_dt, const double* const rho_g[3], const double grav[3], double* b, cudaStream_t st) {
+  size_t n0 = fsize(g, 0), n1 = fsize(g, 1), n2 = fsize(g, 2);
+  int blocks = (int)std::min<size_t>((n0 + n1 + n2 + 255) / 256, 152 * 16);
+  { k_rhs_nc<TN><<<blocks, 256, 0, st>>>(n0, n1, n2, b0, N, rho[0], rho[1], rho[2], u_n, inv_dt, rho_g[0], rho_g[1],
+                                         rho_g[2], grav[0], grav[1], grav[2], b); WSI_COUNT(); }
+  double* q[3] = {b, b + n0, b + n0 + n1};
+  launch_zero_walls(g, q, st);
+}
+template void launch_rhs_nc<double>(const GridDev&, const double*, const double*, const double* const[3],
+                                    const double*, double, const double* const[3], const double[3], double*,
+                                    cudaStream_t);
+template void launch_rhs_nc<float>(const GridDev&, const double*, const float*, const double* const[3],
+                                   const double*, double, const double* const[3], const double[3], double*,
+                                   cudaStream_t);
+
 template void launch_rhs_base<double>(const GridDev&, const Coef<double>&, const double* const[3],
                                       const double* const[3], const double* const[3], double, double,
                                       double* const[3], cudaStream_t);
