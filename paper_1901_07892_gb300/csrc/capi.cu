@@ -1022,8 +1022,8 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
     // 2. SSP-RK3 face density and consistent convection; right-hand side.
     //    Non-conservative form (Sec. 4.2.3): the level sets' face density
     //    rho^{n+1,k+1} stays in the operator, N from the half-step velocity.
-    const bool nc = c->desc.transport_form == WSI_FORM_NONCONSERVATIVE;
-    if (nc) {
+    const bool nonconservative = c->desc.transport_form == WSI_FORM_NONCONSERVATIVE;
+    if (nonconservative) {
       int rn = nc_convection(c);
       if (rn) return rn;
       if (k == 0) {
@@ -1036,7 +1036,7 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
     }
     const double* rg[3];
     for (int d = 0; d < 3; ++d) rg[d] = c->props.gravity_mode == WSI_GRAVITY_FLOW ? c->rho_flow[d] : c->rho_face[d];
-    if (nc) {
+    if (nonconservative) {
       const double* rf[3] = {c->rho_face[0], c->rho_face[1], c->rho_face[2]};
       if (c->mixed())
         launch_rhs_nc<float>(g, c->b0, c->C32, rf, c->vel, 1.0 / dt, rg, c->desc.gravity, c->b, st);
