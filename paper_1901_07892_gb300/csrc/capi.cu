@@ -826,9 +826,9 @@ int wsi_create_grid(const wsi_grid_desc* d, void* stream, wsi_ctx** out) {
     for (int e = 0; e < 3; ++e) c->mu_e_n32[e] = F(esize(g, e));
     // double-float operands: one float2 per element, the size of a double
     auto P2 = [&](size_t n) { return (float2*)A(n); };
-    for (int d = 0; d < 3; ++d) {
-      c->df_rho[d] = P2(fsize(g, d));
-      c->df_mu_e[d] = P2(esize(g, d));
+    for (int a = 0; a < 3; ++a) {
+      c->df_rho[a] = P2(fsize(g, a));
+      c->df_mu_e[a] = P2(esize(g, a));
     }
     c->df_mu_cc = P2(c->ncell);
     c->df_x = P2(c->nstk);
