@@ -24,6 +24,10 @@ and the convection is the explicit CUI-limited N = div(u^{n+1/2,k} u^{n+1/2,k})
 with u^{n+1/2,k} = (u^{n+1,k} + u^n)/2:
   rho^{n+1,k+1} (u~ - u^n)/dt + rho^{n+1,k+1} N = -G p + L_mu u (Crank-Nicolson
   split as above) + rho_g g.
+Parity of this form is pinned in part (at rest; equal to the consistent form
+for one density and a steady solenoidal flow); parity unpinned for the choice
+of rho^{n+1,k+1} rather than rho^n in its mass term, which those cases cannot
+separate.
 """
 import numpy as np
 
