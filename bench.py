@@ -11,7 +11,12 @@ cell) centred on the surface, dt = 5e-4; the surface sloshes, so every solve
 iterates.  Metric: cell-steps/s = cells x steps / time.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl wsi|reference]
-       [--precision mixed|fp64] [--n 256] [--roofline-kernel stokes|rbgs_p|...]
+       [--precision mixed|fp64] [--n 256] [--roofline-kernel stokes|rbgs_p|...|reinit]
+       [--workload tank|cylinder|wave] [--form consistent|nonconservative] [--reinit K]
+--form nonconservative integrates the paper's non-conservative, inconsistent
+formulation instead (Sec. 4.2.3); --reinit K reinitialises phi with K
+pseudo-time steps at the end of every step (Sec. 4.1).  Both change the
+workload's name in the JSON line; the defaults are the headline workload.
 Under torchrun (N > 1) every rank runs an independent replica on its own GPU
 (the method needs no exchange between replicas here): weak scaling.
 """
