@@ -126,8 +126,13 @@ typedef struct {
 typedef struct {
     int iters[4];        /* FGMRES iterations of each cycle's solve           */
     double rel_residual[4];
-    double umax;         /* max |u| after the step                             */
+    double umax;         /* max |u| over all faces after the step              */
     double ms;
+    double F_lm[3];      /* net hydrodynamic force on the body by the Lagrange-
+                            multiplier method (Sec. 8): sum over the markers of
+                            rho_s [(U_b^{n+1} - U_b^n) - dU^{n+1}] dV / dt with
+                            dU = U_b - J u~ of the last cycle; 0 without a
+                            body                                              */
 } wsi_step_stats;
 
 /* Sizes of the packed vectors (doubles). */

@@ -41,12 +41,13 @@ def body_velocity(X, Xc, Ur, Wr):
     return Ur[None, :] + np.cross(Wr[None, :], R)
 
 
-def constrain(g: Grid, vel, X, dV, lock, U_pres, W_pres):
+def constrain(g: Grid, vel, X, dV, lock, U_pres, W_pres, full=False):
     """One rigidity projection for a single body.
 
     vel: (u, v, w) uncorrected velocity; X: marker positions used for J and S
     (X^{n+1/2,k}); lock: 6 booleans (Ux,Uy,Uz,Wx,Wy,Wz), True = prescribed.
-    Returns corrected (u, v, w), U_b per marker, U_r, W_r, X_com."""
+    Returns corrected (u, v, w), U_b per marker, U_r, W_r, X_com (and, with
+    full, the interpolated velocity J u~ per marker)."""
     Ui = interpolate(g, vel, X)
     Ur, Wr, Xc = rigid_fit(X, Ui)
     lock = np.asarray(lock, dtype=bool)
@@ -55,7 +56,17 @@ def constrain(g: Grid, vel, X, dV, lock, U_pres, W_pres):
     Ub = body_velocity(X, Xc, Ur, Wr)
     corr = spread(g, Ub - Ui, X, dV)
     new = [vel[c] + corr[c] for c in range(3)]
+    if full:
+        return new, Ub, Ur, Wr, Xc, Ui
     return new, Ub, Ur, Wr, Xc
+
+
+def lm_force(Ub_new, Ub_old, dU, rho_s, dV, dt):
+    """Net hydrodynamic force on the body by the Lagrange-multiplier method
+    (Sec. 8, the LM-force equation), summed over the markers:
+        F^{n+1} = sum_l rho_s [(U_b^{n+1} - U_b^n)/dt - dU^{n+1}/dt] dV,
+    dU = U_b - J u~ the rigidity correction of the last cycle."""
+    return rho_s * dV * np.sum((Ub_new - Ub_old) / dt - dU / dt, axis=0)
 
 
 def update_positions(Xn, Ub_new, Ub_old, dt):

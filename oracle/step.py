@@ -135,10 +135,11 @@ def step(s: State, dt, n_cycles=2, reinit_iters=0, form="consistent"):
         vel_t = [ut, vt, wt]
         if body is not None:
             X_half = 0.5 * (X_k + X_n)
-            vel_c, Ub, Ur, Wr, Xc = rigid.constrain(g, vel_t, X_half, body.dV, body.lock,
-                                                    body.U_pres, body.W_pres)
+            vel_c, Ub, Ur, Wr, Xc, Ui = rigid.constrain(g, vel_t, X_half, body.dV, body.lock,
+                                                        body.U_pres, body.W_pres, full=True)
             X_k = rigid.update_positions(X_n, Ub, Ub_n, dt)
-            info.update(Ur=Ur, Wr=Wr, Ub=Ub)
+            info.update(Ur=Ur, Wr=Wr, Ub=Ub,
+                        F_lm=rigid.lm_force(Ub, Ub_n, Ub - Ui, pr.rho_s, body.dV, dt))
         else:
             vel_c = vel_t
         u_k = vel_c

@@ -1089,6 +1089,16 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
   cudaMemcpyAsync(c->p, c->x + c->pk.off[3], nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(c->phi, c->phi_k, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(c->psi, c->psi_k, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  // Lagrange-multiplier force (Sec. 8): F = sum_l rho_s [(U_b^{n+1} - U_b^n)
+  // - (U_b^{n+1} - J u~)] dV / dt with the last cycle's J u~ (B.U); the two
+  // U_b^{n+1} sums cancel, so one reduction of J u~ - U_b^n is taken (B.F is
+  // free once the last spreading has run)
+  double fsum[3] = {0.0, 0.0, 0.0};
+  if (c->has_body) {
+    launch_lincomb((size_t)B.n * 3, 1.0, B.U, -1.0, B.Ub_n, 0.0, nullptr, B.F, st);
+    launch_rigid_sums(B.X, B.F, B.n, nullptr, B.sums, B.scratch, st);
+    cudaMemcpyAsync(fsum, B.sums, sizeof(fsum), cudaMemcpyDeviceToHost, st);
+  }
   if (c->has_body) cudaMemcpyAsync(B.Ub_n, B.Ub, (size_t)B.n * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
   int hflag = 0;
   if (c->has_body && B.flag) cudaMemcpyAsync(&hflag, B.flag, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -1102,8 +1112,12 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
   // the last cycle's viscosity is mu(phi^{n+1}) unless the zones relaxed phi
   c->mat_n_valid = !c->has_waves && c->desc.reinit_iters == 0;
   if (s) {
+    s->umax = host_maxabs(c->vel, nv, c->red, st);
+    const double f = c->has_body ? c->props.rho_s * B.dV / dt : 0.0;
+    for (int d = 0; d < 3; ++d) s->F_lm[d] = f * fsum[d];
+    int rs = cuda_check(c, "step stats");
+    if (rs) return rs;
     s->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    s->umax = 0.0;
   }
   return WSI_OK;
 }

@@ -136,6 +136,8 @@ void launch_maxpy(const double* V, size_t ldv, int m, const double* h, double* w
                   cudaStream_t st, const double* scale_dev = nullptr);
 void launch_scale(double* x, size_t n, const double* s_dev, bool inverse, cudaStream_t st);
 double host_norm2(const double* x, size_t n, double* scratch, cudaStream_t st);
+// max |x_i| read back to the host (scratch: RB + 1 doubles)
+double host_maxabs(const double* x, size_t n, double* scratch, cudaStream_t st);
 template <typename T>
 void launch_sum(const T* x, size_t n, double* out_dev, double* scratch, cudaStream_t st);
 template <typename T>

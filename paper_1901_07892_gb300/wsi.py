@@ -72,7 +72,7 @@ class BodyState(ctypes.Structure):
 
 class StepStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int * 4), ("rel_residual", ctypes.c_double * 4),
-                ("umax", ctypes.c_double), ("ms", ctypes.c_double)]
+                ("umax", ctypes.c_double), ("ms", ctypes.c_double), ("F_lm", ctypes.c_double * 3)]
 
 
 class WaveDesc(ctypes.Structure):

@@ -52,6 +52,17 @@ def _random_case(nx, ny, nz, seed, lx=1.0, ly=0.9, lz=0.8):
     return c, rng
 
 
+def _check_step_stats(st, info, s, rho_s, dV, n_markers, dt):
+    """umax and the Lagrange-multiplier force of the last step: umax within
+    the field tolerance; the force within ten times the change a field error
+    of FIELD_TOL * umax in every interpolated velocity makes to it."""
+    umax = max(np.abs(a).max() for a in s.vel)
+    assert abs(st.umax - umax) <= FIELD_TOL * umax, (st.umax, umax)
+    F = np.array(st.F_lm[:])
+    tol = 10.0 * rho_s * dV / dt * n_markers * FIELD_TOL * umax
+    assert np.abs(F - info["F_lm"]).max() <= tol, (F, info["F_lm"], tol)
+
+
 def _oracle_mat(c, g):
     return Materials(g, c.phi, c.psi, c.rho_l, c.rho_g, c.rho_s, c.mu_l, c.mu_g, c.mu_s, c.n_cells)
 
@@ -325,8 +336,9 @@ def test_step_parity_small_tank(precision):
     for _ in range(2):
         # gravity-dominated right-hand side: solve far below 1e-8 (see
         # test_solve_parity_gravity_dominated)
-        ctx.step(c.dt, rtol=1e-13, max_iters=600)
-        ost.step(s, c.dt)
+        st = ctx.step(c.dt, rtol=1e-13, max_iters=600)
+        info = ost.step(s, c.dt)
+    _check_step_stats(st, info, s, c.rho_l, c.dV, len(c.markers), c.dt)
     vel = ctx.get_field(wsi.F_VEL)
     ref = np.concatenate([a.ravel() for a in s.vel])
     assert _rel(vel, ref) < FIELD_TOL
@@ -351,12 +363,13 @@ def test_step_parity_free_cylinder():
     body = ost.Body(c.markers, c.dV, list(c.lock), cylinder=c.extra["cylinder"])
     s = ost.State(g, pr, c.phi, c.psi, body)
     for _ in range(2):
-        ost.step(s, c.dt)
+        info = ost.step(s, c.dt)
     for precision in (wsi.PREC_FP64, wsi.PREC_MIXED):
         ctx = wsi.Context.from_case(c, precision=precision, restart=30)
         ctx.set_case(c)
         for _ in range(2):
-            ctx.step(c.dt, rtol=1e-13, max_iters=600)
+            st = ctx.step(c.dt, rtol=1e-13, max_iters=600)
+        _check_step_stats(st, info, s, c.rho_s, c.dV, len(c.markers), c.dt)
         vel = ctx.get_field(wsi.F_VEL)
         ref = np.concatenate([a.ravel() for a in s.vel])
         assert _rel(vel, ref) < FIELD_TOL, precision

@@ -135,3 +135,39 @@ def test_cylinder_sdf_closed_forms():
     assert v == pytest.approx(np.hypot(np.hypot(px - 0.5, pz - 0.5) - R, abs(py - 0.5) - hl))
     # a distance function: |grad d| = 1 away from the medial surfaces
     assert np.all(np.abs(d) <= np.sqrt(3.0))
+
+
+def test_lm_force_closed_forms():
+    """The Lagrange-multiplier force (Sec. 8): a body held at rest in a
+    fluid moving uniformly at V inside it needs F = rho_s N dV V / dt to
+    stop that fluid each step (U_b = 0, dU = -V on every marker); a free body,
+    whose translation is the mean interpolated velocity, feels exactly its
+    mass times its acceleration (the corrections dU sum to zero)."""
+    from oracle.rigid import lm_force
+    rng = np.random.default_rng(4)
+    n, dV, dt, rho_s = 50, 1e-4, 2e-3, 700.0
+    V = np.array([0.3, -0.2, 0.05])
+    zero = np.zeros((n, 3))
+    F = lm_force(zero, zero, np.tile(-V, (n, 1)), rho_s, dV, dt)
+    assert np.allclose(F, rho_s * n * dV * V / dt, rtol=1e-14)
+    X = rng.uniform(0.3, 0.7, (n, 3))
+    Ui = rng.standard_normal((n, 3))
+    Ur, Wr, Xc = rigid_fit(X, Ui)
+    Ub = body_velocity(X, Xc, Ur, Wr)
+    Ur_old = np.array([0.1, 0.0, -0.4])
+    Ub_old = body_velocity(X, Xc, Ur_old, rng.standard_normal(3))
+    F = lm_force(Ub, Ub_old, Ub - Ui, rho_s, dV, dt)
+    assert np.allclose(F, rho_s * n * dV * (Ur - Ur_old) / dt, rtol=1e-10, atol=1e-10)
+
+
+def test_lm_force_of_a_body_at_rest_in_a_tank_at_rest():
+    """Hydrostatic three-phase tank with a locked box: u~ = 0 everywhere, so
+    the body's Lagrange-multiplier force is zero."""
+    from oracle import step as ost
+    c = inputs.tank3d(n=10, with_body=True, dt=5e-4, gravity_mode="flow")
+    g = Grid(c.nx, c.ny, c.nz, c.lx, c.ly, c.lz, c.bc)
+    pr = ost.Props(rho_l=c.rho_l, rho_g=c.rho_g, rho_s=c.rho_l, mu_l=c.mu_l, mu_g=c.mu_g, gravity=c.gravity,
+                   gravity_mode="flow")
+    s = ost.State(g, pr, c.phi, c.psi, ost.Body(c.markers, c.dV, [True] * 6, half=c.box_half))
+    info = ost.step(s, c.dt)
+    assert np.abs(info["F_lm"]).max() < 1e-6
