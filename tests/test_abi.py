@@ -44,3 +44,14 @@ def test_invalid_arguments_rejected_without_gpu_work():
     d.bc[0] = 0.5  # not a wall sign
     assert L.wsi_create_grid(ctypes.byref(d), None, ctypes.byref(h)) == wsi.ERR_INVALID_ARG
     assert L.wsi_stokes_solve(None, None, None, 1.0, None, None) == wsi.ERR_INVALID_ARG
+    d.bc[0] = -1.0
+    d.reinit_iters = -1  # negative pseudo-time step count
+    assert L.wsi_create_grid(ctypes.byref(d), None, ctypes.byref(h)) == wsi.ERR_INVALID_ARG
+    d.reinit_iters = 0
+    d.transport_form = 7  # neither formulation
+    assert L.wsi_create_grid(ctypes.byref(d), None, ctypes.byref(h)) == wsi.ERR_INVALID_ARG
+    d.transport_form = wsi.FORM_CONSISTENT
+    d.precision = 5
+    assert L.wsi_create_grid(ctypes.byref(d), None, ctypes.byref(h)) == wsi.ERR_INVALID_ARG
+    assert L.wsi_reinit(None, None, 3) == wsi.ERR_INVALID_ARG
+    assert L.wsi_step(None, 1e-3, None, None) == wsi.ERR_INVALID_ARG
