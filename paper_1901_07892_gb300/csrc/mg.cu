@@ -537,7 +537,6 @@ template <typename T>
 static void vcycle(Precond<T>& P, const Opts& o, size_t l, cudaStream_t st) {
   MGLevel<T>& L = P.lev[l];
   const GridDev& g = L.g;
-  dim3 gr = grid3(g.n[0], g.n[1], g.n[2]);
   if (l + 1 == P.lev.size()) {
     { k_coarse_solve<T><<<1, 256, P.ncoarse * sizeof(double), st>>>(P.ncoarse, P.coarse_inv, L.b, L.x); WSI_COUNT(); }
     return;
