@@ -113,8 +113,11 @@ def _adv_velocity(g: Grid, vel, c, d):
     n = q.shape[axc]
     a = 0.5 * (np.take(q, np.arange(0, n - 1), axis=axc) + np.take(q, np.arange(1, n), axis=axc))
     # a lives at the c-face positions interior along c: pad the two wall
-    # positions along c with zeros (those c-faces are not transported)
-    z = np.zeros_like(np.take(a, [0], axis=axc))
+    # positions along c with zeros (those c-faces are not transported; with
+    # one cell along c, as for w in 2-D, there are no interior positions)
+    shape = list(a.shape)
+    shape[axc] = 1
+    z = np.zeros(shape)
     return np.concatenate([z, a, z], axis=axc)
 
 

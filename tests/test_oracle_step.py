@@ -99,3 +99,19 @@ def test_forms_differ_at_high_density_ratio():
             st.step(s, c.dt, form=form)
         out[form] = np.concatenate([a.ravel() for a in s.vel])
     assert np.abs(out["consistent"] - out["nonconservative"]).max() > 1e-6 * np.abs(out["consistent"]).max()
+
+
+def test_two_dimensional_hydrostatic_step():
+    """A 2-D tank (nz = 1, free-slip z walls: every z-derivative vanishes and
+    the w-faces are all wall faces) with a locked square at rest stays at
+    rest in both formulations."""
+    n = 16
+    c = inputs.tank2d(n=n, with_body=True)
+    g = Grid(c.nx, c.ny, c.nz, c.lx, c.ly, c.lz, c.bc)
+    pr = st.Props(rho_l=c.rho_l, rho_g=c.rho_g, rho_s=c.rho_l, mu_l=c.mu_l, mu_g=c.mu_g, gravity=c.gravity,
+                  gravity_mode="flow")
+    for form in ("consistent", "nonconservative"):
+        s = st.State(g, pr, c.phi, c.psi, st.Body(c.markers, c.dV, [True] * 6, half=c.box_half))
+        for _ in range(2):
+            st.step(s, c.dt, form=form)
+        assert max(np.abs(a).max() for a in s.vel) < 1e-12, form
