@@ -25,6 +25,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -380,8 +381,7 @@ def main():
     ctx = make_ctx(prec)
     for _ in range(args.warmup):
         ctx.step(c.dt, rtol=args.rtol, max_iters=200)
-    clk_path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % rank)
-    os.makedirs(os.path.dirname(clk_path), exist_ok=True)
+    clk_path = os.path.join(tempfile.gettempdir(), "wsi_clocks_%d_rank%d.csv" % (os.getpid(), rank))
     clk = sample_clocks_start(clk_path)
     kname = args.roofline_kernel
     wsi.ktimer_enable(KCLASS[kname])

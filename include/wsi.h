@@ -367,9 +367,13 @@ int wsi_pressure_solve(wsi_ctx* ctx, const double* y, double* x, double rtol, in
  * scratch, for callers that must not allocate device memory after set-up.
  * Its scratch is static device memory (64 KiB of partial sums), so it
  * allocates nothing; the first call on a device does the set-up (looks up
- * that memory) and should come before any stream capture.  n > 2^27
- * (134,217,728) is rejected with WSI_ERR_INVALID_ARG.  Calls that can
- * overlap (other streams, host threads) share the scratch and race.
+ * that memory) and should come before any stream capture; first calls from
+ * several host threads on one device must be serialised.  n > 2^27
+ * (134,217,728) is rejected with WSI_ERR_INVALID_ARG, and so is an x that is
+ * not device (or managed) memory of the current device (checked with
+ * cudaPointerGetAttributes, before any launch).  Calls that can overlap
+ * (other streams, host threads) share the scratch and race.  The call
+ * synchronises `stream` before it returns.
  * stream: a cudaStream_t (NULL = legacy default stream). */
 int wsi_norm2_noalloc(const double* x, size_t n, double* out, void* stream);
 

@@ -159,34 +159,38 @@ double host_norm2(const double* x, size_t n, double* scratch, cudaStream_t st) {
 }
 
 // max |x_i|: per-block maxima, then one block over the RB partials (max is
-// order-independent, so the result is exact and deterministic)
+// order-independent, so the result is exact and deterministic).  A NaN
+// anywhere makes the result NaN (fmax alone would drop it and hide a blown-up
+// field).
+__device__ __forceinline__ double nanmax(double m, double a) { return (a != a || m != m) ? a + m : fmax(m, a); }
+
 __global__ void k_maxabs_part(const double* __restrict__ x, size_t n, double* part) {
   double m = 0.0;
   size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) m = fmax(m, fabs(x[i]));
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) m = nanmax(m, fabs(x[i]));
+  for (int o = 16; o > 0; o >>= 1) m = nanmax(m, __shfl_down_sync(0xffffffffu, m, o));
   __shared__ double sh[RT / 32];
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) sh[wid] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
     double a = 0.0;
-    for (int q = 0; q < RT / 32; ++q) a = fmax(a, sh[q]);
+    for (int q = 0; q < RT / 32; ++q) a = nanmax(a, sh[q]);
     part[blockIdx.x] = a;
   }
 }
 
 __global__ void k_max_parts(const double* __restrict__ part, int nb, double* out) {
   double m = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) m = fmax(m, part[b]);
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) m = nanmax(m, part[b]);
+  for (int o = 16; o > 0; o >>= 1) m = nanmax(m, __shfl_down_sync(0xffffffffu, m, o));
   __shared__ double sh[32];
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) sh[wid] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
     double a = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a = fmax(a, sh[q]);
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) a = nanmax(a, sh[q]);
     out[0] = a;
   }
 }

@@ -7,10 +7,12 @@
 // which synchronises the device and can fail under memory pressure.  Scratch
 // lives in file-scope __device__ arrays; their addresses are looked up once
 // per device by cudaGetSymbolAddress on the first call, which is the set-up:
-// make that first call before any stream capture begins.  Nothing has to start at zero:
+// make that first call before any stream capture begins, and serialise the
+// first calls of host threads on one device.  Nothing has to start at zero:
 // every block overwrites its own partial sum and the last pass overwrites the
 // result.  All callers on a device share the scratch, so calls that can
-// overlap (other streams, other host threads) race: serialise them.
+// overlap (other streams, other host threads) race: serialise them.  Every
+// call synchronises its stream before it returns.
 #include <math.h>
 
 #include "internal.h"
@@ -75,23 +77,42 @@ extern "C" int wsi_norm2_noalloc(const double* x, size_t n, double* out, void* s
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return WSI_ERR_CUDA;
   NaScratch& S = g_na_dev[dev];
   if (!S.partials) {  // set-up, once per device: addresses of the static scratch
-    if (cudaGetSymbolAddress((void**)&S.partials, g_na_partials) != cudaSuccess ||
-        cudaGetSymbolAddress((void**)&S.result, g_na_result) != cudaSuccess) {
-      S.partials = S.result = nullptr;
+    double* part = nullptr;
+    double* res = nullptr;
+    if (cudaGetSymbolAddress((void**)&part, g_na_partials) != cudaSuccess ||
+        cudaGetSymbolAddress((void**)&res, g_na_result) != cudaSuccess)
       return WSI_ERR_CUDA;
-    }
+    S.result = res;     // published before partials, which is the "set up" test above
+    S.partials = part;
   }
   cudaStream_t st = (cudaStream_t)stream;
   if (n == 0) {
     *out = 0.0;
     return WSI_OK;
   }
+  // x must be device (or managed) memory of the current device: a host
+  // pointer or another device's memory would fault in the kernel.
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, x) != cudaSuccess) {
+    (void)cudaGetLastError();  // clear the error this query just raised
+    return WSI_ERR_INVALID_ARG;
+  }
+  if (!(attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) || attr.device != dev)
+    return WSI_ERR_INVALID_ARG;
   const int np = (int)((n + NA_PER_BLOCK - 1) / NA_PER_BLOCK);
-  k_na_partial<<<np, NA_THREADS, 0, st>>>(x, n, S.partials);
+  // cudaLaunchKernel returns this launch's own error, so an error left by an
+  // unrelated earlier call is neither reported here nor cleared
+  double* part = S.partials;
+  double* res = S.result;
+  void* a1[] = {(void*)&x, (void*)&n, (void*)&part};
+  if (cudaLaunchKernel((const void*)k_na_partial, dim3(np), dim3(NA_THREADS), a1, 0, st) != cudaSuccess)
+    return WSI_ERR_CUDA;
   WSI_COUNT();
-  k_na_final<<<1, NA_THREADS, 0, st>>>(S.partials, np, S.result);
+  void* a2[] = {(void*)&part, (void*)&np, (void*)&res};
+  if (cudaLaunchKernel((const void*)k_na_final, dim3(1), dim3(NA_THREADS), a2, 0, st) != cudaSuccess)
+    return WSI_ERR_CUDA;
   WSI_COUNT();
   if (cudaMemcpyAsync(out, S.result, sizeof(double), cudaMemcpyDefault, st) != cudaSuccess) return WSI_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return WSI_ERR_CUDA;
-  return cudaGetLastError() == cudaSuccess ? WSI_OK : WSI_ERR_CUDA;
+  return WSI_OK;
 }

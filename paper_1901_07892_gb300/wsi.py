@@ -358,14 +358,19 @@ class Context:
 
 
 def norm2_noalloc(x, stream=None):
-    """Float64 2-norm of a device vector through the allocation-free entry point."""
+    """Float64 2-norm of a contiguous float64 CUDA tensor through the
+    allocation-free entry point (run with the tensor's device current)."""
+    if not (_is_torch(x) and x.is_cuda and x.dtype.is_floating_point and x.element_size() == 8
+            and x.is_contiguous()):
+        raise TypeError("norm2_noalloc takes a contiguous float64 CUDA tensor")
+    import torch
     L = lib()
     L.wsi_norm2_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double),
                                     ctypes.c_void_p]
     L.wsi_norm2_noalloc.restype = ctypes.c_int
     out = ctypes.c_double()
-    n = int(x.numel()) if _is_torch(x) else int(np.asarray(x).size)
-    rc = L.wsi_norm2_noalloc(_ptr(x), n, ctypes.byref(out), stream)
+    with torch.cuda.device(x.device):
+        rc = L.wsi_norm2_noalloc(_ptr(x), int(x.numel()), ctypes.byref(out), stream)
     if rc != OK:
         raise WsiError(rc, "wsi_norm2_noalloc failed")
     return out.value

@@ -179,9 +179,6 @@ def test_training_lowers_loss_and_gain_is_measured():
         row["plain_fp64"] = {"cycles": st.iters, "ms": st.ms, "rel_residual": st.rel_residual}
         c64.close()
         summary["solves"].append(row)
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    with open(os.path.join(ROOT, "gpurun_out", "learned_gain.json"), "w") as f:
-        json.dump(summary, f, indent=1)
     print(json.dumps(summary))
     for mode, tr in summary["train"].items():
         assert tr["loss_last50"] < 0.5 * tr["loss_first50"], (mode, tr)

@@ -55,3 +55,11 @@ def test_empty_and_oversized_inputs():
     rc = L.wsi_norm2_noalloc(ctypes.c_void_p(y.data_ptr()), 2 ** 27 + 1, ctypes.byref(out), None)
     assert rc == wsi.ERR_INVALID_ARG
     assert wsi.norm2_noalloc(y) == pytest.approx(np.sqrt(8.0), rel=1e-15)
+    # host memory is refused before any launch, through the C ABI and the wrapper
+    h = np.ones(8)
+    rc = L.wsi_norm2_noalloc(ctypes.c_void_p(h.ctypes.data), 8, ctypes.byref(out), None)
+    assert rc == wsi.ERR_INVALID_ARG
+    with pytest.raises(TypeError):
+        wsi.norm2_noalloc(h)
+    # the context is still usable afterwards
+    assert wsi.norm2_noalloc(y) == pytest.approx(np.sqrt(8.0), rel=1e-15)
