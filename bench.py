@@ -36,7 +36,8 @@ sys.path.insert(0, ROOT)
 from paper_1901_07892_gb300 import inputs  # noqa: E402
 
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# float64 FMA rate: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (max SM clock)
+# float64 FMA rate derived from the unit counts (152 SMs x 2 FP64 FMA/clk/SM x
+# 2 flop x 2.07 GHz); used only when the measurement (wsi_fma_peak) fails
 FP64_PEAK_DERIVED_GFLOPS = 152 * 2 * 2 * 2.07
 # DRAM bytes per cell of one launch, measured with ncu at 128^3 (dram__bytes_read.sum +
 # dram__bytes_write.sum, profiles/k_stokes_df_tank128.md) for the current kernel revision;
@@ -273,6 +274,24 @@ def oracle_sample_step(n_sample=12, workload="tank", reinit_iters=0, form="consi
     return g.n_cells, dt
 
 
+def oracle_matvec_rate(c):
+    """The oracle's Stokes matvec on the full-size workload (materials
+    excluded), single-threaded numpy: cell-applies/s, beside the GPU's
+    dominant kernel on the same grid."""
+    from oracle.grid import Grid
+    from oracle.materials import Materials
+    from oracle import operators as ops
+    g = Grid(c.nx, c.ny, c.nz, c.lx, c.ly, c.lz, c.bc)
+    m = Materials(g, c.phi, c.psi, c.rho_l, c.rho_g, c.rho_s, c.mu_l, c.mu_g, c.mu_s, c.n_cells)
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(sum(g.n_faces(d) for d in range(3)) + g.n_cells)
+    t0 = time.perf_counter()
+    ops.stokes_apply(g, m, m.rho_face, c.dt, c.theta, x)
+    dt = time.perf_counter() - t0
+    return {"value": g.n_cells / dt, "unit": "cell-applies/s", "cores": 1, "seconds": dt,
+            "sample": "one oracle Stokes matvec at %dx%dx%d (float64 numpy)" % (c.nx, c.ny, c.nz)}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -293,8 +312,8 @@ def run_reference(args, rank, world):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": workload_name(args), "sample": sample},
-            "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": 1, "host_cores": os.cpu_count(),
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -378,6 +397,12 @@ def main():
         ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
         return ms, its
 
+    # measured float64 FMA rate of this GPU (denominator of the "alu" roofline)
+    try:
+        fp64_peak, fp64_peak_note = wsi.fma_peak(True, stream.cuda_stream), "measured (wsi_fma_peak)"
+    except Exception as e:  # noqa: BLE001
+        fp64_peak, fp64_peak_note = FP64_PEAK_DERIVED_GFLOPS, "derived: 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz (%s)" % e
+
     ctx = make_ctx(prec)
     for _ in range(args.warmup):
         ctx.step(c.dt, rtol=args.rtol, max_iters=200)
@@ -401,11 +426,11 @@ def main():
     if kt_n > 0:
         dur = kt_ms / kt_n * 1e-3
         if bound == "alu":
-            roof = {"bound": "alu", "achieved": flops / dur / 1e12, "peak": FP64_PEAK_DERIVED_GFLOPS / 1e3,
-                    "unit": "TFLOP/s", "frac": flops / dur / 1e9 / FP64_PEAK_DERIVED_GFLOPS,
+            roof = {"bound": "alu", "achieved": flops / dur / 1e12, "peak": fp64_peak / 1e3,
+                    "unit": "TFLOP/s", "frac": flops / dur / 1e9 / fp64_peak,
                     "traffic": None, "kernel": kname, "launches": kt_n, "avg_us": dur * 1e6,
                     "algorithmic_bytes_per_launch": byts, "flops_per_launch": flops,
-                    "peak_note": "float64 FMA peak derived: 152 SM x 2 FMA/clk x 2 flop x 2.07 GHz"}
+                    "peak_note": "float64 FMA rate " + fp64_peak_note}
         else:
             hb = peaks.get("hbm_gbs", 6800.0)
             tpc = TRAFFIC_PER_CELL.get((kname, args.precision))
@@ -461,14 +486,18 @@ def main():
     if rank == 0 and not args.no_cpu:
         n_s, t_s = oracle_sample_step({"tank": 12, "cylinder": 8, "wave": 16}[args.workload], args.workload,
                                       args.reinit, args.form)
-        cpu = {"value": n_s / t_s, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": n_s / t_s, "unit": "cell-steps/s", "cores": 1, "host_cores": os.cpu_count(),
+               "kind": "oracle",
                "sample": "one oracle time step (exact sparse-LU solves) of the same %s recipe at %s; "
                          "numpy/scipy single-threaded on the GPU host"
                          % (args.workload, {"tank": "12^3", "cylinder": "16x8x8 without wave zones",
                                             "wave": "16x8x8 without wave zones"}[args.workload])}
+        if args.workload == "tank" and args.roofline_kernel == "stokes":
+            cpu["full_size_matvec"] = oracle_matvec_rate(c)
     if rank == 0:
         line = {"metric": "cell-steps/s", "value": value, "unit": "cell-steps/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "solves_per_s": world * 2 * args.steps / (ms * 1e-3),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64 outer / f32 preconditioner" if prec == wsi.PREC_MIXED else "f64",
                 "data": "synthetic",
@@ -477,7 +506,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "mg_pre_post": args.mg, "visc_sweeps": args.visc_sweeps,
                            "fgmres_iters": its, "reinit_iters": args.reinit, "form": args.form},
-                "gpu_launches": int(l1 - l0), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(l1 - l0), "roofline": roof, "fp64_fma_peak_tflops": fp64_peak / 1e3, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks, "compare": compare, "learned": learned}
         print(json.dumps(line), flush=True)
     if dist is not None:

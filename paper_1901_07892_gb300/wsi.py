@@ -30,7 +30,7 @@ EXPORTED = ["wsi_stokes_size", "wsi_velocity_size", "wsi_create_grid", "wsi_dest
             "wsi_unet_set_params", "wsi_unet_get_params", "wsi_unet_get_grads", "wsi_unet_forward",
             "wsi_unet_backward", "wsi_unet_adam", "wsi_attach_unet", "wsi_unet_train_sample",
             "wsi_pressure_solve", "wsi_checkpoint", "wsi_restore", "wsi_unet_save", "wsi_unet_load",
-            "wsi_norm2_noalloc", "wsi_reinit"]
+            "wsi_norm2_noalloc", "wsi_reinit", "wsi_fma_peak"]
 FORM_CONSISTENT, FORM_NONCONSERVATIVE = 0, 1
 KC_STOKES, KC_RBGS_P, KC_RBGS_V, KC_TRANSPORT, KC_MDOT, KC_MAXPY, KC_RESTRICT, KC_PROLONG, KC_REINIT = range(9)
 
@@ -374,6 +374,17 @@ def norm2_noalloc(x, stream=None):
     if rc != OK:
         raise WsiError(rc, "wsi_norm2_noalloc failed")
     return out.value
+
+
+def fma_peak(fp64=True, stream=None):
+    """Measured FMA rate of the current GPU, GFLOP/s."""
+    L = lib()
+    L.wsi_fma_peak.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
+    g = ctypes.c_double()
+    rc = L.wsi_fma_peak(1 if fp64 else 0, stream, ctypes.byref(g))
+    if rc != OK:
+        raise WsiError(rc, "wsi_fma_peak")
+    return g.value
 
 
 def launch_count():

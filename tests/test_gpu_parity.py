@@ -1,9 +1,11 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 Operator applies and explicit steps: 1e-11 relative (max norm per field).
-Solves: the CUDA FGMRES runs to a relative residual of 1e-10 (well below the
-1e-8 target); fields must agree with the oracle's direct solution within
-1e-6 relative per field (p after mean removal).
+Solves: the CUDA FGMRES runs to a relative residual of 1e-10 (config 1) or
+1e-13 (the 3-D cases, whose saddle systems are far worse conditioned); fields
+must agree with the oracle's direct solution within 1e-6 relative per field
+(p after mean removal), and the oracle re-evaluates the CUDA solution's
+residual.
 """
 import numpy as np
 import pytest
@@ -163,18 +165,6 @@ def _solve_parity(c, precision, rtol=1e-10, rhs_seed=3, gravity=False, **ctx_kw)
     return errs, st, (g, m, b, xo)
 
 
-def _sensitivity(g, m, c, b, xo, rel, seed=99):
-    """Per-field relative change of the exact solution when b moves by a
-    random residual of relative 2-norm `rel`: the accuracy any solver that
-    stops at that residual can promise (the system is very ill-conditioned
-    at density ratio 1000: continuity rows are tiny next to momentum rows)."""
-    rng = np.random.default_rng(seed)
-    pert = rng.standard_normal(b.size) * g.unknown_mask()
-    pert *= rel * np.linalg.norm(b) / np.linalg.norm(pert)
-    x2 = solve_stokes(g, m, m.rho_face, c.dt, c.theta, b + pert)
-    return [_rel(a, o) for a, o in zip(g.unpack(x2), g.unpack(xo))]
-
-
 @pytest.mark.parametrize("precision", [wsi.PREC_FP64, wsi.PREC_MIXED])
 def test_solve_parity_config1_2d(precision):
     """Full config 1: 64x64 tank, flat interface, locked square solid
@@ -184,26 +174,23 @@ def test_solve_parity_config1_2d(precision):
     assert errs[0] < FIELD_TOL and errs[1] < FIELD_TOL and errs[3] < FIELD_TOL, errs
 
 
-def _check_calibrated(c, precision, rtol, gravity):
-    errs, st, (g, m, b, xo) = _solve_parity(c, precision, rtol=rtol, gravity=gravity)
-    sens = _sensitivity(g, m, c, b, xo, max(st.rel_residual, 1e-15))
-    for e, s in zip(errs, sens):
-        # within 1e-6, or within 20x of what the attained residual determines
-        assert e < max(FIELD_TOL, 20.0 * s), (errs, sens)
-
-
 @pytest.mark.parametrize("precision", [wsi.PREC_FP64, wsi.PREC_MIXED])
 def test_solve_parity_3d_ragged(precision):
     """40 x 20 x 4 spans two 32-wide x tiles and three 8-high y tiles, both
-    with ragged tails; wavy surface and a box solid; seeded velocity RHS."""
+    with ragged tails; wavy surface and a box solid; seeded velocity RHS.
+    Solved to 1e-13, so that the ill-conditioned saddle system (a 1e-10
+    residual moves p by ~3.5e-6 at this density ratio) still pins every
+    field to 1e-6."""
     c = inputs.tank3d(nxyz=(40, 20, 4), seed=5, dt=5e-4)
-    _check_calibrated(c, precision, 1e-10, False)
+    errs, st, _ = _solve_parity(c, precision, rtol=1e-13)
+    assert max(errs) < FIELD_TOL, errs
 
 
 @pytest.mark.parametrize("precision", [wsi.PREC_FP64, wsi.PREC_MIXED])
 def test_solve_parity_gravity_dominated(precision):
     c = inputs.tank3d(nxyz=(40, 20, 4), seed=6, dt=5e-4)
-    _check_calibrated(c, precision, 1e-13, True)
+    errs, st, _ = _solve_parity(c, precision, rtol=1e-13, gravity=True)
+    assert max(errs) < FIELD_TOL, errs
 
 
 @pytest.mark.parametrize("precision", [wsi.PREC_FP64, wsi.PREC_MIXED])
@@ -211,13 +198,13 @@ def test_solve_parity_viscous_multigrid(precision):
     """Viscosity-dominated tank (mu_l = 1, mu_g = 0.1, dt = 0.05: in the air
     mu/h^2 is four times rho/dt, so red-black sweeps alone converge slowly):
     the projection preconditioner with viscous V-cycles reaches the exact
-    solution (oracle's sparse LU) in fewer FGMRES iterations than with sweeps."""
+    solution (oracle's sparse LU) to 1e-6 per field, in fewer FGMRES
+    iterations than with sweeps (both compared at 1e-10)."""
     c = inputs.tank3d(nxyz=(32, 16, 8), seed=8, dt=0.05)
     c.mu_l, c.mu_g, c.mu_s = 1.0, 0.1, 1.0
-    errs, st_mg, (g, m, b, xo) = _solve_parity(c, precision, rtol=1e-10, visc_mg=2)
-    sens = _sensitivity(g, m, c, b, xo, max(st_mg.rel_residual, 1e-15))
-    for e, s in zip(errs, sens):
-        assert e < max(FIELD_TOL, 20.0 * s), (errs, sens)
+    errs, _, _ = _solve_parity(c, precision, rtol=1e-13, visc_mg=2)
+    assert max(errs) < FIELD_TOL, errs
+    _, st_mg, _ = _solve_parity(c, precision, rtol=1e-10, visc_mg=2)
     _, st_sw, _ = _solve_parity(c, precision, rtol=1e-10)
     assert st_mg.iters < st_sw.iters, (st_mg.iters, st_sw.iters)
 
