@@ -171,3 +171,31 @@ def test_lm_force_of_a_body_at_rest_in_a_tank_at_rest():
     s = ost.State(g, pr, c.phi, c.psi, ost.Body(c.markers, c.dV, [True] * 6, half=c.box_half))
     info = ost.step(s, c.dt)
     assert np.abs(info["F_lm"]).max() < 1e-6
+
+
+def test_box_sdf_closed_forms():
+    """The structure level set of a box (Sec. 4.1: the signed distance of
+    the body about its centre): at hand-picked cell centres inside, beyond a
+    face, beyond an edge and beyond a corner; and at every cell centre
+    against the geometric definition (outside: the distance to the nearest
+    point of the box, its clamp; inside: minus the distance to the nearest
+    face)."""
+    g = Grid(8, 8, 8)
+    c = np.array([0.5, 0.5, 0.5])
+    a = np.array([0.125, 0.25, 0.375])
+    psi = levelset.box_sdf(g, c, a)
+    # cell (i, j, k) is centred at ((i + 1/2)/8, ...); psi is indexed [k, j, i]
+    assert psi[4, 4, 4] == pytest.approx(-0.0625, abs=1e-15)              # inside, nearest the x faces
+    assert psi[4, 4, 7] == pytest.approx(0.3125, abs=1e-15)               # beyond the x+ face
+    assert psi[4, 7, 7] == pytest.approx(np.hypot(0.3125, 0.1875), abs=1e-15)   # beyond the x+/y+ edge
+    assert psi[7, 7, 7] == pytest.approx(np.sqrt(0.3125 ** 2 + 0.1875 ** 2 + 0.0625 ** 2), abs=1e-15)
+    assert psi[0, 0, 0] == pytest.approx(np.sqrt(0.3125 ** 2 + 0.1875 ** 2 + 0.0625 ** 2), abs=1e-15)
+    lo, hi = c - a, c + a
+    x, y, z = np.broadcast_arrays(*g.cell_centers())
+    p = np.stack([x, y, z], axis=-1)
+    inside = np.all((p > lo) & (p < hi), axis=-1)
+    outside_d = np.linalg.norm(p - np.clip(p, lo, hi), axis=-1)
+    inside_d = np.minimum(p - lo, hi - p).min(axis=-1)
+    ref = np.where(inside, -inside_d, outside_d)
+    assert np.abs(psi - ref).max() < 1e-15
+    assert inside.any() and (~inside).any()
