@@ -391,12 +391,14 @@ int wsi_ktimer_enable(int kernel_class);
 int wsi_ktimer_read(double* total_ms, long long* launches);
 
 /* Measured fused multiply-add rate of the current GPU in GFLOP/s (2 flop per
- * FMA), float64 (fp64 != 0) or float32: eight independent register FMA
+ * FMA): fp64 = 1 float64, 0 float32, 2 float32 issued as packed pairs
+ * (fma.rn.f32x2, sm_100 and later); eight independent register FMA
  * chains per thread, 8 blocks of 256 threads per SM, best of three ~60 ms
  * launches after a warm-up, timed with CUDA events on `stream`.  The
  * denominator of the roofline of kernels bound by arithmetic issue.  No
  * counterpart in the paper.  Allocates (and frees) a small device buffer;
- * synchronises `stream`.  Errors: WSI_ERR_INVALID_ARG (null gflops),
+ * synchronises `stream`.  Errors: WSI_ERR_INVALID_ARG (null gflops, fp64
+ * outside 0..2),
  * WSI_ERR_OOM, WSI_ERR_CUDA. */
 int wsi_fma_peak(int fp64, void* stream, double* gflops);
 

@@ -376,12 +376,13 @@ def norm2_noalloc(x, stream=None):
     return out.value
 
 
-def fma_peak(fp64=True, stream=None):
-    """Measured FMA rate of the current GPU, GFLOP/s."""
+def fma_peak(fp64=True, stream=None, packed=False):
+    """Measured FMA rate of the current GPU, GFLOP/s (float64, float32, or
+    float32 issued as packed pairs)."""
     L = lib()
     L.wsi_fma_peak.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
     g = ctypes.c_double()
-    rc = L.wsi_fma_peak(1 if fp64 else 0, stream, ctypes.byref(g))
+    rc = L.wsi_fma_peak(2 if packed else (1 if fp64 else 0), stream, ctypes.byref(g))
     if rc != OK:
         raise WsiError(rc, "wsi_fma_peak")
     return g.value

@@ -186,11 +186,32 @@ def test_solve_parity_3d_ragged(precision):
     assert max(errs) < FIELD_TOL, errs
 
 
+def _sensitivity(g, m, c, b, xo, rel, seed=99):
+    """Per-field relative change of the exact solution when b moves by a
+    random residual of relative 2-norm `rel`: the accuracy any solver that
+    stops at that residual can promise."""
+    rng = np.random.default_rng(seed)
+    pert = rng.standard_normal(b.size) * g.unknown_mask()
+    pert *= rel * np.linalg.norm(b) / np.linalg.norm(pert)
+    x2 = solve_stokes(g, m, m.rho_face, c.dt, c.theta, b + pert)
+    return [_rel(a, o) for a, o in zip(g.unpack(x2), g.unpack(xo))]
+
+
 @pytest.mark.parametrize("precision", [wsi.PREC_FP64, wsi.PREC_MIXED])
 def test_solve_parity_gravity_dominated(precision):
+    """rho^flow g on top of the random right-hand side: the pressure gradient
+    then carries almost all of b and the velocity is a remainder ~1e-6 of
+    b's scale, so even a 1e-13 residual moves it by several 1e-6 (measured:
+    9e-6 in u on the float64 path).  The pressure, which carries b, must
+    meet 1e-6 outright; each velocity component must be within 20x of what
+    the attained residual determines (the oracle's own solution moved by a
+    random residual of that size) or within 1e-6."""
     c = inputs.tank3d(nxyz=(40, 20, 4), seed=6, dt=5e-4)
-    errs, st, _ = _solve_parity(c, precision, rtol=1e-13, gravity=True)
-    assert max(errs) < FIELD_TOL, errs
+    errs, st, (g, m, b, xo) = _solve_parity(c, precision, rtol=1e-13, gravity=True)
+    assert errs[3] < FIELD_TOL, errs
+    sens = _sensitivity(g, m, c, b, xo, max(st.rel_residual, 1e-15))
+    for e, s in zip(errs[:3], sens[:3]):
+        assert e < max(FIELD_TOL, 20.0 * s), (errs, sens)
 
 
 @pytest.mark.parametrize("precision", [wsi.PREC_FP64, wsi.PREC_MIXED])
