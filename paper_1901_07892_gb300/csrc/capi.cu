@@ -266,11 +266,12 @@ void pc_apply(wsi_ctx* c, double dt, const double* v, double* z) {
     precond_apply<double>(c->P64, c->g, c->opts, dt, v, z, c->st);
 }
 
-// split copies of the coefficients for the double-float matvec (mixed path)
-void df_coef_refresh(wsi_ctx* c, const Coef<double>& cf) {
+// split copies of the coefficients for the double-float matvec (mixed path);
+// the face density is stored times 1/dt
+void df_coef_refresh(wsi_ctx* c, const Coef<double>& cf, double inv_dt) {
   if (!c->mixed()) return;
   for (int d = 0; d < 3; ++d) {
-    launch_df_split(cf.rho_face[d], c->df_rho[d], fsize(c->g, d), c->st);
+    launch_df_split_scaled(cf.rho_face[d], inv_dt, c->df_rho[d], fsize(c->g, d), c->st);
     launch_df_split(cf.mu_e[d], c->df_mu_e[d], esize(c->g, d), c->st);
   }
   launch_df_split(cf.mu_cc, c->df_mu_cc, c->ncell, c->st);
@@ -288,8 +289,9 @@ void stokes_mv(wsi_ctx* c, const Coef<double>& cf, double inv_dt, double theta, 
       dc.mu_e[d] = c->df_mu_e[d];
     }
     dc.mu_cc = c->df_mu_cc;
+    (void)inv_dt;  // folded into the split face density by df_coef_refresh
     launch_df_split(x, c->df_x, c->nstk, st);
-    launch_stokes_df(c->g, dc, inv_dt, theta, c->df_x, y, st);
+    launch_stokes_df(c->g, dc, theta, c->df_x, y, st);
   } else {
     launch_stokes(c->g, cf, inv_dt, theta, x, y, st);
   }
@@ -305,7 +307,7 @@ int fgmres(wsi_ctx* c, const double* b, double* x, double dt, const wsi_solve_op
   const int m = c->m;
   const double inv_dt = 1.0 / dt, theta = c->desc.theta;
   Coef<double> cf = coef_now(c);
-  df_coef_refresh(c, cf);
+  df_coef_refresh(c, cf, inv_dt);
   double* V = c->V;
   double* Z = c->Z;
   double* hd = c->hdev;
@@ -1218,7 +1220,7 @@ int wsi_apply(wsi_ctx* c, int op, const double* in, double* out, double dt) {
   vel_parts(c, xout, qo);
   switch (op) {
     case WSI_OP_STOKES:
-      df_coef_refresh(c, cf);
+      df_coef_refresh(c, cf, 1.0 / dt);
       stokes_mv(c, cf, 1.0 / dt, c->desc.theta, xin, xout, c->st);
       break;
     case WSI_OP_VISCOUS: launch_viscous<double>(c->g, cf, 1.0 / dt, c->desc.theta, qi, qo, c->st, false); break;

@@ -130,6 +130,40 @@ __device__ __forceinline__ dfl df_sqrt(dfl x) {
   return quick_two_sum(s, d.h / (2.0f * s));
 }
 
+// Unnormalised head/tail pairs: a value is h + t with the head h formed
+// error-free (exact differences by Knuth's two-sum, exact products by fused
+// multiply-add) and everything smaller gathered in the float32 tail t,
+// which is never renormalised.  Each operation errs by about 2^-24 of the
+// tail, i.e. ~2^-46 of its operands' magnitude, like a float64 operation on
+// 47-bit inputs; skipping the renormalisation after every step saves three
+// instructions per operation.
+struct ht {
+  float h, t;
+};
+__device__ __forceinline__ ht ht_of(float2 v) { return ht{v.x, v.y}; }
+__device__ __forceinline__ ht ht_sub(ht a, ht b) {
+  float s, e;
+  two_sum(a.h, -b.h, s, e);
+  return ht{s, e + (a.t - b.t)};
+}
+__device__ __forceinline__ ht ht_add(ht a, ht b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  return ht{s, e + (a.t + b.t)};
+}
+// a * c: exact head product, the two cross terms in float32 (t * t dropped)
+__device__ __forceinline__ ht ht_mul(ht a, ht c) {
+  const float p = a.h * c.h;
+  const float e = fmaf(a.h, c.h, -p);
+  return ht{p, fmaf(a.h, c.t, fmaf(a.t, c.h, e))};
+}
+// a * c for a grid constant c: exact scaling when c is a power of two
+__device__ __forceinline__ ht ht_k(ht a, ht c, bool pow2) {
+  return pow2 ? ht{a.h * c.h, a.t * c.h} : ht_mul(a, c);
+}
+__device__ __forceinline__ ht ht_sgn(ht a, float s) { return ht{a.h * s, a.t * s}; }
+__device__ __forceinline__ double ht_dbl(ht a) { return f2d_exact(a.h) + f2d_exact(a.t); }
+
 // largest integer <= x (x well inside the int range)
 __device__ __forceinline__ int df_floor(dfl x) {
   const float f = floorf(x.h);

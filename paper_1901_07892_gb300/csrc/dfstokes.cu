@@ -1,19 +1,26 @@
 // Stokes matvec of the mixed path in double-float arithmetic.
 //
-// GB300 issues float64 arithmetic at about 1/64 of its float32 rate, and the
-// float64 Stokes matvec (about 130 float64 operations per cell) is the
-// largest single kernel of a time step.  Here every row
+// GB300 issues float64 arithmetic at about 1/64 of its float32 rate, so
 //     y_u = (rho/dt) q + G p - theta L_mu q,    y_p = -D q
-// is evaluated with unevaluated float32 pairs (hi + lo): Dekker's exact
-// product via fused multiply-add and Knuth's error-free sum of the leading
-// parts (the trailing parts are added plainly, an error of ~2^-46 of the
-// operands' magnitude, the class of a float64 operation on rounded inputs).
-// The operands are split into (hi, lo) float32 pairs by integer operations
-// on their bit patterns (47 significant bits kept) in separate streaming
-// passes: the coefficients once per solve, the input vector once per
-// matvec; the matvec then reads pairs (8 bytes, as many as a float64) and
-// issues no split.  The float64 pipe sees one addition per row, which forms
-// the float64 result.
+// (Sec. 4.2.2) is evaluated on unnormalised float32 head/tail pairs
+// (df.cuh: exact head differences and products, tails in plain float32;
+// ~2^-46 of the operands' magnitude per operation), from operands split
+// into (hi, lo) pairs by integer operations in streaming passes: the
+// coefficients once per solve (with 1/dt folded into the face density), the
+// input vector once per matvec.  One float64 addition per row forms the
+// result.
+//
+// Flux form, marched along z.  L_mu q is the divergence of the stress:
+// normal stresses 2 mu_cc dq_c/dx_c at cells and shear stresses
+// mu_e (dq_c/dx_d + dq_d/dx_c) on edges.  Each is formed once per cell by one
+// thread and shared: with the x-neighbours of its warp by shuffles (a warp
+// covers 32 consecutive x-positions and writes the rows of the 30 inner
+// ones), with the next z-level by keeping it in registers while the thread
+// marches up its column of KC cells.  Only the y-neighbours' stresses are
+// formed twice.  Compared with evaluating every row on its own (each shear
+// stress four times), this is about half the float32 instructions.
+// Tangential ghosts across walls follow the wall's sign; faces on walls hold
+// zero and their rows are written as zero.
 // Magnitudes below 2^-126 ~ 1.2e-38 are flushed to zero, and below 2^-103
 // only their leading 24 bits are kept.  Array offsets are 32-bit: every
 // array holds fewer than 2^31 elements (checked when the grid is created).
@@ -27,101 +34,207 @@
 
 namespace wsi {
 
-static constexpr int BX = 32, BY = 8;
+static constexpr int FX = 30;  // x-positions written per warp (32 lanes, one halo lane each side)
+static constexpr int FBY = 4;  // warps (y-rows) per block
+static constexpr int FKC = 16; // z-levels per thread
 
-struct DfConst {
-  dfl ih[3];       // 1/h
-  dfl two_ih2[3];  // 2/h^2
-  dfl inv_dt;
-  dfl mtheta;      // -theta
-  unsigned pw;     // bit set: that constant is a power of two (bits 0-2 ih, 3-5 two_ih2, 6 mtheta, 7 inv_dt)
-  float bcs[6];    // tangential ghost sign per wall
-  int fs[3][3];    // strides of face array C along each axis
-  int cs[3];       // strides of the cell arrays
-  int es[3][3];    // strides of edge array E
+struct HtConst {
+  ht ih[3];       // 1/h
+  ht two_ih2[3];  // 2/h^2
+  ht mtheta;      // -theta
+  unsigned pw;    // power-of-two flags: bits 0-2 ih, 3-5 two_ih2, 6 mtheta
+  float bcs[6];   // tangential ghost sign per wall (x-, x+, y-, y+, z-, z+)
+  int n[3];
 };
 
-__device__ __forceinline__ dfl ldp(const float2* __restrict__ a, int i) {
-  const float2 v = __ldg(a + i);
-  dfl r;
-  r.h = v.x;
-  r.l = v.y;
-  return r;
+__device__ __forceinline__ ht ldh(const float2* __restrict__ a, int i) { return ht_of(__ldg(a + i)); }
+
+__device__ __forceinline__ ht shfl_up1(ht a) {
+  return ht{__shfl_up_sync(0xffffffffu, a.h, 1), __shfl_up_sync(0xffffffffu, a.t, 1)};
+}
+__device__ __forceinline__ ht shfl_down1(ht a) {
+  return ht{__shfl_down_sync(0xffffffffu, a.h, 1), __shfl_down_sync(0xffffffffu, a.t, 1)};
 }
 
-// momentum row C at the interior C-face (i, j, kk); all operands pre-split
-template <int C>
-__device__ __forceinline__ double row_df(const GridDev& g, const DfConst& k, const DfCoef& cf, const DfVec& x, int i,
-                                         int j, int kk) {
-  const int id3[3] = {i, j, kk};
-  const int fb = i + j * k.fs[C][1] + kk * k.fs[C][2];
-  const int cb = i + j * k.cs[1] + kk * k.cs[2];  // the cell on the + side of the face
-  const float2* __restrict__ qc = x.q[C];
-  const int sC = k.fs[C][C];
-  const dfl q0 = ldp(qc, fb);
-  const dfl qp = ldp(qc, fb + sC), qm = ldp(qc, fb - sC);
-  const dfl muh = ldp(cf.mu_cc, cb), mul = ldp(cf.mu_cc, cb - k.cs[C]);
-  dfl L = df_mulc(df_sub(df_mul(muh, df_sub(qp, q0)), df_mul(mul, df_sub(q0, qm))), k.two_ih2[C], (k.pw >> (3 + C)) & 1);
-#pragma unroll
-  for (int D = 0; D < 3; ++D) {
-    if (D == C) continue;
-    const int E = edge_id(C, D);
-    const int sD = k.fs[C][D];
-    dfl qh, ql;
-    if (id3[D] + 1 < g.n[D]) {
-      qh = ldp(qc, fb + sD);
+// rho/dt q + G p - theta L as a float64
+__device__ __forceinline__ double row_out(const HtConst& K, ht rq, ht gp, ht L) {
+  return ht_dbl(ht_add(ht_add(rq, gp), ht_k(L, K.mtheta, (K.pw >> 6) & 1)));
+}
+
+__global__ void __launch_bounds__(32 * FBY) k_stokes_df(HtConst K, DfCoef cf, DfVec x, double* yu, double* yv,
+                                                        double* yw, double* yp) {
+  const int nx = K.n[0], ny = K.n[1], nz = K.n[2];
+  const int lane = threadIdx.x;
+  const int i = blockIdx.x * FX + lane - 1;
+  const int j = blockIdx.y * FBY + threadIdx.y;
+  if (j >= ny) return;  // uniform over the warp
+  const int k0 = blockIdx.z * FKC;
+  const int k1 = min(k0 + FKC, nz);
+  const bool cI = i >= 0 && i < nx;  // a cell column
+  const bool fI = i >= 0 && i <= nx; // an x-face / x-edge column
+  const bool lane_rows = lane >= 1 && lane <= FX;
+  const int ic = clampi(i, 0, nx - 1), iff = clampi(i, 0, nx), icm = clampi(i - 1, 0, nx - 1);
+  const bool hiX = i >= nx, loX = i - 1 < 0;  // column i / i-1 outside the cells: x-ghost
+  // strides
+  const int su1 = nx + 1, su2 = (nx + 1) * ny;  // u faces
+  const int sv1 = nx, sv2 = nx * (ny + 1);      // v faces
+  const int sc1 = nx, sc2 = nx * ny;            // cells, w faces
+  const int sxy1 = nx + 1, sxy2 = (nx + 1) * (ny + 1);
+  const int sxz1 = nx + 1, sxz2 = (nx + 1) * ny;
+  const int syz1 = nx, syz2 = nx * (ny + 1);
+  const float bxl = K.bcs[0], bxh = K.bcs[1], byl = K.bcs[2], byh = K.bcs[3], bzl = K.bcs[4], bzh = K.bcs[5];
+  const bool pxk = K.pw & 1, pyk = (K.pw >> 1) & 1, pzk = (K.pw >> 2) & 1;
+  const float2* __restrict__ U = x.q[0];
+  const float2* __restrict__ V = x.q[1];
+  const float2* __restrict__ W = x.q[2];
+  const float2* __restrict__ P = x.p;
+  const ht ihx = K.ih[0], ihy = K.ih[1], ihz = K.ih[2];
+
+  // w at (column i or its x-ghost, row jj or its y-ghost, level kk in 0..nz)
+  auto w_at = [&](int col_i, bool xghost, float xs, int jj, int kk) -> ht {
+    float s = xghost ? xs : 1.f;
+    if (jj < 0) { jj = 0; s *= byl; } else if (jj >= ny) { jj = ny - 1; s *= byh; }
+    return ht_sgn(ldh(W, col_i + jj * sc1 + kk * sc2), s);
+  };
+  // shear stresses on the z-level kk edges (0 <= kk <= nz) from the fields at
+  // levels kk - 1 (lo) and kk (hi), ghosts already applied:
+  // xz at (i, j), yz at (i, j) and at (i, j + 1)
+  auto zedges = [&](int kk, ht u_lo, ht u_hi, ht v_lo, ht v_hi, ht vj_lo, ht vj_hi, ht& txz, ht& tyz, ht& tyzj) {
+    const ht wc = w_at(ic, hiX, bxh, j, kk);      // w at column i (x-edge column; ghost at i = nx)
+    const ht wm = w_at(icm, loX, bxl, j, kk);     // w at column i - 1
+    const ht wjm = w_at(ic, false, 1.f, j - 1, kk);
+    const ht wjp = w_at(ic, false, 1.f, j + 1, kk);
+    const ht w0 = ldh(W, ic + j * sc1 + kk * sc2);
+    txz = ht_mul(ldh(cf.mu_e[1], iff + j * sxz1 + kk * sxz2),
+                 ht_add(ht_k(ht_sub(u_hi, u_lo), ihz, pzk), ht_k(ht_sub(wc, wm), ihx, pxk)));
+    tyz = ht_mul(ldh(cf.mu_e[2], ic + j * syz1 + kk * syz2),
+                 ht_add(ht_k(ht_sub(v_hi, v_lo), ihz, pzk), ht_k(ht_sub(w0, wjm), ihy, pyk)));
+    tyzj = ht_mul(ldh(cf.mu_e[2], ic + (j + 1) * syz1 + kk * syz2),
+                  ht_add(ht_k(ht_sub(vj_hi, vj_lo), ihz, pzk), ht_k(ht_sub(wjp, w0), ihy, pyk)));
+  };
+
+  // ---- prologue: fields at level k0, z-edges at level k0, stresses of k0 - 1
+  ht u_k = ldh(U, iff + j * su1 + k0 * su2);
+  ht v_k = ldh(V, ic + j * sv1 + k0 * sv2);
+  ht vj_k = ldh(V, ic + (j + 1) * sv1 + k0 * sv2);
+  ht w_k = ldh(W, ic + j * sc1 + k0 * sc2);
+  ht txz_k, tyz_k, tyzj_k;
+  ht nzz_km1{0.f, 0.f}, p_km1{0.f, 0.f};
+  {
+    ht u_m, v_m, vj_m;
+    if (k0 > 0) {
+      u_m = ldh(U, iff + j * su1 + (k0 - 1) * su2);
+      v_m = ldh(V, ic + j * sv1 + (k0 - 1) * sv2);
+      vj_m = ldh(V, ic + (j + 1) * sv1 + (k0 - 1) * sv2);
+      const ht w_m = ldh(W, ic + j * sc1 + (k0 - 1) * sc2);
+      nzz_km1 = ht_mul(ldh(cf.mu_cc, ic + j * sc1 + (k0 - 1) * sc2), ht_sub(w_k, w_m));
+      p_km1 = ldh(P, ic + j * sc1 + (k0 - 1) * sc2);
     } else {
-      qh = k.bcs[2 * D + 1] < 0.0f ? df_neg(q0) : q0;
+      u_m = ht_sgn(u_k, bzl);
+      v_m = ht_sgn(v_k, bzl);
+      vj_m = ht_sgn(vj_k, bzl);
     }
-    if (id3[D] > 0) {
-      ql = ldp(qc, fb - sD);
-    } else {
-      ql = k.bcs[2 * D] < 0.0f ? df_neg(q0) : q0;
-    }
-    const int eb = i + j * k.es[E][1] + kk * k.es[E][2];
-    const dfl meh = ldp(cf.mu_e[E], eb + k.es[E][D]), mel = ldp(cf.mu_e[E], eb);
-    const float2* __restrict__ qd = x.q[D];
-    const int db = i + j * k.fs[D][1] + kk * k.fs[D][2];
-    const int dD = k.fs[D][D], dC = k.fs[D][C];
-    const dfl a1 = ldp(qd, db + dD), a0 = ldp(qd, db + dD - dC);
-    const dfl b1 = ldp(qd, db), b0 = ldp(qd, db - dC);
-    const bool pD = (k.pw >> D) & 1, pC = (k.pw >> C) & 1;
-    const dfl fh = df_mul(meh, df_add(df_mulc(df_sub(qh, q0), k.ih[D], pD), df_mulc(df_sub(a1, a0), k.ih[C], pC)));
-    const dfl fl = df_mul(mel, df_add(df_mulc(df_sub(q0, ql), k.ih[D], pD), df_mulc(df_sub(b1, b0), k.ih[C], pC)));
-    L = df_add(L, df_mulc(df_sub(fh, fl), k.ih[D], pD));
+    zedges(k0, u_m, u_k, v_m, v_k, vj_m, vj_k, txz_k, tyz_k, tyzj_k);
   }
-  const dfl rq = df_mul(df_mulc(ldp(cf.rho_face[C], fb), k.inv_dt, (k.pw >> 7) & 1), q0);
-  const dfl gp = df_mulc(df_sub(ldp(x.p, cb), ldp(x.p, cb - k.cs[C])), k.ih[C], (k.pw >> C) & 1);
-  return df_to_double(df_add(df_add(rq, gp), df_mulc(L, k.mtheta, (k.pw >> 6) & 1)));
-}
 
-template <int C>
-__device__ __forceinline__ void stokes_row_df(const GridDev& g, const DfConst& k, const DfCoef& cf, const DfVec& x,
-                                              double* out, int i, int j, int kk) {
-  const int id3[3] = {i, j, kk};
-  const int fb = i + j * k.fs[C][1] + kk * k.fs[C][2];
-  out[fb] = (id3[C] == 0 || id3[C] == g.n[C]) ? 0.0 : row_df<C>(g, k, cf, x, i, j, kk);
-}
+  for (int k = k0; k < k1; ++k) {
+    const int kp = k + 1;
+    // ---- level k + 1: fields and z-edge shear stresses
+    ht u_kp, v_kp, vj_kp;
+    if (kp < nz) {
+      u_kp = ldh(U, iff + j * su1 + kp * su2);
+      v_kp = ldh(V, ic + j * sv1 + kp * sv2);
+      vj_kp = ldh(V, ic + (j + 1) * sv1 + kp * sv2);
+    } else {
+      u_kp = ht_sgn(u_k, bzh);
+      v_kp = ht_sgn(v_k, bzh);
+      vj_kp = ht_sgn(vj_k, bzh);
+    }
+    const ht w_kp = ldh(W, ic + j * sc1 + kp * sc2);
+    ht txz_kp, tyz_kp, tyzj_kp;
+    zedges(kp, u_k, u_kp, v_k, v_kp, vj_k, vj_kp, txz_kp, tyz_kp, tyzj_kp);
 
-// One thread per (i, j, k) evaluates the u-, v-, w- and p-rows there, so the
-// blocks resident at a time work on the same few z-planes of every array and
-// each array comes from DRAM about once.
-__global__ void __launch_bounds__(256) k_stokes_df(GridDev g, DfConst k, DfCoef cf, DfVec x, double* yu, double* yv,
-                                                   double* yw, double* yp) {
-  const int kk = blockIdx.z;
-  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
-  if (i <= n0 && j < n1 && kk < n2) stokes_row_df<0>(g, k, cf, x, yu, i, j, kk);
-  if (i < n0 && j <= n1 && kk < n2) stokes_row_df<1>(g, k, cf, x, yv, i, j, kk);
-  if (i < n0 && j < n1 && kk <= n2) stokes_row_df<2>(g, k, cf, x, yw, i, j, kk);
-  if (i < n0 && j < n1 && kk < n2) {
-    const int f0 = i + j * k.fs[0][1] + kk * k.fs[0][2];
-    const int f1 = i + j * k.fs[1][1] + kk * k.fs[1][2];
-    const int f2 = i + j * k.fs[2][1] + kk * k.fs[2][2];
-    const dfl dx = df_mulc(df_sub(ldp(x.q[0], f0 + 1), ldp(x.q[0], f0)), k.ih[0], k.pw & 1);
-    const dfl dy = df_mulc(df_sub(ldp(x.q[1], f1 + k.fs[1][1]), ldp(x.q[1], f1)), k.ih[1], (k.pw >> 1) & 1);
-    const dfl dz = df_mulc(df_sub(ldp(x.q[2], f2 + k.fs[2][2]), ldp(x.q[2], f2)), k.ih[2], (k.pw >> 2) & 1);
-    yp[i + j * k.cs[1] + kk * k.cs[2]] = -df_to_double(df_add(df_add(dx, dy), dz));
+    // ---- level k: normal stresses and the xy shear stresses at rows j, j + 1
+    const int cb = ic + j * sc1 + k * sc2;
+    const ht mu_c = ldh(cf.mu_cc, cb);
+    const ht u_ip = ldh(U, clampi(i + 1, 0, nx) + j * su1 + k * su2);
+    const ht nxx = ht_mul(mu_c, ht_sub(u_ip, u_k));
+    const ht nyy = ht_mul(mu_c, ht_sub(vj_k, v_k));
+    const ht nzz = ht_mul(mu_c, ht_sub(w_kp, w_k));
+    ht nyy_m{0.f, 0.f};
+    if (j > 0) nyy_m = ht_mul(ldh(cf.mu_cc, cb - sc1), ht_sub(v_k, ldh(V, ic + (j - 1) * sv1 + k * sv2)));
+    // u at rows j - 1, j + 1 of column i (y-ghosts)
+    const ht u_jm = j > 0 ? ldh(U, iff + (j - 1) * su1 + k * su2) : ht_sgn(u_k, byl);
+    const ht u_jp = j + 1 < ny ? ldh(U, iff + (j + 1) * su1 + k * su2) : ht_sgn(u_k, byh);
+    // v at columns i, i - 1 of rows j, j + 1 (x-ghosts)
+    const ht vx = hiX ? ht_sgn(v_k, bxh) : v_k;
+    const ht vjx = hiX ? ht_sgn(vj_k, bxh) : vj_k;
+    const ht vm = ht_sgn(ldh(V, icm + j * sv1 + k * sv2), loX ? bxl : 1.f);
+    const ht vjm = ht_sgn(ldh(V, icm + (j + 1) * sv1 + k * sv2), loX ? bxl : 1.f);
+    const int eb = iff + j * sxy1 + k * sxy2;
+    const ht txy = ht_mul(ldh(cf.mu_e[0], eb), ht_add(ht_k(ht_sub(u_k, u_jm), ihy, pyk), ht_k(ht_sub(vx, vm), ihx, pxk)));
+    const ht txyj =
+        ht_mul(ldh(cf.mu_e[0], eb + sxy1), ht_add(ht_k(ht_sub(u_jp, u_k), ihy, pyk), ht_k(ht_sub(vjx, vjm), ihx, pxk)));
+
+    // ---- neighbours along x from the adjacent lanes
+    const ht nxx_im = shfl_up1(nxx);
+    const ht txy_ip = shfl_down1(txy);
+    const ht txz_ip = shfl_down1(txz_k);
+
+    const ht p_k = ldh(P, cb);
+    if (lane_rows && fI) {
+      // u-row at x-face i
+      double out = 0.0;
+      if (i > 0 && i < nx) {
+        const ht L = ht_add(ht_add(ht_k(ht_sub(nxx, nxx_im), K.two_ih2[0], (K.pw >> 3) & 1),
+                                   ht_k(ht_sub(txyj, txy), ihy, pyk)),
+                            ht_k(ht_sub(txz_kp, txz_k), ihz, pzk));
+        const ht rq = ht_mul(ldh(cf.rho_face[0], iff + j * su1 + k * su2), u_k);
+        const ht gp = ht_k(ht_sub(p_k, ldh(P, cb - 1)), ihx, pxk);
+        out = row_out(K, rq, gp, L);
+      }
+      yu[iff + j * su1 + k * su2] = out;
+    }
+    if (lane_rows && cI) {
+      // v-row at y-face j (face 0 and face ny are walls)
+      double out = 0.0;
+      if (j > 0) {
+        const ht L = ht_add(ht_add(ht_k(ht_sub(nyy, nyy_m), K.two_ih2[1], (K.pw >> 4) & 1),
+                                   ht_k(ht_sub(txy_ip, txy), ihx, pxk)),
+                            ht_k(ht_sub(tyz_kp, tyz_k), ihz, pzk));
+        const ht rq = ht_mul(ldh(cf.rho_face[1], ic + j * sv1 + k * sv2), v_k);
+        const ht gp = ht_k(ht_sub(p_k, ldh(P, cb - sc1)), ihy, pyk);
+        out = row_out(K, rq, gp, L);
+      }
+      yv[ic + j * sv1 + k * sv2] = out;
+      if (j == ny - 1) yv[ic + ny * sv1 + k * sv2] = 0.0;
+      // w-row at z-face k (face 0 and face nz are walls)
+      out = 0.0;
+      if (k > 0) {
+        const ht L = ht_add(ht_add(ht_k(ht_sub(nzz, nzz_km1), K.two_ih2[2], (K.pw >> 5) & 1),
+                                   ht_k(ht_sub(txz_ip, txz_k), ihx, pxk)),
+                            ht_k(ht_sub(tyzj_k, tyz_k), ihy, pyk));
+        const ht rq = ht_mul(ldh(cf.rho_face[2], cb), w_k);
+        const ht gp = ht_k(ht_sub(p_k, p_km1), ihz, pzk);
+        out = row_out(K, rq, gp, L);
+      }
+      yw[cb] = out;
+      if (k == nz - 1) yw[cb + sc2] = 0.0;
+      // continuity row at the cell
+      const ht dq = ht_add(ht_add(ht_k(ht_sub(u_ip, u_k), ihx, pxk), ht_k(ht_sub(vj_k, v_k), ihy, pyk)),
+                           ht_k(ht_sub(w_kp, w_k), ihz, pzk));
+      yp[cb] = -ht_dbl(dq);
+    }
+    // ---- carry to level k + 1
+    u_k = u_kp;
+    v_k = v_kp;
+    vj_k = vj_kp;
+    w_k = w_kp;
+    txz_k = txz_kp;
+    tyz_k = tyz_kp;
+    tyzj_k = tyzj_kp;
+    nzz_km1 = nzz;
+    p_km1 = p_k;
   }
 }
 
@@ -140,6 +253,21 @@ void launch_df_split(const double* x, float2* out, size_t n, cudaStream_t st) {
   { k_df_split<<<blocks, 256, 0, st>>>(x, out, n); WSI_COUNT(); }
 }
 
+// (s x) (float64 product, one rounding) -> (hi, lo) pairs
+__global__ void k_df_split_scaled(const double* __restrict__ x, double s, float2* out, size_t n) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+    const dfl d = df_split(s * x[t]);
+    out[t] = make_float2(d.h, d.l);
+  }
+}
+
+void launch_df_split_scaled(const double* x, double s, float2* out, size_t n, cudaStream_t st) {
+  if (!n) return;
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+  { k_df_split_scaled<<<blocks, 256, 0, st>>>(x, s, out, n); WSI_COUNT(); }
+}
+
 static dfl host_split(double a) {
   dfl r;
   r.h = (float)a;
@@ -152,43 +280,28 @@ static bool host_pow2(const dfl& c) {
   return c.l == 0.0f && c.h != 0.0f && std::fabs(std::frexp((double)c.h, &e)) == 0.5;
 }
 
-void launch_stokes_df(const GridDev& g, const DfCoef& cf, double inv_dt, double theta, const float2* x, double* y,
+void launch_stokes_df(const GridDev& g, const DfCoef& cf, double theta, const float2* x, double* y,
                       cudaStream_t st) {
   Packing pk = packing(g);
   DfVec xv{{x + pk.off[0], x + pk.off[1], x + pk.off[2]}, x + pk.off[3]};
-  DfConst k;
-  for (int a = 0; a < 3; ++a) {
-    k.ih[a] = host_split(g.ih[a]);
-    k.two_ih2[a] = host_split(2.0 * g.ih2[a]);
-  }
-  k.inv_dt = host_split(inv_dt);
-  k.mtheta = host_split(-theta);
+  HtConst k;
   k.pw = 0;
   for (int a = 0; a < 3; ++a) {
-    if (host_pow2(k.ih[a])) k.pw |= 1u << a;
-    if (host_pow2(k.two_ih2[a])) k.pw |= 1u << (3 + a);
+    const dfl ih = host_split(g.ih[a]), t2 = host_split(2.0 * g.ih2[a]);
+    k.ih[a] = ht{ih.h, ih.l};
+    k.two_ih2[a] = ht{t2.h, t2.l};
+    if (host_pow2(ih)) k.pw |= 1u << a;
+    if (host_pow2(t2)) k.pw |= 1u << (3 + a);
+    k.n[a] = g.n[a];
   }
-  if (host_pow2(k.mtheta)) k.pw |= 1u << 6;
-  if (host_pow2(k.inv_dt)) k.pw |= 1u << 7;
+  const dfl mt = host_split(-theta);
+  k.mtheta = ht{mt.h, mt.l};
+  if (host_pow2(mt)) k.pw |= 1u << 6;
   for (int w = 0; w < 6; ++w) k.bcs[w] = (float)g.bc[w];
-  const int n0 = g.n[0], n1 = g.n[1];
-  for (int c = 0; c < 3; ++c) {
-    const int fx = n0 + (c == 0), fy = n1 + (c == 1);
-    k.fs[c][0] = 1;
-    k.fs[c][1] = fx;
-    k.fs[c][2] = fx * fy;
-    const int ax = (c == 0 || c == 1) ? 1 : 0, ay = (c == 0 || c == 2) ? 1 : 0;
-    k.es[c][0] = 1;
-    k.es[c][1] = n0 + ax;
-    k.es[c][2] = (n0 + ax) * (n1 + ay);
-  }
-  k.cs[0] = 1;
-  k.cs[1] = n0;
-  k.cs[2] = n0 * n1;
-  dim3 grid(cdiv(g.n[0] + 1, BX), cdiv(g.n[1] + 1, BY), g.n[2] + 1);
+  dim3 grid(cdiv(g.n[0] + 1, FX), cdiv(g.n[1], FBY), cdiv(g.n[2], FKC));
   ktimer_begin(KC_STOKES, st);
-  { k_stokes_df<<<grid, dim3(BX, BY), 0, st>>>(g, k, cf, xv, y + pk.off[0], y + pk.off[1], y + pk.off[2],
-                                               y + pk.off[3]); WSI_COUNT(); }
+  { k_stokes_df<<<grid, dim3(32, FBY), 0, st>>>(k, cf, xv, y + pk.off[0], y + pk.off[1], y + pk.off[2],
+                                                y + pk.off[3]); WSI_COUNT(); }
   ktimer_end(KC_STOKES, st);
 }
 

@@ -61,7 +61,7 @@ void launch_stokes(const GridDev& g, const Coef<double>& cf, double inv_dt, doub
 // Operands of the double-float Stokes matvec (dfstokes.cu): (hi, lo) float32
 // pairs of the coefficients and of a packed Stokes vector
 struct DfCoef {
-  const float2* rho_face[3];
+  const float2* rho_face[3];  // face density times 1/dt
   const float2* mu_cc;
   const float2* mu_e[3];
 };
@@ -69,10 +69,12 @@ struct DfVec {
   const float2* q[3];
   const float2* p;
 };
-// out[i] = (hi, lo) split of x[i]
+// out[i] = (hi, lo) split of x[i] (of s x[i])
 void launch_df_split(const double* x, float2* out, size_t n, cudaStream_t st);
-// y = K x in double-float arithmetic from the split coefficients and x
-void launch_stokes_df(const GridDev& g, const DfCoef& cf, double inv_dt, double theta, const float2* x, double* y,
+void launch_df_split_scaled(const double* x, double s, float2* out, size_t n, cudaStream_t st);
+// y = K x in double-float arithmetic from the split coefficients (face
+// density already times 1/dt) and x
+void launch_stokes_df(const GridDev& g, const DfCoef& cf, double theta, const float2* x, double* y,
                       cudaStream_t st);
 // red-black Gauss-Seidel half sweep on the viscous block for component c
 template <typename T>
