@@ -71,6 +71,10 @@ def kernel_model(name, nx, ny, nz, prec_bytes):
     if name == "transport":
         byts = 8 * (F + F + F)
         return byts, 300 * F, "alu"
+    if name in ("mdot", "maxpy"):
+        # launches differ in the number of basis vectors: the library sums
+        # each launch's algorithmic bytes (wsi_ktimer_bytes)
+        return None, None, "hbm"
     if name == "reinit":
         # first stage: read phi and the one-byte sign/crossing code, write
         # phi*; second stage: also read phi^m (phi~ itself is read only next
@@ -274,6 +278,64 @@ def oracle_sample_step(n_sample=12, workload="tank", reinit_iters=0, form="consi
     return g.n_cells, dt
 
 
+def other_configs(args, stream):
+    """The other configurations of the workload list, timed the same way
+    (CUDA events on the library's stream after 3 warm-up steps), each from
+    a fresh context: the 128^3 hydrostatic tank (50 steps, solves/s and the
+    spurious velocity left), the 256x128x128 wave tank (200 steps mixed, 20
+    plain float64) and the largest, 512x256x256 wave tank with the free
+    cylinder (10 steps mixed, 5 plain float64: a sample of its 500)."""
+    import torch
+    from paper_1901_07892_gb300 import wsi
+
+    def run(c, prec, steps, waves=None, rho_s=None):
+        ctx = wsi.Context.from_case(c, precision=prec, restart=20, stream=stream.cuda_stream)
+        if rho_s is not None:
+            ctx.set_case(c, rho_s=rho_s)
+        else:
+            ctx.set_case(c)
+        if waves:
+            ctx.set_waves(**waves)
+        for _ in range(3):
+            ctx.step(c.dt, rtol=args.rtol, max_iters=200)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        its = []
+        for _ in range(steps):
+            st = ctx.step(c.dt, rtol=args.rtol, max_iters=200)
+            its.append([st.iters[0], st.iters[1]])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        cells = c.nx * c.ny * c.nz
+        out = {"steps": steps, "ms_per_step": ms / steps, "cell_steps_per_s": cells * steps / (ms * 1e-3),
+               "solves_per_s": 2 * steps / (ms * 1e-3), "fgmres_iters": its, "umax": st.umax}
+        ctx.close()
+        return out
+
+    res = {}
+    c = inputs.tank3d(n=128, seed=None, dt=5e-4)
+    res["hydrostatic128"] = {"what": "128^3 tank, flat surface z = 0.6, locked 0.2x0.2x0.1 box, rho^flow g, "
+                                     "u0 = 0, dt 5e-4, rtol %.0e" % args.rtol,
+                             "mixed": run(c, wsi.PREC_MIXED, 50, rho_s=c.rho_l),
+                             "plain_fp64": run(c, wsi.PREC_FP64, 50, rho_s=c.rho_l)}
+    c = build_case(256, "wave")
+    w = c.extra["waves"]
+    res["wave256x128x128"] = {"what": "wave tank 4x1x1 m, depth 0.5, Stokes wave H 0.05 T 1, locked bar, dt 0.01",
+                              "mixed": run(c, wsi.PREC_MIXED, 200, waves=w),
+                              "plain_fp64": run(c, wsi.PREC_FP64, 20, waves=w)}
+    c = build_case(256, "cylinder")
+    w = c.extra["waves"]
+    res["cylinder512x256x256"] = {"what": "wave tank 8x2x2 m, depth 1, regular wave H 0.1 T 1.2, free cylinder "
+                                          "r 0.15 L 1.6 rho_s 500, dt 2.5e-3 (a 10-step sample of 500)",
+                                  "mixed": run(c, wsi.PREC_MIXED, 10, waves=w),
+                                  "plain_fp64": run(c, wsi.PREC_FP64, 5, waves=w)}
+    for v in res.values():
+        v["speedup_mixed_over_fp64"] = v["plain_fp64"]["ms_per_step"] / v["mixed"]["ms_per_step"]
+    return res
+
+
 def oracle_matvec_rate(c):
     """The oracle's Stokes matvec on the full-size workload (materials
     excluded), single-threaded numpy: cell-applies/s, beside the GPU's
@@ -332,13 +394,17 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned pressure-solve comparison")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other configurations (hydrostatic 128^3, wave tank, largest cylinder tank)")
     ap.add_argument("--visc-sweeps", type=int, default=2, help="viscous red-black sweeps per preconditioner apply")
     ap.add_argument("--form", default="consistent", choices=["consistent", "nonconservative"],
                     help="momentum formulation: consistent mass/momentum transport (default) or the "
                          "non-conservative one with the level-set density")
     ap.add_argument("--reinit", type=int, default=0,
                     help="pseudo-time steps of the level-set reinitialisation at the end of every step")
-    ap.add_argument("--mg", default="2,2", help="pressure V-cycle pre,post smoothing sweeps")
+    ap.add_argument("--mg", default="2,2", help="pressure V-cycle pre,post smoothing sweeps (or degrees)")
+    ap.add_argument("--smoother", default="rbgs", choices=["rbgs", "chebyshev"],
+                    help="pressure multigrid smoother")
     ap.add_argument("--learned-train", type=int, default=1200, help="training samples for the learned comparison")
     ap.add_argument("--workload", default="tank", choices=["tank", "cylinder", "wave"],
                     help="tank: n^3 sloshing tank (default); cylinder: (2n) x n x n wave tank with a free cylinder; "
@@ -374,6 +440,8 @@ def main():
         pre, post = (int(v) for v in args.mg.split(","))
         ctx = wsi.Context.from_case(c, precision=p, restart=20, stream=stream.cuda_stream, mg_pre=pre, mg_post=post,
                                     visc_sweeps=args.visc_sweeps, reinit_iters=args.reinit,
+                                    mg_smoother=(wsi.SMOOTH_CHEBYSHEV if args.smoother == "chebyshev"
+                                                 else wsi.SMOOTH_RBGS),
                                     transport_form=(wsi.FORM_NONCONSERVATIVE if args.form == "nonconservative"
                                                     else wsi.FORM_CONSISTENT))
         if args.workload in ("cylinder", "wave"):
@@ -414,6 +482,7 @@ def main():
     ms, its = timed_steps(ctx, args.steps)
     l1 = wsi.launch_count()
     kt_ms, kt_n = wsi.ktimer_read()
+    kt_bytes = wsi.ktimer_bytes()
     wsi.ktimer_enable(-1)
     clocks = sample_clocks_stop(clk, clk_path, torch.cuda.current_device())
     value = job_throughput(world, cells, args.steps, ms * 1e-3)
@@ -423,6 +492,8 @@ def main():
     byts, flops, bound = kernel_model(kname, c.nx, c.ny, c.nz, pb)
     peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
     roof = None
+    if byts is None and kt_n > 0:
+        byts = kt_bytes / kt_n  # average algorithmic bytes per launch
     if kt_n > 0:
         dur = kt_ms / kt_n * 1e-3
         if bound == "alu":
@@ -478,6 +549,10 @@ def main():
                    "speedup_mixed_over_fp64": ms64 / ms}
         ctx64.close()
 
+    configs = None
+    if not args.no_configs and rank == 0 and args.workload == "tank" and args.n == 256:
+        configs = other_configs(args, stream)
+
     learned = None
     if not args.no_learned and rank == 0 and args.workload == "tank":
         learned = learned_comparison(args, stream)
@@ -504,10 +579,10 @@ def main():
                 "config": {"workload": workload_name(args),
                            "cells": cells, "precision": args.precision, "l2": "inputs larger than L2 (no flush)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
-                           "mg_pre_post": args.mg, "visc_sweeps": args.visc_sweeps,
+                           "mg_pre_post": args.mg, "mg_smoother": args.smoother, "visc_sweeps": args.visc_sweeps,
                            "fgmres_iters": its, "reinit_iters": args.reinit, "form": args.form},
                 "gpu_launches": int(l1 - l0), "roofline": roof, "fp64_fma_peak_tflops": fp64_peak / 1e3, "cpu_baseline": cpu, "e2e": e2e,
-                "clocks": clocks, "compare": compare, "learned": learned}
+                "clocks": clocks, "compare": compare, "configs": configs, "learned": learned}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -57,6 +57,18 @@ extern "C" {
 #define WSI_FORM_NONCONSERVATIVE 1 /* level-set face density, explicit CUI
                                       convection N(u^{n+1/2}) (Sec. 4.2.3)    */
 
+#define WSI_SMOOTH_RBGS 0          /* red-black Gauss-Seidel (the default)    */
+#define WSI_SMOOTH_CHEBYSHEV 1     /* Chebyshev polynomial of the Jacobi-
+                                      preconditioned operator, interval
+                                      [1/4, 2] (Gershgorin bound 2)           */
+
+#define WSI_LIMIT_CUI 0            /* level-set face values: bounded cubic
+                                      upwind (the default stand-in)          */
+#define WSI_LIMIT_XSPPM7 1         /* xsPPM7 (Sec. 4.2.1): seventh-order
+                                      upwind-biased interpolant within the
+                                      monotonicity-preserving, extremum-
+                                      sensitive bounds of Suresh and Huynh   */
+
 #define WSI_GRAVITY_FLOW 0 /* rho^flow g: well-balanced, for locked bodies (Sec. 5) */
 #define WSI_GRAVITY_FULL 1 /* rho g with the transported face density           */
 
@@ -71,7 +83,8 @@ typedef struct {
     double n_cells;      /* Heaviside half-width in cells (paper: 2)          */
     double theta;        /* implicit viscous weight (paper: 1/2, Crank-Nicolson) */
     int precision;       /* WSI_PREC_FP64 or WSI_PREC_MIXED                  */
-    int mg_pre, mg_post; /* red-black Gauss-Seidel sweeps per level           */
+    int mg_pre, mg_post; /* pressure smoothing per level and side: sweeps
+                            (red-black) or polynomial degree (Chebyshev)     */
     int mg_cycles;       /* pressure V-cycles per preconditioner application  */
     int visc_sweeps;     /* viscous red-black sweeps per application (and per
                             level and side of a viscous V-cycle)              */
@@ -83,6 +96,10 @@ typedef struct {
                             (Sec. 4.1); 0: phi is not reinitialised          */
     int transport_form;  /* WSI_FORM_CONSISTENT or WSI_FORM_NONCONSERVATIVE
                             (the formulation wsi_step integrates)            */
+    int mg_smoother;     /* WSI_SMOOTH_RBGS or WSI_SMOOTH_CHEBYSHEV: smoother
+                            of the pressure multigrid                        */
+    int ls_limiter;      /* WSI_LIMIT_CUI or WSI_LIMIT_XSPPM7: face values of
+                            the level-set advection (Sec. 4.2.1)             */
 } wsi_grid_desc;
 
 typedef struct {
@@ -389,6 +406,11 @@ int wsi_norm2_noalloc(const double* x, size_t n, double* out, void* stream);
 long long wsi_launch_count(void);
 int wsi_ktimer_enable(int kernel_class);
 int wsi_ktimer_read(double* total_ms, long long* launches);
+/* Summed algorithmic bytes of the bracketed launches of the enabled class,
+ * for classes whose launches differ in size (Gram-Schmidt dots: each
+ * distinct vector read once; multi-axpy: the rows and w read, w written);
+ * 0 for the other classes. */
+int wsi_ktimer_bytes(double* bytes);
 
 /* Measured fused multiply-add rate of the current GPU in GFLOP/s (2 flop per
  * FMA): fp64 = 1 float64, 0 float32, 2 float32 issued as packed pairs

@@ -14,6 +14,7 @@ For cycles k = 0 .. n_cycles-1 (the paper uses n_cycles = 2):
   3. rigidity projection at X^{n+1/2,k} and the position update.
 At k = 0: u^{n+1,0} = u^n, X^{n+1,0} = X^n.  At n = 0: u^{-1} = u^0.
 With wave zones, u^{n+1} and phi^{n+1} are relaxed at t^{n+1} (Sec. 7.1).
+limiter selects the level-set face values ("cui" or "xsppm7", levelset.py).
 With reinit_iters > 0, phi^{n+1} is then reinitialised to a signed distance
 (Sec. 4.1; reinit.py) before the step is committed.
 
@@ -83,7 +84,7 @@ def _materials(s: State, phi, psi):
     return Materials(s.g, phi, psi, pr.rho_l, pr.rho_g, pr.rho_s, pr.mu_l, pr.mu_g, pr.mu_s, pr.n_cells)
 
 
-def step(s: State, dt, n_cycles=2, reinit_iters=0, form="consistent"):
+def step(s: State, dt, n_cycles=2, reinit_iters=0, form="consistent", limiter="cui"):
     g, pr = s.g, s.props
     u_n = [a.copy() for a in s.vel]
     u_nm1 = [a.copy() for a in s.vel_old]
@@ -102,7 +103,7 @@ def step(s: State, dt, n_cycles=2, reinit_iters=0, form="consistent"):
     info = {}
     for k in range(n_cycles):
         u_half = [0.5 * (a + b) for a, b in zip(u_k, u_n)]
-        phi_new = levelset.advect(g, u_half, phi_n, 0.5 * (phi_k + phi_n), dt)
+        phi_new = levelset.advect(g, u_half, phi_n, 0.5 * (phi_k + phi_n), dt, limiter=limiter)
         if body is not None and body.half is not None:
             psi_new = levelset.box_sdf(g, X_k.mean(axis=0), body.half)
         elif body is not None and body.cylinder is not None:

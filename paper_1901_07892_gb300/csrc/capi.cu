@@ -28,6 +28,7 @@ struct KTimer {
   std::vector<cudaEvent_t> start, stop;
   size_t used = 0;
   bool open = false;
+  double bytes = 0.0;  // algorithmic bytes reported by launchers of the enabled class
 };
 KTimer g_kt;
 constexpr size_t KT_MAX = 1 << 16;
@@ -47,6 +48,10 @@ void wsi::ktimer_begin(int id, cudaStream_t st) {
   }
   cudaEventRecord(g_kt.start[g_kt.used], st);
   g_kt.open = true;
+}
+
+void wsi::ktimer_bytes(int id, double bytes) {
+  if (id == g_kt.enabled && g_kt.used < KT_MAX) g_kt.bytes += bytes;
 }
 
 void wsi::ktimer_end(int id, cudaStream_t st) {
@@ -596,13 +601,13 @@ void levelset_stage(wsi_ctx* c, const double* vk, const double* vn, const double
     launch_lincomb(c->ncell, 0.5, phik, 0.5, phin, 0.0, nullptr, c->phi_half, st);
     const double* vh[3];
     cparts(c, (const double*)c->vel_half, vh);
-    launch_levelset_advect<double>(g, vh, phin, c->phi_half, dt, phi_out, st);
+    launch_levelset_advect<double>(g, vh, phin, c->phi_half, dt, phi_out, st, c->desc.ls_limiter);
   } else {
     launch_lincomb_to_f32(c->nvel, 0.5, vk, 0.5, vn, 0.0, nullptr, c->vh32, st);
     launch_lincomb_to_f32(c->ncell, 0.5, phik, 0.5, phin, 0.0, nullptr, c->phih32, st);
     const float* vh[3];
     cparts(c, (const float*)c->vh32, vh);
-    launch_levelset_advect<float>(g, vh, phin, c->phih32, dt, phi_out, st);
+    launch_levelset_advect<float>(g, vh, phin, c->phih32, dt, phi_out, st, c->desc.ls_limiter);
   }
 }
 
@@ -710,6 +715,13 @@ int wsi_ktimer_enable(int kernel_class) {
   g_kt.enabled = kernel_class;
   g_kt.used = 0;
   g_kt.open = false;
+  g_kt.bytes = 0.0;
+  return WSI_OK;
+}
+
+int wsi_ktimer_bytes(double* bytes) {
+  if (!bytes) return WSI_ERR_INVALID_ARG;
+  *bytes = g_kt.bytes;
   return WSI_OK;
 }
 
@@ -742,6 +754,8 @@ int wsi_create_grid(const wsi_grid_desc* d, void* stream, wsi_ctx** out) {
   if (d->reinit_iters < 0) return WSI_ERR_INVALID_ARG;
   if (d->transport_form != WSI_FORM_CONSISTENT && d->transport_form != WSI_FORM_NONCONSERVATIVE)
     return WSI_ERR_INVALID_ARG;
+  if (d->mg_smoother != WSI_SMOOTH_RBGS && d->mg_smoother != WSI_SMOOTH_CHEBYSHEV) return WSI_ERR_INVALID_ARG;
+  if (d->ls_limiter != WSI_LIMIT_CUI && d->ls_limiter != WSI_LIMIT_XSPPM7) return WSI_ERR_INVALID_ARG;
   if ((double)(d->nx + 1) * (d->ny + 1) * (d->nz + 1) >= 2147483648.0) return WSI_ERR_INVALID_ARG;
   wsi_ctx* c = new wsi_ctx();
   c->desc = *d;
@@ -764,6 +778,7 @@ int wsi_create_grid(const wsi_grid_desc* d, void* stream, wsi_ctx** out) {
   c->opts.mg_cycles = d->mg_cycles > 0 ? d->mg_cycles : 1;
   c->opts.visc_sweeps = d->visc_sweeps > 0 ? d->visc_sweeps : 2;
   c->opts.visc_mg = d->visc_mg > 0 ? d->visc_mg : 0;
+  c->opts.mg_smoother = d->mg_smoother;
   c->opts.theta = d->theta;
   const GridDev& g = c->g;
   bool ok = true;

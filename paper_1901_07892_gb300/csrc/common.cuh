@@ -34,6 +34,9 @@ enum KernelClass {
 };
 void ktimer_begin(int id, cudaStream_t st);
 void ktimer_end(int id, cudaStream_t st);
+// algorithmic bytes of the launch being bracketed (classes whose launches
+// differ in size report them; the sum is read by wsi_ktimer_bytes)
+void ktimer_bytes(int id, double bytes);
 
 struct GridDev {
   int n[3];       // cells per axis

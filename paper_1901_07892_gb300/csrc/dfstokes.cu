@@ -37,6 +37,9 @@ namespace wsi {
 static constexpr int FX = 30;  // x-positions written per warp (32 lanes, one halo lane each side)
 static constexpr int FBY = 4;  // warps (y-rows) per block
 static constexpr int FKC = 16; // z-levels per thread
+#ifndef WSI_MV_PREFETCH
+#define WSI_MV_PREFETCH 0
+#endif
 
 struct HtConst {
   ht ih[3];       // 1/h
@@ -139,6 +142,26 @@ __global__ void __launch_bounds__(32 * FBY) k_stokes_df(HtConst K, DfCoef cf, Df
 
   for (int k = k0; k < k1; ++k) {
     const int kp = k + 1;
+#if WSI_MV_PREFETCH > 0
+    // bring this thread's operands PD levels ahead into L2: the loads of
+    // level k + PD then hit L2 instead of DRAM
+    {
+      const int kq = k + WSI_MV_PREFETCH;
+      if (kq < nz) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(U + iff + j * su1 + kq * su2));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(V + ic + j * sv1 + kq * sv2));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(W + ic + j * sc1 + kq * sc2));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(P + ic + j * sc1 + kq * sc2));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(cf.mu_cc + ic + j * sc1 + kq * sc2));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(cf.mu_e[0] + iff + j * sxy1 + kq * sxy2));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(cf.mu_e[1] + iff + j * sxz1 + kq * sxz2));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(cf.mu_e[2] + ic + j * syz1 + kq * syz2));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(cf.rho_face[0] + iff + j * su1 + kq * su2));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(cf.rho_face[1] + ic + j * sv1 + kq * sv2));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(cf.rho_face[2] + ic + j * sc1 + kq * sc2));
+      }
+    }
+#endif
     // ---- level k + 1: fields and z-edge shear stresses
     ht u_kp, v_kp, vj_kp;
     if (kp < nz) {

@@ -108,7 +108,7 @@ void reinit_levelset(const GridDev& g, double* phi, int iters, double cfl, void*
 
 template <typename T>
 void launch_levelset_advect(const GridDev& g, const T* const vel[3], const double* phi_n, const T* phi_half, double dt,
-                            double* out, cudaStream_t st);
+                            double* out, cudaStream_t st, int limiter);
 void launch_box_sdf(const GridDev& g, const double* xcom_dev, const double half[3], double* psi, cudaStream_t st);
 void launch_cyl_sdf(const GridDev& g, const double* xcom_dev, double radius, double half_length, double* psi,
                     cudaStream_t st);
@@ -191,6 +191,9 @@ struct MGLevel {
   T* x;
   T* b;
   T* res;
+  T* cd;            // Chebyshev smoother: direction, and the second buffer pair
+  T* cx2;
+  T* cd2;
 };
 
 // one level of the viscous multigrid (levels >= 1; level 0 uses the fine
@@ -232,6 +235,7 @@ struct Precond {
 
 struct Opts {
   int mg_pre = 2, mg_post = 2, mg_cycles = 1, visc_sweeps = 2;
+  int mg_smoother = 0;  // WSI_SMOOTH_RBGS or WSI_SMOOTH_CHEBYSHEV (pressure multigrid)
   int visc_mg = 0;  // > 0: that many viscous V-cycles (visc_sweeps pre and post) instead of plain sweeps
   double theta = 0.5;
 };

@@ -75,6 +75,9 @@ void launch_mdot(const double* V, size_t ldv, int m, const double* w, size_t n, 
   for (int t0 = 0; t0 < m; t0 += NV) {
     int mm = std::min(NV, m - t0);
     ktimer_begin(KC_MDOT, st);
+    // each distinct array read once: w is often the last basis row itself
+    const bool w_in_v = w == V + (size_t)(t0 + mm - 1) * ldv;
+    ktimer_bytes(KC_MDOT, 8.0 * (double)n * (mm + (w_in_v ? 0 : 1)));
     { k_mdot<NV><<<RB, RT, 0, st>>>(V + (size_t)t0 * ldv, ldv, mm, w, n, scratch); WSI_COUNT(); }
     ktimer_end(KC_MDOT, st);
     { k_reduce_parts<<<mm, 256, 0, st>>>(scratch, RB, NV, mm, out + t0); WSI_COUNT(); }
@@ -110,6 +113,7 @@ void launch_maxpy(const double* V, size_t ldv, int m, const double* h, double* w
     int mm = std::min(64, m - t0);
     const double* sc = (t0 + 64 >= m) ? scale_dev : nullptr;
     ktimer_begin(KC_MAXPY, st);
+    ktimer_bytes(KC_MAXPY, 8.0 * (double)n * (mm + 2));  // mm rows and w read, w written
     { k_maxpy<<<RB, RT, 0, st>>>(V + (size_t)t0 * ldv, ldv, mm, h + t0, w, n, sign, sc); WSI_COUNT(); }
     ktimer_end(KC_MAXPY, st);
   }

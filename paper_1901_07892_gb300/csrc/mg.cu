@@ -81,7 +81,10 @@ int precond_alloc(Precond<T>& P, const GridDev& g0, std::string& err) {
     L.x = dalloc<T>(P.allocs, nc, err);
     L.b = dalloc<T>(P.allocs, nc, err);
     L.res = dalloc<T>(P.allocs, nc, err);
-    if (!L.x || !L.b || !L.res) return WSI_ERR_OOM;
+    L.cd = dalloc<T>(P.allocs, nc, err);
+    L.cx2 = dalloc<T>(P.allocs, nc, err);
+    L.cd2 = dalloc<T>(P.allocs, nc, err);
+    if (!L.x || !L.b || !L.res || !L.cd || !L.cx2 || !L.cd2) return WSI_ERR_OOM;
     // Semi-coarsening on anisotropic grids: an axis coarsens only while its
     // spacing is within 1.5x of the finest active spacing, so a grid with
     // hx = 2 hy = 2 hz first coarsens y and z and then all three (point
@@ -93,6 +96,14 @@ int precond_alloc(Precond<T>& P, const GridDev& g0, std::string& err) {
     for (int a = 0; a < 3; ++a) {
       L.r[a] = (g.n[a] % 2 == 0 && g.n[a] >= 4 && g.h[a] <= 1.5 * hmin) ? 2 : 1;
       any |= L.r[a] == 2;
+    }
+    if (!any && nc > 64) {
+      // strongly anisotropic grids whose fine axes can no longer coarsen
+      // (wave tanks with long cells): coarsen every axis that still can
+      for (int a = 0; a < 3; ++a) {
+        L.r[a] = (g.n[a] % 2 == 0 && g.n[a] >= 4) ? 2 : 1;
+        any |= L.r[a] == 2;
+      }
     }
     if (nc <= 64 || !any) {
       for (int a = 0; a < 3; ++a) L.r[a] = 1;
@@ -498,6 +509,89 @@ __global__ void k_coarse_solve(int n, const double* __restrict__ Minv, const T* 
   }
 }
 
+// One pass of the Chebyshev smoother on A = -L (positive semi-definite)
+// with Jacobi preconditioning D = diag(A): with x' = x + d (d = 0 on the
+// first pass), r = L x' - b = -b - A x' (the residual of A x = -b), and
+//     x_out = x',  d_out = alpha d + c r / D.
+// Every cell of the level in one coalesced pass (no colouring); the caller
+// alternates two buffer pairs and finishes with x += d.
+template <typename T>
+__global__ void k_cheb_p(GridDev g, const T* __restrict__ bx, const T* __restrict__ by, const T* __restrict__ bz,
+                         const T* __restrict__ x, const T* __restrict__ d, const T* __restrict__ b, T* xo, T* dout,
+                         T alpha, T c, int first) {
+  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.n[0] || j >= g.n[1]) return;
+  const size_t id = fidx(g, 3, i, j, k);
+  const size_t pl = (size_t)g.n[0] * g.n[1];
+  auto xv = [&](size_t q) { return first ? x[q] : x[q] + d[q]; };
+  const T ihx2 = ginv2<T>(g, 0), ihy2 = ginv2<T>(g, 1), ihz2 = ginv2<T>(g, 2);
+  const T xc = xv(id);
+  T s = T(0), dg = T(0);
+  if (i + 1 < g.n[0]) { T w = bx[fidx(g, 0, i + 1, j, k)] * ihx2; s += w * (xv(id + 1) - xc); dg += w; }
+  if (i > 0) { T w = bx[fidx(g, 0, i, j, k)] * ihx2; s += w * (xv(id - 1) - xc); dg += w; }
+  if (j + 1 < g.n[1]) { T w = by[fidx(g, 1, i, j + 1, k)] * ihy2; s += w * (xv(id + g.n[0]) - xc); dg += w; }
+  if (j > 0) { T w = by[fidx(g, 1, i, j, k)] * ihy2; s += w * (xv(id - g.n[0]) - xc); dg += w; }
+  if (k + 1 < g.n[2]) { T w = bz[fidx(g, 2, i, j, k + 1)] * ihz2; s += w * (xv(id + pl) - xc); dg += w; }
+  if (k > 0) { T w = bz[fidx(g, 2, i, j, k)] * ihz2; s += w * (xv(id - pl) - xc); dg += w; }
+  const T r = s - b[id];
+  xo[id] = xc;
+  dout[id] = (first ? T(0) : alpha * d[id]) + (dg > T(0) ? c * r / dg : T(0));
+}
+
+template <typename T>
+__global__ void k_cheb_finish(size_t n, const T* __restrict__ x, const T* __restrict__ d, T* out) {
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    out[t] = x[t] + d[t];
+}
+
+// Chebyshev interval of the Jacobi-preconditioned level operator: Gershgorin
+// bounds its spectrum by 2 (diagonally dominant, zero row sums away from
+// walls); the smoother targets [2/8, 2], the upper part that the coarse grid
+// cannot represent.
+static constexpr double CHEB_HI = 2.0, CHEB_LO = 0.25;
+
+// m passes of smoothing on level l: red-black Gauss-Seidel sweeps (pre: red
+// then black; post: black then red) or a degree-m Chebyshev polynomial
+template <typename T>
+static void smooth(Precond<T>& P, const Opts& o, size_t l, int m, bool pre, cudaStream_t st) {
+  MGLevel<T>& L = P.lev[l];
+  const GridDev& g = L.g;
+  if (m <= 0) return;
+  if (o.mg_smoother != WSI_SMOOTH_CHEBYSHEV) {
+    for (int s = 0; s < m; ++s)
+      for (int q = 0; q < 2; ++q) {
+        const int c = pre ? q : 1 - q;
+        ktimer_begin(KC_RBGS_P, st);
+        { k_rbgs_p<T><<<grid_rb(g), dim3(BX, BY), 0, st>>>(g, L.beta[0], L.beta[1], L.beta[2], L.x, L.b, c); WSI_COUNT(); }
+        ktimer_end(KC_RBGS_P, st);
+      }
+    return;
+  }
+  const double theta = 0.5 * (CHEB_HI + CHEB_LO), delta = 0.5 * (CHEB_HI - CHEB_LO), sigma = theta / delta;
+  double rho_prev = 1.0 / sigma;
+  T* xs[2] = {L.x, L.cx2};
+  T* ds[2] = {L.cd, L.cd2};
+  const dim3 gr = grid3(g.n[0], g.n[1], g.n[2]);
+  int cur = 0;
+  for (int k = 0; k < m; ++k) {
+    double alpha = 0.0, c = 1.0 / theta;
+    if (k > 0) {
+      const double rho = 1.0 / (2.0 * sigma - rho_prev);
+      alpha = rho * rho_prev;
+      c = 2.0 * rho / delta;
+      rho_prev = rho;
+    }
+    ktimer_begin(KC_RBGS_P, st);
+    { k_cheb_p<T><<<gr, dim3(BX, BY), 0, st>>>(g, L.beta[0], L.beta[1], L.beta[2], xs[cur], ds[cur], L.b,
+                                               xs[1 - cur], ds[1 - cur], (T)alpha, (T)c, k == 0 ? 1 : 0); WSI_COUNT(); }
+    ktimer_end(KC_RBGS_P, st);
+    cur = 1 - cur;
+  }
+  const size_t n = fsize(g, 3);
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
+  { k_cheb_finish<T><<<std::max(blocks, 1), 256, 0, st>>>(n, xs[cur], ds[cur], L.x); WSI_COUNT(); }
+}
+
 template <typename T>
 static void vcycle(Precond<T>& P, const Opts& o, size_t l, cudaStream_t st);
 
@@ -508,12 +602,7 @@ static void coarse_part(Precond<T>& P, const Opts& o, size_t l, cudaStream_t st)
   MGLevel<T>& L = P.lev[l];
   const GridDev& g = L.g;
   dim3 gr = grid3(g.n[0], g.n[1], g.n[2]);
-  for (int s = 0; s < o.mg_pre; ++s)
-    for (int c = 0; c < 2; ++c) {
-      ktimer_begin(KC_RBGS_P, st);
-      { k_rbgs_p<T><<<grid_rb(g), dim3(BX, BY), 0, st>>>(g, L.beta[0], L.beta[1], L.beta[2], L.x, L.b, c); WSI_COUNT(); }
-      ktimer_end(KC_RBGS_P, st);
-    }
+  smooth(P, o, l, o.mg_pre, true, st);
   MGLevel<T>& Cl = P.lev[l + 1];
   const GridDev& gc = Cl.g;
   ktimer_begin(KC_RESTRICT, st);
@@ -546,11 +635,7 @@ static void vcycle(Precond<T>& P, const Opts& o, size_t l, cudaStream_t st) {
     // this level, then the usual post-smoothing
     if (P.learn.on && P.learn.ready && (int)l == P.learn.level && P.learn.mode == WSI_LEARN_REPLACE) {
       learned_correction(P, (int)l, L.b, false, st);
-      for (int s = 0; s < o.mg_post; ++s)
-        for (int c = 1; c >= 0; --c) {
-          k_rbgs_p<T><<<grid_rb(g), dim3(BX, BY), 0, st>>>(g, L.beta[0], L.beta[1], L.beta[2], L.x, L.b, c);
-          WSI_COUNT();
-        }
+      smooth(P, o, l, o.mg_post, false, st);
       return;
     }
   }
@@ -566,13 +651,7 @@ static void vcycle(Precond<T>& P, const Opts& o, size_t l, cudaStream_t st) {
       learned_correction(P, (int)l, L.res, true, st);
     }
   }
-  for (int s = 0; s < o.mg_post; ++s)
-    for (int c = 1; c >= 0; --c)
-    {
-      ktimer_begin(KC_RBGS_P, st);
-      { k_rbgs_p<T><<<grid_rb(g), dim3(BX, BY), 0, st>>>(g, L.beta[0], L.beta[1], L.beta[2], L.x, L.b, c); WSI_COUNT(); }
-      ktimer_end(KC_RBGS_P, st);
-    }
+  smooth(P, o, l, o.mg_post, false, st);
 }
 
 template <typename T>

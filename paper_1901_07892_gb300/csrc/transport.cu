@@ -359,22 +359,73 @@ void launch_lincomb_mix(size_t n, double a, const double* x, double b, const flo
 
 // ================================================================ level set
 // Same staging as k_transport: per z-plane the tile of phi^{n+1/2} with a
-// two-cell halo (Neumann mirror ghosts applied while staging) in shared
-// memory, the z taps in a four-entry register window, the face velocities
-// loaded before the staging barrier.
+// halo of H cells (Neumann mirror ghosts applied while staging) in shared
+// memory, the z taps in a 2H-entry register window, the face velocities
+// loaded before the staging barrier.  H = 2 for the CUI limiter, 4 for
+// xsPPM7 (seven-cell upwind-biased stencils).
 template <typename T>
 __device__ __forceinline__ int ls_mirror(int m, int n) {
-  int mm = m;
-  if (m < 0) mm = -m - 1;
-  else if (m >= n) mm = 2 * n - 1 - m;
-  return clampi(mm, 0, n - 1);
+  // repeated even reflection (grids thinner than the halo reflect again)
+  for (int it = 0; it < 8; ++it) {
+    if (m < 0) m = -m - 1;
+    else if (m >= n) m = 2 * n - 1 - m;
+  }
+  return clampi(m, 0, n - 1);
 }
 
 template <typename T>
+__device__ __forceinline__ T mm2(T a, T b) {
+  return (a > T(0) && b > T(0)) ? fmin(a, b) : ((a < T(0) && b < T(0)) ? fmax(a, b) : T(0));
+}
+template <typename T>
+__device__ __forceinline__ T mm4(T a, T b, T c, T d) {
+  if (a > T(0) && b > T(0) && c > T(0) && d > T(0)) return fmin(fmin(a, b), fmin(c, d));
+  if (a < T(0) && b < T(0) && c < T(0) && d < T(0)) return fmax(fmax(a, b), fmax(c, d));
+  return T(0);
+}
+
+// xsPPM7 face value between q0 and p1 (cells ordered along the flow): the
+// seventh-order upwind-biased interpolant, accepted when it lies between q0
+// and the monotonicity-preserving value, otherwise moved into the
+// curvature-widened bounds of Suresh and Huynh (alpha = 4)
+template <typename T>
+__device__ __forceinline__ T xsppm7_face(T m3, T m2, T m1, T q0, T p1, T p2, T p3) {
+  const T u7 = (T(-3) * m3 + T(25) * m2 - T(101) * m1 + T(319) * q0 + T(214) * p1 - T(38) * p2 + T(4) * p3) *
+               T(1.0 / 420.0);
+  const T alpha = T(4);
+  const T ump = q0 + mm2<T>(p1 - q0, alpha * (q0 - m1));
+  if ((u7 - q0) * (u7 - ump) <= T(0)) return u7;
+  const T dm1 = m2 - T(2) * m1 + q0, d0 = m1 - T(2) * q0 + p1, dp1 = q0 - T(2) * p1 + p2;
+  const T dp = mm4<T>(T(4) * d0 - dp1, T(4) * dp1 - d0, d0, dp1);
+  const T dm = mm4<T>(T(4) * dm1 - d0, T(4) * d0 - dm1, dm1, d0);
+  const T uul = q0 + alpha * (q0 - m1);
+  const T umd = T(0.5) * (q0 + p1) - T(0.5) * dp;
+  const T ulc = q0 + T(0.5) * (q0 - m1) + T(4.0 / 3.0) * dm;
+  const T umin = fmax(fmin(fmin(q0, p1), umd), fmin(fmin(q0, uul), ulc));
+  const T umax = fmin(fmax(fmax(q0, p1), umd), fmax(fmax(q0, uul), ulc));
+  return u7 + mm2<T>(umin - u7, umax - u7);
+}
+
+// upwind face value from the 2H cells around the face (c[H-1] | c[H])
+template <typename T, int H>
+struct LsLim;
+template <typename T>
+struct LsLim<T, 2> {
+  static __device__ __forceinline__ T face(const T* c, T adv) { return lim4<T>(c[0], c[1], c[2], c[3], adv); }
+};
+template <typename T>
+struct LsLim<T, 4> {
+  static __device__ __forceinline__ T face(const T* c, T adv) {
+    return adv > T(0) ? xsppm7_face<T>(c[0], c[1], c[2], c[3], c[4], c[5], c[6])
+                      : xsppm7_face<T>(c[7], c[6], c[5], c[4], c[3], c[2], c[1]);
+  }
+};
+
+template <typename T, int H>
 __global__ void __launch_bounds__(BX* BY) k_ls_advect(GridDev g, CVel<T> vel,
                                                       const double* __restrict__ phi_n, const T* __restrict__ phi_h,
                                                       double dt, double* out, int zchunk) {
-  constexpr int HX = BX + 4, HY = BY + 4, NS = (HX * HY + BX * BY - 1) / (BX * BY);
+  constexpr int HX = BX + 2 * H, HY = BY + 2 * H, NS = (HX * HY + BX * BY - 1) / (BX * BY);
   __shared__ T sP[HY][HX];
   __shared__ T sFx[BY][BX + 1];
   __shared__ T sFy[BY + 1][BX];
@@ -393,13 +444,14 @@ __global__ void __launch_bounds__(BX* BY) k_ls_advect(GridDev g, CVel<T> vel,
     soff[r] = -1;
     if (t < HX * HY) {
       const int hy = t / HX, hx = t - hy * HX;
-      soff[r] = ls_mirror<T>(y0 - 2 + hy, n1) * n0 + ls_mirror<T>(x0 - 2 + hx, n0);
+      soff[r] = ls_mirror<T>(y0 - H + hy, n1) * n0 + ls_mirror<T>(x0 - H + hx, n0);
     }
   }
   const size_t col = (size_t)min(j, n1 - 1) * n0 + min(i, n0 - 1);
-  T zp[4];
+  // z window: the 2H cells around the current bottom face (k - H .. k + H - 1)
+  T zp[2 * H];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) zp[q] = phi_h[(size_t)ls_mirror<T>(k0 - 2 + q, n2) * plane + col];
+  for (int q = 0; q < 2 * H; ++q) zp[q] = phi_h[(size_t)ls_mirror<T>(k0 - H + q, n2) * plane + col];
   T Fz_lo = T(0);
   for (int k = k0; k < k1; ++k) {
     T ux = T(0), uxl = T(0), vy = T(0), vyl = T(0), wz = T(0), wzl = T(0);
@@ -421,19 +473,33 @@ __global__ void __launch_bounds__(BX* BY) k_ls_advect(GridDev g, CVel<T> vel,
     }
     __syncthreads();
     if (inside) {
-      const int hy = ty + 2, hx = tx + 2;
-      sFx[ty][tx + 1] = ux * lim4<T>(sP[hy][tx + 1], sP[hy][tx + 2], sP[hy][tx + 3], sP[hy][tx + 4], ux);
-      if (tx == 0) sFx[ty][0] = uxl * lim4<T>(sP[hy][tx], sP[hy][tx + 1], sP[hy][tx + 2], sP[hy][tx + 3], uxl);
-      sFy[ty + 1][tx] = vy * lim4<T>(sP[ty + 1][hx], sP[ty + 2][hx], sP[ty + 3][hx], sP[ty + 4][hx], vy);
-      if (ty == 0) sFy[0][tx] = vyl * lim4<T>(sP[ty][hx], sP[ty + 1][hx], sP[ty + 2][hx], sP[ty + 3][hx], vyl);
+      const int hy = ty + H, hx = tx + H;
+      T c[2 * H];
+      // right x-face of cell i: cells i + 1 - H .. i + H
+#pragma unroll
+      for (int q = 0; q < 2 * H; ++q) c[q] = sP[hy][tx + 1 + q];
+      sFx[ty][tx + 1] = ux * LsLim<T, H>::face(c, ux);
+      if (tx == 0) {
+#pragma unroll
+        for (int q = 0; q < 2 * H; ++q) c[q] = sP[hy][tx + q];
+        sFx[ty][0] = uxl * LsLim<T, H>::face(c, uxl);
+      }
+#pragma unroll
+      for (int q = 0; q < 2 * H; ++q) c[q] = sP[ty + 1 + q][hx];
+      sFy[ty + 1][tx] = vy * LsLim<T, H>::face(c, vy);
+      if (ty == 0) {
+#pragma unroll
+        for (int q = 0; q < 2 * H; ++q) c[q] = sP[ty + q][hx];
+        sFy[0][tx] = vyl * LsLim<T, H>::face(c, vyl);
+      }
     }
     __syncthreads();
-    if (k == k0) Fz_lo = wzl * lim4<T>(zp[0], zp[1], zp[2], zp[3], wzl);
+    if (k == k0) Fz_lo = wzl * LsLim<T, H>::face(zp, wzl);
 #pragma unroll
-    for (int q = 0; q < 3; ++q) zp[q] = zp[q + 1];
-    zp[3] = phi_h[(size_t)ls_mirror<T>(k + 2, n2) * plane + col];
+    for (int q = 0; q < 2 * H - 1; ++q) zp[q] = zp[q + 1];
+    zp[2 * H - 1] = phi_h[(size_t)ls_mirror<T>(k + H, n2) * plane + col];
     if (inside) {
-      const T Fz_hi = wz * lim4<T>(zp[0], zp[1], zp[2], zp[3], wz);
+      const T Fz_hi = wz * LsLim<T, H>::face(zp, wz);
       const T Q = (sFx[ty][tx + 1] - sFx[ty][tx]) * ginv<T>(g, 0) + (sFy[ty + 1][tx] - sFy[ty][tx]) * ginv<T>(g, 1) +
                   (Fz_hi - Fz_lo) * ginv<T>(g, 2);
       const size_t id = (size_t)k * plane + (size_t)j * n0 + i;
@@ -446,16 +512,21 @@ __global__ void __launch_bounds__(BX* BY) k_ls_advect(GridDev g, CVel<T> vel,
 
 template <typename T>
 void launch_levelset_advect(const GridDev& g, const T* const vel[3], const double* phi_n, const T* phi_half, double dt,
-                            double* out, cudaStream_t st) {
+                            double* out, cudaStream_t st, int limiter) {
   CVel<T> v{{vel[0], vel[1], vel[2]}};
   const int zc = transport_chunk(g.n[0], g.n[1], g.n[2]);
   dim3 grid(cdiv(g.n[0], BX), cdiv(g.n[1], BY), cdiv(g.n[2], zc));
-  { k_ls_advect<T><<<grid, dim3(BX, BY), 0, st>>>(g, v, phi_n, phi_half, dt, out, zc); WSI_COUNT(); }
+  if (limiter == WSI_LIMIT_XSPPM7) {
+    k_ls_advect<T, 4><<<grid, dim3(BX, BY), 0, st>>>(g, v, phi_n, phi_half, dt, out, zc);
+  } else {
+    k_ls_advect<T, 2><<<grid, dim3(BX, BY), 0, st>>>(g, v, phi_n, phi_half, dt, out, zc);
+  }
+  WSI_COUNT();
 }
 template void launch_levelset_advect<double>(const GridDev&, const double* const[3], const double*, const double*,
-                                             double, double*, cudaStream_t);
+                                             double, double*, cudaStream_t, int);
 template void launch_levelset_advect<float>(const GridDev&, const float* const[3], const double*, const float*,
-                                            double, double*, cudaStream_t);
+                                            double, double*, cudaStream_t, int);
 
 __global__ void k_box_sdf(GridDev g, const double* __restrict__ xc, double hx_, double hy_, double hz_, double* psi) {
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;

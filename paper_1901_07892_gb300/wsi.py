@@ -30,8 +30,10 @@ EXPORTED = ["wsi_stokes_size", "wsi_velocity_size", "wsi_create_grid", "wsi_dest
             "wsi_unet_set_params", "wsi_unet_get_params", "wsi_unet_get_grads", "wsi_unet_forward",
             "wsi_unet_backward", "wsi_unet_adam", "wsi_attach_unet", "wsi_unet_train_sample",
             "wsi_pressure_solve", "wsi_checkpoint", "wsi_restore", "wsi_unet_save", "wsi_unet_load",
-            "wsi_norm2_noalloc", "wsi_reinit", "wsi_fma_peak"]
+            "wsi_norm2_noalloc", "wsi_reinit", "wsi_fma_peak", "wsi_ktimer_bytes"]
 FORM_CONSISTENT, FORM_NONCONSERVATIVE = 0, 1
+SMOOTH_RBGS, SMOOTH_CHEBYSHEV = 0, 1
+LIMIT_CUI, LIMIT_XSPPM7 = 0, 1
 KC_STOKES, KC_RBGS_P, KC_RBGS_V, KC_TRANSPORT, KC_MDOT, KC_MAXPY, KC_RESTRICT, KC_PROLONG, KC_REINIT = range(9)
 
 
@@ -42,7 +44,8 @@ class GridDesc(ctypes.Structure):
                 ("n_cells", ctypes.c_double), ("theta", ctypes.c_double),
                 ("precision", ctypes.c_int), ("mg_pre", ctypes.c_int), ("mg_post", ctypes.c_int),
                 ("mg_cycles", ctypes.c_int), ("visc_sweeps", ctypes.c_int), ("restart", ctypes.c_int),
-                ("visc_mg", ctypes.c_int), ("reinit_iters", ctypes.c_int), ("transport_form", ctypes.c_int)]
+                ("visc_mg", ctypes.c_int), ("reinit_iters", ctypes.c_int), ("transport_form", ctypes.c_int),
+                ("mg_smoother", ctypes.c_int), ("ls_limiter", ctypes.c_int)]
 
 
 class PhaseProps(ctypes.Structure):
@@ -170,11 +173,11 @@ class Context:
     def __init__(self, nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, bc=(-1.0,) * 6, gravity=(0.0, 0.0, -9.81),
                  n_cells=2.0, theta=0.5, precision=PREC_FP64, mg_pre=2, mg_post=2, mg_cycles=1,
                  visc_sweeps=2, restart=20, stream=None, visc_mg=0, reinit_iters=0,
-                 transport_form=FORM_CONSISTENT):
+                 transport_form=FORM_CONSISTENT, mg_smoother=SMOOTH_RBGS, ls_limiter=LIMIT_CUI):
         L = lib()
         d = GridDesc(nx, ny, nz, lx, ly, lz, (ctypes.c_double * 6)(*bc), (ctypes.c_double * 3)(*gravity),
                      n_cells, theta, precision, mg_pre, mg_post, mg_cycles, visc_sweeps, restart, visc_mg,
-                     reinit_iters, transport_form)
+                     reinit_iters, transport_form, mg_smoother, ls_limiter)
         h = ctypes.c_void_p()
         st = ctypes.c_void_p(stream) if stream is not None else None
         rc = L.wsi_create_grid(ctypes.byref(d), st, ctypes.byref(h))
@@ -396,6 +399,16 @@ def ktimer_enable(kernel_class):
     rc = lib().wsi_ktimer_enable(kernel_class)
     if rc != OK:
         raise WsiError(rc, "wsi_ktimer_enable")
+
+
+def ktimer_bytes():
+    L = lib()
+    L.wsi_ktimer_bytes.argtypes = [ctypes.POINTER(ctypes.c_double)]
+    b = ctypes.c_double()
+    rc = L.wsi_ktimer_bytes(ctypes.byref(b))
+    if rc != OK:
+        raise WsiError(rc, "wsi_ktimer_bytes")
+    return b.value
 
 
 def ktimer_read():

@@ -51,6 +51,12 @@ def test_invalid_arguments_rejected_without_gpu_work():
     d.transport_form = 7  # neither formulation
     assert L.wsi_create_grid(ctypes.byref(d), None, ctypes.byref(h)) == wsi.ERR_INVALID_ARG
     d.transport_form = wsi.FORM_CONSISTENT
+    d.mg_smoother = 3  # neither smoother
+    assert L.wsi_create_grid(ctypes.byref(d), None, ctypes.byref(h)) == wsi.ERR_INVALID_ARG
+    d.mg_smoother = wsi.SMOOTH_RBGS
+    d.ls_limiter = 2  # neither limiter
+    assert L.wsi_create_grid(ctypes.byref(d), None, ctypes.byref(h)) == wsi.ERR_INVALID_ARG
+    d.ls_limiter = wsi.LIMIT_CUI
     d.precision = 5
     assert L.wsi_create_grid(ctypes.byref(d), None, ctypes.byref(h)) == wsi.ERR_INVALID_ARG
     assert L.wsi_reinit(None, None, 3) == wsi.ERR_INVALID_ARG

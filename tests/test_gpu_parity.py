@@ -186,6 +186,19 @@ def test_solve_parity_3d_ragged(precision):
     assert max(errs) < FIELD_TOL, errs
 
 
+@pytest.mark.parametrize("precision", [wsi.PREC_FP64, wsi.PREC_MIXED])
+def test_solve_parity_chebyshev_smoother(precision):
+    """The pressure multigrid with the Chebyshev smoother instead of red-black
+    Gauss-Seidel: same exact solution (the preconditioner changes the
+    iterates, not the result), on the ragged 3-D tank and config 1."""
+    c = inputs.tank3d(nxyz=(40, 20, 4), seed=5, dt=5e-4)
+    errs, st, _ = _solve_parity(c, precision, rtol=1e-13, mg_smoother=wsi.SMOOTH_CHEBYSHEV)
+    assert max(errs) < FIELD_TOL, errs
+    c = inputs.tank2d(n=64, seed=0)
+    errs, st, _ = _solve_parity(c, precision, mg_smoother=wsi.SMOOTH_CHEBYSHEV)
+    assert errs[0] < FIELD_TOL and errs[1] < FIELD_TOL and errs[3] < FIELD_TOL, errs
+
+
 def _sensitivity(g, m, c, b, xo, rel, seed=99):
     """Per-field relative change of the exact solution when b moves by a
     random residual of relative 2-norm `rel`: the accuracy any solver that
@@ -312,18 +325,37 @@ def test_transport_mixed_precision(k):
     assert _rel(C, flat(Co)) < 1e-5
 
 
+@pytest.mark.parametrize("limiter", ["cui", "xsppm7"])
 @pytest.mark.parametrize("precision", [wsi.PREC_FP64, wsi.PREC_MIXED])
-def test_levelset_parity(precision):
+def test_levelset_parity(precision, limiter):
     c, rng = _random_case(23, 17, 12, 7)
     g = _grid(c)
-    ctx = _ctx(c, precision=precision)
+    ctx = _ctx(c, precision=precision, ls_limiter=wsi.LIMIT_XSPPM7 if limiter == "xsppm7" else wsi.LIMIT_CUI)
     vel = [rng.uniform(-1, 1, g.face_shape(d)) * g.interior_face_mask(d) for d in range(3)]
     flat = lambda v: np.concatenate([a.ravel() for a in v])
     phih = c.phi + 0.01 * rng.standard_normal(c.phi.shape)
     got = ctx.advect_levelset(flat(vel), c.phi.ravel().copy(), phih.ravel().copy(), 1e-3)
-    ref = ols.advect(g, vel, c.phi, phih, 1e-3)
+    ref = ols.advect(g, vel, c.phi, phih, 1e-3, limiter=limiter)
     # float64: 1e-11; float32 flux arithmetic: the update dt*Q carries 1e-7
     assert _rel(got, ref.ravel()) < (OP_TOL if precision == wsi.PREC_FP64 else 1e-7)
+
+
+@pytest.mark.parametrize("shape", [(21, 13, 3), (9, 2, 5), (33, 17, 1)])
+def test_levelset_xsppm7_thin_grids(shape):
+    """xsPPM7 needs four ghost layers: on grids thinner than that the mirror
+    images reflect again (and a 2-D grid has one cell in z)."""
+    nx, ny, nz = shape
+    c, rng = _random_case(nx, ny, nz, 17)
+    if nz == 1:
+        c.lz = 1.0 / nx
+        c.bc = (-1.0, -1.0, -1.0, -1.0, 1.0, 1.0)
+    g = _grid(c)
+    ctx = _ctx(c, ls_limiter=wsi.LIMIT_XSPPM7)
+    vel = [rng.uniform(-1, 1, g.face_shape(d)) * g.interior_face_mask(d) for d in range(3)]
+    flat = lambda v: np.concatenate([a.ravel() for a in v])
+    phih = c.phi + 0.01 * rng.standard_normal(c.phi.shape)
+    got = ctx.advect_levelset(flat(vel), c.phi.ravel().copy(), phih.ravel().copy(), 1e-3)
+    assert _rel(got, ols.advect(g, vel, c.phi, phih, 1e-3, limiter="xsppm7").ravel()) < OP_TOL
 
 
 @pytest.mark.parametrize("precision", [wsi.PREC_FP64, wsi.PREC_MIXED])
@@ -437,3 +469,46 @@ def test_stokes_apply_mixed_double_float(shape):
     for d in range(3 if nz > 1 else 2):
         scale = np.abs(L[d]).max()
         assert np.abs(got_L[d] - L[d]).max() <= 1e-6 * scale + 1e-12 * np.abs(m.rho_face[d] / dt * vel[d]).max()
+
+
+def test_step_parity_prescribed_motion_slamming():
+    """A horizontal cylinder (rho_s = rho_l, all DOFs locked) driven down into
+    the water at V = 1 m/s (Sec. 8.5's water-entry set-up, scaled; gravity
+    from rho^flow since the motion is prescribed, Sec. 5): two steps on both
+    precision paths against the oracle's steps.  The markers move with the
+    prescribed velocity, psi is rebuilt about them every cycle, and the
+    Lagrange-multiplier force gives the slamming coefficient
+    C_s = F.e_z / (rho_l R V^2 L) (Sec. 8.5's C_s equation, per unit length
+    L of the cylinder), which must match the oracle's within the force
+    tolerance."""
+    from oracle import step as ost
+    V = 1.0
+    c = inputs.tank_cylinder(nxyz=(24, 8, 20), lxyz=(1.2, 0.4, 1.0), depth=0.5, radius=0.12, length=0.24,
+                             dt=2e-4, rho_s=1000.0)
+    c.gravity_mode = "flow"
+    c.lock = (True,) * 6
+    R, L = c.extra["cylinder"][0], 2 * c.extra["cylinder"][1]
+    g = _grid(c)
+    pr = ost.Props(rho_l=c.rho_l, rho_g=c.rho_g, rho_s=c.rho_s, mu_l=c.mu_l, mu_g=c.mu_g, gravity=c.gravity,
+                   gravity_mode="flow")
+    body = ost.Body(c.markers, c.dV, [True] * 6, U_pres=(0.0, 0.0, -V), cylinder=c.extra["cylinder"])
+    s = ost.State(g, pr, c.phi, c.psi, body)
+    infos = [ost.step(s, c.dt) for _ in range(2)]
+    cs_or = infos[-1]["F_lm"][2] / (c.rho_l * R * V * V * L)
+    for precision in (wsi.PREC_FP64, wsi.PREC_MIXED):
+        ctx = wsi.Context.from_case(c, precision=precision, restart=30)
+        ctx.set_case(c, U_pres=(0.0, 0.0, -V))
+        for _ in range(2):
+            st = ctx.step(c.dt, rtol=1e-13, max_iters=600)
+        _check_step_stats(st, infos[-1], s, c.rho_s, c.dV, len(c.markers), c.dt)
+        cs = st.F_lm[2] / (c.rho_l * R * V * V * L)
+        umax = max(np.abs(a).max() for a in s.vel)
+        tol = 10.0 * c.rho_s * c.dV / c.dt * len(c.markers) * FIELD_TOL * umax / (c.rho_l * R * V * V * L)
+        assert abs(cs - cs_or) <= tol, (precision, cs, cs_or, tol)
+        print("C_s after two steps (%s): %.6e (oracle %.6e)" % ("fp64" if precision == wsi.PREC_FP64 else "mixed",
+                                                              cs, cs_or))
+        vel = ctx.get_field(wsi.F_VEL)
+        assert _rel(vel, np.concatenate([a.ravel() for a in s.vel])) < FIELD_TOL, precision
+        assert _rel(ctx.get_field(wsi.F_PSI), s.psi.ravel()) < 1e-12, precision
+        assert _rel(ctx.get_field(wsi.F_MARKERS), s.body.X.ravel()) < 1e-12, precision
+        ctx.close()
