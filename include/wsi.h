@@ -134,6 +134,9 @@ typedef struct {
     double ms;
     int learned_rejected; /* wsi_pressure_solve: cycle whose learned correction
                              was undone (-1: none); else -1                   */
+    int guess;           /* wsi_pressure_solve with a guess network: 1 its
+                            initial guess was kept, 0 it was dropped (its
+                            residual was not below the zero guess's); else -1 */
 } wsi_solve_stats;
 
 typedef struct {
@@ -366,6 +369,21 @@ int wsi_unet_load(wsi_unet* net, const char* path);
 enum { WSI_LEARN_OFF = 0, WSI_LEARN_REPLACE = 1, WSI_LEARN_AUGMENT = 2 };
 int wsi_attach_unet(wsi_ctx* ctx, wsi_unet* net, int level, int enable);
 int wsi_unet_train_sample(wsi_ctx* ctx, const double* e, double lr, double* loss);
+
+/* Learned initial guess for wsi_pressure_solve (BASELINE workload: the
+ * network "supplies the initial guess"; not in the paper).
+ * wsi_attach_unet_guess: a network sized for multigrid level `level` of this
+ * (WSI_PREC_MIXED) context, or NULL to detach.  Its input is the level's
+ * restriction (cell averages) of the right-hand side with log rho and phi
+ * (as for wsi_attach_unet); its output o gives the level's solution s o / d,
+ * prolongated to the fine grid as the initial iterate, which is kept only if
+ * its residual is below the zero guess's (wsi_solve_stats.guess).
+ * wsi_unet_train_guess: one Adam step (lr = 0: evaluate) on a pair the
+ * solver generated: a fine right-hand side y and its solution x (cell
+ * fields, float64, host or device, x fastest); both are averaged down to the
+ * level and the loss 1/2 mean((o - d x_l / s)^2) is written to *loss. */
+int wsi_attach_unet_guess(wsi_ctx* ctx, wsi_unet* net, int level);
+int wsi_unet_train_guess(wsi_ctx* ctx, const double* y, const double* x, double lr, double* loss);
 
 /* Standalone pressure solve D(beta G) x = y (Sec. 4.2.4's projection
  * sub-problem) on the current coefficients: float64 residuals with

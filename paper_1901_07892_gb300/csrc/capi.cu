@@ -127,6 +127,10 @@ struct wsi_ctx {
   UNetImpl* unet_impl = nullptr;
   int unet_level = 0;
   bool unet_on = false;
+  SpreadWork sw;                  // deterministic spreading work arrays (allocated on first use)
+  double* mbox = nullptr;         // 6 doubles: marker extent
+  UNetImpl* gunet_impl = nullptr;  // initial-guess network (wsi_attach_unet_guess)
+  int gunet_level = 0;
   const double* phi_cur = nullptr;  // level set behind the current coefficients
   // wave tank relaxation zones (Sec. 7.1) and the time of the state
   bool has_waves = false;
@@ -159,6 +163,17 @@ double* dalloc(wsi_ctx* c, size_t n) {
   cudaMemsetAsync(p, 0, std::max<size_t>(n, 1) * sizeof(double), c->st);
   c->allocs.push_back(p);
   return (double*)p;
+}
+
+// deterministic spreading work arrays (zero-filled; they are left zero by
+// every spreading call)
+bool ensure_spread_work(wsi_ctx* c) {
+  if (c->sw.acc) return true;
+  c->sw.acc = (unsigned long long*)dalloc(c, c->nvel);
+  c->sw.cnt = (int*)dalloc(c, c->ncell / 2 + 1);
+  c->sw.qexp = (int*)dalloc(c, 1);
+  c->mbox = dalloc(c, 6);
+  return c->sw.acc && c->sw.cnt && c->sw.qexp && c->mbox;
 }
 
 void vel_parts(wsi_ctx* c, double* base, double* out[3]) {
@@ -255,8 +270,8 @@ int ensure_pc(wsi_ctx* c) {
   int rc = c->desc.precision == WSI_PREC_MIXED ? precond_setup<float>(c->P32, c->g, cf, c->st, c->err)
                                                : precond_setup<double>(c->P64, c->g, cf, c->st, c->err);
   if (rc == WSI_OK && c->mixed()) {
-    rc = learned_alloc(c->P32, c->unet_impl, c->unet_level, c->err);
-    if (rc == WSI_OK && c->unet_impl)
+    rc = learned_alloc(c->P32, c->unet_impl, c->unet_level, c->gunet_impl, c->gunet_level, c->err);
+    if (rc == WSI_OK && (c->unet_impl || c->gunet_impl))
       rc = learned_setup(c->P32, c->rho_cc, c->phi_cur ? c->phi_cur : c->phi, c->st, c->err);
     c->P32.learn.on = c->unet_on;
   }
@@ -469,12 +484,15 @@ int dlm_project(wsi_ctx* c, double* velv, const double* Xuse) {
   double* vq[3];
   vel_parts(c, velv, vq);
   const double* cq[3] = {vq[0], vq[1], vq[2]};
+  if (!ensure_spread_work(c)) return fail(c, WSI_ERR_OOM, "out of device memory for spreading");
   launch_marker_mean(Xuse, B.n, B.xc, B.scratch, c->st);
   launch_ib_interp(c->g, cq, Xuse, B.n, B.U, c->st);
   launch_rigid_sums(Xuse, B.U, B.n, B.xc, B.sums, B.scratch, c->st);
-  double hs[15], xc[3];
+  launch_marker_box(Xuse, B.n, c->mbox, c->st);
+  double hs[15], xc[3], mm[6];
   cudaMemcpyAsync(hs, B.sums, sizeof(hs), cudaMemcpyDeviceToHost, c->st);
   cudaMemcpyAsync(xc, B.xc, sizeof(xc), cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(mm, c->mbox, sizeof(mm), cudaMemcpyDeviceToHost, c->st);
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "dlm sums");
   double Ur[3], Wr[3] = {0, 0, 0};
   for (int d = 0; d < 3; ++d) Ur[d] = hs[d] / (double)B.n;
@@ -491,7 +509,7 @@ int dlm_project(wsi_ctx* c, double* velv, const double* Xuse) {
   double rg[6] = {Ur[0], Ur[1], Ur[2], Wr[0], Wr[1], Wr[2]};
   cudaMemcpyAsync(B.rig, rg, sizeof(rg), cudaMemcpyHostToDevice, c->st);
   launch_body_velocity(Xuse, B.U, B.n, B.rig, B.xc, B.Ub, B.F, c->st);
-  launch_ib_spread(c->g, B.F, Xuse, B.n, B.dV, vq, c->st);
+  launch_ib_spread(c->g, B.F, Xuse, B.n, B.dV, vq, c->sw, spread_box(c->g, mm), c->st);
   for (int d = 0; d < 3; ++d) {
     B.U_r[d] = Ur[d];
     B.W_r[d] = Wr[d];
@@ -1372,6 +1390,9 @@ int wsi_interp(wsi_ctx* c, const double* vel, const double* X, int n, double* U)
 
 int wsi_spread(wsi_ctx* c, const double* F, const double* X, int n, double dV, double* vel) {
   if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
+  // the work arrays first: the two staging buffers below must stay the last
+  // two allocations (they are released at the end)
+  if (!ensure_spread_work(c)) return fail(c, WSI_ERR_OOM, "out of device memory for spreading");
   double* dX = dalloc(c, (size_t)std::max(n, 1) * 3);
   double* dF = dalloc(c, (size_t)std::max(n, 1) * 3);
   if (!dX || !dF) return fail(c, WSI_ERR_OOM, "out of device memory");
@@ -1384,7 +1405,11 @@ int wsi_spread(wsi_ctx* c, const double* F, const double* X, int n, double dV, d
     cudaMemsetAsync(c->vel_half, 0, c->nvel * sizeof(double), c->st);
     double* vq[3];
     vel_parts(c, c->vel_half, vq);
-    launch_ib_spread(c->g, dF, dX, n, dV, vq, c->st);
+    double mm[6];
+    launch_marker_box(dX, n, c->mbox, c->st);
+    cudaMemcpyAsync(mm, c->mbox, sizeof(mm), cudaMemcpyDeviceToHost, c->st);
+    cudaStreamSynchronize(c->st);
+    launch_ib_spread(c->g, dF, dX, n, dV, vq, c->sw, spread_box(c->g, mm), c->st);
     rc = copy_out(c, vel, c->vel_half, c->nvel);
   }
   cudaStreamSynchronize(c->st);
@@ -1668,6 +1693,35 @@ int wsi_attach_unet(wsi_ctx* c, wsi_unet* n, int level, int enable) {
   return WSI_OK;
 }
 
+int wsi_attach_unet_guess(wsi_ctx* c, wsi_unet* n, int level) {
+  if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
+  if (!c->mixed()) return fail(c, WSI_ERR_INVALID_ARG, "the learned guess needs a WSI_PREC_MIXED context");
+  c->gunet_impl = n ? n->u : nullptr;
+  c->gunet_level = level;
+  c->pc_dirty = true;
+  return WSI_OK;
+}
+
+int wsi_unet_train_guess(wsi_ctx* c, const double* y, const double* x, double lr, double* loss) {
+  if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
+  if (!c->gunet_impl || !c->have_phases) return fail(c, WSI_ERR_INVALID_ARG, "attach a guess network and set phases first");
+  int rc = ensure_pc(c);
+  if (rc) return rc;
+  Precond<float>& P = c->P32;
+  const size_t n = c->ncell;
+  // float64 staging in the Krylov work space, then float32 on the level-0 grid
+  double* ys = c->V;
+  double* xs = c->V + n;
+  rc = copy_in(c, ys, y, n);
+  if (!rc) rc = copy_in(c, xs, x, n);
+  if (rc) return rc;
+  launch_lincomb_to_f32(n, 1.0, ys, 0.0, nullptr, 0.0, nullptr, P.lev[0].b, c->st);
+  launch_lincomb_to_f32(n, 1.0, xs, 0.0, nullptr, 0.0, nullptr, P.lev[0].x, c->st);
+  learned_train_guess(P, P.lev[0].b, P.lev[0].x, lr, c->st);
+  if (loss) cudaMemcpyAsync(loss, learned_guess_loss(P), sizeof(double), cudaMemcpyDeviceToHost, c->st);
+  return cuda_check(c, "unet_train_guess");
+}
+
 int wsi_unet_train_sample(wsi_ctx* c, const double* e, double lr, double* loss) {
   if (valid_ctx(c)) return WSI_ERR_INVALID_ARG;
   if (!c->unet || !c->have_phases) return fail(c, WSI_ERR_INVALID_ARG, "attach a network and set phases first");
@@ -1691,6 +1745,7 @@ int wsi_pressure_solve(wsi_ctx* c, const double* y, double* x, double rtol, int 
   if (!c->have_phases) return fail(c, WSI_ERR_INVALID_ARG, "wsi_set_phases must come first");
   if (!(rtol > 0.0) || max_cycles < 1 || !s) return fail(c, WSI_ERR_INVALID_ARG, "bad options");
   s->learned_rejected = -1;
+  s->guess = -1;
   auto t0 = std::chrono::steady_clock::now();
   int rc = ensure_pc(c);
   if (rc) return rc;
@@ -1707,6 +1762,22 @@ int wsi_pressure_solve(wsi_ctx* c, const double* y, double* x, double rtol, int 
   cudaMemsetAsync(xv, 0, n * sizeof(double), st);
   const double ynorm = host_norm2(yv, n, c->red, st);
   const double* bt[3] = {c->beta[0], c->beta[1], c->beta[2]};
+  if (c->mixed() && c->gunet_impl && ynorm > 0.0) {
+    // learned initial guess: the guess network's coarse solution of the
+    // restricted right-hand side, prolongated; kept only if its residual is
+    // below that of the zero guess
+    MGLevel<float>& L0 = c->P32.lev[0];
+    launch_lincomb_to_f32(n, 1.0 / ynorm, yv, 0.0, nullptr, 0.0, nullptr, L0.b, st);
+    learned_guess(c->P32, L0.b, st);
+    launch_lincomb_mix(n, 0.0, xv, ynorm, L0.x, 0.0, L0.x, xv, st);
+    launch_sum<double>(xv, n, c->hdev, c->red, st);
+    launch_add_scalar_from<double>(xv, n, c->hdev, -1.0 / (double)n, st);
+    launch_pressure<double>(g, bt, xv, r, st);
+    launch_lincomb(n, 1.0, yv, -1.0, r, 0.0, nullptr, r, st);
+    const double r0 = host_norm2(r, n, c->red, st);
+    s->guess = (std::isfinite(r0) && r0 < ynorm) ? 1 : 0;
+    if (!s->guess) cudaMemsetAsync(xv, 0, n * sizeof(double), st);
+  }
   // The plain V-cycle judges the network: the first two cycles are plain and
   // the second one's residual reduction is the bar; a learned cycle that
   // reduces the residual less is undone and the solve continues plain.

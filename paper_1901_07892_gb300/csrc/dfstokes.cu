@@ -40,6 +40,9 @@ static constexpr int FKC = 16; // z-levels per thread
 #ifndef WSI_MV_PREFETCH
 #define WSI_MV_PREFETCH 0
 #endif
+#ifndef WSI_MV_PF
+#define WSI_MV_PF "prefetch.global.L2 [%0];"
+#endif
 
 struct HtConst {
   ht ih[3];       // 1/h
@@ -148,17 +151,33 @@ __global__ void __launch_bounds__(32 * FBY) k_stokes_df(HtConst K, DfCoef cf, Df
     {
       const int kq = k + WSI_MV_PREFETCH;
       if (kq < nz) {
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(U + iff + j * su1 + kq * su2));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(V + ic + j * sv1 + kq * sv2));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(W + ic + j * sc1 + kq * sc2));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(P + ic + j * sc1 + kq * sc2));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(cf.mu_cc + ic + j * sc1 + kq * sc2));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(cf.mu_e[0] + iff + j * sxy1 + kq * sxy2));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(cf.mu_e[1] + iff + j * sxz1 + kq * sxz2));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(cf.mu_e[2] + ic + j * syz1 + kq * syz2));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(cf.rho_face[0] + iff + j * su1 + kq * su2));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(cf.rho_face[1] + ic + j * sv1 + kq * sv2));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(cf.rho_face[2] + ic + j * sc1 + kq * sc2));
+        asm volatile(WSI_MV_PF ::"l"(U + iff + j * su1 + kq * su2));
+        asm volatile(WSI_MV_PF ::"l"(V + ic + j * sv1 + kq * sv2));
+        asm volatile(WSI_MV_PF ::"l"(W + ic + j * sc1 + kq * sc2));
+        asm volatile(WSI_MV_PF ::"l"(P + ic + j * sc1 + kq * sc2));
+        asm volatile(WSI_MV_PF ::"l"(cf.mu_cc + ic + j * sc1 + kq * sc2));
+        asm volatile(WSI_MV_PF ::"l"(cf.mu_e[0] + iff + j * sxy1 + kq * sxy2));
+        asm volatile(WSI_MV_PF ::"l"(cf.mu_e[1] + iff + j * sxz1 + kq * sxz2));
+        asm volatile(WSI_MV_PF ::"l"(cf.mu_e[2] + ic + j * syz1 + kq * syz2));
+        asm volatile(WSI_MV_PF ::"l"(cf.rho_face[0] + iff + j * su1 + kq * su2));
+        asm volatile(WSI_MV_PF ::"l"(cf.rho_face[1] + ic + j * sv1 + kq * sv2));
+        asm volatile(WSI_MV_PF ::"l"(cf.rho_face[2] + ic + j * sc1 + kq * sc2));
+#ifdef WSI_MV_PF_ROWS
+        if (threadIdx.y == 0 && j > 0) {
+          asm volatile(WSI_MV_PF ::"l"(U + iff + (j - 1) * su1 + kq * su2));
+          asm volatile(WSI_MV_PF ::"l"(V + ic + (j - 1) * sv1 + kq * sv2));
+          asm volatile(WSI_MV_PF ::"l"(W + ic + (j - 1) * sc1 + kq * sc2));
+          asm volatile(WSI_MV_PF ::"l"(P + ic + (j - 1) * sc1 + kq * sc2));
+          asm volatile(WSI_MV_PF ::"l"(cf.mu_cc + ic + (j - 1) * sc1 + kq * sc2));
+        }
+        if (threadIdx.y == FBY - 1 && j + 1 < ny) {
+          asm volatile(WSI_MV_PF ::"l"(U + iff + (j + 1) * su1 + kq * su2));
+          asm volatile(WSI_MV_PF ::"l"(V + ic + (j + 2) * sv1 + kq * sv2));
+          asm volatile(WSI_MV_PF ::"l"(W + ic + (j + 1) * sc1 + kq * sc2));
+          asm volatile(WSI_MV_PF ::"l"(cf.mu_e[0] + iff + (j + 1) * sxy1 + kq * sxy2));
+          asm volatile(WSI_MV_PF ::"l"(cf.mu_e[2] + ic + (j + 1) * syz1 + kq * syz2));
+        }
+#endif
       }
     }
 #endif

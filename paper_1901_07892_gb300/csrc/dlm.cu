@@ -125,10 +125,38 @@ __global__ void __launch_bounds__(128) k_interp(GridDev g, CVel<double> vel, con
   }
 }
 
+// Deterministic spreading.  Float64 atomics would sum each face's
+// contributions in a varying order; instead every contribution is rounded to
+// a multiple of a power-of-two quantum 2^-E and added as a 64-bit integer,
+// whose sum does not depend on the order.  E is chosen on the device per call
+// from a bound on any face's sum: at most 5 cells per axis hold markers whose
+// taps reach a face (twice that count where taps fold at a wall), each tap
+// weight is at most phi4(0)^3 = 1/8, so |sum| <= 128 c_max max|F| scale with
+// c_max the most markers in one cell; E puts that bound below 2^61.  The
+// quantum is then ~2^-50 of the largest contribution.
+
+// integer nearest to f 2^E for a float f with |f 2^E| < 2^62 (integer
+// operations on the bit pattern; ties away from zero)
+__device__ __forceinline__ long long fixed_of(float f, int E) {
+  const unsigned u = __float_as_uint(f);
+  const int ex = (int)((u >> 23) & 0xFFu);
+  if (ex == 0) return 0;  // zero (and subnormals, < 2^-126)
+  const long long m = (long long)((u & 0x7FFFFFu) | 0x800000u);
+  const int sh = ex - 150 + E;  // f 2^E = m 2^sh
+  long long v;
+  if (sh >= 0) v = m << sh;
+  else if (sh > -25) v = (m + (1LL << (-sh - 1))) >> (-sh);
+  else v = 0;
+  return (u & 0x80000000u) ? -v : v;
+}
+
 __global__ void __launch_bounds__(128) k_spread(GridDev g, const double* __restrict__ F,
-                                                const double* __restrict__ X, int n, double scale, Vel<double> vel) {
+                                                const double* __restrict__ X, int n, double scale,
+                                                unsigned long long* acc0, unsigned long long* acc1,
+                                                unsigned long long* acc2, const int* __restrict__ qexp) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n) return;
+  const int E = qexp[0];
   MarkerTaps T;
   marker_taps(g, X, m, T);
   const dfl sc = df_split(scale);
@@ -137,7 +165,7 @@ __global__ void __launch_bounds__(128) k_spread(GridDev g, const double* __restr
     const Tap& tx = c == 0 ? T.tn[0] : T.tt[0];
     const Tap& ty = c == 1 ? T.tn[1] : T.tt[1];
     const Tap& tz = c == 2 ? T.tn[2] : T.tt[2];
-    double* q = vel.q[c];
+    unsigned long long* q = c == 0 ? acc0 : (c == 1 ? acc1 : acc2);
     const size_t sx = (size_t)(g.n[0] + (c == 0)), sy = sx * (size_t)(g.n[1] + (c == 1));
     const dfl f = df_mul(df_split(F[3 * m + c]), sc);
     dfl fx[4];
@@ -150,11 +178,85 @@ __global__ void __launch_bounds__(128) k_spread(GridDev g, const double* __restr
       for (int ky = 0; ky < 4; ++ky) {
         if (ty.w[ky].h == 0.0f) continue;
         const dfl wyz = df_mul(tz.w[kz], ty.w[ky]);
-        double* row = q + (size_t)tz.idx[kz] * sy + (size_t)ty.idx[ky] * sx;
+        unsigned long long* row = q + (size_t)tz.idx[kz] * sy + (size_t)ty.idx[ky] * sx;
 #pragma unroll
         for (int kx = 0; kx < 4; ++kx)
-          if (tx.w[kx].h != 0.0f) atomicAdd(&row[tx.idx[kx]], df_to_double(df_mul(wyz, fx[kx])));
+          if (tx.w[kx].h != 0.0f) {
+            const dfl v = df_mul(wyz, fx[kx]);
+            atomicAdd(&row[tx.idx[kx]], (unsigned long long)(fixed_of(v.h, E) + fixed_of(v.l, E)));
+          }
       }
+    }
+  }
+}
+
+// markers per cell (the cell holding each marker, clamped into the grid)
+__global__ void k_marker_count(GridDev g, const double* __restrict__ X, int n, int* cnt) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n) return;
+  int c[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) c[d] = clampi((int)floor(X[3 * m + d] * g.ih[d]), 0, g.n[d] - 1);
+  atomicAdd(&cnt[fidx(g, 3, c[0], c[1], c[2])], 1);
+}
+
+// one block: E from the largest cell count in the box and max |F| scale;
+// the box's counts are cleared for the next call
+__global__ void k_spread_exponent(GridDev g, SpreadBox b, int* cnt, const double* __restrict__ F, int n3,
+                                  double scale, int* qexp) {
+  __shared__ int shc[32];
+  __shared__ double shf[32];
+  const int ex = b.hi[0] - b.lo[0] + 1, ey = b.hi[1] - b.lo[1] + 1, ez = b.hi[2] - b.lo[2] + 1;
+  const long long nb = (long long)ex * ey * ez;
+  int cm = 0;
+  for (long long t = threadIdx.x; t < nb; t += blockDim.x) {
+    const int i = b.lo[0] + (int)(t % ex), j = b.lo[1] + (int)((t / ex) % ey), k = b.lo[2] + (int)(t / ((long long)ex * ey));
+    cm = max(cm, cnt[fidx(g, 3, i, j, k)]);
+  }
+  double fm = 0.0;
+  for (int t = threadIdx.x; t < n3; t += blockDim.x) fm = fmax(fm, fabs(F[t]));
+  for (int o = 16; o > 0; o >>= 1) {
+    cm = max(cm, __shfl_down_sync(0xffffffffu, cm, o));
+    fm = fmax(fm, __shfl_down_sync(0xffffffffu, fm, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    shc[threadIdx.x >> 5] = cm;
+    shf[threadIdx.x >> 5] = fm;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int c = 0;
+    double f = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      c = max(c, shc[w]);
+      f = fmax(f, shf[w]);
+    }
+    const double B = 128.0 * (double)c * f * scale;
+    int e = 0;
+    if (B > 0.0 && B < 1e300) frexp(B, &e);  // B < 2^e
+    qexp[0] = (B > 0.0 && B < 1e300) ? 61 - e : 0;
+  }
+  __syncthreads();
+  for (long long t = threadIdx.x; t < nb; t += blockDim.x) {
+    const int i = b.lo[0] + (int)(t % ex), j = b.lo[1] + (int)((t / ex) % ey), k = b.lo[2] + (int)(t / ((long long)ex * ey));
+    cnt[fidx(g, 3, i, j, k)] = 0;
+  }
+}
+
+// vel += acc 2^-E on the box's faces of component C; acc cleared
+template <int C>
+__global__ void k_unfix(GridDev g, SpreadBox b, unsigned long long* acc, const int* __restrict__ qexp, double* vel) {
+  const int ex = b.hi[0] - b.lo[0] + 1 + (C == 0), ey = b.hi[1] - b.lo[1] + 1 + (C == 1);
+  const int ez = b.hi[2] - b.lo[2] + 1 + (C == 2);
+  const long long nb = (long long)ex * ey * ez;
+  const double q = ldexp(1.0, -qexp[0]);
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nb; t += (long long)gridDim.x * blockDim.x) {
+    const int i = b.lo[0] + (int)(t % ex), j = b.lo[1] + (int)((t / ex) % ey), k = b.lo[2] + (int)(t / ((long long)ex * ey));
+    const size_t id = fidx(g, C, i, j, k);
+    const long long a = (long long)acc[id];
+    if (a != 0) {
+      vel[id] += (double)a * q;
+      acc[id] = 0ull;
     }
   }
 }
@@ -166,12 +268,64 @@ void launch_ib_interp(const GridDev& g, const double* const vel[3], const double
   { k_interp<<<cdiv(n, 128), 128, 0, st>>>(g, v, X, n, U); WSI_COUNT(); }
 }
 
+SpreadBox spread_box(const GridDev& g, const double mm[6]) {
+  SpreadBox b;
+  for (int d = 0; d < 3; ++d) {
+    b.lo[d] = std::max(0, (int)std::floor(mm[d] * g.ih[d] - 0.5) - 3);
+    b.hi[d] = std::min(g.n[d] - 1, (int)std::floor(mm[3 + d] * g.ih[d]) + 3);
+    if (b.hi[d] < b.lo[d]) b.hi[d] = b.lo[d];
+  }
+  return b;
+}
+
 void launch_ib_spread(const GridDev& g, const double* F, const double* X, int n, double dV, double* const vel[3],
-                      cudaStream_t st) {
+                      const SpreadWork& w, const SpreadBox& b, cudaStream_t st) {
   if (n <= 0) return;
-  Vel<double> v{{vel[0], vel[1], vel[2]}};
-  double scale = dV / (g.h[0] * g.h[1] * g.h[2]);
-  { k_spread<<<cdiv(n, 128), 128, 0, st>>>(g, F, X, n, scale, v); WSI_COUNT(); }
+  const double scale = dV / (g.h[0] * g.h[1] * g.h[2]);
+  unsigned long long* acc[3] = {w.acc, w.acc + fsize(g, 0), w.acc + fsize(g, 0) + fsize(g, 1)};
+  { k_marker_count<<<cdiv(n, 256), 256, 0, st>>>(g, X, n, w.cnt); WSI_COUNT(); }
+  { k_spread_exponent<<<1, 1024, 0, st>>>(g, b, w.cnt, F, 3 * n, scale, w.qexp); WSI_COUNT(); }
+  { k_spread<<<cdiv(n, 128), 128, 0, st>>>(g, F, X, n, scale, acc[0], acc[1], acc[2], w.qexp); WSI_COUNT(); }
+  const long long nb = (long long)(b.hi[0] - b.lo[0] + 2) * (b.hi[1] - b.lo[1] + 2) * (b.hi[2] - b.lo[2] + 2);
+  const int blocks = (int)std::min<long long>((nb + 255) / 256, 152 * 8);
+  { k_unfix<0><<<blocks, 256, 0, st>>>(g, b, acc[0], w.qexp, vel[0]); WSI_COUNT(); }
+  { k_unfix<1><<<blocks, 256, 0, st>>>(g, b, acc[1], w.qexp, vel[1]); WSI_COUNT(); }
+  { k_unfix<2><<<blocks, 256, 0, st>>>(g, b, acc[2], w.qexp, vel[2]); WSI_COUNT(); }
+}
+
+// min (0..2) and max (3..5) of the marker positions, one block
+__global__ void k_marker_box(const double* __restrict__ X, int n, double* out) {
+  __shared__ double sh[6][32];
+  double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+  for (int m = threadIdx.x; m < n; m += blockDim.x)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      mn[d] = fmin(mn[d], X[3 * m + d]);
+      mx[d] = fmax(mx[d], X[3 * m + d]);
+    }
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    for (int o = 16; o > 0; o >>= 1) {
+      mn[d] = fmin(mn[d], __shfl_down_sync(0xffffffffu, mn[d], o));
+      mx[d] = fmax(mx[d], __shfl_down_sync(0xffffffffu, mx[d], o));
+    }
+  if ((threadIdx.x & 31) == 0)
+    for (int d = 0; d < 3; ++d) {
+      sh[d][threadIdx.x >> 5] = mn[d];
+      sh[3 + d][threadIdx.x >> 5] = mx[d];
+    }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double v = sh[threadIdx.x][0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      v = threadIdx.x < 3 ? fmin(v, sh[threadIdx.x][w]) : fmax(v, sh[threadIdx.x][w]);
+    out[threadIdx.x] = v;
+  }
+}
+
+void launch_marker_box(const double* X, int n, double* out6, cudaStream_t st) {
+  if (n <= 0) return;
+  { k_marker_box<<<1, 1024, 0, st>>>(X, n, out6); WSI_COUNT(); }
 }
 
 // ---------------------------------------------------------------- rigid sums

@@ -180,6 +180,11 @@ struct LearnState {
   float* t2 = nullptr;
   float* t3 = nullptr;
   double* ss = nullptr;  // [0] sum of squares of the network input, [1] training loss
+  // initial-guess network: the level-g solution from the restricted right-hand side
+  UNetImpl* gnet = nullptr;
+  int glevel = 0;
+  float* gdiag = nullptr;
+  double* gss = nullptr;  // [0] sum of squares of the guess network's input
 };
 
 // ---------------------------------------------------------------- mg.cu
@@ -272,7 +277,18 @@ void learned_correction(Precond<float>& P, int level, const float* rhs, bool add
 // is the residual norm of the correction plus a small error term.
 void learned_train(Precond<float>& P, const Opts& o, const float* e, double lr, cudaStream_t st);
 const double* learned_loss(const Precond<float>& P);
-int learned_alloc(Precond<float>& P, UNetImpl* net, int level, std::string& err);
+int learned_alloc(Precond<float>& P, UNetImpl* net, int level, UNetImpl* gnet, int glevel, std::string& err);
+// initial guess: P.lev[0].x = prolongation of the guess network's level-g
+// solution for the fine right-hand side b0 (float, the level-0 grid)
+void learned_guess(Precond<float>& P, const float* b0, cudaStream_t st);
+// one Adam step of the guess network on a solver-generated pair (fine
+// right-hand side y and its solution x, float on the level-0 grid): both
+// averaged down to level g; loss 1/2 mean((o - d x_g / s)^2)
+void learned_train_guess(Precond<float>& P, const float* y, const float* x, double lr, cudaStream_t st);
+const double* learned_guess_loss(const Precond<float>& P);
+// lev[from].x carried to level 0: each finer x set to the prolongation
+template <typename T>
+void precond_prolong_chain(Precond<T>& P, int from, cudaStream_t st);
 // one V-cycle on level 0 of the hierarchy (x, b of level 0)
 template <typename T>
 void precond_vcycle(Precond<T>& P, const Opts& o, cudaStream_t st);
@@ -283,8 +299,21 @@ void precond_coarse_part(Precond<T>& P, const Opts& o, int l, cudaStream_t st);
 // ---------------------------------------------------------------- dlm.cu
 void launch_ib_interp(const GridDev& g, const double* const vel[3], const double* X, int n, double* U,
                       cudaStream_t st);
+// deterministic spreading (fixed-point integer sums): work arrays that stay
+// zero between calls, and the box of cells the markers' taps can reach
+struct SpreadWork {
+  unsigned long long* acc = nullptr;  // one per face of the packed velocity
+  int* cnt = nullptr;                 // one per cell
+  int* qexp = nullptr;                // quantum exponent of the current call
+};
+struct SpreadBox {
+  int lo[3], hi[3];  // cells, inclusive
+};
+// box from the marker extent mm = (min x, y, z, max x, y, z)
+SpreadBox spread_box(const GridDev& g, const double mm[6]);
+void launch_marker_box(const double* X, int n, double* out6, cudaStream_t st);
 void launch_ib_spread(const GridDev& g, const double* F, const double* X, int n, double dV, double* const vel[3],
-                      cudaStream_t st);
+                      const SpreadWork& w, const SpreadBox& b, cudaStream_t st);
 // rigid sums: out[0..2] sum U, [3..5] sum R x U, [6..11] sum of R.R I - R (x) R (xx,yy,zz,xy,xz,yz),
 // [12..14] sum X; R relative to xc_dev
 void launch_rigid_sums(const double* X, const double* U, int n, const double* xc_dev, double* out, double* scratch,

@@ -130,19 +130,23 @@ __global__ void k_apply_out(const float* __restrict__ o, const float* __restrict
 // phi and a built hierarchy
 int learned_setup(Precond<float>& P, const double* rho_cc, const double* phi, cudaStream_t st, std::string& err) {
   LearnState& S = P.learn;
-  if (!S.net) return WSI_OK;
-  if (S.level < 1 || S.level >= (int)P.lev.size()) {
+  if (!S.net && !S.gnet) return WSI_OK;
+  const int top = std::max(S.net ? S.level : 0, S.gnet ? S.glevel : 0);
+  if (top < 1 || top >= (int)P.lev.size()) {
     err = "learned correction level outside the multigrid hierarchy";
     return WSI_ERR_INVALID_ARG;
   }
-  const MGLevel<float>& Lc = P.lev[S.level];
-  if (Lc.g.n[0] != unet_dim(S.net, 2) || Lc.g.n[1] != unet_dim(S.net, 1) || Lc.g.n[2] != unet_dim(S.net, 0)) {
+  auto fits = [&](UNetImpl* net, int l) {
+    const GridDev& gg = P.lev[l].g;
+    return gg.n[0] == unet_dim(net, 2) && gg.n[1] == unet_dim(net, 1) && gg.n[2] == unet_dim(net, 0);
+  };
+  if ((S.net && !fits(S.net, S.level)) || (S.gnet && !fits(S.gnet, S.glevel))) {
     err = "network dimensions differ from the multigrid level";
     return WSI_ERR_INVALID_ARG;
   }
-  // average log(rho) and phi down to the level
+  // average log(rho) and phi down to the deepest level a network uses
   const GridDev& g0 = P.lev[0].g;
-  for (int l = 1; l <= S.level; ++l) {
+  for (int l = 1; l <= top; ++l) {
     const MGLevel<float>& F = P.lev[l - 1];
     const GridDev& gc = P.lev[l].g;
     dim3 gr = grid3(gc.n[0], gc.n[1], gc.n[2]);
@@ -155,11 +159,78 @@ int learned_setup(Precond<float>& P, const double* rho_cc, const double* phi, cu
     }
   }
   (void)g0;
-  { k_diag<<<grid3(Lc.g.n[0], Lc.g.n[1], Lc.g.n[2]), dim3(BX, BY), 0, st>>>(Lc.g, Lc.beta[0], Lc.beta[1], Lc.beta[2],
-                                                                            S.diag); WSI_COUNT(); }
+  if (S.net) {
+    const MGLevel<float>& Lc = P.lev[S.level];
+    { k_diag<<<grid3(Lc.g.n[0], Lc.g.n[1], Lc.g.n[2]), dim3(BX, BY), 0, st>>>(Lc.g, Lc.beta[0], Lc.beta[1],
+                                                                              Lc.beta[2], S.diag); WSI_COUNT(); }
+  }
+  if (S.gnet) {
+    const MGLevel<float>& Lg = P.lev[S.glevel];
+    { k_diag<<<grid3(Lg.g.n[0], Lg.g.n[1], Lg.g.n[2]), dim3(BX, BY), 0, st>>>(Lg.g, Lg.beta[0], Lg.beta[1],
+                                                                              Lg.beta[2], S.gdiag); WSI_COUNT(); }
+  }
   S.ready = true;
   return WSI_OK;
 }
+
+// fine field f (level 0) averaged down to level top, into buf[l] (l >= 1)
+static void avg_chain(Precond<float>& P, const float* f, int top, float* const* buf, cudaStream_t st) {
+  const float* src = f;
+  for (int l = 1; l <= top; ++l) {
+    const MGLevel<float>& F = P.lev[l - 1];
+    const GridDev& gc = P.lev[l].g;
+    { k_avg_down<float><<<grid3(gc.n[0], gc.n[1], gc.n[2]), dim3(BX, BY), 0, st>>>(F.g, gc, F.r[0], F.r[1], F.r[2],
+                                                                                  src, buf[l], 0); WSI_COUNT(); }
+    src = buf[l];
+  }
+}
+
+void learned_guess(Precond<float>& P, const float* b0, cudaStream_t st) {
+  LearnState& S = P.learn;
+  const int lg = S.glevel;
+  std::vector<float*> bb(P.lev.size());
+  for (size_t l = 0; l < P.lev.size(); ++l) bb[l] = P.lev[l].b;
+  avg_chain(P, b0, lg, bb.data(), st);  // the right-hand side of x = 0 restricts to its average
+  MGLevel<float>& L = P.lev[lg];
+  const size_t n = fsize(L.g, 3);
+  cudaMemsetAsync(S.gss, 0, sizeof(double), st);
+  { k_sumsq<<<nb(n), 256, 0, st>>>(L.b, n, S.gss); WSI_COUNT(); }
+  { k_assemble<<<nb(n), 256, 0, st>>>(S.lrho[lg], S.phi[lg], L.b, S.gss, n, unet_input(S.gnet)); WSI_COUNT(); }
+  unet_forward(S.gnet, st);
+  { k_apply_out<<<nb(n), 256, 0, st>>>(unet_output(S.gnet), S.gdiag, S.gss, n, 0, L.x); WSI_COUNT(); }
+  precond_prolong_chain<float>(P, lg, st);
+}
+
+// target d x / s of the guess network (its output o gives x = s o / d)
+__global__ void k_guess_target(const float* __restrict__ x, const float* __restrict__ d,
+                               const double* __restrict__ ss, size_t n, float* tgt) {
+  const float is = (float)(1.0 / sqrt(fmax(ss[0] / (double)n, 1e-300)));
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x)
+    tgt[v] = d[v] * x[v] * is;
+}
+
+void learned_train_guess(Precond<float>& P, const float* y, const float* x, double lr, cudaStream_t st) {
+  LearnState& S = P.learn;
+  const int lg = S.glevel;
+  std::vector<float*> bb(P.lev.size()), xx(P.lev.size());
+  for (size_t l = 0; l < P.lev.size(); ++l) {
+    bb[l] = P.lev[l].b;
+    xx[l] = P.lev[l].res;
+  }
+  avg_chain(P, y, lg, bb.data(), st);
+  avg_chain(P, x, lg, xx.data(), st);
+  MGLevel<float>& L = P.lev[lg];
+  const size_t n = fsize(L.g, 3);
+  cudaMemsetAsync(S.gss, 0, sizeof(double), st);
+  { k_sumsq<<<nb(n), 256, 0, st>>>(L.b, n, S.gss); WSI_COUNT(); }
+  { k_assemble<<<nb(n), 256, 0, st>>>(S.lrho[lg], S.phi[lg], L.b, S.gss, n, unet_input(S.gnet)); WSI_COUNT(); }
+  unet_forward(S.gnet, st);
+  { k_guess_target<<<nb(n), 256, 0, st>>>(L.res, S.gdiag, S.gss, n, unet_target(S.gnet)); WSI_COUNT(); }
+  unet_backward(S.gnet, st);
+  if (lr > 0.0) unet_adam(S.gnet, lr, st);
+}
+
+const double* learned_guess_loss(const Precond<float>& P) { return unet_loss(P.learn.gnet); }
 
 // x_level = (or +=) network correction for rhs on level l
 void learned_correction(Precond<float>& P, int l, const float* rhs, bool add, cudaStream_t st) {

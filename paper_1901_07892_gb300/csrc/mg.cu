@@ -661,13 +661,27 @@ void precond_vcycle(Precond<T>& P, const Opts& o, cudaStream_t st) {
 template void precond_vcycle<double>(Precond<double>&, const Opts&, cudaStream_t);
 template void precond_vcycle<float>(Precond<float>&, const Opts&, cudaStream_t);
 
-int learned_alloc(Precond<float>& P, UNetImpl* net, int level, std::string& err) {
+template <typename T>
+void precond_prolong_chain(Precond<T>& P, int from, cudaStream_t st) {
+  for (int l = from - 1; l >= 0; --l) {
+    MGLevel<T>& L = P.lev[l];
+    const GridDev& g = L.g;
+    cudaMemsetAsync(L.x, 0, fsize(g, 3) * sizeof(T), st);
+    { k_prolong_add<T><<<grid3(g.n[0], g.n[1], g.n[2]), dim3(BX, BY), 0, st>>>(g, P.lev[l + 1].g, L.r[0], L.r[1],
+                                                                              L.r[2], P.lev[l + 1].x, L.x); WSI_COUNT(); }
+  }
+}
+template void precond_prolong_chain<float>(Precond<float>&, int, cudaStream_t);
+
+int learned_alloc(Precond<float>& P, UNetImpl* net, int level, UNetImpl* gnet, int glevel, std::string& err) {
   LearnState& S = P.learn;
   S.net = net;
   S.level = level;
+  S.gnet = gnet;
+  S.glevel = glevel;
   S.ready = false;
-  if (!net) return WSI_OK;
-  if (level < 1 || level >= (int)P.lev.size()) {
+  if (!net && !gnet) return WSI_OK;
+  if ((net && (level < 1 || level >= (int)P.lev.size())) || (gnet && (glevel < 1 || glevel >= (int)P.lev.size()))) {
     err = "learned correction level outside the multigrid hierarchy";
     return WSI_ERR_INVALID_ARG;
   }
@@ -686,7 +700,9 @@ int learned_alloc(Precond<float>& P, UNetImpl* net, int level, std::string& err)
     S.t2 = dalloc<float>(P.allocs, nmax, err);
     S.t3 = dalloc<float>(P.allocs, nmax, err);
     S.ss = dalloc<double>(P.allocs, 4, err);
-    if (!S.diag || !S.e || !S.t1 || !S.t2 || !S.t3 || !S.ss) return WSI_ERR_OOM;
+    S.gdiag = dalloc<float>(P.allocs, nmax, err);
+    S.gss = dalloc<double>(P.allocs, 4, err);
+    if (!S.diag || !S.e || !S.t1 || !S.t2 || !S.t3 || !S.ss || !S.gdiag || !S.gss) return WSI_ERR_OOM;
   }
   return WSI_OK;
 }

@@ -30,7 +30,8 @@ EXPORTED = ["wsi_stokes_size", "wsi_velocity_size", "wsi_create_grid", "wsi_dest
             "wsi_unet_set_params", "wsi_unet_get_params", "wsi_unet_get_grads", "wsi_unet_forward",
             "wsi_unet_backward", "wsi_unet_adam", "wsi_attach_unet", "wsi_unet_train_sample",
             "wsi_pressure_solve", "wsi_checkpoint", "wsi_restore", "wsi_unet_save", "wsi_unet_load",
-            "wsi_norm2_noalloc", "wsi_reinit", "wsi_fma_peak", "wsi_ktimer_bytes"]
+            "wsi_norm2_noalloc", "wsi_reinit", "wsi_fma_peak", "wsi_ktimer_bytes", "wsi_attach_unet_guess",
+            "wsi_unet_train_guess"]
 FORM_CONSISTENT, FORM_NONCONSERVATIVE = 0, 1
 SMOOTH_RBGS, SMOOTH_CHEBYSHEV = 0, 1
 LIMIT_CUI, LIMIT_XSPPM7 = 0, 1
@@ -66,7 +67,7 @@ class SolveOpts(ctypes.Structure):
 
 class SolveStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("rel_residual", ctypes.c_double), ("ms", ctypes.c_double),
-                ("learned_rejected", ctypes.c_int)]
+                ("learned_rejected", ctypes.c_int), ("guess", ctypes.c_int)]
 
 
 class BodyState(ctypes.Structure):
@@ -451,6 +452,10 @@ def _unet_sigs():
     L.wsi_unet_train_sample.restype = ip
     L.wsi_pressure_solve.argtypes = [vp, vp, vp, dp, ip, ctypes.POINTER(SolveStats)]
     L.wsi_pressure_solve.restype = ip
+    L.wsi_attach_unet_guess.argtypes = [vp, vp, ip]
+    L.wsi_attach_unet_guess.restype = ip
+    L.wsi_unet_train_guess.argtypes = [vp, vp, vp, dp, ctypes.POINTER(dp)]
+    L.wsi_unet_train_guess.restype = ip
     _UNET_SIGS = True
 
 
@@ -536,6 +541,22 @@ def attach_unet(ctx, net, level, enable=LEARN_REPLACE):
     _unet_sigs()
     mode = int(enable) if not isinstance(enable, bool) else (LEARN_REPLACE if enable else LEARN_OFF)
     ctx._check(ctx.L.wsi_attach_unet(ctx._h, net._h if net is not None else None, level, mode))
+
+
+def attach_unet_guess(ctx, net, level):
+    """Initial-guess network for pressure_solve (None detaches)."""
+    _unet_sigs()
+    ctx._check(ctx.L.wsi_attach_unet_guess(ctx._h, net._h if net is not None else None, level))
+
+
+def unet_train_guess(ctx, y, x, lr):
+    """One Adam step of the guess network on a solver-generated pair (fine
+    right-hand side y, its solution x)."""
+    _unet_sigs()
+    y, x = _flat(y), _flat(x)
+    loss = ctypes.c_double()
+    ctx._check(ctx.L.wsi_unet_train_guess(ctx._h, _ptr(y), _ptr(x), lr, ctypes.byref(loss)))
+    return loss.value
 
 
 def unet_train_sample(ctx, e, lr):
