@@ -375,13 +375,14 @@ int wsi_unet_train_sample(wsi_ctx* ctx, const double* e, double lr, double* loss
  * wsi_attach_unet_guess: a network sized for multigrid level `level` of this
  * (WSI_PREC_MIXED) context, or NULL to detach.  Its input is the level's
  * restriction (cell averages) of the right-hand side with log rho and phi
- * (as for wsi_attach_unet); its output o gives the level's solution s o / d,
+ * (as for wsi_attach_unet); its output o gives the level's solution
+ * G s o / d (G = (n_max/pi)^2, n_max the level's longest extent in cells),
  * prolongated to the fine grid as the initial iterate, which is kept only if
  * its residual is below the zero guess's (wsi_solve_stats.guess).
  * wsi_unet_train_guess: one Adam step (lr = 0: evaluate) on a pair the
  * solver generated: a fine right-hand side y and its solution x (cell
  * fields, float64, host or device, x fastest); both are averaged down to the
- * level and the loss 1/2 mean((o - d x_l / s)^2) is written to *loss. */
+ * level and the loss 1/2 mean((o - d x_l / (G s))^2) is written to *loss. */
 int wsi_attach_unet_guess(wsi_ctx* ctx, wsi_unet* net, int level);
 int wsi_unet_train_guess(wsi_ctx* ctx, const double* y, const double* x, double lr, double* loss);
 

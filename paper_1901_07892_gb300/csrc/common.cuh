@@ -138,13 +138,6 @@ __device__ __forceinline__ T qget(const GridDev& g, const T* __restrict__ q, int
 
 __device__ __forceinline__ int clampi(int a, int lo, int hi) { return a < lo ? lo : (a > hi ? hi : a); }
 
-// Ask the memory system to bring the line holding p into L2 (no register,
-// no wait).  The plane-marching kernels issue it for the planes a few steps
-// ahead, so that the loads of those planes hit L2 rather than DRAM.
-__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
-#ifndef WSI_ZPF
-#define WSI_ZPF 2  // planes ahead
-#endif
 
 // float64 -> float32 by integer operations on the IEEE-754 bit patterns:
 // sign, exponent rebiased by 1023 - 127, top 23 significand bits, rounded

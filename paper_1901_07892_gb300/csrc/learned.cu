@@ -185,6 +185,23 @@ static void avg_chain(Precond<float>& P, const float* f, int top, float* const* 
   }
 }
 
+// The solution of L x = r exceeds the Jacobi estimate r / d by up to the
+// ratio of the diagonal to the lowest eigenvalue, about (n_max / pi)^2 on a
+// level with n_max cells along its longest axis; the guess network's output
+// is taken in those units (x = G s o / d), so that its targets are O(1).
+static float guess_gain(const GridDev& g) {
+  const double nm = std::max(g.n[0], std::max(g.n[1], g.n[2]));
+  return (float)(nm * nm / (M_PI * M_PI));
+}
+
+// x = G s o / d
+__global__ void k_apply_guess(const float* __restrict__ o, const float* __restrict__ d,
+                              const double* __restrict__ ss, size_t n, float gain, float* x) {
+  const float s = (float)sqrt(fmax(ss[0] / (double)n, 0.0)) * gain;
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x)
+    x[v] = o[v] * s / d[v];
+}
+
 void learned_guess(Precond<float>& P, const float* b0, cudaStream_t st) {
   LearnState& S = P.learn;
   const int lg = S.glevel;
@@ -197,14 +214,14 @@ void learned_guess(Precond<float>& P, const float* b0, cudaStream_t st) {
   { k_sumsq<<<nb(n), 256, 0, st>>>(L.b, n, S.gss); WSI_COUNT(); }
   { k_assemble<<<nb(n), 256, 0, st>>>(S.lrho[lg], S.phi[lg], L.b, S.gss, n, unet_input(S.gnet)); WSI_COUNT(); }
   unet_forward(S.gnet, st);
-  { k_apply_out<<<nb(n), 256, 0, st>>>(unet_output(S.gnet), S.gdiag, S.gss, n, 0, L.x); WSI_COUNT(); }
+  { k_apply_guess<<<nb(n), 256, 0, st>>>(unet_output(S.gnet), S.gdiag, S.gss, n, guess_gain(L.g), L.x); WSI_COUNT(); }
   precond_prolong_chain<float>(P, lg, st);
 }
 
-// target d x / s of the guess network (its output o gives x = s o / d)
+// target d x / (G s) of the guess network (its output o gives x = G s o / d)
 __global__ void k_guess_target(const float* __restrict__ x, const float* __restrict__ d,
-                               const double* __restrict__ ss, size_t n, float* tgt) {
-  const float is = (float)(1.0 / sqrt(fmax(ss[0] / (double)n, 1e-300)));
+                               const double* __restrict__ ss, size_t n, float gain, float* tgt) {
+  const float is = (float)(1.0 / sqrt(fmax(ss[0] / (double)n, 1e-300))) / gain;
   for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (size_t)gridDim.x * blockDim.x)
     tgt[v] = d[v] * x[v] * is;
 }
@@ -225,7 +242,7 @@ void learned_train_guess(Precond<float>& P, const float* y, const float* x, doub
   { k_sumsq<<<nb(n), 256, 0, st>>>(L.b, n, S.gss); WSI_COUNT(); }
   { k_assemble<<<nb(n), 256, 0, st>>>(S.lrho[lg], S.phi[lg], L.b, S.gss, n, unet_input(S.gnet)); WSI_COUNT(); }
   unet_forward(S.gnet, st);
-  { k_guess_target<<<nb(n), 256, 0, st>>>(L.res, S.gdiag, S.gss, n, unet_target(S.gnet)); WSI_COUNT(); }
+  { k_guess_target<<<nb(n), 256, 0, st>>>(L.res, S.gdiag, S.gss, n, guess_gain(L.g), unet_target(S.gnet)); WSI_COUNT(); }
   unet_backward(S.gnet, st);
   if (lr > 0.0) unet_adam(S.gnet, lr, st);
 }

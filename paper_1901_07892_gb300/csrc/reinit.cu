@@ -154,12 +154,6 @@ __global__ void __launch_bounds__(RX* RY) k_reinit(GridDev g, ReinitAxes<T> ax,
   for (int k = k0; k < k1; ++k) {
     const size_t id = (size_t)k * plane + col;
     const unsigned cd = cd_next;
-    if (WSI_ZPF > 0 && k + 1 + WSI_ZPF < n2) {
-      const size_t a = (size_t)(k + 1 + WSI_ZPF) * plane + col;
-      prefetch_l2(pin + a);
-      prefetch_l2(code + a);
-      if (pavg) prefetch_l2(pavg + a);
-    }
 #pragma unroll
     for (int r = 0; r < NS; ++r)
       if (soff[r] >= 0) sP[tid + r * RX * RY] = nxt[r];

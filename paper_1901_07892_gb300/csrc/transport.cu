@@ -170,15 +170,6 @@ __global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, CVel<T> vel, co
     const int mzh = k + oz + 1;
     const bool fzh = inside && ((C == 2) || !wall) && (C != 2 || mzh <= g.n[2] - 1);
     const T azh = fzh ? adv_at<C, 2, T>(g, vel, i, j, k, mzh) : T(0);
-    if (WSI_ZPF > 0 && k + WSI_ZPF < e2) {
-      const size_t a = (size_t)(k + WSI_ZPF) * plane + col;
-      prefetch_l2(rho + a);
-      if (WITHV) prefetch_l2(qc + a);
-      const int kq = min(k + WSI_ZPF, g.n[2] - 1), iq = min(i, g.n[0] - 1), jq = min(j, g.n[1] - 1);
-      prefetch_l2(vel.q[0] + fidx(g, 0, iq, jq, kq));
-      prefetch_l2(vel.q[1] + fidx(g, 1, iq, jq, kq));
-      prefetch_l2(vel.q[2] + fidx(g, 2, iq, jq, kq));
-    }
     // stage plane k
 #pragma unroll
     for (int r = 0; r < NS; ++r) {
@@ -464,15 +455,6 @@ __global__ void __launch_bounds__(BX* BY) k_ls_advect(GridDev g, CVel<T> vel,
   T Fz_lo = T(0);
   for (int k = k0; k < k1; ++k) {
     T ux = T(0), uxl = T(0), vy = T(0), vyl = T(0), wz = T(0), wzl = T(0);
-    if (WSI_ZPF > 0 && k + WSI_ZPF < n2) {
-      const size_t a = (size_t)(k + WSI_ZPF) * plane + col;
-      prefetch_l2(phi_h + a);
-      prefetch_l2(phi_n + a);
-      const int iq = min(i, n0 - 1), jq = min(j, n1 - 1);
-      prefetch_l2(vel.q[0] + fidx(g, 0, iq, jq, k + WSI_ZPF));
-      prefetch_l2(vel.q[1] + fidx(g, 1, iq, jq, k + WSI_ZPF));
-      prefetch_l2(vel.q[2] + fidx(g, 2, iq, jq, k + WSI_ZPF));
-    }
     if (inside) {
       ux = vel.q[0][fidx(g, 0, i + 1, j, k)];
       if (tx == 0) uxl = vel.q[0][fidx(g, 0, i, j, k)];
