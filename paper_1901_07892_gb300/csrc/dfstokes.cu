@@ -161,9 +161,6 @@ __global__ void __launch_bounds__(32 * FBY) k_stokes_df(HtConst K, DfCoef cf, Df
         pf_l2(cf.rho_face[2] + ic + j * sc1 + kq * sc2);
       }
     }
-      }
-    }
-#endif
     // ---- level k + 1: fields and z-edge shear stresses
     ht u_kp, v_kp, vj_kp;
     if (kp < nz) {
