@@ -318,7 +318,9 @@ int wsi_wave_relax(wsi_ctx* ctx, double t, double* vel, double* phi);
  * of nz x ny x nx cells (each divisible by 4): per level two 3x3x3
  * convolutions with ReLU, 2x2x2 average pooling down, nearest up-sampling with
  * skip concatenation up, a 1x1x1 head to one channel.  BF16 weights and
- * activations, float32 accumulation on the tensor cores, float32 master
+ * activations; each 3x3x3 convolution (forward, and the input-gradient
+ * pass) is an implicit GEMM on the fifth-generation tensor cores
+ * (tcgen05.mma, float32 accumulator in tensor memory); float32 master
  * weights and Adam.  Parameters are one float32 vector: per convolution
  * (a1 a2 b1 b2 c1 c2 ub1 ub2 ua1 ua2) weights [27 taps][C_out][C_in]
  * (tap = 9 dz + 3 dy + dx; a1's C_in is padded from 3 to 16) then biases
@@ -327,7 +329,9 @@ int wsi_wave_relax(wsi_ctx* ctx, double t, double* vel, double* phi);
  * wsi_unet_forward: x [V][3] float32 (host or device) -> out [V].
  * wsi_unet_backward (after a forward): gradients of 0.5 mean((out - t)^2),
  * readable with wsi_unet_get_grads; wsi_unet_adam applies one Adam step
- * (beta 0.9 / 0.999). */
+ * (beta 0.9 / 0.999).  Forward and backward return WSI_ERR_DEVICE when a
+ * convolution's bounded wait for the tensor core ran out (its outputs are
+ * then not valid; nothing traps). */
 typedef struct wsi_unet wsi_unet;
 int wsi_unet_create(int nz, int ny, int nx, int c0, int c1, int c2, unsigned long long seed, wsi_unet** out);
 void wsi_unet_destroy(wsi_unet* net);

@@ -1604,7 +1604,8 @@ int wsi_unet_forward(wsi_unet* n, const float* x, float* out) {
   unet_set_input3(n->u, n->x3, 0);
   unet_forward(n->u, 0);
   if (cudaMemcpy(out, unet_output(n->u), V * sizeof(float), cudaMemcpyDefault) != cudaSuccess) return WSI_ERR_CUDA;
-  return cudaDeviceSynchronize() == cudaSuccess ? WSI_OK : WSI_ERR_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return WSI_ERR_CUDA;
+  return unet_take_error(n->u) ? WSI_ERR_DEVICE : WSI_OK;
 }
 
 int wsi_unet_backward(wsi_unet* n, const float* target, double* loss) {
@@ -1614,7 +1615,8 @@ int wsi_unet_backward(wsi_unet* n, const float* target, double* loss) {
   unet_backward(n->u, 0);
   if (loss && cudaMemcpy(loss, unet_loss(n->u), sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
     return WSI_ERR_CUDA;
-  return cudaDeviceSynchronize() == cudaSuccess ? WSI_OK : WSI_ERR_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return WSI_ERR_CUDA;
+  return unet_take_error(n->u) ? WSI_ERR_DEVICE : WSI_OK;
 }
 
 int wsi_unet_adam(wsi_unet* n, double lr) {

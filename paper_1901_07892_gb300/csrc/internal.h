@@ -165,6 +165,9 @@ double* unet_loss(UNetImpl* u);          // device scalar
 float* unet_moment(UNetImpl* u, int which);  // Adam first (0) / second (1) moments
 int* unet_step_count(UNetImpl* u);           // Adam steps taken
 int unet_width(const UNetImpl* u, int level);  // c0, c1, c2
+// reads and clears the flag a tensor-core convolution sets when one of its
+// bounded waits ran out (the outputs of that launch are then not valid)
+bool unet_take_error(UNetImpl* u);
 
 // learned correction state inside the float32 multigrid (learned.cu)
 struct LearnState {

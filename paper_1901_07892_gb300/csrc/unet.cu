@@ -8,13 +8,12 @@
 //
 // Layout: activations [Z][Y][X][C] bf16, C a multiple of 16 (the 3 input
 // channels are padded to 16).  A 3x3x3 convolution is an implicit GEMM:
-// rows = voxels, K = 27 taps x C_in, N = C_out, computed with
-// mma.sync.m16n8k16 (bf16 in, f32 accumulate); each warp owns 16 voxels of
-// one x-row and all output channels.  Forward weights are stored
-// [tap][C_out][C_in] (C_in contiguous: one 32-bit load per B fragment
-// register); the input-gradient pass is the same kernel with the flipped,
-// transposed weights [26 - tap][C_in][C_out].  Weight gradients are float32
-// reductions over voxels on the CUDA cores.
+// rows = voxels, K = 27 taps x C_in, N = C_out, computed on the tcgen05
+// tensor cores with the accumulator in tensor memory (k_conv3_tc below).
+// Forward weights are stored [tap][C_out][C_in] (C_in contiguous: the B
+// operand's rows); the input-gradient pass is the same kernel with the
+// flipped, transposed weights [26 - tap][C_in][C_out].  Weight gradients are
+// float32 reductions over voxels on the CUDA cores.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -29,15 +28,6 @@ typedef __nv_bfloat16 bf16;
 
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ unsigned int ld32(const bf16* p) { return *reinterpret_cast<const unsigned int*>(p); }
-
-__device__ __forceinline__ void mma_bf16(float* d, unsigned int a0, unsigned int a1, unsigned int a2, unsigned int a3,
-                                         unsigned int b0, unsigned int b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
 
 // input of a convolution: channels [0, C0) from in0 (read at half resolution
 // when up0: nearest up-sampling), channels [C0, C0 + C1) from in1
@@ -65,73 +55,209 @@ __device__ __forceinline__ unsigned int in_pair(const ConvIn& a, int Z, int Y, i
   return ld32(a.in1 + v * a.C1 + (c - a.C0));
 }
 
-// ------------------------------------------------------------------ conv
-template <int NT>
-__global__ void __launch_bounds__(128) k_conv3(ConvIn a, const bf16* __restrict__ W, const float* __restrict__ bias,
-                                               bf16* out, int Cout, int Z, int Y, int X, int relu) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  const int x0 = blockIdx.x * 16;
-  const int y = blockIdx.y * 4 + warp;
-  const int z = blockIdx.z;
-  if (y >= Y) return;
+// ------------------------------------------------------------------ conv on tcgen05
+// The same implicit GEMM on the fifth-generation tensor cores: one CTA (4
+// warps) computes 128 consecutive voxels (M = 128) times all output channels
+// (N = Cout) into a float32 accumulator in tensor memory; K = 27 taps x C_in
+// runs in chunks of 16 channels, one tcgen05.mma (kind::f16, bf16 inputs) per
+// chunk.  Every thread gathers its voxel's 16 channels of the chunk (zero
+// outside the grid: the convolution's padding) and the first N threads the
+// weights' rows into this CTA's shared memory, in the K-major layout without
+// swizzling (core matrices of 8 rows x 16 bytes; neighbours along K 128
+// bytes apart, along M/N 256 bytes apart).  Two stages alternate: while the
+// tensor core works on one, the threads fill the other; the MMA's completion
+// is signalled to an mbarrier by tcgen05.commit.  The epilogue reads the
+// accumulator rows back with tcgen05.ld (warp w owns lanes 32w..32w+31), adds
+// the bias, applies the ReLU and stores bf16.  Every mbarrier wait is
+// bounded: on expiry the kernel sets *err, skips the epilogue and still
+// frees its tensor memory.
+namespace tc {
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start address, leading (K) and stride
+// (M/N) byte offsets between core matrices, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: float32 accumulator, bf16 A and B,
+// both K-major, shape M x N
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    __nanosleep(64);
+  }
+  return false;
+}
+
+// byte offset of element (row r, channel k in 0..15) in a K-major tile
+__device__ __forceinline__ int tile_off(int r, int k) { return (r >> 3) * 256 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+
+}  // namespace tc
+
+// 16 channels (cb .. cb+15) of the concatenated input at voxel (x, y, z) of
+// the output grid, as two 16-byte words; zero outside the grid
+__device__ __forceinline__ void in16(const ConvIn& a, int Z, int Y, int X, int z, int y, int x, int cb, uint4& lo,
+                                     uint4& hi) {
+  lo = make_uint4(0u, 0u, 0u, 0u);
+  hi = lo;
+  if (z < 0 || z >= Z || y < 0 || y >= Y || x < 0 || x >= X) return;
+  const bf16* p;
+  if (cb < a.C0) {
+    if (a.up0) {
+      const int Yh = Y >> 1, Xh = X >> 1;
+      p = a.in0 + (((size_t)(z >> 1) * Yh + (y >> 1)) * Xh + (x >> 1)) * a.C0 + cb;
+    } else {
+      p = a.in0 + (((size_t)z * Y + y) * X + x) * a.C0 + cb;
+    }
+  } else {
+    p = a.in1 + (((size_t)z * Y + y) * X + x) * a.C1 + (cb - a.C0);
+  }
+  lo = *reinterpret_cast<const uint4*>(p);
+  hi = *reinterpret_cast<const uint4*>(p + 8);
+}
+
+template <int N>
+__global__ void __launch_bounds__(128) k_conv3_tc(ConvIn a, const bf16* __restrict__ W, const float* __restrict__ bias,
+                                                  bf16* out, int Z, int Y, int X, int relu, int* err) {
+  constexpr int A_BYTES = 128 * 32, B_BYTES = N * 32, STAGE = A_BYTES + B_BYTES;
+  constexpr int TM_COLS = N <= 32 ? 32 : (N <= 64 ? 64 : 128);
+  __shared__ __align__(1024) unsigned char sm[2 * STAGE];
+  __shared__ __align__(8) unsigned long long mbar[2];
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int Cin = a.C0 + a.C1;
-  float acc[NT][4];
-#pragma unroll
-  for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-  for (int tap = 0; tap < 27; ++tap) {
+  const size_t V = (size_t)Z * Y * X;
+  const size_t v = (size_t)blockIdx.x * 128 + tid;  // this thread's voxel (row)
+  const bool vok = v < V;
+  const int x = vok ? (int)(v % X) : 0, y = vok ? (int)((v / X) % Y) : 0, z = vok ? (int)(v / ((size_t)X * Y)) : 0;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::saddr(&mbar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::saddr(&tmem_slot)),
+                 "r"(TM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  const int chunks_per_tap = Cin / 16, nchunk = 27 * chunks_per_tap;
+  constexpr uint32_t IDESC = tc::instr_desc(128, N);
+  bool ok = true;
+  for (int c = 0; c < nchunk && ok; ++c) {
+    const int s = c & 1;
+    if (c >= 2) ok = tc::mbar_wait(tc::saddr(&mbar[s]), ((c - 2) >> 1) & 1);  // stage s free again
+    if (!ok) break;
+    const int tap = c / chunks_per_tap, cb = (c - tap * chunks_per_tap) * 16;
     const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-    const int zz = z + dz, yy = y + dy;
-    if (zz < 0 || zz >= Z || yy < 0 || yy >= Y) continue;  // whole row is padding
-    const int xa = x0 + g + dx, xb = x0 + g + 8 + dx;
-    const bf16* wt = W + (size_t)tap * Cout * Cin;
-    for (int cb = 0; cb < Cin; cb += 16) {
-      unsigned int a0 = in_pair(a, Z, Y, X, zz, yy, xa, cb + 2 * t);
-      unsigned int a1 = in_pair(a, Z, Y, X, zz, yy, xb, cb + 2 * t);
-      unsigned int a2 = in_pair(a, Z, Y, X, zz, yy, xa, cb + 2 * t + 8);
-      unsigned int a3 = in_pair(a, Z, Y, X, zz, yy, xb, cb + 2 * t + 8);
+    unsigned char* As = sm + s * STAGE;
+    unsigned char* Bs = As + A_BYTES;
+    uint4 lo, hi;
+    if (vok) {
+      in16(a, Z, Y, X, z + dz, y + dy, x + dx, cb, lo, hi);
+    } else {
+      lo = make_uint4(0u, 0u, 0u, 0u);
+      hi = lo;
+    }
+    *reinterpret_cast<uint4*>(As + tc::tile_off(tid, 0)) = lo;
+    *reinterpret_cast<uint4*>(As + tc::tile_off(tid, 8)) = hi;
+    if (tid < N) {
+      const bf16* wr = W + ((size_t)tap * N + tid) * Cin + cb;
+      *reinterpret_cast<uint4*>(Bs + tc::tile_off(tid, 0)) = *reinterpret_cast<const uint4*>(wr);
+      *reinterpret_cast<uint4*>(Bs + tc::tile_off(tid, 8)) = *reinterpret_cast<const uint4*>(wr + 8);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint64_t ad = tc::smem_desc(tc::saddr(As), 128, 256), bd = tc::smem_desc(tc::saddr(Bs), 128, 256);
+      const uint32_t acc = c > 0 ? 1u : 0u;
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+          "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          tc::saddr(&mbar[s])));
+    }
+  }
+  // every issued chunk has completed once the last two commits have arrived
+  if (ok) {
+    for (int c = (nchunk >= 2 ? nchunk - 2 : 0); c < nchunk && ok; ++c)
+      ok = tc::mbar_wait(tc::saddr(&mbar[c & 1]), (c >> 1) & 1);
+  }
+  if (!ok && tid == 0) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    const size_t vr = (size_t)blockIdx.x * 128 + 32 * warp + (tid & 31);
 #pragma unroll
-      for (int n = 0; n < NT; ++n) {
-        const bf16* wr = wt + (size_t)(n * 8 + g) * Cin + cb + 2 * t;
-        mma_bf16(acc[n], a0, a1, a2, a3, ld32(wr), ld32(wr + 8));
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (vr < V) {
+        __nv_bfloat162 o[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          float v0 = __uint_as_float(r[2 * q]) + (bias ? bias[c0 + 2 * q] : 0.f);
+          float v1 = __uint_as_float(r[2 * q + 1]) + (bias ? bias[c0 + 2 * q + 1] : 0.f);
+          if (relu) {
+            v0 = fmaxf(v0, 0.f);
+            v1 = fmaxf(v1, 0.f);
+          }
+          o[q] = __floats2bfloat162_rn(v0, v1);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(out + vr * N + c0);
+        dst[0] = *reinterpret_cast<uint4*>(&o[0]);
+        dst[1] = *reinterpret_cast<uint4*>(&o[4]);
       }
     }
   }
-  const int xr0 = x0 + g, xr1 = x0 + g + 8;
-#pragma unroll
-  for (int n = 0; n < NT; ++n) {
-    const int c = n * 8 + 2 * t;
-    float b0 = bias ? bias[c] : 0.f, b1 = bias ? bias[c + 1] : 0.f;
-    float v0 = acc[n][0] + b0, v1 = acc[n][1] + b1, v2 = acc[n][2] + b0, v3 = acc[n][3] + b1;
-    if (relu) {
-      v0 = fmaxf(v0, 0.f);
-      v1 = fmaxf(v1, 0.f);
-      v2 = fmaxf(v2, 0.f);
-      v3 = fmaxf(v3, 0.f);
-    }
-    if (xr0 < X) {
-      __nv_bfloat162 p = __floats2bfloat162_rn(v0, v1);
-      *reinterpret_cast<__nv_bfloat162*>(out + (((size_t)z * Y + y) * X + xr0) * Cout + c) = p;
-    }
-    if (xr1 < X) {
-      __nv_bfloat162 p = __floats2bfloat162_rn(v2, v3);
-      *reinterpret_cast<__nv_bfloat162*>(out + (((size_t)z * Y + y) * X + xr1) * Cout + c) = p;
-    }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TM_COLS));
+}
+
+static bool conv3_tc(const ConvIn& a, const bf16* W, const float* bias, bf16* out, int Cout, int Z, int Y, int X,
+                     bool relu, int* err, cudaStream_t st) {
+  const size_t V = (size_t)Z * Y * X;
+  dim3 grid((unsigned)((V + 127) / 128));
+  switch (Cout) {
+    case 16: k_conv3_tc<16><<<grid, 128, 0, st>>>(a, W, bias, out, Z, Y, X, relu, err); break;
+    case 32: k_conv3_tc<32><<<grid, 128, 0, st>>>(a, W, bias, out, Z, Y, X, relu, err); break;
+    case 48: k_conv3_tc<48><<<grid, 128, 0, st>>>(a, W, bias, out, Z, Y, X, relu, err); break;
+    case 64: k_conv3_tc<64><<<grid, 128, 0, st>>>(a, W, bias, out, Z, Y, X, relu, err); break;
+    case 80: k_conv3_tc<80><<<grid, 128, 0, st>>>(a, W, bias, out, Z, Y, X, relu, err); break;
+    case 96: k_conv3_tc<96><<<grid, 128, 0, st>>>(a, W, bias, out, Z, Y, X, relu, err); break;
+    default: return false;
   }
+  WSI_COUNT();
+  return true;
 }
 
 static void conv3(const ConvIn& a, const bf16* W, const float* bias, bf16* out, int Cout, int Z, int Y, int X,
-                  bool relu, cudaStream_t st) {
-  dim3 grid(cdiv(X, 16), cdiv(Y, 4), Z);
-  switch (Cout / 8) {
-    case 2: { k_conv3<2><<<grid, 128, 0, st>>>(a, W, bias, out, Cout, Z, Y, X, relu); WSI_COUNT(); } break;
-    case 4: { k_conv3<4><<<grid, 128, 0, st>>>(a, W, bias, out, Cout, Z, Y, X, relu); WSI_COUNT(); } break;
-    case 6: { k_conv3<6><<<grid, 128, 0, st>>>(a, W, bias, out, Cout, Z, Y, X, relu); WSI_COUNT(); } break;
-    case 8: { k_conv3<8><<<grid, 128, 0, st>>>(a, W, bias, out, Cout, Z, Y, X, relu); WSI_COUNT(); } break;
-    case 10: { k_conv3<10><<<grid, 128, 0, st>>>(a, W, bias, out, Cout, Z, Y, X, relu); WSI_COUNT(); } break;
-    case 12: { k_conv3<12><<<grid, 128, 0, st>>>(a, W, bias, out, Cout, Z, Y, X, relu); WSI_COUNT(); } break;
-    default: break;
-  }
+                  bool relu, int* err, cudaStream_t st) {
+  // widths are multiples of 16 up to 96 (checked when the network is made)
+  if (!conv3_tc(a, W, bias, out, Cout, Z, Y, X, relu, err, st)) cudaMemsetAsync(err, 0xFF, sizeof(int), st);
 }
 
 // ------------------------------------------------------------------ elementwise
@@ -331,6 +457,7 @@ struct UNetImpl {
   bf16 *g0 = nullptr, *g1 = nullptr, *g2 = nullptr, *gA = nullptr, *gB = nullptr;
   float *out = nullptr, *tgt = nullptr;
   double* loss = nullptr;
+  int* tcerr = nullptr;  // set by a tensor-core convolution whose wait ran out
   int step = 0;
   std::vector<void*> allocs;
 };
@@ -418,7 +545,8 @@ UNetImpl* unet_create(int Z, int Y, int X, int c0, int c1, int c2) {
   ok &= cudaMalloc(&lp, sizeof(double)) == cudaSuccess;
   u->loss = (double*)lp;
   u->allocs.push_back(lp);
-  ok &= u->w && u->g && u->m && u->v && u->x && u->ua2 && u->g2 && u->gB && u->out && u->tgt;
+  u->tcerr = (int*)falloc(*u, 1);
+  ok &= u->w && u->g && u->m && u->v && u->x && u->ua2 && u->g2 && u->gB && u->out && u->tgt && u->tcerr;
   if (!ok) {
     unet_destroy(u);
     return nullptr;
@@ -445,7 +573,7 @@ void unet_forward(UNetImpl* u, cudaStream_t st) {
   auto& L = u->L;
   auto cv = [&](int l, const bf16* in0, const bf16* in1, bf16* out, int z, int y, int x) {
     ConvIn a{in0, L[l].C0, L[l].up0, in1, L[l].C1};
-    conv3(a, L[l].wf, u->w + L[l].boff, out, L[l].Cout, z, y, x, true, st);
+    conv3(a, L[l].wf, u->w + L[l].boff, out, L[l].Cout, z, y, x, true, u->tcerr, st);
   };
   size_t V = (size_t)Z * Y * X;
   cv(0, u->x, nullptr, u->a1, Z, Y, X);
@@ -478,7 +606,7 @@ static void layer_bwd(UNetImpl* u, int l, const bf16* in0, const bf16* in1, cons
   { k_conv_dw<<<grid, 256, 0, st>>>(a, M, L.Cout, z, yy, x, u->g + L.woff, u->g + L.boff, chunk); WSI_COUNT(); }
   if (dX) {
     ConvIn b{M, L.Cout, 0, nullptr, 0};
-    conv3(b, L.wb, nullptr, dX, L.C0 + L.C1, z, yy, x, false, st);
+    conv3(b, L.wb, nullptr, dX, L.C0 + L.C1, z, yy, x, false, u->tcerr, st);
   }
 }
 
@@ -538,6 +666,13 @@ float* unet_target(UNetImpl* u) { return u->tgt; }
 double* unet_loss(UNetImpl* u) { return u->loss; }
 float* unet_moment(UNetImpl* u, int which) { return which == 0 ? u->m : u->v; }
 int* unet_step_count(UNetImpl* u) { return &u->step; }
+bool unet_take_error(UNetImpl* u) {
+  int h = 0;
+  if (cudaMemcpy(&h, u->tcerr, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return true;
+  if (h) cudaMemset(u->tcerr, 0, sizeof(int));
+  return h != 0;
+}
+
 int unet_width(const UNetImpl* u, int level) { return level == 0 ? u->c0 : (level == 1 ? u->c1 : u->c2); }
 
 void unet_adam(UNetImpl* u, double lr, cudaStream_t st) {
