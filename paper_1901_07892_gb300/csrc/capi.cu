@@ -172,8 +172,9 @@ bool ensure_spread_work(wsi_ctx* c) {
   c->sw.acc = (unsigned long long*)dalloc(c, c->nvel);
   c->sw.cnt = (int*)dalloc(c, c->ncell / 2 + 1);
   c->sw.qexp = (int*)dalloc(c, 1);
+  c->sw.part = dalloc(c, 6 * 152);
   c->mbox = dalloc(c, 6);
-  return c->sw.acc && c->sw.cnt && c->sw.qexp && c->mbox;
+  return c->sw.acc && c->sw.cnt && c->sw.qexp && c->sw.part && c->mbox;
 }
 
 void vel_parts(wsi_ctx* c, double* base, double* out[3]) {
@@ -290,11 +291,25 @@ void pc_apply(wsi_ctx* c, double dt, const double* v, double* z) {
 // the face density is stored times 1/dt
 void df_coef_refresh(wsi_ctx* c, const Coef<double>& cf, double inv_dt) {
   if (!c->mixed()) return;
+  const double* x[7];
+  float2* o[7];
+  size_t n[7];
+  double sc[7];
   for (int d = 0; d < 3; ++d) {
-    launch_df_split_scaled(cf.rho_face[d], inv_dt, c->df_rho[d], fsize(c->g, d), c->st);
-    launch_df_split(cf.mu_e[d], c->df_mu_e[d], esize(c->g, d), c->st);
+    x[d] = cf.rho_face[d];
+    o[d] = c->df_rho[d];
+    n[d] = fsize(c->g, d);
+    sc[d] = inv_dt;
+    x[3 + d] = cf.mu_e[d];
+    o[3 + d] = c->df_mu_e[d];
+    n[3 + d] = esize(c->g, d);
+    sc[3 + d] = 1.0;
   }
-  launch_df_split(cf.mu_cc, c->df_mu_cc, c->ncell, c->st);
+  x[6] = cf.mu_cc;
+  o[6] = c->df_mu_cc;
+  n[6] = c->ncell;
+  sc[6] = 1.0;
+  launch_df_split_set(x, o, n, sc, 7, c->st);  // one launch for the seven arrays
 }
 
 // K x: float64 on the plain path; on the mixed path in double-float
@@ -488,7 +503,7 @@ int dlm_project(wsi_ctx* c, double* velv, const double* Xuse) {
   launch_marker_mean(Xuse, B.n, B.xc, B.scratch, c->st);
   launch_ib_interp(c->g, cq, Xuse, B.n, B.U, c->st);
   launch_rigid_sums(Xuse, B.U, B.n, B.xc, B.sums, B.scratch, c->st);
-  launch_marker_box(Xuse, B.n, c->mbox, c->st);
+  launch_marker_box(Xuse, B.n, c->mbox, c->sw.part, c->st);
   double hs[15], xc[3], mm[6];
   cudaMemcpyAsync(hs, B.sums, sizeof(hs), cudaMemcpyDeviceToHost, c->st);
   cudaMemcpyAsync(xc, B.xc, sizeof(xc), cudaMemcpyDeviceToHost, c->st);
@@ -1406,7 +1421,7 @@ int wsi_spread(wsi_ctx* c, const double* F, const double* X, int n, double dV, d
     double* vq[3];
     vel_parts(c, c->vel_half, vq);
     double mm[6];
-    launch_marker_box(dX, n, c->mbox, c->st);
+    launch_marker_box(dX, n, c->mbox, c->sw.part, c->st);
     cudaMemcpyAsync(mm, c->mbox, sizeof(mm), cudaMemcpyDeviceToHost, c->st);
     cudaStreamSynchronize(c->st);
     launch_ib_spread(c->g, dF, dX, n, dV, vq, c->sw, spread_box(c->g, mm), c->st);

@@ -275,6 +275,47 @@ void launch_df_split(const double* x, float2* out, size_t n, cudaStream_t st) {
   { k_df_split<<<blocks, 256, 0, st>>>(x, out, n); WSI_COUNT(); }
 }
 
+// up to eight arrays split in one launch: (scale_k x_k) -> (hi, lo) pairs;
+// blockIdx.y selects the array
+struct SplitSet {
+  const double* x[8];
+  float2* out[8];
+  size_t n[8];
+  double scale[8];
+  int count;
+};
+
+__global__ void k_df_split_set(SplitSet s) {
+  const int a = blockIdx.y;
+  if (a >= s.count) return;
+  const double* __restrict__ x = s.x[a];
+  float2* out = s.out[a];
+  const size_t n = s.n[a];
+  const double sc = s.scale[a];
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+    const dfl d = df_split(sc == 1.0 ? x[t] : sc * x[t]);
+    out[t] = make_float2(d.h, d.l);
+  }
+}
+
+void launch_df_split_set(const double* const* x, float2* const* out, const size_t* n, const double* scale, int count,
+                         cudaStream_t st) {
+  SplitSet s;
+  size_t nmax = 0;
+  s.count = count < 8 ? count : 8;
+  for (int a = 0; a < s.count; ++a) {
+    s.x[a] = x[a];
+    s.out[a] = out[a];
+    s.n[a] = n[a];
+    s.scale[a] = scale[a];
+    nmax = std::max(nmax, n[a]);
+  }
+  if (!nmax) return;
+  const int blocks = (int)std::min<size_t>((nmax + 255) / 256, 152 * 4);
+  { k_df_split_set<<<dim3(blocks, s.count), 256, 0, st>>>(s); WSI_COUNT(); }
+}
+
 // (s x) (float64 product, one rounding) -> (hi, lo) pairs
 __global__ void k_df_split_scaled(const double* __restrict__ x, double s, float2* out, size_t n) {
   const size_t stride = (size_t)gridDim.x * blockDim.x;

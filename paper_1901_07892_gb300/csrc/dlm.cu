@@ -200,21 +200,25 @@ __global__ void k_marker_count(GridDev g, const double* __restrict__ X, int n, i
   atomicAdd(&cnt[fidx(g, 3, c[0], c[1], c[2])], 1);
 }
 
-// one block: E from the largest cell count in the box and max |F| scale;
-// the box's counts are cleared for the next call
-__global__ void k_spread_exponent(GridDev g, SpreadBox b, int* cnt, const double* __restrict__ F, int n3,
-                                  double scale, int* qexp) {
+// Per-block maxima of the box's cell counts and of |F| (partials: two per
+// block), then one small block turns them into E; maxima do not depend on
+// the order in which they are taken.
+static constexpr int XB = 152;  // blocks of the partial maxima
+
+__global__ void k_spread_max_part(GridDev g, SpreadBox b, const int* __restrict__ cnt, const double* __restrict__ F,
+                                  int n3, double* part) {
   __shared__ int shc[32];
   __shared__ double shf[32];
   const int ex = b.hi[0] - b.lo[0] + 1, ey = b.hi[1] - b.lo[1] + 1, ez = b.hi[2] - b.lo[2] + 1;
   const long long nb = (long long)ex * ey * ez;
+  const long long stride = (long long)gridDim.x * blockDim.x;
   int cm = 0;
-  for (long long t = threadIdx.x; t < nb; t += blockDim.x) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nb; t += stride) {
     const int i = b.lo[0] + (int)(t % ex), j = b.lo[1] + (int)((t / ex) % ey), k = b.lo[2] + (int)(t / ((long long)ex * ey));
     cm = max(cm, cnt[fidx(g, 3, i, j, k)]);
   }
   double fm = 0.0;
-  for (int t = threadIdx.x; t < n3; t += blockDim.x) fm = fmax(fm, fabs(F[t]));
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n3; t += stride) fm = fmax(fm, fabs(F[t]));
   for (int o = 16; o > 0; o >>= 1) {
     cm = max(cm, __shfl_down_sync(0xffffffffu, cm, o));
     fm = fmax(fm, __shfl_down_sync(0xffffffffu, fm, o));
@@ -231,13 +235,30 @@ __global__ void k_spread_exponent(GridDev g, SpreadBox b, int* cnt, const double
       c = max(c, shc[w]);
       f = fmax(f, shf[w]);
     }
-    const double B = 128.0 * (double)c * f * scale;
-    int e = 0;
-    if (B > 0.0 && B < 1e300) frexp(B, &e);  // B < 2^e
-    qexp[0] = (B > 0.0 && B < 1e300) ? 61 - e : 0;
+    part[2 * blockIdx.x] = (double)c;
+    part[2 * blockIdx.x + 1] = f;
   }
-  __syncthreads();
-  for (long long t = threadIdx.x; t < nb; t += blockDim.x) {
+}
+
+__global__ void k_spread_exponent(const double* __restrict__ part, int nparts, double scale, int* qexp) {
+  if (threadIdx.x != 0) return;
+  double c = 0.0, f = 0.0;
+  for (int q = 0; q < nparts; ++q) {
+    c = fmax(c, part[2 * q]);
+    f = fmax(f, part[2 * q + 1]);
+  }
+  const double B = 128.0 * c * f * scale;
+  int e = 0;
+  const bool pos = B > 0.0 && B < 1e300;
+  if (pos) frexp(B, &e);  // B < 2^e
+  qexp[0] = pos ? 61 - e : 0;
+}
+
+// counts of the box's cells back to zero for the next call
+__global__ void k_clear_box(GridDev g, SpreadBox b, int* cnt) {
+  const int ex = b.hi[0] - b.lo[0] + 1, ey = b.hi[1] - b.lo[1] + 1, ez = b.hi[2] - b.lo[2] + 1;
+  const long long nb = (long long)ex * ey * ez;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nb; t += (long long)gridDim.x * blockDim.x) {
     const int i = b.lo[0] + (int)(t % ex), j = b.lo[1] + (int)((t / ex) % ey), k = b.lo[2] + (int)(t / ((long long)ex * ey));
     cnt[fidx(g, 3, i, j, k)] = 0;
   }
@@ -283,21 +304,24 @@ void launch_ib_spread(const GridDev& g, const double* F, const double* X, int n,
   if (n <= 0) return;
   const double scale = dV / (g.h[0] * g.h[1] * g.h[2]);
   unsigned long long* acc[3] = {w.acc, w.acc + fsize(g, 0), w.acc + fsize(g, 0) + fsize(g, 1)};
-  { k_marker_count<<<cdiv(n, 256), 256, 0, st>>>(g, X, n, w.cnt); WSI_COUNT(); }
-  { k_spread_exponent<<<1, 1024, 0, st>>>(g, b, w.cnt, F, 3 * n, scale, w.qexp); WSI_COUNT(); }
-  { k_spread<<<cdiv(n, 128), 128, 0, st>>>(g, F, X, n, scale, acc[0], acc[1], acc[2], w.qexp); WSI_COUNT(); }
   const long long nb = (long long)(b.hi[0] - b.lo[0] + 2) * (b.hi[1] - b.lo[1] + 2) * (b.hi[2] - b.lo[2] + 2);
   const int blocks = (int)std::min<long long>((nb + 255) / 256, 152 * 8);
+  { k_marker_count<<<cdiv(n, 256), 256, 0, st>>>(g, X, n, w.cnt); WSI_COUNT(); }
+  { k_spread_max_part<<<XB, 256, 0, st>>>(g, b, w.cnt, F, 3 * n, w.part); WSI_COUNT(); }
+  { k_spread_exponent<<<1, 32, 0, st>>>(w.part, XB, scale, w.qexp); WSI_COUNT(); }
+  { k_clear_box<<<blocks, 256, 0, st>>>(g, b, w.cnt); WSI_COUNT(); }
+  { k_spread<<<cdiv(n, 128), 128, 0, st>>>(g, F, X, n, scale, acc[0], acc[1], acc[2], w.qexp); WSI_COUNT(); }
   { k_unfix<0><<<blocks, 256, 0, st>>>(g, b, acc[0], w.qexp, vel[0]); WSI_COUNT(); }
   { k_unfix<1><<<blocks, 256, 0, st>>>(g, b, acc[1], w.qexp, vel[1]); WSI_COUNT(); }
   { k_unfix<2><<<blocks, 256, 0, st>>>(g, b, acc[2], w.qexp, vel[2]); WSI_COUNT(); }
 }
 
-// min (0..2) and max (3..5) of the marker positions, one block
-__global__ void k_marker_box(const double* __restrict__ X, int n, double* out) {
+// min (0..2) and max (3..5) of the marker positions: per-block extrema,
+// then one small block over the partials
+__global__ void k_marker_box_part(const double* __restrict__ X, int n, double* part) {
   __shared__ double sh[6][32];
   double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
-  for (int m = threadIdx.x; m < n; m += blockDim.x)
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x)
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       mn[d] = fmin(mn[d], X[3 * m + d]);
@@ -319,13 +343,22 @@ __global__ void k_marker_box(const double* __restrict__ X, int n, double* out) {
     double v = sh[threadIdx.x][0];
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
       v = threadIdx.x < 3 ? fmin(v, sh[threadIdx.x][w]) : fmax(v, sh[threadIdx.x][w]);
-    out[threadIdx.x] = v;
+    part[6 * blockIdx.x + threadIdx.x] = v;
   }
 }
 
-void launch_marker_box(const double* X, int n, double* out6, cudaStream_t st) {
+__global__ void k_marker_box_final(const double* __restrict__ part, int nparts, double* out) {
+  const int q = threadIdx.x;
+  if (q >= 6) return;
+  double v = part[q];
+  for (int b = 1; b < nparts; ++b) v = q < 3 ? fmin(v, part[6 * b + q]) : fmax(v, part[6 * b + q]);
+  out[q] = v;
+}
+
+void launch_marker_box(const double* X, int n, double* out6, double* scratch, cudaStream_t st) {
   if (n <= 0) return;
-  { k_marker_box<<<1, 1024, 0, st>>>(X, n, out6); WSI_COUNT(); }
+  { k_marker_box_part<<<XB, 256, 0, st>>>(X, n, scratch); WSI_COUNT(); }
+  { k_marker_box_final<<<1, 32, 0, st>>>(scratch, XB, out6); WSI_COUNT(); }
 }
 
 // ---------------------------------------------------------------- rigid sums

@@ -72,6 +72,9 @@ struct DfVec {
 // out[i] = (hi, lo) split of x[i] (of s x[i])
 void launch_df_split(const double* x, float2* out, size_t n, cudaStream_t st);
 void launch_df_split_scaled(const double* x, double s, float2* out, size_t n, cudaStream_t st);
+// up to eight arrays in one launch (scale[k] 1: plain split)
+void launch_df_split_set(const double* const* x, float2* const* out, const size_t* n, const double* scale, int count,
+                         cudaStream_t st);
 // y = K x in double-float arithmetic from the split coefficients (face
 // density already times 1/dt) and x
 void launch_stokes_df(const GridDev& g, const DfCoef& cf, double theta, const float2* x, double* y,
@@ -308,13 +311,14 @@ struct SpreadWork {
   unsigned long long* acc = nullptr;  // one per face of the packed velocity
   int* cnt = nullptr;                 // one per cell
   int* qexp = nullptr;                // quantum exponent of the current call
+  double* part = nullptr;             // reduction partials (6 x 152 doubles)
 };
 struct SpreadBox {
   int lo[3], hi[3];  // cells, inclusive
 };
 // box from the marker extent mm = (min x, y, z, max x, y, z)
 SpreadBox spread_box(const GridDev& g, const double mm[6]);
-void launch_marker_box(const double* X, int n, double* out6, cudaStream_t st);
+void launch_marker_box(const double* X, int n, double* out6, double* scratch, cudaStream_t st);
 void launch_ib_spread(const GridDev& g, const double* F, const double* X, int n, double dV, double* const vel[3],
                       const SpreadWork& w, const SpreadBox& b, cudaStream_t st);
 // rigid sums: out[0..2] sum U, [3..5] sum R x U, [6..11] sum of R.R I - R (x) R (xx,yy,zz,xy,xz,yz),

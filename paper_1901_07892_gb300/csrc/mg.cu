@@ -269,16 +269,33 @@ __global__ void k_vprolong(GridDev gf, GridDev gc, int r0, int r1, int r2, const
   uf[fidx(gf, C, i, j, k)] += v;
 }
 
+// up to sixteen arrays cast in one launch (blockIdx.y selects the array)
 template <typename Ts, typename Td>
-__global__ void k_cast_arr(const Ts* __restrict__ a, Td* b, size_t n) {
-  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (; t < n; t += stride) b[t] = cvt<Td, Ts>(a[t]);
+struct CastSet {
+  const Ts* a[16];
+  Td* b[16];
+  size_t n[16];
+  int count;
+};
+
+template <typename Ts, typename Td>
+__global__ void k_cast_set(CastSet<Ts, Td> s) {
+  const int q = blockIdx.y;
+  if (q >= s.count) return;
+  const Ts* __restrict__ a = s.a[q];
+  Td* b = s.b[q];
+  const size_t n = s.n[q];
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    b[t] = cvt<Td, Ts>(a[t]);
 }
+
 template <typename Ts, typename Td>
-static void cast_arr(const Ts* a, Td* b, size_t n, cudaStream_t st) {
-  int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
-  { k_cast_arr<Ts, Td><<<std::max(blocks, 1), 256, 0, st>>>(a, b, n); WSI_COUNT(); }
+static void cast_set(const CastSet<Ts, Td>& s, cudaStream_t st) {
+  size_t nmax = 0;
+  for (int q = 0; q < s.count; ++q) nmax = std::max(nmax, s.n[q]);
+  if (!nmax) return;
+  const int blocks = (int)std::min<size_t>((nmax + 255) / 256, 152 * 4);
+  { k_cast_set<Ts, Td><<<dim3(blocks, s.count), 256, 0, st>>>(s); WSI_COUNT(); }
 }
 
 // Gauss-Jordan inverse (host, float64) of an SPD matrix, no pivoting needed
@@ -307,13 +324,24 @@ static void spd_inverse(std::vector<double>& A, int n) {
 
 template <typename T>
 int precond_setup(Precond<T>& P, const GridDev& g, const Coef<double>& fine, cudaStream_t st, std::string& err) {
-  // fine coefficients in T
-  for (int c = 0; c < 3; ++c) {
-    cast_arr<double, T>(fine.rho_face[c], P.rho_face[c], fsize(g, c), st);
-    cast_arr<double, T>(fine.beta[c], P.lev[0].beta[c], fsize(g, c), st);
+  // fine coefficients in T (one launch for the ten arrays)
+  {
+    CastSet<double, T> cs;
+    cs.count = 0;
+    auto add = [&](const double* a, T* b, size_t n) {
+      cs.a[cs.count] = a;
+      cs.b[cs.count] = b;
+      cs.n[cs.count] = n;
+      ++cs.count;
+    };
+    for (int c = 0; c < 3; ++c) {
+      add(fine.rho_face[c], P.rho_face[c], fsize(g, c));
+      add(fine.beta[c], P.lev[0].beta[c], fsize(g, c));
+    }
+    add(fine.mu_cc, P.mu_cc, fsize(g, 3));
+    for (int e = 0; e < 3; ++e) add(fine.mu_e[e], P.mu_e[e], esize(g, e));
+    cast_set(cs, st);
   }
-  cast_arr<double, T>(fine.mu_cc, P.mu_cc, fsize(g, 3), st);
-  for (int e = 0; e < 3; ++e) cast_arr<double, T>(fine.mu_e[e], P.mu_e[e], esize(g, e), st);
   for (size_t l = 0; l + 1 < P.lev.size(); ++l) {
     MGLevel<T>& F = P.lev[l];
     MGLevel<T>& Cl = P.lev[l + 1];
@@ -818,11 +846,20 @@ template <typename T>
 void precond_apply(Precond<T>& P, const GridDev& g, const Opts& o, double dt, const double* v, double* z,
                    cudaStream_t st) {
   Packing pk = packing(g);
-  for (int c = 0; c < 3; ++c) {
-    cast_arr<double, T>(v + pk.off[c], P.ru[c], fsize(g, c), st);
-    cudaMemsetAsync(P.ut[c], 0, fsize(g, c) * sizeof(T), st);
+  {
+    CastSet<double, T> cs;
+    cs.count = 4;
+    for (int c = 0; c < 3; ++c) {
+      cs.a[c] = v + pk.off[c];
+      cs.b[c] = P.ru[c];
+      cs.n[c] = fsize(g, c);
+      cudaMemsetAsync(P.ut[c], 0, fsize(g, c) * sizeof(T), st);
+    }
+    cs.a[3] = v + pk.off[3];
+    cs.b[3] = P.rp;
+    cs.n[3] = fsize(g, 3);
+    cast_set(cs, st);  // one launch for the four parts
   }
-  cast_arr<double, T>(v + pk.off[3], P.rp, fsize(g, 3), st);
   Coef<T> cf;
   for (int c = 0; c < 3; ++c) {
     cf.rho_face[c] = P.rho_face[c];
