@@ -591,20 +591,15 @@ void transport_stage(wsi_ctx* c, int k, double dt, const double* un, const doubl
     parts(c, c->r1_32, r1);
     parts(c, c->r2_32, r2);
     parts(c, c->rn32, rn);
-    if (k == 0) {
-      launch_lincomb_to_f32(nv, 2.0, un, -1.0, unm1, 0.0, nullptr, c->u1_32, st);
-      launch_lincomb_to_f32(nv, 1.5, un, -0.5, unm1, 0.0, nullptr, c->u2_32, st);
-    } else {
-      launch_lincomb_to_f32(nv, 1.0, uk, 0.0, nullptr, 0.0, nullptr, c->u1_32, st);
-      launch_lincomb_to_f32(nv, 0.375, uk, 0.75, un, -0.125, unm1, c->u2_32, st);
-    }
+    // stage velocities (and the float32 u^n when stage 1 is formed afresh)
+    launch_rk_velocities_f32(nv, un, unm1, k == 0 ? nullptr : uk, c->u1_32, c->u2_32,
+                             reuse_stage1 ? nullptr : c->vn32, st);
     const float *cvn[3], *cu1[3], *cu2[3], *crn[3];
     cparts(c, (const float*)c->vn32, cvn);
     cparts(c, (const float*)c->u1_32, cu1);
     cparts(c, (const float*)c->u2_32, cu2);
     cparts(c, (const float*)c->rn32, crn);
     if (!reuse_stage1) {
-      launch_lincomb_to_f32(nv, 1.0, un, 0.0, nullptr, 0.0, nullptr, c->vn32, st);
       for (int d = 0; d < 3; ++d)
         launch_lincomb_to_f32(fsize(g, d), 1.0, c->rho_n[d], 0.0, nullptr, 0.0, nullptr, rn[d], st);
       launch_transport_flux<float>(g, cvn, crn, false, R, st);

@@ -96,6 +96,10 @@ void launch_lincomb_to_f32(size_t n, double a, const double* x, double b, const 
                            const double* z, float* out, cudaStream_t st);
 void launch_lincomb_f32(size_t n, float a, const float* x, float b, const float* y, float c, const float* z,
                         float* out, cudaStream_t st);
+// float32 SSP-RK3 stage velocities (first cycle: uk null) and, with un32, the
+// float32 copy of u^n, in one pass
+void launch_rk_velocities_f32(size_t n, const double* un, const double* unm1, const double* uk, float* u1, float* u2,
+                              float* un32, cudaStream_t st);
 void launch_lincomb_mix(size_t n, double a, const double* x, double b, const float* y, double c, const float* z,
                         double* out, cudaStream_t st);
 // z-chunk of the plane-marching stencil kernels for an ex x ey x ez box of

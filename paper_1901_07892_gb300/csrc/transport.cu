@@ -315,6 +315,26 @@ __global__ void k_lincomb_tof(size_t n, float a, const double* __restrict__ x, f
   }
 }
 
+// the two SSP-RK3 stage velocities of Sec. 4.2.2 in float32 from one pass over
+// u^n, u^{n-1} (and u^{n+1,k} in later cycles), and optionally the float32
+// copy of u^n; the same arithmetic as k_lincomb_tof for each output
+__global__ void k_rk_vel_tof(size_t n, const double* __restrict__ un, const double* __restrict__ unm1,
+                             const double* __restrict__ uk, float* u1, float* u2, float* un32) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+    const float a = d2f_fast(un[t]), b = d2f_fast(unm1[t]);
+    if (uk) {
+      const float q = d2f_fast(uk[t]);
+      u1[t] = 1.0f * q;
+      u2[t] = 0.375f * q + 0.75f * a + -0.125f * b;
+    } else {
+      u1[t] = 2.0f * a + -1.0f * b;
+      u2[t] = 1.5f * a + -0.5f * b;
+    }
+    if (un32) un32[t] = 1.0f * a;
+  }
+}
+
 // same in float32 arithmetic (float32 inputs and outputs)
 __global__ void k_lincomb_f(size_t n, float a, const float* __restrict__ x, float b, const float* __restrict__ y,
                             float c, const float* __restrict__ z, float* out) {
@@ -331,6 +351,11 @@ __global__ void k_lincomb_f(size_t n, float a, const float* __restrict__ x, floa
 static int lc_blocks(size_t n) {
   int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 16);
   return blocks < 1 ? 1 : blocks;
+}
+
+void launch_rk_velocities_f32(size_t n, const double* un, const double* unm1, const double* uk, float* u1, float* u2,
+                              float* un32, cudaStream_t st) {
+  { k_rk_vel_tof<<<lc_blocks(n), 256, 0, st>>>(n, un, unm1, uk, u1, u2, un32); WSI_COUNT(); }
 }
 
 void launch_lincomb(size_t n, double a, const double* x, double b, const double* y, double c, const double* z,
