@@ -21,6 +21,15 @@ are  u_ghost = s * u_interior  with s = -1 for no-slip and s = +1 for
 free-slip.  Cell-centred scalars (phi, psi, rho, mu, p) take homogeneous
 Neumann ghosts (mirror copies).
 
+Open top (Sec. 7.1's wave tank: zero tangential velocity and zero pressure on
+the top boundary).  With open_top the z+ side is not a wall: its tangential
+velocity ghosts take s = -1 (bc[5] must be NO_SLIP), the w-faces on it are
+unknowns, the pressure ghost above it is -p of the cell below (p = 0 on the
+plane, linear across it), and the ghost of w above it is the mirror image
+w[nz+1] = w[nz-1] (a zero normal derivative: the tangential velocity and
+hence its tangential derivatives vanish on the plane, so continuity leaves
+dw/dz = 0 there).
+
 Two-dimensional problems (Sec. 3 says the 2-D discretization is analogous)
 are run as nz = 1 with free-slip walls in z: every z-derivative then vanishes
 identically and all w-faces are wall faces.
@@ -43,6 +52,12 @@ class Grid:
     lz: float = 1.0
     # tangential-ghost sign per side: (x-, x+, y-, y+, z-, z+)
     bc: tuple = field(default=(NO_SLIP,) * 6)
+    # z+ side open (zero tangential velocity, zero pressure)
+    open_top: bool = False
+
+    def __post_init__(self):
+        if self.open_top and (self.bc[5] != NO_SLIP or self.nz < 2):
+            raise ValueError("an open top needs bc[5] = NO_SLIP and nz >= 2")
 
     @property
     def h(self):
@@ -113,7 +128,8 @@ class Grid:
         sl0[ax] = 0
         sl1[ax] = -1
         m[tuple(sl0)] = False
-        m[tuple(sl1)] = False
+        if not (c == 2 and self.open_top):
+            m[tuple(sl1)] = False
         return m
 
     def sign(self, axis, side):

@@ -14,20 +14,24 @@ accepts leading batch axes on its field arguments.
 
 Normal stress uses mu at cell centres; shear stress uses the harmonically
 averaged mu on edges.  Faces on walls are not unknowns: every face-valued
-result is 0 there.
+result is 0 there.  With an open top (grid.py) the top w-faces are rows too:
+G p there is (0 - p)/(h/2) from the pressure ghost -p; the normal stress of
+the ghost cell above is minus that of the cell below (w[nz+1] = w[nz-1]); the
+shear stresses on the top edges take the tangential ghosts -u, -v.
 """
 import numpy as np
 
 from .grid import Grid, pad_tangential
 
 
-def _zero_wall_faces(r, c):
+def _zero_wall_faces(g: Grid, r, c):
     ax = r.ndim - 1 - c
     idx = [slice(None)] * r.ndim
     idx[ax] = 0
     r[tuple(idx)] = 0.0
-    idx[ax] = -1
-    r[tuple(idx)] = 0.0
+    if not (c == 2 and g.open_top):
+        idx[ax] = -1
+        r[tuple(idx)] = 0.0
     return r
 
 
@@ -51,6 +55,9 @@ def grad(g: Grid, p):
         idx = [slice(None)] * p.ndim
         idx[ax] = slice(1, -1)
         r[tuple(idx)] = d
+        if c == 2 and g.open_top:
+            idx[ax] = -1
+            r[tuple(idx)] = -2.0 * np.take(p, -1, axis=ax) / hc
         out.append(r)
     return out
 
@@ -76,13 +83,18 @@ def strain_rate_apply(g: Grid, mat, u, v, w):
     out = []
     for c in range(3):
         q = vel[c]
-        # normal stress 2 mu dq/dx_c at cell centres, differenced back onto faces
+        top = c == 2 and g.open_top  # the last c-face is a row too
+        end = None if top else -1
+        # normal stress 2 mu dq/dx_c at cells, differenced back onto faces
         dq = _diff(q, c, g.h[c])                      # at cells
         tau = 2.0 * mu_cc * dq
         ax = q.ndim - 1 - c
+        if top:
+            # ghost cell above the open top: minus the stress of the cell below
+            tau = np.concatenate([tau, -np.take(tau, [-1], axis=ax)], axis=ax)
         res = np.zeros(q.shape)
         idx = [slice(None)] * q.ndim
-        idx[ax] = slice(1, -1)
+        idx[ax] = slice(1, end)
         res[tuple(idx)] = _diff(tau, c, g.h[c])
         # shear stresses on edges in the (c, d) planes
         qp = pad_tangential(g, q, c)
@@ -99,18 +111,24 @@ def strain_rate_apply(g: Grid, mat, u, v, w):
             ne = dqd.shape[axe]
             dqd = np.take(dqd, np.arange(1, ne - 1), axis=axe)
             # d-component differenced along c: defined on edges interior in c
-            dv = _diff(vel[d], c, g.h[c])
-            # dqd has full extent along c (q is a c-face array); dv lacks the two
-            # wall positions along c.  Shear flux only needed at interior c-faces.
+            # (and on the open top's edges, across the tangential ghost)
+            vd = vel[d]
+            if top:
+                vd = np.concatenate([vd, g.sign(c, 1) * np.take(vd, [-1], axis=vd.ndim - 1 - c)],
+                                    axis=vd.ndim - 1 - c)
+            dv = _diff(vd, c, g.h[c])
+            # dqd has full extent along c (q is a c-face array); dv lacks the
+            # wall positions along c.  Shear flux only needed at c-face rows.
             axc = dqd.ndim - 1 - c
             nc = dqd.shape[axc]
-            dqd_int = np.take(dqd, np.arange(1, nc - 1), axis=axc)
-            mu_int = np.take(mu_e, np.arange(1, mu_e.shape[mu_e.ndim - 1 - c] - 1),
-                             axis=mu_e.ndim - 1 - c)
+            last = nc if top else nc - 1
+            dqd_int = np.take(dqd, np.arange(1, last), axis=axc)
+            axm = mu_e.ndim - 1 - c
+            mu_int = np.take(mu_e, np.arange(1, mu_e.shape[axm] if top else mu_e.shape[axm] - 1), axis=axm)
             flux = mu_int * (dqd_int + dv)
             sh = _diff(flux, d, g.h[d])
             res[tuple(idx)] += sh
-        out.append(_zero_wall_faces(res, c))
+        out.append(_zero_wall_faces(g, res, c))
     return out
 
 
@@ -120,7 +138,7 @@ def viscous_apply(g: Grid, mat, rho_face, dt, theta, u, v, w):
     out = []
     for c, q in enumerate((u, v, w)):
         r = rho_face[c] / dt * q - theta * L[c]
-        out.append(_zero_wall_faces(r, c))
+        out.append(_zero_wall_faces(g, r, c))
     return out
 
 
@@ -129,6 +147,6 @@ def stokes_apply(g: Grid, mat, rho_face, dt, theta, x):
     u, v, w, p = g.unpack(x)
     au = viscous_apply(g, mat, rho_face, dt, theta, u, v, w)
     gp = grad(g, p)
-    ru = [_zero_wall_faces(au[c] + gp[c], c) for c in range(3)]
+    ru = [_zero_wall_faces(g, au[c] + gp[c], c) for c in range(3)]
     rp = -div(g, u, v, w)
     return g.pack(ru[0], ru[1], ru[2], rp)

@@ -85,17 +85,21 @@ def solve_stokes(g: Grid, mat, rho_face, dt, theta, b):
     """Solution x = (u, v, w, p) of K x = b with sum(p) = 0, zero on wall faces.
 
     b is a packed Stokes vector (b_u on faces, b_p at cells); its wall-face
-    entries are ignored.  Returns x packed."""
+    entries are ignored.  Returns x packed.  With an open top the pressure
+    is fixed by p = 0 on the top plane: no constraint on sum(p)."""
     Kfull = stokes_matrix(g, mat, rho_face, dt, theta)
     unk = np.nonzero(g.unknown_mask())[0]
     Ku = Kfull[unk][:, unk]
     nu = unk.size
+    x = np.zeros(b.shape[-1])
+    if g.open_top:
+        x[unk] = spla.spsolve(sp.csc_matrix(Ku), b[unk])
+        return x
     np_ = g.n_cells
     e = np.zeros(nu)
     e[nu - np_:] = 1.0  # pressure entries are last in the packing
     Kb = sp.bmat([[Ku, sp.csr_matrix(e[:, None])], [sp.csr_matrix(e[None, :]), None]], format="csc")
     rhs = np.concatenate([b[unk], [0.0]])
     sol = spla.spsolve(Kb, rhs)
-    x = np.zeros(b.shape[-1])
     x[unk] = sol[:nu]
     return x

@@ -23,7 +23,9 @@ consistent scheme):
   C is the upwind point, U the next point upwind, D the downwind point; the
   direction comes from the sign of the advective velocity (> 0: from below).
 * Ghosts: face density mirrors evenly across walls (Neumann); velocity
-  ghosts follow the wall condition (tangential: sign s, normal: odd).
+  ghosts follow the wall condition (tangential: sign s, normal: odd; across
+  an open top the normal velocity mirrors evenly, its derivative being zero
+  there, grid.py).
 * Faces on walls are not transported (R = C = 0 there).
 """
 import numpy as np
@@ -65,7 +67,7 @@ def _ghost_extend(g: Grid, q, c, d, kind):
             sgn_hi.append(1.0)
         elif face_along_d:
             sgn_lo.append(-1.0)
-            sgn_hi.append(-1.0)
+            sgn_hi.append(1.0 if (d == 2 and g.open_top) else -1.0)
         else:
             sgn_lo.append(g.sign(d, 0))
             sgn_hi.append(g.sign(d, 1))
