@@ -112,10 +112,8 @@ struct wsi_ctx {
   double* inv_mu = nullptr;  // materials scratch: 1/mu per cell
   // mixed path: split (hi, lo) copies of the operator coefficients (refreshed
   // at the start of every solve) and of the matvec input
-  float2* df_rho[3] = {nullptr, nullptr, nullptr};
-  float2* df_mu_cc = nullptr;
-  float2* df_mu_e[3] = {nullptr, nullptr, nullptr};
-  float2* df_x = nullptr;
+  DfOperands df;
+  int* df_err = nullptr;  // set by the matvec when a wait for a tile copy gave up
   // a fully locked body at rest never moves: psi is rebuilt once, then kept
   bool psi_static_done = false;
   // mu_cc / mu_e hold mu(phi^n, psi^n) (true right after a step)
@@ -291,25 +289,7 @@ void pc_apply(wsi_ctx* c, double dt, const double* v, double* z) {
 // the face density is stored times 1/dt
 void df_coef_refresh(wsi_ctx* c, const Coef<double>& cf, double inv_dt) {
   if (!c->mixed()) return;
-  const double* x[7];
-  float2* o[7];
-  size_t n[7];
-  double sc[7];
-  for (int d = 0; d < 3; ++d) {
-    x[d] = cf.rho_face[d];
-    o[d] = c->df_rho[d];
-    n[d] = fsize(c->g, d);
-    sc[d] = inv_dt;
-    x[3 + d] = cf.mu_e[d];
-    o[3 + d] = c->df_mu_e[d];
-    n[3 + d] = esize(c->g, d);
-    sc[3 + d] = 1.0;
-  }
-  x[6] = cf.mu_cc;
-  o[6] = c->df_mu_cc;
-  n[6] = c->ncell;
-  sc[6] = 1.0;
-  launch_df_split_set(x, o, n, sc, 7, c->st);  // one launch for the seven arrays
+  df_split_coefs(c->df, cf.rho_face, cf.mu_e, cf.mu_cc, inv_dt, c->st);  // one launch for the seven arrays
 }
 
 // K x: float64 on the plain path; on the mixed path in double-float
@@ -318,18 +298,22 @@ void df_coef_refresh(wsi_ctx* c, const Coef<double>& cf, double inv_dt) {
 void stokes_mv(wsi_ctx* c, const Coef<double>& cf, double inv_dt, double theta, const double* x, double* y,
                cudaStream_t st) {
   if (c->mixed()) {
-    DfCoef dc;
-    for (int d = 0; d < 3; ++d) {
-      dc.rho_face[d] = c->df_rho[d];
-      dc.mu_e[d] = c->df_mu_e[d];
-    }
-    dc.mu_cc = c->df_mu_cc;
     (void)inv_dt;  // folded into the split face density by df_coef_refresh
-    launch_df_split(x, c->df_x, c->nstk, st);
-    launch_stokes_df(c->g, dc, theta, c->df_x, y, st);
+    launch_stokes_df(c->g, c->df, theta, x, y, c->df_err, st);
   } else {
     launch_stokes(c->g, cf, inv_dt, theta, x, y, st);
   }
+}
+
+// reads and clears the matvec's device error flag (synchronises the stream)
+int df_check(wsi_ctx* c) {
+  if (!c->mixed() || !c->df_err) return WSI_OK;
+  int h = 0;
+  cudaMemcpyAsync(&h, c->df_err, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "matvec");
+  if (!h) return WSI_OK;
+  cudaMemsetAsync(c->df_err, 0, sizeof(int), c->st);
+  return fail(c, WSI_ERR_DEVICE, "the double-float matvec gave up waiting for a tile copy");
 }
 
 // FGMRES(m), right preconditioned by the projection method; float64 Arnoldi
@@ -462,6 +446,8 @@ int fgmres(wsi_ctx* c, const double* b, double* x, double dt, const wsi_solve_op
   s->iters = iters;
   s->rel_residual = beta / bnorm;
   int crc = cuda_check(c, "fgmres");
+  if (crc) return crc;
+  crc = df_check(c);
   if (crc) return crc;
   if (result == WSI_ERR_NOT_CONVERGED) c->err = "FGMRES reached max_iters";
   return result;
@@ -870,13 +856,17 @@ int wsi_create_grid(const wsi_grid_desc* d, void* stream, wsi_ctx** out) {
     c->mu_cc_n32 = F(c->ncell);
     for (int e = 0; e < 3; ++e) c->mu_e_n32[e] = F(esize(g, e));
     // double-float operands: one float2 per element, the size of a double
-    auto P2 = [&](size_t n) { return (float2*)A(n); };
-    for (int a = 0; a < 3; ++a) {
-      c->df_rho[a] = P2(fsize(g, a));
-      c->df_mu_e[a] = P2(esize(g, a));
+    df_operands_shape(g, c->df);
+    for (int a = 0; a < DF_NARR; ++a) c->df.a[a] = (float2*)A(df_operand_elems(c->df, a));
+    c->df_err = (int*)A(1);
+    if (ok) {
+      cudaMemsetAsync(c->df_err, 0, sizeof(int), c->st);
+      if (df_operands_encode(c->df) != WSI_OK) {
+        c->err = "tile-copy descriptors of the matvec operands could not be encoded";
+        wsi_destroy(c);
+        return WSI_ERR_CUDA;
+      }
     }
-    c->df_mu_cc = P2(c->ncell);
-    c->df_x = P2(c->nstk);
   }
   c->red = A(8192);
   if (!ok) {
@@ -897,6 +887,7 @@ void wsi_destroy(wsi_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   precond_free<double>(c->P64);
   precond_free<float>(c->P32);
+  df_operands_release(c->df);
   for (void* p : c->allocs) cudaFree(p);
   delete c;
 }
@@ -1278,7 +1269,9 @@ int wsi_apply(wsi_ctx* c, int op, const double* in, double* out, double dt) {
   }
   rc = copy_out(c, out, xout, nout);
   if (rc) return rc;
-  return cuda_check(c, "apply");
+  rc = cuda_check(c, "apply");
+  if (rc == WSI_OK && op == WSI_OP_STOKES) rc = df_check(c);
+  return rc;
 }
 
 int wsi_transport(wsi_ctx* c, const double* u_n, const double* u_nm1, const double* u_k, int k, double dt,

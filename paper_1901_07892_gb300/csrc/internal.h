@@ -59,25 +59,33 @@ void launch_div(const GridDev& g, const T* const q[3], T* out, T scale, cudaStre
 void launch_stokes(const GridDev& g, const Coef<double>& cf, double inv_dt, double theta, const double* x, double* y,
                    cudaStream_t st);
 // Operands of the double-float Stokes matvec (dfstokes.cu): (hi, lo) float32
-// pairs of the coefficients and of a packed Stokes vector
-struct DfCoef {
-  const float2* rho_face[3];  // face density times 1/dt
-  const float2* mu_cc;
-  const float2* mu_e[3];
+// pairs of the input vector and of the coefficients, each array with an even
+// row pitch (rows start on 16-byte boundaries, as the tile copies need)
+enum DfArray {
+  DF_U = 0, DF_V, DF_W, DF_P,           // input vector
+  DF_RHO_X, DF_RHO_Y, DF_RHO_Z,        // face density times 1/dt
+  DF_MU_CC, DF_MU_XY, DF_MU_XZ, DF_MU_YZ,  // cell and edge viscosity
+  DF_NARR
 };
-struct DfVec {
-  const float2* q[3];
-  const float2* p;
+struct DfOperands {
+  float2* a[DF_NARR] = {};
+  int cols[DF_NARR], rows[DF_NARR], levels[DF_NARR], pitch[DF_NARR];
+  void* maps = nullptr;  // host copy of the arrays' tile-copy descriptors
 };
-// out[i] = (hi, lo) split of x[i] (of s x[i])
-void launch_df_split(const double* x, float2* out, size_t n, cudaStream_t st);
-void launch_df_split_scaled(const double* x, double s, float2* out, size_t n, cudaStream_t st);
-// up to eight arrays in one launch (scale[k] 1: plain split)
-void launch_df_split_set(const double* const* x, float2* const* out, const size_t* n, const double* scale, int count,
-                         cudaStream_t st);
-// y = K x in double-float arithmetic from the split coefficients (face
-// density already times 1/dt) and x
-void launch_stokes_df(const GridDev& g, const DfCoef& cf, double theta, const float2* x, double* y,
+// extents and pitches of the arrays for grid g
+void df_operands_shape(const GridDev& g, DfOperands& o);
+// float2 elements array a takes (pitch x rows x levels)
+size_t df_operand_elems(const DfOperands& o, int a);
+// the tile-copy descriptors of the allocated arrays (WSI_OK or WSI_ERR_CUDA)
+int df_operands_encode(DfOperands& o);
+void df_operands_release(DfOperands& o);
+// split the seven coefficient arrays, the face density times inv_dt
+void df_split_coefs(const DfOperands& o, const double* const rho[3], const double* const mu_e[3], const double* mu_cc,
+                    double inv_dt, cudaStream_t st);
+// y = K x in double-float arithmetic: x split into the operands, then the
+// matvec from the coefficients split by the last df_split_coefs; *err is set
+// to 1 when a wait for a tile copy gave up
+void launch_stokes_df(const GridDev& g, const DfOperands& o, double theta, const double* x, double* y, int* err,
                       cudaStream_t st);
 // red-black Gauss-Seidel half sweep on the viscous block for component c
 template <typename T>

@@ -437,7 +437,13 @@ def test_hydrostatic_config2_full_size():
     assert umax[-1] <= 10 * umax[0] + 1e-12, umax
 
 
-@pytest.mark.parametrize("shape", SHAPES)
+# shapes around the matvec's tiles (30 x-positions, 8 rows, 16 levels per
+# block): several ragged blocks along every axis, exact multiples and one
+# past them, and a grid smaller than one tile
+MV_SHAPES = SHAPES + [(61, 19, 35), (30, 8, 16), (31, 9, 17), (3, 2, 2)]
+
+
+@pytest.mark.parametrize("shape", MV_SHAPES)
 def test_stokes_apply_mixed_double_float(shape):
     """The mixed path's Stokes matvec (strain term in double-float
     arithmetic) meets the same 1e-11 bound as the float64 one."""
