@@ -18,6 +18,13 @@ result is 0 there.  With an open top (grid.py) the top w-faces are rows too:
 G p there is (0 - p)/(h/2) from the pressure ghost -p; the normal stress of
 the ghost cell above is minus that of the cell below (w[nz+1] = w[nz-1]); the
 shear stresses on the top edges take the tangential ghosts -u, -v.
+
+Dirichlet inlet (Sec. 7.1) on the x- side: its faces are not unknowns but
+hold the prescribed normal velocity, which every operator reads like any
+other entry of u; the prescribed tangential velocity w_b of the x- edges
+(inlet_w, shape (nz+1, ny)) enters through the ghost of w across the plane,
+2 w_b - w (zero-data: the no-slip ghost -w).  The inlet's span-wise
+velocity is zero (the no-slip ghost).
 """
 import numpy as np
 
@@ -73,9 +80,10 @@ def pressure_apply(g: Grid, beta, p):
     return div(g, beta[0] * gp[0], beta[1] * gp[1], beta[2] * gp[2])
 
 
-def strain_rate_apply(g: Grid, mat, u, v, w):
+def strain_rate_apply(g: Grid, mat, u, v, w, inlet_w=None):
     """L_mu u = div_h[mu (grad_h u + grad_h u^T)] for all three components,
-    evaluated on every face (wall faces set to 0)."""
+    evaluated on every face (wall faces set to 0); inlet_w: tangential
+    inlet data on the x- edges, or None."""
     hx, hy, hz = g.h
     vel = (u, v, w)
     mu_edge = {(0, 1): mat.mu_xy, (0, 2): mat.mu_xz, (1, 2): mat.mu_yz}
@@ -98,6 +106,9 @@ def strain_rate_apply(g: Grid, mat, u, v, w):
         res[tuple(idx)] = _diff(tau, c, g.h[c])
         # shear stresses on edges in the (c, d) planes
         qp = pad_tangential(g, q, c)
+        if c == 2 and inlet_w is not None:
+            qp = qp.copy()
+            qp[..., 1:-1, 0] += 2.0 * inlet_w  # ghost 2 w_b - w across the inlet
         for d in range(3):
             if d == c:
                 continue
@@ -132,9 +143,9 @@ def strain_rate_apply(g: Grid, mat, u, v, w):
     return out
 
 
-def viscous_apply(g: Grid, mat, rho_face, dt, theta, u, v, w):
+def viscous_apply(g: Grid, mat, rho_face, dt, theta, u, v, w, inlet_w=None):
     """A u = rho/dt u - theta L_mu u (wall faces 0)."""
-    L = strain_rate_apply(g, mat, u, v, w)
+    L = strain_rate_apply(g, mat, u, v, w, inlet_w)
     out = []
     for c, q in enumerate((u, v, w)):
         r = rho_face[c] / dt * q - theta * L[c]
@@ -142,10 +153,12 @@ def viscous_apply(g: Grid, mat, rho_face, dt, theta, u, v, w):
     return out
 
 
-def stokes_apply(g: Grid, mat, rho_face, dt, theta, x):
-    """K x for a packed Stokes vector x = (u, v, w, p)."""
+def stokes_apply(g: Grid, mat, rho_face, dt, theta, x, inlet_w=None):
+    """K x for a packed Stokes vector x = (u, v, w, p); with inlet_w the
+    affine operator of the Dirichlet inlet (its data: x's x- faces and
+    inlet_w)."""
     u, v, w, p = g.unpack(x)
-    au = viscous_apply(g, mat, rho_face, dt, theta, u, v, w)
+    au = viscous_apply(g, mat, rho_face, dt, theta, u, v, w, inlet_w)
     gp = grad(g, p)
     ru = [_zero_wall_faces(g, au[c] + gp[c], c) for c in range(3)]
     rp = -div(g, u, v, w)

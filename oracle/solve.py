@@ -103,3 +103,16 @@ def solve_stokes(g: Grid, mat, rho_face, dt, theta, b):
     sol = spla.spsolve(Kb, rhs)
     x[unk] = sol[:nu]
     return x
+
+
+def solve_stokes_inlet(g: Grid, mat, rho_face, dt, theta, b, u_in, w_in):
+    """Solution of the Stokes system with a Dirichlet inlet on the x- side
+    (Sec. 7.1): normal velocity u_in (nz, ny) on the x- faces, tangential
+    velocity w_in (nz+1, ny) on the x- edges.  The data are lifted to the
+    right-hand side: K x~ = b - K_in x_b with x_b zero except u_in on the x-
+    faces and K_in the operator with the inlet's affine ghost; x = x~ + x_b."""
+    u0 = np.zeros(g.face_shape(0))
+    u0[..., 0] = u_in
+    xb = g.pack(u0, np.zeros(g.face_shape(1)), np.zeros(g.face_shape(2)), np.zeros(g.cell_shape))
+    r = b - stokes_apply(g, mat, rho_face, dt, theta, xb, inlet_w=w_in)
+    return solve_stokes(g, mat, rho_face, dt, theta, r) + xb

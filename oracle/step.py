@@ -14,6 +14,11 @@ For cycles k = 0 .. n_cycles-1 (the paper uses n_cycles = 2):
   3. rigidity projection at X^{n+1/2,k} and the position update.
 At k = 0: u^{n+1,0} = u^n, X^{n+1,0} = X^n.  At n = 0: u^{-1} = u^0.
 With wave zones, u^{n+1} and phi^{n+1} are relaxed at t^{n+1} (Sec. 7.1).
+With a Dirichlet inlet (waves.Inlet, Sec. 7.1) the x- faces hold the inlet's
+normal velocity at the time of each velocity field; the implicit solve takes
+the data at t^{n+1} (solve.solve_stokes_inlet), the explicit viscous term the
+tangential data at t^n, and the transport's stage velocities the same
+combinations of the data at t^n, t^{n-1}, t^{n+1} as of the velocities.
 limiter selects the level-set face values ("cui" or "xsppm7", levelset.py).
 With reinit_iters > 0, phi^{n+1} is then reinitialised to a signed distance
 (Sec. 4.1; reinit.py) before the step is committed.
@@ -36,7 +41,7 @@ from . import levelset, reinit, rigid, transport
 from .grid import Grid
 from .materials import Materials, face_average, flow_only
 from .operators import strain_rate_apply
-from .solve import solve_stokes
+from .solve import solve_stokes, solve_stokes_inlet
 
 
 class Props:
@@ -66,16 +71,23 @@ class Body:
 
 
 class State:
-    def __init__(self, g: Grid, props: Props, phi, psi, body=None, vel=None, p=None, zones=None, time=0.0):
+    def __init__(self, g: Grid, props: Props, phi, psi, body=None, vel=None, p=None, zones=None, time=0.0,
+                 inlet=None):
         self.g = g
         self.zones = zones  # waves.Zones or None (Sec. 7.1 relaxation at step end)
+        self.inlet = inlet  # waves.Inlet or None (Sec. 7.1 Dirichlet inlet on the x- plane)
         self.time = time
         self.props = props
         self.phi = np.array(phi, dtype=np.float64)
         self.psi = np.array(psi, dtype=np.float64)
         self.body = body
         self.vel = [np.zeros(g.face_shape(c)) for c in range(3)] if vel is None else [np.array(a) for a in vel]
+        self.gw = None
+        if inlet is not None:
+            self.vel[0][..., 0] = inlet.normal(g, time, props.n_cells)
+            self.gw = inlet.tangential(g, time, props.n_cells)  # tangential data of vel
         self.vel_old = [a.copy() for a in self.vel]
+        self.gw_old = None if self.gw is None else self.gw.copy()
         self.p = np.zeros(g.cell_shape) if p is None else np.array(p)
 
 
@@ -91,7 +103,13 @@ def step(s: State, dt, n_cycles=2, reinit_iters=0, form="consistent", limiter="c
     phi_n, psi_n = s.phi.copy(), s.psi.copy()
     mat_n = _materials(s, phi_n, psi_n)
     rho_n = mat_n.rho_face
-    Lmu_n = strain_rate_apply(g, mat_n, *u_n)
+    inl = s.inlet
+    gw_n = gw_nm1 = gw_np1 = gn_np1 = None
+    if inl is not None:
+        gw_n, gw_nm1 = s.gw, s.gw_old
+        gw_np1 = inl.tangential(g, s.time + dt, pr.n_cells)
+        gn_np1 = inl.normal(g, s.time + dt, pr.n_cells)
+    Lmu_n = strain_rate_apply(g, mat_n, *u_n, inlet_w=gw_n)
     body = s.body
     X_n = body.X.copy() if body is not None else None
     Ub_n = body.Ub.copy() if body is not None else None
@@ -111,13 +129,16 @@ def step(s: State, dt, n_cycles=2, reinit_iters=0, form="consistent", limiter="c
         else:
             psi_new = psi_k
         mat = _materials(s, phi_new, psi_new)
+        gw_k = gw_n if k == 0 else gw_np1  # tangential inlet data of u_k
         if form == "consistent":
             u1, u2 = transport.rk_velocities(u_n, u_nm1, u_k, k)
-            rho_new, C = transport.ssp_rk3(g, rho_n, u_n, u1, u2, dt)
+            g2 = None if inl is None else transport.rk_velocities([gw_n], [gw_nm1], [gw_k], k)[1][0]
+            rho_new, C = transport.ssp_rk3(g, rho_n, u_n, u1, u2, dt, inlet_w2=g2)
         elif form == "nonconservative":
             rho_new = mat.rho_face
             ones = [np.ones(g.face_shape(c)) for c in range(3)]
-            N = transport.convective(g, [0.5 * (a + b) for a, b in zip(u_k, u_n)], ones)
+            N = transport.convective(g, [0.5 * (a + b) for a, b in zip(u_k, u_n)], ones,
+                                     None if inl is None else 0.5 * (gw_k + gw_n))
         else:
             raise ValueError(form)
         if pr.gravity_mode == "flow":
@@ -131,7 +152,10 @@ def step(s: State, dt, n_cycles=2, reinit_iters=0, form="consistent", limiter="c
             b_u = [rho_new[c] * (u_n[c] / dt - N[c]) + (1.0 - pr.theta) * Lmu_n[c] + rho_grav[c] * pr.gravity[c]
                    for c in range(3)]
         b = g.pack(b_u[0], b_u[1], b_u[2], np.zeros(g.cell_shape))
-        x = solve_stokes(g, mat, rho_new, dt, pr.theta, b)
+        if inl is None:
+            x = solve_stokes(g, mat, rho_new, dt, pr.theta, b)
+        else:
+            x = solve_stokes_inlet(g, mat, rho_new, dt, pr.theta, b, gn_np1, gw_np1)
         ut, vt, wt, p = g.unpack(x)
         vel_t = [ut, vt, wt]
         if body is not None:
@@ -154,6 +178,8 @@ def step(s: State, dt, n_cycles=2, reinit_iters=0, form="consistent", limiter="c
     s.time += dt
     s.vel_old = u_n
     s.vel = u_k
+    if inl is not None:
+        s.gw_old, s.gw = gw_n, gw_np1
     s.p = p
     s.phi = phi_k
     s.psi = psi_k

@@ -27,6 +27,10 @@ consistent scheme):
   an open top the normal velocity mirrors evenly, its derivative being zero
   there, grid.py).
 * Faces on walls are not transported (R = C = 0 there).
+* Across a Dirichlet inlet (Sec. 7.1) the ghosts of the tangential w are
+  2 w_b - (mirror image), with w_b the inlet data of the velocity being
+  transported; a stage velocity's data are the same combination of the data
+  at t^n, t^{n-1} and t^{n+1} as the stage velocity itself.
 """
 import numpy as np
 
@@ -43,10 +47,12 @@ def cui(qU, qC, qD):
     return np.where(den == 0.0, qC, qU + tf * den)
 
 
-def _ghost_extend(g: Grid, q, c, d, kind):
+def _ghost_extend(g: Grid, q, c, d, kind, lo_data=None):
     """Extend array q (values on c-faces, or on cells if c is None) by two
     ghost layers on both ends of axis d.
-    kind: 'even' (density / scalars), 'vel' (velocity component c)."""
+    kind: 'even' (density / scalars), 'vel' (velocity component c).
+    lo_data: Dirichlet data of a tangential velocity on the lower plane of
+    axis d (the inlet's w): its ghosts are 2 data - (mirror image)."""
     ax = q.ndim - 1 - d
     n = q.shape[ax]
     face_along_d = (c == d)
@@ -74,16 +80,18 @@ def _ghost_extend(g: Grid, q, c, d, kind):
     idx_lo = [min(max(i, 0), n - 1) for i in idx_lo]
     idx_hi = [min(max(i, 0), n - 1) for i in idx_hi]
     lo = [np.take(q, [i], axis=ax) * s for i, s in zip(idx_lo, sgn_lo)]
+    if lo_data is not None:
+        lo = [a + 2.0 * np.expand_dims(lo_data, ax) for a in lo]
     hi = [np.take(q, [i], axis=ax) * s for i, s in zip(idx_hi[::-1], sgn_hi[::-1])]
     return np.concatenate(lo + [q] + hi, axis=ax)
 
 
-def _limited(g: Grid, q, c, d, adv, kind, on_cells):
+def _limited(g: Grid, q, c, d, adv, kind, on_cells, lo_data=None):
     """Limited value of q (a c-face array, extended along d) at the CV faces
     along d.  on_cells: CV faces along d are between consecutive q entries
     m and m+1 (d == c), indexed m = 0..n-2; otherwise between m-1 and m,
     m = 0..n (edges, the two ends on walls)."""
-    e = _ghost_extend(g, q, c, d, kind)
+    e = _ghost_extend(g, q, c, d, kind, lo_data)
     ax = e.ndim - 1 - d
     n = q.shape[q.ndim - 1 - d]
 
@@ -123,8 +131,9 @@ def _adv_velocity(g: Grid, vel, c, d):
     return np.concatenate([z, a, z], axis=axc)
 
 
-def _fluxes(g: Grid, vel, rho, qvel, c):
-    """Divergence over the c-face control volumes of adv * rho_lim (* q_lim)."""
+def _fluxes(g: Grid, vel, rho, qvel, c, inlet_w=None):
+    """Divergence over the c-face control volumes of adv * rho_lim (* q_lim);
+    inlet_w: tangential inlet data of qvel = w on the x- plane, or None."""
     out = np.zeros(g.face_shape(c))
     for d in range(3):
         adv = _adv_velocity(g, vel, c, d)
@@ -132,7 +141,8 @@ def _fluxes(g: Grid, vel, rho, qvel, c):
         r_lim = _limited(g, rho, c, d, adv, "even", on_cells)
         F = adv * r_lim
         if qvel is not None:
-            F = F * _limited(g, qvel, c, d, adv, "vel", on_cells)
+            data = inlet_w if (c == 2 and d == 0) else None
+            F = F * _limited(g, qvel, c, d, adv, "vel", on_cells, data)
         ax = F.ndim - 1 - d
         n = F.shape[ax]
         dF = (np.take(F, np.arange(1, n), axis=ax) - np.take(F, np.arange(0, n - 1), axis=ax)) / g.h[d]
@@ -158,9 +168,10 @@ def mass_flux(g: Grid, vel, rho):
     return [_fluxes(g, vel, rho[c], None, c) for c in range(3)]
 
 
-def convective(g: Grid, vel, rho):
-    """C(u_adv, rho_lim u_lim) for the three momentum components."""
-    return [_fluxes(g, vel, rho[c], vel[c], c) for c in range(3)]
+def convective(g: Grid, vel, rho, inlet_w=None):
+    """C(u_adv, rho_lim u_lim) for the three momentum components; inlet_w:
+    the tangential inlet data of vel's w, or None."""
+    return [_fluxes(g, vel, rho[c], vel[c], c, inlet_w) for c in range(3)]
 
 
 def rk_velocities(u_n, u_nm1, u_k, k):
@@ -174,13 +185,14 @@ def rk_velocities(u_n, u_nm1, u_k, k):
     return u1, u2
 
 
-def ssp_rk3(g: Grid, rho_n, u_n, u1, u2, dt):
-    """Returns rho^{n+1,k+1} (3 face arrays) and C (3 face arrays)."""
+def ssp_rk3(g: Grid, rho_n, u_n, u1, u2, dt, inlet_w2=None):
+    """Returns rho^{n+1,k+1} (3 face arrays) and C (3 face arrays);
+    inlet_w2: the tangential inlet data of u2's w, or None."""
     R0 = mass_flux(g, u_n, rho_n)
     r1 = [rho_n[c] - dt * R0[c] for c in range(3)]
     R1 = mass_flux(g, u1, r1)
     r2 = [0.75 * rho_n[c] + 0.25 * r1[c] - 0.25 * dt * R1[c] for c in range(3)]
     R2 = mass_flux(g, u2, r2)
     r3 = [rho_n[c] / 3.0 + 2.0 / 3.0 * r2[c] - 2.0 / 3.0 * dt * R2[c] for c in range(3)]
-    C = convective(g, u2, r2)
+    C = convective(g, u2, r2, inlet_w2)
     return r3, C

@@ -19,6 +19,16 @@ Relaxation at the end of each step: q <- alpha q + (1 - alpha) q_target with
 alpha = 1 - (exp(xb^3.5) - 1)/(e - 1), xb the normalised distance into the
 zone (0 where the zone meets the computed region, 1 at the far wall).
 
+Dirichlet inlet (Sec. 7.1, the inlet's boundary-Heaviside equation): on the
+x- plane the normal velocity of face (j, k) is (1 - H~(phi_b)) u_w(0, y_k, t)
+with phi_b = y_k - eta(0, t) at the face centre, and the tangential
+(vertical) velocity of the x- edge at height y_k = k h - d is
+(1 - H~(phi_b)) v_w(0, y_k, t) with phi_b at the edge; H~ has the width
+n_cells times the characteristic spacing of the Heaviside of the materials
+(sqrt(dx dy) in 2-D, the paper's sqrt(dV); the cube root of the cell volume
+in 3-D).  The span-wise velocity there is zero.  The data are taken at the
+time of the velocity they bound (t^{n+1} for the implicit solve).
+
 Readings (the paper uses a Dirichlet inlet and a damping zone only):
 * the generation zone mirrors the damping zone at the inlet end; its
   targets are the level set phi = y - eta(x, t) and the liquid-only
@@ -84,11 +94,13 @@ class Zones:
         self.wave, self.x_gen, self.x_damp, self.lx, self.vert = wave, x_gen, x_damp, lx, vert
 
     def weights(self, x):
-        """(alpha, in_gen, in_damp) at positions x."""
+        """(alpha, in_gen, in_damp) at positions x (x_gen = 0: no
+        generation zone, as with a Dirichlet inlet)."""
         a = np.ones_like(x, dtype=np.float64)
         gen = x < self.x_gen
         dmp = x > self.x_damp
-        a = np.where(gen, alpha((self.x_gen - x) / self.x_gen), a)
+        if self.x_gen > 0:
+            a = np.where(gen, alpha((self.x_gen - x) / self.x_gen), a)
         a = np.where(dmp, alpha((x - self.x_damp) / (self.lx - self.x_damp)), a)
         return a, gen, dmp
 
@@ -111,7 +123,7 @@ class Zones:
                 tgt_gen = np.zeros_like(x)
             tgt = np.where(gen, tgt_gen, 0.0)
             q = a * vel[c] + (1.0 - a) * tgt
-            q = q * g.interior_face_mask(c)
+            q = np.where(g.interior_face_mask(c), q, vel[c])  # boundary faces keep their values
             out.append(q)
         Xc = np.broadcast_arrays(*g.cell_centers())
         x = Xc[0]
@@ -119,3 +131,30 @@ class Zones:
         a, gen, _ = self.weights(x)
         tgt = np.where(gen, y - self.wave.eta(x, t), y)
         return out, a * phi + (1.0 - a) * tgt
+
+
+class Inlet:
+    """Dirichlet wave inlet on the x- plane (Sec. 7.1) of a tank whose
+    vertical axis is z; still-water depth d = wave.d."""
+
+    def __init__(self, wave: StokesWave):
+        self.wave = wave
+
+    def _liquid(self, g: Grid, y, t, n_cells):
+        phib = y - self.wave.eta(0.0, t)
+        return 1.0 - heaviside(phib, n_cells * char_spacing(g))
+
+    def normal(self, g: Grid, t, n_cells=2.0):
+        """u on the x- faces, shape (nz, ny)."""
+        _, _, z = g.face_centers(0)
+        yy = z[..., 0] - self.wave.d
+        uw, _ = self.wave.velocity(0.0, yy, t)
+        out = self._liquid(g, yy, t, n_cells) * uw
+        return np.broadcast_to(out, (g.nz, g.ny)).copy()
+
+    def tangential(self, g: Grid, t, n_cells=2.0):
+        """w on the x- edges (heights k hz), shape (nz+1, ny)."""
+        yy = np.arange(g.nz + 1)[:, None] * g.hz - self.wave.d
+        _, vw = self.wave.velocity(0.0, yy, t)
+        out = self._liquid(g, yy, t, n_cells) * vw
+        return np.broadcast_to(out, (g.nz + 1, g.ny)).copy()
