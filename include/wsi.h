@@ -100,6 +100,11 @@ typedef struct {
                             of the pressure multigrid                        */
     int ls_limiter;      /* WSI_LIMIT_CUI or WSI_LIMIT_XSPPM7: face values of
                             the level-set advection (Sec. 4.2.1)             */
+    int open_top;        /* 1: the z+ side is open (Sec. 7.1's tank: zero
+                            tangential velocity and zero pressure on the top
+                            plane; its z-faces are unknowns, dw/dz = 0 there).
+                            Needs bc[5] = WSI_NO_SLIP, nz >= 2 and
+                            visc_mg = 0; 0: a wall like the other sides      */
 } wsi_grid_desc;
 
 typedef struct {
@@ -308,6 +313,16 @@ typedef struct {
     double x_gen, x_damp;
     double t0;
     int vertical;
+    int inlet;           /* 1: Dirichlet wave inlet on the x- plane (Sec. 7.1):
+                            the x- faces carry the liquid-only normal Stokes
+                            velocity (1 - H~(phi_b)) u_w(0, z, t), phi_b =
+                            z - d - eta(0, t), and the x- edges the vertical
+                            one, imposed through the ghost 2 w_b - w; the data
+                            of t^{n+1} are lifted into the implicit solve.
+                            Needs vertical = 2 and bc[0] = WSI_NO_SLIP; x_gen
+                            may then be 0 (no generation zone).  Sets the x-
+                            faces of the current velocity and of the previous
+                            one to the data of t0: set the state first      */
 } wsi_wave_desc;
 int wsi_set_waves(wsi_ctx* ctx, const wsi_wave_desc* w);
 int wsi_wave_relax(wsi_ctx* ctx, double t, double* vel, double* phi);

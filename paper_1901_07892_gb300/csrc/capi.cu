@@ -134,6 +134,12 @@ struct wsi_ctx {
   bool has_waves = false;
   WaveDev wave;
   double time = 0.0;
+  // Dirichlet wave inlet on the x- plane (Sec. 7.1): normal data at t^{n+1}
+  // (nz x ny) and tangential data of u^{n-1}, u^n, u^{n+1} ((nz+1) x ny),
+  // with the combination of a stage velocity (float64 and float32)
+  bool inlet = false;
+  double *in_gn = nullptr, *in_gw_nm1 = nullptr, *in_gw_n = nullptr, *in_gw_np1 = nullptr, *in_gs = nullptr;
+  float* in_gs32 = nullptr;
   // float32 shadows of the explicitly transported fields (mixed path)
   float *vn32 = nullptr, *u1_32 = nullptr, *u2_32 = nullptr, *rn32 = nullptr, *r1_32 = nullptr, *r2_32 = nullptr,
         *R32 = nullptr, *C32 = nullptr, *vh32 = nullptr, *phih32 = nullptr, *mu_cc_n32 = nullptr,
@@ -440,9 +446,11 @@ int fgmres(wsi_ctx* c, const double* b, double* x, double dt, const wsi_solve_op
     launch_lincomb(n, 1.0, b, -1.0, Vj(0), 0.0, nullptr, Vj(0), c->st);
     beta = host_norm2(Vj(0), n, red, c->st);
   }
-  // zero-mean pressure
-  launch_sum<double>(x + c->pk.off[3], c->ncell, hd, red, c->st);
-  launch_add_scalar_from<double>(x + c->pk.off[3], c->ncell, hd, -1.0 / (double)c->ncell, c->st);
+  // zero-mean pressure in a closed box (an open top fixes the pressure)
+  if (!c->g.open_top) {
+    launch_sum<double>(x + c->pk.off[3], c->ncell, hd, red, c->st);
+    launch_add_scalar_from<double>(x + c->pk.off[3], c->ncell, hd, -1.0 / (double)c->ncell, c->st);
+  }
   s->iters = iters;
   s->rel_residual = beta / bnorm;
   int crc = cuda_check(c, "fgmres");
@@ -533,11 +541,25 @@ void cparts(wsi_ctx* c, const T* base, const T* out[3]) {
 // rho_face <- rho^{n+1,k+1} (beta <- 1/rho), C into c->Cc (plain) or
 // c->C32 (mixed).  Stage 1 depends on (u^n, rho^n) only; with reuse_stage1
 // its result from an earlier cycle of the same step is kept.
+// tangential inlet data of a stage velocity a u_k + b u_n + c u_{n-1}: the
+// same combination of the data (u_k's data: at t^{n+1}), into in_gs (and its
+// float32 copy on the mixed path); null without an inlet
+const void* inlet_stage_data(wsi_ctx* c, double a, double b, double cc) {
+  if (!c->inlet) return nullptr;
+  const size_t n = (size_t)(c->g.n[2] + 1) * c->g.n[1];
+  launch_lincomb(n, a, c->in_gw_np1, b, c->in_gw_n, cc, c->in_gw_nm1, c->in_gs, c->st);
+  if (!c->mixed()) return c->in_gs;
+  launch_lincomb_to_f32(n, 1.0, c->in_gs, 0.0, nullptr, 0.0, nullptr, c->in_gs32, c->st);
+  return c->in_gs32;
+}
+
 void transport_stage(wsi_ctx* c, int k, double dt, const double* un, const double* unm1, const double* uk,
                      bool reuse_stage1) {
   const GridDev& g = c->g;
   cudaStream_t st = c->st;
   const size_t nv = c->nvel;
+  // the convective term's velocity is u^(2): its inlet data likewise
+  const void* g2 = k == 0 ? inlet_stage_data(c, 0.0, 1.5, -0.5) : inlet_stage_data(c, 0.375, 0.75, -0.125);
   if (!c->mixed()) {
     if (k == 0) {
       launch_lincomb(nv, 2.0, un, -1.0, unm1, 0.0, nullptr, c->u1, st);
@@ -569,7 +591,7 @@ void transport_stage(wsi_ctx* c, int k, double dt, const double* un, const doubl
     for (int d = 0; d < 3; ++d)
       launch_lincomb(fsize(g, d), 1.0 / 3.0, c->rho_n[d], 2.0 / 3.0, r2[d], -2.0 / 3.0 * dt, R[d], c->rho_face[d],
                      st);
-    launch_transport_flux<double>(g, cu2, cr2, true, Cq, st);
+    launch_transport_flux<double>(g, cu2, cr2, true, Cq, st, (const double*)g2);
   } else {
     float *R[3], *Cq[3], *r1[3], *r2[3], *rn[3];
     parts(c, c->R32, R);
@@ -599,7 +621,7 @@ void transport_stage(wsi_ctx* c, int k, double dt, const double* un, const doubl
     for (int d = 0; d < 3; ++d)
       launch_lincomb_mix(fsize(g, d), 1.0 / 3.0, c->rho_n[d], 2.0 / 3.0, r2[d], -2.0 / 3.0 * dt, R[d],
                          c->rho_face[d], st);
-    launch_transport_flux<float>(g, cu2, cr2, true, Cq, st);
+    launch_transport_flux<float>(g, cu2, cr2, true, Cq, st, (const float*)g2);
   }
   for (int d = 0; d < 3; ++d) recip(c, c->rho_face[d], c->beta[d], fsize(g, d));
 }
@@ -672,10 +694,12 @@ __global__ void k_fill_one(double* a, float* f, size_t n) {
 // flux of the consistent scheme at unit density, from the half-step velocity
 // the level-set stage of this cycle formed (vel_half, or vh32 on the mixed
 // path).  Result in Cc (float64) or C32 (float32).
-int nc_convection(wsi_ctx* c) {
+int nc_convection(wsi_ctx* c, int k) {
   const GridDev& g = c->g;
   cudaStream_t st = c->st;
   const size_t nv = c->nvel;
+  // inlet data of the half-step velocity (u_k + u_n) / 2
+  const void* gh = k == 0 ? inlet_stage_data(c, 0.0, 1.0, 0.0) : inlet_stage_data(c, 0.5, 0.5, 0.0);
   if (!c->ones) {
     c->ones = dalloc(c, nv);
     if (!c->ones) return fail(c, WSI_ERR_OOM, "unit density");
@@ -692,14 +716,14 @@ int nc_convection(wsi_ctx* c) {
     cparts(c, (const float*)c->vh32, vh);
     cparts(c, (const float*)c->ones, one);
     parts(c, c->C32, N);
-    launch_transport_flux<float>(g, vh, one, true, N, st);
+    launch_transport_flux<float>(g, vh, one, true, N, st, (const float*)gh);
   } else {
     const double *vh[3], *one[3];
     double* N[3];
     cparts(c, (const double*)c->vel_half, vh);
     cparts(c, (const double*)c->ones, one);
     parts(c, c->Cc, N);
-    launch_transport_flux<double>(g, vh, one, true, N, st);
+    launch_transport_flux<double>(g, vh, one, true, N, st, (const double*)gh);
   }
   return WSI_OK;
 }
@@ -771,6 +795,8 @@ int wsi_create_grid(const wsi_grid_desc* d, void* stream, wsi_ctx** out) {
   if (d->mg_smoother != WSI_SMOOTH_RBGS && d->mg_smoother != WSI_SMOOTH_CHEBYSHEV) return WSI_ERR_INVALID_ARG;
   if (d->ls_limiter != WSI_LIMIT_CUI && d->ls_limiter != WSI_LIMIT_XSPPM7) return WSI_ERR_INVALID_ARG;
   if ((double)(d->nx + 1) * (d->ny + 1) * (d->nz + 1) >= 2147483648.0) return WSI_ERR_INVALID_ARG;
+  if (d->open_top != 0 && d->open_top != 1) return WSI_ERR_INVALID_ARG;
+  if (d->open_top && (d->bc[5] != WSI_NO_SLIP || d->nz < 2 || d->visc_mg > 0)) return WSI_ERR_INVALID_ARG;
   wsi_ctx* c = new wsi_ctx();
   c->desc = *d;
   c->st = (cudaStream_t)stream;
@@ -781,6 +807,7 @@ int wsi_create_grid(const wsi_grid_desc* d, void* stream, wsi_ctx** out) {
   c->g.h[1] = d->ly / d->ny;
   c->g.h[2] = d->lz / d->nz;
   for (int i = 0; i < 6; ++i) c->g.bc[i] = d->bc[i];
+  c->g.open_top = d->open_top;
   grid_finalize(c->g);
   c->pk = packing(c->g);
   c->nvel = c->pk.off[3];
@@ -1030,6 +1057,7 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
                      st);
   }
   c->mat_n_valid = false;
+  if (c->inlet) launch_inlet_data(g, c->wave, c->time + dt, c->in_gn, c->in_gw_np1, st);
   cudaMemcpyAsync(c->vel_k, c->vel, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(c->phi_k, c->phi, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(c->psi_k, c->psi, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
@@ -1060,7 +1088,7 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
     //    rho^{n+1,k+1} stays in the operator, N from the half-step velocity.
     const bool nonconservative = c->desc.transport_form == WSI_FORM_NONCONSERVATIVE;
     if (nonconservative) {
-      int rn = nc_convection(c);
+      int rn = nc_convection(c, k);
       if (rn) return rn;
       if (k == 0) {
         if (c->mixed()) launch_lincomb_to_f32(nv, 1.0, c->vel, 0.0, nullptr, 0.0, nullptr, c->vn32, st);
@@ -1084,14 +1112,25 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
       launch_rhs_cycle<double>(g, c->b0, c->Cc, rg, c->desc.gravity, c->b, st);
     }
     cudaMemsetAsync(c->b + c->pk.off[3], 0, nc * sizeof(double), st);
+    // the inlet's data at t^{n+1} lifted into b; the solve is for the
+    // velocity with zero x- faces, which then take the data
+    if (c->inlet)
+      launch_inlet_lift(g, c->mu_cc, c->mu_e[0], c->mu_e[1], c->mu_e_n[1], c->in_gn, c->in_gw_np1, c->in_gw_n,
+                        c->desc.theta, c->b, st);
     // 3. Stokes solve from (u^{n+1,k}, p^{n+1/2,k})
     cudaMemcpyAsync(c->x, c->vel_k, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (c->inlet) {
+      double* xq[3];
+      parts(c, c->x, xq);
+      launch_zero_walls(g, xq, st);
+    }
     c->pc_dirty = true;
     wsi_solve_stats ss;
     wsi_solve_opts so = *o;
     so.use_x0 = 1;
     int rc = fgmres(c, c->b, c->x, dt, &so, &ss);
     if (rc != WSI_OK && rc != WSI_ERR_NOT_CONVERGED) return rc;
+    if (c->inlet) launch_inlet_set(g, c->in_gn, c->x + c->pk.off[0], st);
     if (s && k < 4) {
       s->iters[k] = ss.iters;
       s->rel_residual[k] = ss.rel_residual;
@@ -1119,6 +1158,10 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
     if (rr) return rr;
   }
   c->time += dt;
+  if (c->inlet) {  // the tangential data move on with the velocities
+    std::swap(c->in_gw_nm1, c->in_gw_n);
+    std::swap(c->in_gw_n, c->in_gw_np1);
+  }
   // commit the step
   cudaMemcpyAsync(c->vel_old, c->vel, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(c->vel, c->vel_k, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
@@ -1315,9 +1358,11 @@ int wsi_set_waves(wsi_ctx* c, const wsi_wave_desc* w) {
   }
   const double L[3] = {c->desc.lx, c->desc.ly, c->desc.lz};
   if (!(w->H > 0.0) || !(w->T > 0.0) || !(w->depth > 0.0) || w->vertical < 1 || w->vertical > 2 ||
-      !(w->x_gen > 0.0) || !(w->x_damp > w->x_gen) || !(w->x_damp < c->desc.lx) ||
-      !(w->depth < L[w->vertical]))
+      !(w->inlet ? w->x_gen >= 0.0 : w->x_gen > 0.0) || !(w->x_damp > w->x_gen) || !(w->x_damp < c->desc.lx) ||
+      !(w->depth < L[w->vertical]) || (w->inlet != 0 && w->inlet != 1))
     return fail(c, WSI_ERR_INVALID_ARG, "bad wave description");
+  if (w->inlet && (w->vertical != 2 || c->desc.bc[0] != WSI_NO_SLIP))
+    return fail(c, WSI_ERR_INVALID_ARG, "the inlet needs vertical = 2 and a no-slip x- side");
   const double* gv = c->desc.gravity;
   double gmag = sqrt(gv[0] * gv[0] + gv[1] * gv[1] + gv[2] * gv[2]);
   if (!(gmag > 0.0)) return fail(c, WSI_ERR_INVALID_ARG, "waves need gravity");
@@ -1325,7 +1370,26 @@ int wsi_set_waves(wsi_ctx* c, const wsi_wave_desc* w) {
   c->wave = wave_setup(w->H, w->T, w->depth, w->x_gen, w->x_damp, c->desc.lx, w->vertical, pc.eps, gmag);
   c->has_waves = true;
   c->time = w->t0;
-  return WSI_OK;
+  c->inlet = w->inlet != 0;
+  if (c->inlet) {
+    const size_t ne = (size_t)(c->g.n[2] + 1) * c->g.n[1];
+    if (!c->in_gn) {
+      c->in_gn = dalloc(c, (size_t)c->g.n[2] * c->g.n[1]);
+      c->in_gw_nm1 = dalloc(c, ne);
+      c->in_gw_n = dalloc(c, ne);
+      c->in_gw_np1 = dalloc(c, ne);
+      c->in_gs = dalloc(c, ne);
+      c->in_gs32 = (float*)dalloc(c, (ne + 1) / 2);
+      if (!c->in_gn || !c->in_gw_nm1 || !c->in_gw_n || !c->in_gw_np1 || !c->in_gs || !c->in_gs32)
+        return fail(c, WSI_ERR_OOM, "inlet data");
+    }
+    // the state's x- faces take the data at t0, for u^n and u^{n-1} alike
+    launch_inlet_data(c->g, c->wave, c->time, c->in_gn, c->in_gw_n, c->st);
+    cudaMemcpyAsync(c->in_gw_nm1, c->in_gw_n, ne * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+    launch_inlet_set(c->g, c->in_gn, c->vel, c->st);
+    launch_inlet_set(c->g, c->in_gn, c->vel_old, c->st);
+  }
+  return cuda_check(c, "set_waves");
 }
 
 int wsi_wave_relax(wsi_ctx* c, double t, double* vel, double* phi) {
@@ -1760,10 +1824,15 @@ int wsi_pressure_solve(wsi_ctx* c, const double* y, double* x, double rtol, int 
   double* yv = c->b + c->pk.off[3];
   double* xv = c->x + c->pk.off[3];
   double* r = c->V;  // scratch
+  // constants are in the null space of a closed box's pressure operator
+  auto demean = [&](double* a) {
+    if (g.open_top) return;
+    launch_sum<double>(a, n, c->hdev, c->red, st);
+    launch_add_scalar_from<double>(a, n, c->hdev, -1.0 / (double)n, st);
+  };
   rc = copy_in(c, yv, y, n);
   if (rc) return rc;
-  launch_sum<double>(yv, n, c->hdev, c->red, st);
-  launch_add_scalar_from<double>(yv, n, c->hdev, -1.0 / (double)n, st);
+  demean(yv);
   cudaMemsetAsync(xv, 0, n * sizeof(double), st);
   const double ynorm = host_norm2(yv, n, c->red, st);
   const double* bt[3] = {c->beta[0], c->beta[1], c->beta[2]};
@@ -1775,8 +1844,7 @@ int wsi_pressure_solve(wsi_ctx* c, const double* y, double* x, double rtol, int 
     launch_lincomb_to_f32(n, 1.0 / ynorm, yv, 0.0, nullptr, 0.0, nullptr, L0.b, st);
     learned_guess(c->P32, L0.b, st);
     launch_lincomb_mix(n, 0.0, xv, ynorm, L0.x, 0.0, L0.x, xv, st);
-    launch_sum<double>(xv, n, c->hdev, c->red, st);
-    launch_add_scalar_from<double>(xv, n, c->hdev, -1.0 / (double)n, st);
+    demean(xv);
     launch_pressure<double>(g, bt, xv, r, st);
     launch_lincomb(n, 1.0, yv, -1.0, r, 0.0, nullptr, r, st);
     const double r0 = host_norm2(r, n, c->red, st);
@@ -1795,8 +1863,7 @@ int wsi_pressure_solve(wsi_ctx* c, const double* y, double* x, double rtol, int 
   while (true) {
     launch_pressure<double>(g, bt, xv, r, st);
     launch_lincomb(n, 1.0, yv, -1.0, r, 0.0, nullptr, r, st);
-    launch_sum<double>(r, n, c->hdev, c->red, st);
-    launch_add_scalar_from<double>(r, n, c->hdev, -1.0 / (double)n, st);
+    demean(r);
     rn = host_norm2(r, n, c->red, st);
     if (!std::isfinite(rn) && !last_learned) return fail(c, WSI_ERR_NAN, "non-finite pressure residual");
     if (last_learned && !(rn <= rho_plain * prev)) {
@@ -1828,8 +1895,7 @@ int wsi_pressure_solve(wsi_ctx* c, const double* y, double* x, double rtol, int 
     ++cycles;
   }
   c->P32.learn.on = c->unet_on;
-  launch_sum<double>(xv, n, c->hdev, c->red, st);
-  launch_add_scalar_from<double>(xv, n, c->hdev, -1.0 / (double)n, st);
+  demean(xv);
   rc = copy_out(c, x, xv, n);
   if (rc) return rc;
   rc = cuda_check(c, "pressure_solve");

@@ -5,6 +5,10 @@
 // on c-faces with extents n + e_c; edges in the (c,d) plane have extents
 // n + e_c + e_d.  Tangential ghosts across a wall are s * (adjacent value),
 // s = -1 no-slip, +1 free-slip; faces on walls hold the zero normal velocity.
+// Open top (Sec. 7.1: zero tangential velocity and zero pressure on the top
+// plane): the z-faces of the top plane are unknowns, the pressure ghost above
+// it is -p of the cell below, the ghost of w above it mirrors w evenly
+// (dw/dz = 0) and tangential ghosts take s = -1.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -44,6 +48,7 @@ struct GridDev {
   double ih[3];   // 1/h (set by grid_finalize)
   double ih2[3];  // 1/h^2
   double bc[6];   // tangential ghost sign per wall (x-, x+, y-, y+, z-, z+)
+  int open_top;   // 1: the z+ side is open (zero tangential velocity, zero pressure)
   // float32 copies for float32 kernels (a float64->float32 conversion issues
   // on the narrow float64 pipe, so kernels never convert these per thread)
   float ihf[3], ih2f[3], bcf[6];
@@ -79,6 +84,11 @@ inline void grid_finalize(GridDev& g) {
 
 __host__ __device__ __forceinline__ int ext(const GridDev& g, int c, int a) {
   return g.n[a] + (a == c ? 1 : 0);
+}
+// a C-face with index a along C is an unknown (a row of the momentum
+// equation): not on a wall; with an open top the top z-faces are rows
+__host__ __device__ __forceinline__ bool face_row(const GridDev& g, int C, int a) {
+  return a > 0 && (a < g.n[C] || (C == 2 && g.open_top));
 }
 // c = 0,1,2 velocity components; c = 3 cell-centred
 __host__ __device__ __forceinline__ size_t fsize(const GridDev& g, int c) {

@@ -31,7 +31,10 @@
 // outside an array read as zero and are never used unghosted.
 //
 // Tangential ghosts across walls follow the wall's sign; faces on walls hold
-// zero and their rows are written as zero.  Magnitudes below 2^-126 ~ 1.2e-38
+// zero and their rows are written as zero.  With an open top the top w-row is
+// formed too: the ghost cell above takes minus the normal stress below, the
+// pressure ghost is -p, the top edges' shear stresses come from the z-edge
+// pass of the last level.  Magnitudes below 2^-126 ~ 1.2e-38
 // are flushed to zero, and below 2^-103 only their leading 24 bits are kept.
 // Array offsets are 32-bit: every array holds fewer than 2^31 elements
 // (checked when the grid is created).
@@ -64,6 +67,7 @@ struct HtConst {
   unsigned pw;    // power-of-two flags: bits 0-2 ih, 3-5 two_ih2, 6 mtheta
   float bcs[6];   // tangential ghost sign per wall (x-, x+, y-, y+, z-, z+)
   int n[3];
+  int open_top;
 };
 
 struct DfMaps {
@@ -306,11 +310,23 @@ __global__ void __launch_bounds__(32 * FBY) k_stokes_df(const __grid_constant__ 
         out = row_out(K, rq, gp, L);
       }
       yw[cb] = out;
-      if (k == nz - 1) yw[cb + sc2] = 0.0;
+      if (k == nz - 1 && !K.open_top) yw[cb + sc2] = 0.0;
       // continuity row at the cell
       const ht dq = ht_add(ht_add(ht_k(ht_sub(u_ip, u_k), ihx, pxk), ht_k(ht_sub(vj_k, v_k), ihy, pyk)),
                            ht_k(ht_sub(w_kp, w_k), ihz, pzk));
       yp[cb] = -ht_dbl(dq);
+    }
+    if (k == nz - 1 && K.open_top) {
+      // w-row at the open top's face nz (warp-uniform branch: all lanes shuffle)
+      const ht txz_kp_ip = shfl_down1(txz_kp);
+      if (jrow && lane_rows && cI) {
+        const ht L = ht_add(ht_add(ht_k(ht_sub(ht_sgn(nzz, -1.f), nzz), K.two_ih2[2], (K.pw >> 5) & 1),
+                                   ht_k(ht_sub(txz_kp_ip, txz_kp), ihx, pxk)),
+                            ht_k(ht_sub(tyzj_kp, tyz_kp), ihy, pyk));
+        const ht rq = ht_mul(at(tile(tp, DF_RHO_Z), j, ic), w_kp);
+        const ht gp = ht_k(ht_sub(ht_sgn(p_k, -1.f), p_k), ihz, pzk);
+        yw[ic + j * sc1 + nz * sc2] = row_out(K, rq, gp, L);
+      }
     }
     // ---- carry to level k + 1
     u_k = u_kp;
@@ -356,13 +372,22 @@ __global__ void __launch_bounds__(256) k_df_split_pad(PadSplit s) {
   for (int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < nr; r += wstride) {
     const double* __restrict__ xr = s.x[a] + (size_t)r * cols;
     float2* orow = s.out[a] + (size_t)r * pitch;
-    for (int c = lane; c < pitch; c += 32) {
-      float2 v = make_float2(0.f, 0.f);
-      if (c < cols) {
-        const dfl d = df_split(sc == 1.0 ? xr[c] : sc * xr[c]);
-        v = make_float2(d.h, d.l);
+    // four loads in flight per lane before the splits and stores
+    for (int c0 = lane; c0 < pitch; c0 += 128) {
+      double v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + 32 * u;
+        v[u] = c < cols ? __ldg(xr + c) : 0.0;
       }
-      orow[c] = v;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + 32 * u;
+        if (c < pitch) {
+          const dfl d = df_split(sc == 1.0 ? v[u] : sc * v[u]);
+          orow[c] = make_float2(d.h, d.l);
+        }
+      }
     }
   }
 }
@@ -486,6 +511,7 @@ void launch_stokes_df(const GridDev& g, const DfOperands& o, double theta, const
   k.mtheta = ht{mt.h, mt.l};
   if (host_pow2(mt)) k.pw |= 1u << 6;
   for (int w = 0; w < 6; ++w) k.bcs[w] = (float)g.bc[w];
+  k.open_top = g.open_top;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_stokes_df, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);

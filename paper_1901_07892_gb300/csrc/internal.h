@@ -93,10 +93,11 @@ void launch_viscous_rbgs(const GridDev& g, const Coef<T>& cf, T inv_dt, T theta,
                          int color, cudaStream_t st);
 
 // transport.cu (Sec. 4.2.2): R or C on all three face arrays, storage and
-// arithmetic in T
+// arithmetic in T; inlet_w: the tangential data of vel's w on a Dirichlet
+// inlet's x- plane ((nz+1) x ny, used for C), or null
 template <typename T>
 void launch_transport_flux(const GridDev& g, const T* const vel[3], const T* const rho[3], bool with_velocity,
-                           T* const out[3], cudaStream_t st);
+                           T* const out[3], cudaStream_t st, const T* inlet_w = nullptr);
 // out = a*x + b*y + c*z elementwise over n (any of y, z may be null)
 void launch_lincomb(size_t n, double a, const double* x, double b, const double* y, double c, const double* z,
                     double* out, cudaStream_t st);
@@ -282,6 +283,15 @@ struct WaveDev {
 };
 WaveDev wave_setup(double H, double T, double d, double x_gen, double x_damp, double lx, int vert, double eps,
                    double grav);
+// Dirichlet inlet on the x- plane (waves.cu): data at time t (gn: nz x ny
+// normal velocities, gw: (nz+1) x ny tangential velocities of the x- edges),
+// their lifting into the right-hand side b of the implicit solve (with the
+// explicit viscous term's tangential data gw_n), and u's x- faces <- gn
+void launch_inlet_data(const GridDev& g, const WaveDev& w, double t, double* gn, double* gw, cudaStream_t st);
+void launch_inlet_lift(const GridDev& g, const double* mu_cc, const double* mu_xy, const double* mu_xz,
+                       const double* mu_xz_n, const double* gn, const double* gw, const double* gw_n, double theta,
+                       double* b, cudaStream_t st);
+void launch_inlet_set(const GridDev& g, const double* gn, double* u, cudaStream_t st);
 void launch_wave_relax(const GridDev& g, const WaveDev& w, double t, double* const vel[3], double* phi,
                        cudaStream_t st);
 

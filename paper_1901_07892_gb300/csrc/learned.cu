@@ -37,7 +37,7 @@ __global__ void k_avg_down(GridDev gf, GridDev gc, int r0, int r1, int r2, const
   c[fidx(gc, 3, I, J, K)] = s / (float)(r0 * r1 * r2);
 }
 
-// d = sum over interior faces of beta/h^2
+// d = sum over interior faces of beta/h^2 (the diagonal of the level operator)
 __global__ void k_diag(GridDev g, const float* __restrict__ bx, const float* __restrict__ by,
                        const float* __restrict__ bz, float* d) {
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
@@ -48,6 +48,7 @@ __global__ void k_diag(GridDev g, const float* __restrict__ bx, const float* __r
   if (j + 1 < g.n[1]) s += by[fidx(g, 1, i, j + 1, k)] * g.ih2f[1];
   if (j > 0) s += by[fidx(g, 1, i, j, k)] * g.ih2f[1];
   if (k + 1 < g.n[2]) s += bz[fidx(g, 2, i, j, k + 1)] * g.ih2f[2];
+  else if (g.open_top) s += 2.f * bz[fidx(g, 2, i, j, k + 1)] * g.ih2f[2];  // ghost -p above the open top
   if (k > 0) s += bz[fidx(g, 2, i, j, k)] * g.ih2f[2];
   d[fidx(g, 3, i, j, k)] = s > 0.f ? s : 1.f;
 }

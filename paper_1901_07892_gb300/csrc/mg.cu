@@ -411,10 +411,14 @@ int precond_setup(Precond<T>& P, const GridDev& g, const Coef<double>& fine, cud
             M[(size_t)row * n + col] -= b;
             M[(size_t)row * n + row] += b;
           }
+          if (a == 2 && k + 1 == gc.n[2] && gc.open_top)  // p = 0 on the open top: ghost -p
+            M[(size_t)row * n + row] += 2.0 * (double)hb[2][fidx(gc, 2, i, j, k + 1)] * ih2;
         }
         dmax = std::max(dmax, M[(size_t)row * n + row]);
       }
-  double creg = dmax / n;
+  // a closed box leaves constants in the null space: M = -L + c 1 1^T is SPD
+  // and its inverse gives the mean-free solution; with an open top -L is SPD
+  const double creg = gc.open_top ? 0.0 : dmax / n;
   for (size_t t = 0; t < M.size(); ++t) M[t] += creg;
   spd_inverse(M, n);
   cudaMemcpyAsync(P.coarse_inv, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice, st);
@@ -446,6 +450,7 @@ __global__ void k_rbgs_p(GridDev g, const T* __restrict__ bx, const T* __restric
   if (j > 0) { T c = by[fidx(g, 1, i, j, k)] * ihy2; s += c * x[id - g.n[0]]; d += c; }
   size_t pl = (size_t)g.n[0] * g.n[1];
   if (k + 1 < g.n[2]) { T c = bz[fidx(g, 2, i, j, k + 1)] * ihz2; s += c * x[id + pl]; d += c; }
+  else if (g.open_top) d += T(2) * bz[fidx(g, 2, i, j, k + 1)] * ihz2;  // ghost -x above the open top
   if (k > 0) { T c = bz[fidx(g, 2, i, j, k)] * ihz2; s += c * x[id - pl]; d += c; }
   if (d > T(0)) x[id] = (s - b[id]) / d;
 }
@@ -463,6 +468,7 @@ __device__ __forceinline__ T lap_at(const GridDev& g, const T* __restrict__ bx, 
   if (j > 0) s -= by[fidx(g, 1, i, j, k)] * (xc - x[id - g.n[0]]) * ihy2;
   size_t pl = (size_t)g.n[0] * g.n[1];
   if (k + 1 < g.n[2]) s += bz[fidx(g, 2, i, j, k + 1)] * (x[id + pl] - xc) * ihz2;
+  else if (g.open_top) s -= T(2) * bz[fidx(g, 2, i, j, k + 1)] * xc * ihz2;
   if (k > 0) s -= bz[fidx(g, 2, i, j, k)] * (xc - x[id - pl]) * ihz2;
   return s;
 }
@@ -560,6 +566,7 @@ __global__ void k_cheb_p(GridDev g, const T* __restrict__ bx, const T* __restric
   if (j + 1 < g.n[1]) { T w = by[fidx(g, 1, i, j + 1, k)] * ihy2; s += w * (xv(id + g.n[0]) - xc); dg += w; }
   if (j > 0) { T w = by[fidx(g, 1, i, j, k)] * ihy2; s += w * (xv(id - g.n[0]) - xc); dg += w; }
   if (k + 1 < g.n[2]) { T w = bz[fidx(g, 2, i, j, k + 1)] * ihz2; s += w * (xv(id + pl) - xc); dg += w; }
+  else if (g.open_top) { T w = T(2) * bz[fidx(g, 2, i, j, k + 1)] * ihz2; s -= w * xc; dg += w; }
   if (k > 0) { T w = bz[fidx(g, 2, i, j, k)] * ihz2; s += w * (xv(id - pl) - xc); dg += w; }
   const T r = s - b[id];
   xo[id] = xc;
@@ -756,13 +763,15 @@ __global__ void k_vel_update(GridDev g, const T* __restrict__ ut, const T* __res
   if (i >= ext(g, C, 0) || j >= ext(g, C, 1)) return;
   int id3[3] = {i, j, k};
   size_t id = fidx(g, C, i, j, k);
-  if (id3[C] == 0 || id3[C] == g.n[C]) {
+  if (!face_row(g, C, id3[C])) {
     z[id] = 0.0;
     return;
   }
   int lo[3] = {i, j, k};
   lo[C] -= 1;
-  T gphi = (phi[fidx(g, 3, i, j, k)] - phi[fidx(g, 3, lo[0], lo[1], lo[2])]) * ginv<T>(g, C);
+  const T plo = phi[fidx(g, 3, lo[0], lo[1], lo[2])];
+  const T phi_hi = (C == 2 && k == g.n[2]) ? -plo : phi[fidx(g, 3, i, j, k)];  // open top: ghost -phi
+  T gphi = (phi_hi - plo) * ginv<T>(g, C);
   z[id] = cvt<double, T>(ut[id] - beta[id] * gphi);
 }
 
@@ -875,11 +884,12 @@ void precond_apply(Precond<T>& P, const GridDev& g, const Opts& o, double dt, co
     for (int s = 0; s < o.visc_sweeps; ++s)
       for (int c = 0; c < 2; ++c) launch_viscous_rbgs<T>(g, cf, inv_dt, theta, P.ut, P.ru, c, st);
   }
-  // y = r_p + D u~, mean-free
+  // y = r_p + D u~, mean-free in a closed box (the pressure problem's
+  // compatibility condition; an open top fixes the pressure instead)
   dim3 gr = grid3(g.n[0], g.n[1], g.n[2]);
   { k_div_add<T><<<gr, dim3(BX, BY), 0, st>>>(g, P.ut[0], P.ut[1], P.ut[2], P.rp, P.y); WSI_COUNT(); }
   size_t ncell = fsize(g, 3);
-  sub_mean<T>(P.y, ncell, P.dsum, P.dscratch, st);
+  if (!g.open_top) sub_mean<T>(P.y, ncell, P.dsum, P.dscratch, st);
   // phi = L^{-1} y
   MGLevel<T>& L0 = P.lev[0];
   cudaMemcpyAsync(L0.b, P.y, ncell * sizeof(T), cudaMemcpyDeviceToDevice, st);
@@ -894,7 +904,7 @@ void precond_apply(Precond<T>& P, const GridDev& g, const Opts& o, double dt, co
                                                                                  z + pk.off[2]); WSI_COUNT(); }
   int blocks = (int)std::min<size_t>((ncell + 255) / 256, 152 * 16);
   { k_p_update<T><<<std::max(blocks, 1), 256, 0, st>>>(ncell, L0.x, P.mu_cc, P.y, 1.0 / dt, o.theta, z + pk.off[3]); WSI_COUNT(); }
-  sub_mean<double>(z + pk.off[3], ncell, P.dsum, P.dscratch, st);
+  if (!g.open_top) sub_mean<double>(z + pk.off[3], ncell, P.dsum, P.dscratch, st);
 }
 
 template int precond_alloc<double>(Precond<double>&, const GridDev&, std::string&);

@@ -223,15 +223,19 @@ __device__ __forceinline__ T strain_at(const GridDev& g, const Coef<T>& cf, cons
   const T ihC = ginv<T>(g, C);
   int id3[3] = {i, j, k};
   T q0 = qc[fidx(g, C, i, j, k)];
+  // the top row of an open top: the cell above is a ghost whose normal stress
+  // is minus the one below (w mirrors evenly) and whose tangential
+  // velocities are -1 times those below
+  const bool top = C == 2 && k == g.n[2];
   // normal stress: cells hi = face index along C, lo = index - 1
   int lo3[3] = {i, j, k};
   lo3[C] -= 1;
   int hi3[3] = {i, j, k};
   hi3[C] += 1;
-  T mu_hi = cf.mu_cc[fidx(g, 3, i, j, k)];
   T mu_lo = cf.mu_cc[fidx(g, 3, lo3[0], lo3[1], lo3[2])];
-  T qp = qc[fidx(g, C, hi3[0], hi3[1], hi3[2])];
   T qm = qc[fidx(g, C, lo3[0], lo3[1], lo3[2])];
+  T mu_hi = top ? mu_lo : cf.mu_cc[fidx(g, 3, i, j, k)];
+  T qp = top ? qm : qc[fidx(g, C, hi3[0], hi3[1], hi3[2])];
   T L = T(2) * ihC * ihC * (mu_hi * (qp - q0) - mu_lo * (q0 - qm));
   T dg = -T(2) * ihC * ihC * (mu_hi + mu_lo);
 #pragma unroll
@@ -268,11 +272,15 @@ __device__ __forceinline__ T strain_at(const GridDev& g, const Coef<T>& cf, cons
     d1[D] += 1;
     int d0[3] = {d1[0], d1[1], d1[2]};
     d0[C] -= 1;
-    T dqd_hi = (qd[fidx(g, D, d1[0], d1[1], d1[2])] - qd[fidx(g, D, d0[0], d0[1], d0[2])]) * ihC;
+    const T qd_d0 = qd[fidx(g, D, d0[0], d0[1], d0[2])];
+    const T qd_d1 = top ? gbc<T>(g, 5) * qd_d0 : qd[fidx(g, D, d1[0], d1[1], d1[2])];
+    T dqd_hi = (qd_d1 - qd_d0) * ihC;
     int c1[3] = {id3[0], id3[1], id3[2]};  // lo edge
     int c0[3] = {id3[0], id3[1], id3[2]};
     c0[C] -= 1;
-    T dqd_lo = (qd[fidx(g, D, c1[0], c1[1], c1[2])] - qd[fidx(g, D, c0[0], c0[1], c0[2])]) * ihC;
+    const T qd_c0 = qd[fidx(g, D, c0[0], c0[1], c0[2])];
+    const T qd_c1 = top ? gbc<T>(g, 5) * qd_c0 : qd[fidx(g, D, c1[0], c1[1], c1[2])];
+    T dqd_lo = (qd_c1 - qd_c0) * ihC;
     T f_hi = mue_hi * ((q_hi - q0) * ihD + dqd_hi);
     T f_lo = mue_lo * ((q0 - q_lo) * ihD + dqd_lo);
     L += (f_hi - f_lo) * ihD;
@@ -289,7 +297,7 @@ __global__ void k_viscous(GridDev g, Coef<T> cf, T inv_dt, T theta, CVel<T> q, T
   if (i >= e0 || j >= e1) return;
   int id3[3] = {i, j, k};
   size_t id = fidx(g, C, i, j, k);
-  if (id3[C] == 0 || id3[C] == g.n[C]) {
+  if (!face_row(g, C, id3[C])) {
     out[id] = T(0);
     return;
   }
@@ -337,7 +345,7 @@ __global__ void k_viscous_rbgs(GridDev g, Coef<T> cf, T inv_dt, T theta, Vel<T> 
   int e0 = ext(g, C, 0), e1 = ext(g, C, 1);
   if (i >= e0 || j >= e1) return;
   int id3[3] = {i, j, k};
-  if (id3[C] == 0 || id3[C] == g.n[C]) return;
+  if (!face_row(g, C, id3[C])) return;
   size_t id = fidx(g, C, i, j, k);
   T dg;
   const T* cq[3] = {q.q[0], q.q[1], q.q[2]};
@@ -379,6 +387,7 @@ __global__ void k_pressure(GridDev g, const T* __restrict__ bx, const T* __restr
   if (j > 0) s -= by[fidx(g, 1, i, j, k)] * (pc - p[id - g.n[0]]) * ihy2;
   size_t pl = (size_t)g.n[0] * g.n[1];
   if (k + 1 < g.n[2]) s += bz[fidx(g, 2, i, j, k + 1)] * (p[id + pl] - pc) * ihz2;
+  else if (g.open_top) s -= T(2) * bz[fidx(g, 2, i, j, k + 1)] * pc * ihz2;  // ghost -p above the open top
   if (k > 0) s -= bz[fidx(g, 2, i, j, k)] * (pc - p[id - pl]) * ihz2;
   out[id] = s;
 }
@@ -394,13 +403,15 @@ __global__ void k_grad(GridDev g, const T* __restrict__ p, T* out) {
   if (i >= ext(g, C, 0) || j >= ext(g, C, 1)) return;
   int id3[3] = {i, j, k};
   size_t id = fidx(g, C, i, j, k);
-  if (id3[C] == 0 || id3[C] == g.n[C]) {
+  if (!face_row(g, C, id3[C])) {
     out[id] = T(0);
     return;
   }
   int lo3[3] = {i, j, k};
   lo3[C] -= 1;
-  out[id] = (p[fidx(g, 3, i, j, k)] - p[fidx(g, 3, lo3[0], lo3[1], lo3[2])]) * ginv<T>(g, C);
+  const T plo = p[fidx(g, 3, lo3[0], lo3[1], lo3[2])];
+  const T phi = (C == 2 && k == g.n[2]) ? -plo : p[fidx(g, 3, i, j, k)];  // open top: ghost -p
+  out[id] = (phi - plo) * ginv<T>(g, C);
 }
 
 template <typename T>
@@ -433,14 +444,16 @@ __device__ __forceinline__ void stokes_row(const GridDev& g, const Coef<double>&
                                            int j, int k) {
   int id3[3] = {i, j, k};
   size_t id = fidx(g, C, i, j, k);
-  if (id3[C] == 0 || id3[C] == g.n[C]) {
+  if (!face_row(g, C, id3[C])) {
     out[id] = 0.0;
     return;
   }
   double L = strain_at<C, double>(g, cf, q.q, i, j, k, nullptr);
   int lo3[3] = {i, j, k};
   lo3[C] -= 1;
-  double gp = (p[fidx(g, 3, i, j, k)] - p[fidx(g, 3, lo3[0], lo3[1], lo3[2])]) * g.ih[C];
+  const double plo = p[fidx(g, 3, lo3[0], lo3[1], lo3[2])];
+  const double phi = (C == 2 && k == g.n[2]) ? -plo : p[fidx(g, 3, i, j, k)];  // open top: ghost -p
+  double gp = (phi - plo) * g.ih[C];
   out[id] = cf.rho_face[C][id] * inv_dt * q.q[C][id] - theta * L + gp;
 }
 
@@ -487,6 +500,7 @@ __global__ void k_zero_walls(GridDev g, double* q) {
   constexpr int A = (C == 0) ? 1 : 0;
   constexpr int B = (C == 2) ? 1 : 2;
   if (a >= g.n[A] || b >= g.n[B]) return;
+  if (C == 2 && side && g.open_top) return;  // the open top's faces are unknowns
   int c3[3];
   c3[C] = side ? g.n[C] : 0;
   c3[A] = a;
@@ -508,7 +522,7 @@ __global__ void k_rhs_base(GridDev g, Coef<T> cf_n, CVel<T> uT, const double* __
   if (i >= ext(g, C, 0) || j >= ext(g, C, 1)) return;
   int id3[3] = {i, j, k};
   size_t id = fidx(g, C, i, j, k);
-  if (id3[C] == 0 || id3[C] == g.n[C]) {
+  if (!face_row(g, C, id3[C])) {
     b0[id] = 0.0;
     return;
   }

@@ -49,7 +49,8 @@ __device__ __forceinline__ T cui(T qU, T qC, T qD) {
 // Entry m of the C-face array along axis D extended by two ghost layers: the
 // stored index it maps to and the velocity ghost sign.  Density ghosts are
 // even mirrors; velocity ghosts are odd about wall faces when C == D (the wall
-// face itself is zero) and take the wall's tangential sign across D != C.
+// face itself is zero; even about an open top, where dw/dz = 0) and take the
+// wall's tangential sign across D != C.
 template <int C, int D, typename T>
 __device__ __forceinline__ int mirror_index(const GridDev& g, int m, T& s) {
   const int n = g.n[D] + (C == D ? 1 : 0);
@@ -68,7 +69,7 @@ __device__ __forceinline__ int mirror_index(const GridDev& g, int m, T& s) {
     const int gl = m - (n - 1);
     if (C == D) {
       mm = (n - 1) - gl;
-      s = T(-1);
+      s = (D == 2 && g.open_top) ? T(1) : T(-1);
     } else {
       mm = n - gl;
       s = gbc<T>(g, 2 * D + 1);
@@ -107,9 +108,12 @@ __device__ __forceinline__ T adv_at(const GridDev& g, const CVel<T>& vel, int i,
 // limiter taps of every x- and y-flux then come from shared memory.  Along z
 // each thread keeps its column's last four entries in registers.  Advective
 // velocities are read from global memory (two values per flux, coalesced).
+// inl (C == 2 with the velocity only, else null): tangential data of w on
+// the x- plane of a Dirichlet inlet, (nz+1) x ny; the ghosts of w across it
+// are then 2 inl - (mirror image)
 template <int C, bool WITHV, typename T>
 __global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, CVel<T> vel, const T* __restrict__ rho, T* out,
-                                                      int zchunk) {
+                                                      int zchunk, const T* __restrict__ inl) {
   constexpr int HX = BX + 4, HY = BY + 4, NS = (HX * HY + BX * BY - 1) / (BX * BY);
   __shared__ T sR[HY][HX];
   __shared__ T sQ[WITHV ? HY : 1][WITHV ? HX : 1];
@@ -128,11 +132,14 @@ __global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, CVel<T> vel, co
   // staged entries of this thread: in-plane offset (mirrored) and velocity sign
   int soff[NS];
   T ssg[NS];
+  constexpr bool INL = C == 2 && WITHV;
+  int sinl[INL ? NS : 1];  // inlet data row of an x-ghost entry, else -1
 #pragma unroll
   for (int r = 0; r < NS; ++r) {
     const int t = tid + r * BX * BY;
     soff[r] = -1;
     ssg[r] = T(1);
+    if (INL) sinl[r] = -1;
     if (t < HX * HY) {
       const int hy = t / HX, hx = t - hy * HX;
       T sx, sy;
@@ -140,6 +147,7 @@ __global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, CVel<T> vel, co
       const int my = mirror_index<C, 1, T>(g, y0 - 2 + hy, sy);
       soff[r] = my * e0 + mx;
       ssg[r] = sx * sy;
+      if (INL && inl && x0 - 2 + hx < 0) sinl[r] = my;
     }
   }
   // z window: entries k-1 .. k+2 of this column (density, velocity)
@@ -178,7 +186,11 @@ __global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, CVel<T> vel, co
         const int hy = t / HX, hx = t - hy * HX;
         const size_t a = (size_t)k * plane + soff[r];
         sR[hy][hx] = rho[a];
-        if (WITHV) sQ[hy][hx] = ssg[r] * qc[a];
+        if (WITHV) {
+          T qv = ssg[r] * qc[a];
+          if (INL && sinl[r] >= 0) qv += T(2) * inl[(size_t)k * e1 + sinl[r]];
+          sQ[hy][hx] = qv;
+        }
       }
     }
     __syncthreads();
@@ -256,34 +268,34 @@ int transport_chunk(int ex, int ey, int ez) {
 
 template <bool WITHV, typename T>
 static void transport_all(const GridDev& g, const CVel<T>& v, const T* const rho[3], T* const out[3],
-                          cudaStream_t st) {
+                          const T* inlet_w, cudaStream_t st) {
   const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
   int zc = transport_chunk(n0 + 1, n1, n2);
   { k_transport<0, WITHV, T><<<dim3(cdiv(n0 + 1, BX), cdiv(n1, BY), cdiv(n2, zc)), dim3(BX, BY), 0, st>>>(
-      g, v, rho[0], out[0], zc); WSI_COUNT(); }
+      g, v, rho[0], out[0], zc, nullptr); WSI_COUNT(); }
   zc = transport_chunk(n0, n1 + 1, n2);
   { k_transport<1, WITHV, T><<<dim3(cdiv(n0, BX), cdiv(n1 + 1, BY), cdiv(n2, zc)), dim3(BX, BY), 0, st>>>(
-      g, v, rho[1], out[1], zc); WSI_COUNT(); }
+      g, v, rho[1], out[1], zc, nullptr); WSI_COUNT(); }
   zc = transport_chunk(n0, n1, n2 + 1);
   { k_transport<2, WITHV, T><<<dim3(cdiv(n0, BX), cdiv(n1, BY), cdiv(n2 + 1, zc)), dim3(BX, BY), 0, st>>>(
-      g, v, rho[2], out[2], zc); WSI_COUNT(); }
+      g, v, rho[2], out[2], zc, WITHV ? inlet_w : nullptr); WSI_COUNT(); }
 }
 
 template <typename T>
 void launch_transport_flux(const GridDev& g, const T* const vel[3], const T* const rho[3], bool with_velocity,
-                           T* const out[3], cudaStream_t st) {
+                           T* const out[3], cudaStream_t st, const T* inlet_w) {
   CVel<T> v{{vel[0], vel[1], vel[2]}};
   ktimer_begin(KC_TRANSPORT, st);
   if (with_velocity)
-    transport_all<true, T>(g, v, rho, out, st);
+    transport_all<true, T>(g, v, rho, out, inlet_w, st);
   else
-    transport_all<false, T>(g, v, rho, out, st);
+    transport_all<false, T>(g, v, rho, out, nullptr, st);
   ktimer_end(KC_TRANSPORT, st);
 }
 template void launch_transport_flux<double>(const GridDev&, const double* const[3], const double* const[3], bool,
-                                            double* const[3], cudaStream_t);
+                                            double* const[3], cudaStream_t, const double*);
 template void launch_transport_flux<float>(const GridDev&, const float* const[3], const float* const[3], bool,
-                                           float* const[3], cudaStream_t);
+                                           float* const[3], cudaStream_t, const float*);
 
 template <typename Ti, typename To>
 __global__ void k_lincomb(size_t n, double a, const Ti* __restrict__ x, double b, const Ti* __restrict__ y, double c,

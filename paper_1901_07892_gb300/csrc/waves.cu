@@ -37,7 +37,8 @@ __device__ __forceinline__ double wv_heaviside(double phi, double eps) {
   return 0.5 * (1.0 + phi / eps + sin(M_PI * phi / eps) / M_PI);
 }
 
-// zone weight at x; returns false outside both zones
+// zone weight at x; returns false outside both zones (x_gen = 0: no
+// generation zone, as with a Dirichlet inlet)
 __device__ __forceinline__ bool wv_zone(const WaveDev& w, double x, double& a, bool& gen) {
   gen = x < w.x_gen;
   bool dmp = x > w.x_damp;
@@ -51,7 +52,7 @@ __global__ void k_relax_faces(GridDev g, WaveDev w, double t, double* q) {
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
   if (i >= ext(g, C, 0) || j >= ext(g, C, 1)) return;
   int id3[3] = {i, j, k};
-  if (id3[C] == 0 || id3[C] == g.n[C]) return;  // wall faces keep their zero
+  if (!face_row(g, C, id3[C])) return;  // faces on walls and the inlet keep their values
   double pos[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) pos[a] = (a == C ? (double)id3[a] : id3[a] + 0.5) * g.h[a];
@@ -89,6 +90,90 @@ void launch_wave_relax(const GridDev& g, const WaveDev& w, double t, double* con
   { k_relax_faces<1><<<dim3(cdiv(g.n[0], BX), cdiv(g.n[1] + 1, BY), g.n[2]), dim3(BX, BY), 0, st>>>(g, w, t, vel[1]); WSI_COUNT(); }
   { k_relax_faces<2><<<dim3(cdiv(g.n[0], BX), cdiv(g.n[1], BY), g.n[2] + 1), dim3(BX, BY), 0, st>>>(g, w, t, vel[2]); WSI_COUNT(); }
   if (phi) { k_relax_cells<<<dim3(cdiv(g.n[0], BX), cdiv(g.n[1], BY), g.n[2]), dim3(BX, BY), 0, st>>>(g, w, t, phi); WSI_COUNT(); }
+}
+
+// ---------------------------------------------------------- Dirichlet inlet
+// Inlet data at time t (Sec. 7.1, the inlet's boundary-Heaviside equation),
+// x- plane, vertical axis z: normal velocity of face (j, k),
+//   gn[k ny + j] = (1 - H~(phi_b)) u_w(0, z_k - d, t),  z_k = (k + 1/2) hz,
+// and tangential (vertical) velocity of the x- edge at height z_k = k hz,
+//   gw[k ny + j] = (1 - H~(phi_b)) v_w(0, z_k - d, t),  k = 0 .. nz,
+// with phi_b = z_k - d - eta(0, t).  Uniform along y.
+__global__ void k_inlet_data(GridDev g, WaveDev w, double t, double* gn, double* gw) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+  if (j >= g.n[1]) return;
+  const double eta = wv_eta(w, 0.0, t);
+  double u, v;
+  if (k < g.n[2]) {
+    const double y = (k + 0.5) * g.h[2] - w.d;
+    wv_vel(w, 0.0, y, t, u, v);
+    gn[(size_t)k * g.n[1] + j] = (1.0 - wv_heaviside(y - eta, w.eps)) * u;
+  }
+  const double ye = k * g.h[2] - w.d;
+  wv_vel(w, 0.0, ye, t, u, v);
+  gw[(size_t)k * g.n[1] + j] = (1.0 - wv_heaviside(ye - eta, w.eps)) * v;
+}
+
+void launch_inlet_data(const GridDev& g, const WaveDev& w, double t, double* gn, double* gw, cudaStream_t st) {
+  { k_inlet_data<<<dim3(cdiv(g.n[1], 64), g.n[2] + 1), 64, 0, st>>>(g, w, t, gn, gw); WSI_COUNT(); }
+}
+
+// The inlet's data lifted to the right-hand side of the implicit solve: the
+// rows the data reach, through the operator of Sec. 4.2.2 with the inlet's
+// affine ghosts (normal velocity gn on the x- faces, tangential velocity gw
+// on the x- edges: ghost 2 gw - w), get b -= K_in x_b:
+//   continuity of cells i = 0:   b_p -= gn / hx
+//   u at faces i = 1:             b_u += 2 theta mu_cc(0) gn / hx^2
+//   v at faces (0, j), 0<j<ny:    b_v -= theta mu_xy (gn(j) - gn(j-1)) / (hy hx)
+//   w at faces (0, k) (rows):     b_w -= theta mu_xz (-2 gw / hx + (gn(k) - gn(k-1)) / hz) / hx
+// (at an open top's row gn(nz) is the tangential ghost -gn(nz-1)); and the
+// explicit viscous term of u^n gets the part of its tangential data gw_n that
+// the homogeneous ghost leaves out: b_w += (1 - theta) 2 mu_xz^n gw_n / hx^2.
+// One thread per (j, k) of the x- plane, k = 0 .. nz.
+__global__ void k_inlet_lift(GridDev g, const double* __restrict__ mu_cc, const double* __restrict__ mu_xy,
+                             const double* __restrict__ mu_xz, const double* __restrict__ mu_xz_n,
+                             const double* __restrict__ gn, const double* __restrict__ gw,
+                             const double* __restrict__ gw_n, double theta, double* bu, double* bv, double* bw,
+                             double* bp) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  if (j >= ny) return;
+  const double ihx = g.ih[0], ihy = g.ih[1], ihz = g.ih[2];
+  auto gn_at = [&](int kk, int jj) { return gn[(size_t)kk * ny + jj]; };
+  if (k < nz) {
+    const double gnv = gn_at(k, j);
+    bp[fidx(g, 3, 0, j, k)] -= gnv * ihx;
+    if (nx >= 2) bu[fidx(g, 0, 1, j, k)] += 2.0 * theta * mu_cc[fidx(g, 3, 0, j, k)] * gnv * ihx * ihx;
+    if (j > 0)
+      bv[fidx(g, 1, 0, j, k)] -= theta * mu_xy[eidx(g, 0, 0, j, k)] * (gnv - gn_at(k, j - 1)) * ihy * ihx;
+  }
+  if (face_row(g, 2, k)) {
+    const double gn_hi = k < nz ? gn_at(k, j) : g.bc[5] * gn_at(nz - 1, j);
+    const double gwv = gw[(size_t)k * ny + j];
+    const size_t e = eidx(g, 1, 0, j, k);
+    bw[fidx(g, 2, 0, j, k)] -= theta * mu_xz[e] * (-2.0 * gwv * ihx + (gn_hi - gn_at(k - 1, j)) * ihz) * ihx;
+    bw[fidx(g, 2, 0, j, k)] += (1.0 - theta) * 2.0 * mu_xz_n[e] * gw_n[(size_t)k * ny + j] * ihx * ihx;
+  }
+}
+
+void launch_inlet_lift(const GridDev& g, const double* mu_cc, const double* mu_xy, const double* mu_xz,
+                       const double* mu_xz_n, const double* gn, const double* gw, const double* gw_n, double theta,
+                       double* b, cudaStream_t st) {
+  Packing pk = packing(g);
+  { k_inlet_lift<<<dim3(cdiv(g.n[1], 64), g.n[2] + 1), 64, 0, st>>>(g, mu_cc, mu_xy, mu_xz, mu_xz_n, gn, gw, gw_n,
+                                                                    theta, b + pk.off[0], b + pk.off[1],
+                                                                    b + pk.off[2], b + pk.off[3]); WSI_COUNT(); }
+}
+
+// u on the x- faces of a velocity vector <- gn
+__global__ void k_inlet_set(GridDev g, const double* __restrict__ gn, double* u) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+  if (j >= g.n[1]) return;
+  u[fidx(g, 0, 0, j, k)] = gn[(size_t)k * g.n[1] + j];
+}
+
+void launch_inlet_set(const GridDev& g, const double* gn, double* u, cudaStream_t st) {
+  { k_inlet_set<<<dim3(cdiv(g.n[1], 64), g.n[2]), 64, 0, st>>>(g, gn, u); WSI_COUNT(); }
 }
 
 // omega^2 = g k tanh(k d) by Newton's method from the deep-water guess

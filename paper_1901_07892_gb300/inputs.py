@@ -50,6 +50,7 @@ class Case:
     box_center: tuple = None
     box_half: tuple = None
     extra: dict = field(default_factory=dict)
+    open_top: bool = False       # z+ side open (zero tangential velocity, zero pressure)
 
     @property
     def h(self):

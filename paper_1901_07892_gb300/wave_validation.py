@@ -4,15 +4,16 @@ tank against the analytic second-order surface, at three resolutions.
 
 Run:  python -m paper_1901_07892_gb300.wave_validation [--case A] [--nx 512,1024,2048]
       [--t-end 20] [--limiter xsppm7|cui] [--precision mixed|fp64]
+      [--generator inlet|zone] [--lid open|wall]
 
 Set-up per case (depth d, height H, period T, wavelength lambda from the
 dispersion relation): a 68 d x 1.3 d tank (water depth d, air above), run as
 a slab four cells thick in y with free-slip y walls (every field is uniform
 along y), no-slip x and z walls; one cell of interface smearing (n_cells =
-1); the wave generated by a relaxation zone one wavelength long at the left
-wall (this build has no Dirichlet inlet; the zone relaxes toward the same
-second-order Stokes solution, Sec. 7.1) and damped over the last 10 d; time
-step dt = 100 / (57 nx) as in Sec. 7.2.  The elevation eta = z - d - phi is
+1); the wave generated by the Dirichlet inlet at the left wall with an open
+top (the paper's set-up, the defaults), or by a relaxation zone one
+wavelength long under a closed lid (--generator zone --lid wall); damped
+over the last 10 d; time step dt = 100 / (57 nx) as in Sec. 7.2.  The elevation eta = z - d - phi is
 read in the probe column at the cell nearest the interface and averaged over
 y.  Reported per resolution: the error in the largest elevation over the
 window after the wave front has passed (the paper's measure) and the
@@ -61,7 +62,7 @@ def analytic_eta(x, t, H, T, d):
     return 0.5 * H * np.cos(th) + c2 * np.cos(2 * th)
 
 
-def build(case, nx):
+def build(case, nx, generator="inlet", lid="open"):
     d, hr, tr = CASES[case]
     H, T = hr * d, tr * math.sqrt(d / G)
     lam = 2 * math.pi / wavenumber(2 * math.pi / T, d)
@@ -73,17 +74,19 @@ def build(case, nx):
                     dt=100.0 / (57.0 * nx))
     c.n_cells = 1.0
     c.rho_s = c.rho_l
+    c.open_top = lid == "open"
     x, y, z = c.cell_xyz()
     c.phi = np.broadcast_to(z - d, (nz, ny, nx)).copy()
     c.psi = np.ones((nz, ny, nx))
-    waves = dict(H=H, T=T, depth=d, x_gen=lam, x_damp=lx - 10 * d)
+    waves = dict(H=H, T=T, depth=d, x_gen=lam if generator == "zone" else 0.0, x_damp=lx - 10 * d,
+                 inlet=generator == "inlet")
     return c, waves, dict(d=d, H=H, T=T, lam=lam, probe=2.87 * lam)
 
 
-def run(case, nx, t_end, precision, limiter, every=2):
+def run(case, nx, t_end, precision, limiter, generator="inlet", lid="open", every=2):
     import torch
     from paper_1901_07892_gb300 import wsi
-    c, waves, p = build(case, nx)
+    c, waves, p = build(case, nx, generator, lid)
     ctx = wsi.Context.from_case(c, precision=precision, restart=20, ls_limiter=limiter)
     ctx.set_case(c, with_body=False)
     ctx.set_waves(**waves)
@@ -131,13 +134,15 @@ def main(argv=None):
     ap.add_argument("--t-end", type=float, default=20.0)
     ap.add_argument("--limiter", default="xsppm7", choices=["xsppm7", "cui"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--generator", default="inlet", choices=["inlet", "zone"])
+    ap.add_argument("--lid", default="open", choices=["open", "wall"])
     a = ap.parse_args(argv)
     from paper_1901_07892_gb300 import wsi
     lim = wsi.LIMIT_XSPPM7 if a.limiter == "xsppm7" else wsi.LIMIT_CUI
     prec = wsi.PREC_MIXED if a.precision == "mixed" else wsi.PREC_FP64
     rows = []
     for nx in [int(v) for v in a.nx.split(",")]:
-        ts, etas, xp, p, its = run(a.case, nx, a.t_end, prec, lim)
+        ts, etas, xp, p, its = run(a.case, nx, a.t_end, prec, lim, a.generator, a.lid)
         r = errors(ts, etas, xp, p, a.t_end)
         r.update(nx=nx, nz=nx // 8, dt=100.0 / (57.0 * nx), mean_fgmres_iters_per_step=its)
         rows.append(r)
@@ -148,7 +153,8 @@ def main(argv=None):
                       "rate_max_elevation": math.log2(r0["max_elevation_error"] / r1["max_elevation_error"])
                       if r1["max_elevation_error"] > 0 else None,
                       "rate_pointwise": math.log2(r0["max_pointwise_error"] / r1["max_pointwise_error"])})
-    print(json.dumps({"case": a.case, "limiter": a.limiter, "precision": a.precision, "rates": rates,
+    print(json.dumps({"case": a.case, "limiter": a.limiter, "precision": a.precision, "generator": a.generator,
+                      "lid": a.lid, "rates": rates,
                       "paper_rates_case_A_context": [1.23, 1.17]}), flush=True)
 
 

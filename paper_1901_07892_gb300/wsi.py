@@ -46,7 +46,7 @@ class GridDesc(ctypes.Structure):
                 ("precision", ctypes.c_int), ("mg_pre", ctypes.c_int), ("mg_post", ctypes.c_int),
                 ("mg_cycles", ctypes.c_int), ("visc_sweeps", ctypes.c_int), ("restart", ctypes.c_int),
                 ("visc_mg", ctypes.c_int), ("reinit_iters", ctypes.c_int), ("transport_form", ctypes.c_int),
-                ("mg_smoother", ctypes.c_int), ("ls_limiter", ctypes.c_int)]
+                ("mg_smoother", ctypes.c_int), ("ls_limiter", ctypes.c_int), ("open_top", ctypes.c_int)]
 
 
 class PhaseProps(ctypes.Structure):
@@ -82,7 +82,7 @@ class StepStats(ctypes.Structure):
 class WaveDesc(ctypes.Structure):
     _fields_ = [("H", ctypes.c_double), ("T", ctypes.c_double), ("depth", ctypes.c_double),
                 ("x_gen", ctypes.c_double), ("x_damp", ctypes.c_double), ("t0", ctypes.c_double),
-                ("vertical", ctypes.c_int)]
+                ("vertical", ctypes.c_int), ("inlet", ctypes.c_int)]
 
 
 class WsiError(RuntimeError):
@@ -174,11 +174,11 @@ class Context:
     def __init__(self, nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, bc=(-1.0,) * 6, gravity=(0.0, 0.0, -9.81),
                  n_cells=2.0, theta=0.5, precision=PREC_FP64, mg_pre=2, mg_post=2, mg_cycles=1,
                  visc_sweeps=2, restart=20, stream=None, visc_mg=0, reinit_iters=0,
-                 transport_form=FORM_CONSISTENT, mg_smoother=SMOOTH_RBGS, ls_limiter=LIMIT_CUI):
+                 transport_form=FORM_CONSISTENT, mg_smoother=SMOOTH_RBGS, ls_limiter=LIMIT_CUI, open_top=0):
         L = lib()
         d = GridDesc(nx, ny, nz, lx, ly, lz, (ctypes.c_double * 6)(*bc), (ctypes.c_double * 3)(*gravity),
                      n_cells, theta, precision, mg_pre, mg_post, mg_cycles, visc_sweeps, restart, visc_mg,
-                     reinit_iters, transport_form, mg_smoother, ls_limiter)
+                     reinit_iters, transport_form, mg_smoother, ls_limiter, int(open_top))
         h = ctypes.c_void_p()
         st = ctypes.c_void_p(stream) if stream is not None else None
         rc = L.wsi_create_grid(ctypes.byref(d), st, ctypes.byref(h))
@@ -194,6 +194,7 @@ class Context:
 
     @classmethod
     def from_case(cls, case, **kw):
+        kw.setdefault("open_top", int(getattr(case, "open_top", False)))
         return cls(case.nx, case.ny, case.nz, case.lx, case.ly, case.lz, case.bc, case.gravity,
                    case.n_cells, case.theta, **kw)
 
@@ -334,8 +335,8 @@ class Context:
         self.L.wsi_restore.argtypes = [ctypes.c_void_p, ctypes.c_char_p]
         self._check(self.L.wsi_restore(self._h, str(path).encode()))
 
-    def set_waves(self, H, T, depth, x_gen, x_damp, t0=0.0, vertical=2):
-        w = WaveDesc(H, T, depth, x_gen, x_damp, t0, vertical)
+    def set_waves(self, H, T, depth, x_gen, x_damp, t0=0.0, vertical=2, inlet=False):
+        w = WaveDesc(H, T, depth, x_gen, x_damp, t0, vertical, int(inlet))
         self._check(self.L.wsi_set_waves(self._h, ctypes.byref(w)))
 
     def wave_relax(self, t, vel, phi):

@@ -57,6 +57,16 @@ def test_invalid_arguments_rejected_without_gpu_work():
     d.ls_limiter = 2  # neither limiter
     assert L.wsi_create_grid(ctypes.byref(d), None, ctypes.byref(h)) == wsi.ERR_INVALID_ARG
     d.ls_limiter = wsi.LIMIT_CUI
+    d.open_top = 2  # neither closed nor open
+    assert L.wsi_create_grid(ctypes.byref(d), None, ctypes.byref(h)) == wsi.ERR_INVALID_ARG
+    d.open_top = 1
+    d.bc[5] = 1.0  # an open top has zero tangential velocity: the lid's sign must be no-slip
+    assert L.wsi_create_grid(ctypes.byref(d), None, ctypes.byref(h)) == wsi.ERR_INVALID_ARG
+    d.bc[5] = -1.0
+    d.visc_mg = 1  # the viscous V-cycle has no open-top rows
+    assert L.wsi_create_grid(ctypes.byref(d), None, ctypes.byref(h)) == wsi.ERR_INVALID_ARG
+    d.visc_mg = 0
+    d.open_top = 0
     d.precision = 5
     assert L.wsi_create_grid(ctypes.byref(d), None, ctypes.byref(h)) == wsi.ERR_INVALID_ARG
     assert L.wsi_reinit(None, None, 3) == wsi.ERR_INVALID_ARG
