@@ -232,10 +232,12 @@ int wsi_set_field(wsi_ctx* ctx, int which, const double* src);
 
 /* Checkpoint / restart of the time-stepping state (no counterpart in the
  * paper): u^n, u^{n-1}, p, phi, psi, the markers, their velocity U_b^n, the
- * body's rigid velocities and centre, the time and the static-psi flag, to a
+ * body's rigid velocities and centre, the time and the static-psi flag, and
+ * with a Dirichlet inlet the tangential inlet data of u^n and u^{n-1}, to a
  * host file (native byte order).  wsi_restore needs a context created with
- * the same grid and precision and wsi_set_phases with the same body (the
- * phase properties and body description are not stored); it recomputes the
+ * the same grid and precision, wsi_set_phases with the same body and, for a
+ * checkpoint with an inlet, wsi_set_waves with the same inlet (the phase
+ * properties, body and wave descriptions are not stored); it recomputes the
  * operator coefficients from the restored level sets, so that stepping on
  * continues exactly as without the interruption.  Errors:
  * WSI_ERR_INVALID_ARG (no phases, unreadable file, other grid), WSI_ERR_CUDA. */

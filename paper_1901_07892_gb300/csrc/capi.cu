@@ -1497,6 +1497,7 @@ struct CkptHeader {
   int nx, ny, nz, precision, n_markers, psi_static_done;
   double time;
   double U_r[3], W_r[3], X_com[3];
+  int inlet, pad;  // 1: the inlet's tangential data of u^n and u^{n-1} follow the state
 };
 
 bool write_dev(FILE* f, const double* d, size_t n, std::vector<double>& h) {
@@ -1527,6 +1528,7 @@ int wsi_checkpoint(wsi_ctx* c, const char* path) {
   hd.n_markers = c->has_body ? c->body.n : 0;
   hd.psi_static_done = c->psi_static_done ? 1 : 0;
   hd.time = c->time;
+  hd.inlet = c->inlet ? 1 : 0;
   for (int a = 0; a < 3; ++a) {
     hd.U_r[a] = c->body.U_r[a];
     hd.W_r[a] = c->body.W_r[a];
@@ -1536,6 +1538,8 @@ int wsi_checkpoint(wsi_ctx* c, const char* path) {
   bool ok = fwrite(&hd, sizeof(hd), 1, f) == 1;
   ok = ok && write_dev(f, c->vel, c->nvel, h) && write_dev(f, c->vel_old, c->nvel, h) &&
        write_dev(f, c->p, c->ncell, h) && write_dev(f, c->phi, c->ncell, h) && write_dev(f, c->psi, c->ncell, h);
+  const size_t ne = (size_t)(c->g.n[2] + 1) * c->g.n[1];
+  if (ok && c->inlet) ok = write_dev(f, c->in_gw_n, ne, h) && write_dev(f, c->in_gw_nm1, ne, h);
   if (ok && c->has_body) {
     const size_t nm = (size_t)c->body.n * 3;
     ok = write_dev(f, c->body.X, nm, h) && write_dev(f, c->body.Ub_n, nm, h) && write_dev(f, c->body.xc, 3, h);
@@ -1555,9 +1559,9 @@ int wsi_restore(wsi_ctx* c, const char* path) {
     return fail(c, WSI_ERR_INVALID_ARG, "restore: not a checkpoint");
   }
   if (hd.nx != c->g.n[0] || hd.ny != c->g.n[1] || hd.nz != c->g.n[2] || hd.precision != c->desc.precision ||
-      hd.n_markers != (c->has_body ? c->body.n : 0)) {
+      hd.n_markers != (c->has_body ? c->body.n : 0) || hd.inlet != (c->inlet ? 1 : 0)) {
     fclose(f);
-    return fail(c, WSI_ERR_INVALID_ARG, "restore: grid, precision or marker count differ");
+    return fail(c, WSI_ERR_INVALID_ARG, "restore: grid, precision, marker count or inlet differ");
   }
   if (cudaStreamSynchronize(c->st) != cudaSuccess) {
     fclose(f);
@@ -1566,6 +1570,8 @@ int wsi_restore(wsi_ctx* c, const char* path) {
   std::vector<double> h;
   bool ok = read_dev(f, c->vel, c->nvel, h) && read_dev(f, c->vel_old, c->nvel, h) && read_dev(f, c->p, c->ncell, h) &&
             read_dev(f, c->phi, c->ncell, h) && read_dev(f, c->psi, c->ncell, h);
+  const size_t ne = (size_t)(c->g.n[2] + 1) * c->g.n[1];
+  if (ok && c->inlet) ok = read_dev(f, c->in_gw_n, ne, h) && read_dev(f, c->in_gw_nm1, ne, h);
   if (ok && c->has_body) {
     const size_t nm = (size_t)c->body.n * 3;
     ok = read_dev(f, c->body.X, nm, h) && read_dev(f, c->body.Ub_n, nm, h) && read_dev(f, c->body.xc, 3, h);

@@ -53,6 +53,39 @@ def test_restart_continues_the_run(tmp_path, prec, body):
     d.close()
 
 
+@pytest.mark.parametrize("prec", [wsi.PREC_FP64, wsi.PREC_MIXED])
+def test_restart_with_inlet_and_open_top(tmp_path, prec):
+    """A wave tank driven by the Dirichlet inlet through an open top: the
+    checkpoint carries the inlet's tangential data of u^n and u^{n-1}, and
+    the restored run goes on bit for bit."""
+    c = inputs.wave_tank(nx=32, ny=4, nz=16, with_bar=False)
+    c.open_top = True
+    w = c.extra["wave"]
+
+    def mk():
+        ctx = wsi.Context.from_case(c, precision=prec, restart=30)
+        ctx.set_case(c, rho_s=c.rho_l, with_body=False)
+        ctx.set_waves(w["H"], w["T"], w["depth"], 0.0, w["x_damp"], 0.0, 2, inlet=True)
+        return ctx
+    a = mk()
+    for _ in range(4):
+        a.step(c.dt, rtol=1e-10)
+    b = mk()
+    for _ in range(2):
+        b.step(c.dt, rtol=1e-10)
+    path = tmp_path / "inlet.bin"
+    b.checkpoint(path)
+    b.close()
+    d = mk()
+    d.restore(path)
+    for _ in range(2):
+        d.step(c.dt, rtol=1e-10)
+    for f in FIELDS:
+        assert np.array_equal(a.get_field(f), d.get_field(f)), f
+    a.close()
+    d.close()
+
+
 def test_spreading_is_deterministic():
     """The same forces spread twice (and from a second context) give the
     same bits, with many markers landing on the same faces."""
