@@ -69,8 +69,12 @@ def kernel_model(name, nx, ny, nz, prec_bytes):
         byts = prec_bytes * (F + F // 2 + F + N + E + F // 2)
         return byts, 50 * F // 2, "hbm"
     if name == "transport":
-        byts = 8 * (F + F + F)
-        return byts, 300 * F, "alu"
+        # launches differ (density only, or with the velocity): the library
+        # sums each launch's algorithmic bytes (wsi_ktimer_bytes): per
+        # component the transported density, the three velocity arrays of the
+        # advective velocities, the transported velocity (convective term)
+        # and the result, in the storage type
+        return None, None, "hbm"
     if name in ("mdot", "maxpy"):
         # launches differ in the number of basis vectors: the library sums
         # each launch's algorithmic bytes (wsi_ktimer_bytes)

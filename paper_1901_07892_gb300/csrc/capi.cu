@@ -1058,7 +1058,11 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
   }
   c->mat_n_valid = false;
   if (c->inlet) launch_inlet_data(g, c->wave, c->time + dt, c->in_gn, c->in_gw_np1, st);
-  cudaMemcpyAsync(c->vel_k, c->vel, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  // the velocity iterate u^{n+1,k} lives in the velocity part of the solve's
+  // packed vector, so that the solves start from it and leave their result
+  // in place (no copies between the cycles)
+  double* const vk = c->x;
+  cudaMemcpyAsync(vk, c->vel, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(c->phi_k, c->phi, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(c->psi_k, c->psi, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
   if (c->has_body) cudaMemcpyAsync(B.Xn, B.X, (size_t)B.n * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
@@ -1066,7 +1070,7 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
   const int ncyc = 2;
   for (int k = 0; k < ncyc; ++k) {
     // 1. level sets and viscosity at (n+1, k+1)
-    levelset_stage(c, c->vel_k, c->vel, c->phi_k, c->phi, dt, c->phi_new);
+    levelset_stage(c, vk, c->vel, c->phi_k, c->phi, dt, c->phi_new);
     const double* psi_use = c->psi_k;
     const bool at_rest = B.lock[0] && B.lock[1] && B.lock[2] && B.lock[3] && B.lock[4] && B.lock[5] &&
                          B.U_pres[0] == 0.0 && B.U_pres[1] == 0.0 && B.U_pres[2] == 0.0 && B.W_pres[0] == 0.0 &&
@@ -1095,7 +1099,7 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
         rhs_base(c, 0.0);
       }
     } else {
-      transport_stage(c, k, dt, c->vel, c->vel_old, c->vel_k, k > 0);
+      transport_stage(c, k, dt, c->vel, c->vel_old, vk, k > 0);
       if (k == 0) rhs_base(c, 1.0 / dt);
     }
     const double* rg[3];
@@ -1117,8 +1121,7 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
     if (c->inlet)
       launch_inlet_lift(g, c->mu_cc, c->mu_e[0], c->mu_e[1], c->mu_e_n[1], c->in_gn, c->in_gw_np1, c->in_gw_n,
                         c->desc.theta, c->b, st);
-    // 3. Stokes solve from (u^{n+1,k}, p^{n+1/2,k})
-    cudaMemcpyAsync(c->x, c->vel_k, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    // 3. Stokes solve from (u^{n+1,k}, p^{n+1/2,k}), in place
     if (c->inlet) {
       double* xq[3];
       parts(c, c->x, xq);
@@ -1136,10 +1139,9 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
       s->rel_residual[k] = ss.rel_residual;
     }
     // 4. rigidity projection at X^{n+1/2,k}, then positions
-    cudaMemcpyAsync(c->vel_k, c->x, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
     if (c->has_body) {
       launch_lincomb((size_t)B.n * 3, 0.5, B.X, 0.5, B.Xn, 0.0, nullptr, B.Xh, st);
-      rc = dlm_project(c, c->vel_k, B.Xh);
+      rc = dlm_project(c, vk, B.Xh);
       if (rc) return rc;
       launch_marker_update(g, B.Xn, B.Ub, B.Ub_n, B.n, dt, B.X, B.flag, st);
     }
@@ -1149,7 +1151,7 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
   // wave generation / damping zones relax u^{n+1} and phi^{n+1} (Sec. 7.1)
   if (c->has_waves) {
     double* vq[3];
-    parts(c, c->vel_k, vq);
+    parts(c, vk, vq);
     launch_wave_relax(g, c->wave, c->time + dt, vq, c->phi_k, st);
   }
   // phi^{n+1} brought back to a signed distance (Sec. 4.1)
@@ -1162,9 +1164,9 @@ int wsi_step(wsi_ctx* c, double dt, const wsi_solve_opts* o, wsi_step_stats* s) 
     std::swap(c->in_gw_nm1, c->in_gw_n);
     std::swap(c->in_gw_n, c->in_gw_np1);
   }
-  // commit the step
-  cudaMemcpyAsync(c->vel_old, c->vel, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
-  cudaMemcpyAsync(c->vel, c->vel_k, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  // commit the step: u^n becomes u^{n-1} by exchanging the two buffers
+  std::swap(c->vel_old, c->vel);
+  cudaMemcpyAsync(c->vel, vk, nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(c->p, c->x + c->pk.off[3], nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(c->phi, c->phi_k, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(c->psi, c->psi_k, nc * sizeof(double), cudaMemcpyDeviceToDevice, st);

@@ -101,13 +101,34 @@ __device__ __forceinline__ T adv_at(const GridDev& g, const CVel<T>& vel, int i,
   return T(0.5) * (vel.q[D][id1 - sc] + vel.q[D][id1]);
 }
 
+// Asynchronous 4- or 8-byte copies global -> shared (cp.async), grouped per
+// staged plane
+template <typename T>
+__device__ __forceinline__ void cpa(T* dst, const T* src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // Per z-plane the block stages the transported field (and, for C, the
-// velocity component) of its tile with a two-entry halo in x and y into
-// shared memory, ghosts already mirrored (the mirror offsets of the staged
-// entries depend only on x and y: computed once per thread); the four
-// limiter taps of every x- and y-flux then come from shared memory.  Along z
-// each thread keeps its column's last four entries in registers.  Advective
-// velocities are read from global memory (two values per flux, coalesced).
+// velocity component) of its tile with a two-entry halo in x and y into a
+// ring of NPL plane slots in shared memory, by asynchronous copies issued
+// three planes ahead (the ghosts beyond walls are mirrored through the copies'
+// source addresses; the velocity ghosts' signs, and the inlet data across a
+// Dirichlet inlet, are applied by the staging thread once its copies have
+// landed).  The four limiter taps of every x- and y-flux then come from plane
+// k's slot, the z taps of a thread's own column from the slots of planes
+// k-1 .. k+2 (a plane beyond a wall reads its mirror image's slot with the
+// mirror's sign).  Advective velocities are loaded one plane ahead into
+// registers.  Two block barriers per plane: one publishes the plane, one the
+// x- and y-fluxes.
+static constexpr int NPL = 6;  // planes k-2 .. k+3
+
 // inl (C == 2 with the velocity only, else null): tangential data of w on
 // the x- plane of a Dirichlet inlet, (nz+1) x ny; the ghosts of w across it
 // are then 2 inl - (mirror image)
@@ -115,8 +136,9 @@ template <int C, bool WITHV, typename T>
 __global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, CVel<T> vel, const T* __restrict__ rho, T* out,
                                                       int zchunk, const T* __restrict__ inl) {
   constexpr int HX = BX + 4, HY = BY + 4, NS = (HX * HY + BX * BY - 1) / (BX * BY);
-  __shared__ T sR[HY][HX];
-  __shared__ T sQ[WITHV ? HY : 1][WITHV ? HX : 1];
+  constexpr int PL = HX * HY;
+  __shared__ __align__(16) T sR[NPL][PL];
+  __shared__ __align__(16) T sQ[WITHV ? NPL : 1][WITHV ? PL : 1];
   __shared__ T sFx[BY][BX + 1];
   __shared__ T sFy[BY + 1][BX];
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
@@ -140,7 +162,7 @@ __global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, CVel<T> vel, co
     soff[r] = -1;
     ssg[r] = T(1);
     if (INL) sinl[r] = -1;
-    if (t < HX * HY) {
+    if (t < PL) {
       const int hy = t / HX, hx = t - hy * HX;
       T sx, sy;
       const int mx = mirror_index<C, 0, T>(g, x0 - 2 + hx, sx);
@@ -150,111 +172,187 @@ __global__ void __launch_bounds__(BX* BY) k_transport(GridDev g, CVel<T> vel, co
       if (INL && inl && x0 - 2 + hx < 0) sinl[r] = my;
     }
   }
-  // z window: entries k-1 .. k+2 of this column (density, velocity)
-  const size_t col = (size_t)min(j, e1 - 1) * e0 + min(i, e0 - 1);
-  T zr[4], zq[4];
-  auto zload = [&](int m, T& r_, T& q_) {
-    T sz;
-    const int mm = mirror_index<C, 2, T>(g, m, sz);
-    r_ = rho[(size_t)mm * plane + col];
-    q_ = WITHV ? sz * qc[(size_t)mm * plane + col] : T(0);
-  };
+  // ring slot of plane p (k0 - 2 <= p; planes k - 2 .. k + 3 are distinct)
+  auto slot = [&](int p) { return (p - k0 + 2) % NPL; };
+  // copies of plane p into its slot (planes outside the array: none); one
+  // group per call
+  auto issue = [&](int p) {
+    if (p >= 0 && p < e2) {
+      const int s = slot(p);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) zload(k0 - 2 + q, zr[q], zq[q]);
-  T Fz_lo = T(0);
-  for (int k = k0; k < k1; ++k) {
-    const int idC = (C == 0) ? i : ((C == 1) ? j : k);
-    const bool wall = idC == 0 || idC == g.n[C];
-    // which fluxes this thread forms, and their advective velocities: loaded
-    // before the staging barrier so that their latency overlaps it
-    const int mxh = i + ox + 1, mxl = i + ox, myh = j + oy + 1, myl = j + oy;
-    const bool okx = inside && ((C == 0) || !wall), oky = inside && ((C == 1) || !wall);
-    const bool fxh = okx && (C != 0 || mxh <= g.n[0] - 1), fxl = okx && tx == 0 && (C != 0 || mxl >= 0);
-    const bool fyh = oky && (C != 1 || myh <= g.n[1] - 1), fyl = oky && ty == 0 && (C != 1 || myl >= 0);
-    const T axh = fxh ? adv_at<C, 0, T>(g, vel, i, j, k, mxh) : T(0);
-    const T axl = fxl ? adv_at<C, 0, T>(g, vel, i, j, k, mxl) : T(0);
-    const T ayh = fyh ? adv_at<C, 1, T>(g, vel, i, j, k, myh) : T(0);
-    const T ayl = fyl ? adv_at<C, 1, T>(g, vel, i, j, k, myl) : T(0);
-    const int mzh = k + oz + 1;
-    const bool fzh = inside && ((C == 2) || !wall) && (C != 2 || mzh <= g.n[2] - 1);
-    const T azh = fzh ? adv_at<C, 2, T>(g, vel, i, j, k, mzh) : T(0);
-    // stage plane k
-#pragma unroll
-    for (int r = 0; r < NS; ++r) {
-      const int t = tid + r * BX * BY;
-      if (soff[r] >= 0) {
-        const int hy = t / HX, hx = t - hy * HX;
-        const size_t a = (size_t)k * plane + soff[r];
-        sR[hy][hx] = rho[a];
-        if (WITHV) {
-          T qv = ssg[r] * qc[a];
-          if (INL && sinl[r] >= 0) qv += T(2) * inl[(size_t)k * e1 + sinl[r]];
-          sQ[hy][hx] = qv;
+      for (int r = 0; r < NS; ++r) {
+        const int t = tid + r * BX * BY;
+        if (soff[r] >= 0) {
+          const size_t a = (size_t)p * plane + soff[r];
+          cpa<T>(&sR[s][t], rho + a);
+          if (WITHV) cpa<T>(&sQ[WITHV ? s : 0][WITHV ? t : 0], qc + a);
         }
       }
     }
-    __syncthreads();
+    cpa_commit();
+  };
+  // signs and inlet data of this thread's entries of plane p, once landed
+  auto fix = [&](int p) {
+    if (!WITHV || p < 0 || p >= e2) return;
+    const int s = slot(p);
+#pragma unroll
+    for (int r = 0; r < NS; ++r) {
+      const int t = tid + r * BX * BY;
+      if (soff[r] < 0) continue;
+      const bool inl_here = INL && sinl[INL ? r : 0] >= 0;
+      if (ssg[r] == T(1) && !inl_here) continue;
+      T q = ssg[r] * sQ[WITHV ? s : 0][WITHV ? t : 0];
+      if (inl_here) q += T(2) * inl[(size_t)p * e1 + sinl[INL ? r : 0]];
+      sQ[WITHV ? s : 0][WITHV ? t : 0] = q;
+    }
+  };
+  // z taps of this thread's column at plane m (mirrored beyond the walls)
+  const int own = (ty + 2) * HX + (tx + 2);
+  auto ztap = [&](int m, T& r_, T& q_) {
+    T sz;
+    const int mm = mirror_index<C, 2, T>(g, m, sz);
+    const int s = slot(mm);
+    r_ = sR[s][own];
+    q_ = WITHV ? sz * sQ[WITHV ? s : 0][WITHV ? own : 0] : T(0);
+  };
+  // fluxes this thread forms at plane k, and their advective velocities: the
+  // two entries of each are found at offsets that move by one z-level of
+  // their array per plane (computed once; 32-bit, every array holds fewer
+  // than 2^31 entries)
+  struct Adv {
+    T xh, xl, yh, yl, zh;
+  };
+  const int mxh = i + ox + 1, mxl = i + ox, myh = j + oy + 1, myl = j + oy;
+  const bool fxh0 = inside && (C != 0 || mxh <= g.n[0] - 1), fxl0 = inside && tx == 0 && (C != 0 || mxl >= 0);
+  const bool fyh0 = inside && (C != 1 || myh <= g.n[1] - 1), fyl0 = inside && ty == 0 && (C != 1 || myl >= 0);
+  // offset at level k0 of the first entry, and the distance to the second
+  auto adv_off = [&](int D, int m, int& d) -> int {
+    int a[3] = {clampi(i, 0, g.n[0]), clampi(j, 0, g.n[1]), k0};
+    a[D] = m;
+    if (C == D) {
+      d = C == 0 ? 1 : (C == 1 ? g.n[0] : g.n[0] * g.n[1]);
+      return (int)fidx(g, C, a[0], a[1], a[2]);
+    }
+    d = -(C == 0 ? 1 : (C == 1 ? (g.n[0] + (D == 0)) : (g.n[0] + (D == 0)) * (g.n[1] + (D == 1))));
+    return (int)fidx(g, D, a[0], a[1], a[2]);
+  };
+  int dxh = 0, dxl = 0, dyh = 0, dyl = 0, dzh = 0;
+  const int oxh = fxh0 ? adv_off(0, mxh, dxh) : 0, oxl = fxl0 ? adv_off(0, mxl, dxl) : 0;
+  const int oyh = fyh0 ? adv_off(1, myh, dyh) : 0, oyl = fyl0 ? adv_off(1, myl, dyl) : 0;
+  const int ozh = inside ? adv_off(2, k0 + oz + 1, dzh) : 0;
+  // one z-level of the u, v, w arrays
+  const int lx = (g.n[0] + 1) * g.n[1], ly = g.n[0] * (g.n[1] + 1), lz = g.n[0] * g.n[1];
+  const T* __restrict__ U_ = vel.q[0];
+  const T* __restrict__ V_ = vel.q[1];
+  const T* __restrict__ W_ = vel.q[2];
+  auto adv_load = [&](int k) {
+    Adv a{T(0), T(0), T(0), T(0), T(0)};
+    const int idC = (C == 0) ? i : ((C == 1) ? j : k);
+    const bool wall = idC == 0 || idC == g.n[C];
+    const int dk = k - k0;
+    if ((C == 0) || !wall) {
+      if (fxh0) { const int o = oxh + dk * lx; a.xh = T(0.5) * (U_[o] + U_[o + dxh]); }
+      if (fxl0) { const int o = oxl + dk * lx; a.xl = T(0.5) * (U_[o] + U_[o + dxl]); }
+    }
+    if ((C == 1) || !wall) {
+      if (fyh0) { const int o = oyh + dk * ly; a.yh = T(0.5) * (V_[o] + V_[o + dyh]); }
+      if (fyl0) { const int o = oyl + dk * ly; a.yl = T(0.5) * (V_[o] + V_[o + dyl]); }
+    }
+    if (inside && ((C == 2) || !wall) && (C != 2 || k + oz + 1 <= g.n[2] - 1)) {
+      const int o = ozh + dk * lz;
+      a.zh = T(0.5) * (W_[o] + W_[o + dzh]);
+    }
+    return a;
+  };
+
+  // prologue: planes k0-2 .. k0+2 in flight, advective velocities of plane k0
+#pragma unroll 1
+  for (int p = k0 - 2; p <= k0 + 2; ++p) issue(p);
+  Adv cur = adv_load(k0);
+  T Fz_lo = T(0);
+  for (int k = k0; k < k1; ++k) {
+    issue(k + 3);
+    const Adv nxt = k + 1 < k1 ? adv_load(k + 1) : Adv{T(0), T(0), T(0), T(0), T(0)};
+    cpa_wait<1>();  // planes up to k + 2 have landed (this thread's copies)
+    if (k == k0) {
+#pragma unroll 1
+      for (int p = k0 - 2; p <= k0 + 2; ++p) fix(p);
+    } else {
+      fix(k + 2);
+    }
+    __syncthreads();  // plane k + 2 published
+    const int s = slot(k);
+    const int idC = (C == 0) ? i : ((C == 1) ? j : k);
+    const bool wall = idC == 0 || idC == g.n[C];
+    T Fz_hi = T(0);
     if (inside) {
+      const T* R_ = sR[s];
+      const T* Q_ = sQ[WITHV ? s : 0];
       // x-fluxes: hi through the CV face above i (taps i-1 .. i+2), lo below (taps i-2 .. i+1)
       T hi = T(0), lo = T(0);
-      const int hy = ty + 2;
-      if (fxh) {
-        hi = axh * lim4<T>(sR[hy][tx + 1], sR[hy][tx + 2], sR[hy][tx + 3], sR[hy][tx + 4], axh);
-        if (WITHV) hi *= lim4<T>(sQ[hy][tx + 1], sQ[hy][tx + 2], sQ[hy][tx + 3], sQ[hy][tx + 4], axh);
+      const int hr = (ty + 2) * HX;
+      if (cur.xh != T(0)) {
+        hi = cur.xh * lim4<T>(R_[hr + tx + 1], R_[hr + tx + 2], R_[hr + tx + 3], R_[hr + tx + 4], cur.xh);
+        if (WITHV) hi *= lim4<T>(Q_[hr + tx + 1], Q_[hr + tx + 2], Q_[hr + tx + 3], Q_[hr + tx + 4], cur.xh);
       }
-      if (fxl) {
-        lo = axl * lim4<T>(sR[hy][tx], sR[hy][tx + 1], sR[hy][tx + 2], sR[hy][tx + 3], axl);
-        if (WITHV) lo *= lim4<T>(sQ[hy][tx], sQ[hy][tx + 1], sQ[hy][tx + 2], sQ[hy][tx + 3], axl);
+      if (cur.xl != T(0)) {
+        lo = cur.xl * lim4<T>(R_[hr + tx], R_[hr + tx + 1], R_[hr + tx + 2], R_[hr + tx + 3], cur.xl);
+        if (WITHV) lo *= lim4<T>(Q_[hr + tx], Q_[hr + tx + 1], Q_[hr + tx + 2], Q_[hr + tx + 3], cur.xl);
       }
       sFx[ty][tx + 1] = hi;
       if (tx == 0) sFx[ty][0] = lo;
       // y-fluxes
       hi = T(0);
       lo = T(0);
-      const int hx = tx + 2;
-      if (fyh) {
-        hi = ayh * lim4<T>(sR[ty + 1][hx], sR[ty + 2][hx], sR[ty + 3][hx], sR[ty + 4][hx], ayh);
-        if (WITHV) hi *= lim4<T>(sQ[ty + 1][hx], sQ[ty + 2][hx], sQ[ty + 3][hx], sQ[ty + 4][hx], ayh);
+      const int hc = tx + 2;
+      if (cur.yh != T(0)) {
+        hi = cur.yh * lim4<T>(R_[(ty + 1) * HX + hc], R_[(ty + 2) * HX + hc], R_[(ty + 3) * HX + hc],
+                              R_[(ty + 4) * HX + hc], cur.yh);
+        if (WITHV)
+          hi *= lim4<T>(Q_[(ty + 1) * HX + hc], Q_[(ty + 2) * HX + hc], Q_[(ty + 3) * HX + hc],
+                        Q_[(ty + 4) * HX + hc], cur.yh);
       }
-      if (fyl) {
-        lo = ayl * lim4<T>(sR[ty][hx], sR[ty + 1][hx], sR[ty + 2][hx], sR[ty + 3][hx], ayl);
-        if (WITHV) lo *= lim4<T>(sQ[ty][hx], sQ[ty + 1][hx], sQ[ty + 2][hx], sQ[ty + 3][hx], ayl);
+      if (cur.yl != T(0)) {
+        lo = cur.yl * lim4<T>(R_[ty * HX + hc], R_[(ty + 1) * HX + hc], R_[(ty + 2) * HX + hc],
+                              R_[(ty + 3) * HX + hc], cur.yl);
+        if (WITHV)
+          lo *= lim4<T>(Q_[ty * HX + hc], Q_[(ty + 1) * HX + hc], Q_[(ty + 2) * HX + hc],
+                        Q_[(ty + 3) * HX + hc], cur.yl);
       }
       sFy[ty + 1][tx] = hi;
       if (ty == 0) sFy[0][tx] = lo;
-    }
-    __syncthreads();
-    if (k == k0) {
-      // lo z-flux of the chunk, from the window's entries k0-2 .. k0+1
-      const bool okz = (C == 2) || !wall;
-      const int mzl = k + oz;
-      Fz_lo = T(0);
-      if (inside && okz && (C != 2 || mzl >= 0)) {
-        const T adv = adv_at<C, 2, T>(g, vel, i, j, k, mzl);
-        Fz_lo = adv * lim4<T>(zr[0], zr[1], zr[2], zr[3], adv);
-        if (WITHV) Fz_lo *= lim4<T>(zq[0], zq[1], zq[2], zq[3], adv);
-      }
-    }
-    // z window -> entries k-1 .. k+2
+      // z-fluxes through the CV faces above (taps k-1 .. k+2) and, at the
+      // chunk start, below (taps k-2 .. k+1)
+      if (k == k0) {
+        Fz_lo = T(0);
+        const int mzl = k + oz;
+        if (((C == 2) || !wall) && (C != 2 || mzl >= 0)) {
+          const T adv = adv_at<C, 2, T>(g, vel, i, j, k, mzl);
+          T r4[4], q4[4];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      zr[q] = zr[q + 1];
-      zq[q] = zq[q + 1];
-    }
-    zload(k + 2, zr[3], zq[3]);
-    if (inside) {
-      T Fz_hi = T(0);
-      if (fzh) {
-        Fz_hi = azh * lim4<T>(zr[0], zr[1], zr[2], zr[3], azh);
-        if (WITHV) Fz_hi *= lim4<T>(zq[0], zq[1], zq[2], zq[3], azh);
+          for (int q = 0; q < 4; ++q) ztap(k - 2 + q, r4[q], q4[q]);
+          Fz_lo = adv * lim4<T>(r4[0], r4[1], r4[2], r4[3], adv);
+          if (WITHV) Fz_lo *= lim4<T>(q4[0], q4[1], q4[2], q4[3], adv);
+        }
       }
+      if (cur.zh != T(0)) {
+        T r4[4], q4[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ztap(k - 1 + q, r4[q], q4[q]);
+        Fz_hi = cur.zh * lim4<T>(r4[0], r4[1], r4[2], r4[3], cur.zh);
+        if (WITHV) Fz_hi *= lim4<T>(q4[0], q4[1], q4[2], q4[3], cur.zh);
+      }
+    }
+    __syncthreads();  // x- and y-fluxes published
+    if (inside) {
       const T r = (sFx[ty][tx + 1] - sFx[ty][tx]) * ginv<T>(g, 0) + (sFy[ty + 1][tx] - sFy[ty][tx]) * ginv<T>(g, 1) +
                   (Fz_hi - Fz_lo) * ginv<T>(g, 2);
       out[(size_t)k * plane + (size_t)j * e0 + i] = wall ? T(0) : r;
       Fz_lo = Fz_hi;
     }
-    __syncthreads();
+    cur = nxt;
   }
+  cpa_wait<0>();  // no copies in flight when the block ends
 }
 
 // z-chunk of the transport kernels: long marches amortise the chunk start,
@@ -286,6 +384,12 @@ void launch_transport_flux(const GridDev& g, const T* const vel[3], const T* con
                            T* const out[3], cudaStream_t st, const T* inlet_w) {
   CVel<T> v{{vel[0], vel[1], vel[2]}};
   ktimer_begin(KC_TRANSPORT, st);
+  {
+    // algorithmic bytes: per component rho_C, u, v, w (advective
+    // velocities), q_C with the velocity, the result
+    const double F = (double)(fsize(g, 0) + fsize(g, 1) + fsize(g, 2));
+    ktimer_bytes(KC_TRANSPORT, sizeof(T) * F * (with_velocity ? 6.0 : 5.0));
+  }
   if (with_velocity)
     transport_all<true, T>(g, v, rho, out, inlet_w, st);
   else
