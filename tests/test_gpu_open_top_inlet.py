@@ -89,10 +89,12 @@ def test_open_top_operator_parity(shape):
         ctx.close()
 
 
-@pytest.mark.parametrize("precision", [wsi.PREC_FP64, wsi.PREC_MIXED])
-def test_open_top_solve_parity(precision):
+@pytest.mark.parametrize("precision,smoother", [(wsi.PREC_FP64, wsi.SMOOTH_RBGS), (wsi.PREC_MIXED, wsi.SMOOTH_RBGS),
+                                                (wsi.PREC_MIXED, wsi.SMOOTH_CHEBYSHEV)])
+def test_open_top_solve_parity(precision, smoother):
     """A Stokes solve to rtol 1e-13 with gravity: the pressure is compared
-    as it is (no mean removed), the open top fixes it."""
+    as it is (no mean removed), the open top fixes it; both multigrid
+    smoothers carry the Dirichlet row of the top cells."""
     c, rng = _open_case(24, 12, 16, 2)
     g = _grid(c)
     m = _mat(c, g)
@@ -101,7 +103,7 @@ def test_open_top_solve_parity(precision):
     bu[2] = bu[2] + m.rho_face[2] * -9.81 * g.interior_face_mask(2)
     b = g.pack(bu[0], bu[1], bu[2], np.zeros(g.cell_shape))
     ref = g.unpack(solve_stokes(g, m, m.rho_face, dt, c.theta, b))
-    ctx = wsi.Context.from_case(c, precision=precision, restart=40)
+    ctx = wsi.Context.from_case(c, precision=precision, restart=40, mg_smoother=smoother)
     ctx.set_case(c)
     x, st = ctx.solve(torch.from_numpy(b).cuda(), dt, rtol=1e-13, max_iters=800)
     got = g.unpack(x.cpu().numpy())
@@ -118,15 +120,18 @@ def _inlet_tank(nx=32, ny=4, nz=16):
     return c
 
 
-@pytest.mark.parametrize("precision", [wsi.PREC_FP64, wsi.PREC_MIXED])
-def test_inlet_open_top_step_parity(precision):
+@pytest.mark.parametrize("precision,form", [(wsi.PREC_FP64, "consistent"), (wsi.PREC_MIXED, "consistent"),
+                                            (wsi.PREC_FP64, "nonconservative")])
+def test_inlet_open_top_step_parity(precision, form):
     """Two steps of a coarse wave tank (32 x 4 x 16 over 4 x 1 x 1, dt = 0.01)
     driven from rest by the inlet's second-order Stokes wave through an open
-    top, damping zone at the far end."""
+    top, damping zone at the far end; also with the non-conservative form,
+    whose convection carries the inlet data of the half-step velocity."""
     c = _inlet_tank()
     g = _grid(c)
     w = c.extra["wave"]
-    ctx = wsi.Context.from_case(c, precision=precision, restart=30)
+    tf = wsi.FORM_CONSISTENT if form == "consistent" else wsi.FORM_NONCONSERVATIVE
+    ctx = wsi.Context.from_case(c, precision=precision, restart=30, transport_form=tf)
     ctx.set_case(c, rho_s=c.rho_l, with_body=False)
     ctx.set_waves(w["H"], w["T"], w["depth"], 0.0, w["x_damp"], 0.0, 2, inlet=True)
     wave = StokesWave(w["H"], w["T"], w["depth"])
@@ -135,15 +140,15 @@ def test_inlet_open_top_step_parity(precision):
     s = ost.State(g, pr, c.phi, c.psi, None, zones=Zones(wave, 0.0, w["x_damp"], c.lx), inlet=Inlet(wave))
     for _ in range(2):
         ctx.step(c.dt, rtol=1e-13, max_iters=600)
-        ost.step(s, c.dt)
+        ost.step(s, c.dt, form=form)
     vel = ctx.get_field(wsi.F_VEL)
     o = np.cumsum([0] + [g.n_faces(d) for d in range(3)])
     vscale = max(np.abs(a).max() for a in s.vel)
     errs = {name: np.abs(vel[o[d]:o[d + 1]] - s.vel[d].ravel()).max() / vscale for d, name in enumerate("uvw")}
     errs["p"] = _rel(ctx.get_field(wsi.F_P), s.p.ravel())
     errs["phi"] = _rel(ctx.get_field(wsi.F_PHI), s.phi.ravel())
-    print("inlet + open top, two steps, %s: per-field error against the oracle %s"
-          % ("float64" if precision == wsi.PREC_FP64 else "mixed", {k: "%.2e" % v for k, v in errs.items()}))
+    print("inlet + open top, two steps, %s, %s form: per-field error against the oracle %s"
+          % ("float64" if precision == wsi.PREC_FP64 else "mixed", form, {k: "%.2e" % v for k, v in errs.items()}))
     # the inlet faces hold the data of t^2 (the device's and numpy's
     # transcendental functions round differently)
     assert np.abs(s.vel[0][..., 0]).max() > 1e-3
