@@ -118,11 +118,23 @@ __device__ __forceinline__ ht shfl_down1(ht a) {
   return ht{__shfl_down_sync(0xffffffffu, a.h, 1), __shfl_down_sync(0xffffffffu, a.t, 1)};
 }
 
-// rho/dt q + G p - theta L as a float64
-__device__ __forceinline__ double row_out(const HtConst& K, ht rq, ht gp, ht L) {
-  return ht_dbl(ht_add(ht_add(rq, gp), ht_k(L, K.mtheta, (K.pw >> 6) & 1)));
+// a * c for a grid constant c: P2 (every constant a power of two, known at
+// compile time) scales both parts exactly; otherwise the constant's own flag
+template <bool P2>
+__device__ __forceinline__ ht hk(ht a, ht c, bool pow2) {
+  return P2 ? ht{a.h * c.h, a.t * c.h} : ht_k(a, c, pow2);
 }
 
+// rho/dt q + G p - theta L as a float64
+template <bool P2>
+__device__ __forceinline__ double row_out(const HtConst& K, ht rq, ht gp, ht L) {
+  return ht_dbl(ht_add(ht_add(rq, gp), hk<P2>(L, K.mtheta, (K.pw >> 6) & 1)));
+}
+
+// P2: 1/h, 2/h^2 and theta are all powers of two (uniform power-of-two
+// spacings), so that every multiplication by a grid constant is an exact
+// scaling
+template <bool P2>
 __global__ void __launch_bounds__(32 * FBY) k_stokes_df(const __grid_constant__ DfMaps maps, const HtConst K,
                                                         double* yu, double* yv, double* yw, double* yp, int* err) {
   extern __shared__ __align__(128) float2 dsm[];
@@ -191,9 +203,9 @@ __global__ void __launch_bounds__(32 * FBY) k_stokes_df(const __grid_constant__ 
     const ht wjp = w_at(Tw, ic, false, 1.f, j + 1);
     const ht w0 = at(Tw, j, ic);
     txz = ht_mul(at(tile(t, DF_MU_XZ), j, iff),
-                 ht_add(ht_k(ht_sub(u_hi, u_lo), ihz, pzk), ht_k(ht_sub(wc, wm), ihx, pxk)));
-    tyz = ht_mul(at(Te, j, ic), ht_add(ht_k(ht_sub(v_hi, v_lo), ihz, pzk), ht_k(ht_sub(w0, wjm), ihy, pyk)));
-    tyzj = ht_mul(at(Te, j + 1, ic), ht_add(ht_k(ht_sub(vj_hi, vj_lo), ihz, pzk), ht_k(ht_sub(wjp, w0), ihy, pyk)));
+                 ht_add(hk<P2>(ht_sub(u_hi, u_lo), ihz, pzk), hk<P2>(ht_sub(wc, wm), ihx, pxk)));
+    tyz = ht_mul(at(Te, j, ic), ht_add(hk<P2>(ht_sub(v_hi, v_lo), ihz, pzk), hk<P2>(ht_sub(w0, wjm), ihy, pyk)));
+    tyzj = ht_mul(at(Te, j + 1, ic), ht_add(hk<P2>(ht_sub(vj_hi, vj_lo), ihz, pzk), hk<P2>(ht_sub(wjp, w0), ihy, pyk)));
   };
 
   // ---- prologue: fields at level k0 (ring 1), z-edges at level k0, stresses of k0 - 1 (ring 0)
@@ -263,9 +275,9 @@ __global__ void __launch_bounds__(32 * FBY) k_stokes_df(const __grid_constant__ 
     const ht vjx = hiX ? ht_sgn(vj_k, bxh) : vj_k;
     const ht vm = ht_sgn(at(TV, j, icm), loX ? bxl : 1.f);
     const ht vjm = ht_sgn(at(TV, j + 1, icm), loX ? bxl : 1.f);
-    const ht txy = ht_mul(at(TE, j, iff), ht_add(ht_k(ht_sub(u_k, u_jm), ihy, pyk), ht_k(ht_sub(vx, vm), ihx, pxk)));
+    const ht txy = ht_mul(at(TE, j, iff), ht_add(hk<P2>(ht_sub(u_k, u_jm), ihy, pyk), hk<P2>(ht_sub(vx, vm), ihx, pxk)));
     const ht txyj =
-        ht_mul(at(TE, j + 1, iff), ht_add(ht_k(ht_sub(u_jp, u_k), ihy, pyk), ht_k(ht_sub(vjx, vjm), ihx, pxk)));
+        ht_mul(at(TE, j + 1, iff), ht_add(hk<P2>(ht_sub(u_jp, u_k), ihy, pyk), hk<P2>(ht_sub(vjx, vjm), ihx, pxk)));
     // ---- neighbours along x from the adjacent lanes
     const ht nxx_im = shfl_up1(nxx);
     const ht txy_ip = shfl_down1(txy);
@@ -276,12 +288,12 @@ __global__ void __launch_bounds__(32 * FBY) k_stokes_df(const __grid_constant__ 
       // u-row at x-face i
       double out = 0.0;
       if (i > 0 && i < nx) {
-        const ht L = ht_add(ht_add(ht_k(ht_sub(nxx, nxx_im), K.two_ih2[0], (K.pw >> 3) & 1),
-                                   ht_k(ht_sub(txyj, txy), ihy, pyk)),
-                            ht_k(ht_sub(txz_kp, txz_k), ihz, pzk));
+        const ht L = ht_add(ht_add(hk<P2>(ht_sub(nxx, nxx_im), K.two_ih2[0], (K.pw >> 3) & 1),
+                                   hk<P2>(ht_sub(txyj, txy), ihy, pyk)),
+                            hk<P2>(ht_sub(txz_kp, txz_k), ihz, pzk));
         const ht rq = ht_mul(at(tile(t, DF_RHO_X), j, iff), u_k);
-        const ht gp = ht_k(ht_sub(p_k, at(TP, j, ic - 1)), ihx, pxk);
-        out = row_out(K, rq, gp, L);
+        const ht gp = hk<P2>(ht_sub(p_k, at(TP, j, ic - 1)), ihx, pxk);
+        out = row_out<P2>(K, rq, gp, L);
       }
       yu[iff + j * su1 + k * su2] = out;
     }
@@ -290,42 +302,42 @@ __global__ void __launch_bounds__(32 * FBY) k_stokes_df(const __grid_constant__ 
       // v-row at y-face j (face 0 and face ny are walls)
       double out = 0.0;
       if (j > 0) {
-        const ht L = ht_add(ht_add(ht_k(ht_sub(nyy, nyy_m), K.two_ih2[1], (K.pw >> 4) & 1),
-                                   ht_k(ht_sub(txy_ip, txy), ihx, pxk)),
-                            ht_k(ht_sub(tyz_kp, tyz_k), ihz, pzk));
+        const ht L = ht_add(ht_add(hk<P2>(ht_sub(nyy, nyy_m), K.two_ih2[1], (K.pw >> 4) & 1),
+                                   hk<P2>(ht_sub(txy_ip, txy), ihx, pxk)),
+                            hk<P2>(ht_sub(tyz_kp, tyz_k), ihz, pzk));
         const ht rq = ht_mul(at(tile(t, DF_RHO_Y), j, ic), v_k);
-        const ht gp = ht_k(ht_sub(p_k, at(TP, j - 1, ic)), ihy, pyk);
-        out = row_out(K, rq, gp, L);
+        const ht gp = hk<P2>(ht_sub(p_k, at(TP, j - 1, ic)), ihy, pyk);
+        out = row_out<P2>(K, rq, gp, L);
       }
       yv[ic + j * sv1 + k * sv2] = out;
       if (j == ny - 1) yv[ic + ny * sv1 + k * sv2] = 0.0;
       // w-row at z-face k (face 0 and face nz are walls)
       out = 0.0;
       if (k > 0) {
-        const ht L = ht_add(ht_add(ht_k(ht_sub(nzz, nzz_km1), K.two_ih2[2], (K.pw >> 5) & 1),
-                                   ht_k(ht_sub(txz_ip, txz_k), ihx, pxk)),
-                            ht_k(ht_sub(tyzj_k, tyz_k), ihy, pyk));
+        const ht L = ht_add(ht_add(hk<P2>(ht_sub(nzz, nzz_km1), K.two_ih2[2], (K.pw >> 5) & 1),
+                                   hk<P2>(ht_sub(txz_ip, txz_k), ihx, pxk)),
+                            hk<P2>(ht_sub(tyzj_k, tyz_k), ihy, pyk));
         const ht rq = ht_mul(at(tile(t, DF_RHO_Z), j, ic), w_k);
-        const ht gp = ht_k(ht_sub(p_k, p_km1), ihz, pzk);
-        out = row_out(K, rq, gp, L);
+        const ht gp = hk<P2>(ht_sub(p_k, p_km1), ihz, pzk);
+        out = row_out<P2>(K, rq, gp, L);
       }
       yw[cb] = out;
       if (k == nz - 1 && !K.open_top) yw[cb + sc2] = 0.0;
       // continuity row at the cell
-      const ht dq = ht_add(ht_add(ht_k(ht_sub(u_ip, u_k), ihx, pxk), ht_k(ht_sub(vj_k, v_k), ihy, pyk)),
-                           ht_k(ht_sub(w_kp, w_k), ihz, pzk));
+      const ht dq = ht_add(ht_add(hk<P2>(ht_sub(u_ip, u_k), ihx, pxk), hk<P2>(ht_sub(vj_k, v_k), ihy, pyk)),
+                           hk<P2>(ht_sub(w_kp, w_k), ihz, pzk));
       yp[cb] = -ht_dbl(dq);
     }
     if (k == nz - 1 && K.open_top) {
       // w-row at the open top's face nz (warp-uniform branch: all lanes shuffle)
       const ht txz_kp_ip = shfl_down1(txz_kp);
       if (jrow && lane_rows && cI) {
-        const ht L = ht_add(ht_add(ht_k(ht_sub(ht_sgn(nzz, -1.f), nzz), K.two_ih2[2], (K.pw >> 5) & 1),
-                                   ht_k(ht_sub(txz_kp_ip, txz_kp), ihx, pxk)),
-                            ht_k(ht_sub(tyzj_kp, tyz_kp), ihy, pyk));
+        const ht L = ht_add(ht_add(hk<P2>(ht_sub(ht_sgn(nzz, -1.f), nzz), K.two_ih2[2], (K.pw >> 5) & 1),
+                                   hk<P2>(ht_sub(txz_kp_ip, txz_kp), ihx, pxk)),
+                            hk<P2>(ht_sub(tyzj_kp, tyz_kp), ihy, pyk));
         const ht rq = ht_mul(at(tile(tp, DF_RHO_Z), j, ic), w_kp);
-        const ht gp = ht_k(ht_sub(ht_sgn(p_k, -1.f), p_k), ihz, pzk);
-        yw[ic + j * sc1 + nz * sc2] = row_out(K, rq, gp, L);
+        const ht gp = hk<P2>(ht_sub(ht_sgn(p_k, -1.f), p_k), ihz, pzk);
+        yw[ic + j * sc1 + nz * sc2] = row_out<P2>(K, rq, gp, L);
       }
     }
     // ---- carry to level k + 1
@@ -514,14 +526,20 @@ void launch_stokes_df(const GridDev& g, const DfOperands& o, double theta, const
   k.open_top = g.open_top;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_stokes_df, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaFuncSetAttribute(k_stokes_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaFuncSetAttribute(k_stokes_df<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     attr = true;
   }
   dim3 grid(cdiv(g.n[0] + 1, FX), cdiv(g.n[1], FBY), cdiv(g.n[2], FKC));
+  const DfMaps& m = *static_cast<const DfMaps*>(o.maps);
   ktimer_begin(KC_STOKES, st);
-  { k_stokes_df<<<grid, dim3(32, FBY), SMEM_BYTES, st>>>(*static_cast<const DfMaps*>(o.maps), k, y + pk.off[0],
-                                                         y + pk.off[1], y + pk.off[2], y + pk.off[3], err);
-    WSI_COUNT(); }
+  if (k.pw == 0x7Fu)
+    k_stokes_df<true><<<grid, dim3(32, FBY), SMEM_BYTES, st>>>(m, k, y + pk.off[0], y + pk.off[1], y + pk.off[2],
+                                                               y + pk.off[3], err);
+  else
+    k_stokes_df<false><<<grid, dim3(32, FBY), SMEM_BYTES, st>>>(m, k, y + pk.off[0], y + pk.off[1], y + pk.off[2],
+                                                                y + pk.off[3], err);
+  WSI_COUNT();
   ktimer_end(KC_STOKES, st);
 }
 
