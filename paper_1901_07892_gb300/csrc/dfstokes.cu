@@ -167,8 +167,9 @@ __global__ void __launch_bounds__(32 * FBY) k_stokes_df(const __grid_constant__ 
   auto wait = [&](int t) {
     if (!tma::mbar_wait(bar0 + 8 * (t % NST), (t / NST) & 1)) ok = false;
   };
-  // tile of array a in ring level t, and its element at grid row jj, column ii
-  auto tile = [&](int t, int a) -> const float2* { return dsm + ((t % NST) * DF_NARR + a) * TILE; };
+  // slot of ring level t, tile of array a in it, and its element at grid row jj, column ii
+  auto slot = [&](int t) -> const float2* { return dsm + (t % NST) * STAGE; };
+  auto tile = [&](const float2* S, int a) -> const float2* { return S + a * TILE; };
   auto at = [&](const float2* T, int jj, int ii) -> ht { return ht_of(T[(jj - ys) * TX + (ii - xs)]); };
 
   const bool cI = i >= 0 && i < nx;  // a cell column
@@ -194,15 +195,16 @@ __global__ void __launch_bounds__(32 * FBY) k_stokes_df(const __grid_constant__ 
   // shear stresses on the z-level edges of ring level t from the fields at the
   // level below (lo) and at it (hi), ghosts already applied:
   // xz at (i, j), yz at (i, j) and at (i, j + 1)
-  auto zedges = [&](int t, ht u_lo, ht u_hi, ht v_lo, ht v_hi, ht vj_lo, ht vj_hi, ht& txz, ht& tyz, ht& tyzj) {
-    const float2* Tw = tile(t, DF_W);
-    const float2* Te = tile(t, DF_MU_YZ);
+  auto zedges = [&](const float2* S, ht u_lo, ht u_hi, ht v_lo, ht v_hi, ht vj_lo, ht vj_hi, ht& txz, ht& tyz,
+                    ht& tyzj) {
+    const float2* Tw = tile(S, DF_W);
+    const float2* Te = tile(S, DF_MU_YZ);
     const ht wc = w_at(Tw, ic, hiX, bxh, j);   // w at column i (x-edge column; ghost at i = nx)
     const ht wm = w_at(Tw, icm, loX, bxl, j);  // w at column i - 1
     const ht wjm = w_at(Tw, ic, false, 1.f, j - 1);
     const ht wjp = w_at(Tw, ic, false, 1.f, j + 1);
     const ht w0 = at(Tw, j, ic);
-    txz = ht_mul(at(tile(t, DF_MU_XZ), j, iff),
+    txz = ht_mul(at(tile(S, DF_MU_XZ), j, iff),
                  ht_add(hk<P2>(ht_sub(u_hi, u_lo), ihz, pzk), hk<P2>(ht_sub(wc, wm), ihx, pxk)));
     tyz = ht_mul(at(Te, j, ic), ht_add(hk<P2>(ht_sub(v_hi, v_lo), ihz, pzk), hk<P2>(ht_sub(w0, wjm), ihy, pyk)));
     tyzj = ht_mul(at(Te, j + 1, ic), ht_add(hk<P2>(ht_sub(vj_hi, vj_lo), ihz, pzk), hk<P2>(ht_sub(wjp, w0), ihy, pyk)));
@@ -211,55 +213,59 @@ __global__ void __launch_bounds__(32 * FBY) k_stokes_df(const __grid_constant__ 
   // ---- prologue: fields at level k0 (ring 1), z-edges at level k0, stresses of k0 - 1 (ring 0)
   wait(0);
   wait(1);
-  ht u_k = at(tile(1, DF_U), j, iff);
-  ht v_k = at(tile(1, DF_V), j, ic);
-  ht vj_k = at(tile(1, DF_V), j + 1, ic);
-  ht w_k = at(tile(1, DF_W), j, ic);
+  const float2* S0 = slot(0);
+  const float2* S1 = slot(1);
+  ht u_k = at(tile(S1, DF_U), j, iff);
+  ht v_k = at(tile(S1, DF_V), j, ic);
+  ht vj_k = at(tile(S1, DF_V), j + 1, ic);
+  ht w_k = at(tile(S1, DF_W), j, ic);
   ht txz_k, tyz_k, tyzj_k;
   ht nzz_km1{0.f, 0.f}, p_km1{0.f, 0.f};
   {
     ht u_m, v_m, vj_m;
     if (k0 > 0) {
-      u_m = at(tile(0, DF_U), j, iff);
-      v_m = at(tile(0, DF_V), j, ic);
-      vj_m = at(tile(0, DF_V), j + 1, ic);
-      const ht w_m = at(tile(0, DF_W), j, ic);
-      nzz_km1 = ht_mul(at(tile(0, DF_MU_CC), j, ic), ht_sub(w_k, w_m));
-      p_km1 = at(tile(0, DF_P), j, ic);
+      u_m = at(tile(S0, DF_U), j, iff);
+      v_m = at(tile(S0, DF_V), j, ic);
+      vj_m = at(tile(S0, DF_V), j + 1, ic);
+      const ht w_m = at(tile(S0, DF_W), j, ic);
+      nzz_km1 = ht_mul(at(tile(S0, DF_MU_CC), j, ic), ht_sub(w_k, w_m));
+      p_km1 = at(tile(S0, DF_P), j, ic);
     } else {
       u_m = ht_sgn(u_k, bzl);
       v_m = ht_sgn(v_k, bzl);
       vj_m = ht_sgn(vj_k, bzl);
     }
-    zedges(1, u_m, u_k, v_m, v_k, vj_m, vj_k, txz_k, tyz_k, tyzj_k);
+    zedges(S1, u_m, u_k, v_m, v_k, vj_m, vj_k, txz_k, tyz_k, tyzj_k);
   }
   __syncthreads();  // ring slot 0 is free
   if (tid == 0 && NST <= tmax) issue(NST);
 
   for (int k = k0; k < k1; ++k) {
     const int t = k - k0 + 1, tp = t + 1;  // ring levels of k and k + 1
+    const float2* Sk = slot(t);
+    const float2* Sp = slot(tp);
     wait(tp);
     // ---- level k + 1: fields and z-edge shear stresses
     ht u_kp, v_kp, vj_kp;
     if (k + 1 < nz) {
-      u_kp = at(tile(tp, DF_U), j, iff);
-      v_kp = at(tile(tp, DF_V), j, ic);
-      vj_kp = at(tile(tp, DF_V), j + 1, ic);
+      u_kp = at(tile(Sp, DF_U), j, iff);
+      v_kp = at(tile(Sp, DF_V), j, ic);
+      vj_kp = at(tile(Sp, DF_V), j + 1, ic);
     } else {
       u_kp = ht_sgn(u_k, bzh);
       v_kp = ht_sgn(v_k, bzh);
       vj_kp = ht_sgn(vj_k, bzh);
     }
-    const ht w_kp = at(tile(tp, DF_W), j, ic);
+    const ht w_kp = at(tile(Sp, DF_W), j, ic);
     ht txz_kp, tyz_kp, tyzj_kp;
-    zedges(tp, u_k, u_kp, v_k, v_kp, vj_k, vj_kp, txz_kp, tyz_kp, tyzj_kp);
+    zedges(Sp, u_k, u_kp, v_k, v_kp, vj_k, vj_kp, txz_kp, tyz_kp, tyzj_kp);
 
     // ---- level k: normal stresses and the xy shear stresses at rows j, j + 1
-    const float2* TU = tile(t, DF_U);
-    const float2* TV = tile(t, DF_V);
-    const float2* TP = tile(t, DF_P);
-    const float2* TM = tile(t, DF_MU_CC);
-    const float2* TE = tile(t, DF_MU_XY);
+    const float2* TU = tile(Sk, DF_U);
+    const float2* TV = tile(Sk, DF_V);
+    const float2* TP = tile(Sk, DF_P);
+    const float2* TM = tile(Sk, DF_MU_CC);
+    const float2* TE = tile(Sk, DF_MU_XY);
     const ht mu_c = at(TM, j, ic);
     const ht u_ip = at(TU, j, ifp);
     const ht nxx = ht_mul(mu_c, ht_sub(u_ip, u_k));
@@ -291,7 +297,7 @@ __global__ void __launch_bounds__(32 * FBY) k_stokes_df(const __grid_constant__ 
         const ht L = ht_add(ht_add(hk<P2>(ht_sub(nxx, nxx_im), K.two_ih2[0], (K.pw >> 3) & 1),
                                    hk<P2>(ht_sub(txyj, txy), ihy, pyk)),
                             hk<P2>(ht_sub(txz_kp, txz_k), ihz, pzk));
-        const ht rq = ht_mul(at(tile(t, DF_RHO_X), j, iff), u_k);
+        const ht rq = ht_mul(at(tile(Sk, DF_RHO_X), j, iff), u_k);
         const ht gp = hk<P2>(ht_sub(p_k, at(TP, j, ic - 1)), ihx, pxk);
         out = row_out<P2>(K, rq, gp, L);
       }
@@ -305,7 +311,7 @@ __global__ void __launch_bounds__(32 * FBY) k_stokes_df(const __grid_constant__ 
         const ht L = ht_add(ht_add(hk<P2>(ht_sub(nyy, nyy_m), K.two_ih2[1], (K.pw >> 4) & 1),
                                    hk<P2>(ht_sub(txy_ip, txy), ihx, pxk)),
                             hk<P2>(ht_sub(tyz_kp, tyz_k), ihz, pzk));
-        const ht rq = ht_mul(at(tile(t, DF_RHO_Y), j, ic), v_k);
+        const ht rq = ht_mul(at(tile(Sk, DF_RHO_Y), j, ic), v_k);
         const ht gp = hk<P2>(ht_sub(p_k, at(TP, j - 1, ic)), ihy, pyk);
         out = row_out<P2>(K, rq, gp, L);
       }
@@ -317,7 +323,7 @@ __global__ void __launch_bounds__(32 * FBY) k_stokes_df(const __grid_constant__ 
         const ht L = ht_add(ht_add(hk<P2>(ht_sub(nzz, nzz_km1), K.two_ih2[2], (K.pw >> 5) & 1),
                                    hk<P2>(ht_sub(txz_ip, txz_k), ihx, pxk)),
                             hk<P2>(ht_sub(tyzj_k, tyz_k), ihy, pyk));
-        const ht rq = ht_mul(at(tile(t, DF_RHO_Z), j, ic), w_k);
+        const ht rq = ht_mul(at(tile(Sk, DF_RHO_Z), j, ic), w_k);
         const ht gp = hk<P2>(ht_sub(p_k, p_km1), ihz, pzk);
         out = row_out<P2>(K, rq, gp, L);
       }
@@ -335,7 +341,7 @@ __global__ void __launch_bounds__(32 * FBY) k_stokes_df(const __grid_constant__ 
         const ht L = ht_add(ht_add(hk<P2>(ht_sub(ht_sgn(nzz, -1.f), nzz), K.two_ih2[2], (K.pw >> 5) & 1),
                                    hk<P2>(ht_sub(txz_kp_ip, txz_kp), ihx, pxk)),
                             hk<P2>(ht_sub(tyzj_kp, tyz_kp), ihy, pyk));
-        const ht rq = ht_mul(at(tile(tp, DF_RHO_Z), j, ic), w_kp);
+        const ht rq = ht_mul(at(tile(Sp, DF_RHO_Z), j, ic), w_kp);
         const ht gp = hk<P2>(ht_sub(ht_sgn(p_k, -1.f), p_k), ihz, pzk);
         yw[ic + j * sc1 + nz * sc2] = row_out<P2>(K, rq, gp, L);
       }
