@@ -391,8 +391,9 @@ enum { WSI_LEARN_OFF = 0, WSI_LEARN_REPLACE = 1, WSI_LEARN_AUGMENT = 2 };
 int wsi_attach_unet(wsi_ctx* ctx, wsi_unet* net, int level, int enable);
 int wsi_unet_train_sample(wsi_ctx* ctx, const double* e, double lr, double* loss);
 
-/* Learned initial guess for wsi_pressure_solve (BASELINE workload: the
- * network "supplies the initial guess"; not in the paper).
+/* Learned initial guess for wsi_pressure_solve (an extension of the
+ * learned pressure part: the network supplies the solve's starting iterate;
+ * not in the paper).
  * wsi_attach_unet_guess: a network sized for multigrid level `level` of this
  * (WSI_PREC_MIXED) context, or NULL to detach.  Its input is the level's
  * restriction (cell averages) of the right-hand side with log rho and phi
