@@ -165,3 +165,30 @@ def test_open_top_needs_no_slip_lid():
         Grid(4, 4, 4, bc=(NO_SLIP,) * 5 + (FREE_SLIP,), open_top=True)
     with pytest.raises(ValueError):
         Grid(4, 4, 1, open_top=True)
+
+
+def test_open_top_transport_ghost_is_even():
+    """Across the open top the transport mirrors w evenly (dw/dz = 0): for a
+    flow leaving downward through the top cell, with w halving from the top
+    face to the face below, the limiter's upwind point is the top face and its
+    far point the mirror image of the face below, i.e. a local extremum, so
+    the upper control-volume face of the last interior w-face carries the
+    first-order upwind value w_top (an odd mirror would feed the limiter a
+    monotone profile and give 0.917 w_below instead)."""
+    from oracle import transport
+    g = Grid(3, 3, 6, lx=0.6, ly=0.6, lz=1.2, open_top=True)
+    nz = g.nz
+    vel = [np.zeros(g.face_shape(c)) for c in range(3)]
+    w_below, w_top = -0.8, -0.4
+    vel[2][1:nz - 1] = -1.0
+    vel[2][nz - 1] = w_below
+    vel[2][nz] = w_top
+    rho = [np.ones(g.face_shape(c)) for c in range(3)]
+    C = transport.convective(g, vel, rho)
+    # the z-flux divergence of the w-face below the top: upper CV face (top
+    # cell) minus lower CV face (the cell below it), over hz; u = v = 0
+    adv_hi = 0.5 * (w_below + w_top)
+    adv_lo = 0.5 * (-1.0 + w_below)
+    lo = adv_lo * transport.cui(w_top, w_below, -1.0)  # adv_lo < 0: upwind from above
+    expected = (adv_hi * w_top - lo) / g.hz
+    assert np.allclose(C[2][nz - 1], expected, rtol=1e-14)
