@@ -42,7 +42,7 @@ FP64_PEAK_DERIVED_GFLOPS = 152 * 2 * 2 * 2.07
 # DRAM bytes per cell of one launch, measured with ncu at 128^3 (dram__bytes_read.sum +
 # dram__bytes_write.sum, profiles/k_stokes_df_tank128.md) for the current kernel revision;
 # scaled by the cells of the workload (empty while no capture of the current revision exists)
-TRAFFIC_PER_CELL = {("stokes", "mixed"): (199.671296e6 + 45.277952e6) / 128 ** 3}
+TRAFFIC_PER_CELL = {("stokes", "mixed"): (200.392192e6 + 46.134528e6) / 128 ** 3}
 KCLASS = {"stokes": 0, "rbgs_p": 1, "rbgs_v": 2, "transport": 3, "mdot": 4, "maxpy": 5, "restrict": 6,
           "prolong": 7, "reinit": 8}
 

@@ -50,11 +50,11 @@
 namespace wsi {
 
 static constexpr int FX = 30;    // x-positions written per warp (32 lanes, one halo lane each side)
-static constexpr int FBY = 8;    // warps (y-rows) per block
+static constexpr int FBY = 4;    // warps (y-rows) per block
 static constexpr int FKC = 16;   // z-levels per block
 static constexpr int TX = 34;    // tile columns: x = FX bx - 2 .. FX bx + 31
 static constexpr int TY = FBY + 2;  // tile rows: y = FBY by - 1 .. FBY by + FBY
-static constexpr int TILE = 352;    // float2 slots per tile (TX TY = 340, padded to a multiple of 128 bytes)
+static constexpr int TILE = 208;    // float2 slots per tile (TX TY = 204, padded to a multiple of 128 bytes)
 static constexpr int NST = 3;       // levels in the ring: two read, one in flight
 static constexpr int STAGE = DF_NARR * TILE;
 static constexpr int SMEM_BYTES = NST * STAGE * 8 + NST * 8;
